@@ -1,0 +1,184 @@
+"""Python access to the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  The oracle exists to check the CUDA library; only
+the tests, the smoke check and the CPU-baseline leg of the benchmark use it.
+It is independent of the CUDA path: it neither imports nor links anything from
+the library package, and the library never imports it.
+
+Array layout (numpy complex128, C-contiguous):
+    links   (V, 4, 3, 3)        U[s][mu][a][b]
+    block   (V, 4, 3, L)        psi[s][spin][colour][rhs]
+Every function follows arXiv:1104.0737; see oracle.c for the passage each
+one restates.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_dbl_p = ctypes.POINTER(ctypes.c_double)
+_int_p = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))
+    ):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=gnu11", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        lib.oracle_gamma.argtypes = [_dbl_p]
+        lib.oracle_gamma.restype = None
+        lib.oracle_apply_D.argtypes = [_int_p, _dbl_p, ctypes.c_double, _dbl_p, _dbl_p, ctypes.c_int]
+        lib.oracle_domain_colour.argtypes = [_int_p, _int_p, ctypes.c_int]
+        lib.oracle_sap.argtypes = [_int_p, _int_p, _dbl_p, ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, _dbl_p, _dbl_p, _dbl_p,
+                                   ctypes.c_int]
+        lib.oracle_qr_mgs.argtypes = [_dbl_p, ctypes.c_long, ctypes.c_int, _dbl_p]
+        lib.oracle_lu_solve.argtypes = [_dbl_p, _dbl_p, ctypes.c_int, ctypes.c_int]
+        lib.oracle_block_bicgstab.argtypes = [
+            _int_p, _dbl_p, ctypes.c_double, _dbl_p, _dbl_p, ctypes.c_int, ctypes.c_double,
+            ctypes.c_int, ctypes.c_int, _dbl_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            _int_p, _dbl_p, ctypes.c_int, _int_p, _dbl_p]
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(_dbl_p) if a is not None else None
+
+
+def _ivec(v):
+    return (ctypes.c_int * 4)(*[int(x) for x in v])
+
+
+def _cplx(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def num_threads() -> int:
+    return _load().oracle_num_threads()
+
+
+def gamma() -> np.ndarray:
+    """gamma_1..gamma_4 of the chiral basis, shape (4, 4, 4)."""
+    g = np.zeros((4, 4, 4), dtype=np.complex128)
+    _load().oracle_gamma(_dp(g))
+    return g
+
+
+def domain_colour(dims, block) -> np.ndarray:
+    """Colour (0 = E, 1 = O) of the SAP domain of every site."""
+    lib = _load()
+    V = int(np.prod(dims))
+    d, b = _ivec(dims), _ivec(block)
+    return np.array([lib.oracle_domain_colour(d, b, s) for s in range(V)], dtype=np.int32)
+
+
+def apply_D(dims, U, kappa: float, psi) -> np.ndarray:
+    """A psi for the Wilson-Dirac matrix A (Sec. 2.1), column by column."""
+    V = int(np.prod(dims))
+    U = _cplx(U, (V, 4, 3, 3))
+    psi = _cplx(psi)
+    if psi.ndim != 4 or psi.shape[:3] != (V, 4, 3):
+        raise ValueError("psi must have shape (V, 4, 3, L)")
+    out = np.empty_like(psi)
+    rc = _load().oracle_apply_D(_ivec(dims), _dp(U), float(kappa), _dp(psi), _dp(out), psi.shape[3])
+    if rc != 0:
+        raise ValueError(f"oracle_apply_D returned {rc}")
+    return out
+
+
+MR_COLUMN, MR_BLOCK, MR_FROZEN = 0, 1, 2
+
+
+def sap(dims, block, U, kappa: float, ncycle: int, nmr: int, eta, mr_mode: int = MR_COLUMN,
+        omega_table=None) -> np.ndarray:
+    """psi = M_SAP eta (Sec. 2.2) with nmr-step MR domain solves.
+
+    mr_mode 0: step lengths per domain and column; 1: per domain, shared by the
+    columns (recorded into omega_table if given); 2: taken from omega_table.
+    omega_table: complex array (ncycle, 2, nmr, n_domains)."""
+    V = int(np.prod(dims))
+    U = _cplx(U, (V, 4, 3, 3))
+    eta = _cplx(eta)
+    out = np.empty_like(eta)
+    if omega_table is not None:
+        nd = V // int(np.prod(block))
+        if (omega_table.dtype != np.complex128 or not omega_table.flags.c_contiguous
+                or omega_table.shape != (ncycle, 2, nmr, nd)):
+            raise ValueError("omega_table must be a C-contiguous complex128 (ncycle, 2, nmr, nd) array")
+    rc = _load().oracle_sap(_ivec(dims), _ivec(block), _dp(U), float(kappa), int(ncycle),
+                            int(nmr), int(mr_mode), _dp(omega_table), _dp(eta), _dp(out),
+                            eta.shape[3])
+    if rc != 0:
+        raise ValueError(f"oracle_sap returned {rc}")
+    return out
+
+
+def qr_mgs(P):
+    """P = Q gamma by modified Gram-Schmidt.  P: (N, L).  Returns (Q, gamma)."""
+    Q = _cplx(P).copy()
+    N, L = Q.shape
+    g = np.zeros((L, L), dtype=np.complex128)
+    rc = _load().oracle_qr_mgs(_dp(Q), N, L, _dp(g))
+    if rc != 0:
+        raise np.linalg.LinAlgError(f"oracle_qr_mgs returned {rc}")
+    return Q, g
+
+
+def lu_solve(G, C) -> np.ndarray:
+    """Solve G X = C by LU with partial pivoting.  G: (L, L), C: (L, M)."""
+    G = _cplx(G)
+    X = _cplx(C).copy()
+    rc = _load().oracle_lu_solve(_dp(G), _dp(X), G.shape[0], X.shape[1])
+    if rc != 0:
+        raise np.linalg.LinAlgError(f"oracle_lu_solve returned {rc}")
+    return X
+
+
+def block_bicgstab(dims, U, kappa: float, B, tol: float, max_iter: int = 1000, X0=None,
+                   rtilde=None, ncycle: int = 0, nmr: int = 0, block=None,
+                   mr_mode: int = MR_COLUMN, history_len: int | None = None) -> dict:
+    """Algorithm 1 of Sec. 2.1.  Returns dict(X, iters, status, history, true_res)."""
+    V = int(np.prod(dims))
+    U = _cplx(U, (V, 4, 3, 3))
+    B = _cplx(B)
+    L = B.shape[3]
+    X = np.zeros_like(B) if X0 is None else _cplx(X0).copy()
+    rt = None if rtilde is None else _cplx(rtilde, B.shape)
+    hl = max_iter if history_len is None else history_len
+    hist = np.zeros(max(hl, 1))
+    iters = ctypes.c_int(0)
+    tres = np.zeros(L)
+    blk = _ivec(block if block is not None else (1, 1, 1, 1))
+    rc = _load().oracle_block_bicgstab(
+        _ivec(dims), _dp(U), float(kappa), _dp(B), _dp(X), L, float(tol), int(max_iter),
+        int(X0 is not None), _dp(rt), int(ncycle), int(nmr), int(mr_mode), blk, _dp(hist), hl,
+        ctypes.byref(iters), _dp(tres))
+    if rc < 0:
+        raise ValueError(f"oracle_block_bicgstab returned {rc}")
+    k = iters.value
+    return dict(X=X, iters=k, status=rc, history=hist[:min(k, hl)].copy(), true_res=tres)
