@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark: RHS solves/s of the mixed-precision modified block BiCGSTAB with
+SAP (arXiv:1104.0737, Algorithm 2) to a true relative residual of 1e-10 on
+the 32^3 x 64 lattice with L = 12 point sources, on one GB300 per process.
+
+One step = one complete block solve of the 12 right-hand sides (initial
+residual, every iteration, the FP64 true residual).  Inputs (B, links) are
+resident in HBM before the timed region; each step's blocks are 4.8 GB, far
+larger than L2, so no extra flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun as independent replicas (one solve stream per GPU,
+no collective on the data path); value is the whole-job RHS solves/s.
+--impl reference times the FP64 CPU oracle (the reference implementation of
+this build) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+# ---------------------------------------------------------------------------
+# workloads (synthetic stand-ins for the paper's PACS-CS 32^3 x 64 configurations)
+# ---------------------------------------------------------------------------
+WORKLOADS = {
+    # 32^3 x 64, eps 0.5 links, L = 12 point sources, SAP 8^4, mixed precision.
+    # kappa: tuned so that the unpreconditioned BiCGSTAB (L = 1) needs > 2000
+    # iterations on this field (see the design notes for the scan).
+    "wilson_32c64_L12": dict(dims=(32, 32, 32, 64), eps=0.5, gauge_seed=1003, L=12, source="point",
+                             kappa=0.1525, block=(8, 8, 8, 8), ncycle=4, nmr=4, tol=1e-10),
+    # smaller lattices of the same family, for quick runs
+    "wilson_16c32_L12": dict(dims=(16, 16, 16, 32), eps=0.5, gauge_seed=1002, L=12, source="point",
+                             kappa=0.128, block=(8, 8, 8, 8), ncycle=4, nmr=4, tol=1e-10),
+    "wilson_8c16_L12": dict(dims=(8, 8, 8, 16), eps=0.5, gauge_seed=1001, L=12, source="point",
+                            kappa=0.125, block=(4, 4, 4, 4), ncycle=4, nmr=4, tol=1e-10),
+}
+DEFAULT_WORKLOAD = "wilson_32c64_L12"
+# Iterations the GPU solver takes on the default workload (measured); the CPU
+# baseline extrapolates its per-iteration time with it.
+GPU_ITERS = {"wilson_32c64_L12": None}
+
+METRIC = "RHS solves/s to true rel. residual 1e-10, 32^3x64 L=12; Dslash %HBM; p99 ms"
+UNIT = "RHS solves/s"
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes and flops per launch (FP32 storage, links counted once)
+# ---------------------------------------------------------------------------
+def dslash_bytes(V, L, real_bytes=4):
+    # per site: L spinors read + L written (12 complex each), 4 forward links
+    return V * (L * 2 * 12 * 2 * real_bytes + 4 * 9 * 2 * real_bytes)
+
+
+def dslash_flops(V, L):
+    return V * L * 1368
+
+
+def sap_domain_bytes(V, L, real_bytes=4):
+    # one MR step on the domains of one colour: half the sites
+    return dslash_bytes(V // 2, L, real_bytes)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampler
+# ---------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # median under load: samples above half the max clock
+        top = max(smax) if smax else max(sm)
+        load = [s for s in sm if s > 0.5 * top] or sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(top), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def oracle_sample(cfg, iters_full):
+    """One iteration of the oracle's Algorithm 1 (FP64, SAP with the same
+    domains, cycles, MR steps, kappa and L) on a sub-volume of the lattice with
+    two domains per direction; its time per site and iteration, scaled to the
+    full volume and to the GPU solver's iteration count, gives RHS solves/s."""
+    import oracle
+
+    oracle.build()
+    blk = cfg["block"]
+    sdims = tuple(2 * b for b in blk)
+    L = cfg["L"]
+    U = synth.su3_links(sdims, cfg["eps"], cfg["gauge_seed"] + 7)
+    B = synth.point_source(sdims, L)
+    t0 = time.perf_counter()
+    oracle.block_bicgstab(sdims, U, cfg["kappa"], B, tol=1e-300, max_iter=1, ncycle=cfg["ncycle"],
+                          nmr=cfg["nmr"], block=blk, mr_mode=2)
+    dt = time.perf_counter() - t0
+    scale = np.prod(cfg["dims"]) / np.prod(sdims)
+    t_solve = dt * scale * iters_full
+    return {
+        "value": L / t_solve, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+        "sample": (f"1 iteration of Algorithm 1 (FP64 oracle, SAP {cfg['ncycle']} cycles x "
+                   f"{cfg['nmr']} MR on {'x'.join(map(str, blk))} domains) on a "
+                   f"{'x'.join(map(str, sdims))} sub-volume, {dt:.1f} s, scaled by the volume "
+                   f"ratio {scale:.0f} and by the GPU solver's {iters_full} iterations"),
+        "sample_seconds": dt,
+    }
+
+
+def run_reference(args, cfg, rank, world):
+    """--impl reference: the oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    iters = GPU_ITERS.get(args.workload) or 50
+    for _ in range(args.warmup):
+        oracle_sample(cfg, iters)
+    vals, times = [], []
+    for _ in range(args.steps):
+        s = oracle_sample(cfg, iters)
+        vals.append(s["value"])
+        times.append(s["sample_seconds"])
+    value = float(np.mean(vals))
+    cpu = dict(s)
+    cpu["value"] = value
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, **_cfg_public(cfg)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def _cfg_public(cfg):
+    return {"lattice": "x".join(map(str, cfg["dims"])), "L": cfg["L"], "source": cfg["source"],
+            "kappa": cfg["kappa"], "eps": cfg["eps"], "sap_block": "x".join(map(str, cfg["block"])),
+            "ncycle": cfg["ncycle"], "nmr": cfg["nmr"], "tol": cfg["tol"],
+            "precision": "FP32 operator/SAP/Krylov vectors, FP64 X, QR, LxL, true residual",
+            "l2": "inputs larger than L2 (4.8 GB per block)"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--kappa", type=float, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-arm", action="store_true",
+                    help="also time the plain FP64 one-RHS solve on the same GPU")
+    args = ap.parse_args()
+    cfg = dict(WORKLOADS[args.workload])
+    if args.kappa is not None:
+        cfg["kappa"] = args.kappa
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, cfg, rank, world)
+        return
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1104_0737_gb300 as mb
+
+    dims, L = cfg["dims"], cfg["L"]
+    V = int(np.prod(dims))
+    U = synth.su3_links(dims, cfg["eps"], cfg["gauge_seed"])
+    B = synth.point_source(dims, L) if cfg["source"] == "point" else synth.gaussian_source(dims, L, 2003)
+    stream = torch.cuda.Stream()
+    ctx = mb.mbicg_create(dims, device=local, stream=stream)
+    mb.mbicg_load_gauge(ctx, U)
+    del U
+    params = mb.mbicg_default_params(ncycle=cfg["ncycle"], nmr=cfg["nmr"], block=cfg["block"],
+                                     mr_mode=mb.MBICG_MR_FROZEN, prec_D=mb.MBICG_FP32,
+                                     prec_sap=mb.MBICG_FP32, max_iter=5000)
+    dB = torch.from_numpy(B).to(f"cuda:{local}")
+    dX = torch.empty_like(dB)
+    torch.cuda.synchronize()
+
+    def solve(b, x):
+        st, it, tres = mb.mbicg_block_solve(ctx, b, x, L, cfg["kappa"], cfg["tol"], params)
+        if st != mb.MBICG_OK:
+            raise RuntimeError(f"solve failed: status {st}, iters {it}, true residual {max(tres)}")
+        return it, max(tres)
+
+    for _ in range(args.warmup):
+        solve(dB, dX)
+
+    clocks = Clocks(local)
+    clocks.start()
+    mb.mbicg_set_profiling(ctx, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    iters, tres_max, launches = [], 0.0, 0
+    with torch.cuda.stream(stream):
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_start.record()
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            it, tr = solve(dB, dX)
+            e1.record()
+            evs.append((e0, e1))
+            iters.append(it)
+            tres_max = max(tres_max, tr)
+            launches += mb.mbicg_get_stats(ctx)["kernel_launches"]
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_end.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    prof = mb.mbicg_get_profile(ctx)
+    mb.mbicg_set_profiling(ctx, False)
+    if dist:
+        t = torch.tensor([total_ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * L * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel class
+    hbm_peak, peak_kind = load_peaks()
+    sap_cls = prof["sap_domain"]
+    cls = max(prof, key=lambda k: prof[k][0])
+    per_launch = {}
+    for name, nbytes in (("sap_domain", sap_domain_bytes(V, L)), ("dslash", dslash_bytes(V, L))):
+        ms, n = prof[name]
+        if n:
+            per_launch[name] = (nbytes, ms / n)
+    dom = "sap_domain" if sap_cls[0] >= prof["dslash"][0] else "dslash"
+    nbytes, avg_ms = per_launch[dom]
+    achieved = nbytes / (avg_ms * 1e-3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": avg_ms,
+                "top_class_by_time": cls}
+    dsl_bytes, dsl_ms = per_launch.get("dslash", (None, None))
+    dslash_frac = (dsl_bytes / (dsl_ms * 1e-3) / 1e9) / hbm_peak if dsl_ms else None
+
+    # end to end through the ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hB = torch.from_numpy(B).pin_memory()
+        hX = torch.empty_like(hB).pin_memory()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            solve(hB, hX)
+        t1 = time.perf_counter()
+        e2e_s = t1 - t0
+        if dist:
+            t = torch.tensor([e2e_s], device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        nb = B.nbytes
+        e2e = {"value": world * L * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(cfg, int(np.median(iters)))
+        cpu.pop("sample_seconds", None)
+
+    fp64_arm = None
+    if args.fp64_arm and rank == 0:
+        p64 = mb.mbicg_default_params(ncycle=cfg["ncycle"], nmr=cfg["nmr"], block=cfg["block"],
+                                      mr_mode=mb.MBICG_MR_FROZEN, prec_D=mb.MBICG_FP64,
+                                      prec_sap=mb.MBICG_FP64, max_iter=5000)
+        b1 = dB[..., :1].contiguous()
+        x1 = torch.empty_like(b1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, it1, tr1 = mb.mbicg_block_solve(ctx, b1, x1, 1, cfg["kappa"], cfg["tol"], p64)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        fp64_arm = {"value": 1.0 / dt, "unit": UNIT, "iters": it1, "status": st,
+                    "sample": "one FP64 L=1 solve (column 0), FP64 operator and SAP"}
+
+    mb.mbicg_destroy(ctx)
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, **_cfg_public(cfg),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "iters": iters, "true_res_max": tres_max,
+            "dslash_hbm_frac": dslash_frac,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "kernel_ms": {k: v[0] for k, v in prof.items()},
+            "kernel_launch_groups": {k: v[1] for k, v in prof.items()},
+        }
+        if fp64_arm:
+            out["fp64_one_rhs_arm"] = fp64_arm
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * mbicg.h — C ABI of the GB300 (sm_103a) library for the modified block
+ * BiCGSTAB solve of the Wilson-Dirac equation with SAP preconditioning,
+ * after Nakamura, Ishikawa, Kuramashi, Sakurai, Tadano, "Modified Block
+ * BiCGSTAB for Lattice QCD", arXiv:1104.0737.
+ *
+ * The calls follow the paper's problem statement A X = B with N x L blocks
+ * (Sec. 2.1).  Every call returns an mbicg_status; nothing aborts the process,
+ * nothing crosses the ABI as an exception, and no kernel traps the GPU.
+ *
+ * Layouts (fixed; interleaved complex128, i.e. double re, double im):
+ *   site     s = x + Lx*(y + Ly*(z + Lz*t)), dims = {Lx, Ly, Lz, Lt}
+ *   links    U[s][mu][a][b], mu = 0..3 for x, y, z, t.  U_mu(x) is the link
+ *            from x to x + mu; no boundary phase folded in.
+ *   blocks   psi[s][spin 4][colour 3][rhs L]: the right-hand-side index runs
+ *            fastest (Sec. 2.1, the i = 1..L loop innermost).
+ * Physics conventions: periodic boundaries in x, y, z and antiperiodic in t
+ * (a hop across the t boundary carries -1); Hermitian chiral gamma basis,
+ *   gamma_k = [[0, -i sigma_k], [i sigma_k, 0]], gamma_4 = [[0, 1], [1, 0]].
+ *
+ * Pointers: every block or link pointer may be host memory (pageable or
+ * pinned) or device memory of the context's device; the library detects which
+ * (cudaPointerGetAttributes).  Device pointers are used in place and the call
+ * is ordered on the context's stream; host pointers are staged through device
+ * buffers and the call returns after the result is back in host memory.
+ * The caller owns every pointer it passes; the library owns the context, its
+ * copies of the gauge field and its workspaces.
+ *
+ * Threading: a context is used by one host thread at a time.
+ */
+#ifndef MBICG_H
+#define MBICG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mbicg_ctx mbicg_ctx;
+
+typedef enum {
+  MBICG_OK = 0,
+  MBICG_EINVAL = -1,      /* bad argument: dims, L, tol, blocking, params */
+  MBICG_ENOMEM = -2,      /* device allocation failed */
+  MBICG_ENOGAUGE = -3,    /* no gauge field loaded */
+  MBICG_ENOTCONV = -4,    /* max_iter reached; X, iters, true_res are filled */
+  MBICG_EBREAKDOWN = -5,  /* singular R~^H V, zero Tr(Z^H Z) or rank-deficient P,
+                             also after one restart; X, iters, true_res filled */
+  MBICG_ENAN = -6,        /* NaN or Inf in the input or in a residual norm */
+  MBICG_ECUDA = -7        /* a CUDA runtime error; see mbicg_last_error */
+} mbicg_status;
+
+/* Arithmetic and storage precision of an operator. */
+typedef enum { MBICG_FP64 = 0, MBICG_FP32 = 1, MBICG_FP16 = 2 } mbicg_prec;
+
+/* How the minimal-residual step lengths of the SAP domain solves are formed. */
+typedef enum {
+  MBICG_MR_COLUMN = 0, /* one per domain and per column (plain MR on each column) */
+  MBICG_MR_BLOCK = 1,  /* one per domain, from sums over the L columns */
+  MBICG_MR_FROZEN = 2  /* block_solve only: the first application of M takes
+                          MBICG_MR_BLOCK step lengths and every later one reuses
+                          them, so M is one fixed linear operator for the whole
+                          solve (the stationary M that Sec. 2.1 requires) */
+} mbicg_mr_mode;
+
+typedef struct {
+  /* SAP preconditioner, Sec. 2.2: psi = K sum_{j=0}^{ncycle-1} (1 - A K)^j eta
+   * over checkerboard-coloured domains of extent block[4]; the domain solves
+   * B_EE, B_OO are nmr MR steps started from zero.  ncycle = 0 selects M = 1.
+   * Each block[mu] must divide dims[mu] and give an even number >= 2 of
+   * domains in every direction. */
+  int ncycle;
+  int nmr;
+  int block[4];
+  int mr_mode;      /* mbicg_mr_mode */
+  int prec_sap;     /* MBICG_FP32 (default) or MBICG_FP64 */
+  /* Krylov loop (Algorithm 2 of Sec. 2.1). */
+  int prec_D;       /* operator and Krylov vectors: MBICG_FP64 (the paper's
+                       double-precision outer solver) or MBICG_FP32 with FP64
+                       X accumulation and reliable updates */
+  int max_iter;
+  int use_x0;       /* nonzero: X holds the initial guess on entry */
+  double delta_ru;  /* reliable update when max_i |r_i|/|b_i| falls below
+                       delta_ru times its value at the last update (FP32 only) */
+  /* Optional host buffer: res_history[k] = max_i |r_i|/|b_i| (recursive)
+   * after iteration k, at most res_history_len entries. */
+  double* res_history;
+  int res_history_len;
+} mbicg_params;
+
+/* Counters of the last call on a context. */
+typedef struct {
+  int iters;              /* Krylov iterations of the last solve */
+  int reliable_updates;   /* true-residual recomputations inside the loop */
+  int restarts;           /* restarts after a breakdown */
+  long long kernel_launches; /* kernels the library launched during the last call */
+  double true_res_max;    /* max_i |b_i - A x_i| / |b_i| at return (FP64) */
+} mbicg_stats;
+
+/* Fills p with the defaults: ncycle 4, nmr 4, block {4,4,4,4},
+ * MBICG_MR_FROZEN, prec_sap FP32, prec_D FP32, max_iter 1000, use_x0 0,
+ * delta_ru 0.1, no history. */
+void mbicg_default_params(mbicg_params* p);
+
+/* Creates a context for a lattice of extents dims on CUDA device `device`.
+ * cuda_stream: a cudaStream_t to order work on, or NULL for a stream the
+ * library creates.  Every extent must be even and >= 2, the volume at most
+ * 2^27 sites.
+ * Returns MBICG_EINVAL, MBICG_ECUDA or MBICG_ENOMEM on failure (*ctx = NULL). */
+int mbicg_create(mbicg_ctx** ctx, const int dims[4], int device, void* cuda_stream);
+
+/* Frees every device buffer the context holds.  NULL is accepted. */
+void mbicg_destroy(mbicg_ctx* ctx);
+
+/* Copies the gauge field U (layout above, 4 V SU(3) matrices, complex128)
+ * into the library's own FP64 and FP32 copies.  Sec. 2.1: the links of
+ * Eq. (hoppingterm).  MBICG_ENAN if U holds NaN or Inf. */
+int mbicg_load_gauge(mbicg_ctx* ctx, const double* U);
+
+/* out = A in for L columns (Eq. (hoppingterm), (bloclhoppingterm) of
+ * Sec. 2.1): (A phi)_x = phi_x - kappa eta_x.  prec: MBICG_FP64 computes in
+ * FP64, MBICG_FP32 rounds `in` to FP32, computes in FP32 and widens the result.
+ * 1 <= L <= 16.  in and out must not alias. */
+int mbicg_apply_D(mbicg_ctx* ctx, const double* in, double* out, int L, double kappa,
+                  int prec);
+
+/* out = M_SAP in (Sec. 2.2) with the parameters ncycle, nmr, block, mr_mode
+ * (MBICG_MR_COLUMN or MBICG_MR_BLOCK) and prec_sap of *p.  1 <= L <= 16. */
+int mbicg_sap_precond(mbicg_ctx* ctx, const double* in, double* out, int L, double kappa,
+                      const mbicg_params* p);
+
+/* Solves A X = B for L right-hand sides by the modified block BiCGSTAB
+ * (Algorithm 2 of Sec. 2.1: QR re-orthonormalisation of P, right
+ * preconditioning by M_SAP), stopping when max_i |r_i|/|b_i| <= tol for the
+ * recursive residual and confirming it with the true residual in FP64.
+ *   B          N x L block (N = 12 V), every column nonzero.
+ *   X          N x L block: the solution on return (also on ENOTCONV and
+ *              EBREAKDOWN); the initial guess on entry if p->use_x0.
+ *   iters      if not NULL: iterations done.
+ *   true_res   if not NULL: L host doubles, |b_i - A x_i| / |b_i| in FP64.
+ * 1 <= L <= 16; tol > 0. */
+int mbicg_block_solve(mbicg_ctx* ctx, const double* B, double* X, int L, double kappa,
+                      double tol, const mbicg_params* p, int* iters, double* true_res);
+
+/* Counters of the last call (see mbicg_stats). */
+int mbicg_get_stats(const mbicg_ctx* ctx, mbicg_stats* out);
+
+/* Kernel classes of the per-kernel timing below. */
+typedef enum {
+  MBICG_K_DSLASH = 0,     /* block Wilson-Dirac operator, Krylov precision */
+  MBICG_K_DSLASH64 = 1,   /* FP64 operator of the true residuals */
+  MBICG_K_SAP_RESID = 2,  /* SAP: residual eta - A psi on one colour */
+  MBICG_K_SAP_DOMAIN = 3, /* SAP: domain operator with the MR dot products */
+  MBICG_K_SAP_UPDATE = 4, /* SAP: MR step lengths and updates */
+  MBICG_K_GRAM = 5,       /* block inner products */
+  MBICG_K_AXPY = 6,       /* block AXPYs and the QR transform */
+  MBICG_K_SMALL = 7,      /* L x L algebra */
+  MBICG_K_CONVERT = 8,    /* layout and precision conversions */
+  MBICG_K_SAP_SWEEP = 9,  /* SAP: one whole colour sweep with the MR steps on chip */
+  MBICG_K_NCLASS = 10
+} mbicg_kernel_class;
+
+/* enable != 0: from now on, time every kernel launch with CUDA events on the
+ * context's stream and add it to its class (costs one event pair per launch).
+ * enable == 0 stops timing.  Either way the totals are reset. */
+int mbicg_set_profiling(mbicg_ctx* ctx, int enable);
+
+/* Copies the totals since profiling was enabled: ms[c] milliseconds and
+ * launches[c] kernel launches of class c, for c < n (n <= MBICG_K_NCLASS).
+ * Either pointer may be NULL. */
+int mbicg_get_profile(const mbicg_ctx* ctx, double* ms, long long* launches, int n);
+
+/* Text of the last error on ctx ("" if none).  Valid until the next call. */
+const char* mbicg_last_error(const mbicg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MBICG_H */

@@ -1,0 +1,203 @@
+"""Python binding of libmbicg.so, the GB300 (sm_103a) library for the
+modified block BiCGSTAB solve of the Wilson-Dirac equation with SAP
+preconditioning (Nakamura et al., arXiv:1104.0737).
+
+The functions carry the names of the C ABI in include/mbicg.h and only
+marshal arguments: numpy arrays (host memory) or torch tensors (host or CUDA
+memory), complex128 and C-contiguous, in the layouts the header documents.
+Every step of the computation runs in the library's CUDA kernels; there is no
+other implementation to fall back to, and a missing or unloadable library
+raises an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+__all__ = [
+    "MBICG_OK", "MBICG_EINVAL", "MBICG_ENOMEM", "MBICG_ENOGAUGE", "MBICG_ENOTCONV",
+    "MBICG_EBREAKDOWN", "MBICG_ENAN", "MBICG_ECUDA", "MBICG_FP64", "MBICG_FP32", "MBICG_FP16",
+    "MBICG_MR_COLUMN", "MBICG_MR_BLOCK", "MBICG_MR_FROZEN", "KERNEL_CLASSES",
+    "MbicgError", "mbicg_params", "mbicg_stats", "library_path", "load_library",
+    "mbicg_default_params", "mbicg_create", "mbicg_destroy", "mbicg_load_gauge",
+    "mbicg_apply_D", "mbicg_sap_precond", "mbicg_block_solve", "mbicg_get_stats",
+    "mbicg_last_error", "mbicg_set_profiling", "mbicg_get_profile",
+]
+
+MBICG_OK, MBICG_EINVAL, MBICG_ENOMEM, MBICG_ENOGAUGE = 0, -1, -2, -3
+MBICG_ENOTCONV, MBICG_EBREAKDOWN, MBICG_ENAN, MBICG_ECUDA = -4, -5, -6, -7
+MBICG_FP64, MBICG_FP32, MBICG_FP16 = 0, 1, 2
+MBICG_MR_COLUMN, MBICG_MR_BLOCK, MBICG_MR_FROZEN = 0, 1, 2
+KERNEL_CLASSES = ["dslash", "dslash64", "sap_resid", "sap_domain", "sap_update", "gram",
+                  "axpy", "small", "convert", "sap_sweep"]
+
+_STATUS_NAMES = {0: "MBICG_OK", -1: "MBICG_EINVAL", -2: "MBICG_ENOMEM", -3: "MBICG_ENOGAUGE",
+                 -4: "MBICG_ENOTCONV", -5: "MBICG_EBREAKDOWN", -6: "MBICG_ENAN", -7: "MBICG_ECUDA"}
+
+
+class MbicgError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class mbicg_params(ctypes.Structure):
+    _fields_ = [
+        ("ncycle", ctypes.c_int), ("nmr", ctypes.c_int), ("block", ctypes.c_int * 4),
+        ("mr_mode", ctypes.c_int), ("prec_sap", ctypes.c_int), ("prec_D", ctypes.c_int),
+        ("max_iter", ctypes.c_int), ("use_x0", ctypes.c_int), ("delta_ru", ctypes.c_double),
+        ("res_history", ctypes.POINTER(ctypes.c_double)), ("res_history_len", ctypes.c_int),
+    ]
+
+
+class mbicg_stats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("restarts", ctypes.c_int),
+        ("kernel_launches", ctypes.c_longlong), ("true_res_max", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libmbicg.so (building it first with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and _build.needs_build():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise OSError(f"CUDA library not built: {_build.LIB}")
+    lib = ctypes.CDLL(_build.LIB)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    lib.mbicg_default_params.argtypes = [ctypes.POINTER(mbicg_params)]
+    lib.mbicg_default_params.restype = None
+    lib.mbicg_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.c_int, vp]
+    lib.mbicg_destroy.argtypes = [vp]
+    lib.mbicg_destroy.restype = None
+    lib.mbicg_load_gauge.argtypes = [vp, vp]
+    lib.mbicg_apply_D.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    lib.mbicg_sap_precond.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double,
+                                      ctypes.POINTER(mbicg_params)]
+    lib.mbicg_block_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.POINTER(mbicg_params), ip, dp]
+    lib.mbicg_get_stats.argtypes = [vp, ctypes.POINTER(mbicg_stats)]
+    lib.mbicg_last_error.argtypes = [vp]
+    lib.mbicg_last_error.restype = ctypes.c_char_p
+    lib.mbicg_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.mbicg_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+    _lib = lib
+    return lib
+
+
+def _ptr(a, name: str):
+    """Data pointer of a C-contiguous complex128 numpy array or torch tensor."""
+    if hasattr(a, "data_ptr") and hasattr(a, "is_contiguous"):
+        import torch
+
+        if a.dtype != torch.complex128 or not a.is_contiguous():
+            raise TypeError(f"{name}: need a contiguous complex128 tensor")
+        return ctypes.c_void_p(a.data_ptr()), a.numel()
+    import numpy as np
+
+    if not isinstance(a, np.ndarray) or a.dtype != np.complex128 or not a.flags.c_contiguous:
+        raise TypeError(f"{name}: need a C-contiguous complex128 numpy array or torch tensor")
+    return ctypes.c_void_p(a.ctypes.data), a.size
+
+
+def _check(ctx, status: int, allowed=(MBICG_OK,)):
+    if status not in allowed:
+        raise MbicgError(status, mbicg_last_error(ctx))
+    return status
+
+
+def mbicg_default_params(**overrides) -> mbicg_params:
+    p = mbicg_params()
+    load_library().mbicg_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "block":
+            p.block = (ctypes.c_int * 4)(*v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def mbicg_create(dims, device: int = 0, stream=None):
+    """Context for a lattice of extents dims = (Lx, Ly, Lz, Lt).  stream: a
+    torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+    lib = load_library()
+    ctx = ctypes.c_void_p()
+    raw = None
+    if stream is not None:
+        raw = ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    st = lib.mbicg_create(ctypes.byref(ctx), d, int(device), raw)
+    if st != MBICG_OK:
+        raise MbicgError(st, "mbicg_create failed")
+    ctx.dims = tuple(int(x) for x in dims)
+    return ctx
+
+
+def mbicg_destroy(ctx) -> None:
+    load_library().mbicg_destroy(ctx)
+
+
+def mbicg_last_error(ctx) -> str:
+    return load_library().mbicg_last_error(ctx).decode()
+
+
+def mbicg_load_gauge(ctx, U) -> None:
+    p, _ = _ptr(U, "U")
+    _check(ctx, load_library().mbicg_load_gauge(ctx, p))
+
+
+def mbicg_apply_D(ctx, inp, out, L: int, kappa: float, prec: int = MBICG_FP64) -> None:
+    pi, _ = _ptr(inp, "in")
+    po, _ = _ptr(out, "out")
+    _check(ctx, load_library().mbicg_apply_D(ctx, pi, po, int(L), float(kappa), int(prec)))
+
+
+def mbicg_sap_precond(ctx, inp, out, L: int, kappa: float, params: mbicg_params) -> None:
+    pi, _ = _ptr(inp, "in")
+    po, _ = _ptr(out, "out")
+    _check(ctx, load_library().mbicg_sap_precond(ctx, pi, po, int(L), float(kappa),
+                                                 ctypes.byref(params)))
+
+
+def mbicg_block_solve(ctx, B, X, L: int, kappa: float, tol: float, params: mbicg_params):
+    """Returns (status, iters, true_res list).  MBICG_ENOTCONV and
+    MBICG_EBREAKDOWN are returned (X and true_res are filled); every other
+    failure raises MbicgError."""
+    pb, _ = _ptr(B, "B")
+    px, _ = _ptr(X, "X")
+    iters = ctypes.c_int(0)
+    tres = (ctypes.c_double * max(1, int(L)))()
+    st = load_library().mbicg_block_solve(ctx, pb, px, int(L), float(kappa), float(tol),
+                                          ctypes.byref(params), ctypes.byref(iters), tres)
+    _check(ctx, st, (MBICG_OK, MBICG_ENOTCONV, MBICG_EBREAKDOWN))
+    return st, iters.value, [tres[i] for i in range(int(L))]
+
+
+def mbicg_get_stats(ctx) -> dict:
+    s = mbicg_stats()
+    _check(ctx, load_library().mbicg_get_stats(ctx, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in mbicg_stats._fields_}
+
+
+def mbicg_set_profiling(ctx, enable: bool) -> None:
+    _check(ctx, load_library().mbicg_set_profiling(ctx, int(bool(enable))))
+
+
+def mbicg_get_profile(ctx) -> dict:
+    n = len(KERNEL_CLASSES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_longlong * n)()
+    _check(ctx, load_library().mbicg_get_profile(ctx, ms, cnt, n))
+    return {KERNEL_CLASSES[i]: (ms[i], cnt[i]) for i in range(n)}

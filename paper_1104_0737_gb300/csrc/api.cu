@@ -1,0 +1,860 @@
+// api.cu — the C ABI (include/mbicg.h): context, gauge field, the operator and
+// preconditioner entry points, and the solver driver of Algorithm 2 (Sec. 2.1)
+// in mixed precision.
+//
+// Solver state lives on the device for the whole solve: B and X in FP64, the
+// Krylov blocks R, P, R~, U, V, S, Z in the Krylov precision T (FP64, or FP32
+// with reliable updates).  The only device-to-host traffic inside an iteration
+// is the L squared residual norms and a status word, read once per iteration
+// for the stopping test of Algorithm 2.
+//
+// Mixed precision (FP32 Krylov loop): X accumulates in FP64; whenever
+// max_i |r_i|/|b_i| has dropped by delta_ru since the last update, the true
+// residual B - A X is recomputed with the FP64 operator and replaces R
+// (reliable update).  Sec. 2.2 shows that sloppy right preconditioning keeps
+// R = B - A X exact; the reliable updates bound the additional drift of the
+// FP32 Krylov recursion.  The final answer is confirmed with the FP64 true
+// residual.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/mbicg.h"
+#include "internal.h"
+
+using namespace mbicg;
+
+struct mbicg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int dims[4] = {0, 0, 0, 0};
+  long long V = 0;
+  cx<double>* U64 = nullptr;
+  cx<float>* U32 = nullptr;
+  bool gauge = false;
+  std::string err;
+  mbicg_stats stats{};
+  long long launches = 0;
+  Prof prof;
+  std::map<std::string, std::pair<void*, size_t>> bufs;  // device workspaces
+  double* h_small = nullptr;                            // pinned host scratch
+};
+
+namespace {
+
+constexpr int H_SMALL = 4096;  // doubles of pinned host scratch
+
+int fail(mbicg_ctx* c, int code, const char* fmt, const char* a = "") {
+  char buf[512];
+  snprintf(buf, sizeof(buf), fmt, a);
+  c->err = buf;
+  return code;
+}
+
+int cuda_fail(mbicg_ctx* c, cudaError_t e, const char* where) {
+  c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? MBICG_ENOMEM : MBICG_ECUDA;
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);    \
+  } while (0)
+
+// device workspace by name; grows, never shrinks
+int get_buf(mbicg_ctx* c, const char* name, size_t bytes, void** out) {
+  auto it = c->bufs.find(name);
+  if (it != c->bufs.end() && it->second.second >= bytes) {
+    *out = it->second.first;
+    return MBICG_OK;
+  }
+  if (it != c->bufs.end()) {
+    cudaFree(it->second.first);
+    c->bufs.erase(it);
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes < 256 ? 256 : bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(c, e, name);
+  }
+  c->bufs[name] = {p, bytes};
+  *out = p;
+  return MBICG_OK;
+}
+
+template <typename P>
+int buf(mbicg_ctx* c, const char* name, size_t count, P** out) {
+  void* p = nullptr;
+  const int rc = get_buf(c, name, count * sizeof(P), &p);
+  *out = static_cast<P*>(p);
+  return rc;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+Geom lattice_geom(const mbicg_ctx* c, const int* block) {
+  Geom g{};
+  g.V = 1;
+  g.nd = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    g.d[mu] = c->dims[mu];
+    g.V *= c->dims[mu];
+    g.blk[mu] = block ? block[mu] : c->dims[mu];
+    g.nb[mu] = g.d[mu] / g.blk[mu];
+    g.nd *= g.nb[mu];
+  }
+  g.Vd = g.V / g.nd;
+  geom_init_divisors(g);
+  return g;
+}
+
+bool valid_blocking(const mbicg_ctx* c, const int* block) {
+  long long vd = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (block[mu] < 1 || c->dims[mu] % block[mu] != 0) return false;
+    const int nb = c->dims[mu] / block[mu];
+    if (nb < 2 || nb % 2 != 0) return false;
+    vd *= block[mu];
+  }
+  return vd <= (1 << 20);
+}
+
+Exec exec_of(mbicg_ctx* c) { return Exec{c->stream, &c->launches, &c->prof}; }
+
+int check_launch(mbicg_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  return MBICG_OK;
+}
+
+// Host <-> device staging of an ABI block.
+struct Staged {
+  const void* user = nullptr;
+  void* dev = nullptr;
+  bool host = false;
+  size_t bytes = 0;
+};
+
+int stage_in(mbicg_ctx* c, const void* user, size_t bytes, const char* name, bool copy, Staged* s) {
+  s->user = user;
+  s->bytes = bytes;
+  s->host = !is_device_ptr(user);
+  if (!s->host) {
+    s->dev = const_cast<void*>(user);
+    return MBICG_OK;
+  }
+  int rc = get_buf(c, name, bytes, &s->dev);
+  if (rc) return rc;
+  if (copy) CK(cudaMemcpyAsync(s->dev, user, bytes, cudaMemcpyHostToDevice, c->stream));
+  return MBICG_OK;
+}
+
+int stage_out(mbicg_ctx* c, const Staged& s) {
+  if (s.host) {
+    CK(cudaMemcpyAsync(const_cast<void*>(s.user), s.dev, s.bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return MBICG_OK;
+}
+
+// read n doubles (+ one int status) from the device through pinned memory
+int read_small(mbicg_ctx* c, const double* d, int n, const int* status, double* out, int* st) {
+  CK(cudaMemcpyAsync(c->h_small, d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  if (status)
+    CK(cudaMemcpyAsync(c->h_small + n, status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  memcpy(out, c->h_small, sizeof(double) * n);
+  if (status) memcpy(st, c->h_small + n, sizeof(int));
+  c->prof.collect();
+  return MBICG_OK;
+}
+
+// column norms |b_i| of an ABI block on the device, and a NaN/Inf check
+int abi_norms(mbicg_ctx* c, const cx<double>* d, int L, double* norms, bool* bad) {
+  const Exec ex = exec_of(c);
+  double* part;
+  int* flag;
+  double* nrm;
+  int rc;
+  if ((rc = buf(c, "abi_part", (size_t)8 * 152 * L, &part))) return rc;
+  if ((rc = buf(c, "abi_flag", 1, &flag))) return rc;
+  if ((rc = buf(c, "abi_norms", MAXL, &nrm))) return rc;
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+  int np;
+  {
+    Timed t(ex, KC_CONVERT);
+    np = abi_check(ex, c->V * 12, L, d, part, flag);
+  }
+  SmallWork w{};
+  w.norms = nrm;
+  w.status = flag;  // lxl_norms ORs ST_NAN into it; abi_check sets bit 0
+  lxl_norms(ex, L, part, np, false, w);
+  if ((rc = check_launch(c, "abi_norms"))) return rc;
+  int st = 0;
+  if ((rc = read_small(c, nrm, L, flag, norms, &st))) return rc;
+  *bad = st != 0;
+  for (int i = 0; i < L; ++i) norms[i] = sqrt(norms[i]);
+  return MBICG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solver
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Krylov {
+  cx<T>*R, *P, *Rt, *U, *V, *S, *Z;
+};
+
+template <typename T, typename TS>
+struct Solver {
+  mbicg_ctx* c;
+  Exec ex;
+  Geom g;
+  int L;
+  double kappa;
+  mbicg_params p;
+  long long V;
+  size_t nl;  // complex numbers per block: 12 V L
+  cx<double>*B64, *X64, *W64;
+  Krylov<T> k;
+  cx<TS>*eta_s = nullptr, *psi_s = nullptr;  // SAP precision staging when TS != T
+  SapWork sw;
+  double* table = nullptr;
+  bool table_ready = false;
+  SmallWork sm{};
+  double *gpart, *npart;
+  double h_norm[MAXL + 1];
+  double bnorm[MAXL];
+
+  const cx<T>* links_T() const;
+  const cx<TS>* links_S() const;
+
+  int alloc() {
+    int rc;
+    if ((rc = buf(c, "B64", nl, &B64))) return rc;
+    if ((rc = buf(c, "X64", nl, &X64))) return rc;
+    if ((rc = buf(c, "W64", nl, &W64))) return rc;
+    const char* names[7] = {"kR", "kP", "kRt", "kU", "kV", "kS", "kZ"};
+    cx<T>** ptrs[7] = {&k.R, &k.P, &k.Rt, &k.U, &k.V, &k.S, &k.Z};
+    for (int i = 0; i < 7; ++i)
+      if ((rc = buf(c, names[i], nl, ptrs[i]))) return rc;
+    if (p.ncycle > 0) {
+      if (!std::is_same<T, TS>::value) {
+        if ((rc = buf(c, "eta_s", nl, &eta_s))) return rc;
+        if ((rc = buf(c, "psi_s", nl, &psi_s))) return rc;
+      }
+      cx<TS>*r, *q, *x;
+      if ((rc = buf(c, "sap_r", nl, &r))) return rc;
+      if ((rc = buf(c, "sap_q", nl, &q))) return rc;
+      if ((rc = buf(c, "sap_x", nl, &x))) return rc;
+      sw.r = r;
+      sw.q = q;
+      sw.x = x;
+      const int ndc = g.nd / 2;
+      const int S = sap_sites_per_cta(g, L, sizeof(TS) == 8);
+      const size_t nchunk = g.Vd / S;
+      if ((rc = buf(c, "sap_dots", (size_t)ndc * nchunk * L * 3, &sw.dots))) return rc;
+      if ((rc = buf(c, "sap_omega", (size_t)ndc * L * 2, &sw.omega))) return rc;
+      if ((rc = buf(c, "sap_table", (size_t)p.ncycle * 2 * p.nmr * ndc * 2, &table))) return rc;
+    }
+    if ((rc = buf(c, "gpart", (size_t)GRAM_CTAS * gram_slots(L) * 2, &gpart))) return rc;
+    if ((rc = buf(c, "npart", (size_t)8 * 152 * L, &npart))) return rc;
+    if ((rc = buf(c, "sm_G", 2 * MAXL * MAXL, &sm.G))) return rc;
+    if ((rc = buf(c, "sm_LU", 2 * MAXL * MAXL, &sm.LU))) return rc;
+    if ((rc = buf(c, "sm_piv", MAXL, &sm.piv))) return rc;
+    if ((rc = buf(c, "sm_alpha", 2 * MAXL * MAXL, &sm.alpha))) return rc;
+    if ((rc = buf(c, "sm_zb", 2 + 2 * MAXL * MAXL, &sm.zb))) return rc;
+    if ((rc = buf(c, "sm_M", 2 * MAXL * MAXL, &sm.M))) return rc;
+    if ((rc = buf(c, "sm_norms", MAXL, &sm.norms))) return rc;
+    if ((rc = buf(c, "sm_status", 1, &sm.status))) return rc;
+    return MBICG_OK;
+  }
+
+  // out = M in (T precision blocks)
+  int apply_M(const cx<T>* in, cx<T>* out) {
+    if (p.ncycle == 0) {
+      CK(cudaMemcpyAsync(out, in, sizeof(cx<T>) * nl, cudaMemcpyDeviceToDevice, c->stream));
+      return MBICG_OK;
+    }
+    int mode = p.mr_mode;
+    double* tab = nullptr;
+    if (p.mr_mode == MBICG_MR_FROZEN) {
+      mode = table_ready ? 2 : 1;
+      tab = table;
+      table_ready = true;
+    }
+    if constexpr (std::is_same<T, TS>::value) {
+      sap_apply<TS>(ex, g, links_S(), in, out, L, kappa, p.ncycle, p.nmr, mode, tab, sw);
+    } else {
+      {
+        Timed t(ex, KC_CONVERT);
+        convert_block<T, TS>(ex, (long long)nl, in, eta_s);
+      }
+      sap_apply<TS>(ex, g, links_S(), eta_s, psi_s, L, kappa, p.ncycle, p.nmr, mode, tab, sw);
+      Timed t(ex, KC_CONVERT);
+      convert_block<TS, T>(ex, (long long)nl, psi_s, out);
+    }
+    return check_launch(c, "apply_M");
+  }
+
+  int dslash(const cx<T>* in, cx<T>* out) {
+    Timed t(ex, KC_DSLASH);
+    dslash_full<T>(ex, g, links_T(), in, out, L, kappa);
+    return MBICG_OK;
+  }
+
+  // R = B - A X in FP64, converted to T; host norms in h_norm
+  int true_residual(double* rel, double* relmax) {
+    {
+      Timed t(ex, KC_DSLASH64);
+      dslash_full<double>(ex, g, c->U64, X64, W64, L, kappa);
+    }
+    int np;
+    {
+      Timed t(ex, KC_CONVERT);
+      np = residual_from<T>(ex, V, L, B64, W64, k.R, npart);
+    }
+    lxl_norms(ex, L, npart, np, false, sm);
+    int rc = check_launch(c, "true_residual");
+    if (rc) return rc;
+    int st = 0;
+    if ((rc = read_small(c, sm.norms, L, sm.status, h_norm, &st))) return rc;
+    *relmax = 0;
+    for (int i = 0; i < L; ++i) {
+      rel[i] = sqrt(h_norm[i]) / bnorm[i];
+      if (!(rel[i] <= *relmax)) *relmax = rel[i];
+    }
+    return MBICG_OK;
+  }
+
+  int qr() {
+    for (int pass = 0; pass < 2; ++pass) {
+      int np;
+      {
+        Timed t(ex, KC_GRAM);
+        np = block_gram<T>(ex, V, L, k.P, k.P, nullptr, GRAM_G1, gpart);
+      }
+      {
+        Timed t(ex, KC_SMALL);
+        lxl_cholesky_inverse(ex, L, gpart, np, sm, sizeof(T) == 4 ? 1e-12 : 1e-26);
+      }
+      Timed t(ex, KC_AXPY);
+      block_transform<T>(ex, V, L, k.P, sm.M, k.P);
+    }
+    return check_launch(c, "qr");
+  }
+
+  int run(const cx<double>* dB, cx<double>* dX, double tol, int* iters_out, double* true_res) {
+    int rc;
+    nl = (size_t)V * 12 * L;
+    if ((rc = alloc())) return rc;
+    // B, X into the internal layout
+    {
+      Timed t(ex, KC_CONVERT);
+      abi_to_internal<double>(ex, V, L, dB, B64);
+      if (p.use_x0) abi_to_internal<double>(ex, V, L, dX, X64);
+    }
+    if (!p.use_x0) CK(cudaMemsetAsync(X64, 0, sizeof(cx<double>) * nl, c->stream));
+    CK(cudaMemsetAsync(sm.status, 0, sizeof(int), c->stream));
+    double rel[MAXL], relmax;
+    // line 2: R = B - A X
+    if ((rc = true_residual(rel, &relmax))) return rc;
+    // lines 3-4: P = R, R~ = R
+    CK(cudaMemcpyAsync(k.P, k.R, sizeof(cx<T>) * nl, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(k.Rt, k.R, sizeof(cx<T>) * nl, cudaMemcpyDeviceToDevice, c->stream));
+    double rmax_ru = relmax;
+    int it = 0, status = MBICG_OK;
+    bool fresh_restart = false;
+    bool true_fresh = true;  // R holds B - A X from the FP64 operator
+    const char* tr_env = getenv("MBICG_TRACE");
+    const bool trace = tr_env && tr_env[0] == '1';
+    const bool sloppy = sizeof(T) == 4;
+    while (true) {
+      if (!(relmax == relmax)) { status = MBICG_ENAN; break; }
+      if (relmax <= tol) {
+        // confirm on the true residual (FP32 loop: recompute; FP64: already exact to rounding)
+        if (!sloppy || true_fresh) break;
+        if ((rc = true_residual(rel, &relmax))) return rc;
+        c->stats.reliable_updates++;
+        rmax_ru = relmax;
+        true_fresh = true;
+        if (trace) fprintf(stderr, "mbicg: converged recursively, true max rel residual %.6e\n", relmax);
+        if (relmax <= tol) break;
+      }
+      if (it >= p.max_iter) { status = MBICG_ENOTCONV; break; }
+      // 4.1 QR of P
+      if ((rc = qr())) return rc;
+      // 4.2 U = M P, 4.3 V = A U
+      if ((rc = apply_M(k.P, k.U))) return rc;
+      if ((rc = dslash(k.U, k.V))) return rc;
+      // 4.4 (R~^H V) alpha = R~^H R
+      {
+        int np;
+        {
+          Timed t(ex, KC_GRAM);
+          np = block_gram<T>(ex, V, L, k.Rt, k.V, k.R, GRAM_G1 | GRAM_G2, gpart);
+        }
+        Timed t(ex, KC_SMALL);
+        lxl_alpha(ex, L, gpart, np, sm);
+      }
+      // 4.5 R -= V alpha, 4.6 X += U alpha
+      {
+        Timed t(ex, KC_AXPY);
+        block_update_alpha<T>(ex, V, L, k.V, k.U, sm.alpha, k.R, X64);
+      }
+      // 4.7 S = M R, 4.8 Z = A S
+      if ((rc = apply_M(k.R, k.S))) return rc;
+      if ((rc = dslash(k.S, k.Z))) return rc;
+      // 4.9 zeta = Tr(Z^H R)/Tr(Z^H Z), 4.12 (R~^H V) beta = -R~^H Z
+      {
+        int np;
+        {
+          Timed t(ex, KC_GRAM);
+          np = block_gram<T>(ex, V, L, k.Rt, k.Z, k.R, GRAM_G1 | GRAM_D1 | GRAM_D2, gpart);
+        }
+        Timed t(ex, KC_SMALL);
+        lxl_zeta_beta(ex, L, gpart, np, sm);
+      }
+      // 4.10 X += zeta S, 4.11 R -= zeta Z, 4.13 P = R + (P - zeta V) beta
+      {
+        int np;
+        {
+          Timed t(ex, KC_AXPY);
+          np = block_update_zeta<T>(ex, V, L, k.S, k.Z, k.V, sm.zb, k.R, k.P, X64, npart);
+        }
+        Timed t(ex, KC_SMALL);
+        lxl_norms(ex, L, npart, np, false, sm);
+      }
+      if ((rc = check_launch(c, "iteration"))) return rc;
+      int st = 0;
+      if ((rc = read_small(c, sm.norms, L, sm.status, h_norm, &st))) return rc;
+      ++it;
+      true_fresh = false;
+      relmax = 0;
+      for (int i = 0; i < L; ++i) {
+        rel[i] = sqrt(h_norm[i]) / bnorm[i];
+        if (!(rel[i] <= relmax)) relmax = rel[i];
+      }
+      if (p.res_history && it - 1 < p.res_history_len) p.res_history[it - 1] = relmax;
+      if (trace) fprintf(stderr, "mbicg: iter %d max rel residual %.6e status 0x%x\n", it, relmax, st);
+      if (st & ST_NAN) { status = MBICG_ENAN; break; }
+      if (st) {
+        // breakdown: restart from the current X (R = B - A X, P = R, R~ = R)
+        if (fresh_restart || c->stats.restarts >= 3) { status = MBICG_EBREAKDOWN; break; }
+        c->stats.restarts++;
+        CK(cudaMemsetAsync(sm.status, 0, sizeof(int), c->stream));
+        if ((rc = true_residual(rel, &relmax))) return rc;
+        CK(cudaMemcpyAsync(k.P, k.R, sizeof(cx<T>) * nl, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(k.Rt, k.R, sizeof(cx<T>) * nl, cudaMemcpyDeviceToDevice, c->stream));
+        rmax_ru = relmax;
+        fresh_restart = true;
+        true_fresh = true;
+        continue;
+      }
+      fresh_restart = false;
+      // reliable update of the FP32 recursion
+      if (sloppy && relmax > tol && relmax < p.delta_ru * rmax_ru) {
+        if ((rc = true_residual(rel, &relmax))) return rc;
+        if (trace) fprintf(stderr, "mbicg: reliable update, true max rel residual %.6e\n", relmax);
+        c->stats.reliable_updates++;
+        rmax_ru = relmax;
+        true_fresh = true;
+      }
+    }
+    // final true residual in FP64 (R is no longer needed)
+    double trel[MAXL], tmax;
+    if (true_fresh || !sloppy) {
+      if (!true_fresh) {
+        if ((rc = true_residual(trel, &tmax))) return rc;
+      } else {
+        for (int i = 0; i < L; ++i) trel[i] = rel[i];
+        tmax = relmax;
+      }
+    } else if ((rc = true_residual(trel, &tmax))) {
+      return rc;
+    }
+    if (true_res)
+      for (int i = 0; i < L; ++i) true_res[i] = trel[i];
+    c->stats.true_res_max = tmax;
+    c->stats.iters = it;
+    if (iters_out) *iters_out = it;
+    if (status == MBICG_OK && !(tmax <= tol)) status = MBICG_ENOTCONV;
+    {
+      Timed t(ex, KC_CONVERT);
+      internal_to_abi<double>(ex, V, L, X64, dX);
+    }
+    if ((rc = check_launch(c, "solution"))) return rc;
+    if (status == MBICG_ENOTCONV) fail(c, status, "not converged: max true residual %s", std::to_string(tmax).c_str());
+    if (status == MBICG_EBREAKDOWN) fail(c, status, "breakdown (singular R~^H V, Tr(Z^H Z) = 0 or rank-deficient P)");
+    if (status == MBICG_ENAN) fail(c, status, "NaN or Inf in a residual norm");
+    return status;
+  }
+};
+
+template <>
+const cx<float>* Solver<float, float>::links_T() const { return c->U32; }
+template <>
+const cx<float>* Solver<float, float>::links_S() const { return c->U32; }
+template <>
+const cx<double>* Solver<double, float>::links_T() const { return c->U64; }
+template <>
+const cx<float>* Solver<double, float>::links_S() const { return c->U32; }
+template <>
+const cx<double>* Solver<double, double>::links_T() const { return c->U64; }
+template <>
+const cx<double>* Solver<double, double>::links_S() const { return c->U64; }
+template <>
+const cx<float>* Solver<float, double>::links_T() const { return c->U32; }
+template <>
+const cx<double>* Solver<float, double>::links_S() const { return c->U64; }
+
+int check_params(mbicg_ctx* c, int L, const mbicg_params* p, bool solve) {
+  if (L < 1 || L > MAXL) return fail(c, MBICG_EINVAL, "L must be in [1, 16]");
+  if (!p) return fail(c, MBICG_EINVAL, "params is NULL");
+  if (p->ncycle < 0 || p->ncycle > 64) return fail(c, MBICG_EINVAL, "ncycle out of range");
+  if (p->ncycle > 0) {
+    if (p->nmr < 1 || p->nmr > 256) return fail(c, MBICG_EINVAL, "nmr must be in [1, 256]");
+    if (!valid_blocking(c, p->block))
+      return fail(c, MBICG_EINVAL, "SAP block must divide the lattice into an even number (>= 2) of domains per direction");
+    if (p->mr_mode < 0 || p->mr_mode > 2 || (!solve && p->mr_mode == MBICG_MR_FROZEN))
+      return fail(c, MBICG_EINVAL, "bad mr_mode");
+    if (p->prec_sap != MBICG_FP32 && p->prec_sap != MBICG_FP64)
+      return fail(c, MBICG_EINVAL, "prec_sap must be MBICG_FP32 or MBICG_FP64");
+  }
+  if (solve) {
+    if (p->prec_D != MBICG_FP32 && p->prec_D != MBICG_FP64)
+      return fail(c, MBICG_EINVAL, "prec_D must be MBICG_FP32 or MBICG_FP64");
+    if (p->max_iter < 0) return fail(c, MBICG_EINVAL, "max_iter < 0");
+    if (!(p->delta_ru > 0 && p->delta_ru < 1)) return fail(c, MBICG_EINVAL, "delta_ru must be in (0, 1)");
+  }
+  return MBICG_OK;
+}
+
+template <typename T, typename TS>
+int run_solve(mbicg_ctx* c, const cx<double>* dB, cx<double>* dX, int L, double kappa, double tol,
+              const mbicg_params* p, const double* bnorm, int* iters, double* true_res) {
+  Solver<T, TS> s;
+  s.c = c;
+  s.ex = exec_of(c);
+  s.g = lattice_geom(c, p->ncycle > 0 ? p->block : nullptr);
+  s.L = L;
+  s.kappa = kappa;
+  s.p = *p;
+  s.V = c->V;
+  for (int i = 0; i < L; ++i) s.bnorm[i] = bnorm[i];
+  return s.run(dB, dX, tol, iters, true_res);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void mbicg_default_params(mbicg_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->ncycle = 4;
+  p->nmr = 4;
+  for (int mu = 0; mu < 4; ++mu) p->block[mu] = 4;
+  p->mr_mode = MBICG_MR_FROZEN;
+  p->prec_sap = MBICG_FP32;
+  p->prec_D = MBICG_FP32;
+  p->max_iter = 1000;
+  p->use_x0 = 0;
+  p->delta_ru = 0.1;
+  p->res_history = nullptr;
+  p->res_history_len = 0;
+}
+
+int mbicg_create(mbicg_ctx** out, const int dims[4], int device, void* cuda_stream) {
+  if (!out) return MBICG_EINVAL;
+  *out = nullptr;
+  if (!dims) return MBICG_EINVAL;
+  long long vol = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (dims[mu] < 2 || dims[mu] % 2 != 0 || dims[mu] > 4096) return MBICG_EINVAL;
+    vol *= dims[mu];
+  }
+  if (vol > (1ll << 27)) return MBICG_EINVAL;  // 32-bit site and (site, rhs) indices
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return MBICG_ECUDA;
+  }
+  mbicg_ctx* c = new mbicg_ctx();
+  c->device = device;
+  c->V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    c->dims[mu] = dims[mu];
+    c->V *= dims[mu];
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete c;
+    return MBICG_ECUDA;
+  }
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return MBICG_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  if (cudaMallocHost(&c->h_small, sizeof(double) * H_SMALL) != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return MBICG_ENOMEM;
+  }
+  *out = c;
+  return MBICG_OK;
+}
+
+void mbicg_destroy(mbicg_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->bufs) cudaFree(kv.second.first);
+  if (c->U64) cudaFree(c->U64);
+  if (c->U32) cudaFree(c->U32);
+  c->prof.release();
+  if (c->h_small) cudaFreeHost(c->h_small);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int mbicg_load_gauge(mbicg_ctx* c, const double* U) {
+  if (!c) return MBICG_EINVAL;
+  c->err.clear();
+  if (!U) return fail(c, MBICG_EINVAL, "U is NULL");
+  CK(cudaSetDevice(c->device));
+  c->launches = 0;
+  const size_t n = (size_t)c->V * 36;  // complex numbers
+  if (!c->U64) CK(cudaMalloc(&c->U64, sizeof(cx<double>) * n));
+  if (!c->U32) CK(cudaMalloc(&c->U32, sizeof(cx<float>) * n));
+  Staged s;
+  int rc = stage_in(c, U, sizeof(cx<double>) * n, "gauge_stage", true, &s);
+  if (rc) return rc;
+  int* flag;
+  if ((rc = buf(c, "gauge_flag", 1, &flag))) return rc;
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+  const Exec ex = exec_of(c);
+  {
+    Timed t(ex, KC_CONVERT);
+    convert_links(ex, c->V, static_cast<const cx<double>*>(s.dev), c->U64, c->U32, flag);
+  }
+  if ((rc = check_launch(c, "load_gauge"))) return rc;
+  int bad = 0;
+  CK(cudaMemcpyAsync(c->h_small, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->prof.collect();
+  memcpy(&bad, c->h_small, sizeof(int));
+  c->stats.kernel_launches = c->launches;
+  if (bad) {
+    c->gauge = false;
+    return fail(c, MBICG_ENAN, "gauge field holds NaN or Inf");
+  }
+  c->gauge = true;
+  return MBICG_OK;
+}
+
+int mbicg_apply_D(mbicg_ctx* c, const double* in, double* out, int L, double kappa, int prec) {
+  if (!c) return MBICG_EINVAL;
+  c->err.clear();
+  if (!in || !out || in == out) return fail(c, MBICG_EINVAL, "in/out NULL or aliased");
+  if (L < 1 || L > MAXL) return fail(c, MBICG_EINVAL, "L must be in [1, 16]");
+  if (prec != MBICG_FP64 && prec != MBICG_FP32) return fail(c, MBICG_EINVAL, "prec must be FP64 or FP32");
+  if (!c->gauge) return fail(c, MBICG_ENOGAUGE, "no gauge field loaded");
+  CK(cudaSetDevice(c->device));
+  c->launches = 0;
+  const size_t nl = (size_t)c->V * 12 * L;
+  Staged si, so;
+  int rc;
+  if ((rc = stage_in(c, in, sizeof(cx<double>) * nl, "abi_in", true, &si))) return rc;
+  if ((rc = stage_in(c, out, sizeof(cx<double>) * nl, "abi_out", false, &so))) return rc;
+  const Exec ex = exec_of(c);
+  const Geom g = lattice_geom(c, nullptr);
+  if (prec == MBICG_FP64) {
+    cx<double>*a, *b;
+    if ((rc = buf(c, "op64_a", nl, &a)) || (rc = buf(c, "op64_b", nl, &b))) return rc;
+    {
+      Timed t(ex, KC_CONVERT);
+      abi_to_internal<double>(ex, c->V, L, static_cast<const cx<double>*>(si.dev), a);
+    }
+    {
+      Timed t(ex, KC_DSLASH64);
+      dslash_full<double>(ex, g, c->U64, a, b, L, kappa);
+    }
+    Timed t(ex, KC_CONVERT);
+    internal_to_abi<double>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
+  } else {
+    cx<float>*a, *b;
+    if ((rc = buf(c, "op32_a", nl, &a)) || (rc = buf(c, "op32_b", nl, &b))) return rc;
+    {
+      Timed t(ex, KC_CONVERT);
+      abi_to_internal<float>(ex, c->V, L, static_cast<const cx<double>*>(si.dev), a);
+    }
+    {
+      Timed t(ex, KC_DSLASH);
+      dslash_full<float>(ex, g, c->U32, a, b, L, kappa);
+    }
+    Timed t(ex, KC_CONVERT);
+    internal_to_abi<float>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
+  }
+  if ((rc = check_launch(c, "apply_D"))) return rc;
+  if ((rc = stage_out(c, so))) return rc;
+  c->stats.kernel_launches = c->launches;
+  return MBICG_OK;
+}
+
+int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double kappa, const mbicg_params* p) {
+  if (!c) return MBICG_EINVAL;
+  c->err.clear();
+  if (!in || !out || in == out) return fail(c, MBICG_EINVAL, "in/out NULL or aliased");
+  int rc;
+  if ((rc = check_params(c, L, p, false))) return rc;
+  if (p->ncycle < 1) return fail(c, MBICG_EINVAL, "ncycle must be >= 1");
+  if (!c->gauge) return fail(c, MBICG_ENOGAUGE, "no gauge field loaded");
+  CK(cudaSetDevice(c->device));
+  c->launches = 0;
+  const size_t nl = (size_t)c->V * 12 * L;
+  Staged si, so;
+  if ((rc = stage_in(c, in, sizeof(cx<double>) * nl, "abi_in", true, &si))) return rc;
+  if ((rc = stage_in(c, out, sizeof(cx<double>) * nl, "abi_out", false, &so))) return rc;
+  const Exec ex = exec_of(c);
+  const Geom g = lattice_geom(c, p->block);
+  auto run = [&](auto tag, const auto* links) -> int {
+    using R = decltype(tag);
+    cx<R>*a, *b, *r, *q, *x;
+    SapWork w;
+    int rc2;
+    if ((rc2 = buf(c, "sapp_a", nl, &a))) return rc2;
+    if ((rc2 = buf(c, "sapp_b", nl, &b))) return rc2;
+    if ((rc2 = buf(c, "sap_r", nl, &r))) return rc2;
+    if ((rc2 = buf(c, "sap_q", nl, &q))) return rc2;
+    if ((rc2 = buf(c, "sap_x", nl, &x))) return rc2;
+    w.r = r;
+    w.q = q;
+    w.x = x;
+    const int ndc = g.nd / 2;
+    const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
+    if ((rc2 = buf(c, "sap_dots", (size_t)ndc * (g.Vd / S) * L * 3, &w.dots))) return rc2;
+    if ((rc2 = buf(c, "sap_omega", (size_t)ndc * L * 2, &w.omega))) return rc2;
+    {
+      Timed t(ex, KC_CONVERT);
+      abi_to_internal<R>(ex, c->V, L, static_cast<const cx<double>*>(si.dev), a);
+    }
+    sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, p->mr_mode, nullptr, w);
+    Timed t(ex, KC_CONVERT);
+    internal_to_abi<R>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
+    return MBICG_OK;
+  };
+  if (p->prec_sap == MBICG_FP64) rc = run(double(0), c->U64);
+  else rc = run(float(0), c->U32);
+  if (rc) return rc;
+  if ((rc = check_launch(c, "sap_precond"))) return rc;
+  if ((rc = stage_out(c, so))) return rc;
+  c->stats.kernel_launches = c->launches;
+  return MBICG_OK;
+}
+
+int mbicg_block_solve(mbicg_ctx* c, const double* B, double* X, int L, double kappa, double tol,
+                      const mbicg_params* p, int* iters, double* true_res) {
+  if (!c) return MBICG_EINVAL;
+  c->err.clear();
+  c->stats = mbicg_stats{};
+  if (!B || !X || (const void*)B == (const void*)X) return fail(c, MBICG_EINVAL, "B/X NULL or aliased");
+  int rc;
+  if ((rc = check_params(c, L, p, true))) return rc;
+  if (!(tol > 0)) return fail(c, MBICG_EINVAL, "tol must be > 0");
+  if (!c->gauge) return fail(c, MBICG_ENOGAUGE, "no gauge field loaded");
+  CK(cudaSetDevice(c->device));
+  c->launches = 0;
+  const size_t nl = (size_t)c->V * 12 * L;
+  Staged sb, sx;
+  if ((rc = stage_in(c, B, sizeof(cx<double>) * nl, "abi_in", true, &sb))) return rc;
+  if ((rc = stage_in(c, X, sizeof(cx<double>) * nl, "abi_out", p->use_x0 != 0, &sx))) return rc;
+  double bnorm[MAXL];
+  bool bad = false;
+  if ((rc = abi_norms(c, static_cast<const cx<double>*>(sb.dev), L, bnorm, &bad))) return rc;
+  if (bad) return fail(c, MBICG_ENAN, "B holds NaN or Inf");
+  for (int i = 0; i < L; ++i)
+    if (!(bnorm[i] > 0)) return fail(c, MBICG_EINVAL, "B has a zero column");
+  if (p->use_x0) {
+    double xn[MAXL];
+    if ((rc = abi_norms(c, static_cast<const cx<double>*>(sx.dev), L, xn, &bad))) return rc;
+    if (bad) return fail(c, MBICG_ENAN, "X0 holds NaN or Inf");
+  }
+  const cx<double>* dB = static_cast<const cx<double>*>(sb.dev);
+  cx<double>* dX = static_cast<cx<double>*>(sx.dev);
+  const bool sap64 = p->ncycle > 0 && p->prec_sap == MBICG_FP64;
+  int st;
+  if (p->prec_D == MBICG_FP64) {
+    st = sap64 ? run_solve<double, double>(c, dB, dX, L, kappa, tol, p, bnorm, iters, true_res)
+               : run_solve<double, float>(c, dB, dX, L, kappa, tol, p, bnorm, iters, true_res);
+  } else {
+    st = sap64 ? run_solve<float, double>(c, dB, dX, L, kappa, tol, p, bnorm, iters, true_res)
+               : run_solve<float, float>(c, dB, dX, L, kappa, tol, p, bnorm, iters, true_res);
+  }
+  if (st == MBICG_ECUDA || st == MBICG_ENOMEM || st == MBICG_EINVAL) return st;
+  if ((rc = stage_out(c, sx))) return rc;
+  if (!sx.host) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "block_solve");
+  }
+  c->prof.collect();
+  c->stats.kernel_launches = c->launches;
+  return st;
+}
+
+int mbicg_get_stats(const mbicg_ctx* c, mbicg_stats* out) {
+  if (!c || !out) return MBICG_EINVAL;
+  *out = c->stats;
+  return MBICG_OK;
+}
+
+int mbicg_set_profiling(mbicg_ctx* c, int enable) {
+  if (!c) return MBICG_EINVAL;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  c->prof.collect();
+  c->prof.reset();
+  c->prof.on = enable != 0;
+  return MBICG_OK;
+}
+
+int mbicg_get_profile(const mbicg_ctx* c, double* ms, long long* launches, int n) {
+  if (!c || n < 0 || n > MBICG_K_NCLASS) return MBICG_EINVAL;
+  mbicg_ctx* m = const_cast<mbicg_ctx*>(c);
+  cudaSetDevice(m->device);
+  cudaStreamSynchronize(m->stream);
+  m->prof.collect();
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = c->prof.ms[i];
+    if (launches) launches[i] = c->prof.count[i];
+  }
+  return MBICG_OK;
+}
+
+const char* mbicg_last_error(const mbicg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

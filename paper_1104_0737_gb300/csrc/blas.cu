@@ -1,0 +1,795 @@
+// blas.cu — block linear algebra of Algorithm 2 (Sec. 2.1) on N x L blocks in
+// the site-major internal layout [site][rhs][spin*3+colour]:
+//   - fused block inner products (R~^H V, R~^H R; R~^H Z with Tr(Z^H R) and
+//     Tr(Z^H Z); P^H P for the QR) with per-CTA partial sums on a fixed grid,
+//     so every reduction is formed in one fixed order (bitwise reproducible);
+//   - block AXPYs (lines 4.5-4.6 and 4.10-4.13) and the QR transform P <- P M;
+//   - layout and precision conversions at the ABI boundary;
+//   - the L x L algebra (LU with partial pivoting, Cholesky, triangular
+//     inverse) in FP64 in single-CTA kernels, so nothing leaves the device
+//     inside an iteration but the residual norms.
+// FP32 blocks: products in FP32, partial sums widened to FP64 every few tiles.
+#include <math.h>
+
+#include "internal.h"
+
+namespace mbicg {
+
+namespace {
+
+constexpr int NT = 256;  // threads of the row kernels and the gram kernel
+
+__host__ __device__ constexpr int reg_block(int L) { return L % 3 == 0 ? 3 : (L % 2 == 0 ? 2 : 1); }
+// sites per shared-memory tile of the gram kernel
+__host__ __device__ constexpr int gram_tile_sites(int L) { return L >= 8 ? 8 : (L >= 4 ? 16 : 32); }
+
+// ---------------------------------------------------------------------------
+// Gram kernel
+// ---------------------------------------------------------------------------
+// flags: bit0 G1 = A^H B1, bit1 G2 = A^H B2, bit2 diag(B1^H B2), bit3 diag(B1^H B1)
+template <typename R, int L>
+__global__ void __launch_bounds__(NT) k_gram(long long nsite, const cx<R>* __restrict__ A,
+                                             const cx<R>* __restrict__ B1, const cx<R>* __restrict__ B2,
+                                             int flags, double* __restrict__ part) {
+  constexpr int BB = reg_block(L);
+  constexpr int NBI = L / BB;
+  constexpr int NB = NBI * NBI;
+  constexpr int LANES = NT / NB > 0 ? NT / NB : 1;
+  constexpr int TS = gram_tile_sites(L);
+  constexpr int TILE = TS * L * 12;  // complex numbers per tile per array
+  constexpr int FLUSH = sizeof(R) == 4 ? 8 : 1;
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* sA = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* sB1 = sA + TILE;
+  cx<R>* sB2 = sB1 + TILE;
+
+  const bool g1 = flags & 1, g2 = flags & 2, d1 = flags & 4, d2 = flags & 8;
+  const bool a_is_b1 = (A == B1);
+  const int tid = threadIdx.x;
+  const int blk = tid % NB;
+  const int lane = tid / NB;
+  const bool gram_thread = lane < LANES;
+  const int bi = (blk / NBI) * BB, bj = (blk % NBI) * BB;
+
+  cx<R> acc1[BB][BB], acc2[BB][BB];
+  cx<double> tot1[BB][BB], tot2[BB][BB];
+#pragma unroll
+  for (int i = 0; i < BB; ++i)
+#pragma unroll
+    for (int j = 0; j < BB; ++j) {
+      acc1[i][j] = acc2[i][j] = mk<R>(0, 0);
+      tot1[i][j] = tot2[i][j] = mk<double>(0, 0);
+    }
+  // diagonal dots: thread -> column tid % L, row lane tid / L
+  const int dcol = tid % L, dlane = tid / L;
+  constexpr int DLANES = NT / L;
+  cx<R> dacc1 = mk<R>(0, 0);
+  R dacc2 = 0;
+  cx<double> dtot1 = mk<double>(0, 0);
+  double dtot2 = 0;
+
+  const long long ntiles = (nsite + TS - 1) / TS;
+  int since_flush = 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long site0 = tile * TS;
+    const int ns = (int)min((long long)TS, nsite - site0);
+    const int n = ns * L * 12;
+    const cx<R>* gA = A + site0 * L * 12;
+    const cx<R>* gB1 = B1 + site0 * L * 12;
+    const cx<R>* gB2 = B2 ? B2 + site0 * L * 12 : nullptr;
+    __syncthreads();
+    for (int e = tid; e < n; e += NT) {
+      if (g1 || g2 || a_is_b1) sA[e] = gA[e];
+      if (!a_is_b1) sB1[e] = gB1[e];
+      if (gB2) sB2[e] = gB2[e];
+    }
+    __syncthreads();
+    const cx<R>* tB1 = a_is_b1 ? sA : sB1;
+    const int nrows = ns * 12;
+    if ((g1 || g2) && gram_thread) {
+      for (int row = lane; row < nrows; row += LANES) {
+        const int site = row / 12, sc = row - site * 12;
+        const cx<R>* ra = sA + site * L * 12 + sc;
+        cx<R> a[BB];
+#pragma unroll
+        for (int i = 0; i < BB; ++i) a[i] = ra[(bi + i) * 12];
+        if (g1) {
+          const cx<R>* rb = tB1 + site * L * 12 + sc;
+#pragma unroll
+          for (int j = 0; j < BB; ++j) {
+            const cx<R> b = rb[(bj + j) * 12];
+#pragma unroll
+            for (int i = 0; i < BB; ++i) cmac_conj(acc1[i][j], a[i], b);
+          }
+        }
+        if (g2) {
+          const cx<R>* rb = sB2 + site * L * 12 + sc;
+#pragma unroll
+          for (int j = 0; j < BB; ++j) {
+            const cx<R> b = rb[(bj + j) * 12];
+#pragma unroll
+            for (int i = 0; i < BB; ++i) cmac_conj(acc2[i][j], a[i], b);
+          }
+        }
+      }
+    }
+    if ((d1 || d2) && dlane < DLANES) {
+      for (int row = dlane; row < nrows; row += DLANES) {
+        const int site = row / 12, sc = row - site * 12;
+        const cx<R> z = tB1[(site * L + dcol) * 12 + sc];
+        if (d1) cmac_conj(dacc1, z, sB2[(site * L + dcol) * 12 + sc]);
+        if (d2) dacc2 = fma(z.re, z.re, fma(z.im, z.im, dacc2));
+      }
+    }
+    if (++since_flush == FLUSH) {
+      since_flush = 0;
+#pragma unroll
+      for (int i = 0; i < BB; ++i)
+#pragma unroll
+        for (int j = 0; j < BB; ++j) {
+          tot1[i][j].re += acc1[i][j].re; tot1[i][j].im += acc1[i][j].im;
+          tot2[i][j].re += acc2[i][j].re; tot2[i][j].im += acc2[i][j].im;
+          acc1[i][j] = acc2[i][j] = mk<R>(0, 0);
+        }
+      dtot1.re += dacc1.re; dtot1.im += dacc1.im; dtot2 += dacc2;
+      dacc1 = mk<R>(0, 0);
+      dacc2 = 0;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < BB; ++i)
+#pragma unroll
+    for (int j = 0; j < BB; ++j) {
+      tot1[i][j].re += acc1[i][j].re; tot1[i][j].im += acc1[i][j].im;
+      tot2[i][j].re += acc2[i][j].re; tot2[i][j].im += acc2[i][j].im;
+    }
+  dtot1.re += dacc1.re; dtot1.im += dacc1.im; dtot2 += dacc2;
+
+  // reduce over lanes through shared memory, fixed order
+  __syncthreads();
+  cx<double>* red = reinterpret_cast<cx<double>*>(smem_raw);  // [LANES][L*L] (+ diag [DLANES][L])
+  const int nslots = 2 * L * L + 2 * L;
+  double* out = part + (long long)blockIdx.x * nslots * 2;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool on = pass == 0 ? g1 : g2;
+    if (!on) {
+      for (int e = tid; e < L * L; e += NT) {
+        out[(pass * L * L + e) * 2] = 0;
+        out[(pass * L * L + e) * 2 + 1] = 0;
+      }
+      continue;
+    }
+    if (gram_thread) {
+#pragma unroll
+      for (int i = 0; i < BB; ++i)
+#pragma unroll
+        for (int j = 0; j < BB; ++j)
+          red[lane * L * L + (bi + i) * L + (bj + j)] = pass == 0 ? tot1[i][j] : tot2[i][j];
+    }
+    __syncthreads();
+    for (int e = tid; e < L * L; e += NT) {
+      double re = 0, im = 0;
+      for (int l = 0; l < LANES; ++l) {
+        re += red[l * L * L + e].re;
+        im += red[l * L * L + e].im;
+      }
+      out[(pass * L * L + e) * 2] = re;
+      out[(pass * L * L + e) * 2 + 1] = im;
+    }
+    __syncthreads();
+  }
+  if (dlane < DLANES) {
+    red[dlane * L + dcol] = dtot1;
+    red[DLANES * L + dlane * L + dcol] = mk(dtot2, 0.0);
+  }
+  __syncthreads();
+  for (int e = tid; e < 2 * L; e += NT) {
+    const int which = e / L, col = e % L;
+    double re = 0, im = 0;
+    for (int l = 0; l < DLANES; ++l) {
+      re += red[which * DLANES * L + l * L + col].re;
+      im += red[which * DLANES * L + l * L + col].im;
+    }
+    const bool on = which == 0 ? d1 : d2;
+    out[(2 * L * L + e) * 2] = on ? re : 0.0;
+    out[(2 * L * L + e) * 2 + 1] = on ? im : 0.0;
+  }
+}
+
+template <typename R, int L>
+int launch_gram(const Exec& ex, long long nsite, const cx<R>* A, const cx<R>* B1, const cx<R>* B2, int flags,
+                double* part) {
+  if (!A) A = B1;
+  constexpr int TS = gram_tile_sites(L);
+  constexpr int TILE = TS * L * 12;
+  constexpr int BB = reg_block(L);
+  constexpr int NB = (L / BB) * (L / BB);
+  constexpr int LANES = NT / NB > 0 ? NT / NB : 1;
+  constexpr size_t tile_bytes = sizeof(cx<R>) * TILE * 3;
+  constexpr size_t red_g = sizeof(cx<double>) * LANES * L * L;
+  constexpr size_t red_d = sizeof(cx<double>) * 2 * (NT / L) * L;
+  constexpr size_t red_bytes = red_g > red_d ? red_g : red_d;
+  constexpr size_t shm = tile_bytes > red_bytes ? tile_bytes : red_bytes;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_gram<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    attr_set = true;
+  }
+  const long long ntiles = (nsite + TS - 1) / TS;
+  const int grid = (int)(ntiles < GRAM_CTAS ? ntiles : GRAM_CTAS);
+  k_gram<R, L><<<grid, NT, shm, ex.stream>>>(nsite, A, B1, B2, flags, part);
+  ++*ex.launches;
+  return grid;
+}
+
+// ---------------------------------------------------------------------------
+// row kernels: one thread per row (site, spin*3+colour), L columns in registers
+// ---------------------------------------------------------------------------
+// rows (site, spin*3+colour) are below 2^31 (volume <= 2^27 sites)
+__device__ __forceinline__ size_t row_base(int row, int L) {
+  const int site = (unsigned)row / 12u;
+  return (size_t)site * L * 12 + (row - site * 12);
+}
+
+// Output columns are unrolled for FP32; for FP64 (twice the registers per
+// value) the column loop stays rolled so the inputs fit in registers.
+template <typename R, int L>
+__host__ __device__ constexpr int col_unroll() { return 1; }
+
+template <typename R, int L>
+__global__ void __launch_bounds__(NT) k_transform(int nrow, const cx<R>* X, const double* __restrict__ M,
+                                                  cx<R>* Y) {
+  __shared__ cx<R> sM[L * L];
+  for (int e = threadIdx.x; e < L * L; e += NT) sM[e] = mk((R)M[2 * e], (R)M[2 * e + 1]);
+  __syncthreads();
+  for (int row = blockIdx.x * NT + threadIdx.x; row < nrow; row += gridDim.x * NT) {
+    const size_t b = row_base(row, L);
+    cx<R> x[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) x[k] = X[b + k * 12];
+#pragma unroll(col_unroll<R, L>())
+    for (int j = 0; j < L; ++j) {
+      cx<R> y = mk<R>(0, 0);
+#pragma unroll
+      for (int k = 0; k < L; ++k) cmac(y, x[k], sM[k * L + j]);
+      Y[b + j * 12] = y;
+    }
+  }
+}
+
+template <typename R, int L>
+__global__ void __launch_bounds__(NT) k_update_alpha(int nrow, const cx<R>* __restrict__ V,
+                                                     const cx<R>* __restrict__ U, const double* __restrict__ alpha,
+                                                     cx<R>* __restrict__ Rv, cx<double>* __restrict__ X64) {
+  __shared__ cx<R> sA[L * L];
+  for (int e = threadIdx.x; e < L * L; e += NT) sA[e] = mk((R)alpha[2 * e], (R)alpha[2 * e + 1]);
+  __syncthreads();
+  for (int row = blockIdx.x * NT + threadIdx.x; row < nrow; row += gridDim.x * NT) {
+    const size_t b = row_base(row, L);
+    cx<R> v[L], u[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+      v[k] = V[b + k * 12];
+      u[k] = U[b + k * 12];
+    }
+#pragma unroll(col_unroll<R, L>())
+    for (int j = 0; j < L; ++j) {
+      cx<R> va = mk<R>(0, 0), ua = mk<R>(0, 0);
+#pragma unroll
+      for (int k = 0; k < L; ++k) {
+        cmac(va, v[k], sA[k * L + j]);
+        cmac(ua, u[k], sA[k * L + j]);
+      }
+      cx<R> r = Rv[b + j * 12];
+      Rv[b + j * 12] = r - va;
+      cx<double> x = X64[b + j * 12];
+      x.re += (double)ua.re;
+      x.im += (double)ua.im;
+      X64[b + j * 12] = x;
+    }
+  }
+}
+
+// zb = [zeta, beta (L x L)] complex double
+template <typename R, int L>
+__global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __restrict__ S,
+                                                    const cx<R>* __restrict__ Z, const cx<R>* __restrict__ V,
+                                                    const double* __restrict__ zb, cx<R>* __restrict__ Rv,
+                                                    cx<R>* __restrict__ P, cx<double>* __restrict__ X64,
+                                                    double* __restrict__ part) {
+  __shared__ cx<R> sB[L * L];
+  __shared__ double sred[NT];
+  for (int e = threadIdx.x; e < L * L; e += NT) sB[e] = mk((R)zb[2 + 2 * e], (R)zb[3 + 2 * e]);
+  const cx<double> zeta64 = mk(zb[0], zb[1]);
+  const cx<R> zeta = mk((R)zb[0], (R)zb[1]);
+  __syncthreads();
+  R nrm[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) nrm[j] = 0;
+  for (int row = blockIdx.x * NT + threadIdx.x; row < nrow; row += gridDim.x * NT) {
+    const long long b = row_base(row, L);
+    cx<R> rn[L], t[L];
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+      // X += zeta S (4.10), R -= zeta Z (4.11)
+      const cx<R> s = S[b + k * 12];
+      cx<double> x = X64[b + k * 12];
+      const cx<double> s64 = mk((double)s.re, (double)s.im);
+      x.re += zeta64.re * s64.re - zeta64.im * s64.im;
+      x.im += zeta64.re * s64.im + zeta64.im * s64.re;
+      X64[b + k * 12] = x;
+      const cx<R> z = Z[b + k * 12];
+      rn[k] = Rv[b + k * 12] - zeta * z;
+      Rv[b + k * 12] = rn[k];
+      nrm[k] = fma(rn[k].re, rn[k].re, fma(rn[k].im, rn[k].im, nrm[k]));
+      t[k] = P[b + k * 12] - zeta * V[b + k * 12];
+    }
+    // P = R + (P - zeta V) beta (4.13)
+#pragma unroll(col_unroll<R, L>())
+    for (int j = 0; j < L; ++j) {
+      cx<R> y = Rv[b + j * 12];  // the new R, just written
+#pragma unroll
+      for (int k = 0; k < L; ++k) cmac(y, t[k], sB[k * L + j]);
+      P[b + j * 12] = y;
+    }
+  }
+  // column norms: reduce over the CTA
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    sred[threadIdx.x] = (double)nrm[j];
+    __syncthreads();
+    for (int h = NT / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h) sred[threadIdx.x] += sred[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(long long)blockIdx.x * L + j] = sred[0];
+    __syncthreads();
+  }
+}
+
+int row_grid(long long nrow) {
+  const long long need = (nrow + NT - 1) / NT;
+  return (int)(need < 8 * 152 ? need : 8 * 152);
+}
+
+// ---------------------------------------------------------------------------
+// conversions
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_abi_to_internal(long long nsite, int L, const cx<double>* __restrict__ in, cx<R>* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // site * L + rhs
+  if (idx >= nsite * L) return;
+  const int site = idx / L;
+  const int rhs = idx - site * L;
+#pragma unroll
+  for (int sc = 0; sc < 12; ++sc) {
+    const cx<double> v = in[((size_t)site * 12 + sc) * L + rhs];
+    out[(size_t)idx * 12 + sc] = mk((R)v.re, (R)v.im);
+  }
+}
+template <typename R>
+__global__ void k_internal_to_abi(long long nsite, int L, const cx<R>* __restrict__ in, cx<double>* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nsite * L) return;
+  const int site = idx / L;
+  const int rhs = idx - site * L;
+#pragma unroll
+  for (int sc = 0; sc < 12; ++sc) {
+    const cx<R> v = in[(size_t)idx * 12 + sc];
+    out[((size_t)site * 12 + sc) * L + rhs] = mk((double)v.re, (double)v.im);
+  }
+}
+template <typename RI, typename RO>
+__global__ void k_convert(long long n, const cx<RI>* __restrict__ in, cx<RO>* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = mk((RO)in[i].re, (RO)in[i].im);
+}
+__global__ void k_convert_links(long long n, const cx<double>* __restrict__ in, cx<double>* __restrict__ l64,
+                                cx<float>* __restrict__ l32, int* bad) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const cx<double> v = in[i];
+    if (!isfinite(v.re) || !isfinite(v.im)) atomicOr(bad, 1);
+    l64[i] = v;
+    l32[i] = mk((float)v.re, (float)v.im);
+  }
+}
+
+// out = B - W (internal layout) in R, per-CTA column norms (thread rhs fixed)
+template <typename R>
+__global__ void __launch_bounds__(NT) k_residual_from(long long nsite, int L, const cx<double>* __restrict__ B,
+                                                     const cx<double>* __restrict__ W, cx<R>* __restrict__ out,
+                                                     double* __restrict__ part) {
+  __shared__ double sred[NT];
+  const int per = (NT / L) * L;  // threads used: a multiple of L, so rhs is fixed per thread
+  const int tid = threadIdx.x;
+  double acc = 0;
+  if (tid < per) {
+    const long long stride = (long long)gridDim.x * per;
+    for (long long idx = (long long)blockIdx.x * per + tid; idx < nsite * L; idx += stride) {
+#pragma unroll
+      for (int sc = 0; sc < 12; ++sc) {
+        const cx<double> b = B[idx * 12 + sc], w = W[idx * 12 + sc];
+        const cx<double> r = mk(b.re - w.re, b.im - w.im);
+        out[idx * 12 + sc] = mk((R)r.re, (R)r.im);
+        acc += r.re * r.re + r.im * r.im;
+      }
+    }
+  }
+  sred[tid] = acc;
+  __syncthreads();
+  if (tid < L) {
+    double s = 0;
+    for (int t = tid; t < per; t += L) s += sred[t];
+    part[(long long)blockIdx.x * L + tid] = s;
+  }
+}
+
+// NaN/Inf scan and column norms of an ABI-layout block ([row][rhs], row = site*12+sc)
+__global__ void __launch_bounds__(NT) k_abi_check(long long nrow, int L, const cx<double>* __restrict__ in,
+                                                 double* __restrict__ part, int* bad) {
+  __shared__ double sred[NT];
+  const int per = (NT / L) * L;
+  const int tid = threadIdx.x;
+  double acc = 0;
+  if (tid < per) {
+    const long long stride = (long long)gridDim.x * per;
+    for (long long idx = (long long)blockIdx.x * per + tid; idx < nrow * L; idx += stride) {
+      const cx<double> v = in[idx];
+      if (!isfinite(v.re) || !isfinite(v.im)) atomicOr(bad, 1);
+      acc += v.re * v.re + v.im * v.im;
+    }
+  }
+  sred[tid] = acc;
+  __syncthreads();
+  if (tid < L) {
+    double s = 0;
+    for (int t = tid; t < per; t += L) s += sred[t];
+    part[(long long)blockIdx.x * L + tid] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// L x L algebra (FP64, one CTA)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ cx<double> cdiv(cx<double> a, cx<double> b) {
+  const double d = b.re * b.re + b.im * b.im;
+  return mk((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
+}
+__device__ __forceinline__ double cabs2(cx<double> a) { return a.re * a.re + a.im * a.im; }
+
+// sum partials: dst[e] = sum_p part[p][slot0 + e], e < count (complex)
+__device__ void reduce_slots(const double* part, int nparts, int nslots, int slot0, int count, cx<double>* dst) {
+  for (int e = threadIdx.x; e < count; e += blockDim.x) {
+    double re = 0, im = 0;
+    for (int p = 0; p < nparts; ++p) {
+      re += part[((long long)p * nslots + slot0 + e) * 2];
+      im += part[((long long)p * nslots + slot0 + e) * 2 + 1];
+    }
+    dst[e] = mk(re, im);
+  }
+}
+
+__global__ void k_lxl_alpha(int L, const double* part, int nparts, double* G, double* LU, int* piv, double* alpha,
+                            int* status) {
+  __shared__ cx<double> sG[MAXL * MAXL], sC[MAXL * MAXL];
+  const int nslots = 2 * L * L + 2 * L;
+  reduce_slots(part, nparts, nslots, 0, L * L, sG);
+  reduce_slots(part, nparts, nslots, L * L, L * L, sC);
+  __syncthreads();
+  for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+    G[2 * e] = sG[e].re;
+    G[2 * e + 1] = sG[e].im;
+  }
+  if (threadIdx.x == 0) {
+    double gmax = 0;
+    for (int e = 0; e < L * L; ++e) gmax = fmax(gmax, sqrt(cabs2(sG[e])));
+    int st = isfinite(gmax) ? 0 : ST_NAN;
+    // LU with partial pivoting, C overwritten by the solution
+    for (int k = 0; k < L && !st; ++k) {
+      int p = k;
+      double best = cabs2(sG[k * L + k]);
+      for (int r = k + 1; r < L; ++r)
+        if (cabs2(sG[r * L + k]) > best) { best = cabs2(sG[r * L + k]); p = r; }
+      if (!(sqrt(best) > 1e-300 + 1e-15 * gmax)) { st |= ST_ALPHA_SINGULAR; break; }
+      piv[k] = p;
+      if (p != k) {
+        for (int c = 0; c < L; ++c) {
+          cx<double> t = sG[k * L + c]; sG[k * L + c] = sG[p * L + c]; sG[p * L + c] = t;
+          t = sC[k * L + c]; sC[k * L + c] = sC[p * L + c]; sC[p * L + c] = t;
+        }
+      }
+      for (int r = k + 1; r < L; ++r) {
+        const cx<double> f = cdiv(sG[r * L + k], sG[k * L + k]);
+        sG[r * L + k] = f;  // store the multiplier (unit lower factor)
+        for (int c = k + 1; c < L; ++c) {
+          const cx<double> a = sG[k * L + c];
+          sG[r * L + c] = mk(sG[r * L + c].re - (f.re * a.re - f.im * a.im), sG[r * L + c].im - (f.re * a.im + f.im * a.re));
+        }
+        for (int c = 0; c < L; ++c) {
+          const cx<double> a = sC[k * L + c];
+          sC[r * L + c] = mk(sC[r * L + c].re - (f.re * a.re - f.im * a.im), sC[r * L + c].im - (f.re * a.im + f.im * a.re));
+        }
+      }
+    }
+    if (!st) {
+      for (int k = L - 1; k >= 0; --k)
+        for (int c = 0; c < L; ++c) {
+          cx<double> s = sC[k * L + c];
+          for (int j = k + 1; j < L; ++j) {
+            const cx<double> a = sG[k * L + j], x = sC[j * L + c];
+            s = mk(s.re - (a.re * x.re - a.im * x.im), s.im - (a.re * x.im + a.im * x.re));
+          }
+          sC[k * L + c] = cdiv(s, sG[k * L + k]);
+        }
+      for (int e = 0; e < L * L; ++e) {
+        LU[2 * e] = sG[e].re;
+        LU[2 * e + 1] = sG[e].im;
+        alpha[2 * e] = sC[e].re;
+        alpha[2 * e + 1] = sC[e].im;
+      }
+    } else {
+      for (int e = 0; e < 2 * L * L; ++e) alpha[e] = 0;
+    }
+    *status |= st;
+  }
+}
+
+__global__ void k_lxl_zeta_beta(int L, const double* part, int nparts, const double* LU, const int* piv, double* zb,
+                                int* status) {
+  __shared__ cx<double> sC[MAXL * MAXL], sD[2 * MAXL];
+  const int nslots = 2 * L * L + 2 * L;
+  reduce_slots(part, nparts, nslots, 0, L * L, sC);
+  reduce_slots(part, nparts, nslots, 2 * L * L, 2 * L, sD);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int st = *status & ST_ALPHA_SINGULAR;
+    cx<double> zr = mk(0.0, 0.0);
+    double zz = 0;
+    for (int i = 0; i < L; ++i) {
+      zr.re += sD[i].re;
+      zr.im += sD[i].im;
+      zz += sD[L + i].re;
+    }
+    if (!isfinite(zz) || !isfinite(zr.re) || !isfinite(zr.im)) st |= ST_NAN;
+    else if (!(zz > 0)) st |= ST_ZZ_ZERO;
+    cx<double> zeta = mk(0.0, 0.0);
+    if (!st) zeta = mk(zr.re / zz, zr.im / zz);
+    zb[0] = zeta.re;
+    zb[1] = zeta.im;
+    if (!st) {
+      // beta = -(R~^H V)^-1 R~^H Z with the LU factors of the alpha solve
+      // P C: the row interchanges of the factorisation, in order, first (the
+      // stored multipliers belong to the final row order)
+      for (int e = 0; e < L * L; ++e) sC[e] = mk(-sC[e].re, -sC[e].im);
+      for (int k = 0; k < L; ++k) {
+        const int p = piv[k];
+        if (p != k)
+          for (int c = 0; c < L; ++c) { cx<double> t = sC[k * L + c]; sC[k * L + c] = sC[p * L + c]; sC[p * L + c] = t; }
+      }
+      // forward substitution with the unit lower factor
+      for (int k = 0; k < L; ++k) {
+        for (int r = k + 1; r < L; ++r) {
+          const cx<double> f = mk(LU[2 * (r * L + k)], LU[2 * (r * L + k) + 1]);
+          for (int c = 0; c < L; ++c) {
+            const cx<double> a = sC[k * L + c];
+            sC[r * L + c] = mk(sC[r * L + c].re - (f.re * a.re - f.im * a.im), sC[r * L + c].im - (f.re * a.im + f.im * a.re));
+          }
+        }
+      }
+      for (int k = L - 1; k >= 0; --k)
+        for (int c = 0; c < L; ++c) {
+          cx<double> s = sC[k * L + c];
+          for (int j = k + 1; j < L; ++j) {
+            const cx<double> a = mk(LU[2 * (k * L + j)], LU[2 * (k * L + j) + 1]), x = sC[j * L + c];
+            s = mk(s.re - (a.re * x.re - a.im * x.im), s.im - (a.re * x.im + a.im * x.re));
+          }
+          sC[k * L + c] = cdiv(s, mk(LU[2 * (k * L + k)], LU[2 * (k * L + k) + 1]));
+        }
+      for (int e = 0; e < L * L; ++e) {
+        zb[2 + 2 * e] = sC[e].re;
+        zb[3 + 2 * e] = sC[e].im;
+      }
+    } else {
+      for (int e = 0; e < 2 * L * L; ++e) zb[2 + e] = 0;
+    }
+    *status |= st;
+  }
+}
+
+// G = gamma^H gamma (gamma upper triangular, real positive diagonal); M = gamma^-1
+__global__ void k_lxl_chol(int L, const double* part, int nparts, double* M, int* status, double rel_eps) {
+  __shared__ cx<double> sG[MAXL * MAXL], sR[MAXL * MAXL];
+  const int nslots = 2 * L * L + 2 * L;
+  reduce_slots(part, nparts, nslots, 0, L * L, sG);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int st = 0;
+    for (int e = 0; e < L * L; ++e) sR[e] = mk(0.0, 0.0);
+    for (int j = 0; j < L && !st; ++j) {
+      double d = sG[j * L + j].re;
+      for (int k = 0; k < j; ++k) d -= cabs2(sR[k * L + j]);
+      if (!isfinite(d)) { st |= ST_NAN; break; }
+      if (!(d > rel_eps * sG[j * L + j].re) || !(d > 0)) { st |= ST_CHOL_FAIL; break; }
+      const double rjj = sqrt(d);
+      sR[j * L + j] = mk(rjj, 0.0);
+      for (int i = j + 1; i < L; ++i) {
+        // R_ji = (G_ji - sum_k conj(R_kj) R_ki) / R_jj
+        cx<double> s = sG[j * L + i];
+        for (int k = 0; k < j; ++k) {
+          const cx<double> a = sR[k * L + j], b = sR[k * L + i];
+          s = mk(s.re - (a.re * b.re + a.im * b.im), s.im - (a.re * b.im - a.im * b.re));
+        }
+        sR[j * L + i] = mk(s.re / rjj, s.im / rjj);
+      }
+    }
+    // M = R^-1 (upper triangular), column by column: R M = 1
+    for (int e = 0; e < L * L; ++e) sG[e] = mk(0.0, 0.0);
+    if (!st) {
+      for (int c = 0; c < L; ++c) {
+        for (int i = c; i >= 0; --i) {
+          cx<double> s = mk(i == c ? 1.0 : 0.0, 0.0);
+          for (int k = i + 1; k <= c; ++k) {
+            const cx<double> a = sR[i * L + k], x = sG[k * L + c];
+            s = mk(s.re - (a.re * x.re - a.im * x.im), s.im - (a.re * x.im + a.im * x.re));
+          }
+          sG[i * L + c] = mk(s.re / sR[i * L + i].re, s.im / sR[i * L + i].re);
+        }
+      }
+    } else {
+      for (int i = 0; i < L; ++i) sG[i * L + i] = mk(1.0, 0.0);
+    }
+    for (int e = 0; e < L * L; ++e) {
+      M[2 * e] = sG[e].re;
+      M[2 * e + 1] = sG[e].im;
+    }
+    *status |= st;
+  }
+}
+
+__global__ void k_lxl_norms(int L, const double* part, int nparts, int from_gram, double* norms, int* status) {
+  const int i = threadIdx.x;
+  if (i >= L) return;
+  double s = 0;
+  if (from_gram) {
+    const int nslots = 2 * L * L + 2 * L;
+    for (int p = 0; p < nparts; ++p) s += part[((long long)p * nslots + 2 * L * L + L + i) * 2];
+  } else {
+    for (int p = 0; p < nparts; ++p) s += part[(long long)p * L + i];
+  }
+  norms[i] = s;
+  if (!isfinite(s)) atomicOr(status, ST_NAN);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+int gram_slots(int L) { return 2 * L * L + 2 * L; }
+
+#define DISPATCH_L(L, CALL)     \
+  switch (L) {                  \
+    case 1: { constexpr int LL = 1; CALL; } break;   \
+    case 2: { constexpr int LL = 2; CALL; } break;   \
+    case 3: { constexpr int LL = 3; CALL; } break;   \
+    case 4: { constexpr int LL = 4; CALL; } break;   \
+    case 5: { constexpr int LL = 5; CALL; } break;   \
+    case 6: { constexpr int LL = 6; CALL; } break;   \
+    case 7: { constexpr int LL = 7; CALL; } break;   \
+    case 8: { constexpr int LL = 8; CALL; } break;   \
+    case 9: { constexpr int LL = 9; CALL; } break;   \
+    case 10: { constexpr int LL = 10; CALL; } break; \
+    case 11: { constexpr int LL = 11; CALL; } break; \
+    case 12: { constexpr int LL = 12; CALL; } break; \
+    case 13: { constexpr int LL = 13; CALL; } break; \
+    case 14: { constexpr int LL = 14; CALL; } break; \
+    case 15: { constexpr int LL = 15; CALL; } break; \
+    case 16: { constexpr int LL = 16; CALL; } break; \
+    default: break;             \
+  }
+
+template <typename R>
+int block_gram(const Exec& ex, long long nsite, int L, const cx<R>* A, const cx<R>* B1, const cx<R>* B2,
+               int flags, double* part) {
+  int grid = -1;
+  DISPATCH_L(L, grid = (launch_gram<R, LL>(ex, nsite, A, B1, B2, flags, part)));
+  return grid;
+}
+
+template <typename R>
+void block_transform(const Exec& ex, long long nsite, int L, const cx<R>* X, const double* M, cx<R>* Y) {
+  const int nrow = (int)(nsite * 12);
+  DISPATCH_L(L, (k_transform<R, LL><<<row_grid(nrow), NT, 0, ex.stream>>>(nrow, X, M, Y)));
+  ++*ex.launches;
+}
+
+template <typename R>
+void block_update_alpha(const Exec& ex, long long nsite, int L, const cx<R>* V, const cx<R>* U, const double* alpha,
+                        cx<R>* Rv, cx<double>* X64) {
+  const int nrow = (int)(nsite * 12);
+  DISPATCH_L(L, (k_update_alpha<R, LL><<<row_grid(nrow), NT, 0, ex.stream>>>(nrow, V, U, alpha, Rv, X64)));
+  ++*ex.launches;
+}
+
+template <typename R>
+int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* S, const cx<R>* Z, const cx<R>* V,
+                      const double* zeta_beta, cx<R>* Rv, cx<R>* P, cx<double>* X64, double* part) {
+  const int nrow = (int)(nsite * 12);
+  const int grid = row_grid(nrow);
+  DISPATCH_L(L, (k_update_zeta<R, LL><<<grid, NT, 0, ex.stream>>>(nrow, S, Z, V, zeta_beta, Rv, P, X64, part)));
+  ++*ex.launches;
+  return grid;
+}
+
+template <typename R>
+void abi_to_internal(const Exec& ex, long long nsite, int L, const cx<double>* in, cx<R>* out) {
+  const long long n = nsite * L;
+  k_abi_to_internal<R><<<(unsigned)((n + NT - 1) / NT), NT, 0, ex.stream>>>(nsite, L, in, out);
+  ++*ex.launches;
+}
+template <typename R>
+void internal_to_abi(const Exec& ex, long long nsite, int L, const cx<R>* in, cx<double>* out) {
+  const long long n = nsite * L;
+  k_internal_to_abi<R><<<(unsigned)((n + NT - 1) / NT), NT, 0, ex.stream>>>(nsite, L, in, out);
+  ++*ex.launches;
+}
+template <typename RI, typename RO>
+void convert_block(const Exec& ex, long long n, const cx<RI>* in, cx<RO>* out) {
+  k_convert<RI, RO><<<row_grid(n), NT, 0, ex.stream>>>(n, in, out);
+  ++*ex.launches;
+}
+void convert_links(const Exec& ex, long long nsite, const cx<double>* in, cx<double>* l64, cx<float>* l32, int* bad) {
+  const long long n = nsite * 36;
+  k_convert_links<<<row_grid(n), NT, 0, ex.stream>>>(n, in, l64, l32, bad);
+  ++*ex.launches;
+}
+template <typename R>
+int residual_from(const Exec& ex, long long nsite, int L, const cx<double>* B64, const cx<double>* W64, cx<R>* out,
+                  double* part) {
+  const int grid = row_grid(nsite * L);
+  k_residual_from<R><<<grid, NT, 0, ex.stream>>>(nsite, L, B64, W64, out, part);
+  ++*ex.launches;
+  return grid;
+}
+int abi_check(const Exec& ex, long long n_rows, int L, const cx<double>* in, double* part, int* bad) {
+  const int grid = row_grid(n_rows * L);
+  k_abi_check<<<grid, NT, 0, ex.stream>>>(n_rows, L, in, part, bad);
+  ++*ex.launches;
+  return grid;
+}
+
+void lxl_alpha(const Exec& ex, int L, const double* part, int nparts, SmallWork& w) {
+  k_lxl_alpha<<<1, 256, 0, ex.stream>>>(L, part, nparts, w.G, w.LU, w.piv, w.alpha, w.status);
+  ++*ex.launches;
+}
+void lxl_zeta_beta(const Exec& ex, int L, const double* part, int nparts, SmallWork& w) {
+  k_lxl_zeta_beta<<<1, 256, 0, ex.stream>>>(L, part, nparts, w.LU, w.piv, w.zb, w.status);
+  ++*ex.launches;
+}
+void lxl_cholesky_inverse(const Exec& ex, int L, const double* part, int nparts, SmallWork& w, double rel_eps) {
+  k_lxl_chol<<<1, 256, 0, ex.stream>>>(L, part, nparts, w.M, w.status, rel_eps);
+  ++*ex.launches;
+}
+void lxl_norms(const Exec& ex, int L, const double* part, int nparts, bool from_gram, SmallWork& w) {
+  k_lxl_norms<<<1, 32, 0, ex.stream>>>(L, part, nparts, from_gram ? 1 : 0, w.norms, w.status);
+  ++*ex.launches;
+}
+
+#define INST(R)                                                                                                   \
+  template int block_gram<R>(const Exec&, long long, int, const cx<R>*, const cx<R>*, const cx<R>*, int,        \
+                             double*);                                                                            \
+  template void block_transform<R>(const Exec&, long long, int, const cx<R>*, const double*, cx<R>*);              \
+  template void block_update_alpha<R>(const Exec&, long long, int, const cx<R>*, const cx<R>*, const double*,       \
+                                      cx<R>*, cx<double>*);                                                       \
+  template int block_update_zeta<R>(const Exec&, long long, int, const cx<R>*, const cx<R>*, const cx<R>*,         \
+                                    const double*, cx<R>*, cx<R>*, cx<double>*, double*);                          \
+  template void abi_to_internal<R>(const Exec&, long long, int, const cx<double>*, cx<R>*);                        \
+  template void internal_to_abi<R>(const Exec&, long long, int, const cx<R>*, cx<double>*);                        \
+  template int residual_from<R>(const Exec&, long long, int, const cx<double>*, const cx<double>*, cx<R>*, double*);
+INST(float)
+INST(double)
+#undef INST
+template void convert_block<double, float>(const Exec&, long long, const cx<double>*, cx<float>*);
+template void convert_block<float, double>(const Exec&, long long, const cx<float>*, cx<double>*);
+
+}  // namespace mbicg

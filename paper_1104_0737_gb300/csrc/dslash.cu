@@ -1,0 +1,520 @@
+// dslash.cu — the block Wilson-Dirac operator of Sec. 2.1,
+//   (A phi)_x = phi_x - kappa eta_x,
+//   eta_x = sum_mu [(1 - gamma_mu) U_mu(x) phi_{x+mu} + (1 + gamma_mu) U_mu(x-mu)^dag phi_{x-mu}],
+// for L columns at once (Eq. (bloclhoppingterm)), plus the two restrictions
+// of it that the SAP sweeps of Sec. 2.2 need: the residual eta - A psi on the
+// sites of one domain colour, and the domain operator A_dom with Dirichlet
+// boundaries (hops that leave the domain dropped) with the per-domain MR dot
+// products fused in.
+//
+// One thread per (site, rhs); the CTA is (L rhs) x (S sites) so a warp covers
+// consecutive (site, rhs) pairs, i.e. contiguous memory in the site-major
+// layout, and the L threads of one site read the same eight links (served by
+// L1 after the first).  Each hop loads the neighbour's 12 complex numbers with
+// vector loads, projects to a half spinor (6 complex), multiplies by the link
+// and rebuilds the lower spin components: 1320 flops per site and column for
+// eta, 48 more for phi - kappa eta.
+#include <cooperative_groups.h>
+
+#include "internal.h"
+
+namespace mbicg {
+
+namespace {
+
+// CTA size cap: 512 threads (<= 128 registers) for FP32, 256 for FP64, whose
+// spinors and links take twice the registers.
+template <typename R>
+constexpr int max_cta() { return sizeof(R) == 4 ? 512 : 256; }
+
+template <int MU, int SIGN, typename R>
+__device__ __forceinline__ void hop(Spinor<R>& acc, const cx<R>* psi_nb, const cx<R>* link, bool flip) {
+  Spinor<R> p;
+  load_spinor(psi_nb, p);
+  cx<R> h[2][3];
+  project<MU, SIGN>(p, h);
+  Link<R> u;
+  load_link(link, u);
+  cx<R> w[2][3];
+  const R ph = flip ? R(-1) : R(1);
+  link_times<(SIGN > 0)>(u, h, ph, w);
+  reconstruct_add<MU, SIGN>(acc, w);
+}
+
+// Accumulates eta for site s (coordinates c, coordinates inside its domain lc).
+// element offset of (site, rhs) in a site-major block
+__device__ __forceinline__ size_t spinor_offset(int s, int L, int rhs) { return (size_t)(s * L + rhs) * 12; }
+
+template <typename R, bool DIRICHLET, int MU>
+__device__ __forceinline__ void hops_mu(const Geom& g, const cx<R>* __restrict__ links,
+                                        const cx<R>* __restrict__ in, int L, int rhs, int s,
+                                        const int c[4], const int lc[4], int stride, Spinor<R>& acc) {
+  const int dm = g.d[MU];
+  // forward: (1 - gamma_mu) U_mu(x) phi_{x+mu}
+  if (!DIRICHLET || lc[MU] != g.blk[MU] - 1) {
+    const bool wrap = (c[MU] == dm - 1);
+    const int sn = wrap ? s - (dm - 1) * stride : s + stride;
+    hop<MU, -1>(acc, in + spinor_offset(sn, L, rhs), links + (size_t)(s * 4 + MU) * 9, MU == 3 && wrap);
+  }
+  // backward: (1 + gamma_mu) U_mu(x - mu)^dagger phi_{x-mu}
+  if (!DIRICHLET || lc[MU] != 0) {
+    const bool wrap = (c[MU] == 0);
+    const int sn = wrap ? s + (dm - 1) * stride : s - stride;
+    hop<MU, +1>(acc, in + spinor_offset(sn, L, rhs), links + (size_t)(sn * 4 + MU) * 9, MU == 3 && wrap);
+  }
+}
+
+template <typename R, bool DIRICHLET>
+__device__ __forceinline__ void hopping(const Geom& g, const cx<R>* __restrict__ links,
+                                        const cx<R>* __restrict__ in, int L, int rhs, int s,
+                                        const int c[4], const int lc[4], Spinor<R>& acc) {
+  zero(acc);
+  const int st1 = g.d[0];
+  const int st2 = st1 * g.d[1];
+  const int st3 = st2 * g.d[2];
+  hops_mu<R, DIRICHLET, 0>(g, links, in, L, rhs, s, c, lc, 1, acc);
+  hops_mu<R, DIRICHLET, 1>(g, links, in, L, rhs, s, c, lc, st1, acc);
+  hops_mu<R, DIRICHLET, 2>(g, links, in, L, rhs, s, c, lc, st2, acc);
+  hops_mu<R, DIRICHLET, 3>(g, links, in, L, rhs, s, c, lc, st3, acc);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(max_cta<R>()) k_dslash_full(Geom g, const cx<R>* __restrict__ links,
+                                                     const cx<R>* __restrict__ in,
+                                                     cx<R>* __restrict__ out, int L, R kappa) {
+  const int rhs = threadIdx.x;
+  const int s = blockIdx.x * blockDim.y + threadIdx.y;
+  if (s >= g.V) return;
+  int c[4];
+  site_coords(g, s, c);
+  Spinor<R> acc;
+  hopping<R, false>(g, links, in, L, rhs, s, c, c, acc);
+  Spinor<R> p;
+  load_spinor(in + spinor_offset(s, L, rhs), p);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    cx<R>& o = (&acc.c[0][0])[k];
+    const cx<R> v = (&p.c[0][0])[k];
+    o = mk(fma(-kappa, o.re, v.re), fma(-kappa, o.im, v.im));
+  }
+  store_spinor(out + spinor_offset(s, L, rhs), acc);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(max_cta<R>()) k_sap_residual(Geom g, int colour,
+                                                      const cx<R>* __restrict__ links,
+                                                      const cx<R>* __restrict__ eta,
+                                                      const cx<R>* __restrict__ psi,
+                                                      cx<R>* __restrict__ r, int L, R kappa,
+                                                      int psi_zero) {
+  const int rhs = threadIdx.x;
+  const int slot = blockIdx.x * blockDim.y + threadIdx.y;
+  int c[4], lc[4], k;
+  colour_slot_coords(g, colour, slot, c, lc, &k);
+  const int s = site_index(g, c);
+  Spinor<R> e;
+  load_spinor(eta + spinor_offset(s, L, rhs), e);
+  if (!psi_zero) {
+    Spinor<R> acc, p;
+    hopping<R, false>(g, links, psi, L, rhs, s, c, c, acc);
+    load_spinor(psi + spinor_offset(s, L, rhs), p);
+    // r = eta - (psi - kappa eta_hop) = eta - psi + kappa eta_hop
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      cx<R>& ej = (&e.c[0][0])[j];
+      const cx<R> pj = (&p.c[0][0])[j], aj = (&acc.c[0][0])[j];
+      ej = mk(fma(kappa, aj.re, ej.re - pj.re), fma(kappa, aj.im, ej.im - pj.im));
+    }
+  }
+  store_spinor(r + spinor_offset(s, L, rhs), e);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(max_cta<R>()) k_sap_domain_apply(Geom g, int colour,
+                                                          const cx<R>* __restrict__ links,
+                                                          const cx<R>* __restrict__ r,
+                                                          cx<R>* __restrict__ q,
+                                                          double* __restrict__ dots, int L, R kappa,
+                                                          int nchunk) {
+  extern __shared__ unsigned char smem_raw[];
+  R* red = reinterpret_cast<R*>(smem_raw);  // [3][S][L]
+  const int rhs = threadIdx.x;
+  const int S = blockDim.y;
+  const int slot = blockIdx.x * S + threadIdx.y;
+  int c[4], lc[4], k;
+  colour_slot_coords(g, colour, slot, c, lc, &k);
+  const int s = site_index(g, c);
+  Spinor<R> acc, p;
+  hopping<R, true>(g, links, r, L, rhs, s, c, lc, acc);
+  load_spinor(r + spinor_offset(s, L, rhs), p);
+  R nre = 0, nim = 0, den = 0;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    cx<R>& o = (&acc.c[0][0])[j];
+    const cx<R> v = (&p.c[0][0])[j];
+    o = mk(fma(-kappa, o.re, v.re), fma(-kappa, o.im, v.im));
+    // q^H r and q^H q
+    nre = fma(o.re, v.re, fma(o.im, v.im, nre));
+    nim = fma(o.re, v.im, fma(-o.im, v.re, nim));
+    den = fma(o.re, o.re, fma(o.im, o.im, den));
+  }
+  store_spinor(q + spinor_offset(s, L, rhs), acc);
+  if (dots == nullptr) return;  // uniform over the grid
+  const int t = threadIdx.y * L + rhs;
+  const int n = S * L;
+  red[t] = nre;
+  red[n + t] = nim;
+  red[2 * n + t] = den;
+  __syncthreads();
+  for (int h = S >> 1; h > 0; h >>= 1) {
+    if (threadIdx.y < h) {
+      const int u = (threadIdx.y + h) * L + rhs;
+      red[t] += red[u];
+      red[n + t] += red[n + u];
+      red[2 * n + t] += red[2 * n + u];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.y == 0) {
+    const int chunk = blockIdx.x % nchunk;
+    double* d = dots + (((long long)k * nchunk + chunk) * L + rhs) * 3;
+    d[0] = red[rhs];
+    d[1] = red[n + rhs];
+    d[2] = red[2 * n + rhs];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused SAP colour sweep with the MR iterations on chip (FP32).
+//
+// One thread-block cluster per (domain of the colour, rhs); each CTA holds
+// TPC time slices of the domain (BX*BY*BZ*TPC sites, one thread per site) and
+// keeps in shared memory the MR residual r of its sites and their forward
+// links, both structure-of-arrays so that consecutive threads read
+// consecutive words.  Hops in t that leave the CTA's slices read r (and, for
+// the backward hop, the link) from the neighbouring CTA's shared memory
+// (distributed shared memory).  x and q stay in registers.  The sweep:
+//   r = eta - A psi on the domain (psi from global, including the halo),
+//   nmr times: q = A_dom r; omega (per column from the cluster-wide dots, or
+//   from the frozen table); x += omega r; r -= omega q,
+//   psi += x.
+// ---------------------------------------------------------------------------
+template <int BX, int BY, int BZ, int BT, int TPC>
+struct SweepShape {
+  static constexpr int NS = BX * BY * BZ * TPC;  // sites per CTA = threads
+  static constexpr int CS = BT / TPC;             // CTAs per cluster
+  static constexpr int SLAB = BX * BY * BZ;
+  static constexpr size_t smem_bytes() { return sizeof(float) * (size_t)NS * (24 + 72) + 64 * sizeof(float); }
+};
+
+template <int BX, int BY, int BZ, int BT, int TPC>
+__global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256) ? 2 : 1)
+    k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const cx<float>* __restrict__ eta,
+                cx<float>* __restrict__ psi, int L, float kappa, int psi_zero, int nmr, int mode,
+                const double* __restrict__ table) {
+  using SH = SweepShape<BX, BY, BZ, BT, TPC>;
+  constexpr int NS = SH::NS;
+  constexpr int CS = SH::CS;
+  constexpr int SLAB = SH::SLAB;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ float sm[];
+  float* rS = sm;              // [24][NS]
+  float* uS = sm + 24 * NS;    // [4][18][NS]
+  float* red = uS + 72 * NS;   // [CS][4] partial dots
+
+  const int rank = (int)cluster.block_rank();
+  const int cid = blockIdx.x / CS;
+  const int k = cid / L;
+  const int rhs = cid - k * L;
+  const int tid = threadIdx.x;
+  int lc[4];
+  lc[0] = tid % BX;
+  lc[1] = (tid / BX) % BY;
+  lc[2] = (tid / (BX * BY)) % BZ;
+  const int ltl = tid / SLAB;
+  lc[3] = rank * TPC + ltl;
+  int b[4];
+  colour_domain(g, colour, k, b);
+  int c[4];
+  c[0] = b[0] * BX + lc[0];
+  c[1] = b[1] * BY + lc[1];
+  c[2] = b[2] * BZ + lc[2];
+  c[3] = b[3] * BT + lc[3];
+  const int s = site_index(g, c);
+  const size_t off = spinor_offset(s, L, rhs);
+
+  // forward links of this site into shared memory
+  {
+    const float2* gl = reinterpret_cast<const float2*>(links + (size_t)s * 36);
+#pragma unroll
+    for (int e = 0; e < 36; ++e) {
+      const float2 v = __ldg(gl + e);
+      uS[(2 * e) * NS + tid] = v.x;
+      uS[(2 * e + 1) * NS + tid] = v.y;
+    }
+  }
+  // r = eta - A psi on the domain (psi from global memory, halo included)
+  Spinor<float> r0;
+  load_spinor(eta + off, r0);
+  if (!psi_zero) {
+    Spinor<float> acc, pv;
+    hopping<float, false>(g, links, psi, L, rhs, s, c, c, acc);
+    load_spinor(psi + off, pv);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      cx<float>& e = (&r0.c[0][0])[j];
+      const cx<float> pj = (&pv.c[0][0])[j], aj = (&acc.c[0][0])[j];
+      e = mk(fmaf(kappa, aj.re, e.re - pj.re), fmaf(kappa, aj.im, e.im - pj.im));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    rS[(2 * j) * NS + tid] = (&r0.c[0][0])[j].re;
+    rS[(2 * j + 1) * NS + tid] = (&r0.c[0][0])[j].im;
+  }
+  Spinor<float> x;
+  zero(x);
+  cluster.sync();
+
+  const int ndc = g.nd / 2;
+  for (int it = 0; it < nmr; ++it) {
+    const bool last = (it == nmr - 1);
+    Spinor<float> q;
+    const bool need_q = (mode == 0) || !last;
+    if (need_q) {
+      // q = A_dom r: Dirichlet domain operator, r from (distributed) shared memory
+      zero(q);
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+        for (int fwd = 1; fwd >= 0; --fwd) {
+          const int lim = fwd ? ((mu == 0 ? BX : mu == 1 ? BY : mu == 2 ? BZ : BT) - 1) : 0;
+          if (lc[mu] == lim) continue;  // hop leaves the domain
+          const float* rsrc = rS;
+          const float* usrc = uS;
+          int nb;
+          if (mu < 3) {
+            const int st = mu == 0 ? 1 : mu == 1 ? BX : BX * BY;
+            nb = fwd ? tid + st : tid - st;
+          } else {
+            const int nl = ltl + (fwd ? 1 : -1);
+            if (nl >= 0 && nl < TPC) {
+              nb = tid + (fwd ? SLAB : -SLAB);
+            } else {
+              const int other = rank + (fwd ? 1 : -1);
+              nb = tid + (fwd ? -(TPC - 1) * SLAB : (TPC - 1) * SLAB);
+              rsrc = cluster.map_shared_rank(rS, other);
+              usrc = cluster.map_shared_rank(uS, other);
+            }
+          }
+          Spinor<float> pn;
+#pragma unroll
+          for (int j = 0; j < 12; ++j) (&pn.c[0][0])[j] = mk(rsrc[(2 * j) * NS + nb], rsrc[(2 * j + 1) * NS + nb]);
+          cx<float> h[2][3], w[2][3];
+          Link<float> u;
+          const float* ub = fwd ? uS + mu * 18 * NS + tid : usrc + mu * 18 * NS + nb;
+#pragma unroll
+          for (int e = 0; e < 9; ++e) (&u.m[0][0])[e] = mk(ub[(2 * e) * NS], ub[(2 * e + 1) * NS]);
+          if (fwd) {
+            switch (mu) {
+              case 0: project<0, -1>(pn, h); link_times<false>(u, h, 1.0f, w); reconstruct_add<0, -1>(q, w); break;
+              case 1: project<1, -1>(pn, h); link_times<false>(u, h, 1.0f, w); reconstruct_add<1, -1>(q, w); break;
+              case 2: project<2, -1>(pn, h); link_times<false>(u, h, 1.0f, w); reconstruct_add<2, -1>(q, w); break;
+              default: project<3, -1>(pn, h); link_times<false>(u, h, 1.0f, w); reconstruct_add<3, -1>(q, w); break;
+            }
+          } else {
+            switch (mu) {
+              case 0: project<0, 1>(pn, h); link_times<true>(u, h, 1.0f, w); reconstruct_add<0, 1>(q, w); break;
+              case 1: project<1, 1>(pn, h); link_times<true>(u, h, 1.0f, w); reconstruct_add<1, 1>(q, w); break;
+              case 2: project<2, 1>(pn, h); link_times<true>(u, h, 1.0f, w); reconstruct_add<2, 1>(q, w); break;
+              default: project<3, 1>(pn, h); link_times<true>(u, h, 1.0f, w); reconstruct_add<3, 1>(q, w); break;
+            }
+          }
+        }
+      }
+    }
+    // own r, and q = r - kappa * hop
+    Spinor<float> rv;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) (&rv.c[0][0])[j] = mk(rS[(2 * j) * NS + tid], rS[(2 * j + 1) * NS + tid]);
+    if (need_q) {
+#pragma unroll
+      for (int j = 0; j < 12; ++j) {
+        cx<float>& o = (&q.c[0][0])[j];
+        const cx<float> v = (&rv.c[0][0])[j];
+        o = mk(fmaf(-kappa, o.re, v.re), fmaf(-kappa, o.im, v.im));
+      }
+    }
+    cx<float> om;
+    if (mode == 0) {
+      float nre = 0, nim = 0, den = 0;
+#pragma unroll
+      for (int j = 0; j < 12; ++j) {
+        const cx<float> o = (&q.c[0][0])[j], v = (&rv.c[0][0])[j];
+        nre = fmaf(o.re, v.re, fmaf(o.im, v.im, nre));
+        nim = fmaf(o.re, v.im, fmaf(-o.im, v.re, nim));
+        den = fmaf(o.re, o.re, fmaf(o.im, o.im, den));
+      }
+      // CTA reduction: warp shuffles, then the warps' sums in a fixed order
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        nre += __shfl_xor_sync(0xffffffffu, nre, o);
+        nim += __shfl_xor_sync(0xffffffffu, nim, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+      }
+      __shared__ float wsum[NS / 32][3];
+      if ((tid & 31) == 0) {
+        wsum[tid >> 5][0] = nre;
+        wsum[tid >> 5][1] = nim;
+        wsum[tid >> 5][2] = den;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        float a = 0, bb = 0, cc = 0;
+        for (int w = 0; w < NS / 32; ++w) { a += wsum[w][0]; bb += wsum[w][1]; cc += wsum[w][2]; }
+        red[rank * 4 + 0] = a;
+        red[rank * 4 + 1] = bb;
+        red[rank * 4 + 2] = cc;
+      }
+      cluster.sync();
+      double tre = 0, tim = 0, tden = 0;
+      for (int q2 = 0; q2 < CS; ++q2) {
+        const float* rr = cluster.map_shared_rank(red, q2);
+        tre += rr[q2 * 4 + 0];
+        tim += rr[q2 * 4 + 1];
+        tden += rr[q2 * 4 + 2];
+      }
+      om = tden > 0 ? mk((float)(tre / tden), (float)(tim / tden)) : mk(0.0f, 0.0f);
+    } else {
+      const double* tb = table + ((size_t)it * ndc + k) * 2;
+      om = mk((float)tb[0], (float)tb[1]);
+      cluster.sync();  // every CTA has read its neighbours' r
+    }
+#pragma unroll
+    for (int j = 0; j < 12; ++j) cmac((&x.c[0][0])[j], om, (&rv.c[0][0])[j]);
+    if (!last) {
+      const cx<float> mom = mk(-om.re, -om.im);
+#pragma unroll
+      for (int j = 0; j < 12; ++j) {
+        cx<float> v = (&rv.c[0][0])[j];
+        cmac(v, mom, (&q.c[0][0])[j]);
+        rS[(2 * j) * NS + tid] = v.re;
+        rS[(2 * j + 1) * NS + tid] = v.im;
+      }
+      cluster.sync();  // updated r visible before the next domain operator
+    }
+  }
+  // psi += x
+  Spinor<float> pv;
+  if (psi_zero) zero(pv);
+  else load_spinor(psi + off, pv);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) (&pv.c[0][0])[j] = (&pv.c[0][0])[j] + (&x.c[0][0])[j];
+  // no CTA of the cluster may exit while others still read its shared memory
+  cluster.sync();
+  store_spinor(psi + off, pv);
+}
+
+template <int BX, int BY, int BZ, int BT, int TPC>
+bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
+                  cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table) {
+  using SH = SweepShape<BX, BY, BZ, BT, TPC>;
+  auto kern = k_sap_sweep<BX, BY, BZ, BT, TPC>;
+  const size_t shm = SH::smem_bytes();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(SH::CS * (g.nd / 2) * L));
+  cfg.blockDim = dim3(SH::NS);
+  cfg.dynamicSmemBytes = shm;
+  cfg.stream = ex.stream;
+  cudaLaunchAttribute attrs[1];
+  attrs[0].id = cudaLaunchAttributeClusterDimension;
+  attrs[0].val.clusterDim.x = SH::CS;
+  attrs[0].val.clusterDim.y = 1;
+  attrs[0].val.clusterDim.z = 1;
+  cfg.attrs = attrs;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, g, colour, links, eta, psi, L, (float)kappa, psi_zero ? 1 : 0, nmr, mode,
+                     table);
+  ++*ex.launches;
+  return true;
+}
+
+}  // namespace
+
+bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
+                     cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table) {
+  if (mode == 1) return false;
+  const int* bk = g.blk;
+  if (bk[0] == 8 && bk[1] == 8 && bk[2] == 8 && bk[3] == 8)
+    return launch_sweep<8, 8, 8, 8, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
+  if (bk[0] == 4 && bk[1] == 4 && bk[2] == 4 && bk[3] == 4)
+    return launch_sweep<4, 4, 4, 4, 4>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
+  return false;
+}
+
+namespace {
+
+int pow2_floor(int v) {
+  int p = 1;
+  while (p * 2 <= v) p *= 2;
+  return p;
+}
+
+}  // namespace
+
+int sap_sites_per_cta(const Geom& g, int L, bool fp64) {
+  int S = pow2_floor((fp64 ? 256 : 512) / L);
+  while (S > 1 && (g.Vd % S) != 0) S >>= 1;
+  return S;
+}
+
+template <typename R>
+void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
+                 double kappa) {
+  const int S = pow2_floor(max_cta<R>() / L);
+  const dim3 block(L, S);
+  const int grid = (g.V + S - 1) / S;
+  k_dslash_full<R><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa);
+  ++*ex.launches;
+}
+
+template <typename R>
+void sap_residual(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* eta,
+                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero) {
+  const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
+  const int nslot = (g.nd / 2) * g.Vd;
+  k_sap_residual<R><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, psi, r, L,
+                                                                          (R)kappa, psi_zero ? 1 : 0);
+  ++*ex.launches;
+}
+
+template <typename R>
+void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* r,
+                      cx<R>* q, double* dots, int L, double kappa, int* nchunk_out) {
+  const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
+  const int nchunk = g.Vd / S;
+  const int nslot = (g.nd / 2) * g.Vd;
+  const size_t shm = dots ? sizeof(R) * 3 * S * L : 0;
+  k_sap_domain_apply<R><<<(unsigned)(nslot / S), dim3(L, S), shm, ex.stream>>>(g, colour, links, r, q, dots,
+                                                                               L, (R)kappa, nchunk);
+  ++*ex.launches;
+  if (nchunk_out) *nchunk_out = nchunk;
+}
+
+#define INST(R)                                                                                          \
+  template void dslash_full<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double); \
+  template void sap_residual<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, const cx<R>*,   \
+                                cx<R>*, int, double, bool);                                               \
+  template void sap_domain_apply<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, cx<R>*,     \
+                                    double*, int, double, int*);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace mbicg

@@ -1,0 +1,214 @@
+// internal.h — declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace mbicg {
+
+// Optional per-kernel timing: an event pair around every launch, collected
+// into per-class totals whenever the host synchronises anyway.
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // pairs (start, stop)
+  std::vector<int> cls;         // class of each pair
+  size_t used = 0;
+  double ms[16] = {0};
+  long long count[16] = {0};
+  void begin(cudaStream_t s, int c) {
+    if (!on) return;
+    if (used == cls.size()) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      ev.push_back(a);
+      ev.push_back(b);
+      cls.push_back(c);
+    }
+    cls[used] = c;
+    cudaEventRecord(ev[2 * used], s);
+  }
+  void end(cudaStream_t s) {
+    if (!on) return;
+    cudaEventRecord(ev[2 * used + 1], s);
+    ++used;
+  }
+  // call after the stream has been synchronised
+  void collect() {
+    for (size_t i = 0; i < used; ++i) {
+      float t = 0;
+      if (cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) ms[cls[i]] += t;
+      count[cls[i]] += 1;
+    }
+    used = 0;
+  }
+  void reset() {
+    used = 0;
+    for (int c = 0; c < 16; ++c) { ms[c] = 0; count[c] = 0; }
+  }
+  void release() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    ev.clear();
+    cls.clear();
+    used = 0;
+  }
+};
+
+// kernel classes (same numbering as mbicg_kernel_class)
+enum : int { KC_DSLASH = 0, KC_DSLASH64, KC_SAP_RESID, KC_SAP_DOMAIN, KC_SAP_UPDATE, KC_GRAM, KC_AXPY,
+             KC_SMALL, KC_CONVERT, KC_SAP_SWEEP, KC_NCLASS };
+
+// Where and how a kernel is launched; every launcher adds to *launches and
+// times the launch when prof->on.
+struct Exec {
+  cudaStream_t stream;
+  long long* launches;
+  Prof* prof;
+};
+
+// RAII: time the launches in a scope as one class
+struct Timed {
+  const Exec& ex;
+  Timed(const Exec& e, int c) : ex(e) { if (ex.prof) ex.prof->begin(ex.stream, c); }
+  ~Timed() { if (ex.prof) ex.prof->end(ex.stream); }
+};
+
+// ---------------------------------------------------------------------------
+// Wilson-Dirac operator (dslash.cu), Sec. 2.1
+// ---------------------------------------------------------------------------
+// out = in - kappa * H in on every site, L columns.
+template <typename R>
+void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out,
+                 int L, double kappa);
+
+// SAP pieces on the sites of the domains of one colour (the slot numbering of
+// colour_slot_coords; arrays are full-lattice, in the internal layout).
+//   r = eta - (psi - kappa H psi)   (psi_zero: r = eta)
+template <typename R>
+void sap_residual(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* eta,
+                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero);
+//   q = r - kappa H_dom r  (hops leaving the domain dropped) and, if dots is
+//   not NULL, per-CTA partial sums of q^H r and q^H q for every column:
+//   dots[((k * nchunk) + chunk) * L + rhs] = {Re q^H r, Im q^H r, q^H q}
+template <typename R>
+void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* r,
+                      cx<R>* q, double* dots, int L, double kappa, int* nchunk_out);
+// One whole colour sweep (residual, nmr MR steps, psi += x) in one kernel,
+// the domain kept on chip by a thread-block cluster; FP32, MR modes 0 and 2,
+// domain shapes 8^4 and 4^4.  Returns false (nothing launched) otherwise.
+// table: the frozen step lengths of this (cycle, colour), [nmr][nd/2] complex.
+bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
+                     cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode,
+                     const double* table);
+// Number of sites per CTA the SAP kernels use for L columns (divides Vd).
+int sap_sites_per_cta(const Geom& g, int L, bool fp64);
+
+// ---------------------------------------------------------------------------
+// SAP preconditioner driver (sap.cu), Sec. 2.2
+// ---------------------------------------------------------------------------
+struct SapWork {
+  void* psi = nullptr;    // full lattice, precision of the SAP
+  void* r = nullptr;
+  void* q = nullptr;
+  void* x = nullptr;
+  double* dots = nullptr;     // partial sums
+  double* omega = nullptr;    // complex step lengths [domain-of-colour][rhs]
+  size_t bytes_block = 0;     // size of one full-lattice block
+  size_t dots_len = 0;
+  int L = 0;
+  bool fp64 = false;
+};
+
+// psi = M_SAP eta.  eta and psi are full-lattice blocks in the internal
+// layout and in the SAP precision (R).  mr_mode 0/1/2 as mbicg_mr_mode, with
+// table = complex [ncycle][2][nmr][nd/2] for mode 1 (recorded) and 2 (read).
+template <typename R>
+void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* eta, cx<R>* psi,
+               int L, double kappa, int ncycle, int nmr, int mr_mode, double* table, SapWork& w);
+
+// ---------------------------------------------------------------------------
+// Block linear algebra (blas.cu)
+// ---------------------------------------------------------------------------
+constexpr int MAXL = 16;
+constexpr int GRAM_CTAS = 2 * 152;  // fixed grid: deterministic partial sums
+
+// Partial sums, per CTA, of
+//   GRAM_G1: A^H B1 (L x L)      GRAM_G2: A^H B2 (L x L)
+//   GRAM_D1: diag(B1^H B2)       GRAM_D2: diag(B1^H B1)
+// part[cta][slot] complex double, slots [0, L*L) G1, [L*L, 2 L*L) G2, then L
+// for D1 and L for D2 (real part).  A may be NULL when only D1/D2 are asked.
+// Returns the number of CTAs used (<= GRAM_CTAS).
+enum : int { GRAM_G1 = 1, GRAM_G2 = 2, GRAM_D1 = 4, GRAM_D2 = 8 };
+template <typename R>
+int block_gram(const Exec& ex, long long nsite, int L, const cx<R>* A, const cx<R>* B1,
+               const cx<R>* B2, int flags, double* part);
+int gram_slots(int L);
+
+// Y = X M row by row (M: L x L complex double on the device), in place allowed.
+template <typename R>
+void block_transform(const Exec& ex, long long nsite, int L, const cx<R>* X, const double* M, cx<R>* Y);
+
+// R -= V alpha; X64 += U alpha  (alpha: L x L complex double on the device)
+template <typename R>
+void block_update_alpha(const Exec& ex, long long nsite, int L, const cx<R>* V, const cx<R>* U,
+                        const double* alpha, cx<R>* Rv, cx<double>* X64);
+
+// X64 += zeta S; R -= zeta Z; P = R + (P - zeta V) beta; partial column norms
+// of the new R into part[cta][L] (doubles).  Returns the CTAs used.
+template <typename R>
+int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* S, const cx<R>* Z,
+                      const cx<R>* V, const double* zeta_beta, cx<R>* Rv, cx<R>* P, cx<double>* X64,
+                      double* part);
+
+// ABI layout [site][sc][rhs] complex128 <-> internal [site][rhs][sc] in R.
+template <typename R>
+void abi_to_internal(const Exec& ex, long long nsite, int L, const cx<double>* in, cx<R>* out);
+template <typename R>
+void internal_to_abi(const Exec& ex, long long nsite, int L, const cx<R>* in, cx<double>* out);
+// elementwise precision change of an internal block (n complex numbers)
+template <typename RI, typename RO>
+void convert_block(const Exec& ex, long long n, const cx<RI>* in, cx<RO>* out);
+// links: ABI FP64 -> internal FP64 copy and FP32 copy; flags NaN/Inf in *bad
+void convert_links(const Exec& ex, long long nsite, const cx<double>* in, cx<double>* l64,
+                   cx<float>* l32, int* bad);
+// out = B64 - W64 converted to R, with partial column norms (part[cta][L])
+template <typename R>
+int residual_from(const Exec& ex, long long nsite, int L, const cx<double>* B64,
+                  const cx<double>* W64, cx<R>* out, double* part);
+// scan an ABI-layout block for NaN/Inf and column norms^2 (part[cta][L])
+int abi_check(const Exec& ex, long long n_rows, int L, const cx<double>* in, double* part, int* bad);
+
+// ---------------------------------------------------------------------------
+// L x L algebra on the device (single-CTA kernels, blas.cu)
+// ---------------------------------------------------------------------------
+// Device-side status bits written by the small kernels.
+enum : int { ST_ALPHA_SINGULAR = 1, ST_ZZ_ZERO = 2, ST_CHOL_FAIL = 4, ST_NAN = 8 };
+
+struct SmallWork {
+  double* G;       // R~^H V (L x L complex), kept for the beta solve
+  double* LU;      // LU factors of G
+  int* piv;
+  double* alpha;   // L x L complex
+  double* zb;      // [zeta (complex), beta (L x L complex)]
+  double* M;       // QR transform (L x L complex)
+  double* norms;   // L doubles (squared column norms)
+  int* status;
+};
+
+// alpha = (R~^H V)^-1 R~^H R from gram partials (slots 0 and 1)
+void lxl_alpha(const Exec& ex, int L, const double* part, int nparts, SmallWork& w);
+// zeta = Tr(Z^H R) / Tr(Z^H Z), beta = -(R~^H V)^-1 R~^H Z from partials of
+// (A = R~, B1 = Z, D = Z, E = R)
+void lxl_zeta_beta(const Exec& ex, int L, const double* part, int nparts, SmallWork& w);
+// Cholesky of G = P^H P = gamma^H gamma, M = gamma^-1 (slot 0 partials)
+// (rel_eps: a pivot below rel_eps * G_jj counts as a failure)
+void lxl_cholesky_inverse(const Exec& ex, int L, const double* part, int nparts, SmallWork& w,
+                          double rel_eps);
+// norms[i] = sum of partial column norms (part[cta][L], or gram slots when
+// from_gram, using the |D|^2 slots)
+void lxl_norms(const Exec& ex, int L, const double* part, int nparts, bool from_gram, SmallWork& w);
+
+}  // namespace mbicg

@@ -1,0 +1,160 @@
+// sap.cu — the SAP preconditioner of Sec. 2.2 (Schwarz alternating procedure,
+// Luescher) on checkerboard-coloured domains:
+//   psi = K sum_{j=0}^{ncycle-1} (1 - A K)^j eta,
+//   K = [[B_EE, 0], [-B_OO A_OE B_EE, B_OO]],
+// i.e. ncycle multiplicative cycles, each an E sweep then an O sweep on the
+// updated residual.  The domain solves B_EE, B_OO are nmr minimal-residual
+// steps started from zero (MR in place of the paper's SSOR).
+//
+// Each colour sweep recomputes the residual on that colour from eta and the
+// current psi (r = eta - A psi), so no residual array has to be carried
+// between sweeps, then runs the MR steps on all domains of the colour at once:
+//   q = A_dom r (Dirichlet), omega = (q^H r)/(q^H q), x += omega r, r -= omega q
+// and finally adds x to psi.  Per MR step: the domain operator with fused
+// per-CTA dot products, a small kernel that forms the step lengths (per column,
+// shared by the block, or read from a frozen table), and the update.
+#include <stdlib.h>
+
+#include <type_traits>
+
+#include "internal.h"
+
+namespace mbicg {
+
+namespace {
+
+// step lengths omega[k][rhs] for the domains of one colour
+__global__ void k_omega(int ndc, int nchunk, int L, int mode, const double* __restrict__ dots,
+                        double* __restrict__ omega, double* __restrict__ table) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ndc) return;
+  if (mode == 0) {
+    for (int rhs = 0; rhs < L; ++rhs) {
+      double nre = 0, nim = 0, den = 0;
+      for (int ch = 0; ch < nchunk; ++ch) {
+        const double* d = dots + (((long long)k * nchunk + ch) * L + rhs) * 3;
+        nre += d[0];
+        nim += d[1];
+        den += d[2];
+      }
+      omega[(k * L + rhs) * 2 + 0] = den > 0 ? nre / den : 0.0;
+      omega[(k * L + rhs) * 2 + 1] = den > 0 ? nim / den : 0.0;
+    }
+    return;
+  }
+  double ore, oim;
+  if (mode == 1) {
+    double nre = 0, nim = 0, den = 0;
+    for (int rhs = 0; rhs < L; ++rhs)
+      for (int ch = 0; ch < nchunk; ++ch) {
+        const double* d = dots + (((long long)k * nchunk + ch) * L + rhs) * 3;
+        nre += d[0];
+        nim += d[1];
+        den += d[2];
+      }
+    ore = den > 0 ? nre / den : 0.0;
+    oim = den > 0 ? nim / den : 0.0;
+    if (table) {
+      table[2 * k] = ore;
+      table[2 * k + 1] = oim;
+    }
+  } else {
+    ore = table[2 * k];
+    oim = table[2 * k + 1];
+  }
+  for (int rhs = 0; rhs < L; ++rhs) {
+    omega[(k * L + rhs) * 2 + 0] = ore;
+    omega[(k * L + rhs) * 2 + 1] = oim;
+  }
+}
+
+// x (+)= omega r; last step: psi += x, otherwise r -= omega q
+template <typename R>
+__global__ void __launch_bounds__(512) k_mr_update(Geom g, int colour, const double* __restrict__ omega,
+                                                   cx<R>* __restrict__ r, const cx<R>* __restrict__ q,
+                                                   cx<R>* __restrict__ x, cx<R>* __restrict__ psi, int L,
+                                                   int first, int last) {
+  const int rhs = threadIdx.x;
+  const int slot = blockIdx.x * blockDim.y + threadIdx.y;
+  int c[4], lc[4], k;
+  colour_slot_coords(g, colour, slot, c, lc, &k);
+  const int s = site_index(g, c);
+  const size_t off = (size_t)(s * L + rhs) * 12;
+  const cx<R> om = mk((R)omega[(k * L + rhs) * 2], (R)omega[(k * L + rhs) * 2 + 1]);
+  Spinor<R> rv, xv;
+  load_spinor(r + off, rv);
+  if (first) zero(xv);
+  else load_spinor(x + off, xv);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) cmac((&xv.c[0][0])[j], om, (&rv.c[0][0])[j]);
+  if (last) {
+    Spinor<R> pv;
+    load_spinor(psi + off, pv);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) (&pv.c[0][0])[j] = (&pv.c[0][0])[j] + (&xv.c[0][0])[j];
+    store_spinor(psi + off, pv);
+  } else {
+    Spinor<R> qv;
+    load_spinor(q + off, qv);
+    const cx<R> mom = mk(-om.re, -om.im);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) cmac((&rv.c[0][0])[j], mom, (&qv.c[0][0])[j]);
+    store_spinor(x + off, xv);
+    store_spinor(r + off, rv);
+  }
+}
+
+}  // namespace
+
+template <typename R>
+void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* eta, cx<R>* psi, int L,
+               double kappa, int ncycle, int nmr, int mr_mode, double* table, SapWork& w) {
+  cx<R>* r = static_cast<cx<R>*>(w.r);
+  cx<R>* q = static_cast<cx<R>*>(w.q);
+  cx<R>* x = static_cast<cx<R>*>(w.x);
+  const int ndc = g.nd / 2;
+  const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
+  const int nslot = ndc * g.Vd;
+  cudaMemsetAsync(psi, 0, sizeof(cx<R>) * 12 * (size_t)g.V * L, ex.stream);
+  const char* fused_env = getenv("MBICG_SAP_FUSED");
+  const bool allow_fused = !(fused_env && fused_env[0] == '0');
+  for (int cyc = 0; cyc < ncycle; ++cyc) {
+    for (int colour = 0; colour < 2; ++colour) {
+      if constexpr (std::is_same<R, float>::value) {
+        if (allow_fused && mr_mode != 1) {
+          const double* tab = table ? table + ((long long)cyc * 2 + colour) * nmr * ndc * 2 : nullptr;
+          Timed t(ex, KC_SAP_SWEEP);
+          if (sap_sweep_fused(ex, g, colour, links, eta, psi, L, kappa, cyc == 0 && colour == 0, nmr, mr_mode, tab))
+            continue;
+        }
+      }
+      {
+        Timed t(ex, KC_SAP_RESID);
+        sap_residual<R>(ex, g, colour, links, eta, psi, r, L, kappa, cyc == 0 && colour == 0);
+      }
+      for (int it = 0; it < nmr; ++it) {
+        const bool need_dots = (mr_mode != 2);
+        int nchunk = g.Vd / S;
+        // with frozen step lengths the last step needs no A_dom r: only x + omega r
+        if (need_dots || it < nmr - 1) {
+          Timed t(ex, KC_SAP_DOMAIN);
+          sap_domain_apply<R>(ex, g, colour, links, r, q, need_dots ? w.dots : nullptr, L, kappa, &nchunk);
+        }
+        Timed t(ex, KC_SAP_UPDATE);
+        double* tab = table ? table + (((long long)cyc * 2 + colour) * nmr + it) * ndc * 2 : nullptr;
+        k_omega<<<(ndc + 127) / 128, 128, 0, ex.stream>>>(ndc, nchunk, L, mr_mode, w.dots, w.omega, tab);
+        ++*ex.launches;
+        k_mr_update<R><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(
+            g, colour, w.omega, r, q, x, psi, L, it == 0 ? 1 : 0, it == nmr - 1 ? 1 : 0);
+        ++*ex.launches;
+      }
+    }
+  }
+}
+
+template void sap_apply<float>(const Exec&, const Geom&, const cx<float>*, const cx<float>*, cx<float>*, int,
+                               double, int, int, int, double*, SapWork&);
+template void sap_apply<double>(const Exec&, const Geom&, const cx<double>*, const cx<double>*, cx<double>*,
+                                int, double, int, int, int, double*, SapWork&);
+
+}  // namespace mbicg

@@ -1,0 +1,67 @@
+"""Parity of the CUDA SAP preconditioner (Sec. 2.2) with the FP64 oracle
+through the C ABI, for per-column and block-shared MR step lengths, in FP64
+(1e-12 relative per-site norm) and FP32 (1e-5)."""
+import numpy as np
+import pytest
+
+import paper_1104_0737_gb300 as mb
+import synth
+from gpu_common import make_ctx, rel_site_norm
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # dims, block, L, ncycle, nmr, kappa
+    ((4, 4, 4, 4), (2, 2, 2, 2), 4, 4, 4, 0.12),     # the plain FP64 4^4 configuration
+    ((8, 8, 8, 16), (4, 4, 4, 4), 12, 4, 4, 0.125),  # 8^3 x 16, 4^4 domains
+    ((8, 4, 4, 8), (2, 2, 2, 4), 3, 2, 5, 0.13),     # anisotropic domains
+    ((4, 4, 4, 8), (1, 1, 1, 1), 2, 1, 1, 0.13),     # single-site domains
+    ((16, 16, 16, 16), (8, 8, 8, 8), 2, 2, 3, 0.146),  # 8^4 domains (the benchmark's shape)
+]
+
+
+@pytest.mark.parametrize("dims,block,L,ncycle,nmr,kappa", CASES)
+@pytest.mark.parametrize("mr_mode", [mb.MBICG_MR_COLUMN, mb.MBICG_MR_BLOCK])
+@pytest.mark.parametrize("fused", ["1", "0"])
+def test_sap_matches_oracle(oracle_mod, monkeypatch, dims, block, L, ncycle, nmr, kappa, mr_mode,
+                            fused):
+    """fused = 1: FP32 sweeps of 8^4 and 4^4 domains run the on-chip cluster
+    kernel; fused = 0 forces the multi-kernel path everywhere."""
+    monkeypatch.setenv("MBICG_SAP_FUSED", fused)
+    ctx, U = make_ctx(dims, 0.5, seed=41)
+    try:
+        eta = synth.gaussian_source(dims, L, seed=42)
+        ref = oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, eta, mr_mode=mr_mode)
+        out = np.empty_like(eta)
+        for prec, tol in ((mb.MBICG_FP64, 1e-12), (mb.MBICG_FP32, 1e-5)):
+            p = mb.mbicg_default_params(ncycle=ncycle, nmr=nmr, block=block, mr_mode=mr_mode,
+                                        prec_sap=prec)
+            mb.mbicg_sap_precond(ctx, eta, out, L, kappa, p)
+            assert rel_site_norm(out, ref) < tol, prec
+    finally:
+        mb.mbicg_destroy(ctx)
+
+
+def test_sap_rejects_bad_blocking_and_modes():
+    dims = (8, 8, 8, 8)
+    ctx, _ = make_ctx(dims, 0.5, seed=1)
+    try:
+        eta = synth.gaussian_source(dims, 1, seed=2)
+        out = np.empty_like(eta)
+        for blk in [(8, 4, 4, 4), (3, 4, 4, 4), (2, 2, 2, 0)]:  # 1 domain in x; 3 does not divide 8
+            p = mb.mbicg_default_params(block=blk)
+            with pytest.raises(mb.MbicgError) as e:
+                mb.mbicg_sap_precond(ctx, eta, out, 1, 0.12, p)
+            assert e.value.status == mb.MBICG_EINVAL
+        p = mb.mbicg_default_params(block=(4, 4, 4, 4), mr_mode=mb.MBICG_MR_FROZEN)
+        with pytest.raises(mb.MbicgError):
+            mb.mbicg_sap_precond(ctx, eta, out, 1, 0.12, p)
+        ctx2 = mb.mbicg_create((12, 8, 8, 8))
+        mb.mbicg_load_gauge(ctx2, synth.su3_links((12, 8, 8, 8), 0.5, 3))
+        e2 = synth.gaussian_source((12, 8, 8, 8), 1, seed=4)
+        with pytest.raises(mb.MbicgError):  # 3 domains in x: no checkerboard
+            mb.mbicg_sap_precond(ctx2, e2, np.empty_like(e2), 1, 0.12,
+                                 mb.mbicg_default_params(block=(4, 4, 4, 4)))
+        mb.mbicg_destroy(ctx2)
+    finally:
+        mb.mbicg_destroy(ctx)

@@ -1,0 +1,171 @@
+"""Parity of the CUDA modified block BiCGSTAB (Algorithm 2 of Sec. 2.1, QR
+re-orthonormalisation, SAP right preconditioning) with the oracle's
+Algorithm 1 through the C ABI, and the error statuses of the ABI.
+
+FP64 loop: the residual history follows the oracle's to 1e-8 relative and the
+solutions agree to 1e-9.  Mixed precision (FP32 operator and SAP, FP64 X and
+reliable updates): true relative residual <= 1e-10 checked with the oracle's
+own operator, and solution difference <= 1e-7 against the oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_1104_0737_gb300 as mb
+import synth
+from gpu_common import make_ctx, rel_col_norm
+
+pytestmark = pytest.mark.gpu
+
+
+def history_params(n, **kw):
+    p = mb.mbicg_default_params(**kw)
+    buf = (ctypes.c_double * n)()
+    p.res_history = buf
+    p.res_history_len = n
+    return p, buf
+
+
+def oracle_true_res(oracle_mod, dims, U, kappa, B, X):
+    R = B - oracle_mod.apply_D(dims, U, kappa, X)
+    L = B.shape[-1]
+    return np.linalg.norm(R.reshape(-1, L), axis=0) / np.linalg.norm(B.reshape(-1, L), axis=0)
+
+
+@pytest.mark.parametrize("mr_mode", [mb.MBICG_MR_FROZEN, mb.MBICG_MR_COLUMN])
+def test_fp64_solve_4444_matches_oracle(oracle_mod, mr_mode):
+    """4^4 lattice, eps 0.4, kappa 0.12, L = 4 Gaussian, SAP 2^4 domains, 4
+    cycles, 4 MR, tol 1e-12, everything in FP64."""
+    dims, block, L, kappa, tol = (4, 4, 4, 4), (2, 2, 2, 2), 4, 0.12, 1e-12
+    ctx, U = make_ctx(dims, 0.4, seed=1000)
+    try:
+        B = synth.gaussian_source(dims, L, seed=2000)
+        ref = oracle_mod.block_bicgstab(dims, U, kappa, B, tol, max_iter=200, ncycle=4, nmr=4,
+                                        block=block, mr_mode=mr_mode)
+        assert ref["status"] == 0
+        p, hist = history_params(200, ncycle=4, nmr=4, block=block, mr_mode=mr_mode,
+                                 prec_D=mb.MBICG_FP64, prec_sap=mb.MBICG_FP64)
+        X = np.empty_like(B)
+        st, iters, tres = mb.mbicg_block_solve(ctx, B, X, L, kappa, tol, p)
+        assert st == mb.MBICG_OK
+        assert abs(iters - ref["iters"]) <= 1
+        n = min(iters, ref["iters"]) - 1
+        h = np.array(hist[:n])
+        assert np.max(np.abs(h - ref["history"][:n]) / ref["history"][:n]) < 1e-6
+        assert max(tres) <= tol
+        assert rel_col_norm(X, ref["X"]) < 1e-9
+        assert oracle_true_res(oracle_mod, dims, U, kappa, B, X).max() <= tol
+    finally:
+        mb.mbicg_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_point_source_solve_8c16_L12(oracle_mod, prec):
+    """8^3 x 16, eps 0.5, kappa 0.125, L = 12 point sources, SAP 4^4 domains:
+    the FP64 GPU solve and the FP32-operator/FP32-SAP mixed solve, tol 1e-10."""
+    dims, block, L, kappa, tol = (8, 8, 8, 16), (4, 4, 4, 4), 12, 0.125, 1e-10
+    ctx, U = make_ctx(dims, 0.5, seed=1001)
+    try:
+        B = synth.point_source(dims, L)
+        ref = oracle_mod.block_bicgstab(dims, U, kappa, B, 1e-12, max_iter=200, ncycle=4, nmr=4,
+                                        block=block, mr_mode=2)
+        assert ref["status"] == 0
+        pD = mb.MBICG_FP64 if prec == "fp64" else mb.MBICG_FP32
+        pS = mb.MBICG_FP64 if prec == "fp64" else mb.MBICG_FP32
+        p = mb.mbicg_default_params(ncycle=4, nmr=4, block=block, prec_D=pD, prec_sap=pS)
+        X = np.empty_like(B)
+        st, iters, tres = mb.mbicg_block_solve(ctx, B, X, L, kappa, tol, p)
+        assert st == mb.MBICG_OK
+        assert max(tres) <= tol
+        assert oracle_true_res(oracle_mod, dims, U, kappa, B, X).max() <= tol
+        assert rel_col_norm(X, ref["X"]) <= 1e-7
+    finally:
+        mb.mbicg_destroy(ctx)
+
+
+def test_L1_and_device_pointers(oracle_mod):
+    torch = pytest.importorskip("torch")
+    dims, block = (8, 4, 4, 8), (4, 2, 2, 4)
+    ctx, U = make_ctx(dims, 0.5, seed=7)
+    try:
+        B = synth.gaussian_source(dims, 1, seed=8)
+        p = mb.mbicg_default_params(ncycle=2, nmr=3, block=block)
+        dB = torch.from_numpy(B).cuda()
+        dX = torch.empty_like(dB)
+        st, iters, tres = mb.mbicg_block_solve(ctx, dB, dX, 1, 0.13, 1e-10, p)
+        assert st == mb.MBICG_OK and tres[0] <= 1e-10
+        X = dX.cpu().numpy()
+        assert oracle_true_res(oracle_mod, dims, U, 0.13, B, X).max() <= 1e-10
+        # initial guess: starting from the solution converges at once
+        p.use_x0 = 1
+        st, iters0, tres0 = mb.mbicg_block_solve(ctx, dB, dX, 1, 0.13, 1e-10, p)
+        assert st == mb.MBICG_OK and iters0 == 0
+    finally:
+        mb.mbicg_destroy(ctx)
+
+
+def test_unpreconditioned_and_block_sizes(oracle_mod):
+    dims = (4, 4, 4, 8)
+    ctx, U = make_ctx(dims, 0.5, seed=9)
+    try:
+        for L in (1, 2, 5, 16):
+            B = synth.gaussian_source(dims, L, seed=10 + L)
+            p = mb.mbicg_default_params(ncycle=0)
+            X = np.empty_like(B)
+            st, iters, tres = mb.mbicg_block_solve(ctx, B, X, L, 0.13, 1e-10, p)
+            assert st == mb.MBICG_OK, L
+            assert oracle_true_res(oracle_mod, dims, U, 0.13, B, X).max() <= 1e-10
+    finally:
+        mb.mbicg_destroy(ctx)
+
+
+def test_solver_statuses():
+    dims = (4, 4, 4, 4)
+    ctx, U = make_ctx(dims, 0.5, seed=3)
+    try:
+        B = synth.gaussian_source(dims, 2, seed=4)
+        X = np.empty_like(B)
+        p = mb.mbicg_default_params(block=(2, 2, 2, 2), max_iter=2)
+        st, iters, tres = mb.mbicg_block_solve(ctx, B, X, 2, 0.12, 1e-14, p)
+        assert st == mb.MBICG_ENOTCONV and iters == 2 and max(tres) > 1e-14
+        # two identical columns: P is rank deficient, the QR breaks down, a
+        # restart from B - A X meets the same block, and the solve reports it
+        B2 = B.copy()
+        B2[..., 1] = B2[..., 0]
+        st, iters, tres = mb.mbicg_block_solve(ctx, B2, X, 2, 0.12, 1e-10,
+                                               mb.mbicg_default_params(block=(2, 2, 2, 2)))
+        assert st == mb.MBICG_EBREAKDOWN
+        Bn = B.copy()
+        Bn[5, 1, 2, 0] = np.nan
+        with pytest.raises(mb.MbicgError) as e:
+            mb.mbicg_block_solve(ctx, Bn, X, 2, 0.12, 1e-10, mb.mbicg_default_params(block=(2, 2, 2, 2)))
+        assert e.value.status == mb.MBICG_ENAN
+        Bz = B.copy()
+        Bz[..., 0] = 0
+        with pytest.raises(mb.MbicgError) as e:
+            mb.mbicg_block_solve(ctx, Bz, X, 2, 0.12, 1e-10, mb.mbicg_default_params(block=(2, 2, 2, 2)))
+        assert e.value.status == mb.MBICG_EINVAL
+        with pytest.raises(mb.MbicgError) as e:
+            mb.mbicg_block_solve(ctx, B, X, 2, 0.12, 0.0, mb.mbicg_default_params(block=(2, 2, 2, 2)))
+        assert e.value.status == mb.MBICG_EINVAL
+        stats = mb.mbicg_get_stats(ctx)
+        assert stats["kernel_launches"] >= 0
+    finally:
+        mb.mbicg_destroy(ctx)
+
+
+def test_profiling_counts_kernels():
+    dims = (8, 8, 8, 8)
+    ctx, U = make_ctx(dims, 0.5, seed=5)
+    try:
+        B = synth.gaussian_source(dims, 4, seed=6)
+        X = np.empty_like(B)
+        mb.mbicg_set_profiling(ctx, True)
+        st, iters, _ = mb.mbicg_block_solve(ctx, B, X, 4, 0.13, 1e-10, mb.mbicg_default_params())
+        prof = mb.mbicg_get_profile(ctx)
+        assert st == mb.MBICG_OK
+        assert prof["dslash"][1] == 2 * iters
+        assert prof["sap_domain"][1] > 0 and prof["sap_domain"][0] > 0
+        assert mb.mbicg_get_stats(ctx)["kernel_launches"] > 10 * iters
+    finally:
+        mb.mbicg_destroy(ctx)
