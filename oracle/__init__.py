@@ -119,7 +119,8 @@ def sap(dims, block, U, kappa: float, ncycle: int, nmr: int, eta, mr_mode: int =
     """psi = M_SAP eta (Sec. 2.2) with nmr-step MR domain solves.
 
     mr_mode 0: step lengths per domain and column; 1: per domain, shared by the
-    columns (recorded into omega_table if given); 2: taken from omega_table.
+    columns; 2: frozen in omega_table (NaN entries are recorded from the
+    mode-1 sums the first time their domain's residual is nonzero).
     omega_table: complex array (ncycle, 2, nmr, n_domains)."""
     V = int(np.prod(dims))
     U = _cplx(U, (V, 4, 3, 3))

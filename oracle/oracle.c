@@ -399,8 +399,11 @@ int oracle_sap(const int dims[4], const int block[4], const double* Ud, double k
           }
         }
         /* step lengths: per column (mode 0), shared by the columns of the
-         * block (mode 1, the sums over columns), or read from the table of a
-         * previous mode-1 call (mode 2, a fixed linear domain solve) */
+         * block (mode 1, the sums over columns), or frozen (mode 2): a table
+         * entry is recorded from the block sums the first time its domain's
+         * MR residual is nonzero and reused from then on.  Where the residual
+         * is exactly zero the step length multiplies zero, so every call is
+         * the same linear operator, the one of the final table. */
         for (int dd = 0; dd < nd; ++dd) {
           cplx* tab = table ? table + (((long)cyc * 2 + colour) * nmr + it) * nd + dd : NULL;
           if (mr_mode == 0) {
@@ -408,15 +411,18 @@ int oracle_sap(const int dims[4], const int block[4], const double* Ud, double k
               const long di = (long)dd * L + i;
               num[di] = den[di] > 0 ? num[di] / den[di] : 0;
             }
-          } else if (mr_mode == 1) {
-            cplx n_sum = 0;
-            double d_sum = 0;
-            for (int i = 0; i < L; ++i) { n_sum += num[(long)dd * L + i]; d_sum += den[(long)dd * L + i]; }
-            const cplx om = d_sum > 0 ? n_sum / d_sum : 0;
-            for (int i = 0; i < L; ++i) num[(long)dd * L + i] = om;
-            if (tab) *tab = om;
           } else {
-            for (int i = 0; i < L; ++i) num[(long)dd * L + i] = *tab;
+            cplx om;
+            if (mr_mode == 2 && !isnan(creal(*tab))) {
+              om = *tab;
+            } else {
+              cplx n_sum = 0;
+              double d_sum = 0;
+              for (int i = 0; i < L; ++i) { n_sum += num[(long)dd * L + i]; d_sum += den[(long)dd * L + i]; }
+              om = d_sum > 0 ? n_sum / d_sum : 0;
+              if (mr_mode == 2 && d_sum > 0) *tab = om;
+            }
+            for (int i = 0; i < L; ++i) num[(long)dd * L + i] = om;
           }
         }
 #pragma omp parallel for schedule(static)
@@ -443,18 +449,13 @@ int oracle_sap(const int dims[4], const int block[4], const double* Ud, double k
 /* ------------------------------------------------------------------------ */
 /* Modified block BiCGSTAB, Algorithm 1                                      */
 /* ------------------------------------------------------------------------ */
-/* M = M_SAP, or M = 1 when ncycle == 0.  With mr_mode 2 the first call
- * records block-shared MR step lengths and every later call reuses them, so
- * that M is one fixed linear operator for the whole solve (the stationarity
- * Sec. 2.1 asks of M). */
+/* M = M_SAP, or M = 1 when ncycle == 0; with mr_mode 2 one table of frozen
+ * step lengths serves every application in the solve. */
 static void apply_M(const int dims[4], const int block[4], const double* U, double kappa,
-                    int ncycle, int nmr, int mr_mode, double* table, int* table_ready,
+                    int ncycle, int nmr, int mr_mode, double* table,
                     const cplx* in, cplx* out, int L, long NL) {
   if (ncycle == 0) {
     memcpy(out, in, sizeof(cplx) * NL);
-  } else if (mr_mode == 2 && !*table_ready) {
-    oracle_sap(dims, block, U, kappa, ncycle, nmr, 1, table, (const double*)in, (double*)out, L);
-    *table_ready = 1;
   } else {
     oracle_sap(dims, block, U, kappa, ncycle, nmr, mr_mode, table, (const double*)in,
                (double*)out, L);
@@ -479,11 +480,12 @@ int oracle_block_bicgstab(const int dims[4], const double* Ud, double kappa,
   if (ncycle > 0 && (!block || !valid_blocking(dims, block))) return -1;
   if (mr_mode < 0 || mr_mode > 2) return -1;
   double* table = NULL;
-  int table_ready = 0;
   if (ncycle > 0 && mr_mode == 2) {
     long nd = 1;
     for (int mu = 0; mu < 4; ++mu) nd *= dims[mu] / block[mu];
-    table = (double*)calloc((size_t)(2 * ncycle * 2 * (nmr > 0 ? nmr : 1) * nd), sizeof(double));
+    const long n = 2L * ncycle * 2 * (nmr > 0 ? nmr : 1) * nd;
+    table = (double*)malloc(sizeof(double) * n);
+    for (long i = 0; i < n; ++i) table[i] = NAN; /* every entry unrecorded */
   }
   const long N = 12L * volume(dims);
   const long NL = N * L;
@@ -520,7 +522,7 @@ int oracle_block_bicgstab(const int dims[4], const double* Ud, double kappa,
     /* 4.1 QR decomposition P = Q gamma, P <- Q */
     if (oracle_qr_mgs((double*)P, N, L, NULL) != 0) { status = 2; break; }
     /* 4.2 U = M P */
-    apply_M(dims, block, Ud, kappa, ncycle, nmr, mr_mode, table, &table_ready, P, Ub, L, NL);
+    apply_M(dims, block, Ud, kappa, ncycle, nmr, mr_mode, table, P, Ub, L, NL);
     /* 4.3 V = A U */
     oracle_apply_D(dims, Ud, kappa, (const double*)Ub, (double*)Vb, L);
     /* 4.4 solve (R~^H V) alpha = R~^H R */
@@ -531,7 +533,7 @@ int oracle_block_bicgstab(const int dims[4], const double* Ud, double kappa,
     block_times(Vb, alpha, N, L, W);
     for (long n = 0; n < NL; ++n) T[n] = R[n] - W[n];
     /* 4.6 S = M T */
-    apply_M(dims, block, Ud, kappa, ncycle, nmr, mr_mode, table, &table_ready, T, S, L, NL);
+    apply_M(dims, block, Ud, kappa, ncycle, nmr, mr_mode, table, T, S, L, NL);
     /* 4.7 Z = A S */
     oracle_apply_D(dims, Ud, kappa, (const double*)S, (double*)Z, L);
     /* 4.8 zeta = Tr(Z^H T) / Tr(Z^H Z) */

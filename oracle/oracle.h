@@ -50,10 +50,13 @@ int oracle_domain_colour(const int dims[4], const int block[4], int s);
  * complex step lengths omega = (q^H r)/(q^H q) are
  *   mr_mode 0: one per domain and per column;
  *   mr_mode 1: one per domain, from the sums of q^H r and q^H q over the L
- *              columns; recorded into omega_table when it is not NULL;
- *   mr_mode 2: read from omega_table (a fixed linear operator).
- * omega_table: complex [ncycle][2 colours][nmr][domain], domain numbered
- * lexicographically over domain coordinates (x fastest).
+ *              columns;
+ *   mr_mode 2: frozen: one per domain taken from omega_table; an entry that is
+ *              NaN (unrecorded) is recorded from the mode-1 sums the first
+ *              time that domain's residual is nonzero.  With one table shared
+ *              by several calls, every call applies the same linear operator.
+ * omega_table: complex [ncycle][2 colours][nmr][domain] (mode 2 only), domain
+ * numbered lexicographically over domain coordinates (x fastest).
  * Every extent of block must divide dims and give an even number (>= 2) of
  * domains per direction. */
 int oracle_sap(const int dims[4], const int block[4], const double* U, double kappa,
@@ -72,11 +75,11 @@ int oracle_qr_mgs(double* P, long N, int L, double* gamma);
 int oracle_lu_solve(const double* G, double* C, int L, int M);
 
 /* Modified block BiCGSTAB, Algorithm 1 (Sec. 2.1), right-preconditioned with
- * M = M_SAP (ncycle, nmr, block) or M = 1 when ncycle == 0.  mr_mode 0 and 1
- * are as in oracle_sap; mr_mode 2 runs the first application of M in mode 1,
- * records its step lengths and reuses them in every later application, so M
- * is one fixed linear operator for the whole solve (the stationary
- * preconditioner Sec. 2.1 asks for).
+ * M = M_SAP (ncycle, nmr, block) or M = 1 when ncycle == 0.  mr_mode as in
+ * oracle_sap; with mr_mode 2 one table of frozen step lengths (all entries
+ * unrecorded at the start) serves every application of M in the solve, so M
+ * is one fixed linear operator (the stationary preconditioner Sec. 2.1 asks
+ * for).
  *   B, X       N x L blocks in the layout above; X is the initial guess when
  *               use_x0 != 0, otherwise it is set to zero first.
  *   rtilde      the shadow block R~; NULL selects R~ = R_0.

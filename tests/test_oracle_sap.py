@@ -103,20 +103,23 @@ def test_one_mr_step_closed_form(oracle_mod, small_problem, mr_mode):
 
 
 def test_frozen_step_lengths_make_sap_linear(oracle_mod, small_problem):
-    """mr_mode 1 records the shared step lengths; mr_mode 2 replays them.  The
-    replay reproduces the recording call and is a linear operator (the
-    stationary preconditioner Sec. 2.1 requires); plain MR is not linear."""
+    """mr_mode 2 records the block-shared step lengths into an empty (NaN)
+    table and replays them afterwards.  The recording call equals mode 1, the
+    replay reproduces it, and the replay is a linear operator (the stationary
+    preconditioner Sec. 2.1 requires); plain MR is not linear."""
     dims, block, U, kappa, _ = small_problem
     nd = int(np.prod(dims)) // int(np.prod(block))
     ncycle, nmr = 2, 3
-    table = np.zeros((ncycle, 2, nmr, nd), dtype=np.complex128)
+    table = np.full((ncycle, 2, nmr, nd), np.nan, dtype=np.complex128)
     a = synth.gaussian_source(dims, 3, seed=72)
     b = synth.gaussian_source(dims, 3, seed=73)
-    rec = oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, a, mr_mode=1, omega_table=table)
+    rec = oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, a, mr_mode=2, omega_table=table)
+    assert np.max(np.abs(rec - oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, a, mr_mode=1))) < 1e-14
     # entries exist for the domains of each sweep's own colour only
     dcol = np.array([sum(np.unravel_index(d, (4 // 2,) * 4)) % 2 for d in range(nd)])
     for c in (0, 1):
-        assert np.all(table[:, c, :, dcol == c] != 0) and np.all(table[:, c, :, dcol != c] == 0)
+        assert np.all(np.isfinite(table[:, c, :, dcol == c]))
+        assert np.all(np.isnan(table[:, c, :, dcol != c]))
     rep = oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, a, mr_mode=2, omega_table=table)
     assert np.max(np.abs(rep - rec)) < 1e-14 * np.max(np.abs(rec))
     M2 = lambda v: oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, v, mr_mode=2,
@@ -127,6 +130,28 @@ def test_frozen_step_lengths_make_sap_linear(oracle_mod, small_problem):
     M0 = lambda v: oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, v, mr_mode=0)
     nonlin = M0(a + b) - (M0(a) + M0(b))
     assert np.max(np.abs(nonlin)) > 1e-3 * np.max(np.abs(rec))
+
+
+def test_frozen_table_fills_lazily_from_a_point_source(oracle_mod):
+    """A point source reaches only the domains near it in the first
+    application; the other entries stay unrecorded (their residual is exactly
+    zero, so their step length multiplies zero) and are recorded by a later
+    application with a wider input.  The first result is unchanged when it is
+    replayed with the completed table: one linear operator throughout."""
+    dims, block = (8, 8, 8, 8), (2, 2, 2, 2)
+    U = synth.su3_links(dims, 0.5, seed=74)
+    nd = int(np.prod(dims)) // int(np.prod(block))
+    ncycle, nmr, kappa = 1, 2, 0.13
+    table = np.full((ncycle, 2, nmr, nd), np.nan, dtype=np.complex128)
+    pt = synth.point_source(dims, 2)
+    first = oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, pt, mr_mode=2, omega_table=table)
+    n_first = int(np.count_nonzero(np.isfinite(table)))
+    assert 0 < n_first < table.size // 2
+    wide = synth.gaussian_source(dims, 2, seed=75)
+    oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, wide, mr_mode=2, omega_table=table)
+    assert int(np.count_nonzero(np.isfinite(table))) == table.size // 2
+    again = oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, pt, mr_mode=2, omega_table=table)
+    assert np.max(np.abs(again - first)) < 1e-14 * np.max(np.abs(first))
 
 
 def test_sap_gauge_covariance(oracle_mod):
