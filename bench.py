@@ -41,7 +41,7 @@ WORKLOADS = {
     # kappa: tuned so that the unpreconditioned BiCGSTAB (L = 1) needs > 2000
     # iterations on this field (see the design notes for the scan).
     "wilson_32c64_L12": dict(dims=(32, 32, 32, 64), eps=0.5, gauge_seed=1003, L=12, source="point",
-                             kappa=0.1525, block=(8, 8, 8, 8), ncycle=4, nmr=4, tol=1e-10),
+                             kappa=0.14775, block=(8, 8, 8, 8), ncycle=4, nmr=4, tol=1e-10),
     # smaller lattices of the same family, for quick runs
     "wilson_16c32_L12": dict(dims=(16, 16, 16, 32), eps=0.5, gauge_seed=1002, L=12, source="point",
                              kappa=0.128, block=(8, 8, 8, 8), ncycle=4, nmr=4, tol=1e-10),
@@ -51,7 +51,7 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "wilson_32c64_L12"
 # Iterations the GPU solver takes on the default workload (measured); the CPU
 # baseline extrapolates its per-iteration time with it.
-GPU_ITERS = {"wilson_32c64_L12": None}
+GPU_ITERS = {"wilson_32c64_L12": 54}
 
 METRIC = "RHS solves/s to true rel. residual 1e-10, 32^3x64 L=12; Dslash %HBM; p99 ms"
 UNIT = "RHS solves/s"
@@ -82,6 +82,29 @@ def dslash_flops(V, L):
 def sap_domain_bytes(V, L, real_bytes=4):
     # one MR step on the domains of one colour: half the sites
     return dslash_bytes(V // 2, L, real_bytes)
+
+
+def sap_sweep_bytes(V, L, real_bytes=4):
+    """One colour sweep of the fused SAP kernel: on the sweep's half of the
+    sites eta and psi read and psi written, the four forward links read, and
+    psi of the other half read once for the domain boundaries."""
+    spinor = 24 * real_bytes
+    return (V // 2) * (L * 3 * spinor + 4 * 18 * real_bytes) + (V // 2) * L * spinor
+
+
+def sap_sweep_flops(V, L, nmr, frozen=True):
+    """Residual eta - A psi (one operator application) and nmr MR steps, each a
+    domain operator application (not needed in the last step when the step
+    lengths are frozen) plus x += w r, r -= w q (16 flops per complex pair,
+    12 pairs) and, per column, the two dot products (8 flops per pair)."""
+    ops = 1 + (nmr - 1 if frozen else nmr)
+    mr = nmr * 12 * 16 + (0 if frozen else nmr * 12 * 8)
+    return (V // 2) * L * (ops * 1368 + mr)
+
+
+def fp32_alu_peak_tflops(sm_mhz, sms=152, lanes=128):
+    """FP32 FMA throughput from the unit counts: SMs x FP32 lanes x 2 flops x clock."""
+    return sms * lanes * 2 * sm_mhz * 1e6 / 1e12
 
 
 # ---------------------------------------------------------------------------
@@ -143,29 +166,30 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
-def oracle_sample(cfg, iters_full):
-    """One iteration of the oracle's Algorithm 1 (FP64, SAP with the same
+def oracle_sample(cfg, iters_full, n_iter=2):
+    """n_iter iterations of the oracle's Algorithm 1 (FP64, SAP with the same
     domains, cycles, MR steps, kappa and L) on a sub-volume of the lattice with
-    two domains per direction; its time per site and iteration, scaled to the
-    full volume and to the GPU solver's iteration count, gives RHS solves/s."""
+    two domains in x, y, z and four in t; its time per iteration, scaled by the
+    volume ratio and the GPU solver's iteration count, gives RHS solves/s.
+    The oracle's work per iteration is proportional to the volume."""
     import oracle
 
     oracle.build()
     blk = cfg["block"]
-    sdims = tuple(2 * b for b in blk)
+    sdims = (2 * blk[0], 2 * blk[1], 2 * blk[2], 4 * blk[3])
     L = cfg["L"]
     U = synth.su3_links(sdims, cfg["eps"], cfg["gauge_seed"] + 7)
     B = synth.point_source(sdims, L)
     t0 = time.perf_counter()
-    oracle.block_bicgstab(sdims, U, cfg["kappa"], B, tol=1e-300, max_iter=1, ncycle=cfg["ncycle"],
+    oracle.block_bicgstab(sdims, U, cfg["kappa"], B, tol=1e-300, max_iter=n_iter, ncycle=cfg["ncycle"],
                           nmr=cfg["nmr"], block=blk, mr_mode=2)
     dt = time.perf_counter() - t0
     scale = np.prod(cfg["dims"]) / np.prod(sdims)
-    t_solve = dt * scale * iters_full
+    t_solve = dt / n_iter * scale * iters_full
     return {
         "value": L / t_solve, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-        "sample": (f"1 iteration of Algorithm 1 (FP64 oracle, SAP {cfg['ncycle']} cycles x "
-                   f"{cfg['nmr']} MR on {'x'.join(map(str, blk))} domains) on a "
+        "sample": (f"{n_iter} iterations of Algorithm 1 (FP64 oracle, SAP {cfg['ncycle']} cycles x "
+                   f"{cfg['nmr']} MR on {'x'.join(map(str, blk))} domains, L={L}) on a "
                    f"{'x'.join(map(str, sdims))} sub-volume, {dt:.1f} s, scaled by the volume "
                    f"ratio {scale:.0f} and by the GPU solver's {iters_full} iterations"),
         "sample_seconds": dt,
@@ -304,24 +328,33 @@ def main():
         total_ms = float(t.item())
     value = world * L * args.steps / (total_ms / 1e3)
 
-    # roofline of the dominant kernel class
+    # roofline of the dominant kernel class (CUDA events around every launch on
+    # the library's stream, over the timed region)
     hbm_peak, peak_kind = load_peaks()
-    sap_cls = prof["sap_domain"]
-    cls = max(prof, key=lambda k: prof[k][0])
-    per_launch = {}
-    for name, nbytes in (("sap_domain", sap_domain_bytes(V, L)), ("dslash", dslash_bytes(V, L))):
-        ms, n = prof[name]
-        if n:
-            per_launch[name] = (nbytes, ms / n)
-    dom = "sap_domain" if sap_cls[0] >= prof["dslash"][0] else "dslash"
-    nbytes, avg_ms = per_launch[dom]
-    achieved = nbytes / (avg_ms * 1e-3) / 1e9
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": avg_ms,
-                "top_class_by_time": cls}
-    dsl_bytes, dsl_ms = per_launch.get("dslash", (None, None))
-    dslash_frac = (dsl_bytes / (dsl_ms * 1e-3) / 1e9) / hbm_peak if dsl_ms else None
+    sm_mhz = clk.get("sm_mhz") or 1492.0
+    alu_peak = fp32_alu_peak_tflops(sm_mhz)
+    models = {
+        "sap_sweep": ("alu", sap_sweep_bytes(V, L), sap_sweep_flops(V, L, cfg["nmr"])),
+        "sap_domain": ("hbm", sap_domain_bytes(V, L), dslash_flops(V // 2, L)),
+        "dslash": ("hbm", dslash_bytes(V, L), dslash_flops(V, L)),
+    }
+    dom = max((k for k in models if prof[k][1] > 0), key=lambda k: prof[k][0])
+    bound, nbytes, nflops = models[dom]
+    avg_ms = prof[dom][0] / prof[dom][1]
+    gbs = nbytes / (avg_ms * 1e-3) / 1e9
+    tfs = nflops / (avg_ms * 1e-3) / 1e12
+    if bound == "alu":
+        roofline = {"kernel": dom, "bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": tfs / alu_peak, "traffic": None,
+                    "peak_kind": f"FP32 FMA units x clock: 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz (sampled)",
+                    "algorithmic_flops_per_launch": nflops, "algorithmic_bytes_per_launch": nbytes,
+                    "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak, "avg_launch_ms": avg_ms}
+    else:
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": avg_ms}
+    dsl_ms = prof["dslash"][0] / prof["dslash"][1] if prof["dslash"][1] else None
+    dslash_frac = (dslash_bytes(V, L) / (dsl_ms * 1e-3) / 1e9) / hbm_peak if dsl_ms else None
 
     # end to end through the ABI with pinned host buffers
     e2e = None

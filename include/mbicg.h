@@ -56,10 +56,12 @@ typedef enum { MBICG_FP64 = 0, MBICG_FP32 = 1, MBICG_FP16 = 2 } mbicg_prec;
 typedef enum {
   MBICG_MR_COLUMN = 0, /* one per domain and per column (plain MR on each column) */
   MBICG_MR_BLOCK = 1,  /* one per domain, from sums over the L columns */
-  MBICG_MR_FROZEN = 2  /* block_solve only: the first application of M takes
-                          MBICG_MR_BLOCK step lengths and every later one reuses
-                          them, so M is one fixed linear operator for the whole
-                          solve (the stationary M that Sec. 2.1 requires) */
+  MBICG_MR_FROZEN = 2  /* block_solve only: one step length per domain, colour,
+                          cycle and MR step, recorded (as MBICG_MR_BLOCK) the
+                          first time that domain's MR residual is nonzero and
+                          reused by every later application, so M is one fixed
+                          linear operator for the whole solve (the stationary M
+                          that Sec. 2.1 requires) */
 } mbicg_mr_mode;
 
 typedef struct {

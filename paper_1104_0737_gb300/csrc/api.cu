@@ -237,7 +237,8 @@ struct Solver {
   cx<TS>*eta_s = nullptr, *psi_s = nullptr;  // SAP precision staging when TS != T
   SapWork sw;
   double* table = nullptr;
-  bool table_ready = false;
+  int* unset = nullptr;
+  bool table_complete = false;
   SmallWork sm{};
   double *gpart, *npart;
   double h_norm[MAXL + 1];
@@ -273,6 +274,9 @@ struct Solver {
       if ((rc = buf(c, "sap_dots", (size_t)ndc * nchunk * L * 3, &sw.dots))) return rc;
       if ((rc = buf(c, "sap_omega", (size_t)ndc * L * 2, &sw.omega))) return rc;
       if ((rc = buf(c, "sap_table", (size_t)p.ncycle * 2 * p.nmr * ndc * 2, &table))) return rc;
+      if ((rc = buf(c, "sap_unset", 1, &unset))) return rc;
+      // every frozen step length starts unrecorded (NaN)
+      CK(cudaMemsetAsync(table, 0xff, sizeof(double) * (size_t)p.ncycle * 2 * p.nmr * ndc * 2, c->stream));
     }
     if ((rc = buf(c, "gpart", (size_t)GRAM_CTAS * gram_slots(L) * 2, &gpart))) return rc;
     if ((rc = buf(c, "npart", (size_t)8 * 152 * L, &npart))) return rc;
@@ -296,20 +300,28 @@ struct Solver {
     int mode = p.mr_mode;
     double* tab = nullptr;
     if (p.mr_mode == MBICG_MR_FROZEN) {
-      mode = table_ready ? 2 : 1;
+      // record until every entry of the table is set, then replay only
+      mode = table_complete ? 3 : 2;
       tab = table;
-      table_ready = true;
+      if (!table_complete) CK(cudaMemsetAsync(unset, 0, sizeof(int), c->stream));
     }
     if constexpr (std::is_same<T, TS>::value) {
-      sap_apply<TS>(ex, g, links_S(), in, out, L, kappa, p.ncycle, p.nmr, mode, tab, sw);
+      sap_apply<TS>(ex, g, links_S(), in, out, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw);
     } else {
       {
         Timed t(ex, KC_CONVERT);
         convert_block<T, TS>(ex, (long long)nl, in, eta_s);
       }
-      sap_apply<TS>(ex, g, links_S(), eta_s, psi_s, L, kappa, p.ncycle, p.nmr, mode, tab, sw);
+      sap_apply<TS>(ex, g, links_S(), eta_s, psi_s, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw);
       Timed t(ex, KC_CONVERT);
       convert_block<TS, T>(ex, (long long)nl, psi_s, out);
+    }
+    if (mode == 2) {
+      int flag = 1;
+      CK(cudaMemcpyAsync(c->h_small, unset, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      memcpy(&flag, c->h_small, sizeof(int));
+      table_complete = (flag == 0);
     }
     return check_launch(c, "apply_M");
   }
@@ -763,7 +775,7 @@ int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double
       Timed t(ex, KC_CONVERT);
       abi_to_internal<R>(ex, c->V, L, static_cast<const cx<double>*>(si.dev), a);
     }
-    sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, p->mr_mode, nullptr, w);
+    sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, p->mr_mode, nullptr, nullptr, w);
     Timed t(ex, KC_CONVERT);
     internal_to_abi<R>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
     return MBICG_OK;

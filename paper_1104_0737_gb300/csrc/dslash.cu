@@ -207,6 +207,102 @@ struct SweepShape {
   static constexpr size_t smem_bytes() { return sizeof(float) * (size_t)NS * (24 + 72) + 64 * sizeof(float); }
 };
 
+// Hop sum over the eight neighbours of a site of the domain, reading the
+// neighbour's spinor from the (distributed) shared-memory array vS [24][NS]
+// when it lies in the domain.  Hops that leave the domain are dropped
+// (HALO = false: the Dirichlet domain operator A_dom) or taken from global
+// memory (HALO = true: the full operator, psi_g and the global links, with
+// the antiperiodic phase of the t boundary).
+template <int BX, int BY, int BZ, int BT, int TPC, bool HALO>
+__device__ __forceinline__ void domain_hops(cooperative_groups::cluster_group& cluster, const Geom& g,
+                                            const float* vS, const float* uS, int tid, int rank, int ltl,
+                                            const int lc[4], const int c[4], int s, int L, int rhs,
+                                            const cx<float>* __restrict__ links,
+                                            const cx<float>* __restrict__ psi_g, Spinor<float>& acc) {
+  constexpr int NS = BX * BY * BZ * TPC;
+  constexpr int SLAB = BX * BY * BZ;
+  zero(acc);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+    for (int fwd = 1; fwd >= 0; --fwd) {
+      const int ext = mu == 0 ? BX : mu == 1 ? BY : mu == 2 ? BZ : BT;
+      const bool leaves = fwd ? (lc[mu] == ext - 1) : (lc[mu] == 0);
+      if (leaves && !HALO) continue;
+      Spinor<float> pn;
+      Link<float> u;
+      float phase = 1.0f;
+      if (!leaves) {
+        const float* rsrc = vS;
+        const float* usrc = uS;
+        int nb;
+        if (mu < 3) {
+          const int st = mu == 0 ? 1 : mu == 1 ? BX : BX * BY;
+          nb = fwd ? tid + st : tid - st;
+        } else {
+          const int nl = ltl + (fwd ? 1 : -1);
+          if (nl >= 0 && nl < TPC) {
+            nb = tid + (fwd ? SLAB : -SLAB);
+          } else {
+            const int other = rank + (fwd ? 1 : -1);
+            nb = tid + (fwd ? -(TPC - 1) * SLAB : (TPC - 1) * SLAB);
+            rsrc = cluster.map_shared_rank(vS, other);
+            usrc = cluster.map_shared_rank(uS, other);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 12; ++j) (&pn.c[0][0])[j] = mk(rsrc[(2 * j) * NS + nb], rsrc[(2 * j + 1) * NS + nb]);
+        const float* ub = fwd ? uS + mu * 18 * NS + tid : usrc + mu * 18 * NS + nb;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) (&u.m[0][0])[e] = mk(ub[(2 * e) * NS], ub[(2 * e + 1) * NS]);
+      } else {
+        // the neighbour is in another domain: global memory
+        const int dm = g.d[mu];
+        const int stride = mu == 0 ? 1 : mu == 1 ? g.d[0] : mu == 2 ? g.d[0] * g.d[1] : g.d[0] * g.d[1] * g.d[2];
+        const bool wrap = fwd ? (c[mu] == dm - 1) : (c[mu] == 0);
+        const int sn = fwd ? (wrap ? s - (dm - 1) * stride : s + stride) : (wrap ? s + (dm - 1) * stride : s - stride);
+        if (mu == 3 && wrap) phase = -1.0f;
+        load_spinor(psi_g + spinor_offset(sn, L, rhs), pn);
+        if (fwd) {
+          const float* ub = uS + mu * 18 * NS + tid;
+#pragma unroll
+          for (int e = 0; e < 9; ++e) (&u.m[0][0])[e] = mk(ub[(2 * e) * NS], ub[(2 * e + 1) * NS]);
+        } else {
+          load_link(links + (size_t)(sn * 4 + mu) * 9, u);
+        }
+      }
+      cx<float> h[2][3], w[2][3];
+      if (fwd) {
+        switch (mu) {
+          case 0: project<0, -1>(pn, h); link_times<false>(u, h, phase, w); reconstruct_add<0, -1>(acc, w); break;
+          case 1: project<1, -1>(pn, h); link_times<false>(u, h, phase, w); reconstruct_add<1, -1>(acc, w); break;
+          case 2: project<2, -1>(pn, h); link_times<false>(u, h, phase, w); reconstruct_add<2, -1>(acc, w); break;
+          default: project<3, -1>(pn, h); link_times<false>(u, h, phase, w); reconstruct_add<3, -1>(acc, w); break;
+        }
+      } else {
+        switch (mu) {
+          case 0: project<0, 1>(pn, h); link_times<true>(u, h, phase, w); reconstruct_add<0, 1>(acc, w); break;
+          case 1: project<1, 1>(pn, h); link_times<true>(u, h, phase, w); reconstruct_add<1, 1>(acc, w); break;
+          case 2: project<2, 1>(pn, h); link_times<true>(u, h, phase, w); reconstruct_add<2, 1>(acc, w); break;
+          default: project<3, 1>(pn, h); link_times<true>(u, h, phase, w); reconstruct_add<3, 1>(acc, w); break;
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void spinor_to_soa(float* vS, int NS, int tid, const Spinor<float>& v) {
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    vS[(2 * j) * NS + tid] = (&v.c[0][0])[j].re;
+    vS[(2 * j + 1) * NS + tid] = (&v.c[0][0])[j].im;
+  }
+}
+__device__ __forceinline__ void soa_to_spinor(const float* vS, int NS, int tid, Spinor<float>& v) {
+#pragma unroll
+  for (int j = 0; j < 12; ++j) (&v.c[0][0])[j] = mk(vS[(2 * j) * NS + tid], vS[(2 * j + 1) * NS + tid]);
+}
+
 template <int BX, int BY, int BZ, int BT, int TPC>
 __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256) ? 2 : 1)
     k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const cx<float>* __restrict__ eta,
@@ -219,9 +315,10 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ float sm[];
-  float* rS = sm;              // [24][NS]
-  float* uS = sm + 24 * NS;    // [4][18][NS]
+  float* rS = sm;              // [24][NS]: psi, then the MR residual r
+  float* uS = sm + 24 * NS;    // [4][18][NS] forward links
   float* red = uS + 72 * NS;   // [CS][4] partial dots
+  __shared__ float wsum[NS / 32][3];
 
   const int rank = (int)cluster.block_rank();
   const int cid = blockIdx.x / CS;
@@ -254,13 +351,16 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
       uS[(2 * e + 1) * NS + tid] = v.y;
     }
   }
-  // r = eta - A psi on the domain (psi from global memory, halo included)
+  // r = eta - A psi on the domain: psi staged in shared memory, the halo
+  // (neighbours in other domains) from global memory
   Spinor<float> r0;
   load_spinor(eta + off, r0);
   if (!psi_zero) {
-    Spinor<float> acc, pv;
-    hopping<float, false>(g, links, psi, L, rhs, s, c, c, acc);
+    Spinor<float> pv, acc;
     load_spinor(psi + off, pv);
+    spinor_to_soa(rS, NS, tid, pv);
+    cluster.sync();
+    domain_hops<BX, BY, BZ, BT, TPC, true>(cluster, g, rS, uS, tid, rank, ltl, lc, c, s, L, rhs, links, psi, acc);
 #pragma unroll
     for (int j = 0; j < 12; ++j) {
       cx<float>& e = (&r0.c[0][0])[j];
@@ -268,11 +368,8 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
       e = mk(fmaf(kappa, aj.re, e.re - pj.re), fmaf(kappa, aj.im, e.im - pj.im));
     }
   }
-#pragma unroll
-  for (int j = 0; j < 12; ++j) {
-    rS[(2 * j) * NS + tid] = (&r0.c[0][0])[j].re;
-    rS[(2 * j + 1) * NS + tid] = (&r0.c[0][0])[j].im;
-  }
+  cluster.sync();  // psi reads done (and the links of every CTA are in place)
+  spinor_to_soa(rS, NS, tid, r0);
   Spinor<float> x;
   zero(x);
   cluster.sync();
@@ -280,64 +377,11 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
   const int ndc = g.nd / 2;
   for (int it = 0; it < nmr; ++it) {
     const bool last = (it == nmr - 1);
-    Spinor<float> q;
+    Spinor<float> q, rv;
     const bool need_q = (mode == 0) || !last;
-    if (need_q) {
-      // q = A_dom r: Dirichlet domain operator, r from (distributed) shared memory
-      zero(q);
-#pragma unroll
-      for (int mu = 0; mu < 4; ++mu) {
-#pragma unroll
-        for (int fwd = 1; fwd >= 0; --fwd) {
-          const int lim = fwd ? ((mu == 0 ? BX : mu == 1 ? BY : mu == 2 ? BZ : BT) - 1) : 0;
-          if (lc[mu] == lim) continue;  // hop leaves the domain
-          const float* rsrc = rS;
-          const float* usrc = uS;
-          int nb;
-          if (mu < 3) {
-            const int st = mu == 0 ? 1 : mu == 1 ? BX : BX * BY;
-            nb = fwd ? tid + st : tid - st;
-          } else {
-            const int nl = ltl + (fwd ? 1 : -1);
-            if (nl >= 0 && nl < TPC) {
-              nb = tid + (fwd ? SLAB : -SLAB);
-            } else {
-              const int other = rank + (fwd ? 1 : -1);
-              nb = tid + (fwd ? -(TPC - 1) * SLAB : (TPC - 1) * SLAB);
-              rsrc = cluster.map_shared_rank(rS, other);
-              usrc = cluster.map_shared_rank(uS, other);
-            }
-          }
-          Spinor<float> pn;
-#pragma unroll
-          for (int j = 0; j < 12; ++j) (&pn.c[0][0])[j] = mk(rsrc[(2 * j) * NS + nb], rsrc[(2 * j + 1) * NS + nb]);
-          cx<float> h[2][3], w[2][3];
-          Link<float> u;
-          const float* ub = fwd ? uS + mu * 18 * NS + tid : usrc + mu * 18 * NS + nb;
-#pragma unroll
-          for (int e = 0; e < 9; ++e) (&u.m[0][0])[e] = mk(ub[(2 * e) * NS], ub[(2 * e + 1) * NS]);
-          if (fwd) {
-            switch (mu) {
-              case 0: project<0, -1>(pn, h); link_times<false>(u, h, 1.0f, w); reconstruct_add<0, -1>(q, w); break;
-              case 1: project<1, -1>(pn, h); link_times<false>(u, h, 1.0f, w); reconstruct_add<1, -1>(q, w); break;
-              case 2: project<2, -1>(pn, h); link_times<false>(u, h, 1.0f, w); reconstruct_add<2, -1>(q, w); break;
-              default: project<3, -1>(pn, h); link_times<false>(u, h, 1.0f, w); reconstruct_add<3, -1>(q, w); break;
-            }
-          } else {
-            switch (mu) {
-              case 0: project<0, 1>(pn, h); link_times<true>(u, h, 1.0f, w); reconstruct_add<0, 1>(q, w); break;
-              case 1: project<1, 1>(pn, h); link_times<true>(u, h, 1.0f, w); reconstruct_add<1, 1>(q, w); break;
-              case 2: project<2, 1>(pn, h); link_times<true>(u, h, 1.0f, w); reconstruct_add<2, 1>(q, w); break;
-              default: project<3, 1>(pn, h); link_times<true>(u, h, 1.0f, w); reconstruct_add<3, 1>(q, w); break;
-            }
-          }
-        }
-      }
-    }
-    // own r, and q = r - kappa * hop
-    Spinor<float> rv;
-#pragma unroll
-    for (int j = 0; j < 12; ++j) (&rv.c[0][0])[j] = mk(rS[(2 * j) * NS + tid], rS[(2 * j + 1) * NS + tid]);
+    if (need_q) domain_hops<BX, BY, BZ, BT, TPC, false>(cluster, g, rS, uS, tid, rank, ltl, lc, c, s, L, rhs, links,
+                                                       psi, q);
+    soa_to_spinor(rS, NS, tid, rv);
     if (need_q) {
 #pragma unroll
       for (int j = 0; j < 12; ++j) {
@@ -363,7 +407,6 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
         nim += __shfl_xor_sync(0xffffffffu, nim, o);
         den += __shfl_xor_sync(0xffffffffu, den, o);
       }
-      __shared__ float wsum[NS / 32][3];
       if ((tid & 31) == 0) {
         wsum[tid >> 5][0] = nre;
         wsum[tid >> 5][1] = nim;
@@ -396,12 +439,8 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
     if (!last) {
       const cx<float> mom = mk(-om.re, -om.im);
 #pragma unroll
-      for (int j = 0; j < 12; ++j) {
-        cx<float> v = (&rv.c[0][0])[j];
-        cmac(v, mom, (&q.c[0][0])[j]);
-        rS[(2 * j) * NS + tid] = v.re;
-        rS[(2 * j + 1) * NS + tid] = v.im;
-      }
+      for (int j = 0; j < 12; ++j) cmac((&rv.c[0][0])[j], mom, (&q.c[0][0])[j]);
+      spinor_to_soa(rS, NS, tid, rv);
       cluster.sync();  // updated r visible before the next domain operator
     }
   }

@@ -123,11 +123,15 @@ struct SapWork {
 };
 
 // psi = M_SAP eta.  eta and psi are full-lattice blocks in the internal
-// layout and in the SAP precision (R).  mr_mode 0/1/2 as mbicg_mr_mode, with
-// table = complex [ncycle][2][nmr][nd/2] for mode 1 (recorded) and 2 (read).
+// layout and in the SAP precision (R).  mr_mode: 0 per column, 1 shared by the
+// columns, 2 frozen while recording (NaN entries of table are recorded from
+// the shared sums where the domain's residual is nonzero; *unset is raised if
+// an entry stays unrecorded), 3 frozen replay.
+// table = complex [ncycle][2][nmr][nd/2] (modes 2, 3).
 template <typename R>
 void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* eta, cx<R>* psi,
-               int L, double kappa, int ncycle, int nmr, int mr_mode, double* table, SapWork& w);
+               int L, double kappa, int ncycle, int nmr, int mr_mode, double* table, int* unset,
+               SapWork& w);
 
 // ---------------------------------------------------------------------------
 // Block linear algebra (blas.cu)

@@ -13,6 +13,7 @@
 // and finally adds x to psi.  Per MR step: the domain operator with fused
 // per-CTA dot products, a small kernel that forms the step lengths (per column,
 // shared by the block, or read from a frozen table), and the update.
+#include <math.h>
 #include <stdlib.h>
 
 #include <type_traits>
@@ -23,9 +24,13 @@ namespace mbicg {
 
 namespace {
 
-// step lengths omega[k][rhs] for the domains of one colour
+// Step lengths omega[k][rhs] for the domains of one colour.
+//   mode 0: per column; mode 1: shared by the columns (sums over them);
+//   mode 2: frozen, recording: a NaN table entry is recorded from the mode-1
+//           sums when the domain's residual is nonzero (otherwise omega
+//           multiplies zero and *unset is raised); mode 3: frozen, replay.
 __global__ void k_omega(int ndc, int nchunk, int L, int mode, const double* __restrict__ dots,
-                        double* __restrict__ omega, double* __restrict__ table) {
+                        double* __restrict__ omega, double* __restrict__ table, int* __restrict__ unset) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= ndc) return;
   if (mode == 0) {
@@ -43,7 +48,10 @@ __global__ void k_omega(int ndc, int nchunk, int L, int mode, const double* __re
     return;
   }
   double ore, oim;
-  if (mode == 1) {
+  if (mode == 3 || (mode == 2 && !isnan(table[2 * k]))) {
+    ore = table[2 * k];
+    oim = table[2 * k + 1];
+  } else {
     double nre = 0, nim = 0, den = 0;
     for (int rhs = 0; rhs < L; ++rhs)
       for (int ch = 0; ch < nchunk; ++ch) {
@@ -54,13 +62,14 @@ __global__ void k_omega(int ndc, int nchunk, int L, int mode, const double* __re
       }
     ore = den > 0 ? nre / den : 0.0;
     oim = den > 0 ? nim / den : 0.0;
-    if (table) {
-      table[2 * k] = ore;
-      table[2 * k + 1] = oim;
+    if (mode == 2) {
+      if (den > 0) {
+        table[2 * k] = ore;
+        table[2 * k + 1] = oim;
+      } else {
+        atomicOr(unset, 1);
+      }
     }
-  } else {
-    ore = table[2 * k];
-    oim = table[2 * k + 1];
   }
   for (int rhs = 0; rhs < L; ++rhs) {
     omega[(k * L + rhs) * 2 + 0] = ore;
@@ -108,7 +117,7 @@ __global__ void __launch_bounds__(512) k_mr_update(Geom g, int colour, const dou
 
 template <typename R>
 void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* eta, cx<R>* psi, int L,
-               double kappa, int ncycle, int nmr, int mr_mode, double* table, SapWork& w) {
+               double kappa, int ncycle, int nmr, int mr_mode, double* table, int* unset, SapWork& w) {
   cx<R>* r = static_cast<cx<R>*>(w.r);
   cx<R>* q = static_cast<cx<R>*>(w.q);
   cx<R>* x = static_cast<cx<R>*>(w.x);
@@ -121,7 +130,7 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
   for (int cyc = 0; cyc < ncycle; ++cyc) {
     for (int colour = 0; colour < 2; ++colour) {
       if constexpr (std::is_same<R, float>::value) {
-        if (allow_fused && mr_mode != 1) {
+        if (allow_fused && (mr_mode == 0 || mr_mode == 3)) {
           const double* tab = table ? table + ((long long)cyc * 2 + colour) * nmr * ndc * 2 : nullptr;
           Timed t(ex, KC_SAP_SWEEP);
           if (sap_sweep_fused(ex, g, colour, links, eta, psi, L, kappa, cyc == 0 && colour == 0, nmr, mr_mode, tab))
@@ -133,16 +142,16 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
         sap_residual<R>(ex, g, colour, links, eta, psi, r, L, kappa, cyc == 0 && colour == 0);
       }
       for (int it = 0; it < nmr; ++it) {
-        const bool need_dots = (mr_mode != 2);
+        const bool need_dots = (mr_mode != 3);
         int nchunk = g.Vd / S;
-        // with frozen step lengths the last step needs no A_dom r: only x + omega r
+        // replaying frozen step lengths, the last step needs no A_dom r: only x + omega r
         if (need_dots || it < nmr - 1) {
           Timed t(ex, KC_SAP_DOMAIN);
           sap_domain_apply<R>(ex, g, colour, links, r, q, need_dots ? w.dots : nullptr, L, kappa, &nchunk);
         }
         Timed t(ex, KC_SAP_UPDATE);
         double* tab = table ? table + (((long long)cyc * 2 + colour) * nmr + it) * ndc * 2 : nullptr;
-        k_omega<<<(ndc + 127) / 128, 128, 0, ex.stream>>>(ndc, nchunk, L, mr_mode, w.dots, w.omega, tab);
+        k_omega<<<(ndc + 127) / 128, 128, 0, ex.stream>>>(ndc, nchunk, L, mr_mode, w.dots, w.omega, tab, unset);
         ++*ex.launches;
         k_mr_update<R><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(
             g, colour, w.omega, r, q, x, psi, L, it == 0 ? 1 : 0, it == nmr - 1 ? 1 : 0);
@@ -153,8 +162,8 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
 }
 
 template void sap_apply<float>(const Exec&, const Geom&, const cx<float>*, const cx<float>*, cx<float>*, int,
-                               double, int, int, int, double*, SapWork&);
+                               double, int, int, int, double*, int*, SapWork&);
 template void sap_apply<double>(const Exec&, const Geom&, const cx<double>*, const cx<double>*, cx<double>*,
-                                int, double, int, int, int, double*, SapWork&);
+                                int, double, int, int, int, double*, int*, SapWork&);
 
 }  // namespace mbicg
