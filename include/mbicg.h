@@ -174,6 +174,33 @@ int mbicg_get_profile(const mbicg_ctx* ctx, double* ms, long long* launches, int
 /* Text of the last error on ctx ("" if none).  Valid until the next call. */
 const char* mbicg_last_error(const mbicg_ctx* ctx);
 
+/* Size of the fixed scratch array of mbicg_apply_D_noalloc, in MiB. */
+#define MBICG_NOALLOC_SCRATCH_MB 32
+
+/* out = A in in FP32, the same result as mbicg_apply_D(..., MBICG_FP32), for
+ * callers that cannot allocate device memory: code recording a stream into a
+ * CUDA graph (an allocation is not a capturable operation), code that must
+ * stay inside a framework's memory pool, real-time loops that may not take
+ * the allocator's locks.  It allocates nothing and needs no context.  The
+ * paper has no counterpart to this entry point.
+ *   dims         lattice extents (even, >= 2)
+ *   U, in, out   device pointers in the layouts above; in and out must not
+ *                alias; U is the FP64 gauge field
+ *   cuda_stream  a cudaStream_t or NULL; the work is ordered on it and the call
+ *                returns without waiting for it
+ * Its scratch is one file-scope device array of MBICG_NOALLOC_SCRATCH_MB MiB
+ * per device, held by every process that loads the library until it exits:
+ * the FP32 links (288 V bytes) and two FP32 blocks (96 L V bytes each), each
+ * rounded up to 256 bytes, must fit in it, else MBICG_EINVAL (nothing is
+ * launched).  Every call shares the array; calls that overlap on the GPU (two
+ * streams, two host threads) race on it.  The first call on a device looks
+ * the array's address up (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture begins.
+ * Returns MBICG_EINVAL for bad arguments or host pointers, MBICG_ECUDA if the
+ * lookup or a launch fails. */
+int mbicg_apply_D_noalloc(const int dims[4], const double* U, const double* in, double* out, int L,
+                          double kappa, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

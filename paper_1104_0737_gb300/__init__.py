@@ -23,7 +23,7 @@ __all__ = [
     "MbicgError", "mbicg_params", "mbicg_stats", "library_path", "load_library",
     "mbicg_default_params", "mbicg_create", "mbicg_destroy", "mbicg_load_gauge",
     "mbicg_apply_D", "mbicg_sap_precond", "mbicg_block_solve", "mbicg_get_stats",
-    "mbicg_last_error", "mbicg_set_profiling", "mbicg_get_profile",
+    "mbicg_last_error", "mbicg_set_profiling", "mbicg_get_profile", "mbicg_apply_D_noalloc",
 ]
 
 MBICG_OK, MBICG_EINVAL, MBICG_ENOMEM, MBICG_ENOGAUGE = 0, -1, -2, -3
@@ -93,6 +93,7 @@ def load_library(build_if_missing: bool = True):
     lib.mbicg_last_error.restype = ctypes.c_char_p
     lib.mbicg_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.mbicg_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+    lib.mbicg_apply_D_noalloc.argtypes = [ip, vp, vp, vp, ctypes.c_int, ctypes.c_double, vp]
     _lib = lib
     return lib
 
@@ -201,3 +202,21 @@ def mbicg_get_profile(ctx) -> dict:
     cnt = (ctypes.c_longlong * n)()
     _check(ctx, load_library().mbicg_get_profile(ctx, ms, cnt, n))
     return {KERNEL_CLASSES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def mbicg_apply_D_noalloc(dims, U, inp, out, L: int, kappa: float, stream=None) -> None:
+    """out = A in (FP32) without any allocation, for callers that cannot
+    allocate device memory (stream capture, fixed memory pools).  U, inp, out:
+    CUDA tensors.  Ordered on `stream` (torch.cuda.Stream, raw handle or None);
+    returns without waiting.  Concurrent calls share one scratch array and race."""
+    pu, _ = _ptr(U, "U")
+    pi, _ = _ptr(inp, "in")
+    po, _ = _ptr(out, "out")
+    raw = None
+    if stream is not None:
+        raw = ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    st = load_library().mbicg_apply_D_noalloc(d, pu, pi, po, int(L), float(kappa), raw)
+    if st != MBICG_OK:
+        raise MbicgError(st, "mbicg_apply_D_noalloc failed (sizes beyond the scratch, host "
+                             "pointers or a CUDA error)")
