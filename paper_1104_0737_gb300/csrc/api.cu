@@ -332,16 +332,17 @@ struct Solver {
     return MBICG_OK;
   }
 
-  // R = B - A X in FP64, converted to T; host norms in h_norm
-  int true_residual(double* rel, double* relmax) {
-    {
+  // R = B - A X in FP64, converted to T; host norms in h_norm.  x_zero: X = 0
+  // is known, so R = B without applying the operator.
+  int true_residual(double* rel, double* relmax, bool x_zero = false) {
+    if (!x_zero) {
       Timed t(ex, KC_DSLASH64);
       dslash_full<double>(ex, g, c->U64, X64, W64, L, kappa);
     }
     int np;
     {
       Timed t(ex, KC_CONVERT);
-      np = residual_from<T>(ex, V, L, B64, W64, k.R, npart);
+      np = residual_from<T>(ex, V, L, B64, x_zero ? nullptr : W64, k.R, npart);
     }
     lxl_norms(ex, L, npart, np, false, sm);
     int rc = check_launch(c, "true_residual");
@@ -361,7 +362,7 @@ struct Solver {
       int np;
       {
         Timed t(ex, KC_GRAM);
-        np = block_gram<T>(ex, V, L, k.P, k.P, nullptr, GRAM_G1, gpart);
+        np = block_gram<T>(ex, V, L, k.P, k.P, nullptr, GRAM_G1, gpart, sm.status);
       }
       {
         Timed t(ex, KC_SMALL);
@@ -387,7 +388,7 @@ struct Solver {
     CK(cudaMemsetAsync(sm.status, 0, sizeof(int), c->stream));
     double rel[MAXL], relmax;
     // line 2: R = B - A X
-    if ((rc = true_residual(rel, &relmax))) return rc;
+    if ((rc = true_residual(rel, &relmax, !p.use_x0))) return rc;
     // lines 3-4: P = R, R~ = R
     CK(cudaMemcpyAsync(k.P, k.R, sizeof(cx<T>) * nl, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemcpyAsync(k.Rt, k.R, sizeof(cx<T>) * nl, cudaMemcpyDeviceToDevice, c->stream));
@@ -421,15 +422,15 @@ struct Solver {
         int np;
         {
           Timed t(ex, KC_GRAM);
-          np = block_gram<T>(ex, V, L, k.Rt, k.V, k.R, GRAM_G1 | GRAM_G2, gpart);
+          np = block_gram<T>(ex, V, L, k.Rt, k.V, k.R, GRAM_G1 | GRAM_G2, gpart, sm.status);
         }
         Timed t(ex, KC_SMALL);
         lxl_alpha(ex, L, gpart, np, sm);
       }
-      // 4.5 R -= V alpha, 4.6 X += U alpha
+      // 4.5 R -= V alpha (4.6, X += U alpha, is folded into the update after zeta)
       {
         Timed t(ex, KC_AXPY);
-        block_update_alpha<T>(ex, V, L, k.V, k.U, sm.alpha, k.R, X64);
+        block_update_alpha<T>(ex, V, L, k.V, sm.alpha, k.R);
       }
       // 4.7 S = M R, 4.8 Z = A S
       if ((rc = apply_M(k.R, k.S))) return rc;
@@ -439,17 +440,17 @@ struct Solver {
         int np;
         {
           Timed t(ex, KC_GRAM);
-          np = block_gram<T>(ex, V, L, k.Rt, k.Z, k.R, GRAM_G1 | GRAM_D1 | GRAM_D2, gpart);
+          np = block_gram<T>(ex, V, L, k.Rt, k.Z, k.R, GRAM_G1 | GRAM_D1 | GRAM_D2, gpart, sm.status);
         }
         Timed t(ex, KC_SMALL);
         lxl_zeta_beta(ex, L, gpart, np, sm);
       }
-      // 4.10 X += zeta S, 4.11 R -= zeta Z, 4.13 P = R + (P - zeta V) beta
+      // 4.6 + 4.10 X += U alpha + zeta S, 4.11 R -= zeta Z, 4.13 P = R + (P - zeta V) beta
       {
         int np;
         {
           Timed t(ex, KC_AXPY);
-          np = block_update_zeta<T>(ex, V, L, k.S, k.Z, k.V, sm.zb, k.R, k.P, X64, npart);
+          np = block_update_zeta<T>(ex, V, L, k.U, sm.alpha, k.S, k.Z, k.V, sm.zb, k.R, k.P, X64, npart);
         }
         Timed t(ex, KC_SMALL);
         lxl_norms(ex, L, npart, np, false, sm);
@@ -466,6 +467,7 @@ struct Solver {
       }
       if (p.res_history && it - 1 < p.res_history_len) p.res_history[it - 1] = relmax;
       if (trace) fprintf(stderr, "mbicg: iter %d max rel residual %.6e status 0x%x\n", it, relmax, st);
+      if (st & ST_TIMEOUT) return fail(c, MBICG_ECUDA, "a bounded wait for a bulk copy gave up in a kernel");
       if (st & ST_NAN) { status = MBICG_ENAN; break; }
       if (st) {
         // breakdown: restart from the current X (R = B - A X, P = R, R~ = R)

@@ -19,37 +19,73 @@ namespace {
 
 constexpr int NT = 256;  // threads of the row kernels and the gram kernel
 
-__host__ __device__ constexpr int reg_block(int L) { return L % 3 == 0 ? 3 : (L % 2 == 0 ? 2 : 1); }
+// register block of the gram kernel: BB x BB entries per thread
+__host__ __device__ constexpr int reg_block(int L) { return L % 2 == 0 ? 2 : (L % 3 == 0 ? 3 : 1); }
 // sites per shared-memory tile of the gram kernel
 __host__ __device__ constexpr int gram_tile_sites(int L) { return L >= 8 ? 8 : (L >= 4 ? 16 : 32); }
 
 // ---------------------------------------------------------------------------
 // Gram kernel
+//
+// A persistent grid of GRAM_CTAS CTAs walks over tiles of TS sites.  One
+// thread streams each tile of every input block into shared memory with bulk
+// asynchronous copies (TMA) completing on an mbarrier, STAGES tiles ahead, while
+// all threads multiply the tile already in shared memory: thread (lane, block)
+// accumulates a BB x BB block of the L x L product over the tile rows
+// lane, lane + LANES, ...  With HERM (A^H A), only the blocks on or above the
+// diagonal are formed and the rest is mirrored.
 // ---------------------------------------------------------------------------
 // flags: bit0 G1 = A^H B1, bit1 G2 = A^H B2, bit2 diag(B1^H B2), bit3 diag(B1^H B1)
-template <typename R, int L>
-__global__ void __launch_bounds__(NT) k_gram(long long nsite, const cx<R>* __restrict__ A,
+template <typename R, int L, bool HERM>
+struct GramShape {
+  static constexpr int BB = reg_block(L);
+  static constexpr int NBI = L / BB;
+  static constexpr int NB = HERM ? NBI * (NBI + 1) / 2 : NBI * NBI;
+  static constexpr int LANES = NT / NB > 0 ? NT / NB : 1;
+  static constexpr int TS = gram_tile_sites(L);
+  static constexpr int TILE = TS * L * 12;  // complex numbers per tile per array
+  static constexpr int STAGES = sizeof(R) == 4 ? 3 : 2;
+  static constexpr size_t tile_bytes = sizeof(cx<R>) * (size_t)TILE;
+  static constexpr size_t red_g = sizeof(cx<double>) * LANES * L * L;
+  static constexpr size_t red_d = sizeof(cx<double>) * 2 * (NT / L) * L;
+  static constexpr size_t stage_area = tile_bytes * 3 * STAGES;
+  static constexpr size_t red_bytes = red_g > red_d ? red_g : red_d;
+  static constexpr size_t smem = (stage_area > red_bytes ? stage_area : red_bytes) + 64;
+};
+
+template <typename R, int L, bool HERM>
+__global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __restrict__ A,
                                              const cx<R>* __restrict__ B1, const cx<R>* __restrict__ B2,
-                                             int flags, double* __restrict__ part) {
-  constexpr int BB = reg_block(L);
-  constexpr int NBI = L / BB;
-  constexpr int NB = NBI * NBI;
-  constexpr int LANES = NT / NB > 0 ? NT / NB : 1;
-  constexpr int TS = gram_tile_sites(L);
-  constexpr int TILE = TS * L * 12;  // complex numbers per tile per array
+                                             int flags, double* __restrict__ part, int* __restrict__ err) {
+  using SH = GramShape<R, L, HERM>;
+  constexpr int BB = SH::BB, NBI = SH::NBI, NB = SH::NB, LANES = SH::LANES, TS = SH::TS, TILE = SH::TILE;
+  constexpr int STAGES = SH::STAGES;
+  // FP32 per-tile sums are widened into FP64 running sums every FLUSH tiles
   constexpr int FLUSH = sizeof(R) == 4 ? 8 : 1;
-  extern __shared__ unsigned char smem_raw[];
-  cx<R>* sA = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* sB1 = sA + TILE;
-  cx<R>* sB2 = sB1 + TILE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (SH::smem - 64));
+  cx<R>* stage0 = reinterpret_cast<cx<R>*>(smem_raw);
 
   const bool g1 = flags & 1, g2 = flags & 2, d1 = flags & 4, d2 = flags & 8;
   const bool a_is_b1 = (A == B1);
+  const bool loadA = g1 || g2 || a_is_b1;
+  const bool loadB1 = !a_is_b1;
+  const bool loadB2 = B2 != nullptr;
   const int tid = threadIdx.x;
   const int blk = tid % NB;
   const int lane = tid / NB;
   const bool gram_thread = lane < LANES;
-  const int bi = (blk / NBI) * BB, bj = (blk % NBI) * BB;
+  // block coordinates (on and above the diagonal when HERM)
+  int bi, bj;
+  if (HERM) {
+    int r = 0, rem = blk;
+    while (rem >= NBI - r) { rem -= NBI - r; ++r; }
+    bi = r * BB;
+    bj = (r + rem) * BB;
+  } else {
+    bi = (blk / NBI) * BB;
+    bj = (blk % NBI) * BB;
+  }
 
   cx<R> acc1[BB][BB], acc2[BB][BB];
   cx<double> tot1[BB][BB], tot2[BB][BB];
@@ -60,7 +96,6 @@ __global__ void __launch_bounds__(NT) k_gram(long long nsite, const cx<R>* __res
       acc1[i][j] = acc2[i][j] = mk<R>(0, 0);
       tot1[i][j] = tot2[i][j] = mk<double>(0, 0);
     }
-  // diagonal dots: thread -> column tid % L, row lane tid / L
   const int dcol = tid % L, dlane = tid / L;
   constexpr int DLANES = NT / L;
   cx<R> dacc1 = mk<R>(0, 0);
@@ -69,22 +104,43 @@ __global__ void __launch_bounds__(NT) k_gram(long long nsite, const cx<R>* __res
   double dtot2 = 0;
 
   const long long ntiles = (nsite + TS - 1) / TS;
-  int since_flush = 0;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int my_tiles = (int)(ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int j) {  // tile j of this CTA into stage j % STAGES (thread 0)
+    const long long tile = blockIdx.x + (long long)j * gridDim.x;
     const long long site0 = tile * TS;
     const int ns = (int)min((long long)TS, nsite - site0);
-    const int n = ns * L * 12;
-    const cx<R>* gA = A + site0 * L * 12;
-    const cx<R>* gB1 = B1 + site0 * L * 12;
-    const cx<R>* gB2 = B2 ? B2 + site0 * L * 12 : nullptr;
-    __syncthreads();
-    for (int e = tid; e < n; e += NT) {
-      if (g1 || g2 || a_is_b1) sA[e] = gA[e];
-      if (!a_is_b1) sB1[e] = gB1[e];
-      if (gB2) sB2[e] = gB2[e];
+    const uint32_t bytes = (uint32_t)(sizeof(cx<R>) * (size_t)ns * L * 12);
+    const int st = j % STAGES;
+    cx<R>* dst = stage0 + (size_t)st * 3 * TILE;
+    const uint32_t total = bytes * ((loadA ? 1 : 0) + (loadB1 ? 1 : 0) + (loadB2 ? 1 : 0));
+    mbar_arrive_expect_tx(&bars[st], total);
+    const size_t off = (size_t)site0 * L * 12;
+    if (loadA) bulk_g2s(dst, A + off, bytes, &bars[st]);
+    if (loadB1) bulk_g2s(dst + TILE, B1 + off, bytes, &bars[st]);
+    if (loadB2) bulk_g2s(dst + 2 * TILE, B2 + off, bytes, &bars[st]);
+  };
+  if (tid == 0)
+    for (int j = 0; j < STAGES && j < my_tiles; ++j) issue(j);
+
+  bool ok = true;
+  int since_flush = 0;
+  int j = 0;
+  for (; j < my_tiles; ++j) {
+    const int st = j % STAGES;
+    if (!mbar_wait_bounded(&bars[st], (uint32_t)((j / STAGES) & 1))) {
+      ok = false;
+      break;
     }
-    __syncthreads();
-    const cx<R>* tB1 = a_is_b1 ? sA : sB1;
+    const long long site0 = (blockIdx.x + (long long)j * gridDim.x) * TS;
+    const int ns = (int)min((long long)TS, nsite - site0);
+    const cx<R>* sA = stage0 + (size_t)st * 3 * TILE;
+    const cx<R>* tB1 = a_is_b1 ? sA : sA + TILE;
+    const cx<R>* sB2 = sA + 2 * TILE;
     const int nrows = ns * 12;
     if ((g1 || g2) && gram_thread) {
       for (int row = lane; row < nrows; row += LANES) {
@@ -96,19 +152,19 @@ __global__ void __launch_bounds__(NT) k_gram(long long nsite, const cx<R>* __res
         if (g1) {
           const cx<R>* rb = tB1 + site * L * 12 + sc;
 #pragma unroll
-          for (int j = 0; j < BB; ++j) {
-            const cx<R> b = rb[(bj + j) * 12];
+          for (int jj = 0; jj < BB; ++jj) {
+            const cx<R> bv = rb[(bj + jj) * 12];
 #pragma unroll
-            for (int i = 0; i < BB; ++i) cmac_conj(acc1[i][j], a[i], b);
+            for (int i = 0; i < BB; ++i) cmac_conj(acc1[i][jj], a[i], bv);
           }
         }
         if (g2) {
           const cx<R>* rb = sB2 + site * L * 12 + sc;
 #pragma unroll
-          for (int j = 0; j < BB; ++j) {
-            const cx<R> b = rb[(bj + j) * 12];
+          for (int jj = 0; jj < BB; ++jj) {
+            const cx<R> bv = rb[(bj + jj) * 12];
 #pragma unroll
-            for (int i = 0; i < BB; ++i) cmac_conj(acc2[i][j], a[i], b);
+            for (int i = 0; i < BB; ++i) cmac_conj(acc2[i][jj], a[i], bv);
           }
         }
       }
@@ -126,28 +182,41 @@ __global__ void __launch_bounds__(NT) k_gram(long long nsite, const cx<R>* __res
 #pragma unroll
       for (int i = 0; i < BB; ++i)
 #pragma unroll
-        for (int j = 0; j < BB; ++j) {
-          tot1[i][j].re += acc1[i][j].re; tot1[i][j].im += acc1[i][j].im;
-          tot2[i][j].re += acc2[i][j].re; tot2[i][j].im += acc2[i][j].im;
-          acc1[i][j] = acc2[i][j] = mk<R>(0, 0);
+        for (int jj = 0; jj < BB; ++jj) {
+          tot1[i][jj].re += acc1[i][jj].re; tot1[i][jj].im += acc1[i][jj].im;
+          tot2[i][jj].re += acc2[i][jj].re; tot2[i][jj].im += acc2[i][jj].im;
+          acc1[i][jj] = acc2[i][jj] = mk<R>(0, 0);
         }
       dtot1.re += dacc1.re; dtot1.im += dacc1.im; dtot2 += dacc2;
       dacc1 = mk<R>(0, 0);
       dacc2 = 0;
     }
+    __syncthreads();  // every thread is done with this stage
+    if (tid == 0 && j + STAGES < my_tiles) issue(j + STAGES);
+  }
+  if (!ok) {
+    // a copy never completed: record it, and wait (bounded) for the copies
+    // still in flight before the shared memory is released
+    if (tid == 0) {
+      atomicOr(err, ST_TIMEOUT);
+      for (int jj = j; jj < my_tiles && jj < j + STAGES; ++jj)
+        mbar_wait_bounded(&bars[jj % STAGES], (uint32_t)((jj / STAGES) & 1));
+    }
+    __syncthreads();
+    return;
   }
 #pragma unroll
   for (int i = 0; i < BB; ++i)
 #pragma unroll
-    for (int j = 0; j < BB; ++j) {
-      tot1[i][j].re += acc1[i][j].re; tot1[i][j].im += acc1[i][j].im;
-      tot2[i][j].re += acc2[i][j].re; tot2[i][j].im += acc2[i][j].im;
+    for (int jj = 0; jj < BB; ++jj) {
+      tot1[i][jj].re += acc1[i][jj].re; tot1[i][jj].im += acc1[i][jj].im;
+      tot2[i][jj].re += acc2[i][jj].re; tot2[i][jj].im += acc2[i][jj].im;
     }
   dtot1.re += dacc1.re; dtot1.im += dacc1.im; dtot2 += dacc2;
 
   // reduce over lanes through shared memory, fixed order
   __syncthreads();
-  cx<double>* red = reinterpret_cast<cx<double>*>(smem_raw);  // [LANES][L*L] (+ diag [DLANES][L])
+  cx<double>* red = reinterpret_cast<cx<double>*>(smem_raw);
   const int nslots = 2 * L * L + 2 * L;
   double* out = part + (long long)blockIdx.x * nslots * 2;
   for (int pass = 0; pass < 2; ++pass) {
@@ -163,18 +232,24 @@ __global__ void __launch_bounds__(NT) k_gram(long long nsite, const cx<R>* __res
 #pragma unroll
       for (int i = 0; i < BB; ++i)
 #pragma unroll
-        for (int j = 0; j < BB; ++j)
-          red[lane * L * L + (bi + i) * L + (bj + j)] = pass == 0 ? tot1[i][j] : tot2[i][j];
+        for (int jj = 0; jj < BB; ++jj)
+          red[lane * L * L + (bi + i) * L + (bj + jj)] = pass == 0 ? tot1[i][jj] : tot2[i][jj];
     }
     __syncthreads();
     for (int e = tid; e < L * L; e += NT) {
+      int ei = e / L, ej = e % L;
+      bool mirror = false;
+      if (HERM && (ei / BB) > (ej / BB)) {  // below the block diagonal: mirror
+        const int t = ei; ei = ej; ej = t;
+        mirror = true;
+      }
       double re = 0, im = 0;
       for (int l = 0; l < LANES; ++l) {
-        re += red[l * L * L + e].re;
-        im += red[l * L * L + e].im;
+        re += red[l * L * L + ei * L + ej].re;
+        im += red[l * L * L + ei * L + ej].im;
       }
       out[(pass * L * L + e) * 2] = re;
-      out[(pass * L * L + e) * 2 + 1] = im;
+      out[(pass * L * L + e) * 2 + 1] = mirror ? -im : im;
     }
     __syncthreads();
   }
@@ -196,30 +271,29 @@ __global__ void __launch_bounds__(NT) k_gram(long long nsite, const cx<R>* __res
   }
 }
 
-template <typename R, int L>
-int launch_gram(const Exec& ex, long long nsite, const cx<R>* A, const cx<R>* B1, const cx<R>* B2, int flags,
-                double* part) {
-  if (!A) A = B1;
-  constexpr int TS = gram_tile_sites(L);
-  constexpr int TILE = TS * L * 12;
-  constexpr int BB = reg_block(L);
-  constexpr int NB = (L / BB) * (L / BB);
-  constexpr int LANES = NT / NB > 0 ? NT / NB : 1;
-  constexpr size_t tile_bytes = sizeof(cx<R>) * TILE * 3;
-  constexpr size_t red_g = sizeof(cx<double>) * LANES * L * L;
-  constexpr size_t red_d = sizeof(cx<double>) * 2 * (NT / L) * L;
-  constexpr size_t red_bytes = red_g > red_d ? red_g : red_d;
-  constexpr size_t shm = tile_bytes > red_bytes ? tile_bytes : red_bytes;
+template <typename R, int L, bool HERM>
+int launch_gram_t(const Exec& ex, long long nsite, const cx<R>* A, const cx<R>* B1, const cx<R>* B2, int flags,
+                  double* part, int* err) {
+  using SH = GramShape<R, L, HERM>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_gram<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaFuncSetAttribute(k_gram<R, L, HERM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::smem);
     attr_set = true;
   }
-  const long long ntiles = (nsite + TS - 1) / TS;
+  const long long ntiles = (nsite + SH::TS - 1) / SH::TS;
   const int grid = (int)(ntiles < GRAM_CTAS ? ntiles : GRAM_CTAS);
-  k_gram<R, L><<<grid, NT, shm, ex.stream>>>(nsite, A, B1, B2, flags, part);
+  k_gram<R, L, HERM><<<grid, NT, SH::smem, ex.stream>>>(nsite, A, B1, B2, flags, part, err);
   ++*ex.launches;
   return grid;
+}
+
+template <typename R, int L>
+int launch_gram(const Exec& ex, long long nsite, const cx<R>* A, const cx<R>* B1, const cx<R>* B2, int flags,
+                double* part, int* err) {
+  if (!A) A = B1;
+  // A^H A alone: Hermitian, only the upper block triangle is formed
+  if (A == B1 && flags == GRAM_G1) return launch_gram_t<R, L, true>(ex, nsite, A, B1, B2, flags, part, err);
+  return launch_gram_t<R, L, false>(ex, nsite, A, B1, B2, flags, part, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -257,49 +331,46 @@ __global__ void __launch_bounds__(NT) k_transform(int nrow, const cx<R>* X, cons
   }
 }
 
+// R -= V alpha (4.5); X += U alpha is deferred to k_update_zeta
 template <typename R, int L>
 __global__ void __launch_bounds__(NT) k_update_alpha(int nrow, const cx<R>* __restrict__ V,
-                                                     const cx<R>* __restrict__ U, const double* __restrict__ alpha,
-                                                     cx<R>* __restrict__ Rv, cx<double>* __restrict__ X64) {
+                                                     const double* __restrict__ alpha, cx<R>* __restrict__ Rv) {
   __shared__ cx<R> sA[L * L];
   for (int e = threadIdx.x; e < L * L; e += NT) sA[e] = mk((R)alpha[2 * e], (R)alpha[2 * e + 1]);
   __syncthreads();
   for (int row = blockIdx.x * NT + threadIdx.x; row < nrow; row += gridDim.x * NT) {
     const size_t b = row_base(row, L);
-    cx<R> v[L], u[L];
+    cx<R> v[L];
 #pragma unroll
-    for (int k = 0; k < L; ++k) {
-      v[k] = V[b + k * 12];
-      u[k] = U[b + k * 12];
-    }
+    for (int k = 0; k < L; ++k) v[k] = V[b + k * 12];
 #pragma unroll(col_unroll<R, L>())
     for (int j = 0; j < L; ++j) {
-      cx<R> va = mk<R>(0, 0), ua = mk<R>(0, 0);
+      cx<R> va = mk<R>(0, 0);
 #pragma unroll
-      for (int k = 0; k < L; ++k) {
-        cmac(va, v[k], sA[k * L + j]);
-        cmac(ua, u[k], sA[k * L + j]);
-      }
-      cx<R> r = Rv[b + j * 12];
-      Rv[b + j * 12] = r - va;
-      cx<double> x = X64[b + j * 12];
-      x.re += (double)ua.re;
-      x.im += (double)ua.im;
-      X64[b + j * 12] = x;
+      for (int k = 0; k < L; ++k) cmac(va, v[k], sA[k * L + j]);
+      Rv[b + j * 12] = Rv[b + j * 12] - va;
     }
   }
 }
 
+// X += U alpha + zeta S (the X update of Algorithm 1, 4.9, which Algorithm 2
+// splits into 4.6 and 4.10), R -= zeta Z (4.11), P = R + (P - zeta V) beta
+// (4.13), and the squared column norms of the new R.
 // zb = [zeta, beta (L x L)] complex double
 template <typename R, int L>
-__global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __restrict__ S,
+__global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __restrict__ U,
+                                                    const double* __restrict__ alpha, const cx<R>* __restrict__ S,
                                                     const cx<R>* __restrict__ Z, const cx<R>* __restrict__ V,
                                                     const double* __restrict__ zb, cx<R>* __restrict__ Rv,
                                                     cx<R>* __restrict__ P, cx<double>* __restrict__ X64,
                                                     double* __restrict__ part) {
   __shared__ cx<R> sB[L * L];
+  __shared__ cx<R> sA[L * L];
   __shared__ double sred[NT];
-  for (int e = threadIdx.x; e < L * L; e += NT) sB[e] = mk((R)zb[2 + 2 * e], (R)zb[3 + 2 * e]);
+  for (int e = threadIdx.x; e < L * L; e += NT) {
+    sB[e] = mk((R)zb[2 + 2 * e], (R)zb[3 + 2 * e]);
+    sA[e] = mk((R)alpha[2 * e], (R)alpha[2 * e + 1]);
+  }
   const cx<double> zeta64 = mk(zb[0], zb[1]);
   const cx<R> zeta = mk((R)zb[0], (R)zb[1]);
   __syncthreads();
@@ -307,24 +378,31 @@ __global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __res
 #pragma unroll
   for (int j = 0; j < L; ++j) nrm[j] = 0;
   for (int row = blockIdx.x * NT + threadIdx.x; row < nrow; row += gridDim.x * NT) {
-    const long long b = row_base(row, L);
-    cx<R> rn[L], t[L];
+    const size_t b = row_base(row, L);
+    cx<R> t[L];
+    {
+      cx<R> u[L];
+#pragma unroll
+      for (int k = 0; k < L; ++k) u[k] = U[b + k * 12];
+#pragma unroll(col_unroll<R, L>())
+      for (int j = 0; j < L; ++j) {
+        cx<R> ua = mk<R>(0, 0);
+#pragma unroll
+        for (int k = 0; k < L; ++k) cmac(ua, u[k], sA[k * L + j]);
+        const cx<R> s = S[b + j * 12];
+        cx<double> x = X64[b + j * 12];
+        x.re += (double)ua.re + (zeta64.re * (double)s.re - zeta64.im * (double)s.im);
+        x.im += (double)ua.im + (zeta64.re * (double)s.im + zeta64.im * (double)s.re);
+        X64[b + j * 12] = x;
+      }
+    }
 #pragma unroll
     for (int k = 0; k < L; ++k) {
-      // X += zeta S (4.10), R -= zeta Z (4.11)
-      const cx<R> s = S[b + k * 12];
-      cx<double> x = X64[b + k * 12];
-      const cx<double> s64 = mk((double)s.re, (double)s.im);
-      x.re += zeta64.re * s64.re - zeta64.im * s64.im;
-      x.im += zeta64.re * s64.im + zeta64.im * s64.re;
-      X64[b + k * 12] = x;
-      const cx<R> z = Z[b + k * 12];
-      rn[k] = Rv[b + k * 12] - zeta * z;
-      Rv[b + k * 12] = rn[k];
-      nrm[k] = fma(rn[k].re, rn[k].re, fma(rn[k].im, rn[k].im, nrm[k]));
+      const cx<R> rn = Rv[b + k * 12] - zeta * Z[b + k * 12];
+      Rv[b + k * 12] = rn;
+      nrm[k] = fma(rn.re, rn.re, fma(rn.im, rn.im, nrm[k]));
       t[k] = P[b + k * 12] - zeta * V[b + k * 12];
     }
-    // P = R + (P - zeta V) beta (4.13)
 #pragma unroll(col_unroll<R, L>())
     for (int j = 0; j < L; ++j) {
       cx<R> y = Rv[b + j * 12];  // the new R, just written
@@ -408,7 +486,8 @@ __global__ void __launch_bounds__(NT) k_residual_from(long long nsite, int L, co
     for (long long idx = (long long)blockIdx.x * per + tid; idx < nsite * L; idx += stride) {
 #pragma unroll
       for (int sc = 0; sc < 12; ++sc) {
-        const cx<double> b = B[idx * 12 + sc], w = W[idx * 12 + sc];
+        const cx<double> b = B[idx * 12 + sc];
+        const cx<double> w = W ? W[idx * 12 + sc] : mk(0.0, 0.0);
         const cx<double> r = mk(b.re - w.re, b.im - w.im);
         out[idx * 12 + sc] = mk((R)r.re, (R)r.im);
         acc += r.re * r.re + r.im * r.im;
@@ -690,9 +769,9 @@ int gram_slots(int L) { return 2 * L * L + 2 * L; }
 
 template <typename R>
 int block_gram(const Exec& ex, long long nsite, int L, const cx<R>* A, const cx<R>* B1, const cx<R>* B2,
-               int flags, double* part) {
+               int flags, double* part, int* err) {
   int grid = -1;
-  DISPATCH_L(L, grid = (launch_gram<R, LL>(ex, nsite, A, B1, B2, flags, part)));
+  DISPATCH_L(L, grid = (launch_gram<R, LL>(ex, nsite, A, B1, B2, flags, part, err)));
   return grid;
 }
 
@@ -704,19 +783,20 @@ void block_transform(const Exec& ex, long long nsite, int L, const cx<R>* X, con
 }
 
 template <typename R>
-void block_update_alpha(const Exec& ex, long long nsite, int L, const cx<R>* V, const cx<R>* U, const double* alpha,
-                        cx<R>* Rv, cx<double>* X64) {
+void block_update_alpha(const Exec& ex, long long nsite, int L, const cx<R>* V, const double* alpha, cx<R>* Rv) {
   const int nrow = (int)(nsite * 12);
-  DISPATCH_L(L, (k_update_alpha<R, LL><<<row_grid(nrow), NT, 0, ex.stream>>>(nrow, V, U, alpha, Rv, X64)));
+  DISPATCH_L(L, (k_update_alpha<R, LL><<<row_grid(nrow), NT, 0, ex.stream>>>(nrow, V, alpha, Rv)));
   ++*ex.launches;
 }
 
 template <typename R>
-int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* S, const cx<R>* Z, const cx<R>* V,
-                      const double* zeta_beta, cx<R>* Rv, cx<R>* P, cx<double>* X64, double* part) {
+int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* U, const double* alpha, const cx<R>* S,
+                      const cx<R>* Z, const cx<R>* V, const double* zeta_beta, cx<R>* Rv, cx<R>* P, cx<double>* X64,
+                      double* part) {
   const int nrow = (int)(nsite * 12);
   const int grid = row_grid(nrow);
-  DISPATCH_L(L, (k_update_zeta<R, LL><<<grid, NT, 0, ex.stream>>>(nrow, S, Z, V, zeta_beta, Rv, P, X64, part)));
+  DISPATCH_L(L, (k_update_zeta<R, LL><<<grid, NT, 0, ex.stream>>>(nrow, U, alpha, S, Z, V, zeta_beta, Rv, P, X64,
+                                                                  part)));
   ++*ex.launches;
   return grid;
 }
@@ -777,12 +857,12 @@ void lxl_norms(const Exec& ex, int L, const double* part, int nparts, bool from_
 
 #define INST(R)                                                                                                   \
   template int block_gram<R>(const Exec&, long long, int, const cx<R>*, const cx<R>*, const cx<R>*, int,        \
-                             double*);                                                                            \
+                             double*, int*);                                                                      \
   template void block_transform<R>(const Exec&, long long, int, const cx<R>*, const double*, cx<R>*);              \
-  template void block_update_alpha<R>(const Exec&, long long, int, const cx<R>*, const cx<R>*, const double*,       \
-                                      cx<R>*, cx<double>*);                                                       \
-  template int block_update_zeta<R>(const Exec&, long long, int, const cx<R>*, const cx<R>*, const cx<R>*,         \
-                                    const double*, cx<R>*, cx<R>*, cx<double>*, double*);                          \
+  template void block_update_alpha<R>(const Exec&, long long, int, const cx<R>*, const double*, cx<R>*);         \
+  template int block_update_zeta<R>(const Exec&, long long, int, const cx<R>*, const double*, const cx<R>*,        \
+                                    const cx<R>*, const cx<R>*, const double*, cx<R>*, cx<R>*, cx<double>*,       \
+                                    double*);                                                                    \
   template void abi_to_internal<R>(const Exec&, long long, int, const cx<double>*, cx<R>*);                        \
   template void internal_to_abi<R>(const Exec&, long long, int, const cx<R>*, cx<double>*);                        \
   template int residual_from<R>(const Exec&, long long, int, const cx<double>*, const cx<double>*, cx<R>*, double*);

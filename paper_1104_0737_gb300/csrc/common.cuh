@@ -110,6 +110,50 @@ __device__ __forceinline__ void zero(Spinor<R>& s) {
 }
 
 // ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, cp.async.bulk) completing on an mbarrier.
+// Every wait is bounded: after MBAR_SPIN_LIMIT polls the caller gives up and
+// reports an error instead of hanging.
+// ---------------------------------------------------------------------------
+constexpr int MBAR_SPIN_LIMIT = 1 << 24;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// true when the phase completed, false when the wait gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+  for (int i = 0; i < MBAR_SPIN_LIMIT; ++i)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+// global -> shared bulk copy of `bytes` (multiple of 16, 16-byte aligned ends)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // 3x3 link matrices
 // ---------------------------------------------------------------------------
 template <typename R>

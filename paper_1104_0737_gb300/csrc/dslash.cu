@@ -22,10 +22,12 @@ namespace mbicg {
 
 namespace {
 
-// CTA size cap: 512 threads (<= 128 registers) for FP32, 256 for FP64, whose
-// spinors and links take twice the registers.
+// CTA size cap: 384 threads for FP32 with two CTAs per SM (<= 80 registers,
+// 24 warps), 256 for FP64, whose spinors and links take twice the registers.
 template <typename R>
-constexpr int max_cta() { return sizeof(R) == 4 ? 512 : 256; }
+constexpr int max_cta() { return sizeof(R) == 4 ? 384 : 256; }
+template <typename R>
+constexpr int min_ctas() { return sizeof(R) == 4 ? 2 : 1; }
 
 template <int MU, int SIGN, typename R>
 __device__ __forceinline__ void hop(Spinor<R>& acc, const cx<R>* psi_nb, const cx<R>* link, bool flip) {
@@ -79,7 +81,7 @@ __device__ __forceinline__ void hopping(const Geom& g, const cx<R>* __restrict__
 }
 
 template <typename R>
-__global__ void __launch_bounds__(max_cta<R>()) k_dslash_full(Geom g, const cx<R>* __restrict__ links,
+__global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_dslash_full(Geom g, const cx<R>* __restrict__ links,
                                                      const cx<R>* __restrict__ in,
                                                      cx<R>* __restrict__ out, int L, R kappa) {
   const int rhs = threadIdx.x;
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(max_cta<R>()) k_dslash_full(Geom g, const cx<R
 }
 
 template <typename R>
-__global__ void __launch_bounds__(max_cta<R>()) k_sap_residual(Geom g, int colour,
+__global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Geom g, int colour,
                                                       const cx<R>* __restrict__ links,
                                                       const cx<R>* __restrict__ eta,
                                                       const cx<R>* __restrict__ psi,
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(max_cta<R>()) k_sap_residual(Geom g, int colou
 }
 
 template <typename R>
-__global__ void __launch_bounds__(max_cta<R>()) k_sap_domain_apply(Geom g, int colour,
+__global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_domain_apply(Geom g, int colour,
                                                           const cx<R>* __restrict__ links,
                                                           const cx<R>* __restrict__ r,
                                                           cx<R>* __restrict__ q,
@@ -187,14 +189,18 @@ __global__ void __launch_bounds__(max_cta<R>()) k_sap_domain_apply(Geom g, int c
 // ---------------------------------------------------------------------------
 // Fused SAP colour sweep with the MR iterations on chip (FP32).
 //
-// One thread-block cluster per (domain of the colour, rhs); each CTA holds
-// TPC time slices of the domain (BX*BY*BZ*TPC sites, one thread per site) and
-// keeps in shared memory the MR residual r of its sites and their forward
-// links, both structure-of-arrays so that consecutive threads read
-// consecutive words.  Hops in t that leave the CTA's slices read r (and, for
-// the backward hop, the link) from the neighbouring CTA's shared memory
-// (distributed shared memory).  x and q stay in registers.  The sweep:
-//   r = eta - A psi on the domain (psi from global, including the halo),
+// One thread-block cluster per (domain of the colour, chunk of columns); each
+// CTA holds TPC time slices of the domain (BX*BY*BZ*TPC sites, one thread per
+// site) and runs the whole sweep for the columns of its chunk in turn.  The MR
+// residual of its sites lives in shared memory, double buffered so that one
+// cluster barrier per MR step separates the neighbour reads of one step from
+// the writes of the next; x and q stay in registers.  Spinors are stored as
+// 6 float4 planes so consecutive threads read consecutive 16-byte words.  Hops
+// in t that leave the CTA's slices read the residual from the neighbouring
+// CTA's shared memory (distributed shared memory).  Links are read through L1
+// (the domain's links are re-used by every column and MR step).
+// For every column:
+//   r = eta - A psi on the domain (psi staged in shared memory, halo from global),
 //   nmr times: q = A_dom r; omega (per column from the cluster-wide dots, or
 //   from the frozen table); x += omega r; r -= omega q,
 //   psi += x.
@@ -204,19 +210,36 @@ struct SweepShape {
   static constexpr int NS = BX * BY * BZ * TPC;  // sites per CTA = threads
   static constexpr int CS = BT / TPC;             // CTAs per cluster
   static constexpr int SLAB = BX * BY * BZ;
-  static constexpr size_t smem_bytes() { return sizeof(float) * (size_t)NS * (24 + 72) + 64 * sizeof(float); }
+  // two spinor buffers of 6 float4 planes + partial dots
+  static constexpr size_t smem_bytes() { return (size_t)NS * 2 * 6 * 16 + 64 * sizeof(float); }
 };
 
+__device__ __forceinline__ void spinor_to_planes(float4* vS, int NS, int site, const Spinor<float>& v) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const cx<float> a = (&v.c[0][0])[2 * k], b = (&v.c[0][0])[2 * k + 1];
+    vS[k * NS + site] = make_float4(a.re, a.im, b.re, b.im);
+  }
+}
+__device__ __forceinline__ void planes_to_spinor(const float4* vS, int NS, int site, Spinor<float>& v) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float4 t = vS[k * NS + site];
+    (&v.c[0][0])[2 * k] = mk(t.x, t.y);
+    (&v.c[0][0])[2 * k + 1] = mk(t.z, t.w);
+  }
+}
+
 // Hop sum over the eight neighbours of a site of the domain, reading the
-// neighbour's spinor from the (distributed) shared-memory array vS [24][NS]
-// when it lies in the domain.  Hops that leave the domain are dropped
-// (HALO = false: the Dirichlet domain operator A_dom) or taken from global
-// memory (HALO = true: the full operator, psi_g and the global links, with
-// the antiperiodic phase of the t boundary).
+// neighbour's spinor from the (distributed) shared-memory planes vS when it
+// lies in the domain.  Hops that leave the domain are dropped (HALO = false:
+// the Dirichlet domain operator A_dom) or taken from global memory (HALO =
+// true: the full operator, psi_g, with the antiperiodic phase of the t
+// boundary).
 template <int BX, int BY, int BZ, int BT, int TPC, bool HALO>
 __device__ __forceinline__ void domain_hops(cooperative_groups::cluster_group& cluster, const Geom& g,
-                                            const float* vS, const float* uS, int tid, int rank, int ltl,
-                                            const int lc[4], const int c[4], int s, int L, int rhs,
+                                            const float4* vS, int tid, int rank, int ltl, const int lc[4],
+                                            const int c[4], int s, int L, int rhs,
                                             const cx<float>* __restrict__ links,
                                             const cx<float>* __restrict__ psi_g, Spinor<float>& acc) {
   constexpr int NS = BX * BY * BZ * TPC;
@@ -230,11 +253,17 @@ __device__ __forceinline__ void domain_hops(cooperative_groups::cluster_group& c
       const bool leaves = fwd ? (lc[mu] == ext - 1) : (lc[mu] == 0);
       if (leaves && !HALO) continue;
       Spinor<float> pn;
-      Link<float> u;
       float phase = 1.0f;
+      int sn;  // global index of the neighbour (for its backward link)
+      {
+        const int dm = g.d[mu];
+        const int stride = mu == 0 ? 1 : mu == 1 ? g.d[0] : mu == 2 ? g.d[0] * g.d[1] : g.d[0] * g.d[1] * g.d[2];
+        const bool wrap = fwd ? (c[mu] == dm - 1) : (c[mu] == 0);
+        sn = fwd ? (wrap ? s - (dm - 1) * stride : s + stride) : (wrap ? s + (dm - 1) * stride : s - stride);
+        if (mu == 3 && wrap) phase = -1.0f;
+      }
       if (!leaves) {
-        const float* rsrc = vS;
-        const float* usrc = uS;
+        const float4* rsrc = vS;
         int nb;
         if (mu < 3) {
           const int st = mu == 0 ? 1 : mu == 1 ? BX : BX * BY;
@@ -244,33 +273,16 @@ __device__ __forceinline__ void domain_hops(cooperative_groups::cluster_group& c
           if (nl >= 0 && nl < TPC) {
             nb = tid + (fwd ? SLAB : -SLAB);
           } else {
-            const int other = rank + (fwd ? 1 : -1);
             nb = tid + (fwd ? -(TPC - 1) * SLAB : (TPC - 1) * SLAB);
-            rsrc = cluster.map_shared_rank(vS, other);
-            usrc = cluster.map_shared_rank(uS, other);
+            rsrc = cluster.map_shared_rank(vS, rank + (fwd ? 1 : -1));
           }
         }
-#pragma unroll
-        for (int j = 0; j < 12; ++j) (&pn.c[0][0])[j] = mk(rsrc[(2 * j) * NS + nb], rsrc[(2 * j + 1) * NS + nb]);
-        const float* ub = fwd ? uS + mu * 18 * NS + tid : usrc + mu * 18 * NS + nb;
-#pragma unroll
-        for (int e = 0; e < 9; ++e) (&u.m[0][0])[e] = mk(ub[(2 * e) * NS], ub[(2 * e + 1) * NS]);
+        planes_to_spinor(rsrc, NS, nb, pn);
       } else {
-        // the neighbour is in another domain: global memory
-        const int dm = g.d[mu];
-        const int stride = mu == 0 ? 1 : mu == 1 ? g.d[0] : mu == 2 ? g.d[0] * g.d[1] : g.d[0] * g.d[1] * g.d[2];
-        const bool wrap = fwd ? (c[mu] == dm - 1) : (c[mu] == 0);
-        const int sn = fwd ? (wrap ? s - (dm - 1) * stride : s + stride) : (wrap ? s + (dm - 1) * stride : s - stride);
-        if (mu == 3 && wrap) phase = -1.0f;
         load_spinor(psi_g + spinor_offset(sn, L, rhs), pn);
-        if (fwd) {
-          const float* ub = uS + mu * 18 * NS + tid;
-#pragma unroll
-          for (int e = 0; e < 9; ++e) (&u.m[0][0])[e] = mk(ub[(2 * e) * NS], ub[(2 * e + 1) * NS]);
-        } else {
-          load_link(links + (size_t)(sn * 4 + mu) * 9, u);
-        }
       }
+      Link<float> u;
+      load_link(links + (size_t)((fwd ? s : sn) * 4 + mu) * 9, u);
       cx<float> h[2][3], w[2][3];
       if (fwd) {
         switch (mu) {
@@ -291,22 +303,10 @@ __device__ __forceinline__ void domain_hops(cooperative_groups::cluster_group& c
   }
 }
 
-__device__ __forceinline__ void spinor_to_soa(float* vS, int NS, int tid, const Spinor<float>& v) {
-#pragma unroll
-  for (int j = 0; j < 12; ++j) {
-    vS[(2 * j) * NS + tid] = (&v.c[0][0])[j].re;
-    vS[(2 * j + 1) * NS + tid] = (&v.c[0][0])[j].im;
-  }
-}
-__device__ __forceinline__ void soa_to_spinor(const float* vS, int NS, int tid, Spinor<float>& v) {
-#pragma unroll
-  for (int j = 0; j < 12; ++j) (&v.c[0][0])[j] = mk(vS[(2 * j) * NS + tid], vS[(2 * j + 1) * NS + tid]);
-}
-
 template <int BX, int BY, int BZ, int BT, int TPC>
 __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256) ? 2 : 1)
     k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const cx<float>* __restrict__ eta,
-                cx<float>* __restrict__ psi, int L, float kappa, int psi_zero, int nmr, int mode,
+                cx<float>* __restrict__ psi, int L, int rchunk, float kappa, int psi_zero, int nmr, int mode,
                 const double* __restrict__ table) {
   using SH = SweepShape<BX, BY, BZ, BT, TPC>;
   constexpr int NS = SH::NS;
@@ -314,16 +314,18 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
   constexpr int SLAB = SH::SLAB;
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ float sm[];
-  float* rS = sm;              // [24][NS]: psi, then the MR residual r
-  float* uS = sm + 24 * NS;    // [4][18][NS] forward links
-  float* red = uS + 72 * NS;   // [CS][4] partial dots
+  extern __shared__ float4 sm4[];
+  float4* buf0 = sm4;                                      // [6][NS]
+  float4* buf1 = sm4 + 6 * NS;                             // [6][NS]
+  float* red = reinterpret_cast<float*>(sm4 + 12 * NS);   // [CS][4] partial dots
   __shared__ float wsum[NS / 32][3];
 
   const int rank = (int)cluster.block_rank();
+  const int nchunks = (L + rchunk - 1) / rchunk;
   const int cid = blockIdx.x / CS;
-  const int k = cid / L;
-  const int rhs = cid - k * L;
+  const int k = cid / nchunks;  // domain of this colour
+  const int rhs0 = (cid - k * nchunks) * rchunk;
+  const int rhs1 = min(L, rhs0 + rchunk);
   const int tid = threadIdx.x;
   int lc[4];
   lc[0] = tid % BX;
@@ -339,120 +341,120 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
   c[2] = b[2] * BZ + lc[2];
   c[3] = b[3] * BT + lc[3];
   const int s = site_index(g, c);
-  const size_t off = spinor_offset(s, L, rhs);
-
-  // forward links of this site into shared memory
-  {
-    const float2* gl = reinterpret_cast<const float2*>(links + (size_t)s * 36);
-#pragma unroll
-    for (int e = 0; e < 36; ++e) {
-      const float2 v = __ldg(gl + e);
-      uS[(2 * e) * NS + tid] = v.x;
-      uS[(2 * e + 1) * NS + tid] = v.y;
-    }
-  }
-  // r = eta - A psi on the domain: psi staged in shared memory, the halo
-  // (neighbours in other domains) from global memory
-  Spinor<float> r0;
-  load_spinor(eta + off, r0);
-  if (!psi_zero) {
-    Spinor<float> pv, acc;
-    load_spinor(psi + off, pv);
-    spinor_to_soa(rS, NS, tid, pv);
-    cluster.sync();
-    domain_hops<BX, BY, BZ, BT, TPC, true>(cluster, g, rS, uS, tid, rank, ltl, lc, c, s, L, rhs, links, psi, acc);
-#pragma unroll
-    for (int j = 0; j < 12; ++j) {
-      cx<float>& e = (&r0.c[0][0])[j];
-      const cx<float> pj = (&pv.c[0][0])[j], aj = (&acc.c[0][0])[j];
-      e = mk(fmaf(kappa, aj.re, e.re - pj.re), fmaf(kappa, aj.im, e.im - pj.im));
-    }
-  }
-  cluster.sync();  // psi reads done (and the links of every CTA are in place)
-  spinor_to_soa(rS, NS, tid, r0);
-  Spinor<float> x;
-  zero(x);
-  cluster.sync();
-
   const int ndc = g.nd / 2;
-  for (int it = 0; it < nmr; ++it) {
-    const bool last = (it == nmr - 1);
-    Spinor<float> q, rv;
-    const bool need_q = (mode == 0) || !last;
-    if (need_q) domain_hops<BX, BY, BZ, BT, TPC, false>(cluster, g, rS, uS, tid, rank, ltl, lc, c, s, L, rhs, links,
-                                                       psi, q);
-    soa_to_spinor(rS, NS, tid, rv);
-    if (need_q) {
-#pragma unroll
-      for (int j = 0; j < 12; ++j) {
-        cx<float>& o = (&q.c[0][0])[j];
-        const cx<float> v = (&rv.c[0][0])[j];
-        o = mk(fmaf(-kappa, o.re, v.re), fmaf(-kappa, o.im, v.im));
-      }
-    }
-    cx<float> om;
-    if (mode == 0) {
-      float nre = 0, nim = 0, den = 0;
-#pragma unroll
-      for (int j = 0; j < 12; ++j) {
-        const cx<float> o = (&q.c[0][0])[j], v = (&rv.c[0][0])[j];
-        nre = fmaf(o.re, v.re, fmaf(o.im, v.im, nre));
-        nim = fmaf(o.re, v.im, fmaf(-o.im, v.re, nim));
-        den = fmaf(o.re, o.re, fmaf(o.im, o.im, den));
-      }
-      // CTA reduction: warp shuffles, then the warps' sums in a fixed order
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        nre += __shfl_xor_sync(0xffffffffu, nre, o);
-        nim += __shfl_xor_sync(0xffffffffu, nim, o);
-        den += __shfl_xor_sync(0xffffffffu, den, o);
-      }
-      if ((tid & 31) == 0) {
-        wsum[tid >> 5][0] = nre;
-        wsum[tid >> 5][1] = nim;
-        wsum[tid >> 5][2] = den;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        float a = 0, bb = 0, cc = 0;
-        for (int w = 0; w < NS / 32; ++w) { a += wsum[w][0]; bb += wsum[w][1]; cc += wsum[w][2]; }
-        red[rank * 4 + 0] = a;
-        red[rank * 4 + 1] = bb;
-        red[rank * 4 + 2] = cc;
-      }
+
+  // A buffer is written only after the cluster barrier that follows the last
+  // reads of it by other CTAs; every write is followed by a barrier before
+  // the buffer is read.
+  float4* cur = buf0;
+  float4* nxt = buf1;
+  for (int rhs = rhs0; rhs < rhs1; ++rhs) {
+    const size_t off = spinor_offset(s, L, rhs);
+    Spinor<float> r0;
+    load_spinor(eta + off, r0);
+    if (!psi_zero) {
+      // r = eta - A psi on the domain: psi staged in shared memory, the halo
+      // (neighbours in other domains) from global memory
+      Spinor<float> pv, acc;
+      load_spinor(psi + off, pv);
+      spinor_to_planes(nxt, NS, tid, pv);
       cluster.sync();
-      double tre = 0, tim = 0, tden = 0;
-      for (int q2 = 0; q2 < CS; ++q2) {
-        const float* rr = cluster.map_shared_rank(red, q2);
-        tre += rr[q2 * 4 + 0];
-        tim += rr[q2 * 4 + 1];
-        tden += rr[q2 * 4 + 2];
+      float4* t = cur; cur = nxt; nxt = t;
+      domain_hops<BX, BY, BZ, BT, TPC, true>(cluster, g, cur, tid, rank, ltl, lc, c, s, L, rhs, links, psi, acc);
+#pragma unroll
+      for (int j = 0; j < 12; ++j) {
+        cx<float>& e = (&r0.c[0][0])[j];
+        const cx<float> pj = (&pv.c[0][0])[j], aj = (&acc.c[0][0])[j];
+        e = mk(fmaf(kappa, aj.re, e.re - pj.re), fmaf(kappa, aj.im, e.im - pj.im));
       }
-      om = tden > 0 ? mk((float)(tre / tden), (float)(tim / tden)) : mk(0.0f, 0.0f);
-    } else {
-      const double* tb = table + ((size_t)it * ndc + k) * 2;
-      om = mk((float)tb[0], (float)tb[1]);
-      cluster.sync();  // every CTA has read its neighbours' r
     }
+    spinor_to_planes(nxt, NS, tid, r0);
+    cluster.sync();
+    { float4* t = cur; cur = nxt; nxt = t; }
+    Spinor<float> x;
+    zero(x);
+
+    for (int it = 0; it < nmr; ++it) {
+      const bool last = (it == nmr - 1);
+      Spinor<float> q, rv;
+      const bool need_q = (mode == 0) || !last;
+      if (need_q)
+        domain_hops<BX, BY, BZ, BT, TPC, false>(cluster, g, cur, tid, rank, ltl, lc, c, s, L, rhs, links, psi, q);
+      planes_to_spinor(cur, NS, tid, rv);
+      if (need_q) {
 #pragma unroll
-    for (int j = 0; j < 12; ++j) cmac((&x.c[0][0])[j], om, (&rv.c[0][0])[j]);
-    if (!last) {
-      const cx<float> mom = mk(-om.re, -om.im);
+        for (int j = 0; j < 12; ++j) {
+          cx<float>& o = (&q.c[0][0])[j];
+          const cx<float> v = (&rv.c[0][0])[j];
+          o = mk(fmaf(-kappa, o.re, v.re), fmaf(-kappa, o.im, v.im));
+        }
+      }
+      cx<float> om;
+      if (mode == 0) {
+        float nre = 0, nim = 0, den = 0;
 #pragma unroll
-      for (int j = 0; j < 12; ++j) cmac((&rv.c[0][0])[j], mom, (&q.c[0][0])[j]);
-      spinor_to_soa(rS, NS, tid, rv);
-      cluster.sync();  // updated r visible before the next domain operator
+        for (int j = 0; j < 12; ++j) {
+          const cx<float> o = (&q.c[0][0])[j], v = (&rv.c[0][0])[j];
+          nre = fmaf(o.re, v.re, fmaf(o.im, v.im, nre));
+          nim = fmaf(o.re, v.im, fmaf(-o.im, v.re, nim));
+          den = fmaf(o.re, o.re, fmaf(o.im, o.im, den));
+        }
+        // CTA reduction: warp shuffles, then the warps' sums in a fixed order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          nre += __shfl_xor_sync(0xffffffffu, nre, o);
+          nim += __shfl_xor_sync(0xffffffffu, nim, o);
+          den += __shfl_xor_sync(0xffffffffu, den, o);
+        }
+        if ((tid & 31) == 0) {
+          wsum[tid >> 5][0] = nre;
+          wsum[tid >> 5][1] = nim;
+          wsum[tid >> 5][2] = den;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          float a = 0, bb = 0, cc = 0;
+          for (int w = 0; w < NS / 32; ++w) { a += wsum[w][0]; bb += wsum[w][1]; cc += wsum[w][2]; }
+          red[rank * 4 + 0] = a;
+          red[rank * 4 + 1] = bb;
+          red[rank * 4 + 2] = cc;
+        }
+        cluster.sync();
+        double tre = 0, tim = 0, tden = 0;
+        for (int q2 = 0; q2 < CS; ++q2) {
+          const float* rr = cluster.map_shared_rank(red, q2);
+          tre += rr[q2 * 4 + 0];
+          tim += rr[q2 * 4 + 1];
+          tden += rr[q2 * 4 + 2];
+        }
+        om = tden > 0 ? mk((float)(tre / tden), (float)(tim / tden)) : mk(0.0f, 0.0f);
+      } else {
+        const double* tb = table + ((size_t)it * ndc + k) * 2;
+        om = mk((float)tb[0], (float)tb[1]);
+      }
+#pragma unroll
+      for (int j = 0; j < 12; ++j) cmac((&x.c[0][0])[j], om, (&rv.c[0][0])[j]);
+      if (!last) {
+        const cx<float> mom = mk(-om.re, -om.im);
+#pragma unroll
+        for (int j = 0; j < 12; ++j) cmac((&rv.c[0][0])[j], mom, (&q.c[0][0])[j]);
+        spinor_to_planes(nxt, NS, tid, rv);
+        cluster.sync();
+        float4* t = cur; cur = nxt; nxt = t;
+      }
     }
+    // psi += x
+    Spinor<float> pv;
+    if (psi_zero) zero(pv);
+    else load_spinor(psi + off, pv);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) (&pv.c[0][0])[j] = (&pv.c[0][0])[j] + (&x.c[0][0])[j];
+    store_spinor(psi + off, pv);
+    // the next column writes psi into nxt: the last reads of nxt by other CTAs
+    // were fenced by the barrier that followed them
   }
-  // psi += x
-  Spinor<float> pv;
-  if (psi_zero) zero(pv);
-  else load_spinor(psi + off, pv);
-#pragma unroll
-  for (int j = 0; j < 12; ++j) (&pv.c[0][0])[j] = (&pv.c[0][0])[j] + (&x.c[0][0])[j];
   // no CTA of the cluster may exit while others still read its shared memory
   cluster.sync();
-  store_spinor(psi + off, pv);
 }
 
 template <int BX, int BY, int BZ, int BT, int TPC>
@@ -466,8 +468,14 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     attr = true;
   }
+  // columns per cluster: all of them when there are enough domains to fill
+  // the GPU, fewer on small lattices
+  const int ndc = g.nd / 2;
+  int rchunk = L;
+  while (rchunk > 1 && (long long)ndc * ((L + rchunk - 1) / rchunk) * SH::CS < 4 * 152) rchunk = (rchunk + 1) / 2;
+  const int nchunks = (L + rchunk - 1) / rchunk;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(SH::CS * (g.nd / 2) * L));
+  cfg.gridDim = dim3((unsigned)(SH::CS * ndc * nchunks));
   cfg.blockDim = dim3(SH::NS);
   cfg.dynamicSmemBytes = shm;
   cfg.stream = ex.stream;
@@ -478,7 +486,7 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
   attrs[0].val.clusterDim.z = 1;
   cfg.attrs = attrs;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, g, colour, links, eta, psi, L, (float)kappa, psi_zero ? 1 : 0, nmr, mode,
+  cudaLaunchKernelEx(&cfg, kern, g, colour, links, eta, psi, L, rchunk, (float)kappa, psi_zero ? 1 : 0, nmr, mode,
                      table);
   ++*ex.launches;
   return true;
@@ -508,7 +516,7 @@ int pow2_floor(int v) {
 }  // namespace
 
 int sap_sites_per_cta(const Geom& g, int L, bool fp64) {
-  int S = pow2_floor((fp64 ? 256 : 512) / L);
+  int S = pow2_floor((fp64 ? 256 : 384) / L);
   while (S > 1 && (g.Vd % S) != 0) S >>= 1;
   return S;
 }

@@ -146,26 +146,27 @@ constexpr int GRAM_CTAS = 2 * 152;  // fixed grid: deterministic partial sums
 // for D1 and L for D2 (real part).  A may be NULL when only D1/D2 are asked.
 // Returns the number of CTAs used (<= GRAM_CTAS).
 enum : int { GRAM_G1 = 1, GRAM_G2 = 2, GRAM_D1 = 4, GRAM_D2 = 8 };
+// err: device status word; ST_TIMEOUT is OR-ed in if a bounded wait for a
+// bulk copy gave up.
 template <typename R>
 int block_gram(const Exec& ex, long long nsite, int L, const cx<R>* A, const cx<R>* B1,
-               const cx<R>* B2, int flags, double* part);
+               const cx<R>* B2, int flags, double* part, int* err);
 int gram_slots(int L);
 
 // Y = X M row by row (M: L x L complex double on the device), in place allowed.
 template <typename R>
 void block_transform(const Exec& ex, long long nsite, int L, const cx<R>* X, const double* M, cx<R>* Y);
 
-// R -= V alpha; X64 += U alpha  (alpha: L x L complex double on the device)
+// R -= V alpha (alpha: L x L complex double on the device)
 template <typename R>
-void block_update_alpha(const Exec& ex, long long nsite, int L, const cx<R>* V, const cx<R>* U,
-                        const double* alpha, cx<R>* Rv, cx<double>* X64);
+void block_update_alpha(const Exec& ex, long long nsite, int L, const cx<R>* V, const double* alpha, cx<R>* Rv);
 
-// X64 += zeta S; R -= zeta Z; P = R + (P - zeta V) beta; partial column norms
-// of the new R into part[cta][L] (doubles).  Returns the CTAs used.
+// X64 += U alpha + zeta S; R -= zeta Z; P = R + (P - zeta V) beta; partial
+// column norms of the new R into part[cta][L] (doubles).  Returns the CTAs used.
 template <typename R>
-int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* S, const cx<R>* Z,
-                      const cx<R>* V, const double* zeta_beta, cx<R>* Rv, cx<R>* P, cx<double>* X64,
-                      double* part);
+int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* U, const double* alpha,
+                      const cx<R>* S, const cx<R>* Z, const cx<R>* V, const double* zeta_beta, cx<R>* Rv,
+                      cx<R>* P, cx<double>* X64, double* part);
 
 // ABI layout [site][sc][rhs] complex128 <-> internal [site][rhs][sc] in R.
 template <typename R>
@@ -178,7 +179,8 @@ void convert_block(const Exec& ex, long long n, const cx<RI>* in, cx<RO>* out);
 // links: ABI FP64 -> internal FP64 copy and FP32 copy; flags NaN/Inf in *bad
 void convert_links(const Exec& ex, long long nsite, const cx<double>* in, cx<double>* l64,
                    cx<float>* l32, int* bad);
-// out = B64 - W64 converted to R, with partial column norms (part[cta][L])
+// out = B64 - W64 converted to R (W64 NULL: out = B64), with partial column
+// norms (part[cta][L])
 template <typename R>
 int residual_from(const Exec& ex, long long nsite, int L, const cx<double>* B64,
                   const cx<double>* W64, cx<R>* out, double* part);
@@ -189,7 +191,7 @@ int abi_check(const Exec& ex, long long n_rows, int L, const cx<double>* in, dou
 // L x L algebra on the device (single-CTA kernels, blas.cu)
 // ---------------------------------------------------------------------------
 // Device-side status bits written by the small kernels.
-enum : int { ST_ALPHA_SINGULAR = 1, ST_ZZ_ZERO = 2, ST_CHOL_FAIL = 4, ST_NAN = 8 };
+enum : int { ST_ALPHA_SINGULAR = 1, ST_ZZ_ZERO = 2, ST_CHOL_FAIL = 4, ST_NAN = 8, ST_TIMEOUT = 16 };
 
 struct SmallWork {
   double* G;       // R~^H V (L x L complex), kept for the beta solve
