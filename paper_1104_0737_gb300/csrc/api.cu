@@ -40,6 +40,7 @@ struct mbicg_ctx {
   cx<double>* U64 = nullptr;
   cx<float>* U32 = nullptr;
   bool gauge = false;
+  bool su3 = false;  // every link SU(3): the fused SAP kernel may rebuild third rows
   std::string err;
   mbicg_stats stats{};
   long long launches = 0;
@@ -121,6 +122,7 @@ Geom lattice_geom(const mbicg_ctx* c, const int* block) {
     g.nd *= g.nb[mu];
   }
   g.Vd = g.V / g.nd;
+  g.su3 = c->su3 ? 1 : 0;
   geom_init_divisors(g);
   return g;
 }
@@ -683,10 +685,11 @@ int mbicg_load_gauge(mbicg_ctx* c, const double* U) {
   c->prof.collect();
   memcpy(&bad, c->h_small, sizeof(int));
   c->stats.kernel_launches = c->launches;
-  if (bad) {
+  if (bad & 1) {
     c->gauge = false;
     return fail(c, MBICG_ENAN, "gauge field holds NaN or Inf");
   }
+  c->su3 = (bad & 2) == 0;
   c->gauge = true;
   return MBICG_OK;
 }

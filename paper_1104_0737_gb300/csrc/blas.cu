@@ -462,13 +462,43 @@ __global__ void k_convert(long long n, const cx<RI>* __restrict__ in, cx<RO>* __
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = mk((RO)in[i].re, (RO)in[i].im);
 }
-__global__ void k_convert_links(long long n, const cx<double>* __restrict__ in, cx<double>* __restrict__ l64,
+// copies and converts the links, flags NaN/Inf (bit 0) and links that are
+// not SU(3) to 1e-10 (bit 1: U U^dagger != 1 or det U != 1)
+__global__ void k_convert_links(long long nlinks, const cx<double>* __restrict__ in, cx<double>* __restrict__ l64,
                                 cx<float>* __restrict__ l32, int* bad) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const cx<double> v = in[i];
-    if (!isfinite(v.re) || !isfinite(v.im)) atomicOr(bad, 1);
-    l64[i] = v;
-    l32[i] = mk((float)v.re, (float)v.im);
+  for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < nlinks;
+       l += (long long)gridDim.x * blockDim.x) {
+    cx<double> u[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      u[e] = in[l * 9 + e];
+      if (!isfinite(u[e].re) || !isfinite(u[e].im)) atomicOr(bad, 1);
+      l64[l * 9 + e] = u[e];
+      l32[l * 9 + e] = mk((float)u[e].re, (float)u[e].im);
+    }
+    double dev = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        double re = (i == j) ? -1.0 : 0.0, im = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {  // (U U^dagger)_ij = sum_k U_ik conj(U_jk)
+          const cx<double> a = u[i * 3 + k], b = u[j * 3 + k];
+          re += a.re * b.re + a.im * b.im;
+          im += a.im * b.re - a.re * b.im;
+        }
+        dev = fmax(dev, fabs(re) + fabs(im));
+      }
+    // det U = u0 (u4 u8 - u5 u7) - u1 (u3 u8 - u5 u6) + u2 (u3 u7 - u4 u6)
+    auto mul = [](cx<double> a, cx<double> b) { return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); };
+    auto sub = [](cx<double> a, cx<double> b) { return mk(a.re - b.re, a.im - b.im); };
+    const cx<double> m0 = sub(mul(u[4], u[8]), mul(u[5], u[7]));
+    const cx<double> m1 = sub(mul(u[3], u[8]), mul(u[5], u[6]));
+    const cx<double> m2 = sub(mul(u[3], u[7]), mul(u[4], u[6]));
+    const cx<double> det = sub(mul(u[0], m0), sub(mul(u[1], m1), mul(u[2], m2)));
+    dev = fmax(dev, fabs(det.re - 1.0) + fabs(det.im));
+    if (!(dev <= 1e-10)) atomicOr(bad, 2);
   }
 }
 
@@ -819,7 +849,7 @@ void convert_block(const Exec& ex, long long n, const cx<RI>* in, cx<RO>* out) {
   ++*ex.launches;
 }
 void convert_links(const Exec& ex, long long nsite, const cx<double>* in, cx<double>* l64, cx<float>* l32, int* bad) {
-  const long long n = nsite * 36;
+  const long long n = nsite * 4;
   k_convert_links<<<row_grid(n), NT, 0, ex.stream>>>(n, in, l64, l32, bad);
   ++*ex.launches;
 }

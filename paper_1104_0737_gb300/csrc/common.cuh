@@ -204,6 +204,7 @@ struct Geom {
   int V;         // sites
   int Vd;        // sites per domain
   int nd;        // domains
+  int su3;       // every link is unitary with det 1 (third rows may be rebuilt)
   FastDiv fd0, fd1, fd2;      // lattice extents x, y, z
   FastDiv fb0, fb1, fb2;      // domain extents x, y, z
   FastDiv fVd, fhalf, fnb1, fnb2;  // sites per domain, nb[0]/2, nb[1], nb[2]

@@ -15,6 +15,7 @@
 // and rebuilds the lower spin components: 1320 flops per site and column for
 // eta, 48 more for phi - kappa eta.
 #include <cooperative_groups.h>
+#include <stdlib.h>
 
 #include "internal.h"
 
@@ -189,29 +190,36 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_domain_appl
 // ---------------------------------------------------------------------------
 // Fused SAP colour sweep with the MR iterations on chip (FP32).
 //
-// One thread-block cluster per (domain of the colour, chunk of columns); each
-// CTA holds TPC time slices of the domain (BX*BY*BZ*TPC sites, one thread per
-// site) and runs the whole sweep for the columns of its chunk in turn.  The MR
-// residual of its sites lives in shared memory, double buffered so that one
-// cluster barrier per MR step separates the neighbour reads of one step from
-// the writes of the next; x and q stay in registers.  Spinors are stored as
-// 6 float4 planes so consecutive threads read consecutive 16-byte words.  Hops
-// in t that leave the CTA's slices read the residual from the neighbouring
-// CTA's shared memory (distributed shared memory).  Links are read through L1
-// (the domain's links are re-used by every column and MR step).
+// One thread-block cluster per (domain of the colour, chunk of columns).  The
+// DX x DY x DZ x DT domain is cut into CX x CY x CZ x CT sub-blocks, one per
+// CTA of the cluster, one thread per site; cutting x, y and z in two gives
+// every CTA the same number of hops that leave the domain and of hops into a
+// neighbouring CTA, so no CTA lags at the cluster barriers.  Each CTA runs the
+// whole sweep for the columns of its chunk in turn.  The MR residual of its
+// sites lives in shared memory, double buffered so that one cluster barrier
+// per MR step separates the neighbour reads of one step from the writes of
+// the next; x and q stay in registers.  Spinors are stored as 6 float4
+// planes so consecutive threads read consecutive 16-byte words; hops into a
+// neighbouring CTA read its shared memory (distributed shared memory).  Links
+// are read through L1 (the domain's links serve every column and MR step).
 // For every column:
 //   r = eta - A psi on the domain (psi staged in shared memory, halo from global),
 //   nmr times: q = A_dom r; omega (per column from the cluster-wide dots, or
 //   from the frozen table); x += omega r; r -= omega q,
 //   psi += x.
 // ---------------------------------------------------------------------------
-template <int BX, int BY, int BZ, int BT, int TPC>
+__host__ __device__ constexpr int pick4(int mu, int a, int b, int c, int d) {
+  return mu == 0 ? a : mu == 1 ? b : mu == 2 ? c : d;
+}
+
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
 struct SweepShape {
-  static constexpr int NS = BX * BY * BZ * TPC;  // sites per CTA = threads
-  static constexpr int CS = BT / TPC;             // CTAs per cluster
-  static constexpr int SLAB = BX * BY * BZ;
-  // two spinor buffers of 6 float4 planes + partial dots
-  static constexpr size_t smem_bytes() { return (size_t)NS * 2 * 6 * 16 + 64 * sizeof(float); }
+  static constexpr int SX = DX / CX, SY = DY / CY, SZ = DZ / CZ, ST = DT / CT;
+  static constexpr int NS = SX * SY * SZ * ST;  // sites per CTA = threads
+  static constexpr int CS = CX * CY * CZ * CT;  // CTAs per cluster
+  // two residual buffers (6 float4 planes each), the first two rows of the
+  // four forward links of each site (12 float4 planes), partial dots
+  static constexpr size_t smem_bytes() { return (size_t)NS * (12 + 12) * 16 + 64 * sizeof(float); }
 };
 
 __device__ __forceinline__ void spinor_to_planes(float4* vS, int NS, int site, const Spinor<float>& v) {
@@ -230,31 +238,56 @@ __device__ __forceinline__ void planes_to_spinor(const float4* vS, int NS, int s
   }
 }
 
+// The first two rows of an SU(3) link from its 3 float4 planes; the third
+// row is rebuilt as the complex conjugate of the cross product of the first
+// two (unitarity with det = 1).
+__device__ __forceinline__ void planes_to_link12(const float4* uS, int NS, int mu, int site, Link<float>& u) {
+  const float4 a = uS[(mu * 3 + 0) * NS + site], b = uS[(mu * 3 + 1) * NS + site], c = uS[(mu * 3 + 2) * NS + site];
+  u.m[0][0] = mk(a.x, a.y);
+  u.m[0][1] = mk(a.z, a.w);
+  u.m[0][2] = mk(b.x, b.y);
+  u.m[1][0] = mk(b.z, b.w);
+  u.m[1][1] = mk(c.x, c.y);
+  u.m[1][2] = mk(c.z, c.w);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+    const cx<float> t = u.m[0][j1] * u.m[1][j2] - u.m[0][j2] * u.m[1][j1];
+    u.m[2][j] = conjg(t);
+  }
+}
+
 // Hop sum over the eight neighbours of a site of the domain, reading the
 // neighbour's spinor from the (distributed) shared-memory planes vS when it
 // lies in the domain.  Hops that leave the domain are dropped (HALO = false:
 // the Dirichlet domain operator A_dom) or taken from global memory (HALO =
 // true: the full operator, psi_g, with the antiperiodic phase of the t
-// boundary).
-template <int BX, int BY, int BZ, int BT, int TPC, bool HALO>
+// boundary).  sb: coordinates inside the CTA's sub-block, lc: inside the
+// domain, c: on the lattice.
+template <typename SH, int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, bool HALO>
 __device__ __forceinline__ void domain_hops(cooperative_groups::cluster_group& cluster, const Geom& g,
-                                            const float4* vS, int tid, int rank, int ltl, const int lc[4],
+                                            const float4* vS, const float4* uS, int tid, int rank,
+                                            const int sb[4], const int lc[4],
                                             const int c[4], int s, int L, int rhs,
                                             const cx<float>* __restrict__ links,
                                             const cx<float>* __restrict__ psi_g, Spinor<float>& acc) {
-  constexpr int NS = BX * BY * BZ * TPC;
-  constexpr int SLAB = BX * BY * BZ;
+  constexpr int NS = SH::NS;
   zero(acc);
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
     for (int fwd = 1; fwd >= 0; --fwd) {
-      const int ext = mu == 0 ? BX : mu == 1 ? BY : mu == 2 ? BZ : BT;
+      constexpr int dummy = 0;
+      (void)dummy;
+      const int ext = pick4(mu, DX, DY, DZ, DT);
+      const int sub = pick4(mu, SH::SX, SH::SY, SH::SZ, SH::ST);
+      const int sub_stride = pick4(mu, 1, SH::SX, SH::SX * SH::SY, SH::SX * SH::SY * SH::SZ);
+      const int cta_stride = pick4(mu, 1, CX, CX * CY, CX * CY * CZ);
       const bool leaves = fwd ? (lc[mu] == ext - 1) : (lc[mu] == 0);
       if (leaves && !HALO) continue;
       Spinor<float> pn;
       float phase = 1.0f;
-      int sn;  // global index of the neighbour (for its backward link)
+      int sn;  // lattice index of the neighbour (for its backward link)
       {
         const int dm = g.d[mu];
         const int stride = mu == 0 ? 1 : mu == 1 ? g.d[0] : mu == 2 ? g.d[0] * g.d[1] : g.d[0] * g.d[1] * g.d[2];
@@ -262,27 +295,29 @@ __device__ __forceinline__ void domain_hops(cooperative_groups::cluster_group& c
         sn = fwd ? (wrap ? s - (dm - 1) * stride : s + stride) : (wrap ? s + (dm - 1) * stride : s - stride);
         if (mu == 3 && wrap) phase = -1.0f;
       }
+      Link<float> u;
       if (!leaves) {
         const float4* rsrc = vS;
+        const float4* usrc = uS;
         int nb;
-        if (mu < 3) {
-          const int st = mu == 0 ? 1 : mu == 1 ? BX : BX * BY;
-          nb = fwd ? tid + st : tid - st;
+        const int sn_sub = sb[mu] + (fwd ? 1 : -1);
+        if (sn_sub >= 0 && sn_sub < sub) {
+          nb = tid + (fwd ? sub_stride : -sub_stride);
         } else {
-          const int nl = ltl + (fwd ? 1 : -1);
-          if (nl >= 0 && nl < TPC) {
-            nb = tid + (fwd ? SLAB : -SLAB);
-          } else {
-            nb = tid + (fwd ? -(TPC - 1) * SLAB : (TPC - 1) * SLAB);
-            rsrc = cluster.map_shared_rank(vS, rank + (fwd ? 1 : -1));
-          }
+          // across into the neighbouring CTA of the cluster, same position on the far face
+          const int other = rank + (fwd ? cta_stride : -cta_stride);
+          nb = tid + (fwd ? -(sub - 1) * sub_stride : (sub - 1) * sub_stride);
+          rsrc = cluster.map_shared_rank(vS, other);
+          usrc = cluster.map_shared_rank(uS, other);
         }
         planes_to_spinor(rsrc, NS, nb, pn);
+        if (fwd) planes_to_link12(uS, NS, mu, tid, u);
+        else planes_to_link12(usrc, NS, mu, nb, u);
       } else {
         load_spinor(psi_g + spinor_offset(sn, L, rhs), pn);
+        if (fwd) planes_to_link12(uS, NS, mu, tid, u);
+        else load_link(links + (size_t)(sn * 4 + mu) * 9, u);
       }
-      Link<float> u;
-      load_link(links + (size_t)((fwd ? s : sn) * 4 + mu) * 9, u);
       cx<float> h[2][3], w[2][3];
       if (fwd) {
         switch (mu) {
@@ -303,21 +338,22 @@ __device__ __forceinline__ void domain_hops(cooperative_groups::cluster_group& c
   }
 }
 
-template <int BX, int BY, int BZ, int BT, int TPC>
-__global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256) ? 2 : 1)
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
+__global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS,
+                                  (SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS <= 256) ? 2 : 1)
     k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const cx<float>* __restrict__ eta,
                 cx<float>* __restrict__ psi, int L, int rchunk, float kappa, int psi_zero, int nmr, int mode,
                 const double* __restrict__ table) {
-  using SH = SweepShape<BX, BY, BZ, BT, TPC>;
+  using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   constexpr int NS = SH::NS;
   constexpr int CS = SH::CS;
-  constexpr int SLAB = SH::SLAB;
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ float4 sm4[];
-  float4* buf0 = sm4;                                      // [6][NS]
-  float4* buf1 = sm4 + 6 * NS;                             // [6][NS]
-  float* red = reinterpret_cast<float*>(sm4 + 12 * NS);   // [CS][4] partial dots
+  float4* buf0 = sm4;                                      // [6][NS] residual
+  float4* buf1 = sm4 + 6 * NS;                             // [6][NS] residual
+  float4* uS = sm4 + 12 * NS;                              // [12][NS] link rows 0, 1
+  float* red = reinterpret_cast<float*>(sm4 + 24 * NS);   // [CS][4] partial dots
   __shared__ float wsum[NS / 32][3];
 
   const int rank = (int)cluster.block_rank();
@@ -327,25 +363,43 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
   const int rhs0 = (cid - k * nchunks) * rchunk;
   const int rhs1 = min(L, rhs0 + rchunk);
   const int tid = threadIdx.x;
-  int lc[4];
-  lc[0] = tid % BX;
-  lc[1] = (tid / BX) % BY;
-  lc[2] = (tid / (BX * BY)) % BZ;
-  const int ltl = tid / SLAB;
-  lc[3] = rank * TPC + ltl;
+  int sb[4], cb[4], lc[4];
+  sb[0] = tid % SH::SX;
+  sb[1] = (tid / SH::SX) % SH::SY;
+  sb[2] = (tid / (SH::SX * SH::SY)) % SH::SZ;
+  sb[3] = tid / (SH::SX * SH::SY * SH::SZ);
+  cb[0] = rank % CX;
+  cb[1] = (rank / CX) % CY;
+  cb[2] = (rank / (CX * CY)) % CZ;
+  cb[3] = rank / (CX * CY * CZ);
+  lc[0] = cb[0] * SH::SX + sb[0];
+  lc[1] = cb[1] * SH::SY + sb[1];
+  lc[2] = cb[2] * SH::SZ + sb[2];
+  lc[3] = cb[3] * SH::ST + sb[3];
   int b[4];
   colour_domain(g, colour, k, b);
   int c[4];
-  c[0] = b[0] * BX + lc[0];
-  c[1] = b[1] * BY + lc[1];
-  c[2] = b[2] * BZ + lc[2];
-  c[3] = b[3] * BT + lc[3];
+  c[0] = b[0] * DX + lc[0];
+  c[1] = b[1] * DY + lc[1];
+  c[2] = b[2] * DZ + lc[2];
+  c[3] = b[3] * DT + lc[3];
   const int s = site_index(g, c);
   const int ndc = g.nd / 2;
 
   // A buffer is written only after the cluster barrier that follows the last
   // reads of it by other CTAs; every write is followed by a barrier before
   // the buffer is read.
+  // the first two rows of this site's four forward links, once for all columns
+  {
+    const float2* gl = reinterpret_cast<const float2*>(links + (size_t)s * 36);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float2 v0 = __ldg(gl + mu * 9 + 2 * q), v1 = __ldg(gl + mu * 9 + 2 * q + 1);
+        uS[(mu * 3 + q) * NS + tid] = make_float4(v0.x, v0.y, v1.x, v1.y);
+      }
+  }
   float4* cur = buf0;
   float4* nxt = buf1;
   for (int rhs = rhs0; rhs < rhs1; ++rhs) {
@@ -360,7 +414,8 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
       spinor_to_planes(nxt, NS, tid, pv);
       cluster.sync();
       float4* t = cur; cur = nxt; nxt = t;
-      domain_hops<BX, BY, BZ, BT, TPC, true>(cluster, g, cur, tid, rank, ltl, lc, c, s, L, rhs, links, psi, acc);
+      domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, true>(cluster, g, cur, uS, tid, rank, sb, lc, c, s, L, rhs, links,
+                                                       psi, acc);
 #pragma unroll
       for (int j = 0; j < 12; ++j) {
         cx<float>& e = (&r0.c[0][0])[j];
@@ -369,7 +424,7 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
       }
     }
     spinor_to_planes(nxt, NS, tid, r0);
-    cluster.sync();
+    cluster.sync();  // r0 (and, for the first column, every CTA's links) visible
     { float4* t = cur; cur = nxt; nxt = t; }
     Spinor<float> x;
     zero(x);
@@ -379,7 +434,8 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
       Spinor<float> q, rv;
       const bool need_q = (mode == 0) || !last;
       if (need_q)
-        domain_hops<BX, BY, BZ, BT, TPC, false>(cluster, g, cur, tid, rank, ltl, lc, c, s, L, rhs, links, psi, q);
+        domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, false>(cluster, g, cur, uS, tid, rank, sb, lc, c, s, L, rhs,
+                                                          links, psi, q);
       planes_to_spinor(cur, NS, tid, rv);
       if (need_q) {
 #pragma unroll
@@ -457,15 +513,16 @@ __global__ void __launch_bounds__(BX * BY * BZ * TPC, (BX * BY * BZ * TPC <= 256
   cluster.sync();
 }
 
-template <int BX, int BY, int BZ, int BT, int TPC>
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
 bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
                   cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table) {
-  using SH = SweepShape<BX, BY, BZ, BT, TPC>;
-  auto kern = k_sap_sweep<BX, BY, BZ, BT, TPC>;
+  using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
+  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   const size_t shm = SH::smem_bytes();
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (SH::CS > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     attr = true;
   }
   // columns per cluster: all of them when there are enough domains to fill
@@ -496,12 +553,13 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
 
 bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
                      cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table) {
-  if (mode == 1) return false;
+  if (mode == 1 || !g.su3) return false;  // the kernel rebuilds the third link row
   const int* bk = g.blk;
+  // 8^4: eight CTAs of 4 x 4 x 4 x 8 sites; 4^4: one CTA
   if (bk[0] == 8 && bk[1] == 8 && bk[2] == 8 && bk[3] == 8)
-    return launch_sweep<8, 8, 8, 8, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
+    return launch_sweep<8, 8, 8, 8, 2, 2, 2, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
   if (bk[0] == 4 && bk[1] == 4 && bk[2] == 4 && bk[3] == 4)
-    return launch_sweep<4, 4, 4, 4, 4>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
+    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
   return false;
 }
 

@@ -177,6 +177,7 @@ void internal_to_abi(const Exec& ex, long long nsite, int L, const cx<R>* in, cx
 template <typename RI, typename RO>
 void convert_block(const Exec& ex, long long n, const cx<RI>* in, cx<RO>* out);
 // links: ABI FP64 -> internal FP64 copy and FP32 copy; flags NaN/Inf in *bad
+// (bit 0) and links that are not SU(3) to 1e-10 (bit 1)
 void convert_links(const Exec& ex, long long nsite, const cx<double>* in, cx<double>* l64,
                    cx<float>* l32, int* bad);
 // out = B64 - W64 converted to R (W64 NULL: out = B64), with partial column
