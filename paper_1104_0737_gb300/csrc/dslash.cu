@@ -238,11 +238,41 @@ __device__ __forceinline__ void planes_to_spinor(const float4* vS, int NS, int s
   }
 }
 
-// The first two rows of an SU(3) link from its 3 float4 planes; the third
-// row is rebuilt as the complex conjugate of the cross product of the first
-// two (unitarity with det = 1).
-__device__ __forceinline__ void planes_to_link12(const float4* uS, int NS, int mu, int site, Link<float>& u) {
-  const float4 a = uS[(mu * 3 + 0) * NS + site], b = uS[(mu * 3 + 1) * NS + site], c = uS[(mu * 3 + 2) * NS + site];
+// Shared-memory words of any CTA of the cluster by 32-bit shared::cluster
+// address: mapa turns a CTA-local shared address into the address of the
+// same offset in CTA `rank`; one load instruction then serves hops inside
+// the CTA and hops into a neighbouring CTA alike, so warps do not diverge.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr));
+  return v;
+}
+
+// Spinor of site `site` from 6 float4 planes of NS sites at cluster address base.
+__device__ __forceinline__ void cluster_planes_to_spinor(uint32_t base, int NS, int site, Spinor<float>& v) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float4 t = ld_cluster_f4(base + (uint32_t)(k * NS + site) * 16u);
+    (&v.c[0][0])[2 * k] = mk(t.x, t.y);
+    (&v.c[0][0])[2 * k + 1] = mk(t.z, t.w);
+  }
+}
+
+// The first two rows of an SU(3) link from its 3 float4 planes (link mu of
+// site `site`, cluster address base); the third row is rebuilt as the
+// complex conjugate of the cross product of the first two (unitarity with
+// det = 1).
+__device__ __forceinline__ void cluster_planes_to_link12(uint32_t base, int NS, int mu, int site, Link<float>& u) {
+  const float4 a = ld_cluster_f4(base + (uint32_t)((mu * 3 + 0) * NS + site) * 16u);
+  const float4 b = ld_cluster_f4(base + (uint32_t)((mu * 3 + 1) * NS + site) * 16u);
+  const float4 c = ld_cluster_f4(base + (uint32_t)((mu * 3 + 2) * NS + site) * 16u);
   u.m[0][0] = mk(a.x, a.y);
   u.m[0][1] = mk(a.z, a.w);
   u.m[0][2] = mk(b.x, b.y);
@@ -258,17 +288,19 @@ __device__ __forceinline__ void planes_to_link12(const float4* uS, int NS, int m
 }
 
 // Hop sum over the eight neighbours of a site of the domain, reading the
-// neighbour's spinor from the (distributed) shared-memory planes vS when it
-// lies in the domain.  Hops that leave the domain are dropped (HALO = false:
-// the Dirichlet domain operator A_dom) or taken from global memory (HALO =
-// true: the full operator, psi_g, with the antiperiodic phase of the t
-// boundary).  sb: coordinates inside the CTA's sub-block, lc: inside the
+// neighbour's spinor from the (distributed) shared-memory planes at cluster
+// address vS when it lies in the domain, and the link rows from the planes
+// at uS (the site's own forward links; the neighbour's for a backward hop).
+// vS is a CTA-local shared address, uS the CTA's link planes already in the
+// cluster window.
+// Hops that leave the domain are dropped (HALO = false: the Dirichlet
+// domain operator A_dom) or taken from global memory (HALO = true: the full
+// operator, psi_g and the global links, with the antiperiodic phase of the
+// t boundary).  sb: coordinates inside the CTA's sub-block, lc: inside the
 // domain, c: on the lattice.
 template <typename SH, int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, bool HALO>
-__device__ __forceinline__ void domain_hops(cooperative_groups::cluster_group& cluster, const Geom& g,
-                                            const float4* vS, const float4* uS, int tid, int rank,
-                                            const int sb[4], const int lc[4],
-                                            const int c[4], int s, int L, int rhs,
+__device__ __forceinline__ void domain_hops(const Geom& g, uint32_t vS, uint32_t uS, int tid, int rank,
+                                            const int sb[4], const int lc[4], const int c[4], int s, int L, int rhs,
                                             const cx<float>* __restrict__ links,
                                             const cx<float>* __restrict__ psi_g, Spinor<float>& acc) {
   constexpr int NS = SH::NS;
@@ -277,8 +309,6 @@ __device__ __forceinline__ void domain_hops(cooperative_groups::cluster_group& c
   for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
     for (int fwd = 1; fwd >= 0; --fwd) {
-      constexpr int dummy = 0;
-      (void)dummy;
       const int ext = pick4(mu, DX, DY, DZ, DT);
       const int sub = pick4(mu, SH::SX, SH::SY, SH::SZ, SH::ST);
       const int sub_stride = pick4(mu, 1, SH::SX, SH::SX * SH::SY, SH::SX * SH::SY * SH::SZ);
@@ -286,36 +316,27 @@ __device__ __forceinline__ void domain_hops(cooperative_groups::cluster_group& c
       const bool leaves = fwd ? (lc[mu] == ext - 1) : (lc[mu] == 0);
       if (leaves && !HALO) continue;
       Spinor<float> pn;
+      Link<float> u;
       float phase = 1.0f;
-      int sn;  // lattice index of the neighbour (for its backward link)
-      {
+      if (!leaves) {
+        // the neighbour is in this CTA or, across a face of the sub-block,
+        // at the same position on the far face of the next CTA
+        const int sn_sub = sb[mu] + (fwd ? 1 : -1);
+        const bool cross = sn_sub < 0 || sn_sub >= sub;
+        const int nb = cross ? tid + (fwd ? -(sub - 1) * sub_stride : (sub - 1) * sub_stride)
+                             : tid + (fwd ? sub_stride : -sub_stride);
+        const uint32_t other = (uint32_t)(cross ? rank + (fwd ? cta_stride : -cta_stride) : rank);
+        cluster_planes_to_spinor(cluster_addr(vS, other), NS, nb, pn);
+        if (fwd) cluster_planes_to_link12(uS, NS, mu, tid, u);
+        else cluster_planes_to_link12(cluster_addr(uS, other), NS, mu, nb, u);
+      } else {
         const int dm = g.d[mu];
         const int stride = mu == 0 ? 1 : mu == 1 ? g.d[0] : mu == 2 ? g.d[0] * g.d[1] : g.d[0] * g.d[1] * g.d[2];
         const bool wrap = fwd ? (c[mu] == dm - 1) : (c[mu] == 0);
-        sn = fwd ? (wrap ? s - (dm - 1) * stride : s + stride) : (wrap ? s + (dm - 1) * stride : s - stride);
+        const int sn = fwd ? (wrap ? s - (dm - 1) * stride : s + stride) : (wrap ? s + (dm - 1) * stride : s - stride);
         if (mu == 3 && wrap) phase = -1.0f;
-      }
-      Link<float> u;
-      if (!leaves) {
-        const float4* rsrc = vS;
-        const float4* usrc = uS;
-        int nb;
-        const int sn_sub = sb[mu] + (fwd ? 1 : -1);
-        if (sn_sub >= 0 && sn_sub < sub) {
-          nb = tid + (fwd ? sub_stride : -sub_stride);
-        } else {
-          // across into the neighbouring CTA of the cluster, same position on the far face
-          const int other = rank + (fwd ? cta_stride : -cta_stride);
-          nb = tid + (fwd ? -(sub - 1) * sub_stride : (sub - 1) * sub_stride);
-          rsrc = cluster.map_shared_rank(vS, other);
-          usrc = cluster.map_shared_rank(uS, other);
-        }
-        planes_to_spinor(rsrc, NS, nb, pn);
-        if (fwd) planes_to_link12(uS, NS, mu, tid, u);
-        else planes_to_link12(usrc, NS, mu, nb, u);
-      } else {
         load_spinor(psi_g + spinor_offset(sn, L, rhs), pn);
-        if (fwd) planes_to_link12(uS, NS, mu, tid, u);
+        if (fwd) cluster_planes_to_link12(uS, NS, mu, tid, u);
         else load_link(links + (size_t)(sn * 4 + mu) * 9, u);
       }
       cx<float> h[2][3], w[2][3];
@@ -400,28 +421,35 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
         uS[(mu * 3 + q) * NS + tid] = make_float4(v0.x, v0.y, v1.x, v1.y);
       }
   }
+  const uint32_t uA = cluster_addr(smem_addr(uS), (uint32_t)rank);  // own link planes, cluster window
   float4* cur = buf0;
   float4* nxt = buf1;
   for (int rhs = rhs0; rhs < rhs1; ++rhs) {
     const size_t off = spinor_offset(s, L, rhs);
     Spinor<float> r0;
-    load_spinor(eta + off, r0);
     if (!psi_zero) {
       // r = eta - A psi on the domain: psi staged in shared memory, the halo
       // (neighbours in other domains) from global memory
-      Spinor<float> pv, acc;
-      load_spinor(psi + off, pv);
-      spinor_to_planes(nxt, NS, tid, pv);
+      {
+        Spinor<float> pv;
+        load_spinor(psi + off, pv);
+        spinor_to_planes(nxt, NS, tid, pv);
+      }
       cluster.sync();
       float4* t = cur; cur = nxt; nxt = t;
-      domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, true>(cluster, g, cur, uS, tid, rank, sb, lc, c, s, L, rhs, links,
-                                                       psi, acc);
+      Spinor<float> acc, pv;
+      domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, true>(g, smem_addr(cur), uA, tid, rank, sb, lc, c, s, L, rhs,
+                                                       links, psi, acc);
+      load_spinor(eta + off, r0);
+      planes_to_spinor(cur, NS, tid, pv);
 #pragma unroll
       for (int j = 0; j < 12; ++j) {
         cx<float>& e = (&r0.c[0][0])[j];
         const cx<float> pj = (&pv.c[0][0])[j], aj = (&acc.c[0][0])[j];
         e = mk(fmaf(kappa, aj.re, e.re - pj.re), fmaf(kappa, aj.im, e.im - pj.im));
       }
+    } else {
+      load_spinor(eta + off, r0);
     }
     spinor_to_planes(nxt, NS, tid, r0);
     cluster.sync();  // r0 (and, for the first column, every CTA's links) visible
@@ -434,7 +462,7 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
       Spinor<float> q, rv;
       const bool need_q = (mode == 0) || !last;
       if (need_q)
-        domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, false>(cluster, g, cur, uS, tid, rank, sb, lc, c, s, L, rhs,
+        domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, false>(g, smem_addr(cur), uA, tid, rank, sb, lc, c, s, L, rhs,
                                                           links, psi, q);
       planes_to_spinor(cur, NS, tid, rv);
       if (need_q) {
