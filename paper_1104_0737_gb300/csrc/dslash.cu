@@ -15,6 +15,7 @@
 // and rebuilds the lower spin components: 1320 flops per site and column for
 // eta, 48 more for phi - kappa eta.
 #include <cooperative_groups.h>
+#include <algorithm>
 #include <stdlib.h>
 
 #include "internal.h"
@@ -287,19 +288,38 @@ __device__ __forceinline__ void cluster_planes_to_link12(uint32_t base, int NS, 
   }
 }
 
+// As cluster_planes_to_link12, from the CTA's own planes.
+__device__ __forceinline__ void planes_to_link12(const float4* uS, int NS, int mu, int site, Link<float>& u) {
+  const float4 a = uS[(mu * 3 + 0) * NS + site], b = uS[(mu * 3 + 1) * NS + site], c = uS[(mu * 3 + 2) * NS + site];
+  u.m[0][0] = mk(a.x, a.y);
+  u.m[0][1] = mk(a.z, a.w);
+  u.m[0][2] = mk(b.x, b.y);
+  u.m[1][0] = mk(b.z, b.w);
+  u.m[1][1] = mk(c.x, c.y);
+  u.m[1][2] = mk(c.z, c.w);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+    const cx<float> t = u.m[0][j1] * u.m[1][j2] - u.m[0][j2] * u.m[1][j1];
+    u.m[2][j] = conjg(t);
+  }
+}
+
 // Hop sum over the eight neighbours of a site of the domain, reading the
 // neighbour's spinor from the (distributed) shared-memory planes at cluster
 // address vS when it lies in the domain, and the link rows from the planes
 // at uS (the site's own forward links; the neighbour's for a backward hop).
 // vS is a CTA-local shared address, uS the CTA's link planes already in the
-// cluster window.
+// cluster window; vL and uL are the same planes as pointers, read directly
+// where the hop cannot leave the CTA.
 // Hops that leave the domain are dropped (HALO = false: the Dirichlet
 // domain operator A_dom) or taken from global memory (HALO = true: the full
 // operator, psi_g and the global links, with the antiperiodic phase of the
 // t boundary).  sb: coordinates inside the CTA's sub-block, lc: inside the
 // domain, c: on the lattice.
 template <typename SH, int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, bool HALO>
-__device__ __forceinline__ void domain_hops(const Geom& g, uint32_t vS, uint32_t uS, int tid, int rank,
+__device__ __forceinline__ void domain_hops(const Geom& g, const float4* vL, uint32_t vS, const float4* uL,
+                                            uint32_t uS, int tid, int rank,
                                             const int sb[4], const int lc[4], const int c[4], int s, int L, int rhs,
                                             const cx<float>* __restrict__ links,
                                             const cx<float>* __restrict__ psi_g, Spinor<float>& acc) {
@@ -325,10 +345,16 @@ __device__ __forceinline__ void domain_hops(const Geom& g, uint32_t vS, uint32_t
         const bool cross = sn_sub < 0 || sn_sub >= sub;
         const int nb = cross ? tid + (fwd ? -(sub - 1) * sub_stride : (sub - 1) * sub_stride)
                              : tid + (fwd ? sub_stride : -sub_stride);
-        const uint32_t other = (uint32_t)(cross ? rank + (fwd ? cta_stride : -cta_stride) : rank);
-        cluster_planes_to_spinor(cluster_addr(vS, other), NS, nb, pn);
-        if (fwd) cluster_planes_to_link12(uS, NS, mu, tid, u);
-        else cluster_planes_to_link12(cluster_addr(uS, other), NS, mu, nb, u);
+        if (pick4(mu, CX, CY, CZ, SH::CS / (CX * CY * CZ)) == 1) {
+          // the domain is not split in this direction: plain shared loads
+          planes_to_spinor(reinterpret_cast<const float4*>(vL), NS, nb, pn);
+          planes_to_link12(uL, NS, mu, fwd ? tid : nb, u);
+        } else {
+          const uint32_t other = (uint32_t)(cross ? rank + (fwd ? cta_stride : -cta_stride) : rank);
+          cluster_planes_to_spinor(cluster_addr(vS, other), NS, nb, pn);
+          if (fwd) planes_to_link12(uL, NS, mu, tid, u);
+          else cluster_planes_to_link12(cluster_addr(uS, other), NS, mu, nb, u);
+        }
       } else {
         const int dm = g.d[mu];
         const int stride = mu == 0 ? 1 : mu == 1 ? g.d[0] : mu == 2 ? g.d[0] * g.d[1] : g.d[0] * g.d[1] * g.d[2];
@@ -336,7 +362,7 @@ __device__ __forceinline__ void domain_hops(const Geom& g, uint32_t vS, uint32_t
         const int sn = fwd ? (wrap ? s - (dm - 1) * stride : s + stride) : (wrap ? s + (dm - 1) * stride : s - stride);
         if (mu == 3 && wrap) phase = -1.0f;
         load_spinor(psi_g + spinor_offset(sn, L, rhs), pn);
-        if (fwd) cluster_planes_to_link12(uS, NS, mu, tid, u);
+        if (fwd) planes_to_link12(uL, NS, mu, tid, u);
         else load_link(links + (size_t)(sn * 4 + mu) * 9, u);
       }
       cx<float> h[2][3], w[2][3];
@@ -363,7 +389,7 @@ template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
 __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS,
                                   (SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS <= 256) ? 2 : 1)
     k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const cx<float>* __restrict__ eta,
-                cx<float>* __restrict__ psi, int L, int rchunk, float kappa, int psi_zero, int nmr, int mode,
+                cx<float>* __restrict__ psi, int L, float kappa, int psi_zero, int nmr, int mode,
                 const double* __restrict__ table) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   constexpr int NS = SH::NS;
@@ -378,11 +404,6 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
   __shared__ float wsum[NS / 32][3];
 
   const int rank = (int)cluster.block_rank();
-  const int nchunks = (L + rchunk - 1) / rchunk;
-  const int cid = blockIdx.x / CS;
-  const int k = cid / nchunks;  // domain of this colour
-  const int rhs0 = (cid - k * nchunks) * rchunk;
-  const int rhs1 = min(L, rhs0 + rchunk);
   const int tid = threadIdx.x;
   int sb[4], cb[4], lc[4];
   sb[0] = tid % SH::SX;
@@ -397,34 +418,48 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
   lc[1] = cb[1] * SH::SY + sb[1];
   lc[2] = cb[2] * SH::SZ + sb[2];
   lc[3] = cb[3] * SH::ST + sb[3];
-  int b[4];
-  colour_domain(g, colour, k, b);
-  int c[4];
-  c[0] = b[0] * DX + lc[0];
-  c[1] = b[1] * DY + lc[1];
-  c[2] = b[2] * DZ + lc[2];
-  c[3] = b[3] * DT + lc[3];
-  const int s = site_index(g, c);
   const int ndc = g.nd / 2;
+  // persistent clusters: the (domain, column) items of this colour, domain
+  // major, are cut into one contiguous range per cluster
+  const int nclu = gridDim.x / CS;
+  const int cid = blockIdx.x / CS;
+  const long long nitems = (long long)ndc * L;
+  const int item0 = (int)(nitems * cid / nclu);
+  const int item1 = (int)(nitems * (cid + 1) / nclu);
+  const uint32_t uA = cluster_addr(smem_addr(uS), (uint32_t)rank);  // own link planes, cluster window
 
   // A buffer is written only after the cluster barrier that follows the last
   // reads of it by other CTAs; every write is followed by a barrier before
   // the buffer is read.
-  // the first two rows of this site's four forward links, once for all columns
-  {
-    const float2* gl = reinterpret_cast<const float2*>(links + (size_t)s * 36);
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const float2 v0 = __ldg(gl + mu * 9 + 2 * q), v1 = __ldg(gl + mu * 9 + 2 * q + 1);
-        uS[(mu * 3 + q) * NS + tid] = make_float4(v0.x, v0.y, v1.x, v1.y);
-      }
-  }
-  const uint32_t uA = cluster_addr(smem_addr(uS), (uint32_t)rank);  // own link planes, cluster window
   float4* cur = buf0;
   float4* nxt = buf1;
-  for (int rhs = rhs0; rhs < rhs1; ++rhs) {
+  int k = -1, s = 0;
+  int c[4];
+  for (int item = item0; item < item1; ++item) {
+    const int kk = item / L;
+    const int rhs = item - kk * L;
+    if (kk != k) {
+      k = kk;  // a new domain of this colour
+      int b[4];
+      colour_domain(g, colour, k, b);
+      c[0] = b[0] * DX + lc[0];
+      c[1] = b[1] * DY + lc[1];
+      c[2] = b[2] * DZ + lc[2];
+      c[3] = b[3] * DT + lc[3];
+      s = site_index(g, c);
+      if (item != item0) cluster.sync();  // no CTA still reads the previous domain's links
+      // the first two rows of this site's four forward links, for all columns
+      // of the domain; the barrier after the first staging of r or psi makes
+      // them visible to the cluster
+      const float2* gl = reinterpret_cast<const float2*>(links + (size_t)s * 36);
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const float2 v0 = __ldg(gl + mu * 9 + 2 * q), v1 = __ldg(gl + mu * 9 + 2 * q + 1);
+          uS[(mu * 3 + q) * NS + tid] = make_float4(v0.x, v0.y, v1.x, v1.y);
+        }
+    }
     const size_t off = spinor_offset(s, L, rhs);
     Spinor<float> r0;
     if (!psi_zero) {
@@ -438,8 +473,8 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
       cluster.sync();
       float4* t = cur; cur = nxt; nxt = t;
       Spinor<float> acc, pv;
-      domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, true>(g, smem_addr(cur), uA, tid, rank, sb, lc, c, s, L, rhs,
-                                                       links, psi, acc);
+      domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, true>(g, cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, c, s, L,
+                                                       rhs, links, psi, acc);
       load_spinor(eta + off, r0);
       planes_to_spinor(cur, NS, tid, pv);
 #pragma unroll
@@ -462,8 +497,8 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
       Spinor<float> q, rv;
       const bool need_q = (mode == 0) || !last;
       if (need_q)
-        domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, false>(g, smem_addr(cur), uA, tid, rank, sb, lc, c, s, L, rhs,
-                                                          links, psi, q);
+        domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, false>(g, cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, c, s,
+                                                          L, rhs, links, psi, q);
       planes_to_spinor(cur, NS, tid, rv);
       if (need_q) {
 #pragma unroll
@@ -553,14 +588,7 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
     if (SH::CS > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     attr = true;
   }
-  // columns per cluster: all of them when there are enough domains to fill
-  // the GPU, fewer on small lattices
-  const int ndc = g.nd / 2;
-  int rchunk = L;
-  while (rchunk > 1 && (long long)ndc * ((L + rchunk - 1) / rchunk) * SH::CS < 4 * 152) rchunk = (rchunk + 1) / 2;
-  const int nchunks = (L + rchunk - 1) / rchunk;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(SH::CS * ndc * nchunks));
   cfg.blockDim = dim3(SH::NS);
   cfg.dynamicSmemBytes = shm;
   cfg.stream = ex.stream;
@@ -571,8 +599,22 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
   attrs[0].val.clusterDim.z = 1;
   cfg.attrs = attrs;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, g, colour, links, eta, psi, L, rchunk, (float)kappa, psi_zero ? 1 : 0, nmr, mode,
-                     table);
+  // one persistent cluster per cluster slot of the GPU (clusters must fit
+  // in one GPC, so fewer than SMs / CS may be resident at once)
+  static int max_clusters = 0;
+  if (max_clusters == 0) {
+    cfg.gridDim = dim3((unsigned)SH::CS);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 1;
+    }
+    max_clusters = n;
+  }
+  const long long nitems = (long long)(g.nd / 2) * L;
+  const int nclu = (int)std::min<long long>(max_clusters, nitems);
+  cfg.gridDim = dim3((unsigned)(SH::CS * nclu));
+  cudaLaunchKernelEx(&cfg, kern, g, colour, links, eta, psi, L, (float)kappa, psi_zero ? 1 : 0, nmr, mode, table);
   ++*ex.launches;
   return true;
 }
