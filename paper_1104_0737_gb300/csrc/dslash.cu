@@ -625,9 +625,10 @@ bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>*
                      cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table) {
   if (mode == 1 || !g.su3) return false;  // the kernel rebuilds the third link row
   const int* bk = g.blk;
-  // 8^4: eight CTAs of 4 x 4 x 4 x 8 sites; 4^4: one CTA
+  // 8^4: eight CTAs of 8 x 4 x 4 x 4 sites (x, the unit-stride direction, is
+  // not split, so its hops never leave the CTA); 4^4: one CTA
   if (bk[0] == 8 && bk[1] == 8 && bk[2] == 8 && bk[3] == 8)
-    return launch_sweep<8, 8, 8, 8, 2, 2, 2, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
+    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
   if (bk[0] == 4 && bk[1] == 4 && bk[2] == 4 && bk[3] == 4)
     return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
   return false;
