@@ -22,7 +22,9 @@ constexpr int NT = 256;  // threads of the row kernels and the gram kernel
 // register block of the gram kernel: BB x BB entries per thread
 __host__ __device__ constexpr int reg_block(int L) { return L % 2 == 0 ? 2 : (L % 3 == 0 ? 3 : 1); }
 // sites per shared-memory tile of the gram kernel
-__host__ __device__ constexpr int gram_tile_sites(int L) { return L >= 8 ? 8 : (L >= 4 ? 16 : 32); }
+__host__ __device__ constexpr int gram_tile_sites(int L, int real_bytes) {
+  return L >= 8 ? (real_bytes == 4 ? 16 : 8) : (L >= 4 ? 16 : 32);
+}
 
 // ---------------------------------------------------------------------------
 // Gram kernel
@@ -42,9 +44,9 @@ struct GramShape {
   static constexpr int NBI = L / BB;
   static constexpr int NB = HERM ? NBI * (NBI + 1) / 2 : NBI * NBI;
   static constexpr int LANES = NT / NB > 0 ? NT / NB : 1;
-  static constexpr int TS = gram_tile_sites(L);
+  static constexpr int TS = gram_tile_sites(L, (int)sizeof(R));
   static constexpr int TILE = TS * L * 12;  // complex numbers per tile per array
-  static constexpr int STAGES = sizeof(R) == 4 ? 3 : 2;
+  static constexpr int STAGES = 2;
   static constexpr size_t tile_bytes = sizeof(cx<R>) * (size_t)TILE;
   static constexpr size_t red_g = sizeof(cx<double>) * LANES * L * L;
   static constexpr size_t red_d = sizeof(cx<double>) * 2 * (NT / L) * L;
@@ -132,10 +134,8 @@ __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __
   int j = 0;
   for (; j < my_tiles; ++j) {
     const int st = j % STAGES;
-    if (!mbar_wait_bounded(&bars[st], (uint32_t)((j / STAGES) & 1))) {
-      ok = false;
-      break;
-    }
+    // a wait that gives up is acted on below, by all threads together
+    const bool arrived = mbar_wait_bounded(&bars[st], (uint32_t)((j / STAGES) & 1));
     const long long site0 = (blockIdx.x + (long long)j * gridDim.x) * TS;
     const int ns = (int)min((long long)TS, nsite - site0);
     const cx<R>* sA = stage0 + (size_t)st * 3 * TILE;
@@ -191,7 +191,10 @@ __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __
       dacc1 = mk<R>(0, 0);
       dacc2 = 0;
     }
-    __syncthreads();  // every thread is done with this stage
+    if (__syncthreads_or(!arrived)) {  // every thread is done with this stage
+      ok = false;
+      break;
+    }
     if (tid == 0 && j + STAGES < my_tiles) issue(j + STAGES);
   }
   if (!ok) {

@@ -12,7 +12,10 @@ from gpu_common import make_ctx, rel_site_norm
 pytestmark = pytest.mark.gpu
 
 CASES = [((4, 4, 4, 4), 4), ((6, 2, 4, 10), 12), ((8, 8, 8, 16), 1), ((2, 2, 2, 2), 16),
-         ((4, 6, 2, 10), 3), ((10, 6, 6, 4), 7)]
+         ((4, 6, 2, 10), 3), ((10, 6, 6, 4), 7),
+         # L = 4, 8, 12 on lattices with extents 32 and 2 (every hop of a
+         # site wraps in y, z and t at once on the last one)
+         ((8, 8, 8, 16), 12), ((16, 8, 4, 4), 8), ((32, 2, 2, 4), 12), ((8, 4, 2, 2), 4)]
 
 
 @pytest.mark.parametrize("dims,L", CASES)
@@ -107,3 +110,28 @@ def test_dslash_full_size_32c64_L12(oracle_mod):
         assert rel_site_norm(out, ref) < 1e-6
     finally:
         mb.mbicg_destroy(ctx)
+
+
+def test_dslash_fp32_on_links_that_are_not_su3(oracle_mod):
+    """The FP32 operator uses all nine link entries, so a field that is not
+    SU(3) (links scaled by 1.05) matches the oracle as well as an SU(3) one,
+    for L = 12 and for the first four columns alone."""
+    dims, L = (8, 8, 8, 16), 12
+    psi = synth.gaussian_source(dims, L, seed=52)
+    kappa = 0.13
+    for scale in (1.0, 1.05):
+        U = scale * synth.su3_links(dims, 0.5, 51)
+        ctx = mb.mbicg_create(dims)
+        try:
+            mb.mbicg_load_gauge(ctx, U)
+            ref = oracle_mod.apply_D(dims, U, kappa, psi)
+            out = np.empty_like(psi)
+            mb.mbicg_apply_D(ctx, psi, out, L, kappa, mb.MBICG_FP32)
+            assert rel_site_norm(out, ref) < 1e-6, scale
+            # columns 0..3 alone
+            part = np.ascontiguousarray(psi[..., :4])
+            out4 = np.empty_like(part)
+            mb.mbicg_apply_D(ctx, part, out4, 4, kappa, mb.MBICG_FP32)
+            assert rel_site_norm(out4, np.ascontiguousarray(ref[..., :4])) < 1e-6, scale
+        finally:
+            mb.mbicg_destroy(ctx)
