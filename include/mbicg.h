@@ -114,13 +114,22 @@ int mbicg_create(mbicg_ctx** ctx, const int dims[4], int device, void* cuda_stre
 void mbicg_destroy(mbicg_ctx* ctx);
 
 /* Copies the gauge field U (layout above, 4 V SU(3) matrices, complex128)
- * into the library's own FP64 and FP32 copies.  Sec. 2.1: the links of
- * Eq. (hoppingterm).  MBICG_ENAN if U holds NaN or Inf. */
+ * into the library's own FP64, FP32 and FP16 copies (the FP16 copy keeps the
+ * first two rows of each link).  Sec. 2.1: the links of Eq. (hoppingterm).
+ * Every link is checked for unitarity and det = 1 (to 1e-10); a field that is
+ * not SU(3) is accepted, but the kernels that rebuild a link's third row from
+ * its first two (the fused SAP sweep, FP16 storage) are then not used.
+ * MBICG_ENAN if U holds NaN or Inf. */
 int mbicg_load_gauge(mbicg_ctx* ctx, const double* U);
 
 /* out = A in for L columns (Eq. (hoppingterm), (bloclhoppingterm) of
  * Sec. 2.1): (A phi)_x = phi_x - kappa eta_x.  prec: MBICG_FP64 computes in
  * FP64, MBICG_FP32 rounds `in` to FP32, computes in FP32 and widens the result.
+ * MBICG_FP16 stores `in`, the result and the links in FP16 and computes in
+ * FP32: each (site, column) spinor is kept as 12 complex FP16 numbers times
+ * one FP32 scale (its largest |re| or |im|), each link as its first two rows
+ * (the third is rebuilt), and the result is rounded into the same format
+ * before it is widened; it needs SU(3) links (MBICG_EINVAL otherwise).
  * 1 <= L <= 16.  in and out must not alias. */
 int mbicg_apply_D(mbicg_ctx* ctx, const double* in, double* out, int L, double kappa,
                   int prec);

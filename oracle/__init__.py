@@ -183,3 +183,37 @@ def block_bicgstab(dims, U, kappa: float, B, tol: float, max_iter: int = 1000, X
         raise ValueError(f"oracle_block_bicgstab returned {rc}")
     k = iters.value
     return dict(X=X, iters=k, status=rc, history=hist[:min(k, hl)].copy(), true_res=tres)
+
+
+# ---------------------------------------------------------------------------
+# FP16 storage format (numpy; no arithmetic of the method, only rounding)
+# ---------------------------------------------------------------------------
+def quantize_fp16(psi) -> np.ndarray:
+    """The block that FP16 storage with one scale per (site, rhs) represents.
+
+    For every site and column the scale is the largest |re| or |im| of the
+    spinor (12 complex numbers), rounded to FP32; each real component divided
+    by it (in FP64) is rounded to nearest FP16; the value represented is the
+    FP16 number times the scale, exactly.  A zero spinor stays zero.
+    psi: (V, 4, 3, L) complex128."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    V, L = psi.shape[0], psi.shape[-1]
+    parts = np.stack([psi.real, psi.imag], axis=-1).reshape(V, 12, L, 2)
+    m = np.abs(parts).max(axis=(1, 3))                      # (V, L)
+    s = m.astype(np.float32).astype(np.float64)
+    safe = np.where(s > 0, s, 1.0)
+    q = (parts / safe[:, None, :, None]).astype(np.float16).astype(np.float64)
+    out = q * s[:, None, :, None]
+    return (out[..., 0] + 1j * out[..., 1]).reshape(psi.shape)
+
+
+def quantize_links_fp16(U) -> np.ndarray:
+    """Links as FP16 storage of their first two rows represents them: rows 0
+    and 1 rounded component-wise to FP16 (no scale: |U_ab| <= 1), row 2 rebuilt
+    as the complex conjugate of the cross product of rows 0 and 1 (the
+    relation that holds for SU(3)).  U: (V, 4, 3, 3) complex128."""
+    U = np.asarray(U, dtype=np.complex128)
+    r = U[..., :2, :]
+    rq = r.real.astype(np.float16).astype(np.float64) + 1j * r.imag.astype(np.float16).astype(np.float64)
+    row2 = np.conj(np.cross(rq[..., 0, :], rq[..., 1, :]))
+    return np.concatenate([rq, row2[..., None, :]], axis=-2)

@@ -39,6 +39,7 @@ struct mbicg_ctx {
   long long V = 0;
   cx<double>* U64 = nullptr;
   cx<float>* U32 = nullptr;
+  __half2* U16 = nullptr;  // first two rows of each link in FP16, [site][mu][6]
   bool gauge = false;
   bool su3 = false;  // every link SU(3): the fused SAP kernel may rebuild third rows
   std::string err;
@@ -652,6 +653,7 @@ void mbicg_destroy(mbicg_ctx* c) {
   for (auto& kv : c->bufs) cudaFree(kv.second.first);
   if (c->U64) cudaFree(c->U64);
   if (c->U32) cudaFree(c->U32);
+  if (c->U16) cudaFree(c->U16);
   c->prof.release();
   if (c->h_small) cudaFreeHost(c->h_small);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -667,6 +669,7 @@ int mbicg_load_gauge(mbicg_ctx* c, const double* U) {
   const size_t n = (size_t)c->V * 36;  // complex numbers
   if (!c->U64) CK(cudaMalloc(&c->U64, sizeof(cx<double>) * n));
   if (!c->U32) CK(cudaMalloc(&c->U32, sizeof(cx<float>) * n));
+  if (!c->U16) CK(cudaMalloc(&c->U16, sizeof(__half2) * (size_t)c->V * 24));
   Staged s;
   int rc = stage_in(c, U, sizeof(cx<double>) * n, "gauge_stage", true, &s);
   if (rc) return rc;
@@ -677,6 +680,7 @@ int mbicg_load_gauge(mbicg_ctx* c, const double* U) {
   {
     Timed t(ex, KC_CONVERT);
     convert_links(ex, c->V, static_cast<const cx<double>*>(s.dev), c->U64, c->U32, flag);
+    links_to_half(ex, c->V, static_cast<const cx<double>*>(s.dev), c->U16);
   }
   if ((rc = check_launch(c, "load_gauge"))) return rc;
   int bad = 0;
@@ -699,8 +703,11 @@ int mbicg_apply_D(mbicg_ctx* c, const double* in, double* out, int L, double kap
   c->err.clear();
   if (!in || !out || in == out) return fail(c, MBICG_EINVAL, "in/out NULL or aliased");
   if (L < 1 || L > MAXL) return fail(c, MBICG_EINVAL, "L must be in [1, 16]");
-  if (prec != MBICG_FP64 && prec != MBICG_FP32) return fail(c, MBICG_EINVAL, "prec must be FP64 or FP32");
+  if (prec != MBICG_FP64 && prec != MBICG_FP32 && prec != MBICG_FP16)
+    return fail(c, MBICG_EINVAL, "prec must be FP64, FP32 or FP16");
   if (!c->gauge) return fail(c, MBICG_ENOGAUGE, "no gauge field loaded");
+  if (prec == MBICG_FP16 && !c->su3)
+    return fail(c, MBICG_EINVAL, "FP16 storage keeps two link rows and needs SU(3) links");
   CK(cudaSetDevice(c->device));
   c->launches = 0;
   const size_t nl = (size_t)c->V * 12 * L;
@@ -723,6 +730,24 @@ int mbicg_apply_D(mbicg_ctx* c, const double* in, double* out, int L, double kap
     }
     Timed t(ex, KC_CONVERT);
     internal_to_abi<double>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
+  } else if (prec == MBICG_FP16) {
+    // FP16 blocks (48 bytes per spinor) and their scales, carved from FP32-sized buffers
+    cx<float>*a, *b;
+    float *sa, *sb;
+    if ((rc = buf(c, "op16_a", nl / 2, &a)) || (rc = buf(c, "op16_b", nl / 2, &b))) return rc;
+    if ((rc = buf(c, "op16_sa", (size_t)c->V * L, &sa)) || (rc = buf(c, "op16_sb", (size_t)c->V * L, &sb))) return rc;
+    __half2* qa = reinterpret_cast<__half2*>(a);
+    __half2* qb = reinterpret_cast<__half2*>(b);
+    {
+      Timed t(ex, KC_CONVERT);
+      abi_to_half(ex, c->V, L, static_cast<const cx<double>*>(si.dev), qa, sa);
+    }
+    {
+      Timed t(ex, KC_DSLASH);
+      dslash_half(ex, g, c->U16, qa, sa, qb, sb, L, kappa);
+    }
+    Timed t(ex, KC_CONVERT);
+    half_to_abi(ex, c->V, L, qb, sb, static_cast<cx<double>*>(so.dev));
   } else {
     cx<float>*a, *b;
     if ((rc = buf(c, "op32_a", nl, &a)) || (rc = buf(c, "op32_b", nl, &b))) return rc;

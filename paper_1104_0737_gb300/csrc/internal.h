@@ -1,6 +1,7 @@
 // internal.h — declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -83,6 +84,16 @@ struct Timed {
 template <typename R>
 void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out,
                  int L, double kappa);
+
+// FP16 storage (half.cu): spinor blocks q[site][rhs][12] __half2 with one FP32
+// scale per (site, rhs) (the largest |re|, |im| of the spinor; the value is
+// q * s), links as their first two rows [site][mu][6] __half2.
+void abi_to_half(const Exec& ex, long long nsite, int L, const cx<double>* in, __half2* q, float* sc);
+void half_to_abi(const Exec& ex, long long nsite, int L, const __half2* q, const float* sc, cx<double>* out);
+void links_to_half(const Exec& ex, long long nsite, const cx<double>* in, __half2* l16);
+// out = in - kappa * hops with FP16 storage and FP32 arithmetic (SU(3) links)
+void dslash_half(const Exec& ex, const Geom& g, const __half2* l16, const __half2* q, const float* sc, __half2* qo,
+                 float* so, int L, double kappa);
 
 // SAP pieces on the sites of the domains of one colour (the slot numbering of
 // colour_slot_coords; arrays are full-lattice, in the internal layout).

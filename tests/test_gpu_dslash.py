@@ -89,7 +89,7 @@ def test_dslash_errors():
                 mb.mbicg_apply_D(ctx, psi, out, L, 0.1, mb.MBICG_FP64)
             assert e.value.status == mb.MBICG_EINVAL
         with pytest.raises(mb.MbicgError) as e:
-            mb.mbicg_apply_D(ctx, psi, out, 2, 0.1, mb.MBICG_FP16)
+            mb.mbicg_apply_D(ctx, psi, out, 2, 0.1, 7)  # no such precision
         assert e.value.status == mb.MBICG_EINVAL
     finally:
         mb.mbicg_destroy(ctx)
