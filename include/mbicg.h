@@ -210,6 +210,71 @@ const char* mbicg_last_error(const mbicg_ctx* ctx);
 int mbicg_apply_D_noalloc(const int dims[4], const double* U, const double* in, double* out, int L,
                           double kappa, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: a request loop over resident gauge fields (no counterpart in the
+ * paper, whose solver takes one block at a time; the method's block solve of
+ * Sec. 2.1 is what packs the requests' columns together).
+ *
+ * Each field added to a server gets solver slots — a context with its own
+ * CUDA stream, device buffers and host thread — as many as max_slots and the
+ * HBM budget allow (at least one, else MBICG_ENOMEM).  A request is a source
+ * block B of 1..12 columns (ABI layout, host memory, copied at submit) for one
+ * field, kappa and tol.  A free slot of the field takes the oldest waiting
+ * request and packs behind it, in arrival order, the waiting requests with the
+ * same kappa and tol that fit into one block of at most 12 columns; it solves
+ * the packed block with mbicg_block_solve (the field's params) and hands each
+ * request its columns of X and of the true residuals.  Requests arriving while
+ * every slot is busy wait for the next block; the slots of different fields,
+ * and the slots of one field, solve concurrently.  Thread-safe: submit and
+ * wait may be called from any host threads.
+ * ------------------------------------------------------------------------ */
+typedef struct mbicg_server mbicg_server;
+
+typedef struct {
+  double queue_ms;    /* submit -> start of its block solve */
+  double latency_ms;  /* submit -> result ready */
+  double start_ms, done_ms;  /* steady-clock times of the block solve */
+  int batch_columns;  /* columns of the block it was solved in */
+} mbicg_request_info;
+
+/* A server on `device` that gives its solver slots at most hbm_budget_gb
+ * gigabytes (1e9 bytes) of device memory, by the estimate
+ * V (48 + 96 + 48) 12 * 12 + 1152 V bytes per slot. */
+int mbicg_server_create(mbicg_server** server, int device, double hbm_budget_gb);
+
+/* Makes the gauge field U (dims, layout of mbicg_load_gauge) resident with up
+ * to max_slots solver slots solving with the parameters *p; *field_id names
+ * it in submit. */
+int mbicg_server_add_field(mbicg_server* server, const int dims[4], const double* U,
+                           const mbicg_params* p, int max_slots, int* field_id);
+
+/* Queues the solve of A X = B (L columns, 1 <= L <= 12, host memory, copied)
+ * on field field_id; *request_id names it in wait.  MBICG_EINVAL for an
+ * unknown field, L outside 1..12 or tol <= 0. */
+int mbicg_server_submit(mbicg_server* server, int field_id, const double* B, int L,
+                        double kappa, double tol, long long* request_id);
+
+/* Blocks until the request is solved, then copies its columns of X (host,
+ * caller owned, the request's L columns), the iterations of its block solve,
+ * its true residuals (L doubles) and its timings (each may be NULL), forgets
+ * the request and returns the status of its block solve. */
+int mbicg_server_wait(mbicg_server* server, long long request_id, double* X, int* iters,
+                      double* true_res, mbicg_request_info* info);
+
+/* hold != 0: no slot starts a new block solve (solves already running
+ * finish) and submitted requests wait; hold == 0 releases them, and the slots
+ * form their blocks from everything waiting.  For admission control and for
+ * tests that need a known packing. */
+int mbicg_server_hold(mbicg_server* server, int hold);
+
+/* Block solves run, columns solved, the widest block, solver slots. */
+int mbicg_server_stats(mbicg_server* server, long long* solves, long long* columns,
+                       long long* max_columns, int* slots);
+
+/* Stops the slots (after their current solves) and frees everything; every
+ * submitted request should have been waited for. */
+void mbicg_server_destroy(mbicg_server* server);
+
 #ifdef __cplusplus
 }
 #endif

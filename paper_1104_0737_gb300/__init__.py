@@ -24,6 +24,8 @@ __all__ = [
     "mbicg_default_params", "mbicg_create", "mbicg_destroy", "mbicg_load_gauge",
     "mbicg_apply_D", "mbicg_sap_precond", "mbicg_block_solve", "mbicg_get_stats",
     "mbicg_last_error", "mbicg_set_profiling", "mbicg_get_profile", "mbicg_apply_D_noalloc",
+    "mbicg_request_info", "mbicg_server_create", "mbicg_server_add_field", "mbicg_server_submit",
+    "mbicg_server_wait", "mbicg_server_hold", "mbicg_server_stats", "mbicg_server_destroy",
 ]
 
 MBICG_OK, MBICG_EINVAL, MBICG_ENOMEM, MBICG_ENOGAUGE = 0, -1, -2, -3
@@ -57,6 +59,12 @@ class mbicg_stats(ctypes.Structure):
         ("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("restarts", ctypes.c_int),
         ("kernel_launches", ctypes.c_longlong), ("true_res_max", ctypes.c_double),
     ]
+
+
+class mbicg_request_info(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double),
+                ("batch_columns", ctypes.c_int)]
 
 
 _lib = None
@@ -94,6 +102,15 @@ def load_library(build_if_missing: bool = True):
     lib.mbicg_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.mbicg_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     lib.mbicg_apply_D_noalloc.argtypes = [ip, vp, vp, vp, ctypes.c_int, ctypes.c_double, vp]
+    llp = ctypes.POINTER(ctypes.c_longlong)
+    lib.mbicg_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double]
+    lib.mbicg_server_add_field.argtypes = [vp, ip, vp, ctypes.POINTER(mbicg_params), ctypes.c_int, ip]
+    lib.mbicg_server_submit.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, llp]
+    lib.mbicg_server_wait.argtypes = [vp, ctypes.c_longlong, vp, ip, dp, ctypes.POINTER(mbicg_request_info)]
+    lib.mbicg_server_stats.argtypes = [vp, llp, llp, llp, ip]
+    lib.mbicg_server_hold.argtypes = [vp, ctypes.c_int]
+    lib.mbicg_server_destroy.argtypes = [vp]
+    lib.mbicg_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -220,3 +237,75 @@ def mbicg_apply_D_noalloc(dims, U, inp, out, L: int, kappa: float, stream=None) 
     if st != MBICG_OK:
         raise MbicgError(st, "mbicg_apply_D_noalloc failed (sizes beyond the scratch, host "
                              "pointers or a CUDA error)")
+
+
+def _host(a, name: str):
+    import numpy as np
+
+    if not isinstance(a, np.ndarray) or a.dtype != np.complex128 or not a.flags.c_contiguous:
+        raise TypeError(f"{name}: need a C-contiguous complex128 numpy array (host memory)")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def mbicg_server_create(device: int = 0, hbm_budget_gb: float = 100.0):
+    """A request server on `device` whose solver slots may take hbm_budget_gb
+    gigabytes of device memory."""
+    srv = ctypes.c_void_p()
+    st = load_library().mbicg_server_create(ctypes.byref(srv), int(device), float(hbm_budget_gb))
+    if st != MBICG_OK:
+        raise MbicgError(st, "mbicg_server_create failed")
+    return srv
+
+
+def mbicg_server_add_field(server, dims, U, params: mbicg_params, max_slots: int = 1) -> int:
+    """Makes the gauge field U (host numpy) resident with up to max_slots
+    solver slots; returns its field id."""
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    fid = ctypes.c_int(-1)
+    st = load_library().mbicg_server_add_field(server, d, _host(U, "U"), ctypes.byref(params),
+                                               int(max_slots), ctypes.byref(fid))
+    if st != MBICG_OK:
+        raise MbicgError(st, "mbicg_server_add_field failed (HBM budget, bad dims or a CUDA error)")
+    return fid.value
+
+
+def mbicg_server_submit(server, field: int, B, L: int, kappa: float, tol: float) -> int:
+    """Queues A X = B (host numpy, L columns, copied now); returns the request id."""
+    rid = ctypes.c_longlong(0)
+    st = load_library().mbicg_server_submit(server, int(field), _host(B, "B"), int(L), float(kappa),
+                                            float(tol), ctypes.byref(rid))
+    if st != MBICG_OK:
+        raise MbicgError(st, "mbicg_server_submit: unknown field, L outside 1..12 or tol <= 0")
+    return rid.value
+
+
+def mbicg_server_wait(server, request_id: int, X, L: int):
+    """Blocks until the request is solved; fills X (host numpy, its L columns).
+    Returns (status, iters, true_res list, info dict)."""
+    it = ctypes.c_int(0)
+    tres = (ctypes.c_double * max(1, int(L)))()
+    info = mbicg_request_info()
+    st = load_library().mbicg_server_wait(server, int(request_id), _host(X, "X"), ctypes.byref(it), tres,
+                                          ctypes.byref(info))
+    if st not in (MBICG_OK, MBICG_ENOTCONV, MBICG_EBREAKDOWN):
+        raise MbicgError(st, "mbicg_server_wait: unknown request or a failed block solve")
+    return st, it.value, [tres[i] for i in range(int(L))], {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def mbicg_server_hold(server, hold: bool) -> None:
+    """While held, no slot starts a new block solve; releasing lets the slots
+    pack everything that waits."""
+    st = load_library().mbicg_server_hold(server, int(bool(hold)))
+    if st != MBICG_OK:
+        raise MbicgError(st, "mbicg_server_hold failed")
+
+
+def mbicg_server_stats(server) -> dict:
+    a, b, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    n = ctypes.c_int()
+    load_library().mbicg_server_stats(server, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(n))
+    return {"solves": a.value, "columns": b.value, "max_columns": c.value, "slots": n.value}
+
+
+def mbicg_server_destroy(server) -> None:
+    load_library().mbicg_server_destroy(server)

@@ -584,6 +584,8 @@ int run_solve(mbicg_ctx* c, const cx<double>* dB, cx<double>* dX, int L, double 
 // ---------------------------------------------------------------------------
 // ABI
 // ---------------------------------------------------------------------------
+cudaStream_t mbicg::ctx_stream(const mbicg_ctx* c) { return c->stream; }
+
 extern "C" {
 
 void mbicg_default_params(mbicg_params* p) {

@@ -278,11 +278,9 @@ template <typename R, int L, bool HERM>
 int launch_gram_t(const Exec& ex, long long nsite, const cx<R>* A, const cx<R>* B1, const cx<R>* B2, int flags,
                   double* part, int* err) {
   using SH = GramShape<R, L, HERM>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_gram<R, L, HERM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::smem);
-    attr_set = true;
-  }
+  static const cudaError_t attr_set =  // once per process, thread-safely
+      cudaFuncSetAttribute(k_gram<R, L, HERM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::smem);
+  (void)attr_set;
   const long long ntiles = (nsite + SH::TS - 1) / SH::TS;
   const int grid = (int)(ntiles < GRAM_CTAS ? ntiles : GRAM_CTAS);
   k_gram<R, L, HERM><<<grid, NT, SH::smem, ex.stream>>>(nsite, A, B1, B2, flags, part, err);

@@ -576,18 +576,29 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
   cluster.sync();
 }
 
+// sets the sweep kernel's shared-memory and cluster attributes and returns
+// how many of its clusters the GPU holds at once
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
+int sweep_setup(cudaLaunchConfig_t cfg) {
+  using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
+  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::smem_bytes());
+  if (SH::CS > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cfg.gridDim = dim3((unsigned)SH::CS);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return n;
+}
+
 template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
 bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
                   cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   const size_t shm = SH::smem_bytes();
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    if (SH::CS > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    attr = true;
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(SH::NS);
   cfg.dynamicSmemBytes = shm;
@@ -600,17 +611,9 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
   cfg.attrs = attrs;
   cfg.numAttrs = 1;
   // one persistent cluster per cluster slot of the GPU (clusters must fit
-  // in one GPC, so fewer than SMs / CS may be resident at once)
-  static int max_clusters = 0;
-  if (max_clusters == 0) {
-    cfg.gridDim = dim3((unsigned)SH::CS);
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
-      cudaGetLastError();
-      n = 1;
-    }
-    max_clusters = n;
-  }
+  // in one GPC, so fewer than SMs / CS may be resident at once); set up once
+  // per process, thread-safely (contexts may run on several host threads)
+  static const int max_clusters = sweep_setup<DX, DY, DZ, DT, CX, CY, CZ, CT>(cfg);
   const long long nitems = (long long)(g.nd / 2) * L;
   const int nclu = (int)std::min<long long>(max_clusters, nitems);
   cfg.gridDim = dim3((unsigned)(SH::CS * nclu));

@@ -8,6 +8,8 @@
 
 #include "common.cuh"
 
+struct mbicg_ctx;  // the C ABI's opaque context (api.cu)
+
 namespace mbicg {
 
 // Optional per-kernel timing: an event pair around every launch, collected
@@ -84,6 +86,9 @@ struct Timed {
 template <typename R>
 void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out,
                  int L, double kappa);
+
+// the CUDA stream a context orders its work on (api.cu)
+cudaStream_t ctx_stream(const ::mbicg_ctx* c);
 
 // FP16 storage (half.cu): spinor blocks q[site][rhs][12] __half2 with one FP32
 // scale per (site, rhs) (the largest |re|, |im| of the spinor; the value is

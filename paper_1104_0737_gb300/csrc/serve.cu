@@ -1,0 +1,379 @@
+// serve.cu — a request loop over resident gauge fields.
+//
+// Requests are source blocks of 1..12 columns for one of several resident
+// gauge fields and a hopping parameter.  Each field has a fixed set of solver
+// slots, as many as the HBM budget admits (at least one); a slot is a solver
+// context with its own CUDA stream, device buffers and host thread.  A free
+// slot takes the oldest waiting request of its field and packs behind it, in
+// arrival order, the waiting requests with the same kappa and tolerance that
+// still fit into one block of at most 12 columns; the packed block is solved
+// by the modified block BiCGSTAB (Algorithm 2 of Sec. 2.1 — the method
+// solves the L columns of a block together) and the columns are handed back
+// to their requests.  Requests that arrive while the slots are busy wait and
+// join the next block their slot forms: slots of different fields, and
+// several slots of one field, run their solves concurrently on the device.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/mbicg.h"
+#include "internal.h"
+
+using namespace mbicg;
+
+namespace {
+
+constexpr int SERVE_MAXL = 12;
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// columns [o, o + Lj) of the packed block (L columns) <-> a request's block
+// (Lj columns); both in the ABI layout [site][spin*colour][column]
+__global__ void k_pack_columns(long long nrow, int L, int o, int Lj, const cx<double>* __restrict__ in,
+                               cx<double>* __restrict__ out, int to_packed) {
+  const long long n = nrow * Lj;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long row = i / Lj;
+    const int j = (int)(i - row * Lj);
+    if (to_packed)
+      out[row * L + o + j] = in[i];
+    else
+      out[i] = in[row * L + o + j];
+  }
+}
+
+struct Request {
+  long long id = 0;
+  int field = 0, L = 0;
+  double kappa = 0, tol = 0;
+  std::vector<double> B, X;  // ABI layout, interleaved complex
+  std::vector<double> tres;
+  int status = 1, iters = 0, batch_cols = 0;
+  double t_submit = 0, t_start = 0, t_done = 0;
+  bool done = false;
+};
+
+struct Slot {
+  int field = 0;
+  mbicg_ctx* ctx = nullptr;
+  cx<double>* dB = nullptr;  // packed block
+  cx<double>* dX = nullptr;
+  cx<double>* dS = nullptr;  // one request's columns
+  std::thread th;
+};
+
+struct Field {
+  int dims[4] = {0, 0, 0, 0};
+  long long V = 0;
+  mbicg_params params{};
+  int nslots = 0;
+};
+
+}  // namespace
+
+struct mbicg_server {
+  int device = 0;
+  double budget = 0, used = 0;  // bytes
+  std::vector<Field> fields;
+  std::vector<Slot*> slots;
+  std::deque<Request*> pending;
+  std::map<long long, Request*> requests;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  bool hold = false;  // while set, no slot starts a new block solve
+  long long next_id = 1;
+  long long solves = 0, columns = 0, max_cols = 0;
+};
+
+namespace {
+
+// Device bytes one slot of a field holds: the solver's blocks (B, X, W in
+// FP64; R, P, R~, U, V, S, Z in FP32; SAP workspace) at 12 columns, the
+// packing buffers (three FP64 blocks) and the link copies.
+double slot_bytes(long long V) {
+  const double f64 = 16.0 * 12 * SERVE_MAXL * V, f32 = 8.0 * 12 * SERVE_MAXL * V;
+  return 3 * f64 + 10 * f32 + 3 * f64 + V * (576.0 + 288 + 96 + 192);
+}
+
+// takes the oldest waiting request of `field` and the compatible ones behind it
+std::vector<Request*> take_batch(mbicg_server* s, int field) {
+  std::vector<Request*> batch;
+  int cols = 0;
+  for (auto it = s->pending.begin(); it != s->pending.end();) {
+    Request* r = *it;
+    const bool fits = r->field == field && cols + r->L <= SERVE_MAXL &&
+                      (batch.empty() || (r->kappa == batch[0]->kappa && r->tol == batch[0]->tol));
+    if (fits) {
+      batch.push_back(r);
+      cols += r->L;
+      it = s->pending.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return batch;
+}
+
+void run_batch(mbicg_server* s, Slot* sl, std::vector<Request*>& batch) {
+  const Field& f = s->fields[sl->field];
+  const long long nrow = f.V * 12;
+  int L = 0;
+  for (Request* r : batch) L += r->L;
+  const double t0 = now_ms();
+  for (Request* r : batch) r->t_start = t0;
+  cudaStream_t st = nullptr;
+  int status = MBICG_OK, iters = 0;
+  double tres[MAXL] = {0};
+  cudaSetDevice(s->device);
+  {
+    // the stream of the slot's context is its own non-blocking stream
+    st = ctx_stream(sl->ctx);
+    int o = 0;
+    for (Request* r : batch) {
+      if (cudaMemcpyAsync(sl->dS, r->B.data(), sizeof(cx<double>) * nrow * r->L, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
+        status = MBICG_ECUDA;
+      k_pack_columns<<<1024, 256, 0, st>>>(nrow, L, o, r->L, sl->dS, sl->dB, 1);
+      o += r->L;
+    }
+    if (status == MBICG_OK && cudaGetLastError() != cudaSuccess) status = MBICG_ECUDA;
+  }
+  if (status == MBICG_OK)
+    status = mbicg_block_solve(sl->ctx, reinterpret_cast<const double*>(sl->dB), reinterpret_cast<double*>(sl->dX),
+                               L, batch[0]->kappa, batch[0]->tol, &f.params, &iters, tres);
+  const bool have_x = status == MBICG_OK || status == MBICG_ENOTCONV || status == MBICG_EBREAKDOWN;
+  int o = 0;
+  for (Request* r : batch) {
+    r->X.assign(2 * (size_t)nrow * r->L, 0.0);
+    r->tres.assign(r->L, 0.0);
+    if (have_x) {
+      k_pack_columns<<<1024, 256, 0, st>>>(nrow, L, o, r->L, sl->dX, sl->dS, 0);
+      if (cudaMemcpyAsync(r->X.data(), sl->dS, sizeof(cx<double>) * nrow * r->L, cudaMemcpyDeviceToHost, st) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        status = MBICG_ECUDA;
+      for (int j = 0; j < r->L; ++j) r->tres[j] = tres[o + j];
+    }
+    o += r->L;
+  }
+  const double t1 = now_ms();
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (Request* r : batch) {
+    r->status = status;
+    r->iters = iters;
+    r->batch_cols = L;
+    r->t_done = t1;
+    r->done = true;
+  }
+  ++s->solves;
+  s->columns += L;
+  s->max_cols = std::max<long long>(s->max_cols, L);
+  s->cv_done.notify_all();
+}
+
+void worker(mbicg_server* s, Slot* sl) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    std::vector<Request*> batch;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait(lk, [&] {
+        if (s->stop) return true;
+        if (s->hold) return false;
+        for (Request* r : s->pending)
+          if (r->field == sl->field) return true;
+        return false;
+      });
+      if (s->stop) return;
+      batch = take_batch(s, sl->field);
+    }
+    if (!batch.empty()) run_batch(s, sl, batch);
+  }
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice;
+}
+
+void free_slot(Slot* sl) {
+  if (sl->dB) cudaFree(sl->dB);
+  if (sl->dX) cudaFree(sl->dX);
+  if (sl->dS) cudaFree(sl->dS);
+  if (sl->ctx) mbicg_destroy(sl->ctx);
+  delete sl;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mbicg_server_create(mbicg_server** out, int device, double hbm_budget_gb) {
+  if (!out || !(hbm_budget_gb > 0)) return MBICG_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return MBICG_ECUDA;
+  }
+  mbicg_server* s = new mbicg_server();
+  s->device = device;
+  s->budget = hbm_budget_gb * 1e9;
+  *out = s;
+  return MBICG_OK;
+}
+
+int mbicg_server_add_field(mbicg_server* s, const int dims[4], const double* U, const mbicg_params* p, int max_slots,
+                           int* field_id) {
+  if (!s || !dims || !U || !p || !field_id || max_slots < 1) return MBICG_EINVAL;
+  Field f;
+  f.V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    f.dims[mu] = dims[mu];
+    f.V *= dims[mu];
+  }
+  f.params = *p;
+  const double need = slot_bytes(f.V);
+  std::vector<Slot*> made;
+  int rc = MBICG_OK;
+  cudaSetDevice(s->device);
+  for (int k = 0; k < max_slots; ++k) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->used + need > s->budget) break;  // admission by HBM footprint
+    }
+    Slot* sl = new Slot();
+    sl->field = (int)s->fields.size();
+    if ((rc = mbicg_create(&sl->ctx, dims, s->device, nullptr)) != MBICG_OK ||
+        (rc = mbicg_load_gauge(sl->ctx, U)) != MBICG_OK) {
+      free_slot(sl);
+      break;
+    }
+    const size_t blk = sizeof(cx<double>) * (size_t)f.V * 12 * SERVE_MAXL;
+    if (cudaMalloc(&sl->dB, blk) != cudaSuccess || cudaMalloc(&sl->dX, blk) != cudaSuccess ||
+        cudaMalloc(&sl->dS, blk) != cudaSuccess) {
+      cudaGetLastError();
+      free_slot(sl);
+      rc = MBICG_ENOMEM;
+      break;
+    }
+    made.push_back(sl);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->used += need;
+  }
+  if (made.empty()) return rc != MBICG_OK ? rc : MBICG_ENOMEM;
+  std::lock_guard<std::mutex> lk(s->mu);
+  f.nslots = (int)made.size();
+  s->fields.push_back(f);
+  *field_id = (int)s->fields.size() - 1;
+  for (Slot* sl : made) {
+    s->slots.push_back(sl);
+    sl->th = std::thread(worker, s, sl);
+  }
+  return MBICG_OK;
+}
+
+int mbicg_server_submit(mbicg_server* s, int field, const double* B, int L, double kappa, double tol,
+                        long long* request_id) {
+  if (!s || !B || !request_id || L < 1 || L > SERVE_MAXL || !(tol > 0)) return MBICG_EINVAL;
+  if (on_device(B)) return MBICG_EINVAL;  // B is read on the host
+  Request* r = new Request();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (field < 0 || field >= (int)s->fields.size()) {
+      delete r;
+      return MBICG_EINVAL;
+    }
+    r->B.assign(B, B + 2 * (size_t)s->fields[field].V * 12 * L);
+  }
+  r->field = field;
+  r->L = L;
+  r->kappa = kappa;
+  r->tol = tol;
+  r->t_submit = now_ms();
+  std::lock_guard<std::mutex> lk(s->mu);
+  r->id = s->next_id++;
+  s->requests[r->id] = r;
+  s->pending.push_back(r);
+  *request_id = r->id;
+  s->cv_work.notify_all();
+  return MBICG_OK;
+}
+
+int mbicg_server_wait(mbicg_server* s, long long request_id, double* X, int* iters, double* true_res,
+                      mbicg_request_info* info) {
+  if (!s || (X && on_device(X))) return MBICG_EINVAL;
+  Request* r = nullptr;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->requests.find(request_id);
+    if (it == s->requests.end()) return MBICG_EINVAL;
+    r = it->second;
+    s->cv_done.wait(lk, [&] { return r->done; });
+    s->requests.erase(it);
+  }
+  if (X) std::copy(r->X.begin(), r->X.end(), X);
+  if (iters) *iters = r->iters;
+  if (true_res) std::copy(r->tres.begin(), r->tres.end(), true_res);
+  if (info) {
+    info->queue_ms = r->t_start - r->t_submit;
+    info->latency_ms = r->t_done - r->t_submit;
+    info->start_ms = r->t_start;
+    info->done_ms = r->t_done;
+    info->batch_columns = r->batch_cols;
+  }
+  const int st = r->status;
+  delete r;
+  return st;
+}
+
+int mbicg_server_hold(mbicg_server* s, int hold) {
+  if (!s) return MBICG_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->hold = hold != 0;
+  }
+  s->cv_work.notify_all();
+  return MBICG_OK;
+}
+
+int mbicg_server_stats(mbicg_server* s, long long* solves, long long* columns, long long* max_columns,
+                       int* slots) {
+  if (!s) return MBICG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (solves) *solves = s->solves;
+  if (columns) *columns = s->columns;
+  if (max_columns) *max_columns = s->max_cols;
+  if (slots) *slots = (int)s->slots.size();
+  return MBICG_OK;
+}
+
+void mbicg_server_destroy(mbicg_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (Slot* sl : s->slots)
+    if (sl->th.joinable()) sl->th.join();
+  cudaSetDevice(s->device);
+  for (Slot* sl : s->slots) free_slot(sl);
+  for (auto& kv : s->requests) delete kv.second;
+  delete s;
+}
+
+}  // extern "C"

@@ -37,9 +37,10 @@ def test_ctypes_structs_match_c_layout(tmp_path):
 #include <stdio.h>
 #include "mbicg.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(mbicg_params), offsetof(mbicg_params, delta_ru),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mbicg_params), offsetof(mbicg_params, delta_ru),
          offsetof(mbicg_params, res_history), offsetof(mbicg_params, res_history_len),
-         sizeof(mbicg_stats), offsetof(mbicg_stats, true_res_max));
+         sizeof(mbicg_stats), offsetof(mbicg_stats, true_res_max),
+         sizeof(mbicg_request_info), offsetof(mbicg_request_info, batch_columns));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -48,7 +49,8 @@ int main(void) {
                                           check=True).stdout.split()]
     want = [ctypes.sizeof(mb.mbicg_params), mb.mbicg_params.delta_ru.offset,
             mb.mbicg_params.res_history.offset, mb.mbicg_params.res_history_len.offset,
-            ctypes.sizeof(mb.mbicg_stats), mb.mbicg_stats.true_res_max.offset]
+            ctypes.sizeof(mb.mbicg_stats), mb.mbicg_stats.true_res_max.offset,
+            ctypes.sizeof(mb.mbicg_request_info), mb.mbicg_request_info.batch_columns.offset]
     assert got == want
 
 
@@ -83,3 +85,17 @@ def test_create_without_gpu_reports_cuda_error():
     ctx = ctypes.c_void_p()
     st = lib.mbicg_create(ctypes.byref(ctx), (ctypes.c_int * 4)(4, 4, 4, 4), 0, None)
     assert st == mb.MBICG_ECUDA and not ctx.value
+
+
+def test_server_rejects_bad_arguments_without_a_device():
+    lib = mb.load_library()
+    srv = ctypes.c_void_p()
+    assert lib.mbicg_server_create(None, 0, 10.0) == mb.MBICG_EINVAL
+    assert lib.mbicg_server_create(ctypes.byref(srv), 0, 0.0) == mb.MBICG_EINVAL
+    assert lib.mbicg_server_submit(None, 0, None, 1, 0.1, 1e-8, None) == mb.MBICG_EINVAL
+    assert lib.mbicg_server_wait(None, 1, None, None, None, None) == mb.MBICG_EINVAL
+    assert lib.mbicg_server_stats(None, None, None, None, None) == mb.MBICG_EINVAL
+    lib.mbicg_server_destroy(None)
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        assert lib.mbicg_server_create(ctypes.byref(srv), 0, 10.0) == mb.MBICG_ECUDA

@@ -1,0 +1,124 @@
+"""The request server (include/mbicg.h, serving): columns of several requests
+packed into one block solve give the same solutions as each request solved
+alone, within the solver's tolerance; slots of one field and of different
+fields solve concurrently; compatible requests only are packed."""
+import threading
+
+import numpy as np
+import pytest
+
+import paper_1104_0737_gb300 as mb
+import synth
+from gpu_common import rel_col_norm
+
+pytestmark = pytest.mark.gpu
+
+F1, F2 = (8, 8, 8, 16), (8, 8, 8, 8)
+KAPPA, TOL = 0.125, 1e-10
+
+
+def params():
+    return mb.mbicg_default_params(block=(4, 4, 4, 4), ncycle=4, nmr=4, max_iter=2000)
+
+
+def solve(srv, field, B, L, kappa=KAPPA):
+    rid = mb.mbicg_server_submit(srv, field, B, L, kappa, TOL)
+    X = np.empty_like(B)
+    st, it, tres, info = mb.mbicg_server_wait(srv, rid, X, L)
+    return st, X, tres, info
+
+
+def test_packed_columns_equal_solo_solves():
+    srv = mb.mbicg_server_create(0, 60.0)
+    try:
+        f1 = mb.mbicg_server_add_field(srv, F1, synth.su3_links(F1, 0.5, 901), params(), 1)
+        f2 = mb.mbicg_server_add_field(srv, F2, synth.su3_links(F2, 0.5, 902), params(), 1)
+        B0 = synth.gaussian_source(F1, 3, seed=910)
+        B1 = synth.gaussian_source(F1, 4, seed=911)
+        B2 = synth.gaussian_source(F1, 5, seed=912)
+        B3 = synth.gaussian_source(F2, 6, seed=913)
+        # alone: one block of its own 3 columns
+        st, X0, tres0, info0 = solve(srv, f1, B0, 3)
+        assert st == mb.MBICG_OK and info0["batch_columns"] == 3 and max(tres0) <= TOL
+        # in the mix: held, then released together; field 1's three requests
+        # (3 + 4 + 5 columns, same kappa) form one block of 12, field 2 runs beside it
+        mb.mbicg_server_hold(srv, True)
+        ids = [(mb.mbicg_server_submit(srv, f1, B0, 3, KAPPA, TOL), B0, 3),
+               (mb.mbicg_server_submit(srv, f1, B1, 4, KAPPA, TOL), B1, 4),
+               (mb.mbicg_server_submit(srv, f1, B2, 5, KAPPA, TOL), B2, 5),
+               (mb.mbicg_server_submit(srv, f2, B3, 6, KAPPA, TOL), B3, 6)]
+        mb.mbicg_server_hold(srv, False)
+        res = []
+        for rid, B, L in ids:
+            X = np.empty_like(B)
+            st, it, tres, info = mb.mbicg_server_wait(srv, rid, X, L)
+            assert st == mb.MBICG_OK and max(tres) <= TOL
+            res.append((X, info))
+        assert [r[1]["batch_columns"] for r in res] == [12, 12, 12, 6]
+        # the same solution alone and in the mix: both within tol of A^-1 b,
+        # so they differ by at most cond * tol; 1e-7 is the stated bound
+        assert rel_col_norm(res[0][0], X0) < 1e-7
+        # field 2's solve overlapped field 1's block
+        a, b = res[0][1], res[3][1]
+        assert a["start_ms"] < b["done_ms"] and b["start_ms"] < a["done_ms"]
+        s = mb.mbicg_server_stats(srv)
+        assert s["solves"] == 3 and s["max_columns"] == 12 and s["slots"] == 2
+    finally:
+        mb.mbicg_server_destroy(srv)
+
+
+def test_two_slots_of_one_field_overlap_and_kappas_are_not_mixed():
+    srv = mb.mbicg_server_create(0, 60.0)
+    try:
+        f = mb.mbicg_server_add_field(srv, F1, synth.su3_links(F1, 0.5, 903), params(), 2)
+        B = [synth.gaussian_source(F1, 6, seed=920 + i) for i in range(4)]
+        mb.mbicg_server_hold(srv, True)
+        ids = [mb.mbicg_server_submit(srv, f, B[0], 6, 0.12, TOL), mb.mbicg_server_submit(srv, f, B[1], 6, 0.125, TOL),
+               mb.mbicg_server_submit(srv, f, B[2], 6, 0.12, TOL), mb.mbicg_server_submit(srv, f, B[3], 6, 0.125, TOL)]
+        mb.mbicg_server_hold(srv, False)
+        infos = []
+        for rid, b in zip(ids, B):
+            X = np.empty_like(b)
+            st, it, tres, info = mb.mbicg_server_wait(srv, rid, X, 6)
+            assert st == mb.MBICG_OK and max(tres) <= TOL
+            infos.append(info)
+        # requests 0 and 2 (kappa 0.12) share a block, 1 and 3 (0.125) another
+        assert [i["batch_columns"] for i in infos] == [12, 12, 12, 12]
+        assert infos[0]["start_ms"] == infos[2]["start_ms"] and infos[1]["start_ms"] == infos[3]["start_ms"]
+        assert infos[0]["start_ms"] < infos[1]["done_ms"] and infos[1]["start_ms"] < infos[0]["done_ms"]
+    finally:
+        mb.mbicg_server_destroy(srv)
+
+
+def test_concurrent_submitters_and_bad_requests():
+    srv = mb.mbicg_server_create(0, 60.0)
+    try:
+        f = mb.mbicg_server_add_field(srv, F2, synth.su3_links(F2, 0.5, 904), params(), 2)
+        B = synth.gaussian_source(F2, 2, seed=930)
+        with pytest.raises(mb.MbicgError):
+            mb.mbicg_server_submit(srv, 7, B, 2, KAPPA, TOL)       # unknown field
+        with pytest.raises(mb.MbicgError):
+            mb.mbicg_server_submit(srv, f, synth.gaussian_source(F2, 13, seed=1), 13, KAPPA, TOL)
+        with pytest.raises(mb.MbicgError):
+            mb.mbicg_server_submit(srv, f, B, 2, KAPPA, 0.0)
+        out = {}
+
+        def client(i):
+            b = synth.gaussian_source(F2, 1 + i % 3, seed=940 + i)
+            out[i] = (b, solve(srv, f, b, b.shape[-1]))
+
+        th = [threading.Thread(target=client, args=(i,)) for i in range(8)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        ref_ctx = mb.mbicg_create(F2)
+        mb.mbicg_load_gauge(ref_ctx, synth.su3_links(F2, 0.5, 904))
+        for i, (b, (st, X, tres, info)) in out.items():
+            assert st == mb.MBICG_OK and max(tres) <= TOL
+            Xs = np.empty_like(b)
+            st2, _, tr2 = mb.mbicg_block_solve(ref_ctx, b, Xs, b.shape[-1], KAPPA, TOL, params())
+            assert st2 == mb.MBICG_OK and rel_col_norm(X, Xs) < 1e-7
+        mb.mbicg_destroy(ref_ctx)
+    finally:
+        mb.mbicg_server_destroy(srv)
