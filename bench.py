@@ -164,6 +164,81 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+# serving: a Poisson stream of source blocks on three resident gauge fields
+# ---------------------------------------------------------------------------
+SERVING = dict(fields=[(8, 8, 8, 16), (16, 16, 16, 32), (24, 24, 24, 48)], eps=0.5, gauge_seed=1004,
+               kappas=(0.12, 0.125, 0.128), max_L=12, tol=1e-10, block=(4, 4, 4, 4), ncycle=4, nmr=4,
+               requests=64, rates_per_s=(8.0, 128.0), slots=2, seed=2004)
+
+
+def run_serving(device=0):
+    """Requests of 1..12 Gaussian columns arrive as a Poisson stream on three
+    resident fields with kappa drawn from `kappas`; the library's server packs
+    compatible requests into block solves.  One stream per arrival rate (a
+    light load and one that queues); for each: throughput, p50/p99 of
+    arrival-to-result latency and the mean width of the block solves."""
+    import threading
+
+    import paper_1104_0737_gb300 as mb
+
+    cfg = SERVING
+    rng = np.random.default_rng(cfg["seed"])
+    srv = mb.mbicg_server_create(device, 120.0)
+    phases = []
+    try:
+        params = mb.mbicg_default_params(block=cfg["block"], ncycle=cfg["ncycle"], nmr=cfg["nmr"],
+                                         mr_mode=mb.MBICG_MR_FROZEN, max_iter=5000)
+        fids = [mb.mbicg_server_add_field(srv, d, synth.su3_links(d, cfg["eps"], cfg["gauge_seed"] + i), params,
+                                          cfg["slots"]) for i, d in enumerate(cfg["fields"])]
+        for rate in cfg["rates_per_s"]:
+            reqs = []
+            for i in range(cfg["requests"]):
+                f = int(rng.integers(len(fids)))
+                L = int(rng.integers(1, cfg["max_L"] + 1))
+                kappa = float(cfg["kappas"][int(rng.integers(len(cfg["kappas"])))])
+                reqs.append((f, L, kappa, synth.gaussian_source(cfg["fields"][f], L, seed=int(rng.integers(1 << 30))),
+                             float(rng.exponential(1.0 / rate))))
+            results = [None] * len(reqs)
+
+            def wait(i, rid, B, L):
+                X = np.empty_like(B)
+                results[i] = mb.mbicg_server_wait(srv, rid, X, L)
+
+            s0 = mb.mbicg_server_stats(srv)
+            threads = []
+            t0 = time.perf_counter()
+            for i, (f, L, kappa, B, gap) in enumerate(reqs):
+                time.sleep(gap)
+                rid = mb.mbicg_server_submit(srv, fids[f], B, L, kappa, cfg["tol"])
+                th = threading.Thread(target=wait, args=(i, rid, B, L))
+                th.start()
+                threads.append(th)
+            for th in threads:
+                th.join()
+            wall = time.perf_counter() - t0
+            s1 = mb.mbicg_server_stats(srv)
+            lat = np.array([r[3]["latency_ms"] for r in results])
+            cols = sum(r[1] for r in reqs)
+            solves = s1["solves"] - s0["solves"]
+            phases.append({
+                "rate_per_s": rate, "requests": len(reqs), "rhs": cols,
+                "all_converged": all(r[0] == mb.MBICG_OK and max(r[2]) <= cfg["tol"] for r in results),
+                "rhs_per_s": cols / wall, "wall_s": wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "block_solves": solves, "mean_block_columns": (s1["columns"] - s0["columns"]) / max(solves, 1)})
+        slots = mb.mbicg_server_stats(srv)["slots"]
+    finally:
+        mb.mbicg_server_destroy(srv)
+    return {
+        "workload": (f"Poisson streams of {cfg['requests']} requests of 1-{cfg['max_L']} Gaussian columns on fields "
+                     + ", ".join('x'.join(map(str, d)) for d in cfg["fields"])
+                     + f" (eps {cfg['eps']}), kappa in {list(cfg['kappas'])}, SAP "
+                     + 'x'.join(map(str, cfg["block"])) + f", tol {cfg['tol']}, {slots} solver slots"),
+        "rates": phases,
+    }
+
+
+# ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
 def oracle_sample(cfg, iters_full, n_iter=2):
@@ -243,6 +318,8 @@ def main():
     ap.add_argument("--kappa", type=float, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the Poisson request stream on three resident fields")
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="skip the plain FP64 one-RHS-at-a-time solve timed on the same GPU")
     args = ap.parse_args()
@@ -398,6 +475,11 @@ def main():
                     "sample": "one FP64 L=1 solve (column 0), FP64 operator and SAP"}
 
     mb.mbicg_destroy(ctx)
+    del dB, dX
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        torch.cuda.empty_cache()
+        serving = run_serving(local)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -414,6 +496,8 @@ def main():
         }
         if fp64_arm:
             out["fp64_one_rhs_arm"] = fp64_arm
+        if serving:
+            out["serving"] = serving
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
