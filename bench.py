@@ -297,6 +297,24 @@ def run_reference(args, cfg, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest of `value` over the ranks of the process group (the timed
+    region of the slowest replica), or value itself without one."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, L: int, steps: int, seconds: float) -> float:
+    """RHS solves per second of the whole job: every replica solved L columns
+    per step."""
+    return world * L * steps / seconds
+
+
 def _cfg_public(cfg):
     return {"lattice": "x".join(map(str, cfg["dims"])), "L": cfg["L"], "source": cfg["source"],
             "kappa": cfg["kappa"], "eps": cfg["eps"], "sap_block": "x".join(map(str, cfg["block"])),
@@ -399,11 +417,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in evs]
     prof = mb.mbicg_get_profile(ctx)
     mb.mbicg_set_profiling(ctx, False)
-    if dist:
-        t = torch.tensor([total_ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * L * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, dist, f"cuda:{local}")
+    value = whole_job_rate(world, L, args.steps, total_ms / 1e3)
 
     # roofline of the dominant kernel class (CUDA events around every launch on
     # the library's stream, over the timed region)
@@ -446,12 +461,9 @@ def main():
             solve(hB, hX)
         t1 = time.perf_counter()
         e2e_s = t1 - t0
-        if dist:
-            t = torch.tensor([e2e_s], device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dist, f"cuda:{local}")
         nb = B.nbytes
-        e2e = {"value": world * L * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nb,
+        e2e = {"value": whole_job_rate(world, L, args.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb}
 
     cpu = None

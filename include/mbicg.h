@@ -210,6 +210,16 @@ const char* mbicg_last_error(const mbicg_ctx* ctx);
 int mbicg_apply_D_noalloc(const int dims[4], const double* U, const double* in, double* out, int L,
                           double kappa, void* cuda_stream);
 
+/* Diagnostic (no counterpart in the paper): runs, in one CTA on `device`, the
+ * bounded mbarrier wait that the kernels streaming blocks through shared
+ * memory use, on a barrier that expects `expect_bytes` (a multiple of 16) that
+ * no copy will deliver — or, with expect_bytes = 0, on one that completes by a
+ * plain arrival — polling at most spin_limit times (1 <= spin_limit <= 2^24).
+ * *timed_out = 1 when the wait gave up and the kernel returned with its error
+ * flag set, 0 when it completed.  Nothing is copied, so giving up leaves no
+ * transfer in flight; the device stays usable either way. */
+int mbicg_selftest_bounded_wait(int device, int spin_limit, int expect_bytes, int* timed_out);
+
 /* ------------------------------------------------------------------------
  * Serving: a request loop over resident gauge fields (no counterpart in the
  * paper, whose solver takes one block at a time; the method's block solve of

@@ -26,6 +26,7 @@ __all__ = [
     "mbicg_last_error", "mbicg_set_profiling", "mbicg_get_profile", "mbicg_apply_D_noalloc",
     "mbicg_request_info", "mbicg_server_create", "mbicg_server_add_field", "mbicg_server_submit",
     "mbicg_server_wait", "mbicg_server_hold", "mbicg_server_stats", "mbicg_server_destroy",
+    "mbicg_selftest_bounded_wait",
 ]
 
 MBICG_OK, MBICG_EINVAL, MBICG_ENOMEM, MBICG_ENOGAUGE = 0, -1, -2, -3
@@ -111,6 +112,7 @@ def load_library(build_if_missing: bool = True):
     lib.mbicg_server_hold.argtypes = [vp, ctypes.c_int]
     lib.mbicg_server_destroy.argtypes = [vp]
     lib.mbicg_server_destroy.restype = None
+    lib.mbicg_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip]
     _lib = lib
     return lib
 
@@ -309,3 +311,14 @@ def mbicg_server_stats(server) -> dict:
 
 def mbicg_server_destroy(server) -> None:
     load_library().mbicg_server_destroy(server)
+
+
+def mbicg_selftest_bounded_wait(device: int = 0, spin_limit: int = 1 << 12, expect_bytes: int = 16) -> bool:
+    """Runs the kernels' bounded mbarrier wait on a barrier whose bytes never
+    arrive (expect_bytes > 0) or that completes (0); True when it gave up."""
+    out = ctypes.c_int(-1)
+    st = load_library().mbicg_selftest_bounded_wait(int(device), int(spin_limit), int(expect_bytes),
+                                                    ctypes.byref(out))
+    if st != MBICG_OK:
+        raise MbicgError(st, "mbicg_selftest_bounded_wait failed")
+    return bool(out.value)
