@@ -102,6 +102,26 @@ def sap_sweep_flops(V, L, nmr, frozen=True):
     return (V // 2) * L * (ops * 1368 + mr)
 
 
+# DRAM bytes per launch of the dominant kernel at the benchmark workload, from one
+# ncu capture (profiles/dram_traffic_wilson_32c64_L12.md), valid only for the
+# kernel source it was taken on (a hash of csrc/dslash.cu, first 16 hex digits)
+NCU_TRAFFIC = {("sap_sweep", "wilson_32c64_L12"): {"bytes": 4.887e9, "dslash_cu_sha256": "8cc5bdf7d1d0da4c"}}
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """The recorded DRAM traffic of the kernel per launch, or None when none was
+    recorded or the kernel's source has changed since."""
+    import hashlib
+
+    rec = NCU_TRAFFIC.get((kernel, workload))
+    if rec is None:
+        return None
+    src = os.path.join(ROOT, "paper_1104_0737_gb300", "csrc", "dslash.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    return rec["bytes"] if sha == rec["dslash_cu_sha256"] else None
+
+
 def fp32_alu_peak_tflops(sm_mhz, sms=152, lanes=128):
     """FP32 FMA throughput from the unit counts: SMs x FP32 lanes x 2 flops x clock."""
     return sms * lanes * 2 * sm_mhz * 1e6 / 1e12
@@ -437,13 +457,13 @@ def main():
     tfs = nflops / (avg_ms * 1e-3) / 1e12
     if bound == "alu":
         roofline = {"kernel": dom, "bound": "alu", "achieved": tfs, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": tfs / alu_peak, "traffic": None,
+                    "frac": tfs / alu_peak, "traffic": ncu_traffic(dom, args.workload),
                     "peak_kind": f"FP32 FMA units x clock: 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz (sampled)",
                     "algorithmic_flops_per_launch": nflops, "algorithmic_bytes_per_launch": nbytes,
                     "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak, "avg_launch_ms": avg_ms}
     else:
         roofline = {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                    "frac": gbs / hbm_peak, "traffic": ncu_traffic(dom, args.workload), "peak_kind": peak_kind,
                     "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": avg_ms}
     dsl_ms = prof["dslash"][0] / prof["dslash"][1] if prof["dslash"][1] else None
     dslash_frac = (dslash_bytes(V, L) / (dsl_ms * 1e-3) / 1e9) / hbm_peak if dsl_ms else None
