@@ -345,8 +345,13 @@ __device__ __forceinline__ void domain_hops(const Geom& g, const float4* vL, uin
         const bool cross = sn_sub < 0 || sn_sub >= sub;
         const int nb = cross ? tid + (fwd ? -(sub - 1) * sub_stride : (sub - 1) * sub_stride)
                              : tid + (fwd ? sub_stride : -sub_stride);
-        if (pick4(mu, CX, CY, CZ, SH::CS / (CX * CY * CZ)) == 1) {
-          // the domain is not split in this direction: plain shared loads
+        // A warp covers one (z, t) position of the sub-block (SX * SY >= 32),
+        // so in z and t the choice between this CTA and the next is the same
+        // for the whole warp: branch, and read this CTA's planes directly.
+        // In y it differs inside a warp: one cluster-window load path for all.
+        constexpr bool warp_uniform_zt = SH::SX * SH::SY >= 32;
+        if (pick4(mu, CX, CY, CZ, SH::CS / (CX * CY * CZ)) == 1 || (mu >= 2 && warp_uniform_zt && !cross)) {
+          // the neighbour is in this CTA: plain shared loads
           planes_to_spinor(reinterpret_cast<const float4*>(vL), NS, nb, pn);
           planes_to_link12(uL, NS, mu, fwd ? tid : nb, u);
         } else {
