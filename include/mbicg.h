@@ -96,6 +96,9 @@ typedef struct {
   int restarts;           /* restarts after a breakdown */
   long long kernel_launches; /* kernels the library launched during the last call */
   double true_res_max;    /* max_i |b_i - A x_i| / |b_i| at return (FP64) */
+  int graph_iterations;   /* iterations replayed from one captured CUDA graph (the
+                             loop's launches once the frozen step lengths are
+                             recorded; off with MBICG_GRAPHS=0 or while profiling) */
 } mbicg_stats;
 
 /* Fills p with the defaults: ncycle 4, nmr 4, block {4,4,4,4},

@@ -377,6 +377,109 @@ struct Solver {
     return check_launch(c, "qr");
   }
 
+  // One iteration's launches, Algorithm 2 lines 4.1-4.13 and the column
+  // norms, with no host synchronisation (so that it can be captured).
+  int iteration_launches() {
+    int rc;
+    // 4.1 QR of P
+    if ((rc = qr())) return rc;
+    // 4.2 U = M P, 4.3 V = A U
+    if ((rc = apply_M(k.P, k.U))) return rc;
+    if ((rc = dslash(k.U, k.V))) return rc;
+    // 4.4 (R~^H V) alpha = R~^H R
+    {
+      int np;
+      {
+        Timed t(ex, KC_GRAM);
+        np = block_gram<T>(ex, V, L, k.Rt, k.V, k.R, GRAM_G1 | GRAM_G2, gpart, sm.status);
+      }
+      Timed t(ex, KC_SMALL);
+      lxl_alpha(ex, L, gpart, np, sm);
+    }
+    // 4.5 R -= V alpha (4.6, X += U alpha, is folded into the update after zeta)
+    {
+      Timed t(ex, KC_AXPY);
+      block_update_alpha<T>(ex, V, L, k.V, sm.alpha, k.R);
+    }
+    // 4.7 S = M R, 4.8 Z = A S
+    if ((rc = apply_M(k.R, k.S))) return rc;
+    if ((rc = dslash(k.S, k.Z))) return rc;
+    // 4.9 zeta = Tr(Z^H R)/Tr(Z^H Z), 4.12 (R~^H V) beta = -R~^H Z
+    {
+      int np;
+      {
+        Timed t(ex, KC_GRAM);
+        np = block_gram<T>(ex, V, L, k.Rt, k.Z, k.R, GRAM_G1 | GRAM_D1 | GRAM_D2, gpart, sm.status);
+      }
+      Timed t(ex, KC_SMALL);
+      lxl_zeta_beta(ex, L, gpart, np, sm);
+    }
+    // 4.6 + 4.10 X += U alpha + zeta S, 4.11 R -= zeta Z, 4.13 P = R + (P - zeta V) beta
+    {
+      int np;
+      {
+        Timed t(ex, KC_AXPY);
+        np = block_update_zeta<T>(ex, V, L, k.U, sm.alpha, k.S, k.Z, k.V, sm.zb, k.R, k.P, X64, npart);
+      }
+      Timed t(ex, KC_SMALL);
+      lxl_norms(ex, L, npart, np, false, sm);
+    }
+    return check_launch(c, "iteration");
+  }
+
+  // The iteration as a CUDA graph: captured once per solve on the context's
+  // stream (once the frozen step lengths are recorded, so that its launches no
+  // longer change), then replayed with one launch.  Eager when profiling, when
+  // MBICG_GRAPHS=0, or if capture fails.
+  cudaGraphExec_t gexec = nullptr;
+  long long graph_kernels = 0;
+  bool graph_failed = false;
+  int launch_iteration() {
+    const char* env = getenv("MBICG_GRAPHS");
+    const bool enabled = !(env && env[0] == '0');
+    const bool stable = p.ncycle == 0 || p.mr_mode != MBICG_MR_FROZEN || table_complete;
+    if (!enabled || c->prof.on || !stable || graph_failed) return iteration_launches();
+    if (!gexec) {
+      const long long before = c->launches;
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        const char* tr = getenv("MBICG_TRACE");
+        if (tr && tr[0] == '1') fprintf(stderr, "mbicg: stream capture could not begin\n");
+        cudaGetLastError();
+        graph_failed = true;
+        return iteration_launches();
+      }
+      const int rc = iteration_launches();
+      cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+      if (rc == MBICG_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&gexec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      graph_kernels = c->launches - before;
+      c->launches = before;
+      if (rc != MBICG_OK || e != cudaSuccess || !gexec) {
+        const char* tr = getenv("MBICG_TRACE");
+        if (tr && tr[0] == '1')
+          fprintf(stderr, "mbicg: iteration graph not used (status %d, %s; %s)\n", rc, cudaGetErrorString(e),
+                  c->err.c_str());
+        cudaGetLastError();
+        c->err.clear();
+        gexec = nullptr;
+        graph_failed = true;
+        return iteration_launches();
+      }
+    }
+    CK(cudaGraphLaunch(gexec, c->stream));
+    c->launches += graph_kernels;
+    ++c->stats.graph_iterations;
+    return MBICG_OK;
+  }
+
+  ~Solver() {
+    if (gexec) {
+      cudaStreamSynchronize(c->stream);  // no replay of it still pending
+      cudaGraphExecDestroy(gexec);
+    }
+  }
+
   int run(const cx<double>* dB, cx<double>* dX, double tol, int* iters_out, double* true_res) {
     int rc;
     nl = (size_t)V * 12 * L;
@@ -415,50 +518,7 @@ struct Solver {
         if (relmax <= tol) break;
       }
       if (it >= p.max_iter) { status = MBICG_ENOTCONV; break; }
-      // 4.1 QR of P
-      if ((rc = qr())) return rc;
-      // 4.2 U = M P, 4.3 V = A U
-      if ((rc = apply_M(k.P, k.U))) return rc;
-      if ((rc = dslash(k.U, k.V))) return rc;
-      // 4.4 (R~^H V) alpha = R~^H R
-      {
-        int np;
-        {
-          Timed t(ex, KC_GRAM);
-          np = block_gram<T>(ex, V, L, k.Rt, k.V, k.R, GRAM_G1 | GRAM_G2, gpart, sm.status);
-        }
-        Timed t(ex, KC_SMALL);
-        lxl_alpha(ex, L, gpart, np, sm);
-      }
-      // 4.5 R -= V alpha (4.6, X += U alpha, is folded into the update after zeta)
-      {
-        Timed t(ex, KC_AXPY);
-        block_update_alpha<T>(ex, V, L, k.V, sm.alpha, k.R);
-      }
-      // 4.7 S = M R, 4.8 Z = A S
-      if ((rc = apply_M(k.R, k.S))) return rc;
-      if ((rc = dslash(k.S, k.Z))) return rc;
-      // 4.9 zeta = Tr(Z^H R)/Tr(Z^H Z), 4.12 (R~^H V) beta = -R~^H Z
-      {
-        int np;
-        {
-          Timed t(ex, KC_GRAM);
-          np = block_gram<T>(ex, V, L, k.Rt, k.Z, k.R, GRAM_G1 | GRAM_D1 | GRAM_D2, gpart, sm.status);
-        }
-        Timed t(ex, KC_SMALL);
-        lxl_zeta_beta(ex, L, gpart, np, sm);
-      }
-      // 4.6 + 4.10 X += U alpha + zeta S, 4.11 R -= zeta Z, 4.13 P = R + (P - zeta V) beta
-      {
-        int np;
-        {
-          Timed t(ex, KC_AXPY);
-          np = block_update_zeta<T>(ex, V, L, k.U, sm.alpha, k.S, k.Z, k.V, sm.zb, k.R, k.P, X64, npart);
-        }
-        Timed t(ex, KC_SMALL);
-        lxl_norms(ex, L, npart, np, false, sm);
-      }
-      if ((rc = check_launch(c, "iteration"))) return rc;
+      if ((rc = launch_iteration())) return rc;
       int st = 0;
       if ((rc = read_small(c, sm.norms, L, sm.status, h_norm, &st))) return rc;
       ++it;

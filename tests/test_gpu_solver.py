@@ -169,3 +169,25 @@ def test_profiling_counts_kernels():
         assert mb.mbicg_get_stats(ctx)["kernel_launches"] > 10 * iters
     finally:
         mb.mbicg_destroy(ctx)
+
+
+def test_graph_replay_gives_the_eager_solution(monkeypatch):
+    """Once the frozen step lengths are recorded the loop is replayed from one
+    captured CUDA graph; the kernels and their order are the same, so the
+    solution and the iteration count are bit-identical to eager launches."""
+    dims, L = (8, 8, 8, 16), 4
+    ctx, U = make_ctx(dims, 0.5, seed=81)
+    try:
+        B = synth.gaussian_source(dims, L, seed=82)
+        p = mb.mbicg_default_params(block=(4, 4, 4, 4), max_iter=500)
+        X1, X2 = np.empty_like(B), np.empty_like(B)
+        st1, it1, _ = mb.mbicg_block_solve(ctx, B, X1, L, 0.125, 1e-10, p)
+        g1 = mb.mbicg_get_stats(ctx)["graph_iterations"]
+        monkeypatch.setenv("MBICG_GRAPHS", "0")
+        st2, it2, _ = mb.mbicg_block_solve(ctx, B, X2, L, 0.125, 1e-10, p)
+        g2 = mb.mbicg_get_stats(ctx)["graph_iterations"]
+        assert st1 == st2 == mb.MBICG_OK and it1 == it2
+        assert g1 >= it1 - 2 and g2 == 0
+        assert np.array_equal(X1, X2)
+    finally:
+        mb.mbicg_destroy(ctx)
