@@ -20,7 +20,7 @@ namespace {
 constexpr int NT = 256;  // threads of the row kernels and the gram kernel
 
 // register block of the gram kernel: BB x BB entries per thread
-__host__ __device__ constexpr int reg_block(int L) { return L % 2 == 0 ? 2 : (L % 3 == 0 ? 3 : 1); }
+__host__ __device__ constexpr int reg_block(int L) { return L % 3 == 0 ? 3 : (L % 2 == 0 ? 2 : 1); }
 // sites per shared-memory tile of the gram kernel
 __host__ __device__ constexpr int gram_tile_sites(int L, int real_bytes) {
   return L >= 8 ? (real_bytes == 4 ? 16 : 8) : (L >= 4 ? 16 : 32);
