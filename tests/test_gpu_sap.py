@@ -86,3 +86,24 @@ def test_sap_non_su3_links(oracle_mod, monkeypatch, dims, block):
         assert rel_site_norm(out, ref) < 1e-5
     finally:
         mb.mbicg_destroy(ctx)
+
+
+@pytest.mark.slow
+def test_sap_full_size_32c64_L12(oracle_mod):
+    """The benchmark's lattice, domains and launch configuration of the fused
+    sweep (32^3 x 64, 8^4 domains split over 8-CTA clusters, L = 12, FP32),
+    with per-column MR step lengths (the mode the oracle reproduces without
+    the solver's recorded table), one cycle of two MR steps to keep the oracle
+    within a minute: every site against the oracle."""
+    dims, block, L = (32, 32, 32, 64), (8, 8, 8, 8), 12
+    ctx, U = make_ctx(dims, 0.5, seed=1003)
+    try:
+        eta = synth.gaussian_source(dims, L, seed=2003)
+        ref = oracle_mod.sap(dims, block, U, 0.14775, 1, 2, eta, mr_mode=mb.MBICG_MR_COLUMN)
+        out = np.empty_like(eta)
+        p = mb.mbicg_default_params(ncycle=1, nmr=2, block=block, mr_mode=mb.MBICG_MR_COLUMN,
+                                    prec_sap=mb.MBICG_FP32)
+        mb.mbicg_sap_precond(ctx, eta, out, L, 0.14775, p)
+        assert rel_site_norm(out, ref) < 1e-5
+    finally:
+        mb.mbicg_destroy(ctx)

@@ -191,3 +191,27 @@ def test_graph_replay_gives_the_eager_solution(monkeypatch):
         assert np.array_equal(X1, X2)
     finally:
         mb.mbicg_destroy(ctx)
+
+
+@pytest.mark.slow
+def test_benchmark_solve_true_residual_by_oracle(oracle_mod):
+    """The benchmark's solve (32^3 x 64, L = 12 point sources, kappa 0.14775,
+    SAP 8^4 / 4 cycles / 4 MR with frozen step lengths, mixed precision, tol
+    1e-10): its solution checked by the oracle's own FP64 operator, column by
+    column: |b_i - A x_i| / |b_i| <= 1e-10."""
+    dims, L = (32, 32, 32, 64), 12
+    ctx, U = make_ctx(dims, 0.5, seed=1003)
+    try:
+        B = synth.point_source(dims, L)
+        X = np.empty_like(B)
+        p = mb.mbicg_default_params(ncycle=4, nmr=4, block=(8, 8, 8, 8), mr_mode=mb.MBICG_MR_FROZEN,
+                                    max_iter=2000)
+        st, it, tres = mb.mbicg_block_solve(ctx, B, X, L, 0.14775, 1e-10, p)
+        assert st == mb.MBICG_OK
+        R = B - oracle_mod.apply_D(dims, U, 0.14775, X)
+        rel = np.linalg.norm(R.reshape(-1, L), axis=0) / np.linalg.norm(B.reshape(-1, L), axis=0)
+        assert np.max(rel) <= 1e-10, rel
+        # the library's own FP64 true residuals agree with the oracle's
+        assert np.allclose(rel, tres, rtol=1e-3, atol=1e-14)
+    finally:
+        mb.mbicg_destroy(ctx)
