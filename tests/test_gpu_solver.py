@@ -215,3 +215,28 @@ def test_benchmark_solve_true_residual_by_oracle(oracle_mod):
         assert np.allclose(rel, tres, rtol=1e-3, atol=1e-14)
     finally:
         mb.mbicg_destroy(ctx)
+
+
+def test_degenerate_cases():
+    """kappa = 0 makes A the identity: the solve returns B after a few
+    iterations (each FP32 iteration reduces the residual by ~1e-7, so 1e-10
+    takes at most 3); a converged solution passed back as the initial guess
+    needs no iteration; both report true residuals within tol."""
+    dims, L = (8, 4, 4, 8), 3
+    ctx, U = make_ctx(dims, 0.5, seed=91)
+    try:
+        B = synth.gaussian_source(dims, L, seed=92)
+        X = np.empty_like(B)
+        p = mb.mbicg_default_params(block=(4, 2, 2, 4), max_iter=50)
+        st, it, tres = mb.mbicg_block_solve(ctx, B, X, L, 0.0, 1e-10, p)
+        assert st == mb.MBICG_OK and it <= 3 and max(tres) <= 1e-10
+        assert rel_col_norm(X, B) < 1e-10
+        st, it, tres = mb.mbicg_block_solve(ctx, B, X, L, 0.13, 1e-10, p)
+        assert st == mb.MBICG_OK and it > 0
+        X0 = X.copy()
+        st, it0, tres0 = mb.mbicg_block_solve(ctx, B, X, L, 0.13, 1e-10,
+                                              mb.mbicg_default_params(block=(4, 2, 2, 4), use_x0=1))
+        assert st == mb.MBICG_OK and it0 == 0 and max(tres0) <= 1e-10
+        assert np.array_equal(X, X0)
+    finally:
+        mb.mbicg_destroy(ctx)
