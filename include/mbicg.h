@@ -99,6 +99,9 @@ typedef struct {
   int graph_iterations;   /* iterations replayed from one captured CUDA graph (the
                              loop's launches once the frozen step lengths are
                              recorded; off with MBICG_GRAPHS=0 or while profiling) */
+  int precision_fallbacks; /* 1 when a solve with FP32 Krylov vectors broke down
+                              after its restarts and was continued from its X
+                              with FP64 Krylov vectors */
 } mbicg_stats;
 
 /* Fills p with the defaults: ncycle 4, nmr 4, block {4,4,4,4},

@@ -59,7 +59,7 @@ class mbicg_stats(ctypes.Structure):
     _fields_ = [
         ("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("restarts", ctypes.c_int),
         ("kernel_launches", ctypes.c_longlong), ("true_res_max", ctypes.c_double),
-        ("graph_iterations", ctypes.c_int),
+        ("graph_iterations", ctypes.c_int), ("precision_fallbacks", ctypes.c_int),
     ]
 
 

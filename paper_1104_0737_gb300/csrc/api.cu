@@ -242,6 +242,7 @@ struct Solver {
   double* table = nullptr;
   int* unset = nullptr;
   bool table_complete = false;
+  bool keep_table = false;  // continue with the frozen step lengths already recorded
   SmallWork sm{};
   double *gpart, *npart;
   double h_norm[MAXL + 1];
@@ -278,8 +279,10 @@ struct Solver {
       if ((rc = buf(c, "sap_omega", (size_t)ndc * L * 2, &sw.omega))) return rc;
       if ((rc = buf(c, "sap_table", (size_t)p.ncycle * 2 * p.nmr * ndc * 2, &table))) return rc;
       if ((rc = buf(c, "sap_unset", 1, &unset))) return rc;
-      // every frozen step length starts unrecorded (NaN)
-      CK(cudaMemsetAsync(table, 0xff, sizeof(double) * (size_t)p.ncycle * 2 * p.nmr * ndc * 2, c->stream));
+      // every frozen step length starts unrecorded (NaN), unless this solve
+      // continues another one with the same preconditioner
+      if (!keep_table)
+        CK(cudaMemsetAsync(table, 0xff, sizeof(double) * (size_t)p.ncycle * 2 * p.nmr * ndc * 2, c->stream));
     }
     if ((rc = buf(c, "gpart", (size_t)GRAM_CTAS * gram_slots(L) * 2, &gpart))) return rc;
     if ((rc = buf(c, "npart", (size_t)8 * 152 * L, &npart))) return rc;
@@ -501,6 +504,7 @@ struct Solver {
     double rmax_ru = relmax;
     int it = 0, status = MBICG_OK;
     bool fresh_restart = false;
+    int restarts_here = 0;  // restarts of this run (a continuation has its own)
     bool true_fresh = true;  // R holds B - A X from the FP64 operator
     const char* tr_env = getenv("MBICG_TRACE");
     const bool trace = tr_env && tr_env[0] == '1';
@@ -534,7 +538,8 @@ struct Solver {
       if (st & ST_NAN) { status = MBICG_ENAN; break; }
       if (st) {
         // breakdown: restart from the current X (R = B - A X, P = R, R~ = R)
-        if (fresh_restart || c->stats.restarts >= 3) { status = MBICG_EBREAKDOWN; break; }
+        if (fresh_restart || restarts_here >= 3) { status = MBICG_EBREAKDOWN; break; }
+        ++restarts_here;
         c->stats.restarts++;
         CK(cudaMemsetAsync(sm.status, 0, sizeof(int), c->stream));
         if ((rc = true_residual(rel, &relmax))) return rc;
@@ -626,8 +631,9 @@ int check_params(mbicg_ctx* c, int L, const mbicg_params* p, bool solve) {
 
 template <typename T, typename TS>
 int run_solve(mbicg_ctx* c, const cx<double>* dB, cx<double>* dX, int L, double kappa, double tol,
-              const mbicg_params* p, const double* bnorm, int* iters, double* true_res) {
+              const mbicg_params* p, const double* bnorm, int* iters, double* true_res, bool keep_table = false) {
   Solver<T, TS> s;
+  s.keep_table = keep_table;
   s.c = c;
   s.ex = exec_of(c);
   s.g = lattice_geom(c, p->ncycle > 0 ? p->block : nullptr);
@@ -918,6 +924,24 @@ int mbicg_block_solve(mbicg_ctx* c, const double* B, double* X, int L, double ka
   } else {
     st = sap64 ? run_solve<float, double>(c, dB, dX, L, kappa, tol, p, bnorm, iters, true_res)
                : run_solve<float, float>(c, dB, dX, L, kappa, tol, p, bnorm, iters, true_res);
+    if (st == MBICG_EBREAKDOWN) {
+      // The FP32 Krylov vectors lost the rank of the search block again after
+      // every restart: continue from the current X with FP64 Krylov vectors
+      // (the FP32 preconditioner with its frozen step lengths stays), for the
+      // iterations that remain.
+      const mbicg_stats first = c->stats;
+      mbicg_params q = *p;
+      q.use_x0 = 1;
+      q.max_iter = std::max(1, p->max_iter - first.iters);
+      c->err.clear();
+      int it2 = 0;
+      // the same preconditioner: the frozen MR step lengths recorded so far are kept
+      st = sap64 ? run_solve<double, double>(c, dB, dX, L, kappa, tol, &q, bnorm, &it2, true_res, true)
+                 : run_solve<double, float>(c, dB, dX, L, kappa, tol, &q, bnorm, &it2, true_res, true);
+      c->stats.iters = first.iters + it2;
+      c->stats.precision_fallbacks = 1;
+      if (iters) *iters = first.iters + it2;
+    }
   }
   if (st == MBICG_ECUDA || st == MBICG_ENOMEM || st == MBICG_EINVAL) return st;
   if ((rc = stage_out(c, sx))) return rc;

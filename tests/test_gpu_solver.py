@@ -135,6 +135,9 @@ def test_solver_statuses():
         st, iters, tres = mb.mbicg_block_solve(ctx, B2, X, 2, 0.12, 1e-10,
                                                mb.mbicg_default_params(block=(2, 2, 2, 2)))
         assert st == mb.MBICG_EBREAKDOWN
+        # the FP32 solve gave up after its restarts and was continued with FP64
+        # Krylov vectors, which meet the same rank-deficient block
+        assert mb.mbicg_get_stats(ctx)["precision_fallbacks"] == 1
         Bn = B.copy()
         Bn[5, 1, 2, 0] = np.nan
         with pytest.raises(mb.MbicgError) as e:
