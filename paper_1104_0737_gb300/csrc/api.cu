@@ -363,8 +363,14 @@ struct Solver {
     return MBICG_OK;
   }
 
+  // QR of P by CholeskyQR2; with FP32 Krylov vectors a shifted first pass
+  // (Cholesky of P^H P + s I, s = 1e-5 max_j |p_j|^2) and two plain passes
+  // (shifted CholeskyQR3): the plain Cholesky of an FP32 Gram matrix fails
+  // once cond(P) passes ~1/sqrt(u) ~ 4e3, the shifted pass brings any P of
+  // cond up to ~1/u to a well-conditioned basis of the same space first.
   int qr() {
-    for (int pass = 0; pass < 2; ++pass) {
+    const int npass = sizeof(T) == 4 ? 3 : 2;
+    for (int pass = 0; pass < npass; ++pass) {
       int np;
       {
         Timed t(ex, KC_GRAM);
@@ -372,7 +378,8 @@ struct Solver {
       }
       {
         Timed t(ex, KC_SMALL);
-        lxl_cholesky_inverse(ex, L, gpart, np, sm, sizeof(T) == 4 ? 1e-12 : 1e-26);
+        lxl_cholesky_inverse(ex, L, gpart, np, sm, sizeof(T) == 4 ? 1e-12 : 1e-26,
+                             (sizeof(T) == 4 && pass == 0) ? 1e-5 : 0.0);
       }
       Timed t(ex, KC_AXPY);
       block_transform<T>(ex, V, L, k.P, sm.M, k.P);

@@ -707,13 +707,20 @@ __global__ void k_lxl_zeta_beta(int L, const double* part, int nparts, const dou
 }
 
 // G = gamma^H gamma (gamma upper triangular, real positive diagonal); M = gamma^-1
-__global__ void k_lxl_chol(int L, const double* part, int nparts, double* M, int* status, double rel_eps) {
+__global__ void k_lxl_chol(int L, const double* part, int nparts, double* M, int* status, double rel_eps,
+                           double shift) {
   __shared__ cx<double> sG[MAXL * MAXL], sR[MAXL * MAXL];
   const int nslots = 2 * L * L + 2 * L;
   reduce_slots(part, nparts, nslots, 0, L * L, sG);
   __syncthreads();
   if (threadIdx.x == 0) {
     int st = 0;
+    if (shift > 0) {
+      // shifted factorisation: G + s I with s = shift * max_j G_jj
+      double gmax = 0;
+      for (int j = 0; j < L; ++j) gmax = fmax(gmax, sG[j * L + j].re);
+      for (int j = 0; j < L; ++j) sG[j * L + j].re += shift * gmax;
+    }
     for (int e = 0; e < L * L; ++e) sR[e] = mk(0.0, 0.0);
     for (int j = 0; j < L && !st; ++j) {
       double d = sG[j * L + j].re;
@@ -877,8 +884,9 @@ void lxl_zeta_beta(const Exec& ex, int L, const double* part, int nparts, SmallW
   k_lxl_zeta_beta<<<1, 256, 0, ex.stream>>>(L, part, nparts, w.LU, w.piv, w.zb, w.status);
   ++*ex.launches;
 }
-void lxl_cholesky_inverse(const Exec& ex, int L, const double* part, int nparts, SmallWork& w, double rel_eps) {
-  k_lxl_chol<<<1, 256, 0, ex.stream>>>(L, part, nparts, w.M, w.status, rel_eps);
+void lxl_cholesky_inverse(const Exec& ex, int L, const double* part, int nparts, SmallWork& w, double rel_eps,
+                          double shift) {
+  k_lxl_chol<<<1, 256, 0, ex.stream>>>(L, part, nparts, w.M, w.status, rel_eps, shift);
   ++*ex.launches;
 }
 void lxl_norms(const Exec& ex, int L, const double* part, int nparts, bool from_gram, SmallWork& w) {

@@ -227,9 +227,10 @@ void lxl_alpha(const Exec& ex, int L, const double* part, int nparts, SmallWork&
 // (A = R~, B1 = Z, D = Z, E = R)
 void lxl_zeta_beta(const Exec& ex, int L, const double* part, int nparts, SmallWork& w);
 // Cholesky of G = P^H P = gamma^H gamma, M = gamma^-1 (slot 0 partials)
-// (rel_eps: a pivot below rel_eps * G_jj counts as a failure)
+// (rel_eps: a pivot below rel_eps * G_jj counts as a failure; shift > 0
+// factors G + shift * max_j G_jj * I instead)
 void lxl_cholesky_inverse(const Exec& ex, int L, const double* part, int nparts, SmallWork& w,
-                          double rel_eps);
+                          double rel_eps, double shift = 0.0);
 // norms[i] = sum of partial column norms (part[cta][L], or gram slots when
 // from_gram, using the |D|^2 slots)
 void lxl_norms(const Exec& ex, int L, const double* part, int nparts, bool from_gram, SmallWork& w);
