@@ -105,7 +105,7 @@ def sap_sweep_flops(V, L, nmr, frozen=True):
 # DRAM bytes per launch of the dominant kernel at the benchmark workload, from one
 # ncu capture (profiles/dram_traffic_wilson_32c64_L12.md), valid only for the
 # kernel source it was taken on (a hash of csrc/dslash.cu, first 16 hex digits)
-NCU_TRAFFIC = {("sap_sweep", "wilson_32c64_L12"): {"bytes": 4.887e9, "dslash_cu_sha256": "8cc5bdf7d1d0da4c"}}
+NCU_TRAFFIC = {("sap_sweep", "wilson_32c64_L12"): {"bytes": 4.950e9, "dslash_cu_sha256": "428787d72f9b0766"}}
 
 
 def ncu_traffic(kernel: str, workload: str):
