@@ -122,3 +122,30 @@ def test_concurrent_submitters_and_bad_requests():
         mb.mbicg_destroy(ref_ctx)
     finally:
         mb.mbicg_server_destroy(srv)
+
+
+def test_slots_follow_the_hbm_budget():
+    """A field gets as many solver slots as the budget admits: none (ENOMEM)
+    when one slot does not fit, one when only one fits although three were
+    asked for."""
+    U = synth.su3_links(F2, 0.5, 905)
+    one_slot_gb = 2.0  # 8^3 x 8 at 12 columns: well under 2 GB per slot
+    srv = mb.mbicg_server_create(0, 1e-3)
+    try:
+        with pytest.raises(mb.MbicgError) as e:
+            mb.mbicg_server_add_field(srv, F2, U, params(), 3)
+        assert e.value.status == mb.MBICG_ENOMEM
+    finally:
+        mb.mbicg_server_destroy(srv)
+    V = int(np.prod(F2))
+    per_slot = (3 * 16 + 10 * 8 + 3 * 16) * 12 * 12 * V + V * (576 + 288 + 96 + 192)
+    srv = mb.mbicg_server_create(0, 1.5 * per_slot / 1e9)
+    try:
+        f = mb.mbicg_server_add_field(srv, F2, U, params(), 3)
+        assert mb.mbicg_server_stats(srv)["slots"] == 1
+        B = synth.gaussian_source(F2, 2, seed=950)
+        st, X, tres, info = solve(srv, f, B, 2)
+        assert st == mb.MBICG_OK and max(tres) <= TOL
+    finally:
+        mb.mbicg_server_destroy(srv)
+    assert one_slot_gb > per_slot / 1e9
