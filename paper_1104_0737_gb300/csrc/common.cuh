@@ -71,15 +71,18 @@ struct Spinor {
   cx<R> c[4][3];
 };
 
+// An FP32 spinor is 96 bytes at a multiple of 96 bytes from a 256-byte aligned
+// block, so it is 32-byte aligned: three 256-bit loads (stores) move it, and a
+// warp's load of (site, rhs) spinors uses every 32-byte sector it touches
+// (16-byte loads at a 96-byte stride fetch each sector twice).
 __device__ __forceinline__ void load_spinor(const cx<float>* p, Spinor<float>& s) {
-  const float4* q = reinterpret_cast<const float4*>(p);
+  float* d = &s.c[0][0].re;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const float4 v = __ldg(q + k);
-    cx<float>* d = &s.c[0][0] + 2 * k;
-    d[0] = mk(v.x, v.y);
-    d[1] = mk(v.z, v.w);
-  }
+  for (int k = 0; k < 3; ++k)
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(d[8 * k]), "=f"(d[8 * k + 1]), "=f"(d[8 * k + 2]), "=f"(d[8 * k + 3]), "=f"(d[8 * k + 4]),
+                   "=f"(d[8 * k + 5]), "=f"(d[8 * k + 6]), "=f"(d[8 * k + 7])
+                 : "l"(reinterpret_cast<const float*>(p) + 8 * k));
 }
 __device__ __forceinline__ void load_spinor(const cx<double>* p, Spinor<double>& s) {
   const double2* q = reinterpret_cast<const double2*>(p);
@@ -90,12 +93,13 @@ __device__ __forceinline__ void load_spinor(const cx<double>* p, Spinor<double>&
   }
 }
 __device__ __forceinline__ void store_spinor(cx<float>* p, const Spinor<float>& s) {
-  float4* q = reinterpret_cast<float4*>(p);
+  const float* d = &s.c[0][0].re;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const cx<float>* d = &s.c[0][0] + 2 * k;
-    q[k] = make_float4(d[0].re, d[0].im, d[1].re, d[1].im);
-  }
+  for (int k = 0; k < 3; ++k)
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(reinterpret_cast<float*>(p) + 8 * k),
+                 "f"(d[8 * k]), "f"(d[8 * k + 1]), "f"(d[8 * k + 2]), "f"(d[8 * k + 3]), "f"(d[8 * k + 4]),
+                 "f"(d[8 * k + 5]), "f"(d[8 * k + 6]), "f"(d[8 * k + 7])
+                 : "memory");
 }
 __device__ __forceinline__ void store_spinor(cx<double>* p, const Spinor<double>& s) {
   double2* q = reinterpret_cast<double2*>(p);
