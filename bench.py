@@ -104,8 +104,9 @@ def sap_sweep_flops(V, L, nmr, frozen=True):
 
 # DRAM bytes per launch of the dominant kernel at the benchmark workload, from one
 # ncu capture (profiles/dram_traffic_wilson_32c64_L12.md), valid only for the
-# kernel source it was taken on (a hash of csrc/dslash.cu, first 16 hex digits)
-NCU_TRAFFIC = {("sap_sweep", "wilson_32c64_L12"): {"bytes": 4.950e9, "dslash_cu_sha256": "428787d72f9b0766"}}
+# kernel source it was taken on (a hash of csrc/dslash.cu and csrc/common.cuh,
+# first 16 hex digits)
+NCU_TRAFFIC = {("sap_sweep", "wilson_32c64_L12"): {"bytes": 4.970e9, "source_sha256": "f3e1f38c88f3a05a"}}
 
 
 def ncu_traffic(kernel: str, workload: str):
@@ -116,10 +117,11 @@ def ncu_traffic(kernel: str, workload: str):
     rec = NCU_TRAFFIC.get((kernel, workload))
     if rec is None:
         return None
-    src = os.path.join(ROOT, "paper_1104_0737_gb300", "csrc", "dslash.cu")
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    return rec["bytes"] if sha == rec["dslash_cu_sha256"] else None
+    h = hashlib.sha256()
+    for name in ("dslash.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1104_0737_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return rec["bytes"] if h.hexdigest()[:16] == rec["source_sha256"] else None
 
 
 def fp32_alu_peak_tflops(sm_mhz, sms=152, lanes=128):
