@@ -87,6 +87,14 @@ typedef struct {
    * after iteration k, at most res_history_len entries. */
   double* res_history;
   int res_history_len;
+  /* Dummy right-hand sides (Sec. 2.1: where the single-vector solve fails to
+   * converge the block solve may still converge when extra right-hand sides
+   * play a supplementary role): dummy_rhs extra columns of Gaussian random
+   * numbers (seeded by dummy_seed, a counter-based generator) are appended to
+   * B for the solve; the stopping test, X and the true residuals cover the L
+   * given columns only.  L + dummy_rhs <= 16.  Default 0. */
+  int dummy_rhs;
+  unsigned long long dummy_seed;
 } mbicg_params;
 
 /* Counters of the last call on a context. */

@@ -52,6 +52,7 @@ class mbicg_params(ctypes.Structure):
         ("mr_mode", ctypes.c_int), ("prec_sap", ctypes.c_int), ("prec_D", ctypes.c_int),
         ("max_iter", ctypes.c_int), ("use_x0", ctypes.c_int), ("delta_ru", ctypes.c_double),
         ("res_history", ctypes.POINTER(ctypes.c_double)), ("res_history_len", ctypes.c_int),
+        ("dummy_rhs", ctypes.c_int), ("dummy_seed", ctypes.c_ulonglong),
     ]
 
 

@@ -243,6 +243,7 @@ struct Solver {
   int* unset = nullptr;
   bool table_complete = false;
   bool keep_table = false;  // continue with the frozen step lengths already recorded
+  int Lc = 0;               // columns the stopping test covers (the others are dummies)
   SmallWork sm{};
   double *gpart, *npart;
   double h_norm[MAXL + 1];
@@ -357,6 +358,7 @@ struct Solver {
     if ((rc = read_small(c, sm.norms, L, sm.status, h_norm, &st))) return rc;
     *relmax = 0;
     for (int i = 0; i < L; ++i) {
+      if (i == Lc) break;
       rel[i] = sqrt(h_norm[i]) / bnorm[i];
       if (!(rel[i] <= *relmax)) *relmax = rel[i];
     }
@@ -502,7 +504,7 @@ struct Solver {
     }
     if (!p.use_x0) CK(cudaMemsetAsync(X64, 0, sizeof(cx<double>) * nl, c->stream));
     CK(cudaMemsetAsync(sm.status, 0, sizeof(int), c->stream));
-    double rel[MAXL], relmax;
+    double rel[MAXL] = {0}, relmax;
     // line 2: R = B - A X
     if ((rc = true_residual(rel, &relmax, !p.use_x0))) return rc;
     // lines 3-4: P = R, R~ = R
@@ -536,6 +538,7 @@ struct Solver {
       true_fresh = false;
       relmax = 0;
       for (int i = 0; i < L; ++i) {
+        if (i == Lc) break;
         rel[i] = sqrt(h_norm[i]) / bnorm[i];
         if (!(rel[i] <= relmax)) relmax = rel[i];
       }
@@ -568,7 +571,7 @@ struct Solver {
       }
     }
     // final true residual in FP64 (R is no longer needed)
-    double trel[MAXL], tmax;
+    double trel[MAXL] = {0}, tmax;
     if (true_fresh || !sloppy) {
       if (!true_fresh) {
         if ((rc = true_residual(trel, &tmax))) return rc;
@@ -617,6 +620,8 @@ const cx<double>* Solver<float, double>::links_S() const { return c->U64; }
 int check_params(mbicg_ctx* c, int L, const mbicg_params* p, bool solve) {
   if (L < 1 || L > MAXL) return fail(c, MBICG_EINVAL, "L must be in [1, 16]");
   if (!p) return fail(c, MBICG_EINVAL, "params is NULL");
+  if (solve && (p->dummy_rhs < 0 || L + p->dummy_rhs > MAXL))
+    return fail(c, MBICG_EINVAL, "dummy_rhs must be >= 0 with L + dummy_rhs <= 16");
   if (p->ncycle < 0 || p->ncycle > 64) return fail(c, MBICG_EINVAL, "ncycle out of range");
   if (p->ncycle > 0) {
     if (p->nmr < 1 || p->nmr > 256) return fail(c, MBICG_EINVAL, "nmr must be in [1, 256]");
@@ -638,9 +643,11 @@ int check_params(mbicg_ctx* c, int L, const mbicg_params* p, bool solve) {
 
 template <typename T, typename TS>
 int run_solve(mbicg_ctx* c, const cx<double>* dB, cx<double>* dX, int L, double kappa, double tol,
-              const mbicg_params* p, const double* bnorm, int* iters, double* true_res, bool keep_table = false) {
+              const mbicg_params* p, const double* bnorm, int* iters, double* true_res, bool keep_table = false,
+              int Lc = 0) {
   Solver<T, TS> s;
   s.keep_table = keep_table;
+  s.Lc = Lc > 0 ? Lc : L;
   s.c = c;
   s.ex = exec_of(c);
   s.g = lattice_geom(c, p->ncycle > 0 ? p->block : nullptr);
@@ -923,14 +930,29 @@ int mbicg_block_solve(mbicg_ctx* c, const double* B, double* X, int L, double ka
   }
   const cx<double>* dB = static_cast<const cx<double>*>(sb.dev);
   cx<double>* dX = static_cast<cx<double>*>(sx.dev);
+  // dummy right-hand sides: solve the block widened by seeded Gaussian
+  // columns; the stopping test and the results cover the first L columns
+  const int Lt = L + p->dummy_rhs;
+  double tres_all[MAXL] = {0};
+  if (p->dummy_rhs > 0) {
+    const Exec ex = exec_of(c);
+    const size_t nlt = (size_t)c->V * 12 * Lt;
+    cx<double>*Bt, *Xt;
+    if ((rc = buf(c, "dummy_B", nlt, &Bt)) || (rc = buf(c, "dummy_X", nlt, &Xt))) return rc;
+    pack_dummies(ex, c->V, L, Lt, dB, Bt, p->dummy_seed, true);
+    if (p->use_x0) pack_dummies(ex, c->V, L, Lt, dX, Xt, 0, false);
+    if ((rc = abi_norms(c, Bt, Lt, bnorm, &bad))) return rc;
+    dB = Bt;
+    dX = Xt;
+  }
   const bool sap64 = p->ncycle > 0 && p->prec_sap == MBICG_FP64;
   int st;
   if (p->prec_D == MBICG_FP64) {
-    st = sap64 ? run_solve<double, double>(c, dB, dX, L, kappa, tol, p, bnorm, iters, true_res)
-               : run_solve<double, float>(c, dB, dX, L, kappa, tol, p, bnorm, iters, true_res);
+    st = sap64 ? run_solve<double, double>(c, dB, dX, Lt, kappa, tol, p, bnorm, iters, tres_all, false, L)
+               : run_solve<double, float>(c, dB, dX, Lt, kappa, tol, p, bnorm, iters, tres_all, false, L);
   } else {
-    st = sap64 ? run_solve<float, double>(c, dB, dX, L, kappa, tol, p, bnorm, iters, true_res)
-               : run_solve<float, float>(c, dB, dX, L, kappa, tol, p, bnorm, iters, true_res);
+    st = sap64 ? run_solve<float, double>(c, dB, dX, Lt, kappa, tol, p, bnorm, iters, tres_all, false, L)
+               : run_solve<float, float>(c, dB, dX, Lt, kappa, tol, p, bnorm, iters, tres_all, false, L);
     if (st == MBICG_EBREAKDOWN) {
       // The FP32 Krylov vectors lost the rank of the search block again after
       // every restart: continue from the current X with FP64 Krylov vectors
@@ -943,13 +965,17 @@ int mbicg_block_solve(mbicg_ctx* c, const double* B, double* X, int L, double ka
       c->err.clear();
       int it2 = 0;
       // the same preconditioner: the frozen MR step lengths recorded so far are kept
-      st = sap64 ? run_solve<double, double>(c, dB, dX, L, kappa, tol, &q, bnorm, &it2, true_res, true)
-                 : run_solve<double, float>(c, dB, dX, L, kappa, tol, &q, bnorm, &it2, true_res, true);
+      st = sap64 ? run_solve<double, double>(c, dB, dX, Lt, kappa, tol, &q, bnorm, &it2, tres_all, true, L)
+                 : run_solve<double, float>(c, dB, dX, Lt, kappa, tol, &q, bnorm, &it2, tres_all, true, L);
       c->stats.iters = first.iters + it2;
       c->stats.precision_fallbacks = 1;
       if (iters) *iters = first.iters + it2;
     }
   }
+  if (true_res)
+    for (int i = 0; i < L; ++i) true_res[i] = tres_all[i];
+  if (p->dummy_rhs > 0 && (st == MBICG_OK || st == MBICG_ENOTCONV || st == MBICG_EBREAKDOWN))
+    first_columns(exec_of(c), c->V, Lt, L, dX, static_cast<cx<double>*>(sx.dev));
   if (st == MBICG_ECUDA || st == MBICG_ENOMEM || st == MBICG_EINVAL) return st;
   if ((rc = stage_out(c, sx))) return rc;
   if (!sx.host) {

@@ -426,6 +426,48 @@ __global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __res
   }
 }
 
+// Columns of an ABI block (rows [site][spin*colour], L columns) copied into
+// the first L of Lt columns, the other Lt - L filled with Gaussian random
+// numbers (or zeros): a counter-based generator, splitmix64 of (seed, row,
+// column) giving two uniforms, and the Box-Muller transform.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__global__ void k_pack_dummies(long long nrow, int L, int Lt, const cx<double>* __restrict__ in,
+                               cx<double>* __restrict__ out, unsigned long long seed, int random) {
+  const long long n = nrow * Lt;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long row = i / Lt;
+    const int j = (int)(i - row * Lt);
+    if (j < L) {
+      out[i] = in[row * L + j];
+    } else if (random) {
+      const unsigned long long h1 = splitmix64(seed ^ splitmix64((unsigned long long)i));
+      const unsigned long long h2 = splitmix64(h1);
+      const double u1 = ((double)(h1 >> 11) + 1.0) * 0x1.0p-53;  // (0, 1]
+      const double u2 = (double)(h2 >> 11) * 0x1.0p-53;          // [0, 1)
+      const double rad = sqrt(-2.0 * log(u1));
+      double sn, cs;
+      sincospi(2.0 * u2, &sn, &cs);
+      out[i] = mk(rad * cs, rad * sn);
+    } else {
+      out[i] = mk(0.0, 0.0);
+    }
+  }
+}
+// the first L of Lt columns
+__global__ void k_first_columns(long long nrow, int Lt, int L, const cx<double>* __restrict__ in,
+                                cx<double>* __restrict__ out) {
+  const long long n = nrow * L;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long row = i / L;
+    out[i] = in[row * Lt + (i - row * L)];
+  }
+}
+
 int row_grid(long long nrow) {
   const long long need = (nrow + NT - 1) / NT;
   return (int)(need < 8 * 152 ? need : 8 * 152);
@@ -854,6 +896,15 @@ void internal_to_abi(const Exec& ex, long long nsite, int L, const cx<R>* in, cx
 template <typename RI, typename RO>
 void convert_block(const Exec& ex, long long n, const cx<RI>* in, cx<RO>* out) {
   k_convert<RI, RO><<<row_grid(n), NT, 0, ex.stream>>>(n, in, out);
+  ++*ex.launches;
+}
+void pack_dummies(const Exec& ex, long long nsite, int L, int Lt, const cx<double>* in, cx<double>* out,
+                  unsigned long long seed, bool random) {
+  k_pack_dummies<<<row_grid(nsite * 12 * Lt), NT, 0, ex.stream>>>(nsite * 12, L, Lt, in, out, seed, random ? 1 : 0);
+  ++*ex.launches;
+}
+void first_columns(const Exec& ex, long long nsite, int Lt, int L, const cx<double>* in, cx<double>* out) {
+  k_first_columns<<<row_grid(nsite * 12 * L), NT, 0, ex.stream>>>(nsite * 12, Lt, L, in, out);
   ++*ex.launches;
 }
 void convert_links(const Exec& ex, long long nsite, const cx<double>* in, cx<double>* l64, cx<float>* l32, int* bad) {

@@ -87,6 +87,13 @@ template <typename R>
 void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out,
                  int L, double kappa);
 
+// ABI blocks with dummy columns: the L columns of in into the first L of Lt
+// columns of out, the rest seeded Gaussian random numbers (random) or zeros;
+// and back, the first L of Lt columns.
+void pack_dummies(const Exec& ex, long long nsite, int L, int Lt, const cx<double>* in, cx<double>* out,
+                  unsigned long long seed, bool random);
+void first_columns(const Exec& ex, long long nsite, int Lt, int L, const cx<double>* in, cx<double>* out);
+
 // the CUDA stream a context orders its work on (api.cu)
 cudaStream_t ctx_stream(const ::mbicg_ctx* c);
 

@@ -243,3 +243,33 @@ def test_degenerate_cases():
         assert np.array_equal(X, X0)
     finally:
         mb.mbicg_destroy(ctx)
+
+
+def test_dummy_right_hand_sides(oracle_mod):
+    """Sec. 2.1's dummy right-hand sides: seeded Gaussian columns appended to
+    the block; the given columns converge (checked with the oracle's
+    operator) to the solution of the solve without them, within tol."""
+    dims, L = (8, 8, 8, 16), 3
+    ctx, U = make_ctx(dims, 0.5, seed=95)
+    try:
+        B = synth.gaussian_source(dims, L, seed=96)
+        X0, X1 = np.empty_like(B), np.empty_like(B)
+        p = mb.mbicg_default_params(block=(4, 4, 4, 4), max_iter=500)
+        st0, it0, tr0 = mb.mbicg_block_solve(ctx, B, X0, L, 0.125, 1e-10, p)
+        pd = mb.mbicg_default_params(block=(4, 4, 4, 4), max_iter=500, dummy_rhs=5, dummy_seed=1234)
+        st1, it1, tr1 = mb.mbicg_block_solve(ctx, B, X1, L, 0.125, 1e-10, pd)
+        assert st0 == st1 == mb.MBICG_OK and max(tr1) <= 1e-10
+        R = B - oracle_mod.apply_D(dims, U, 0.125, X1)
+        rel = np.linalg.norm(R.reshape(-1, L), axis=0) / np.linalg.norm(B.reshape(-1, L), axis=0)
+        assert np.max(rel) <= 1e-10 and np.allclose(rel, tr1, rtol=1e-3, atol=1e-14)
+        assert rel_col_norm(X1, X0) < 1e-7
+        # the same seed gives the same dummies, hence the same solve
+        X2 = np.empty_like(B)
+        st2, it2, _ = mb.mbicg_block_solve(ctx, B, X2, L, 0.125, 1e-10, pd)
+        assert it2 == it1 and np.array_equal(X2, X1)
+        with pytest.raises(mb.MbicgError) as e:
+            mb.mbicg_block_solve(ctx, B, X2, L, 0.125, 1e-10,
+                                 mb.mbicg_default_params(block=(4, 4, 4, 4), dummy_rhs=14))
+        assert e.value.status == mb.MBICG_EINVAL
+    finally:
+        mb.mbicg_destroy(ctx)
