@@ -621,79 +621,109 @@ __device__ void reduce_slots(const double* part, int nparts, int nslots, int slo
   }
 }
 
+// The L x L kernels run in one CTA.  The factorisations proceed column by
+// column with the work of a step spread over the threads (rows, matrix
+// entries or right-hand-side columns); every entry is computed by the same
+// expression, with the same operands in the same order, as in a sequential
+// loop, so the result does not depend on the thread count.
+__device__ __forceinline__ cx<double> csub_mul(cx<double> s, cx<double> f, cx<double> a) {  // s - f a
+  return mk(s.re - (f.re * a.re - f.im * a.im), s.im - (f.re * a.im + f.im * a.re));
+}
+
 __global__ void k_lxl_alpha(int L, const double* part, int nparts, double* G, double* LU, int* piv, double* alpha,
                             int* status) {
   __shared__ cx<double> sG[MAXL * MAXL], sC[MAXL * MAXL];
+  __shared__ double smax[256];
+  __shared__ int s_st, s_p;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int nslots = 2 * L * L + 2 * L;
   reduce_slots(part, nparts, nslots, 0, L * L, sG);
   reduce_slots(part, nparts, nslots, L * L, L * L, sC);
   __syncthreads();
-  for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+  double m = 0;
+  for (int e = tid; e < L * L; e += nt) {
     G[2 * e] = sG[e].re;
     G[2 * e + 1] = sG[e].im;
+    m = fmax(m, sqrt(cabs2(sG[e])));
   }
-  if (threadIdx.x == 0) {
+  smax[tid] = m;
+  __syncthreads();
+  if (tid == 0) {
     double gmax = 0;
-    for (int e = 0; e < L * L; ++e) gmax = fmax(gmax, sqrt(cabs2(sG[e])));
-    int st = isfinite(gmax) ? 0 : ST_NAN;
-    // LU with partial pivoting, C overwritten by the solution
-    for (int k = 0; k < L && !st; ++k) {
+    for (int t = 0; t < nt; ++t) gmax = fmax(gmax, smax[t]);  // max: exact in any order
+    smax[0] = gmax;
+    s_st = isfinite(gmax) ? 0 : ST_NAN;
+  }
+  __syncthreads();
+  const double gmax = smax[0];
+  // LU with partial pivoting; C carried along
+  for (int k = 0; k < L; ++k) {
+    if (tid == 0 && !s_st) {
       int p = k;
       double best = cabs2(sG[k * L + k]);
       for (int r = k + 1; r < L; ++r)
         if (cabs2(sG[r * L + k]) > best) { best = cabs2(sG[r * L + k]); p = r; }
-      if (!(sqrt(best) > 1e-300 + 1e-15 * gmax)) { st |= ST_ALPHA_SINGULAR; break; }
+      if (!(sqrt(best) > 1e-300 + 1e-15 * gmax)) s_st |= ST_ALPHA_SINGULAR;
       piv[k] = p;
-      if (p != k) {
-        for (int c = 0; c < L; ++c) {
-          cx<double> t = sG[k * L + c]; sG[k * L + c] = sG[p * L + c]; sG[p * L + c] = t;
-          t = sC[k * L + c]; sC[k * L + c] = sC[p * L + c]; sC[p * L + c] = t;
-        }
+      s_p = p;
+    }
+    __syncthreads();
+    if (s_st) break;
+    const int p = s_p;
+    if (p != k)
+      for (int c = tid; c < L; c += nt) {
+        cx<double> t = sG[k * L + c]; sG[k * L + c] = sG[p * L + c]; sG[p * L + c] = t;
+        t = sC[k * L + c]; sC[k * L + c] = sC[p * L + c]; sC[p * L + c] = t;
       }
-      for (int r = k + 1; r < L; ++r) {
-        const cx<double> f = cdiv(sG[r * L + k], sG[k * L + k]);
-        sG[r * L + k] = f;  // store the multiplier (unit lower factor)
-        for (int c = k + 1; c < L; ++c) {
-          const cx<double> a = sG[k * L + c];
-          sG[r * L + c] = mk(sG[r * L + c].re - (f.re * a.re - f.im * a.im), sG[r * L + c].im - (f.re * a.im + f.im * a.re));
-        }
-        for (int c = 0; c < L; ++c) {
-          const cx<double> a = sC[k * L + c];
-          sC[r * L + c] = mk(sC[r * L + c].re - (f.re * a.re - f.im * a.im), sC[r * L + c].im - (f.re * a.im + f.im * a.re));
-        }
+    __syncthreads();
+    for (int r = k + 1 + tid; r < L; r += nt) sG[r * L + k] = cdiv(sG[r * L + k], sG[k * L + k]);  // multipliers
+    __syncthreads();
+    const int nr = L - 1 - k, ncg = L - 1 - k;
+    for (int w = tid; w < nr * (ncg + L); w += nt) {
+      const int r = k + 1 + w / (ncg + L), q = w % (ncg + L);
+      const cx<double> f = sG[r * L + k];
+      if (q < ncg) {
+        const int c = k + 1 + q;
+        sG[r * L + c] = csub_mul(sG[r * L + c], f, sG[k * L + c]);
+      } else {
+        const int c = q - ncg;
+        sC[r * L + c] = csub_mul(sC[r * L + c], f, sC[k * L + c]);
       }
     }
-    if (!st) {
-      for (int k = L - 1; k >= 0; --k)
-        for (int c = 0; c < L; ++c) {
-          cx<double> s = sC[k * L + c];
-          for (int j = k + 1; j < L; ++j) {
-            const cx<double> a = sG[k * L + j], x = sC[j * L + c];
-            s = mk(s.re - (a.re * x.re - a.im * x.im), s.im - (a.re * x.im + a.im * x.re));
-          }
-          sC[k * L + c] = cdiv(s, sG[k * L + k]);
-        }
-      for (int e = 0; e < L * L; ++e) {
-        LU[2 * e] = sG[e].re;
-        LU[2 * e + 1] = sG[e].im;
-        alpha[2 * e] = sC[e].re;
-        alpha[2 * e + 1] = sC[e].im;
-      }
-    } else {
-      for (int e = 0; e < 2 * L * L; ++e) alpha[e] = 0;
-    }
-    *status |= st;
+    __syncthreads();
   }
+  const int st = s_st;
+  if (!st) {
+    // back substitution, one right-hand-side column per thread
+    for (int c = tid; c < L; c += nt)
+      for (int k = L - 1; k >= 0; --k) {
+        cx<double> s = sC[k * L + c];
+        for (int j = k + 1; j < L; ++j) s = csub_mul(s, sG[k * L + j], sC[j * L + c]);
+        sC[k * L + c] = cdiv(s, sG[k * L + k]);
+      }
+    __syncthreads();
+    for (int e = tid; e < L * L; e += nt) {
+      LU[2 * e] = sG[e].re;
+      LU[2 * e + 1] = sG[e].im;
+      alpha[2 * e] = sC[e].re;
+      alpha[2 * e + 1] = sC[e].im;
+    }
+  } else {
+    for (int e = tid; e < 2 * L * L; e += nt) alpha[e] = 0;
+  }
+  if (tid == 0) *status |= st;
 }
 
 __global__ void k_lxl_zeta_beta(int L, const double* part, int nparts, const double* LU, const int* piv, double* zb,
                                 int* status) {
   __shared__ cx<double> sC[MAXL * MAXL], sD[2 * MAXL];
+  __shared__ int s_st;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int nslots = 2 * L * L + 2 * L;
   reduce_slots(part, nparts, nslots, 0, L * L, sC);
   reduce_slots(part, nparts, nslots, 2 * L * L, 2 * L, sD);
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     int st = *status & ST_ALPHA_SINGULAR;
     cx<double> zr = mk(0.0, 0.0);
     double zz = 0;
@@ -708,101 +738,108 @@ __global__ void k_lxl_zeta_beta(int L, const double* part, int nparts, const dou
     if (!st) zeta = mk(zr.re / zz, zr.im / zz);
     zb[0] = zeta.re;
     zb[1] = zeta.im;
-    if (!st) {
-      // beta = -(R~^H V)^-1 R~^H Z with the LU factors of the alpha solve
-      // P C: the row interchanges of the factorisation, in order, first (the
-      // stored multipliers belong to the final row order)
-      for (int e = 0; e < L * L; ++e) sC[e] = mk(-sC[e].re, -sC[e].im);
+    s_st = st;
+  }
+  __syncthreads();
+  const int st = s_st;
+  if (!st) {
+    // beta = -(R~^H V)^-1 R~^H Z with the LU factors of the alpha solve, one
+    // column per thread: the row interchanges of the factorisation in order
+    // (the stored multipliers belong to the final row order), forward
+    // substitution with the unit lower factor, back substitution
+    for (int c = tid; c < L; c += nt) {
+      for (int r = 0; r < L; ++r) sC[r * L + c] = mk(-sC[r * L + c].re, -sC[r * L + c].im);
       for (int k = 0; k < L; ++k) {
         const int p = piv[k];
-        if (p != k)
-          for (int c = 0; c < L; ++c) { cx<double> t = sC[k * L + c]; sC[k * L + c] = sC[p * L + c]; sC[p * L + c] = t; }
+        if (p != k) { cx<double> t = sC[k * L + c]; sC[k * L + c] = sC[p * L + c]; sC[p * L + c] = t; }
       }
-      // forward substitution with the unit lower factor
-      for (int k = 0; k < L; ++k) {
-        for (int r = k + 1; r < L; ++r) {
-          const cx<double> f = mk(LU[2 * (r * L + k)], LU[2 * (r * L + k) + 1]);
-          for (int c = 0; c < L; ++c) {
-            const cx<double> a = sC[k * L + c];
-            sC[r * L + c] = mk(sC[r * L + c].re - (f.re * a.re - f.im * a.im), sC[r * L + c].im - (f.re * a.im + f.im * a.re));
-          }
-        }
+      for (int k = 0; k < L; ++k)
+        for (int r = k + 1; r < L; ++r)
+          sC[r * L + c] = csub_mul(sC[r * L + c], mk(LU[2 * (r * L + k)], LU[2 * (r * L + k) + 1]), sC[k * L + c]);
+      for (int k = L - 1; k >= 0; --k) {
+        cx<double> s = sC[k * L + c];
+        for (int j = k + 1; j < L; ++j)
+          s = csub_mul(s, mk(LU[2 * (k * L + j)], LU[2 * (k * L + j) + 1]), sC[j * L + c]);
+        sC[k * L + c] = cdiv(s, mk(LU[2 * (k * L + k)], LU[2 * (k * L + k) + 1]));
       }
-      for (int k = L - 1; k >= 0; --k)
-        for (int c = 0; c < L; ++c) {
-          cx<double> s = sC[k * L + c];
-          for (int j = k + 1; j < L; ++j) {
-            const cx<double> a = mk(LU[2 * (k * L + j)], LU[2 * (k * L + j) + 1]), x = sC[j * L + c];
-            s = mk(s.re - (a.re * x.re - a.im * x.im), s.im - (a.re * x.im + a.im * x.re));
-          }
-          sC[k * L + c] = cdiv(s, mk(LU[2 * (k * L + k)], LU[2 * (k * L + k) + 1]));
-        }
-      for (int e = 0; e < L * L; ++e) {
-        zb[2 + 2 * e] = sC[e].re;
-        zb[3 + 2 * e] = sC[e].im;
-      }
-    } else {
-      for (int e = 0; e < 2 * L * L; ++e) zb[2 + e] = 0;
     }
-    *status |= st;
+    __syncthreads();
+    for (int e = tid; e < L * L; e += nt) {
+      zb[2 + 2 * e] = sC[e].re;
+      zb[3 + 2 * e] = sC[e].im;
+    }
+  } else {
+    for (int e = tid; e < 2 * L * L; e += nt) zb[2 + e] = 0;
   }
+  if (tid == 0) *status |= st;
 }
 
 // G = gamma^H gamma (gamma upper triangular, real positive diagonal); M = gamma^-1
 __global__ void k_lxl_chol(int L, const double* part, int nparts, double* M, int* status, double rel_eps,
                            double shift) {
   __shared__ cx<double> sG[MAXL * MAXL], sR[MAXL * MAXL];
+  __shared__ int s_st;
+  __shared__ double s_rjj;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int nslots = 2 * L * L + 2 * L;
   reduce_slots(part, nparts, nslots, 0, L * L, sG);
+  for (int e = tid; e < L * L; e += nt) sR[e] = mk(0.0, 0.0);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int st = 0;
+  if (tid == 0) {
     if (shift > 0) {
       // shifted factorisation: G + s I with s = shift * max_j G_jj
       double gmax = 0;
       for (int j = 0; j < L; ++j) gmax = fmax(gmax, sG[j * L + j].re);
       for (int j = 0; j < L; ++j) sG[j * L + j].re += shift * gmax;
     }
-    for (int e = 0; e < L * L; ++e) sR[e] = mk(0.0, 0.0);
-    for (int j = 0; j < L && !st; ++j) {
+    s_st = 0;
+  }
+  __syncthreads();
+  for (int j = 0; j < L; ++j) {
+    if (tid == 0) {
       double d = sG[j * L + j].re;
       for (int k = 0; k < j; ++k) d -= cabs2(sR[k * L + j]);
-      if (!isfinite(d)) { st |= ST_NAN; break; }
-      if (!(d > rel_eps * sG[j * L + j].re) || !(d > 0)) { st |= ST_CHOL_FAIL; break; }
-      const double rjj = sqrt(d);
-      sR[j * L + j] = mk(rjj, 0.0);
-      for (int i = j + 1; i < L; ++i) {
-        // R_ji = (G_ji - sum_k conj(R_kj) R_ki) / R_jj
-        cx<double> s = sG[j * L + i];
-        for (int k = 0; k < j; ++k) {
-          const cx<double> a = sR[k * L + j], b = sR[k * L + i];
-          s = mk(s.re - (a.re * b.re + a.im * b.im), s.im - (a.re * b.im - a.im * b.re));
-        }
-        sR[j * L + i] = mk(s.re / rjj, s.im / rjj);
+      if (!isfinite(d)) s_st |= ST_NAN;
+      else if (!(d > rel_eps * sG[j * L + j].re) || !(d > 0)) s_st |= ST_CHOL_FAIL;
+      else {
+        s_rjj = sqrt(d);
+        sR[j * L + j] = mk(s_rjj, 0.0);
       }
     }
-    // M = R^-1 (upper triangular), column by column: R M = 1
-    for (int e = 0; e < L * L; ++e) sG[e] = mk(0.0, 0.0);
-    if (!st) {
-      for (int c = 0; c < L; ++c) {
-        for (int i = c; i >= 0; --i) {
-          cx<double> s = mk(i == c ? 1.0 : 0.0, 0.0);
-          for (int k = i + 1; k <= c; ++k) {
-            const cx<double> a = sR[i * L + k], x = sG[k * L + c];
-            s = mk(s.re - (a.re * x.re - a.im * x.im), s.im - (a.re * x.im + a.im * x.re));
-          }
-          sG[i * L + c] = mk(s.re / sR[i * L + i].re, s.im / sR[i * L + i].re);
-        }
+    __syncthreads();
+    if (s_st) break;
+    const double rjj = s_rjj;
+    for (int i = j + 1 + tid; i < L; i += nt) {
+      // R_ji = (G_ji - sum_k conj(R_kj) R_ki) / R_jj
+      cx<double> s = sG[j * L + i];
+      for (int k = 0; k < j; ++k) {
+        const cx<double> a = sR[k * L + j], b = sR[k * L + i];
+        s = mk(s.re - (a.re * b.re + a.im * b.im), s.im - (a.re * b.im - a.im * b.re));
       }
-    } else {
-      for (int i = 0; i < L; ++i) sG[i * L + i] = mk(1.0, 0.0);
+      sR[j * L + i] = mk(s.re / rjj, s.im / rjj);
     }
-    for (int e = 0; e < L * L; ++e) {
-      M[2 * e] = sG[e].re;
-      M[2 * e + 1] = sG[e].im;
-    }
-    *status |= st;
+    __syncthreads();
   }
+  const int st = s_st;
+  // M = R^-1 (upper triangular), one column per thread: R M = 1
+  for (int e = tid; e < L * L; e += nt) sG[e] = mk(0.0, 0.0);
+  __syncthreads();
+  if (!st) {
+    for (int c = tid; c < L; c += nt)
+      for (int i = c; i >= 0; --i) {
+        cx<double> s = mk(i == c ? 1.0 : 0.0, 0.0);
+        for (int k = i + 1; k <= c; ++k) s = csub_mul(s, sR[i * L + k], sG[k * L + c]);
+        sG[i * L + c] = mk(s.re / sR[i * L + i].re, s.im / sR[i * L + i].re);
+      }
+  } else {
+    for (int i = tid; i < L; i += nt) sG[i * L + i] = mk(1.0, 0.0);
+  }
+  __syncthreads();
+  for (int e = tid; e < L * L; e += nt) {
+    M[2 * e] = sG[e].re;
+    M[2 * e + 1] = sG[e].im;
+  }
+  if (tid == 0) *status |= st;
 }
 
 __global__ void k_lxl_norms(int L, const double* part, int nparts, int from_gram, double* norms, int* status) {
