@@ -56,3 +56,25 @@ def test_reference_arm_prints_on_rank_zero_only(capsys):
 
     bench.run_reference(A(), dict(bench.WORKLOADS["wilson_8c16_L12"]), rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_line_keeps_the_contract(capsys, monkeypatch):
+    """The reference arm (the oracle on the host cores) prints one JSON line
+    with the contract's keys; a one-iteration sample of the 8^3 x 16 workload
+    keeps the test short."""
+    import json
+
+    real = bench.oracle_sample
+    monkeypatch.setattr(bench, "oracle_sample", lambda cfg, iters: real(cfg, iters, n_iter=1))
+
+    class A:
+        workload, steps, warmup = "wilson_8c16_L12", 1, 0
+
+    bench.run_reference(A(), dict(bench.WORKLOADS["wilson_8c16_L12"]), rank=0, world=1)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == bench.UNIT
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["config"]["workload"] == "wilson_8c16_L12"
