@@ -114,7 +114,7 @@ typedef struct {
 
 /* Fills p with the defaults: ncycle 4, nmr 4, block {4,4,4,4},
  * MBICG_MR_FROZEN, prec_sap FP32, prec_D FP32, max_iter 1000, use_x0 0,
- * delta_ru 0.1, no history. */
+ * delta_ru 0.1, no history, no dummy right-hand sides. */
 void mbicg_default_params(mbicg_params* p);
 
 /* Creates a context for a lattice of extents dims on CUDA device `device`.
@@ -162,7 +162,17 @@ int mbicg_sap_precond(mbicg_ctx* ctx, const double* in, double* out, int L, doub
  *              EBREAKDOWN); the initial guess on entry if p->use_x0.
  *   iters      if not NULL: iterations done.
  *   true_res   if not NULL: L host doubles, |b_i - A x_i| / |b_i| in FP64.
- * 1 <= L <= 16; tol > 0. */
+ * 1 <= L <= 16 (L + p->dummy_rhs <= 16); tol > 0.
+ * The QR of P is CholeskyQR2 (FP64 Krylov vectors) or shifted CholeskyQR3
+ * (FP32 Krylov vectors).  A breakdown (rank-deficient P, singular R~^H V,
+ * Tr(Z^H Z) = 0) restarts from the current X (at most three times, not twice
+ * in a row); with FP32 Krylov vectors a solve that still breaks down continues
+ * from its X with FP64 Krylov vectors (mbicg_stats.precision_fallbacks).  Once
+ * the frozen step lengths are recorded each iteration's kernels are replayed
+ * from one captured CUDA graph on the context's stream.
+ * Returns MBICG_OK, MBICG_ENOTCONV (max_iter reached or the final true
+ * residual above tol), MBICG_EBREAKDOWN, MBICG_ENAN, or MBICG_EINVAL /
+ * MBICG_ENOGAUGE / MBICG_ENOMEM / MBICG_ECUDA before or instead of a result. */
 int mbicg_block_solve(mbicg_ctx* ctx, const double* B, double* X, int L, double kappa,
                       double tol, const mbicg_params* p, int* iters, double* true_res);
 
