@@ -12,8 +12,9 @@ larger than L2, so no extra flush is needed.
 
 N > 1 runs under torchrun as independent replicas (one solve stream per GPU,
 no collective on the data path); value is the whole-job RHS solves/s.
---impl reference times the FP64 CPU oracle (the reference implementation of
-this build) on the host cores, on a bounded sample of the same workload.
+--impl reference times the FP64 CPU oracle (the reference arm: the method
+written plainly from the paper) on the host cores, on a bounded sample of the
+same workload.
 """
 from __future__ import annotations
 
@@ -38,8 +39,8 @@ import synth  # noqa: E402
 # ---------------------------------------------------------------------------
 WORKLOADS = {
     # 32^3 x 64, eps 0.5 links, L = 12 point sources, SAP 8^4, mixed precision.
-    # kappa: tuned so that the unpreconditioned BiCGSTAB (L = 1) needs > 2000
-    # iterations on this field (see the design notes for the scan).
+    # kappa: chosen from a scan of kappa on this field so that the
+    # unpreconditioned BiCGSTAB (L = 1) needs more than 2000 iterations.
     "wilson_32c64_L12": dict(dims=(32, 32, 32, 64), eps=0.5, gauge_seed=1003, L=12, source="point",
                              kappa=0.14775, block=(8, 8, 8, 8), ncycle=4, nmr=4, tol=1e-10),
     # smaller lattices of the same family, for quick runs

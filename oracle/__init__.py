@@ -58,6 +58,24 @@ def _load():
             _int_p, _dbl_p, ctypes.c_double, _dbl_p, _dbl_p, ctypes.c_int, ctypes.c_double,
             ctypes.c_int, ctypes.c_int, _dbl_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
             _int_p, _dbl_p, ctypes.c_int, _int_p, _dbl_p]
+        lib.oracle_clover.argtypes = [_int_p, _dbl_p, ctypes.c_double, ctypes.c_double, _dbl_p]
+        lib.oracle_clover_inverse.argtypes = [ctypes.c_long, _dbl_p, _dbl_p]
+        lib.oracle_apply_clover_D.argtypes = [_int_p, _dbl_p, ctypes.c_double, _dbl_p, _dbl_p,
+                                              _dbl_p, ctypes.c_int]
+        lib.oracle_apply_A.argtypes = [_int_p, _dbl_p, ctypes.c_double, _dbl_p, _dbl_p, _dbl_p,
+                                       ctypes.c_int]
+        lib.oracle_ssor_domains.argtypes = [_int_p, _int_p, _dbl_p, ctypes.c_double, _dbl_p,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_int, _dbl_p,
+                                            _dbl_p, ctypes.c_int]
+        lib.oracle_sap_ext.argtypes = [_int_p, _int_p, _dbl_p, ctypes.c_double, _dbl_p,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       _dbl_p, ctypes.c_int, ctypes.c_double, _dbl_p, _dbl_p,
+                                       ctypes.c_int]
+        lib.oracle_block_bicgstab_ext.argtypes = [
+            _int_p, _dbl_p, ctypes.c_double, _dbl_p, _dbl_p, _dbl_p, ctypes.c_int,
+            ctypes.c_double, ctypes.c_int, ctypes.c_int, _dbl_p, ctypes.c_int, ctypes.c_int,
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _int_p, _dbl_p,
+            ctypes.c_int, _int_p, _dbl_p]
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -112,6 +130,7 @@ def apply_D(dims, U, kappa: float, psi) -> np.ndarray:
 
 
 MR_COLUMN, MR_BLOCK, MR_FROZEN = 0, 1, 2
+DOMAIN_MR, DOMAIN_SSOR = 0, 1      # SAP domain solvers (sap_ext, block_bicgstab)
 
 
 def sap(dims, block, U, kappa: float, ncycle: int, nmr: int, eta, mr_mode: int = MR_COLUMN,
@@ -162,27 +181,137 @@ def lu_solve(G, C) -> np.ndarray:
 
 def block_bicgstab(dims, U, kappa: float, B, tol: float, max_iter: int = 1000, X0=None,
                    rtilde=None, ncycle: int = 0, nmr: int = 0, block=None,
-                   mr_mode: int = MR_COLUMN, history_len: int | None = None) -> dict:
-    """Algorithm 1 of Sec. 2.1.  Returns dict(X, iters, status, history, true_res)."""
+                   mr_mode: int = MR_COLUMN, history_len: int | None = None, Tinv=None,
+                   solver: int = DOMAIN_MR, nssor: int = 1, omega: float = 1.26) -> dict:
+    """Algorithm 1 of Sec. 2.1 for A X = B.  A is the Wilson matrix, or with
+    Tinv the Jacobi-preconditioned clover matrix T^{-1} D_c (Sec. 2.2; pass
+    T^{-1} B to solve D_c X = B).  The SAP domain solver is MR (nmr, mr_mode)
+    or SSOR (nssor, omega).  Returns dict(X, iters, status, history, true_res)."""
     V = int(np.prod(dims))
     U = _cplx(U, (V, 4, 3, 3))
     B = _cplx(B)
     L = B.shape[3]
     X = np.zeros_like(B) if X0 is None else _cplx(X0).copy()
     rt = None if rtilde is None else _cplx(rtilde, B.shape)
+    Ti = None if Tinv is None else _cplx(Tinv, (V, 12, 12))
     hl = max_iter if history_len is None else history_len
     hist = np.zeros(max(hl, 1))
     iters = ctypes.c_int(0)
     tres = np.zeros(L)
     blk = _ivec(block if block is not None else (1, 1, 1, 1))
-    rc = _load().oracle_block_bicgstab(
-        _ivec(dims), _dp(U), float(kappa), _dp(B), _dp(X), L, float(tol), int(max_iter),
-        int(X0 is not None), _dp(rt), int(ncycle), int(nmr), int(mr_mode), blk, _dp(hist), hl,
-        ctypes.byref(iters), _dp(tres))
+    rc = _load().oracle_block_bicgstab_ext(
+        _ivec(dims), _dp(U), float(kappa), _dp(Ti), _dp(B), _dp(X), L, float(tol),
+        int(max_iter), int(X0 is not None), _dp(rt), int(ncycle), int(solver), int(nmr),
+        int(mr_mode), int(nssor), float(omega), blk, _dp(hist), hl, ctypes.byref(iters),
+        _dp(tres))
     if rc < 0:
-        raise ValueError(f"oracle_block_bicgstab returned {rc}")
+        raise ValueError(f"oracle_block_bicgstab_ext returned {rc}")
     k = iters.value
     return dict(X=X, iters=k, status=rc, history=hist[:min(k, hl)].copy(), true_res=tres)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.2: clover term, Jacobi preconditioning, SSOR domain solves
+# ---------------------------------------------------------------------------
+
+
+def clover(dims, U, kappa: float, csw: float) -> np.ndarray:
+    """T_x = 1 + i kappa csw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x), shape (V, 12, 12)
+    (index spin * 3 + colour); F from the four-plaquette clover leaf."""
+    V = int(np.prod(dims))
+    U = _cplx(U, (V, 4, 3, 3))
+    T = np.empty((V, 12, 12), dtype=np.complex128)
+    rc = _load().oracle_clover(_ivec(dims), _dp(U), float(kappa), float(csw), _dp(T))
+    if rc != 0:
+        raise ValueError(f"oracle_clover returned {rc}")
+    return T
+
+
+def clover_inverse(T) -> np.ndarray:
+    """T_x^{-1} at every site."""
+    T = _cplx(T)
+    if T.ndim != 3 or T.shape[1:] != (12, 12):
+        raise ValueError("T must have shape (V, 12, 12)")
+    Ti = np.empty_like(T)
+    rc = _load().oracle_clover_inverse(T.shape[0], _dp(T), _dp(Ti))
+    if rc != 0:
+        raise np.linalg.LinAlgError(f"oracle_clover_inverse returned {rc}")
+    return Ti
+
+
+def _block_arg(dims, psi):
+    V = int(np.prod(dims))
+    psi = _cplx(psi)
+    if psi.ndim != 4 or psi.shape[:3] != (V, 4, 3):
+        raise ValueError("psi must have shape (V, 4, 3, L)")
+    return psi
+
+
+def apply_clover_D(dims, U, kappa: float, T, psi) -> np.ndarray:
+    """D_c psi = T psi - kappa H psi."""
+    V = int(np.prod(dims))
+    U = _cplx(U, (V, 4, 3, 3))
+    T = _cplx(T, (V, 12, 12))
+    psi = _block_arg(dims, psi)
+    out = np.empty_like(psi)
+    rc = _load().oracle_apply_clover_D(_ivec(dims), _dp(U), float(kappa), _dp(T), _dp(psi),
+                                       _dp(out), psi.shape[3])
+    if rc != 0:
+        raise ValueError(f"oracle_apply_clover_D returned {rc}")
+    return out
+
+
+def apply_A(dims, U, kappa: float, Tinv, psi) -> np.ndarray:
+    """A psi, A = T^{-1} D_c = 1 - kappa T^{-1} H (Wilson D when Tinv is None)."""
+    V = int(np.prod(dims))
+    U = _cplx(U, (V, 4, 3, 3))
+    Ti = None if Tinv is None else _cplx(Tinv, (V, 12, 12))
+    psi = _block_arg(dims, psi)
+    out = np.empty_like(psi)
+    rc = _load().oracle_apply_A(_ivec(dims), _dp(U), float(kappa), _dp(Ti), _dp(psi), _dp(out),
+                                psi.shape[3])
+    if rc != 0:
+        raise ValueError(f"oracle_apply_A returned {rc}")
+    return out
+
+
+def ssor_domains(dims, block, U, kappa: float, nssor: int, omega: float, colour: int, psi,
+                 Tinv=None) -> np.ndarray:
+    """B_cc psi: the SSOR domain solve of Sec. 2.2 on every domain of one colour."""
+    V = int(np.prod(dims))
+    U = _cplx(U, (V, 4, 3, 3))
+    Ti = None if Tinv is None else _cplx(Tinv, (V, 12, 12))
+    psi = _block_arg(dims, psi)
+    out = np.empty_like(psi)
+    rc = _load().oracle_ssor_domains(_ivec(dims), _ivec(block), _dp(U), float(kappa), _dp(Ti),
+                                     int(nssor), float(omega), int(colour), _dp(psi), _dp(out),
+                                     psi.shape[3])
+    if rc != 0:
+        raise ValueError(f"oracle_ssor_domains returned {rc}")
+    return out
+
+
+def sap_ext(dims, block, U, kappa: float, ncycle: int, eta, Tinv=None, solver: int = DOMAIN_SSOR,
+            nmr: int = 0, mr_mode: int = MR_COLUMN, omega_table=None, nssor: int = 1,
+            omega: float = 1.26) -> np.ndarray:
+    """psi = M_SAP eta (Sec. 2.2) for the matrix of apply_A, with MR or SSOR
+    domain solves."""
+    V = int(np.prod(dims))
+    U = _cplx(U, (V, 4, 3, 3))
+    Ti = None if Tinv is None else _cplx(Tinv, (V, 12, 12))
+    eta = _block_arg(dims, eta)
+    out = np.empty_like(eta)
+    if omega_table is not None:
+        nd = V // int(np.prod(block))
+        if (omega_table.dtype != np.complex128 or not omega_table.flags.c_contiguous
+                or omega_table.shape != (ncycle, 2, nmr, nd)):
+            raise ValueError("omega_table must be a C-contiguous complex128 (ncycle, 2, nmr, nd) array")
+    rc = _load().oracle_sap_ext(_ivec(dims), _ivec(block), _dp(U), float(kappa), _dp(Ti),
+                                int(ncycle), int(solver), int(nmr), int(mr_mode), _dp(omega_table),
+                                int(nssor), float(omega), _dp(eta), _dp(out), eta.shape[3])
+    if rc != 0:
+        raise ValueError(f"oracle_sap_ext returned {rc}")
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -95,6 +95,68 @@ int oracle_block_bicgstab(const int dims[4], const double* U, double kappa,
                           int ncycle, int nmr, int mr_mode, const int block[4],
                           double* history, int history_len, int* iters, double* true_res);
 
+/* ---- Sec. 2.2: the O(a)-improved operator, Jacobi preconditioning, SSOR ---- */
+
+/* The site-local clover matrix T_x = 1 + i kappa csw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x)
+ * of the O(a)-improved Wilson-Dirac matrix D_c = T - kappa H, with
+ *   sigma_{mu nu} = (i/2) [gamma_mu, gamma_nu],
+ *   F_{mu nu}(x)  = (Q_{mu nu}(x) - Q_{mu nu}(x)^dagger) / 8,
+ *   Q_{mu nu}(x)  = the sum of the four plaquettes of the (mu, nu) plane that
+ *                   start and end at x, each traversed in the mu-then-nu sense
+ *                   (no trace subtracted, no boundary phase: links only).
+ * T: [site][12][12] complex, row and column index spin * 3 + colour. */
+int oracle_clover(const int dims[4], const double* U, double kappa, double csw, double* T);
+
+/* Tinv[s] = T[s]^{-1} for V sites (LU with partial pivoting per site).
+ * Returns 2 if a site matrix is singular. */
+int oracle_clover_inverse(long V, const double* T, double* Tinv);
+
+/* out = D_c in = T in - kappa H in (H the hopping term of Sec. 2.1). */
+int oracle_apply_clover_D(const int dims[4], const double* U, double kappa, const double* T,
+                          const double* in, double* out, int L);
+
+/* out = A in for the Jacobi-preconditioned matrix A = T^{-1} D_c
+ * = 1 - kappa T^{-1} H (Sec. 2.2, the division by 1 + clover term).
+ * Tinv == NULL gives the Wilson matrix (oracle_apply_D). */
+int oracle_apply_A(const int dims[4], const double* U, double kappa, const double* Tinv,
+                   const double* in, double* out, int L);
+
+/* Domain solvers of the SAP preconditioner. */
+#define ORACLE_DOMAIN_MR 0   /* nmr minimal-residual steps (mr_mode as in oracle_sap) */
+#define ORACLE_DOMAIN_SSOR 1 /* the SSOR approximation of Sec. 2.2 */
+
+/* out = B_cc in on every domain of colour `colour` (0 = E, 1 = O), zero on the
+ * other colour, with the SSOR approximation of Sec. 2.2: on a domain with
+ * matrix A_dom = 1 - L - U, L = kappa T^{-1} (forward hops inside the domain),
+ * U = kappa T^{-1} (backward hops inside the domain),
+ *   B = (1 - omega U)^{-1} [sum_{j=0}^{nssor} (1 - Ahat)^j] (1 - omega L)^{-1},
+ *   Ahat = (1/omega) [(1 - omega L)^{-1} + (1 - omega U)^{-1}
+ *                     + (omega - 2) (1 - omega L)^{-1} (1 - omega U)^{-1}],
+ * the triangular inverses by substitution over the domain's sites (decreasing
+ * site order for L, increasing for U).  nssor >= 0 is the upper limit of the
+ * sum, as printed; 0 < omega < 2.  Tinv == NULL: T = 1 (Wilson). */
+int oracle_ssor_domains(const int dims[4], const int block[4], const double* U, double kappa,
+                        const double* Tinv, int nssor, double omega, int colour,
+                        const double* in, double* out, int L);
+
+/* psi = M_SAP eta as oracle_sap, for the matrix A of oracle_apply_A and with
+ * either domain solver: ORACLE_DOMAIN_MR (nmr, mr_mode, omega_table as in
+ * oracle_sap) or ORACLE_DOMAIN_SSOR (nssor, omega as in oracle_ssor_domains). */
+int oracle_sap_ext(const int dims[4], const int block[4], const double* U, double kappa,
+                   const double* Tinv, int ncycle, int solver, int nmr, int mr_mode,
+                   double* omega_table, int nssor, double omega,
+                   const double* eta, double* psi, int L);
+
+/* oracle_block_bicgstab for the matrix A of oracle_apply_A (A X = B; with a
+ * clover term the caller passes T^{-1} B for D_c X = B) and the SAP domain
+ * solver of oracle_sap_ext.  true_res is |b_i - A x_i| / |b_i|. */
+int oracle_block_bicgstab_ext(const int dims[4], const double* U, double kappa,
+                              const double* Tinv, const double* B, double* X, int L,
+                              double tol, int max_iter, int use_x0, const double* rtilde,
+                              int ncycle, int solver, int nmr, int mr_mode, int nssor,
+                              double omega, const int block[4], double* history,
+                              int history_len, int* iters, double* true_res);
+
 /* Number of OpenMP threads the oracle runs with. */
 int oracle_num_threads(void);
 
