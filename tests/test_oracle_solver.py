@@ -165,6 +165,29 @@ def test_algorithm2_equals_algorithm1(oracle_mod):
     assert np.max(np.abs(res["X"].reshape(N, L) - X)) < 1e-9 * np.max(np.abs(X))
 
 
+@pytest.mark.parametrize("ncycle", [0, 2])
+@pytest.mark.parametrize("delta", [1e-6, 1e-10])
+def test_qr_keeps_true_residual_with_nearly_dependent_columns(oracle_mod, ncycle, delta):
+    """Sec. 2.1: the QR of P is there for numerical accuracy (in exact
+    arithmetic P -> P gamma^{-1} only rescales alpha and beta, and the
+    residuals are unchanged).  With right-hand sides that differ by delta the
+    unorthogonalised block becomes nearly rank deficient and the recursive
+    residual drifts away from the true one (true residual 1e-9 .. 1e-6 at a
+    recursive 1e-12 when the QR is left out); with the QR both stay together."""
+    dims = (4, 4, 4, 4)
+    U = synth.su3_links(dims, 0.4, seed=1000)
+    B = synth.gaussian_source(dims, 4, seed=5)
+    rng = np.random.default_rng(3)
+    for i in range(1, 4):
+        B[..., i] = B[..., 0] + delta * (rng.standard_normal(B.shape[:3])
+                                         + 1j * rng.standard_normal(B.shape[:3]))
+    rt = synth.gaussian_source(dims, 4, seed=9)
+    res = oracle_mod.block_bicgstab(dims, U, 0.12, B, 1e-12, max_iter=300, ncycle=ncycle, nmr=4,
+                                    block=(2, 2, 2, 2), mr_mode=oracle_mod.MR_FROZEN, rtilde=rt)
+    assert res["status"] == 0
+    assert np.max(res["true_res"]) < 1e-11
+
+
 def test_block_solve_statuses(oracle_mod):
     dims = (2, 2, 2, 2)
     U = synth.su3_links(dims, 0.4, seed=1)
