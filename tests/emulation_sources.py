@@ -140,3 +140,48 @@ def blas_parts(csrc=CSRC):
     bl, slots = bind_shared(bl)
     return "\n".join([f"#define EMU_STATIC_SLOTS {max(slots, 1)}", '#include "shim_threads.h"',
                       common, internal, "namespace mbicg {", "namespace emu_blas {", bl, "}", "}"])
+
+
+def _split_launch_config(cfg):
+    parts = _split_top(cfg)
+    while len(parts) < 4:
+        parts.append("0")
+    return parts
+
+
+def rewrite_launches(src):
+    """kernel<<<grid, block, smem, stream>>>(args); -> an emulated launch, and
+    cudaLaunchKernelEx(cfg, kernel, args) -> emu_launch_ex(cfg, kernel, args)."""
+    pat = re.compile(r"([A-Za-z_][\w:]*(?:<[^;{}]*?>)?)<<<(.*?)>>>\((.*?)\);", re.S)
+
+    def sub(m):
+        grid, block, smem, stream = _split_launch_config(m.group(2))
+        return (f"emu_kernel_launch({grid}, {block}, {smem}, {stream}, [&] {{ {m.group(1)}({m.group(3)}); }});")
+
+    src = pat.sub(sub, src)
+    return src.replace("cudaLaunchKernelEx(", "emu_launch_ex(")
+
+
+def driver_parts(csrc=CSRC):
+    """The SAP driver (sap.cu) and everything it launches (dslash.cu), host
+    code included, for the threaded emulation: launches rewritten onto the
+    emulator, inline PTX helpers replaced, shared memory bound to the arenas."""
+    common = read("common.cuh", csrc)
+    common = replace_body(common, "__device__ __forceinline__ void load_spinor(const cx<float>* p, Spinor<float>& s)",
+                          "{ for (int k = 0; k < 12; ++k) (&s.c[0][0])[k] = p[k]; }")
+    common = replace_body(common, "__device__ __forceinline__ void store_spinor(cx<float>* p, const Spinor<float>& s)",
+                          "{ for (int k = 0; k < 12; ++k) p[k] = (&s.c[0][0])[k]; }")
+    internal = read("internal.h", csrc).replace('#include "common.cuh"', "")
+    ds = read("dslash.cu", csrc)
+    ds = ds[ds.index("namespace mbicg {"):]
+    ds = replace_body(ds, "__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank)",
+                      "{ return emu_mapa(local, rank); }")
+    ds = replace_body(ds, "__device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr)",
+                      "{ return emu_ld_cluster_f4(addr); }")
+    sp = read("sap.cu", csrc)
+    sp = sp[sp.index("namespace mbicg {"):]
+    body = rewrite_launches(ds + "\n" + sp)
+    body, slots = bind_shared(body)
+    return "\n".join([f"#define EMU_STATIC_SLOTS {max(slots, 1)}", '#include "shim_threads.h"',
+                      "#include <algorithm>", "#include <cstdlib>", "#include <type_traits>",
+                      '#include "emu_runtime.h"', common, internal, body])
