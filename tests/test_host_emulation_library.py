@@ -42,7 +42,8 @@ def lib(tmp_path_factory):
         src.write_text(emulation_sources.library_unit(name))
         units.append(src)
     units.append(os.path.join(HERE, "emu_cudart.cpp"))
-    flags = ["g++", "-std=c++20", "-O1", "-fPIC", "-pthread", "-I", str(d), "-I", CUDA_INCLUDE]
+    flags = ["g++", "-std=c++20", "-O1", "-fPIC", "-pthread", "-I", str(d), "-I", emulation_sources.CSRC,
+             "-I", CUDA_INCLUDE]
 
     def compile_one(src):
         obj = str(d / (os.path.basename(str(src)) + ".o"))
