@@ -9,7 +9,8 @@ CUDA runtime calls are emulated over host memory
 solver runs its iterations eagerly).  Checked against the oracle: the
 operator with host pointers in FP64 and FP32, and mbicg_block_solve in FP64
 and in mixed precision (reliable updates), with dummy right-hand sides and an
-initial guess, plus the ABI's argument errors.  This exercises the solver's
+initial guess, the allocation-free operator on emulated device buffers, plus
+the ABI's argument errors.  This exercises the solver's
 host logic of Algorithm 2 on a machine without a GPU; the -m gpu tests run the
 same code on the hardware."""
 import ctypes
@@ -119,3 +120,39 @@ def test_abi_errors(lib, ctx):
     assert lib.mbicg_create(ctypes.byref(fresh), (ctypes.c_int * 4)(*DIMS), 0, None) == mb.MBICG_OK
     assert _solve(lib, fresh, B, X, _params(lib))[0] == mb.MBICG_ENOGAUGE
     lib.mbicg_destroy(fresh)
+
+
+def _device_copy(lib, a):
+    """An emulated device buffer (the runtime's own allocation) holding a copy of a."""
+    p = ctypes.c_void_p()
+    assert lib.cudaMalloc(ctypes.byref(p), a.nbytes) == 0
+    ctypes.memmove(p, a.ctypes.data, a.nbytes)
+    return p
+
+
+def test_noalloc_operator(lib, ctx):
+    """mbicg_apply_D_noalloc (device pointers, a fixed scratch array) gives the
+    FP32 operator of mbicg_apply_D bit for bit, on two calls in a row with
+    different blocks; sizes beyond its scratch and host pointers are refused."""
+    c, U = ctx
+    dims = (ctypes.c_int * 4)(*DIMS)
+    dU = _device_copy(lib, U)
+    try:
+        for Lc, kappa, seed in ((3, 0.13, 2004), (1, 0.121, 2005)):
+            psi = synth.gaussian_source(DIMS, Lc, seed=seed)
+            ref = np.empty_like(psi)
+            assert lib.mbicg_apply_D(c, _v(psi), _v(ref), Lc, kappa, mb.MBICG_FP32) == mb.MBICG_OK
+            d_in = _device_copy(lib, psi)
+            d_out = _device_copy(lib, np.full_like(psi, np.nan))
+            assert lib.mbicg_apply_D_noalloc(dims, dU, d_in, d_out, Lc, kappa, None) == mb.MBICG_OK
+            out = np.empty_like(psi)
+            ctypes.memmove(out.ctypes.data, d_out, out.nbytes)
+            assert np.array_equal(out, ref)
+            lib.cudaFree(d_in)
+            lib.cudaFree(d_out)
+        big = (ctypes.c_int * 4)(16, 16, 16, 16)
+        assert lib.mbicg_apply_D_noalloc(big, dU, dU, dU, 12, 0.12, None) == mb.MBICG_EINVAL
+        host = np.zeros_like(U)
+        assert lib.mbicg_apply_D_noalloc(dims, _v(host), dU, dU, 1, 0.12, None) == mb.MBICG_EINVAL
+    finally:
+        lib.cudaFree(dU)
