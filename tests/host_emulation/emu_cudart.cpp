@@ -89,6 +89,10 @@ cudaError_t cudaMemcpy(void* d, const void* s, size_t n, enum cudaMemcpyKind) {
   memmove(d, s, n);
   return cudaSuccess;
 }
+cudaError_t cudaMemset(void* p, int v, size_t n) {
+  memset(p, v, n);
+  return cudaSuccess;
+}
 cudaError_t cudaMemsetAsync(void* p, int v, size_t n, cudaStream_t) {
   memset(p, v, n);
   return cudaSuccess;
