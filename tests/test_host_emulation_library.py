@@ -9,8 +9,9 @@ CUDA runtime calls are emulated over host memory
 solver runs its iterations eagerly).  Checked against the oracle: the
 operator with host pointers in FP64 and FP32, and mbicg_block_solve in FP64
 and in mixed precision (reliable updates), with dummy right-hand sides and an
-initial guess, the allocation-free operator on emulated device buffers, the
-give-up path of the bounded mbarrier wait, plus the ABI's argument errors.  This exercises the solver's
+initial guess, the FP16-storage operator against the oracle's FP16 format,
+the allocation-free operator on emulated device buffers, the give-up path of
+the bounded mbarrier wait, plus the ABI's argument errors.  This exercises the solver's
 host logic of Algorithm 2 on a machine without a GPU; the -m gpu tests run the
 same code on the hardware."""
 import ctypes
@@ -20,6 +21,7 @@ import numpy as np
 import pytest
 
 import emulation_sources
+import oracle
 
 import paper_1104_0737_gb300 as mb  # the ctypes structures only; no library is loaded
 import synth
@@ -183,3 +185,30 @@ def test_every_cuda_source_is_emulated():
     """The emulated library is built from every CUDA source of the package."""
     sources = {f for f in os.listdir(emulation_sources.CSRC) if f.endswith(".cu")}
     assert set(emulation_sources.LIBRARY_SOURCES) == sources
+
+
+def _comps(a):
+    """(V, 4, 3, L) complex -> (V, L, 24) reals of each (site, rhs) spinor."""
+    V, Lc = a.shape[0], a.shape[-1]
+    return np.stack([a.real, a.imag], -1).reshape(V, 12, Lc, 2).transpose(0, 2, 1, 3).reshape(V, Lc, 24)
+
+
+def test_fp16_operator_through_the_abi(lib, ctx, oracle_mod):
+    """mbicg_apply_D with MBICG_FP16 (conversions into and out of FP16 storage
+    with one scale per (site, column), the FP16 operator): kappa = 0 gives the
+    input as the oracle's FP16 format represents it, bit for bit (a zero spinor
+    keeps scale 0); kappa = 0.13 gives the oracle's operator on the
+    FP16-represented links and input, rounded into the format, up to one FP16
+    step of the output scale where the FP32 and FP64 sums round differently."""
+    c, U = ctx
+    psi = synth.gaussian_source(DIMS, 3, seed=2007)
+    psi[3] = 0
+    out = np.empty_like(psi)
+    assert lib.mbicg_apply_D(c, _v(psi), _v(out), 3, 0.0, mb.MBICG_FP16) == mb.MBICG_OK
+    assert np.array_equal(out, oracle.quantize_fp16(psi))
+    assert lib.mbicg_apply_D(c, _v(psi), _v(out), 3, 0.13, mb.MBICG_FP16) == mb.MBICG_OK
+    exp = oracle.quantize_fp16(oracle_mod.apply_D(DIMS, oracle.quantize_links_fp16(U), 0.13, oracle.quantize_fp16(psi)))
+    g, e = _comps(out), _comps(exp)
+    sc = np.abs(e).max(axis=2, keepdims=True)
+    assert np.all(np.abs(g - e) <= 2.0 ** -10 * sc)
+    assert np.mean(np.abs(g - e) > 2.0 ** -20 * sc) < 0.05
