@@ -9,7 +9,8 @@ CUDA runtime calls are emulated over host memory
 solver runs its iterations eagerly).  Checked against the oracle: the
 operator with host pointers in FP64 and FP32, and mbicg_block_solve in FP64
 and in mixed precision (reliable updates), with dummy right-hand sides and an
-initial guess, the FP16-storage operator against the oracle's FP16 format,
+initial guess, mbicg_sap_precond (per-column and block MR, FP64 and FP32),
+the FP16-storage operator against the oracle's FP16 format,
 the allocation-free operator on emulated device buffers, the give-up path of
 the bounded mbarrier wait, plus the ABI's argument errors.  This exercises the solver's
 host logic of Algorithm 2 on a machine without a GPU; the -m gpu tests run the
@@ -212,3 +213,17 @@ def test_fp16_operator_through_the_abi(lib, ctx, oracle_mod):
     sc = np.abs(e).max(axis=2, keepdims=True)
     assert np.all(np.abs(g - e) <= 2.0 ** -10 * sc)
     assert np.mean(np.abs(g - e) > 2.0 ** -20 * sc) < 0.05
+
+
+@pytest.mark.parametrize("mode,prec,tol", [(0, mb.MBICG_FP64, 1e-12), (1, mb.MBICG_FP64, 1e-12),
+                                           (0, mb.MBICG_FP32, 1e-5), (1, mb.MBICG_FP32, 1e-5)])
+def test_sap_precond_through_the_abi(lib, ctx, oracle_mod, mode, prec, tol):
+    """mbicg_sap_precond (host pointers) against the oracle's SAP: per-column
+    and block-shared MR, FP64 and FP32."""
+    c, U = ctx
+    eta = synth.gaussian_source(DIMS, L, seed=2008)
+    out = np.empty_like(eta)
+    p = _params(lib, ncycle=2, nmr=3, mr_mode=mode, prec_sap=prec)
+    assert lib.mbicg_sap_precond(c, _v(eta), _v(out), L, KAPPA, ctypes.byref(p)) == mb.MBICG_OK
+    ref = oracle_mod.sap(DIMS, (2, 2, 2, 2), U, KAPPA, 2, 3, eta, mr_mode=mode)
+    assert np.max(np.abs(out - ref)) < tol * np.max(np.abs(ref))
