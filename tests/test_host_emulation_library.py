@@ -10,7 +10,8 @@ solver runs its iterations eagerly).  Checked against the oracle: the
 operator with host pointers in FP64 and FP32, and mbicg_block_solve in FP64
 and in mixed precision (reliable updates), with dummy right-hand sides and an
 initial guess, mbicg_sap_precond (per-column and block MR, FP64 and FP32),
-the FP16-storage operator against the oracle's FP16 format,
+the residual history and the per-class launch profile, the FP16-storage
+operator against the oracle's FP16 format,
 the allocation-free operator on emulated device buffers, the give-up path of
 the bounded mbarrier wait, plus the ABI's argument errors.  This exercises the solver's
 host logic of Algorithm 2 on a machine without a GPU; the -m gpu tests run the
@@ -227,3 +228,39 @@ def test_sap_precond_through_the_abi(lib, ctx, oracle_mod, mode, prec, tol):
     assert lib.mbicg_sap_precond(c, _v(eta), _v(out), L, KAPPA, ctypes.byref(p)) == mb.MBICG_OK
     ref = oracle_mod.sap(DIMS, (2, 2, 2, 2), U, KAPPA, 2, 3, eta, mr_mode=mode)
     assert np.max(np.abs(out - ref)) < tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec_D,dummies", [(mb.MBICG_FP64, 0), (mb.MBICG_FP32, 2)])
+def test_history_and_profile_through_the_abi(lib, ctx, prec_D, dummies):
+    """res_history holds the recursive residual after each iteration (one entry
+    per iteration, falling to the tolerance); with profiling on, every launch
+    of the solve (FP64, and mixed precision with dummy columns) is counted in
+    a kernel class and timed (the emulated events read the host clock): the
+    counts add up to the solve's launches, and the operator's class has its
+    two launches per iteration."""
+    c, _ = ctx
+    lib.mbicg_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.mbicg_get_profile.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+    ncls = 10  # MBICG_K_NCLASS of include/mbicg.h
+    B = synth.gaussian_source(DIMS, L, seed=2009)
+    X = np.empty_like(B)
+    hist = np.full(64, np.nan)
+    p = _params(lib, prec_D=prec_D, dummy_rhs=dummies, dummy_seed=3)
+    p.res_history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.res_history_len = len(hist)
+    assert lib.mbicg_set_profiling(c, 1) == mb.MBICG_OK
+    try:
+        rc, iters, tres, st = _solve(lib, c, B, X, p)
+        ms = np.zeros(ncls)
+        n = np.zeros(ncls, dtype=np.int64)
+        assert lib.mbicg_get_profile(c, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     n.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), ncls) == mb.MBICG_OK
+    finally:
+        lib.mbicg_set_profiling(c, 0)
+    assert rc == mb.MBICG_OK and 0 < iters <= len(hist)
+    h = hist[:iters]
+    assert np.all(np.isfinite(h)) and np.all(np.isnan(hist[iters:]))
+    assert h[-1] <= 1e-10 < h[0] and h[-1] < h[:-1].min()
+    assert n.sum() == st.kernel_launches > 0 and np.all(ms >= 0) and ms.sum() > 0
+    assert n[0] == 2 * iters  # MBICG_K_DSLASH
