@@ -82,12 +82,28 @@ __device__ __forceinline__ void hopping(const Geom& g, const cx<R>* __restrict__
   hops_mu<R, DIRICHLET, 3>(g, links, in, L, rhs, s, c, lc, st3, acc);
 }
 
+// The order in which the CTAs of the operator walk the lattice.  A CTA takes a
+// segment of S consecutive sites; the segments are taken in slabs of tt time
+// slices with the time slice running fastest, so the CTAs that read a site as
+// a t +- 1 neighbour run close in time to the one that reads it as its own
+// site and the data is still in L2 (in lexicographic order they are a whole
+// time slice, ~40 MB at 32^3 x 64, L = 12, apart).  wslice = segments per time
+// slice; tt = 1 keeps the lexicographic order.
+__host__ __device__ __forceinline__ int segment_of(int b, int wslice, int tt) {
+  if (tt <= 1) return b;
+  const int per_slab = wslice * tt;
+  const int slab = b / per_slab, r = b - slab * per_slab;
+  const int w = r / tt, dt = r - w * tt;
+  return (slab * tt + dt) * wslice + w;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_dslash_full(Geom g, const cx<R>* __restrict__ links,
                                                      const cx<R>* __restrict__ in,
-                                                     cx<R>* __restrict__ out, int L, R kappa) {
+                                                     cx<R>* __restrict__ out, int L, R kappa, int wslice,
+                                                     int tt) {
   const int rhs = threadIdx.x;
-  const int s = blockIdx.x * blockDim.y + threadIdx.y;
+  const int s = segment_of(blockIdx.x, wslice, tt) * blockDim.y + threadIdx.y;
   if (s >= g.V) return;
   int c[4];
   site_coords(g, s, c);
@@ -664,7 +680,11 @@ void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>*
   const int S = pow2_floor(max_cta<R>() / L);
   const dim3 block(L, S);
   const int grid = (g.V + S - 1) / S;
-  k_dslash_full<R><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa);
+  // time slabs of 8 slices where the segments tile the time slices exactly
+  const int slice = g.d[0] * g.d[1] * g.d[2];
+  const bool slabs = slice % S == 0 && g.d[3] % 8 == 0;
+  k_dslash_full<R><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa, slabs ? slice / S : 0,
+                                                             slabs ? 8 : 1);
   ++*ex.launches;
 }
 
