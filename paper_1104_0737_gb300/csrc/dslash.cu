@@ -19,6 +19,7 @@
 #include <stdlib.h>
 
 #include "internal.h"
+#include "tune.h"
 
 namespace mbicg {
 
@@ -674,18 +675,62 @@ int sap_sites_per_cta(const Geom& g, int L, bool fp64) {
   return S;
 }
 
+// one launch of the operator in configuration cfg (tune.h)
 template <typename R>
-void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
-                 double kappa) {
-  const int S = pow2_floor(max_cta<R>() / L);
+void launch_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
+                   double kappa, DslashConfig cfg) {
+  const int S = cfg.S;
   const dim3 block(L, S);
   const int grid = (g.V + S - 1) / S;
-  // time slabs of 8 slices where the segments tile the time slices exactly
   const int slice = g.d[0] * g.d[1] * g.d[2];
-  const bool slabs = slice % S == 0 && g.d[3] % 8 == 0;
+  const bool slabs = cfg.order == 1 && slice % S == 0 && g.d[3] % 8 == 0;
   k_dslash_full<R><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa, slabs ? slice / S : 0,
                                                              slabs ? 8 : 1);
   ++*ex.launches;
+}
+
+// the configuration the tuner chose for this operator, else the default: the
+// most sites per CTA, in time slabs where they tile the time slices
+template <typename R>
+DslashConfig dslash_config(const Geom& g, int L) {
+  const std::vector<DslashConfig> cand = dslash_candidates(g.d, L, max_cta<R>());
+  int idx;
+  if (tune_table().lookup(dslash_key((int)sizeof(R), g.d, L), &idx) && idx >= 0 && idx < (int)cand.size())
+    return cand[idx];
+  return cand.size() > 1 && cand[1].S == cand[0].S ? cand[1] : cand[0];
+}
+
+template <typename R>
+void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
+                 double kappa) {
+  launch_dslash<R>(ex, g, links, in, out, L, kappa, dslash_config<R>(g, L));
+}
+
+template <typename R>
+void tune_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
+                 double kappa) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ex.stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
+  const std::vector<DslashConfig> cand = dslash_candidates(g.d, L, max_cta<R>());
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return;
+  }
+  tune_table().pick(dslash_key((int)sizeof(R), g.d, L), (int)cand.size(), [&](int i) -> double {
+    cudaEventRecord(e0, ex.stream);
+    launch_dslash<R>(ex, g, links, in, out, L, kappa, cand[i]);
+    cudaEventRecord(e1, ex.stream);
+    float ms = -1.0f;
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      return -1.0;
+    return ms;
+  });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (const char* p = getenv("MBICG_TUNE_FILE")) tune_table().save(p);
 }
 
 template <typename R>
@@ -713,6 +758,7 @@ void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* li
 
 #define INST(R)                                                                                          \
   template void dslash_full<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double); \
+  template void tune_dslash<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double); \
   template void sap_residual<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, const cx<R>*,   \
                                 cx<R>*, int, double, bool);                                               \
   template void sap_domain_apply<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, cx<R>*,     \

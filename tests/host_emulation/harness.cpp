@@ -49,10 +49,11 @@ using C = cx<double>;
 extern "C" {
 // the operator with the launch shape of the library: CTAs of S sites, walked
 // in time slabs where the library uses them
-void emu_dslash(const int* dims, const double* U, const double* in, double* out, int L, double kappa, int S) {
+void emu_dslash(const int* dims, const double* U, const double* in, double* out, int L, double kappa, int S,
+                int order) {
   const Geom g = make_geom(dims, nullptr);
   const int slice = g.d[0] * g.d[1] * g.d[2];
-  const bool slabs = slice % S == 0 && g.d[3] % 8 == 0;
+  const bool slabs = order == 1 && slice % S == 0 && g.d[3] % 8 == 0;
   const int nblk = (g.V + S - 1) / S;
   blockDim = {(unsigned)L, (unsigned)S, 1};
   gridDim = {(unsigned)nblk, 1, 1};

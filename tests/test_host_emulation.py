@@ -52,7 +52,7 @@ def emu(tmp_path_factory):
                     os.path.join(HERE, "harness.cpp"), "-o", str(lib_path)], check=True)
     lib = ctypes.CDLL(str(lib_path))
     D, I = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
-    lib.emu_dslash.argtypes = [I, D, D, D, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    lib.emu_dslash.argtypes = [I, D, D, D, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]
     lib.emu_segment_of.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.emu_nslot.argtypes = [I, I]
     lib.emu_slot.argtypes = [I, I, ctypes.c_int, ctypes.c_int, I, I]
@@ -90,9 +90,26 @@ def test_operator_kernel_matches_oracle(emu, oracle_mod, dims, L, S):
     kappa = 0.1375
     a = _internal(psi)
     out = np.full_like(a, np.nan)
-    emu.emu_dslash(_iv(dims), _dp(U), _dp(a), _dp(out), L, kappa, S)
+    emu.emu_dslash(_iv(dims), _dp(U), _dp(a), _dp(out), L, kappa, S, 1)
     ref = oracle_mod.apply_D(dims, U, kappa, psi)
     assert np.max(np.abs(_oracle_layout(out) - ref)) < 1e-14 * np.max(np.abs(ref))
+
+
+def test_operator_launch_configurations_are_bit_identical(emu, oracle_mod):
+    """Every configuration the autotuner may choose (sites per CTA, CTA order)
+    gives the same result bit for bit."""
+    dims, L = (8, 4, 4, 16), 3
+    U = np.ascontiguousarray(synth.su3_links(dims, 0.5, seed=99))
+    a = _internal(synth.gaussian_source(dims, L, seed=100))
+    outs = []
+    for S in (32, 16, 8):
+        for order in (0, 1):
+            out = np.full_like(a, np.nan)
+            emu.emu_dslash(_iv(dims), _dp(U), _dp(a), _dp(out), L, 0.13, S, order)
+            outs.append(out)
+    assert all(np.array_equal(o, outs[0]) for o in outs[1:])
+    ref = oracle_mod.apply_D(dims, U, 0.13, _oracle_layout(a))
+    assert np.max(np.abs(_oracle_layout(outs[0]) - ref)) < 1e-14 * np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("wslice,tt,nt", [(32, 8, 64), (1, 8, 16), (7, 8, 24), (5, 1, 3)])
