@@ -133,6 +133,10 @@ cudaError_t cudaEventDestroy(cudaEvent_t e) {
   event_times.erase(reinterpret_cast<size_t>(e));
   return cudaSuccess;
 }
+cudaError_t cudaStreamIsCapturing(cudaStream_t, enum cudaStreamCaptureStatus* st) {
+  *st = cudaStreamCaptureStatusNone;  // capture is never begun
+  return cudaSuccess;
+}
 cudaError_t cudaStreamBeginCapture(cudaStream_t, enum cudaStreamCaptureMode) { return cudaErrorNotSupported; }
 cudaError_t cudaStreamEndCapture(cudaStream_t, cudaGraph_t* g) {
   *g = nullptr;
