@@ -107,6 +107,14 @@ def main(so):
     small.solve(3, b2, X=X, use_x0=1)
     small.close()
 
+    # every launch configuration of the operator the autotuner times (CTA
+    # sizes, lexicographic and time-slab order), on a lattice where the slabs apply
+    os.environ["MBICG_AUTOTUNE"] = "1"
+    tuned = Ctx(lib, (4, 4, 4, 8), seed=3)
+    tuned.solve(2, (2, 2, 2, 4), tol=1e-6)
+    tuned.close()
+    os.environ.pop("MBICG_AUTOTUNE")
+
     # the 8-CTA cluster sweep over 4^4 domains, and a few iterations of a
     # block solve on it (the frozen step lengths recorded, then replayed)
     big = Ctx(lib, (8, 8, 8, 8), seed=2)

@@ -6,7 +6,8 @@ buffers are allocated at their exact size and each CTA's dynamic shared
 memory is followed by a poisoned gap, so that an access past either is
 reported: the operator in FP64, FP32 and FP16, SAP with the fused cluster
 sweep and the multi-kernel path (per-column and block MR, FP64 and FP32),
-block solves with dummy columns and an initial guess, and the 8-CTA cluster
+block solves with dummy columns and an initial guess, every launch
+configuration of the operator that the autotuner times, and the 8-CTA cluster
 sweep in a block solve on an 8^4 lattice.  An off-by-one write planted in a
 layout kernel is reported by this run."""
 import os
@@ -34,6 +35,8 @@ def test_library_under_address_sanitizer(asan_lib):
     so, runtime = asan_lib
     env = dict(os.environ, LD_PRELOAD=runtime, ASAN_OPTIONS="detect_leaks=0:halt_on_error=1:exitcode=23")
     env.pop("MBICG_SAP_FUSED", None)
+    env.pop("MBICG_AUTOTUNE", None)
+    env.pop("MBICG_TUNE_FILE", None)
     r = subprocess.run([sys.executable, EXERCISE, so], env=env, capture_output=True, text=True, timeout=900)
     report = r.stdout[-3000:] + r.stderr[-6000:]
     assert "AddressSanitizer" not in r.stderr, report
