@@ -21,8 +21,8 @@ cluster sweep and the multi-kernel path (per-column and block MR, FP64 and
 FP32), block solves with dummy columns and an initial guess, every launch
 configuration of the operator that the autotuner times, the request server
 (two solver slots on host threads, four clients submitting and waiting from
-host threads at once), and the 8-CTA cluster sweep alone and in a block
-solve on an 8^4 lattice.  Mistakes
+host threads at once), and the 8-CTA cluster sweep alone and
+(AddressSanitizer) in a block solve on an 8^4 lattice.  Mistakes
 planted in a copy of the sources were each reported: an off-by-one write and
 a misaligned float4 load in a layout kernel, and a removed barrier before a
 block reduction (a data race)."""
