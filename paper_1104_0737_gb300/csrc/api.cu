@@ -298,6 +298,11 @@ struct Solver {
     if ((rc = buf(c, "sm_M", 2 * MAXL * MAXL, &sm.M))) return rc;
     if ((rc = buf(c, "sm_norms", MAXL, &sm.norms))) return rc;
     if ((rc = buf(c, "sm_status", 1, &sm.status))) return rc;
+    if (autotune_enabled()) {
+      // the operator's launch shape, once per lattice, L and precision (before any capture)
+      tune_dslash<T>(ex, g, links_T(), k.U, k.V, L, kappa);
+      tune_dslash<double>(ex, g, c->U64, X64, W64, L, kappa);
+    }
     return MBICG_OK;
   }
 

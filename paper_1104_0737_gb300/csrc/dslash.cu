@@ -19,6 +19,7 @@
 #include <stdlib.h>
 
 #include "internal.h"
+#include "tune.h"
 
 namespace mbicg {
 
@@ -82,12 +83,28 @@ __device__ __forceinline__ void hopping(const Geom& g, const cx<R>* __restrict__
   hops_mu<R, DIRICHLET, 3>(g, links, in, L, rhs, s, c, lc, st3, acc);
 }
 
+// The order in which the CTAs of the operator walk the lattice.  A CTA takes a
+// segment of S consecutive sites; the segments are taken in slabs of tt time
+// slices with the time slice running fastest, so the CTAs that read a site as
+// a t +- 1 neighbour run close in time to the one that reads it as its own
+// site and the data is still in L2 (in lexicographic order they are a whole
+// time slice, ~40 MB at 32^3 x 64, L = 12, apart).  wslice = segments per time
+// slice; tt = 1 keeps the lexicographic order.
+__host__ __device__ __forceinline__ int segment_of(int b, int wslice, int tt) {
+  if (tt <= 1) return b;
+  const int per_slab = wslice * tt;
+  const int slab = b / per_slab, r = b - slab * per_slab;
+  const int w = r / tt, dt = r - w * tt;
+  return (slab * tt + dt) * wslice + w;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_dslash_full(Geom g, const cx<R>* __restrict__ links,
                                                      const cx<R>* __restrict__ in,
-                                                     cx<R>* __restrict__ out, int L, R kappa) {
+                                                     cx<R>* __restrict__ out, int L, R kappa, int wslice,
+                                                     int tt) {
   const int rhs = threadIdx.x;
-  const int s = blockIdx.x * blockDim.y + threadIdx.y;
+  const int s = segment_of(blockIdx.x, wslice, tt) * blockDim.y + threadIdx.y;
   if (s >= g.V) return;
   int c[4];
   site_coords(g, s, c);
@@ -658,14 +675,62 @@ int sap_sites_per_cta(const Geom& g, int L, bool fp64) {
   return S;
 }
 
+// one launch of the operator in configuration cfg (tune.h)
+template <typename R>
+void launch_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
+                   double kappa, DslashConfig cfg) {
+  const int S = cfg.S;
+  const dim3 block(L, S);
+  const int grid = (g.V + S - 1) / S;
+  const int slice = g.d[0] * g.d[1] * g.d[2];
+  const bool slabs = cfg.order == 1 && slice % S == 0 && g.d[3] % 8 == 0;
+  k_dslash_full<R><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa, slabs ? slice / S : 0,
+                                                             slabs ? 8 : 1);
+  ++*ex.launches;
+}
+
+// the configuration the tuner chose for this operator, else the default: the
+// most sites per CTA, in time slabs where they tile the time slices
+template <typename R>
+DslashConfig dslash_config(const Geom& g, int L) {
+  const std::vector<DslashConfig> cand = dslash_candidates(g.d, L, max_cta<R>());
+  int idx;
+  if (tune_table().lookup(dslash_key((int)sizeof(R), g.d, L), &idx) && idx >= 0 && idx < (int)cand.size())
+    return cand[idx];
+  return cand.size() > 1 && cand[1].S == cand[0].S ? cand[1] : cand[0];
+}
+
 template <typename R>
 void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
                  double kappa) {
-  const int S = pow2_floor(max_cta<R>() / L);
-  const dim3 block(L, S);
-  const int grid = (g.V + S - 1) / S;
-  k_dslash_full<R><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa);
-  ++*ex.launches;
+  launch_dslash<R>(ex, g, links, in, out, L, kappa, dslash_config<R>(g, L));
+}
+
+template <typename R>
+void tune_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
+                 double kappa) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ex.stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
+  const std::vector<DslashConfig> cand = dslash_candidates(g.d, L, max_cta<R>());
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return;
+  }
+  tune_table().pick(dslash_key((int)sizeof(R), g.d, L), (int)cand.size(), [&](int i) -> double {
+    cudaEventRecord(e0, ex.stream);
+    launch_dslash<R>(ex, g, links, in, out, L, kappa, cand[i]);
+    cudaEventRecord(e1, ex.stream);
+    float ms = -1.0f;
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      return -1.0;
+    return ms;
+  });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (const char* p = getenv("MBICG_TUNE_FILE")) tune_table().save(p);
 }
 
 template <typename R>
@@ -693,6 +758,7 @@ void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* li
 
 #define INST(R)                                                                                          \
   template void dslash_full<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double); \
+  template void tune_dslash<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double); \
   template void sap_residual<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, const cx<R>*,   \
                                 cx<R>*, int, double, bool);                                               \
   template void sap_domain_apply<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, cx<R>*,     \

@@ -91,6 +91,15 @@ struct Timed {
 template <typename R>
 void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out,
                  int L, double kappa);
+// Times the operator's launch configurations for this lattice, L and
+// precision once per process (in -> out, both overwritten-safe scratch for
+// out) and records the fastest for dslash_full; does nothing while the stream
+// is being captured or when the choice is already known.
+template <typename R>
+void tune_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
+                 double kappa);
+// the autotuner is on when MBICG_AUTOTUNE is set and not "0"
+bool autotune_enabled();
 
 // ABI blocks with dummy columns: the L columns of in into the first L of Lt
 // columns of out, the rest seeded Gaussian random numbers (random) or zeros;

@@ -201,7 +201,7 @@ def rewrite_launches(src):
 
 def driver_parts(csrc=CSRC):
     """The SAP driver (sap.cu) and everything it launches (dslash.cu), host
-    code included, for the threaded emulation: launches rewritten onto the
+    code included (with the autotuner's table, tune.cu), for the threaded emulation: launches rewritten onto the
     emulator, inline PTX helpers replaced, shared memory bound to the arenas."""
     common = read("common.cuh", csrc)
     common = replace_body(common, "__device__ __forceinline__ void load_spinor(const cx<float>* p, Spinor<float>& s)",
@@ -209,6 +209,8 @@ def driver_parts(csrc=CSRC):
     common = replace_body(common, "__device__ __forceinline__ void store_spinor(cx<float>* p, const Spinor<float>& s)",
                           "{ for (int k = 0; k < 12; ++k) p[k] = (&s.c[0][0])[k]; }")
     internal = read("internal.h", csrc).replace('#include "common.cuh"', "")
+    # the operator's launch configurations come from the autotuner's table (host code)
+    tune = read("tune.h", csrc) + "\n" + read("tune.cu", csrc).replace('#include "tune.h"', "")
     ds = read("dslash.cu", csrc)
     ds = ds[ds.index("namespace mbicg {"):]
     ds = replace_body(ds, "__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank)",
@@ -221,7 +223,7 @@ def driver_parts(csrc=CSRC):
     body, slots = bind_shared(body)
     return "\n".join([f"#define EMU_STATIC_SLOTS {max(slots, 1)}", '#include "shim_threads.h"',
                       "#include <algorithm>", "#include <cstdlib>", "#include <type_traits>",
-                      '#include "emu_runtime.h"', common, internal, body])
+                      '#include "emu_runtime.h"', common, internal, tune, body])
 
 
 INCLUDE = os.path.join(ROOT, "include")
@@ -238,7 +240,7 @@ def _patched_common(csrc):
     return common
 
 
-LIBRARY_SOURCES = ["api.cu", "dslash.cu", "sap.cu", "blas.cu", "half.cu", "serve.cu", "noalloc.cu", "selftest.cu"]
+LIBRARY_SOURCES = ["api.cu", "dslash.cu", "sap.cu", "blas.cu", "half.cu", "serve.cu", "noalloc.cu", "selftest.cu", "tune.cu"]
 
 
 def library_unit(name, csrc=CSRC):

@@ -47,10 +47,26 @@ static void grid(int n, int L, F body) {
 using C = cx<double>;
 
 extern "C" {
-void emu_dslash(const int* dims, const double* U, const double* in, double* out, int L, double kappa) {
+// the operator with the launch shape of the library: CTAs of S sites, walked
+// in time slabs where the library uses them
+void emu_dslash(const int* dims, const double* U, const double* in, double* out, int L, double kappa, int S,
+                int order) {
   const Geom g = make_geom(dims, nullptr);
-  grid(g.V, L, [&] { emu_dslash::k_dslash_full<double>(g, (const C*)U, (const C*)in, (C*)out, L, kappa); });
+  const int slice = g.d[0] * g.d[1] * g.d[2];
+  const bool slabs = order == 1 && slice % S == 0 && g.d[3] % 8 == 0;
+  const int nblk = (g.V + S - 1) / S;
+  blockDim = {(unsigned)L, (unsigned)S, 1};
+  gridDim = {(unsigned)nblk, 1, 1};
+  for (int b = 0; b < nblk; ++b)
+    for (int y = 0; y < S; ++y)
+      for (int r = 0; r < L; ++r) {
+        blockIdx = {(unsigned)b, 0, 0};
+        threadIdx = {(unsigned)r, (unsigned)y, 0};
+        emu_dslash::k_dslash_full<double>(g, (const C*)U, (const C*)in, (C*)out, L, kappa, slabs ? slice / S : 0,
+                                          slabs ? 8 : 1);
+      }
 }
+int emu_segment_of(int b, int wslice, int tt) { return emu_dslash::segment_of(b, wslice, tt); }
 int emu_nslot(const int* dims, const int* block) {
   const Geom g = make_geom(dims, block);
   return (g.nd / 2) * g.Vd;

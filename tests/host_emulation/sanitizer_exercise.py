@@ -127,6 +127,14 @@ def main(so, sanitizer):
     small.solve(3, b2, X=X, use_x0=1)
     small.close()
 
+    # every launch configuration of the operator the autotuner times (CTA
+    # sizes, lexicographic and time-slab order), on a lattice where the slabs apply
+    os.environ["MBICG_AUTOTUNE"] = "1"
+    tuned = Ctx(lib, (4, 4, 4, 8), seed=3)
+    tuned.solve(2, (2, 2, 2, 4), tol=1e-6)
+    tuned.close()
+    os.environ.pop("MBICG_AUTOTUNE")
+
     # the request server: two slots of one field, four clients on host threads
     srv = ctypes.c_void_p()
     assert lib.mbicg_server_create(ctypes.byref(srv), 0, 1.0) == mb.MBICG_OK

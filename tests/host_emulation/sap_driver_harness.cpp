@@ -21,6 +21,13 @@ extern "C" cudaError_t cudaGetLastError(void) { return cudaSuccess; }
 // per-kernel timing stays off in the emulation; these only satisfy the linker
 extern "C" cudaError_t cudaEventCreate(cudaEvent_t*) { return cudaErrorNotSupported; }
 extern "C" cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t) { return cudaErrorNotSupported; }
+extern "C" cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaErrorNotSupported; }
+extern "C" cudaError_t cudaEventElapsedTime(float*, cudaEvent_t, cudaEvent_t) { return cudaErrorNotSupported; }
+extern "C" cudaError_t cudaEventDestroy(cudaEvent_t) { return cudaSuccess; }
+extern "C" cudaError_t cudaStreamIsCapturing(cudaStream_t, enum cudaStreamCaptureStatus* st) {
+  *st = cudaStreamCaptureStatusNone;
+  return cudaSuccess;
+}
 extern "C" cudaError_t cudaMemcpyAsync(void* d, const void* s, size_t n, enum cudaMemcpyKind, cudaStream_t) {
   memmove(d, s, n);
   return cudaSuccess;

@@ -52,7 +52,8 @@ def emu(tmp_path_factory):
                     os.path.join(HERE, "harness.cpp"), "-o", str(lib_path)], check=True)
     lib = ctypes.CDLL(str(lib_path))
     D, I = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
-    lib.emu_dslash.argtypes = [I, D, D, D, ctypes.c_int, ctypes.c_double]
+    lib.emu_dslash.argtypes = [I, D, D, D, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    lib.emu_segment_of.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.emu_nslot.argtypes = [I, I]
     lib.emu_slot.argtypes = [I, I, ctypes.c_int, ctypes.c_int, I, I]
     lib.emu_sap_residual.argtypes = [I, I, D, ctypes.c_int, D, D, D, ctypes.c_int, ctypes.c_double, ctypes.c_int]
@@ -79,16 +80,52 @@ def _oracle_layout(a):
     return np.ascontiguousarray(a.transpose(0, 2, 1)).reshape(a.shape[0], 4, 3, -1)
 
 
-@pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 3), ((6, 2, 4, 10), 2), ((2, 2, 2, 2), 5), ((8, 4, 2, 6), 1)])
-def test_operator_kernel_matches_oracle(emu, oracle_mod, dims, L):
+@pytest.mark.parametrize("dims,L,S", [((4, 4, 4, 4), 3, 1), ((6, 2, 4, 10), 2, 4), ((2, 2, 2, 2), 5, 2),
+                                      ((8, 4, 2, 6), 1, 32), ((8, 4, 4, 16), 12, 32), ((8, 2, 2, 8), 4, 8)])
+def test_operator_kernel_matches_oracle(emu, oracle_mod, dims, L, S):
+    """S sites per CTA as the library launches it (time-slab order where the
+    segments tile the time slices: the last two cases)."""
     U = np.ascontiguousarray(synth.su3_links(dims, 0.5, seed=91))
     psi = synth.gaussian_source(dims, L, seed=92)
     kappa = 0.1375
     a = _internal(psi)
-    out = np.zeros_like(a)
-    emu.emu_dslash(_iv(dims), _dp(U), _dp(a), _dp(out), L, kappa)
+    out = np.full_like(a, np.nan)
+    emu.emu_dslash(_iv(dims), _dp(U), _dp(a), _dp(out), L, kappa, S, 1)
     ref = oracle_mod.apply_D(dims, U, kappa, psi)
     assert np.max(np.abs(_oracle_layout(out) - ref)) < 1e-14 * np.max(np.abs(ref))
+
+
+def test_operator_launch_configurations_are_bit_identical(emu, oracle_mod):
+    """Every configuration the autotuner may choose (sites per CTA, CTA order)
+    gives the same result bit for bit."""
+    dims, L = (8, 4, 4, 16), 3
+    U = np.ascontiguousarray(synth.su3_links(dims, 0.5, seed=99))
+    a = _internal(synth.gaussian_source(dims, L, seed=100))
+    outs = []
+    for S in (32, 16, 8):
+        for order in (0, 1):
+            out = np.full_like(a, np.nan)
+            emu.emu_dslash(_iv(dims), _dp(U), _dp(a), _dp(out), L, 0.13, S, order)
+            outs.append(out)
+    assert all(np.array_equal(o, outs[0]) for o in outs[1:])
+    ref = oracle_mod.apply_D(dims, U, 0.13, _oracle_layout(a))
+    assert np.max(np.abs(_oracle_layout(outs[0]) - ref)) < 1e-14 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("wslice,tt,nt", [(32, 8, 64), (1, 8, 16), (7, 8, 24), (5, 1, 3)])
+def test_segment_order_is_a_permutation_with_near_t_neighbours(emu, wslice, tt, nt):
+    """Every segment is taken once; within a slab a segment's t +- 1 neighbours
+    are taken within one slab's worth of CTAs of it."""
+    n = wslice * nt
+    seg = np.array([emu.emu_segment_of(b, wslice, tt) for b in range(n)])
+    assert sorted(seg) == list(range(n))
+    if tt > 1:
+        pos = np.empty(n, int)
+        pos[seg] = np.arange(n)
+        t, w = seg // wslice, seg % wslice
+        inner = (t % tt) != tt - 1                     # t + 1 in the same slab
+        nxt = (t + 1) * wslice + w
+        assert np.all(np.abs(pos[nxt[inner]] - pos[seg[inner]]) == 1)
 
 
 def _slots(emu, dims, block, colour):
