@@ -52,7 +52,7 @@ class mbicg_params(ctypes.Structure):
         ("mr_mode", ctypes.c_int), ("prec_sap", ctypes.c_int), ("prec_D", ctypes.c_int),
         ("max_iter", ctypes.c_int), ("use_x0", ctypes.c_int), ("delta_ru", ctypes.c_double),
         ("res_history", ctypes.POINTER(ctypes.c_double)), ("res_history_len", ctypes.c_int),
-        ("dummy_rhs", ctypes.c_int), ("dummy_seed", ctypes.c_ulonglong),
+        ("dummy_rhs", ctypes.c_int), ("dummy_seed", ctypes.c_ulonglong), ("clover", ctypes.c_int),
     ]
 
 
@@ -95,6 +95,8 @@ def load_library(build_if_missing: bool = True):
     lib.mbicg_destroy.restype = None
     lib.mbicg_load_gauge.argtypes = [vp, vp]
     lib.mbicg_apply_D.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    lib.mbicg_load_clover.argtypes = [vp, ctypes.c_double]
+    lib.mbicg_apply_clover.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]
     lib.mbicg_sap_precond.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double,
                                       ctypes.POINTER(mbicg_params)]
     lib.mbicg_block_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -184,6 +186,16 @@ def mbicg_apply_D(ctx, inp, out, L: int, kappa: float, prec: int = MBICG_FP64) -
     pi, _ = _ptr(inp, "in")
     po, _ = _ptr(out, "out")
     _check(ctx, load_library().mbicg_apply_D(ctx, pi, po, int(L), float(kappa), int(prec)))
+
+
+def mbicg_load_clover(ctx, csw: float) -> None:
+    _check(ctx, load_library().mbicg_load_clover(ctx, float(csw)))
+
+
+def mbicg_apply_clover(ctx, inp, out, L: int, kappa: float, prec: int = MBICG_FP64, jacobi: int = 0) -> None:
+    pi, _ = _ptr(inp, "in")
+    po, _ = _ptr(out, "out")
+    _check(ctx, load_library().mbicg_apply_clover(ctx, pi, po, int(L), float(kappa), int(prec), int(jacobi)))
 
 
 def mbicg_sap_precond(ctx, inp, out, L: int, kappa: float, params: mbicg_params) -> None:

@@ -48,6 +48,14 @@ struct mbicg_ctx {
   Prof prof;
   std::map<std::string, std::pair<void*, size_t>> bufs;  // device workspaces
   double* h_small = nullptr;                            // pinned host scratch
+  // clover term (clover.cu): C packed per site in FP64 and FP32, T^{-1} for
+  // the kappa tinv_kappa (NaN: not formed); csw == 0: no clover term
+  double csw = 0.0;
+  double* C64 = nullptr;
+  float* C32 = nullptr;
+  double* Ti64 = nullptr;
+  float* Ti32 = nullptr;
+  double tinv_kappa = NAN;
 };
 
 namespace {
@@ -245,12 +253,20 @@ struct Solver {
   bool keep_table = false;  // continue with the frozen step lengths already recorded
   int Lc = 0;               // columns the stopping test covers (the others are dummies)
   SmallWork sm{};
+  // Jacobi-preconditioned clover matrix: T^{-1} per site (NULL: Wilson)
+  const double* ti64 = nullptr;
+  const float* ti32 = nullptr;
   double *gpart, *npart;
   double h_norm[MAXL + 1];
   double bnorm[MAXL];
 
   const cx<T>* links_T() const;
   const cx<TS>* links_S() const;
+  template <typename R>
+  const R* tinv() const {
+    return reinterpret_cast<const R*>(sizeof(R) == 8 ? static_cast<const void*>(ti64)
+                                                     : static_cast<const void*>(ti32));
+  }
 
   int alloc() {
     int rc;
@@ -313,13 +329,13 @@ struct Solver {
       if (!table_complete) CK(cudaMemsetAsync(unset, 0, sizeof(int), c->stream));
     }
     if constexpr (std::is_same<T, TS>::value) {
-      sap_apply<TS>(ex, g, links_S(), in, out, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw);
+      sap_apply<TS>(ex, g, links_S(), in, out, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw, tinv<TS>());
     } else {
       {
         Timed t(ex, KC_CONVERT);
         convert_block<T, TS>(ex, (long long)nl, in, eta_s);
       }
-      sap_apply<TS>(ex, g, links_S(), eta_s, psi_s, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw);
+      sap_apply<TS>(ex, g, links_S(), eta_s, psi_s, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw, tinv<TS>());
       Timed t(ex, KC_CONVERT);
       convert_block<TS, T>(ex, (long long)nl, psi_s, out);
     }
@@ -335,7 +351,7 @@ struct Solver {
 
   int dslash(const cx<T>* in, cx<T>* out) {
     Timed t(ex, KC_DSLASH);
-    dslash_full<T>(ex, g, links_T(), in, out, L, kappa);
+    dslash_full<T>(ex, g, links_T(), in, out, L, kappa, tinv<T>(), ti64 ? 1 : 0);
     return MBICG_OK;
   }
 
@@ -344,7 +360,7 @@ struct Solver {
   int true_residual(double* rel, double* relmax, bool x_zero = false) {
     if (!x_zero) {
       Timed t(ex, KC_DSLASH64);
-      dslash_full<double>(ex, g, c->U64, X64, W64, L, kappa);
+      dslash_full<double>(ex, g, c->U64, X64, W64, L, kappa, ti64, ti64 ? 1 : 0);
     }
     int np;
     {
@@ -622,6 +638,8 @@ int check_params(mbicg_ctx* c, int L, const mbicg_params* p, bool solve) {
   if (!p) return fail(c, MBICG_EINVAL, "params is NULL");
   if (solve && (p->dummy_rhs < 0 || L + p->dummy_rhs > MAXL))
     return fail(c, MBICG_EINVAL, "dummy_rhs must be >= 0 with L + dummy_rhs <= 16");
+  if (p->clover != 0 && p->clover != 1) return fail(c, MBICG_EINVAL, "clover must be 0 or 1");
+  if (p->clover && !(c->csw > 0)) return fail(c, MBICG_EINVAL, "no clover term loaded");
   if (p->ncycle < 0 || p->ncycle > 64) return fail(c, MBICG_EINVAL, "ncycle out of range");
   if (p->ncycle > 0) {
     if (p->nmr < 1 || p->nmr > 256) return fail(c, MBICG_EINVAL, "nmr must be in [1, 256]");
@@ -655,8 +673,38 @@ int run_solve(mbicg_ctx* c, const cx<double>* dB, cx<double>* dX, int L, double 
   s.kappa = kappa;
   s.p = *p;
   s.V = c->V;
+  if (p->clover) {
+    s.ti64 = c->Ti64;
+    s.ti32 = c->Ti32;
+  }
   for (int i = 0; i < L; ++i) s.bnorm[i] = bnorm[i];
   return s.run(dB, dX, tol, iters, true_res);
+}
+
+// T^{-1} = (1 + kappa C)^{-1} of the loaded clover term, formed when kappa changes
+int clover_for_kappa(mbicg_ctx* c, double kappa) {
+  if (!(c->csw > 0)) return fail(c, MBICG_EINVAL, "no clover term loaded");
+  if (c->tinv_kappa == kappa) return MBICG_OK;
+  int* st;
+  int rc;
+  if ((rc = buf(c, "clover_status", 1, &st))) return rc;
+  CK(cudaMemsetAsync(st, 0, sizeof(int), c->stream));
+  const Exec ex = exec_of(c);
+  {
+    Timed t(ex, KC_CONVERT);
+    clover_terms(ex, c->V, c->C64, kappa, c->Ti64, c->Ti32, c->C32, st);
+  }
+  if ((rc = check_launch(c, "clover_terms"))) return rc;
+  CK(cudaMemcpyAsync(c->h_small, st, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int bad = 0;
+  memcpy(&bad, c->h_small, sizeof(int));
+  if (bad) {
+    c->tinv_kappa = NAN;
+    return fail(c, MBICG_EINVAL, "1 + kappa C is singular at some site");
+  }
+  c->tinv_kappa = kappa;
+  return MBICG_OK;
 }
 
 }  // namespace
@@ -736,6 +784,10 @@ void mbicg_destroy(mbicg_ctx* c) {
   if (c->U64) cudaFree(c->U64);
   if (c->U32) cudaFree(c->U32);
   if (c->U16) cudaFree(c->U16);
+  if (c->C64) cudaFree(c->C64);
+  if (c->C32) cudaFree(c->C32);
+  if (c->Ti64) cudaFree(c->Ti64);
+  if (c->Ti32) cudaFree(c->Ti32);
   c->prof.release();
   if (c->h_small) cudaFreeHost(c->h_small);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -748,6 +800,8 @@ int mbicg_load_gauge(mbicg_ctx* c, const double* U) {
   if (!U) return fail(c, MBICG_EINVAL, "U is NULL");
   CK(cudaSetDevice(c->device));
   c->launches = 0;
+  c->csw = 0.0;  // a clover term belongs to the previous field
+  c->tinv_kappa = NAN;
   const size_t n = (size_t)c->V * 36;  // complex numbers
   if (!c->U64) CK(cudaMalloc(&c->U64, sizeof(cx<double>) * n));
   if (!c->U32) CK(cudaMalloc(&c->U32, sizeof(cx<float>) * n));
@@ -850,6 +904,87 @@ int mbicg_apply_D(mbicg_ctx* c, const double* in, double* out, int L, double kap
   return MBICG_OK;
 }
 
+int mbicg_load_clover(mbicg_ctx* c, double csw) {
+  if (!c) return MBICG_EINVAL;
+  c->err.clear();
+  if (!(csw >= 0) || !isfinite(csw)) return fail(c, MBICG_EINVAL, "csw must be finite and >= 0");
+  if (!c->gauge) return fail(c, MBICG_ENOGAUGE, "no gauge field loaded");
+  CK(cudaSetDevice(c->device));
+  c->launches = 0;
+  c->tinv_kappa = NAN;
+  c->csw = 0.0;
+  if (csw == 0) return MBICG_OK;
+  const size_t n = (size_t)c->V * HERM_PER_SITE;
+  if (!c->C64) CK(cudaMalloc(&c->C64, sizeof(double) * n));
+  if (!c->C32) CK(cudaMalloc(&c->C32, sizeof(float) * n));
+  if (!c->Ti64) CK(cudaMalloc(&c->Ti64, sizeof(double) * n));
+  if (!c->Ti32) CK(cudaMalloc(&c->Ti32, sizeof(float) * n));
+  const Exec ex = exec_of(c);
+  {
+    Timed t(ex, KC_CONVERT);
+    clover_field(ex, lattice_geom(c, nullptr), c->U64, csw, c->C64);
+  }
+  int rc;
+  if ((rc = check_launch(c, "load_clover"))) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  c->prof.collect();
+  c->csw = csw;
+  c->stats.kernel_launches = c->launches;
+  return MBICG_OK;
+}
+
+int mbicg_apply_clover(mbicg_ctx* c, const double* in, double* out, int L, double kappa, int prec, int jacobi) {
+  if (!c) return MBICG_EINVAL;
+  c->err.clear();
+  if (!in || !out || in == out) return fail(c, MBICG_EINVAL, "in/out NULL or aliased");
+  if (L < 1 || L > MAXL) return fail(c, MBICG_EINVAL, "L must be in [1, 16]");
+  if (prec != MBICG_FP64 && prec != MBICG_FP32) return fail(c, MBICG_EINVAL, "prec must be FP64 or FP32");
+  if (jacobi != 0 && jacobi != 1) return fail(c, MBICG_EINVAL, "jacobi must be 0 or 1");
+  if (!c->gauge) return fail(c, MBICG_ENOGAUGE, "no gauge field loaded");
+  CK(cudaSetDevice(c->device));
+  c->launches = 0;
+  int rc;
+  if ((rc = clover_for_kappa(c, kappa))) return rc;
+  const size_t nl = (size_t)c->V * 12 * L;
+  Staged si, so;
+  if ((rc = stage_in(c, in, sizeof(cx<double>) * nl, "abi_in", true, &si))) return rc;
+  if ((rc = stage_in(c, out, sizeof(cx<double>) * nl, "abi_out", false, &so))) return rc;
+  const Exec ex = exec_of(c);
+  const Geom g = lattice_geom(c, nullptr);
+  const int cm = jacobi ? 1 : 2;
+  if (prec == MBICG_FP64) {
+    cx<double>*a, *b;
+    if ((rc = buf(c, "op64_a", nl, &a)) || (rc = buf(c, "op64_b", nl, &b))) return rc;
+    {
+      Timed t(ex, KC_CONVERT);
+      abi_to_internal<double>(ex, c->V, L, static_cast<const cx<double>*>(si.dev), a);
+    }
+    {
+      Timed t(ex, KC_DSLASH64);
+      dslash_full<double>(ex, g, c->U64, a, b, L, kappa, jacobi ? c->Ti64 : c->C64, cm);
+    }
+    Timed t(ex, KC_CONVERT);
+    internal_to_abi<double>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
+  } else {
+    cx<float>*a, *b;
+    if ((rc = buf(c, "op32_a", nl, &a)) || (rc = buf(c, "op32_b", nl, &b))) return rc;
+    {
+      Timed t(ex, KC_CONVERT);
+      abi_to_internal<float>(ex, c->V, L, static_cast<const cx<double>*>(si.dev), a);
+    }
+    {
+      Timed t(ex, KC_DSLASH);
+      dslash_full<float>(ex, g, c->U32, a, b, L, kappa, jacobi ? c->Ti32 : c->C32, cm);
+    }
+    Timed t(ex, KC_CONVERT);
+    internal_to_abi<float>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
+  }
+  if ((rc = check_launch(c, "apply_clover"))) return rc;
+  if ((rc = stage_out(c, so))) return rc;
+  c->stats.kernel_launches = c->launches;
+  return MBICG_OK;
+}
+
 int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double kappa, const mbicg_params* p) {
   if (!c) return MBICG_EINVAL;
   c->err.clear();
@@ -860,6 +995,7 @@ int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double
   if (!c->gauge) return fail(c, MBICG_ENOGAUGE, "no gauge field loaded");
   CK(cudaSetDevice(c->device));
   c->launches = 0;
+  if (p->clover && (rc = clover_for_kappa(c, kappa))) return rc;
   const size_t nl = (size_t)c->V * 12 * L;
   Staged si, so;
   if ((rc = stage_in(c, in, sizeof(cx<double>) * nl, "abi_in", true, &si))) return rc;
@@ -887,7 +1023,10 @@ int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double
       Timed t(ex, KC_CONVERT);
       abi_to_internal<R>(ex, c->V, L, static_cast<const cx<double>*>(si.dev), a);
     }
-    sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, p->mr_mode, nullptr, nullptr, w);
+    const R* tinv = nullptr;
+    if (p->clover) tinv = reinterpret_cast<const R*>(sizeof(R) == 8 ? static_cast<const void*>(c->Ti64)
+                                                                     : static_cast<const void*>(c->Ti32));
+    sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, p->mr_mode, nullptr, nullptr, w, tinv);
     Timed t(ex, KC_CONVERT);
     internal_to_abi<R>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
     return MBICG_OK;
@@ -930,6 +1069,17 @@ int mbicg_block_solve(mbicg_ctx* c, const double* B, double* X, int L, double ka
   }
   const cx<double>* dB = static_cast<const cx<double>*>(sb.dev);
   cx<double>* dX = static_cast<cx<double>*>(sx.dev);
+  if (p->clover) {
+    // D_c X = B is solved as A X = T^{-1} B with A = T^{-1} D_c
+    if ((rc = clover_for_kappa(c, kappa))) return rc;
+    cx<double>* Bc;
+    if ((rc = buf(c, "clover_B", nl, &Bc))) return rc;
+    clover_abi(exec_of(c), c->V, L, c->Ti64, dB, Bc);
+    if ((rc = abi_norms(c, Bc, L, bnorm, &bad))) return rc;
+    for (int i = 0; i < L; ++i)
+      if (!(bnorm[i] > 0)) return fail(c, MBICG_EINVAL, "T^{-1} B has a zero column");
+    dB = Bc;
+  }
   // dummy right-hand sides: solve the block widened by seeded Gaussian
   // columns; the stopping test and the results cover the first L columns
   const int Lt = L + p->dummy_rhs;

@@ -82,10 +82,35 @@ __device__ __forceinline__ void hopping(const Geom& g, const cx<R>* __restrict__
   hops_mu<R, DIRICHLET, 3>(g, links, in, L, rhs, s, c, lc, st3, acc);
 }
 
-template <typename R>
+// Clover variants of the operator (clover.cu): CM = 0 the Wilson matrix,
+// CM = 1 the Jacobi-preconditioned A = 1 - kappa M H with M = T^{-1},
+// CM = 2 D_c = 1 + kappa M - kappa H with M = C (M packed per site).
+template <typename R, int CM>
+__device__ __forceinline__ void finish_site(const R* __restrict__ clov, int s, R kappa, const Spinor<R>& p,
+                                            Spinor<R>& acc) {
+  if (CM == 1) {
+    Spinor<R> h;
+    herm_apply<R>(clov + (size_t)s * HERM_PER_SITE, acc, h);
+    acc = h;
+  } else if (CM == 2) {
+    Spinor<R> cp;
+    herm_apply<R>(clov + (size_t)s * HERM_PER_SITE, p, cp);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) (&acc.c[0][0])[k] = (&acc.c[0][0])[k] - (&cp.c[0][0])[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    cx<R>& o = (&acc.c[0][0])[k];
+    const cx<R> v = (&p.c[0][0])[k];
+    o = mk(fma(-kappa, o.re, v.re), fma(-kappa, o.im, v.im));
+  }
+}
+
+template <typename R, int CM>
 __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_dslash_full(Geom g, const cx<R>* __restrict__ links,
                                                      const cx<R>* __restrict__ in,
-                                                     cx<R>* __restrict__ out, int L, R kappa) {
+                                                     cx<R>* __restrict__ out, int L, R kappa,
+                                                     const R* __restrict__ clov) {
   const int rhs = threadIdx.x;
   const int s = blockIdx.x * blockDim.y + threadIdx.y;
   if (s >= g.V) return;
@@ -95,22 +120,17 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_dslash_full(Geo
   hopping<R, false>(g, links, in, L, rhs, s, c, c, acc);
   Spinor<R> p;
   load_spinor(in + spinor_offset(s, L, rhs), p);
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    cx<R>& o = (&acc.c[0][0])[k];
-    const cx<R> v = (&p.c[0][0])[k];
-    o = mk(fma(-kappa, o.re, v.re), fma(-kappa, o.im, v.im));
-  }
+  finish_site<R, CM>(clov, s, kappa, p, acc);
   store_spinor(out + spinor_offset(s, L, rhs), acc);
 }
 
-template <typename R>
+template <typename R, int CM>
 __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Geom g, int colour,
                                                       const cx<R>* __restrict__ links,
                                                       const cx<R>* __restrict__ eta,
                                                       const cx<R>* __restrict__ psi,
                                                       cx<R>* __restrict__ r, int L, R kappa,
-                                                      int psi_zero) {
+                                                      int psi_zero, const R* __restrict__ clov) {
   const int rhs = threadIdx.x;
   const int slot = blockIdx.x * blockDim.y + threadIdx.y;
   int c[4], lc[4], k;
@@ -121,6 +141,11 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Ge
   if (!psi_zero) {
     Spinor<R> acc, p;
     hopping<R, false>(g, links, psi, L, rhs, s, c, c, acc);
+    if (CM == 1) {  // A = 1 - kappa T^{-1} H
+      Spinor<R> h;
+      herm_apply<R>(clov + (size_t)s * HERM_PER_SITE, acc, h);
+      acc = h;
+    }
     load_spinor(psi + spinor_offset(s, L, rhs), p);
     // r = eta - (psi - kappa eta_hop) = eta - psi + kappa eta_hop
 #pragma unroll
@@ -133,13 +158,13 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Ge
   store_spinor(r + spinor_offset(s, L, rhs), e);
 }
 
-template <typename R>
+template <typename R, int CM>
 __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_domain_apply(Geom g, int colour,
                                                           const cx<R>* __restrict__ links,
                                                           const cx<R>* __restrict__ r,
                                                           cx<R>* __restrict__ q,
                                                           double* __restrict__ dots, int L, R kappa,
-                                                          int nchunk) {
+                                                          int nchunk, const R* __restrict__ clov) {
   extern __shared__ unsigned char smem_raw[];
   R* red = reinterpret_cast<R*>(smem_raw);  // [3][S][L]
   const int rhs = threadIdx.x;
@@ -150,6 +175,11 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_domain_appl
   const int s = site_index(g, c);
   Spinor<R> acc, p;
   hopping<R, true>(g, links, r, L, rhs, s, c, lc, acc);
+  if (CM == 1) {  // A_dom = 1 - kappa T^{-1} H_dom
+    Spinor<R> h;
+    herm_apply<R>(clov + (size_t)s * HERM_PER_SITE, acc, h);
+    acc = h;
+  }
   load_spinor(r + spinor_offset(s, L, rhs), p);
   R nre = 0, nim = 0, den = 0;
 #pragma unroll
@@ -660,43 +690,57 @@ int sap_sites_per_cta(const Geom& g, int L, bool fp64) {
 
 template <typename R>
 void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
-                 double kappa) {
+                 double kappa, const R* clov, int cm) {
   const int S = pow2_floor(max_cta<R>() / L);
   const dim3 block(L, S);
   const int grid = (g.V + S - 1) / S;
-  k_dslash_full<R><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa);
+  if (cm == 1)
+    k_dslash_full<R, 1><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa, clov);
+  else if (cm == 2)
+    k_dslash_full<R, 2><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa, clov);
+  else
+    k_dslash_full<R, 0><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa, nullptr);
   ++*ex.launches;
 }
 
 template <typename R>
 void sap_residual(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* eta,
-                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero) {
+                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero, const R* tinv) {
   const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
   const int nslot = (g.nd / 2) * g.Vd;
-  k_sap_residual<R><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, psi, r, L,
-                                                                          (R)kappa, psi_zero ? 1 : 0);
+  if (tinv)
+    k_sap_residual<R, 1><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, psi, r, L,
+                                                                               (R)kappa, psi_zero ? 1 : 0, tinv);
+  else
+    k_sap_residual<R, 0><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, psi, r, L,
+                                                                               (R)kappa, psi_zero ? 1 : 0, nullptr);
   ++*ex.launches;
 }
 
 template <typename R>
 void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* r,
-                      cx<R>* q, double* dots, int L, double kappa, int* nchunk_out) {
+                      cx<R>* q, double* dots, int L, double kappa, int* nchunk_out, const R* tinv) {
   const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
   const int nchunk = g.Vd / S;
   const int nslot = (g.nd / 2) * g.Vd;
   const size_t shm = dots ? sizeof(R) * 3 * S * L : 0;
-  k_sap_domain_apply<R><<<(unsigned)(nslot / S), dim3(L, S), shm, ex.stream>>>(g, colour, links, r, q, dots,
-                                                                               L, (R)kappa, nchunk);
+  if (tinv)
+    k_sap_domain_apply<R, 1><<<(unsigned)(nslot / S), dim3(L, S), shm, ex.stream>>>(g, colour, links, r, q, dots,
+                                                                                    L, (R)kappa, nchunk, tinv);
+  else
+    k_sap_domain_apply<R, 0><<<(unsigned)(nslot / S), dim3(L, S), shm, ex.stream>>>(g, colour, links, r, q, dots,
+                                                                                    L, (R)kappa, nchunk, nullptr);
   ++*ex.launches;
   if (nchunk_out) *nchunk_out = nchunk;
 }
 
 #define INST(R)                                                                                          \
-  template void dslash_full<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double); \
+  template void dslash_full<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double,  \
+                               const R*, int);                                                          \
   template void sap_residual<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, const cx<R>*,   \
-                                cx<R>*, int, double, bool);                                               \
+                                cx<R>*, int, double, bool, const R*);                                     \
   template void sap_domain_apply<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, cx<R>*,     \
-                                    double*, int, double, int*);
+                                    double*, int, double, int*, const R*);
 INST(float)
 INST(double)
 #undef INST

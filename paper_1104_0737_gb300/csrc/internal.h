@@ -4,6 +4,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -83,9 +84,22 @@ struct Timed {
 // Wilson-Dirac operator (dslash.cu), Sec. 2.1
 // ---------------------------------------------------------------------------
 // out = in - kappa * H in on every site, L columns.
+// With clov != NULL: cm = 1 the Jacobi-preconditioned clover matrix
+// out = in - kappa T^{-1} H in (clov = T^{-1}), cm = 2 the clover matrix
+// out = in + kappa C in - kappa H in (clov = C); packed per site (herm_off).
 template <typename R>
 void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out,
-                 int L, double kappa);
+                 int L, double kappa, const R* clov = nullptr, int cm = 0);
+
+// Clover term (clover.cu), Sec. 2.2: C = i c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}
+// per site from the FP64 links (packed, 72 doubles per site); for one kappa
+// T^{-1} = (1 + kappa C)^{-1} in FP64 and FP32 and C in FP32 (bit 0 of *status
+// set if a block is singular); out = M in for a packed M on an ABI-layout
+// FP64 block (in and out may alias).
+void clover_field(const Exec& ex, const Geom& g, const cx<double>* U64, double csw, double* C64);
+void clover_terms(const Exec& ex, long long nsite, const double* C64, double kappa, double* Ti64, float* Ti32,
+                  float* C32, int* status);
+void clover_abi(const Exec& ex, long long nsite, int L, const double* M, const cx<double>* in, cx<double>* out);
 
 // ABI blocks with dummy columns: the L columns of in into the first L of Lt
 // columns of out, the rest seeded Gaussian random numbers (random) or zeros;
@@ -110,15 +124,16 @@ void dslash_half(const Exec& ex, const Geom& g, const __half2* l16, const __half
 // SAP pieces on the sites of the domains of one colour (the slot numbering of
 // colour_slot_coords; arrays are full-lattice, in the internal layout).
 //   r = eta - (psi - kappa H psi)   (psi_zero: r = eta)
+//   (tinv != NULL: the Jacobi-preconditioned clover matrix, H -> T^{-1} H)
 template <typename R>
 void sap_residual(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* eta,
-                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero);
+                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero, const R* tinv = nullptr);
 //   q = r - kappa H_dom r  (hops leaving the domain dropped) and, if dots is
 //   not NULL, per-CTA partial sums of q^H r and q^H q for every column:
 //   dots[((k * nchunk) + chunk) * L + rhs] = {Re q^H r, Im q^H r, q^H q}
 template <typename R>
 void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* r,
-                      cx<R>* q, double* dots, int L, double kappa, int* nchunk_out);
+                      cx<R>* q, double* dots, int L, double kappa, int* nchunk_out, const R* tinv = nullptr);
 // One whole colour sweep (residual, nmr MR steps, psi += x) in one kernel,
 // the domain kept on chip by a thread-block cluster; FP32, MR modes 0 and 2,
 // domain shapes 8^4 and 4^4.  Returns false (nothing launched) otherwise.
@@ -151,10 +166,12 @@ struct SapWork {
 // the shared sums where the domain's residual is nonzero; *unset is raised if
 // an entry stays unrecorded), 3 frozen replay.
 // table = complex [ncycle][2][nmr][nd/2] (modes 2, 3).
+// tinv != NULL: SAP for the Jacobi-preconditioned clover matrix (multi-kernel
+// path; the fused sweep has no clover term).
 template <typename R>
 void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* eta, cx<R>* psi,
                int L, double kappa, int ncycle, int nmr, int mr_mode, double* table, int* unset,
-               SapWork& w);
+               SapWork& w, const R* tinv = nullptr);
 
 // ---------------------------------------------------------------------------
 // Block linear algebra (blas.cu)

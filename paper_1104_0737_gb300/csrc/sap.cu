@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(512) k_mr_update(Geom g, int colour, const dou
 
 template <typename R>
 void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* eta, cx<R>* psi, int L,
-               double kappa, int ncycle, int nmr, int mr_mode, double* table, int* unset, SapWork& w) {
+               double kappa, int ncycle, int nmr, int mr_mode, double* table, int* unset, SapWork& w,
+               const R* tinv) {
   cx<R>* r = static_cast<cx<R>*>(w.r);
   cx<R>* q = static_cast<cx<R>*>(w.q);
   cx<R>* x = static_cast<cx<R>*>(w.x);
@@ -130,7 +131,7 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
   for (int cyc = 0; cyc < ncycle; ++cyc) {
     for (int colour = 0; colour < 2; ++colour) {
       if constexpr (std::is_same<R, float>::value) {
-        if (allow_fused && (mr_mode == 0 || mr_mode == 3)) {
+        if (allow_fused && !tinv && (mr_mode == 0 || mr_mode == 3)) {
           const double* tab = table ? table + ((long long)cyc * 2 + colour) * nmr * ndc * 2 : nullptr;
           Timed t(ex, KC_SAP_SWEEP);
           if (sap_sweep_fused(ex, g, colour, links, eta, psi, L, kappa, cyc == 0 && colour == 0, nmr, mr_mode, tab))
@@ -139,7 +140,7 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
       }
       {
         Timed t(ex, KC_SAP_RESID);
-        sap_residual<R>(ex, g, colour, links, eta, psi, r, L, kappa, cyc == 0 && colour == 0);
+        sap_residual<R>(ex, g, colour, links, eta, psi, r, L, kappa, cyc == 0 && colour == 0, tinv);
       }
       for (int it = 0; it < nmr; ++it) {
         const bool need_dots = (mr_mode != 3);
@@ -147,7 +148,7 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
         // replaying frozen step lengths, the last step needs no A_dom r: only x + omega r
         if (need_dots || it < nmr - 1) {
           Timed t(ex, KC_SAP_DOMAIN);
-          sap_domain_apply<R>(ex, g, colour, links, r, q, need_dots ? w.dots : nullptr, L, kappa, &nchunk);
+          sap_domain_apply<R>(ex, g, colour, links, r, q, need_dots ? w.dots : nullptr, L, kappa, &nchunk, tinv);
         }
         Timed t(ex, KC_SAP_UPDATE);
         double* tab = table ? table + (((long long)cyc * 2 + colour) * nmr + it) * ndc * 2 : nullptr;
@@ -162,8 +163,8 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
 }
 
 template void sap_apply<float>(const Exec&, const Geom&, const cx<float>*, const cx<float>*, cx<float>*, int,
-                               double, int, int, int, double*, int*, SapWork&);
+                               double, int, int, int, double*, int*, SapWork&, const float*);
 template void sap_apply<double>(const Exec&, const Geom&, const cx<double>*, const cx<double>*, cx<double>*,
-                                int, double, int, int, int, double*, int*, SapWork&);
+                                int, double, int, int, int, double*, int*, SapWork&, const double*);
 
 }  // namespace mbicg
