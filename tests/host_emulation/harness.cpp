@@ -1,4 +1,4 @@
-// Host emulation of the library's FP64 operator and SAP kernels: every kernel
+// Host emulation of the library's FP64 operator, SAP and clover kernels: every kernel
 // body runs once per emulated (block, thread) in order.  device_parts.inc is
 // cut out of the CUDA sources by the test (kernels and device helpers, no
 // launches).
@@ -45,9 +45,32 @@ static void grid(int n, int L, F body) {
 using C = cx<double>;
 
 extern "C" {
-void emu_dslash(const int* dims, const double* U, const double* in, double* out, int L, double kappa) {
+// cm: 0 Wilson, 1 Jacobi-preconditioned clover (clov = T^{-1}), 2 clover (clov = C)
+void emu_dslash(const int* dims, const double* U, const double* in, double* out, int L, double kappa,
+                const double* clov, int cm) {
   const Geom g = make_geom(dims, nullptr);
-  grid(g.V, L, [&] { emu_dslash::k_dslash_full<double>(g, (const C*)U, (const C*)in, (C*)out, L, kappa); });
+  grid(g.V, L, [&] {
+    if (cm == 1) emu_dslash::k_dslash_full<double, 1>(g, (const C*)U, (const C*)in, (C*)out, L, kappa, clov);
+    else if (cm == 2) emu_dslash::k_dslash_full<double, 2>(g, (const C*)U, (const C*)in, (C*)out, L, kappa, clov);
+    else emu_dslash::k_dslash_full<double, 0>(g, (const C*)U, (const C*)in, (C*)out, L, kappa, nullptr);
+  });
+}
+void emu_clover_field(const int* dims, const double* U, double csw, double* Cl) {
+  const Geom g = make_geom(dims, nullptr);
+  grid(1, 1, [&] { emu_clover::k_clover_field(g, (const C*)U, csw, Cl); });  // grid-stride loop over sites
+}
+int emu_clover_terms(long long nsite, const double* Cl, double kappa, double* Ti64, float* Ti32, float* C32) {
+  int status = 0;
+  grid(1, 1, [&] { emu_clover::k_clover_terms(2 * nsite, Cl, kappa, Ti64, Ti32, C32, &status); });
+  return status;
+}
+void emu_clover_abi(long long nsite, int L, const double* M, const double* in, double* out) {
+  blockDim = {256, 1, 1};
+  for (long long idx = 0; idx < nsite * L; ++idx) {
+    blockIdx = {(unsigned)(idx / 256), 0, 0};
+    threadIdx = {(unsigned)(idx % 256), 0, 0};
+    emu_clover::k_clover_abi(nsite, L, M, (const C*)in, (C*)out);
+  }
 }
 int emu_nslot(const int* dims, const int* block) {
   const Geom g = make_geom(dims, block);
@@ -60,18 +83,27 @@ void emu_slot(const int* dims, const int* block, int colour, int slot, int* site
   *site = site_index(g, c);
 }
 void emu_sap_residual(const int* dims, const int* block, const double* U, int colour, const double* eta,
-                      const double* psi, double* r, int L, double kappa, int psi_zero) {
+                      const double* psi, double* r, int L, double kappa, int psi_zero, const double* tinv) {
   const Geom g = make_geom(dims, block);
   grid((g.nd / 2) * g.Vd, L, [&] {
-    emu_dslash::k_sap_residual<double>(g, colour, (const C*)U, (const C*)eta, (const C*)psi, (C*)r, L, kappa,
-                                       psi_zero);
+    if (tinv)
+      emu_dslash::k_sap_residual<double, 1>(g, colour, (const C*)U, (const C*)eta, (const C*)psi, (C*)r, L, kappa,
+                                            psi_zero, tinv);
+    else
+      emu_dslash::k_sap_residual<double, 0>(g, colour, (const C*)U, (const C*)eta, (const C*)psi, (C*)r, L, kappa,
+                                            psi_zero, nullptr);
   });
 }
 void emu_sap_domain_apply(const int* dims, const int* block, const double* U, int colour, const double* r,
-                          double* q, int L, double kappa) {
+                          double* q, int L, double kappa, const double* tinv) {
   const Geom g = make_geom(dims, block);
   grid((g.nd / 2) * g.Vd, L, [&] {
-    emu_dslash::k_sap_domain_apply<double>(g, colour, (const C*)U, (const C*)r, (C*)q, nullptr, L, kappa, 1);
+    if (tinv)
+      emu_dslash::k_sap_domain_apply<double, 1>(g, colour, (const C*)U, (const C*)r, (C*)q, nullptr, L, kappa, 1,
+                                                tinv);
+    else
+      emu_dslash::k_sap_domain_apply<double, 0>(g, colour, (const C*)U, (const C*)r, (C*)q, nullptr, L, kappa, 1,
+                                                nullptr);
   });
 }
 void emu_mr_update(const int* dims, const int* block, int colour, const double* omega, double* r, const double* q,
