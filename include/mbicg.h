@@ -49,6 +49,9 @@ typedef enum {
   MBICG_ECUDA = -7        /* a CUDA runtime error; see mbicg_last_error */
 } mbicg_status;
 
+/* SAP domain solvers. */
+typedef enum { MBICG_DOMAIN_MR = 0, MBICG_DOMAIN_SSOR = 1 } mbicg_domain_solver;
+
 /* Arithmetic and storage precision of an operator. */
 typedef enum { MBICG_FP64 = 0, MBICG_FP32 = 1, MBICG_FP16 = 2 } mbicg_prec;
 
@@ -101,6 +104,15 @@ typedef struct {
    * stopping test refer to that system), mbicg_sap_precond preconditions A.
    * Default 0 (the Wilson matrix). */
   int clover;
+  /* SAP domain solver (Sec. 2.2): MBICG_DOMAIN_MR (default: nmr minimal-
+   * residual steps, mr_mode) or MBICG_DOMAIN_SSOR: the paper's SSOR
+   * approximation B = (1 - omega U)^{-1} [sum_{j=0}^{nssor} (1 - A^SSOR)^j]
+   * (1 - omega L)^{-1} on each domain (L, U the forward and backward hops
+   * inside the domain), a fixed linear operator.  0 <= nssor <= 16,
+   * 0 < ssor_omega < 2; defaults 1 and 1.26 (the paper's values). */
+  int domain_solver;
+  int nssor;
+  double ssor_omega;
 } mbicg_params;
 
 /* Counters of the last call on a context. */
@@ -120,7 +132,8 @@ typedef struct {
 
 /* Fills p with the defaults: ncycle 4, nmr 4, block {4,4,4,4},
  * MBICG_MR_FROZEN, prec_sap FP32, prec_D FP32, max_iter 1000, use_x0 0,
- * delta_ru 0.1, no history, no dummy right-hand sides. */
+ * delta_ru 0.1, no history, no dummy right-hand sides, no clover term,
+ * MR domain solves (nssor 1, ssor_omega 1.26 for SSOR). */
 void mbicg_default_params(mbicg_params* p);
 
 /* Creates a context for a lattice of extents dims on CUDA device `device`.

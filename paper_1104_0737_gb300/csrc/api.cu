@@ -296,6 +296,16 @@ struct Solver {
       if ((rc = buf(c, "sap_omega", (size_t)ndc * L * 2, &sw.omega))) return rc;
       if ((rc = buf(c, "sap_table", (size_t)p.ncycle * 2 * p.nmr * ndc * 2, &table))) return rc;
       if ((rc = buf(c, "sap_unset", 1, &unset))) return rc;
+      if (p.domain_solver == MBICG_DOMAIN_SSOR) {
+        const char* names4[4] = {"ssor_acc", "ssor_term", "ssor_pv", "ssor_pqv"};
+        for (int i = 0; i < 4; ++i) {
+          cx<TS>* b;
+          if ((rc = buf(c, names4[i], nl, &b))) return rc;
+          sw.ssor[i] = b;
+        }
+        if ((rc = buf(c, "ssor_levels", (size_t)g.Vd, &sw.levels))) return rc;
+        CK(sap_prepare_ssor(g, sw, c->stream));
+      }
       // every frozen step length starts unrecorded (NaN), unless this solve
       // continues another one with the same preconditioner
       if (!keep_table)
@@ -322,20 +332,23 @@ struct Solver {
     }
     int mode = p.mr_mode;
     double* tab = nullptr;
-    if (p.mr_mode == MBICG_MR_FROZEN) {
+    const SsorParams sp{p.nssor, p.ssor_omega};
+    const SsorParams* ssor = p.domain_solver == MBICG_DOMAIN_SSOR ? &sp : nullptr;
+    if (p.mr_mode == MBICG_MR_FROZEN && !ssor) {
       // record until every entry of the table is set, then replay only
       mode = table_complete ? 3 : 2;
       tab = table;
       if (!table_complete) CK(cudaMemsetAsync(unset, 0, sizeof(int), c->stream));
     }
     if constexpr (std::is_same<T, TS>::value) {
-      sap_apply<TS>(ex, g, links_S(), in, out, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw, tinv<TS>());
+      sap_apply<TS>(ex, g, links_S(), in, out, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw, tinv<TS>(), ssor);
     } else {
       {
         Timed t(ex, KC_CONVERT);
         convert_block<T, TS>(ex, (long long)nl, in, eta_s);
       }
-      sap_apply<TS>(ex, g, links_S(), eta_s, psi_s, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw, tinv<TS>());
+      sap_apply<TS>(ex, g, links_S(), eta_s, psi_s, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw, tinv<TS>(),
+                    ssor);
       Timed t(ex, KC_CONVERT);
       convert_block<TS, T>(ex, (long long)nl, psi_s, out);
     }
@@ -465,7 +478,8 @@ struct Solver {
   int launch_iteration() {
     const char* env = getenv("MBICG_GRAPHS");
     const bool enabled = !(env && env[0] == '0');
-    const bool stable = p.ncycle == 0 || p.mr_mode != MBICG_MR_FROZEN || table_complete;
+    const bool stable = p.ncycle == 0 || p.domain_solver == MBICG_DOMAIN_SSOR || p.mr_mode != MBICG_MR_FROZEN ||
+                        table_complete;
     if (!enabled || c->prof.on || !stable || graph_failed) return iteration_launches();
     if (!gexec) {
       const long long before = c->launches;
@@ -645,8 +659,14 @@ int check_params(mbicg_ctx* c, int L, const mbicg_params* p, bool solve) {
     if (p->nmr < 1 || p->nmr > 256) return fail(c, MBICG_EINVAL, "nmr must be in [1, 256]");
     if (!valid_blocking(c, p->block))
       return fail(c, MBICG_EINVAL, "SAP block must divide the lattice into an even number (>= 2) of domains per direction");
-    if (p->mr_mode < 0 || p->mr_mode > 2 || (!solve && p->mr_mode == MBICG_MR_FROZEN))
+    if (p->domain_solver != MBICG_DOMAIN_MR && p->domain_solver != MBICG_DOMAIN_SSOR)
+      return fail(c, MBICG_EINVAL, "bad domain_solver");
+    if (p->domain_solver == MBICG_DOMAIN_SSOR) {
+      if (p->nssor < 0 || p->nssor > 16) return fail(c, MBICG_EINVAL, "nssor must be in [0, 16]");
+      if (!(p->ssor_omega > 0 && p->ssor_omega < 2)) return fail(c, MBICG_EINVAL, "ssor_omega must be in (0, 2)");
+    } else if (p->mr_mode < 0 || p->mr_mode > 2 || (!solve && p->mr_mode == MBICG_MR_FROZEN)) {
       return fail(c, MBICG_EINVAL, "bad mr_mode");
+    }
     if (p->prec_sap != MBICG_FP32 && p->prec_sap != MBICG_FP64)
       return fail(c, MBICG_EINVAL, "prec_sap must be MBICG_FP32 or MBICG_FP64");
   }
@@ -730,6 +750,9 @@ void mbicg_default_params(mbicg_params* p) {
   p->delta_ru = 0.1;
   p->res_history = nullptr;
   p->res_history_len = 0;
+  p->domain_solver = MBICG_DOMAIN_MR;
+  p->nssor = 1;
+  p->ssor_omega = 1.26;
 }
 
 int mbicg_create(mbicg_ctx** out, const int dims[4], int device, void* cuda_stream) {
@@ -1019,6 +1042,17 @@ int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double
     const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
     if ((rc2 = buf(c, "sap_dots", (size_t)ndc * (g.Vd / S) * L * 3, &w.dots))) return rc2;
     if ((rc2 = buf(c, "sap_omega", (size_t)ndc * L * 2, &w.omega))) return rc2;
+    const SsorParams sp{p->nssor, p->ssor_omega};
+    if (p->domain_solver == MBICG_DOMAIN_SSOR) {
+      const char* names4[4] = {"ssor_acc", "ssor_term", "ssor_pv", "ssor_pqv"};
+      for (int i = 0; i < 4; ++i) {
+        cx<R>* b4;
+        if ((rc2 = buf(c, names4[i], nl, &b4))) return rc2;
+        w.ssor[i] = b4;
+      }
+      if ((rc2 = buf(c, "ssor_levels", (size_t)g.Vd, &w.levels))) return rc2;
+      if (sap_prepare_ssor(g, w, c->stream) != cudaSuccess) return fail(c, MBICG_ECUDA, "ssor level table");
+    }
     {
       Timed t(ex, KC_CONVERT);
       abi_to_internal<R>(ex, c->V, L, static_cast<const cx<double>*>(si.dev), a);
@@ -1026,9 +1060,13 @@ int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double
     const R* tinv = nullptr;
     if (p->clover) tinv = reinterpret_cast<const R*>(sizeof(R) == 8 ? static_cast<const void*>(c->Ti64)
                                                                      : static_cast<const void*>(c->Ti32));
-    sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, p->mr_mode, nullptr, nullptr, w, tinv);
+    sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, p->mr_mode, nullptr, nullptr, w, tinv,
+                 p->domain_solver == MBICG_DOMAIN_SSOR ? &sp : nullptr);
     Timed t(ex, KC_CONVERT);
     internal_to_abi<R>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
+    // the level table's host copy lives in w: wait for its upload before w goes
+    if (p->domain_solver == MBICG_DOMAIN_SSOR && cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return fail(c, MBICG_ECUDA, "sap_precond");
     return MBICG_OK;
   };
   if (p->prec_sap == MBICG_FP64) rc = run(double(0), c->U64);

@@ -219,6 +219,65 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_domain_appl
 }
 
 // ---------------------------------------------------------------------------
+// SSOR domain solves (Sec. 2.2): one wavefront level of a triangular
+// substitution on every domain of one colour.  With L the forward and U the
+// backward hops inside a domain (times kappa T^{-1} for the clover matrix),
+// z = (1 - omega L)^{-1} y sets z_x = y_x + omega kappa [T^{-1}] (forward hops
+// of z)_x, and a forward hop raises the level lx + ly + lz + lt of the site by
+// one: the sites of one level depend only on the level above (below for U),
+// so each level is one launch over all domains of the colour.
+// ---------------------------------------------------------------------------
+template <typename R, int MU, bool FWD>
+__device__ __forceinline__ void hop_in_domain(const Geom& g, const cx<R>* __restrict__ links,
+                                              const cx<R>* __restrict__ in, int L, int rhs, int s, const int lc[4],
+                                              int stride, Spinor<R>& acc) {
+  // no hop inside a domain crosses the lattice boundary (>= 2 domains per direction)
+  if (FWD) {
+    if (lc[MU] != g.blk[MU] - 1)
+      hop<MU, -1>(acc, in + spinor_offset(s + stride, L, rhs), links + (size_t)(s * 4 + MU) * 9, false);
+  } else {
+    if (lc[MU] != 0)
+      hop<MU, +1>(acc, in + spinor_offset(s - stride, L, rhs), links + (size_t)((s - stride) * 4 + MU) * 9, false);
+  }
+}
+
+template <typename R, int CM, bool FWD>
+__global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_ssor_level(Geom g, int colour,
+                                                    const cx<R>* __restrict__ links, const R* __restrict__ tinv,
+                                                    const cx<R>* __restrict__ y, cx<R>* z, int L, R komega,
+                                                    const int* __restrict__ local, int count) {
+  const int rhs = threadIdx.x;
+  const int i = blockIdx.x * blockDim.y + threadIdx.y;
+  if (i >= (g.nd / 2) * count) return;
+  const int k = i / count;
+  const int slot = k * g.Vd + __ldg(local + (i - k * count));
+  int c[4], lc[4], kk;
+  colour_slot_coords(g, colour, slot, c, lc, &kk);
+  const int s = site_index(g, c);
+  const int st1 = g.d[0], st2 = st1 * g.d[1], st3 = st2 * g.d[2];
+  Spinor<R> h;
+  zero(h);
+  hop_in_domain<R, 0, FWD>(g, links, z, L, rhs, s, lc, 1, h);
+  hop_in_domain<R, 1, FWD>(g, links, z, L, rhs, s, lc, st1, h);
+  hop_in_domain<R, 2, FWD>(g, links, z, L, rhs, s, lc, st2, h);
+  hop_in_domain<R, 3, FWD>(g, links, z, L, rhs, s, lc, st3, h);
+  if (CM == 1) {
+    Spinor<R> t;
+    herm_apply<R>(tinv + (size_t)s * HERM_PER_SITE, h, t);
+    h = t;
+  }
+  Spinor<R> v;
+  load_spinor(y + spinor_offset(s, L, rhs), v);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    cx<R>& o = (&v.c[0][0])[j];
+    const cx<R> a = (&h.c[0][0])[j];
+    o = mk(fma(komega, a.re, o.re), fma(komega, a.im, o.im));
+  }
+  store_spinor(z + spinor_offset(s, L, rhs), v);
+}
+
+// ---------------------------------------------------------------------------
 // Fused SAP colour sweep with the MR iterations on chip (FP32).
 //
 // One thread-block cluster per (domain of the colour, chunk of columns).  The
@@ -734,13 +793,32 @@ void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* li
   if (nchunk_out) *nchunk_out = nchunk;
 }
 
+template <typename R>
+void ssor_level(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const R* tinv, const cx<R>* y,
+                cx<R>* z, int L, double komega, const int* local, int count, bool fwd) {
+  const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
+  const int n = (g.nd / 2) * count;
+  const unsigned grid = (unsigned)((n + S - 1) / S);
+  const dim3 block(L, S);
+  if (tinv) {
+    if (fwd) k_ssor_level<R, 1, true><<<grid, block, 0, ex.stream>>>(g, colour, links, tinv, y, z, L, (R)komega, local, count);
+    else k_ssor_level<R, 1, false><<<grid, block, 0, ex.stream>>>(g, colour, links, tinv, y, z, L, (R)komega, local, count);
+  } else {
+    if (fwd) k_ssor_level<R, 0, true><<<grid, block, 0, ex.stream>>>(g, colour, links, nullptr, y, z, L, (R)komega, local, count);
+    else k_ssor_level<R, 0, false><<<grid, block, 0, ex.stream>>>(g, colour, links, nullptr, y, z, L, (R)komega, local, count);
+  }
+  ++*ex.launches;
+}
+
 #define INST(R)                                                                                          \
   template void dslash_full<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double,  \
                                const R*, int);                                                          \
   template void sap_residual<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, const cx<R>*,   \
                                 cx<R>*, int, double, bool, const R*);                                     \
   template void sap_domain_apply<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, cx<R>*,     \
-                                    double*, int, double, int*, const R*);
+                                    double*, int, double, int*, const R*);                                \
+  template void ssor_level<R>(const Exec&, const Geom&, int, const cx<R>*, const R*, const cx<R>*, cx<R>*, \
+                              int, double, const int*, int, bool);
 INST(float)
 INST(double)
 #undef INST

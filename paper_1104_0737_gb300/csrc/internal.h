@@ -141,6 +141,13 @@ void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* li
 bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
                      cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode,
                      const double* table);
+// SSOR (Sec. 2.2): one wavefront level of z = (1 - omega L)^{-1} y (fwd) or
+// z = (1 - omega U)^{-1} y on every domain of one colour, L and U the forward
+// and backward hops inside a domain (times T^{-1} with tinv); komega =
+// kappa * omega; local[0..count) the local site indices of the level.
+template <typename R>
+void ssor_level(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const R* tinv, const cx<R>* y,
+                cx<R>* z, int L, double komega, const int* local, int count, bool fwd);
 // Number of sites per CTA the SAP kernels use for L columns (divides Vd).
 int sap_sites_per_cta(const Geom& g, int L, bool fp64);
 
@@ -158,7 +165,24 @@ struct SapWork {
   size_t dots_len = 0;
   int L = 0;
   bool fp64 = false;
+  // SSOR domain solves: the local site indices of a domain sorted by
+  // wavefront level lx + ly + lz + lt (device copy of level_host), level k at
+  // [level_off[k], level_off[k + 1]); four full-lattice scratch blocks
+  int* levels = nullptr;
+  std::vector<int> level_host, level_off;
+  void* ssor[4] = {nullptr, nullptr, nullptr, nullptr};
 };
+
+// The SAP domain solver (Sec. 2.2): nmr MR steps (the default) or SSOR with
+// N_SSOR = nssor and relaxation omega.
+struct SsorParams {
+  int nssor;
+  double omega;
+};
+// Fills w.level_host / w.level_off for the domain shape of g and copies the
+// level table to w.levels (device, Vd ints) on the stream; w must stay alive
+// until the copy has completed.
+cudaError_t sap_prepare_ssor(const Geom& g, SapWork& w, cudaStream_t stream);
 
 // psi = M_SAP eta.  eta and psi are full-lattice blocks in the internal
 // layout and in the SAP precision (R).  mr_mode: 0 per column, 1 shared by the
@@ -167,11 +191,12 @@ struct SapWork {
 // an entry stays unrecorded), 3 frozen replay.
 // table = complex [ncycle][2][nmr][nd/2] (modes 2, 3).
 // tinv != NULL: SAP for the Jacobi-preconditioned clover matrix (multi-kernel
-// path; the fused sweep has no clover term).
+// path; the fused sweep has no clover term).  ssor != NULL: SSOR domain solves
+// instead of MR (nmr, mr_mode, table and unset unused; w.levels and w.ssor set).
 template <typename R>
 void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* eta, cx<R>* psi,
                int L, double kappa, int ncycle, int nmr, int mr_mode, double* table, int* unset,
-               SapWork& w, const R* tinv = nullptr);
+               SapWork& w, const R* tinv = nullptr, const SsorParams* ssor = nullptr);
 
 // ---------------------------------------------------------------------------
 // Block linear algebra (blas.cu)

@@ -106,6 +106,31 @@ void emu_sap_domain_apply(const int* dims, const int* block, const double* U, in
                                                 nullptr);
   });
 }
+void emu_ssor_level(const int* dims, const int* block, const double* U, const double* tinv, int colour,
+                    const double* y, double* z, int L, double komega, const int* local, int count, int fwd) {
+  const Geom g = make_geom(dims, block);
+  grid((g.nd / 2) * count, L, [&] {
+    const C* U_ = (const C*)U;
+    if (tinv) {
+      if (fwd) emu_dslash::k_ssor_level<double, 1, true>(g, colour, U_, tinv, (const C*)y, (C*)z, L, komega, local, count);
+      else emu_dslash::k_ssor_level<double, 1, false>(g, colour, U_, tinv, (const C*)y, (C*)z, L, komega, local, count);
+    } else {
+      if (fwd) emu_dslash::k_ssor_level<double, 0, true>(g, colour, U_, nullptr, (const C*)y, (C*)z, L, komega, local, count);
+      else emu_dslash::k_ssor_level<double, 0, false>(g, colour, U_, nullptr, (const C*)y, (C*)z, L, komega, local, count);
+    }
+  });
+}
+void emu_ssor_combine(const int* dims, const int* block, int colour, const double* pv, const double* qv,
+                      const double* pqv, double* term, double* acc, int L, double omega) {
+  const Geom g = make_geom(dims, block);
+  grid((g.nd / 2) * g.Vd, L, [&] {
+    emu_sap::k_ssor_combine<double>(g, colour, (const C*)pv, (const C*)qv, (const C*)pqv, (C*)term, (C*)acc, L, omega);
+  });
+}
+void emu_colour_add(const int* dims, const int* block, int colour, const double* x, double* psi, int L) {
+  const Geom g = make_geom(dims, block);
+  grid((g.nd / 2) * g.Vd, L, [&] { emu_sap::k_colour_add<double>(g, colour, (const C*)x, (C*)psi, L); });
+}
 void emu_mr_update(const int* dims, const int* block, int colour, const double* omega, double* r, const double* q,
                    double* x, double* psi, int L, int first, int last) {
   const Geom g = make_geom(dims, block);

@@ -28,7 +28,8 @@ CUDA_INCLUDE = "/usr/local/cuda/include"
 PARTS = [
     ("emu_dslash", "dslash.cu", "namespace {",
      "// ---------------------------------------------------------------------------\n// Fused SAP colour sweep"),
-    ("emu_sap", "sap.cu", "namespace {", "}  // namespace\n\ntemplate <typename R>\nvoid sap_apply("),
+    ("emu_sap", "sap.cu", "namespace {",
+     "}  // namespace\n\n// ---------------------------------------------------------------------------\n// Host side"),
     ("emu_clover", "clover.cu", "namespace {", "}  // namespace\n\nvoid clover_field("),
 ]
 
@@ -67,6 +68,10 @@ def emu(tmp_path_factory):
     lib.emu_sap_residual.argtypes = [I, I, D, ctypes.c_int, D, D, D, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                      D]
     lib.emu_sap_domain_apply.argtypes = [I, I, D, ctypes.c_int, D, D, ctypes.c_int, ctypes.c_double, D]
+    lib.emu_ssor_level.argtypes = [I, I, D, D, ctypes.c_int, D, D, ctypes.c_int, ctypes.c_double, I, ctypes.c_int,
+                                   ctypes.c_int]
+    lib.emu_ssor_combine.argtypes = [I, I, ctypes.c_int, D, D, D, D, D, ctypes.c_int, ctypes.c_double]
+    lib.emu_colour_add.argtypes = [I, I, ctypes.c_int, D, D, ctypes.c_int]
     lib.emu_mr_update.argtypes = [I, I, ctypes.c_int, D, D, D, D, D, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     return lib
 
@@ -241,3 +246,81 @@ def test_clover_sap_kernels(emu, oracle_mod, clover_case, mode):
     ref = oracle_mod.sap_ext(c["dims"], block, c["U"], c["kappa"], 2, eta, Tinv=c["Ti"],
                              solver=oracle_mod.DOMAIN_MR, nmr=3, mr_mode=mode)
     assert np.max(np.abs(got - ref)) < 1e-14 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------------------
+# SSOR domain solves
+# ---------------------------------------------------------------------------
+def _levels(block):
+    """Local site indices of a domain (x fastest) grouped by lx + ly + lz + lt."""
+    bx, by, bz, bt = block
+    n = bx * by * bz * bt
+    lev = [[] for _ in range(bx + by + bz + bt - 3)]
+    for l in range(n):
+        x, y, z, t = l % bx, (l // bx) % by, (l // (bx * by)) % bz, l // (bx * by * bz)
+        lev[x + y + z + t].append(l)
+    return [np.array(v, dtype=np.int32) for v in lev]
+
+
+def _ssor_colour(emu, dims, block, U, tinv, colour, y, kappa, nssor, omega):
+    """B y on the domains of one colour with the emulated kernels, launched in
+    the order of the library's SSOR driver."""
+    L = y.shape[1]
+    lev = _levels(block)
+    acc, term, qv, pv, pqv, out = (np.zeros_like(y) for _ in range(6))
+
+    def substitute(fwd, src, dst):
+        for k in (range(len(lev) - 1, -1, -1) if fwd else range(len(lev))):
+            loc = lev[k]
+            emu.emu_ssor_level(_iv(dims), _iv(block), _dp(U), _dp(tinv), colour, _dp(src), _dp(dst), L,
+                               kappa * omega, loc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(loc), int(fwd))
+
+    substitute(True, y, acc)
+    term[...] = acc
+    for _ in range(nssor):
+        substitute(False, term, qv)
+        substitute(True, term, pv)
+        substitute(True, qv, pqv)
+        emu.emu_ssor_combine(_iv(dims), _iv(block), colour, _dp(pv), _dp(qv), _dp(pqv), _dp(term), _dp(acc), L,
+                             omega)
+    substitute(False, acc, out)
+    return out
+
+
+@pytest.mark.parametrize("clover", [False, True])
+@pytest.mark.parametrize("nssor,omega", [(0, 1.0), (1, 1.26), (2, 0.9)])
+def test_ssor_domain_kernels(emu, oracle_mod, clover_case, clover, nssor, omega):
+    c = clover_case
+    dims, block = c["dims"], (2, 2, 1, 2)
+    tinv = c["Ti64"] if clover else None
+    y = synth.gaussian_source(dims, 2, seed=98)
+    col = domain_colour(dims, block)
+    for colour in (0, 1):
+        got = _oracle_layout(_ssor_colour(emu, dims, block, c["U"], tinv, colour, _internal(y), c["kappa"],
+                                          nssor, omega))
+        ref = oracle_mod.ssor_domains(dims, block, c["U"], c["kappa"], nssor, omega, colour, y,
+                                      Tinv=c["Ti"] if clover else None)
+        on = col == colour
+        assert np.max(np.abs(got[on] - ref[on])) < 1e-14 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("clover", [False, True])
+def test_ssor_sap_kernels(emu, oracle_mod, clover_case, clover):
+    """M_SAP with SSOR domain solves: per colour the residual kernel, the SSOR
+    solve and psi += x, in the order of the library's driver."""
+    c = clover_case
+    dims, block, kappa = c["dims"], (2, 2, 1, 2), c["kappa"]
+    tinv = c["Ti64"] if clover else None
+    eta = synth.gaussian_source(dims, 2, seed=99)
+    e = _internal(eta)
+    psi, r = np.zeros_like(e), np.zeros_like(e)
+    L = e.shape[1]
+    for cyc in range(2):
+        for colour in (0, 1):
+            emu.emu_sap_residual(_iv(dims), _iv(block), _dp(c["U"]), colour, _dp(e), _dp(psi), _dp(r), L, kappa,
+                                 int(cyc == 0 and colour == 0), _dp(tinv))
+            x = _ssor_colour(emu, dims, block, c["U"], tinv, colour, r, kappa, 1, 1.26)
+            emu.emu_colour_add(_iv(dims), _iv(block), colour, _dp(x), _dp(psi), L)
+    ref = oracle_mod.sap_ext(dims, block, c["U"], kappa, 2, eta, Tinv=c["Ti"] if clover else None,
+                             solver=oracle_mod.DOMAIN_SSOR, nssor=1, omega=1.26)
+    assert np.max(np.abs(_oracle_layout(psi) - ref)) < 1e-14 * np.max(np.abs(ref))
