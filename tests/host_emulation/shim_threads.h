@@ -1,0 +1,171 @@
+// Threaded host emulation shim: every CUDA thread of a launch runs as its own
+// host thread, so kernels that synchronise (__syncthreads, cluster barriers,
+// warp shuffles) and share on-chip memory (shared memory, distributed shared
+// memory of a thread-block cluster) can run on the CPU.  Shared memory is one
+// arena per CTA, filled with NaN bytes before the launch so that a read of a
+// word no thread has written shows up in the result.
+#pragma once
+#include <cuda_runtime.h>
+#include <pthread.h>
+
+#include <barrier>
+#include <cmath>
+#include <cstddef>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+struct EmuDim {
+  unsigned x, y, z;
+};
+
+struct EmuCta {
+  std::vector<unsigned char> arena;  // dynamic shared memory, then the static variables
+  size_t dyn_bytes = 0;
+  std::unique_ptr<std::barrier<>> bar;
+  std::vector<std::unique_ptr<std::barrier<>>> warp_bar;
+  std::vector<unsigned long long> warp_slot;
+};
+
+struct EmuCluster {
+  std::vector<EmuCta*> ctas;
+  std::unique_ptr<std::barrier<>> bar;
+};
+
+struct EmuThread {
+  EmuDim block, thread;
+  EmuCta* cta;
+  EmuCluster* cluster;
+  unsigned rank;
+};
+
+extern thread_local EmuThread emu_t;
+extern EmuDim blockDim, gridDim;
+// set when an emulated access leaves the cluster or a CTA's arena (the access
+// reads NaN or CTA 0 instead); the harness reports it
+extern int emu_bad_access;
+#define blockIdx (emu_t.block)
+#define threadIdx (emu_t.thread)
+
+template <typename T>
+inline T __ldg(const T* p) { return *p; }
+inline unsigned __umulhi(unsigned a, unsigned b) { return (unsigned)(((unsigned long long)a * b) >> 32); }
+inline size_t __cvta_generic_to_shared(const void* p) {
+  return (size_t)((const unsigned char*)p - emu_t.cta->arena.data());
+}
+inline void __syncthreads() { emu_t.cta->bar->arrive_and_wait(); }
+inline int atomicOr(int* p, int v) { return __atomic_fetch_or(p, v, __ATOMIC_SEQ_CST); }
+
+template <typename T>
+inline T __shfl_xor_sync(unsigned, T v, int o) {
+  static_assert(sizeof(T) <= 8, "shuffle of a type wider than 8 bytes");
+  const unsigned tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const unsigned w = tid / 32, lane = tid % 32;
+  unsigned long long bits = 0;
+  memcpy(&bits, &v, sizeof(T));
+  emu_t.cta->warp_slot[w * 32 + lane] = bits;
+  emu_t.cta->warp_bar[w]->arrive_and_wait();
+  const unsigned long long rb = emu_t.cta->warp_slot[w * 32 + (lane ^ (unsigned)o)];
+  emu_t.cta->warp_bar[w]->arrive_and_wait();
+  T r;
+  memcpy(&r, &rb, sizeof(T));
+  return r;
+}
+
+inline void* emu_dyn_smem() { return emu_t.cta->arena.data(); }
+inline void* emu_static_smem() { return emu_t.cta->arena.data() + emu_t.cta->dyn_bytes; }
+
+namespace cooperative_groups {
+struct cluster_group {
+  unsigned block_rank() const { return emu_t.rank; }
+  void sync() const { emu_t.cluster->bar->arrive_and_wait(); }
+  template <typename T>
+  T* map_shared_rank(T* p, unsigned r) const;
+};
+inline cluster_group this_cluster() { return {}; }
+}  // namespace cooperative_groups
+
+template <typename T>
+T* cooperative_groups::cluster_group::map_shared_rank(T* p, unsigned r) const {
+  const size_t off = (size_t)((unsigned char*)p - emu_t.cta->arena.data());
+  if (r >= emu_t.cluster->ctas.size() || off >= emu_t.cta->arena.size()) {
+    __atomic_store_n(&emu_bad_access, 1, __ATOMIC_SEQ_CST);
+    r = 0;
+  }
+  return reinterpret_cast<T*>(emu_t.cluster->ctas[r]->arena.data() + off);
+}
+
+// shared::cluster window addresses: the CTA rank in the top 8 bits, the
+// offset in the CTA's arena below; mapa of a window address replaces the rank
+inline uint32_t emu_mapa(uint32_t addr, uint32_t rank) { return (rank << 24) | (addr & 0xffffffu); }
+inline float4 emu_ld_cluster_f4(uint32_t a) {
+  const uint32_t r = a >> 24, off = a & 0xffffffu;
+  if (r >= emu_t.cluster->ctas.size() || (size_t)off + 16 > emu_t.cluster->ctas[r]->arena.size()) {
+    __atomic_store_n(&emu_bad_access, 1, __ATOMIC_SEQ_CST);
+    const float n = std::nanf("");
+    return make_float4(n, n, n, n);
+  }
+  float4 v;
+  memcpy(&v, emu_t.cluster->ctas[r]->arena.data() + off, 16);
+  return v;
+}
+
+#define __launch_bounds__(...)
+using std::fma;
+using std::isnan;
+
+// Runs kernel() for a grid of nclusters clusters of cs CTAs of `threads`
+// threads each (1-D), one cluster at a time; static_bytes of static shared
+// memory follow dyn_bytes of dynamic shared memory in each CTA's arena.
+template <typename F>
+void emu_launch(int nclusters, int cs, int threads, size_t dyn_bytes, size_t static_bytes, F kernel) {
+  blockDim = {(unsigned)threads, 1, 1};
+  gridDim = {(unsigned)(nclusters * cs), 1, 1};
+  for (int cl = 0; cl < nclusters; ++cl) {
+    EmuCluster cluster;
+    std::vector<std::unique_ptr<EmuCta>> ctas;
+    for (int r = 0; r < cs; ++r) {
+      auto c = std::make_unique<EmuCta>();
+      c->arena.assign(dyn_bytes + static_bytes + 16, 0xff);
+      c->dyn_bytes = dyn_bytes;
+      c->bar = std::make_unique<std::barrier<>>(threads);
+      for (int w = 0; w < (threads + 31) / 32; ++w) c->warp_bar.push_back(std::make_unique<std::barrier<>>(32));
+      c->warp_slot.assign((size_t)((threads + 31) / 32) * 32, 0);
+      cluster.ctas.push_back(c.get());
+      ctas.push_back(std::move(c));
+    }
+    cluster.bar = std::make_unique<std::barrier<>>(cs * threads);
+    struct Arg {
+      EmuThread t;
+      F* k;
+    };
+    std::vector<Arg> args((size_t)cs * threads);
+    std::vector<pthread_t> tids((size_t)cs * threads);
+    pthread_attr_t attr;
+    pthread_attr_init(&attr);
+    pthread_attr_setstacksize(&attr, 1 << 19);
+    for (int r = 0; r < cs; ++r)
+      for (int t = 0; t < threads; ++t) {
+        Arg& a = args[(size_t)r * threads + t];
+        a.t = EmuThread{{(unsigned)(cl * cs + r), 0, 0}, {(unsigned)t, 0, 0}, ctas[r].get(), &cluster, (unsigned)r};
+        a.k = &kernel;
+        const int rc = pthread_create(&tids[(size_t)r * threads + t], &attr,
+                                      [](void* p) -> void* {
+                                        Arg* a = static_cast<Arg*>(p);
+                                        emu_t = a->t;
+                                        (*a->k)();
+                                        return nullptr;
+                                      },
+                                      &a);
+        if (rc != 0) {  // a missing thread would leave the others waiting at a barrier
+          fprintf(stderr, "emu_launch: pthread_create failed (%d)\n", rc);
+          abort();
+        }
+      }
+    pthread_attr_destroy(&attr);
+    for (pthread_t& t : tids) pthread_join(t, nullptr);
+  }
+}

@@ -1,0 +1,112 @@
+"""The fused SAP sweep kernel (Sec. 2.2) of the CUDA path, compiled for the
+host and run with one host thread per CUDA thread (tests/host_emulation/
+shim_threads.h: real barriers for __syncthreads, the cluster barrier and warp
+shuffles; one shared-memory arena per CTA, read across the cluster through
+emulated distributed shared memory), against the oracle's SAP in FP32
+tolerance: the 4^4 variant (one CTA per domain) and the 8^4 variant (an
+8-CTA cluster per domain), per-column MR and frozen step lengths, several
+persistent clusters sharing the (domain, column) items unevenly.
+
+This checks the sweep's index maps, its on-chip data flow and its barriers'
+placement for reads of data no thread has written (shared memory starts as
+NaN) on a machine without a GPU; timing and the real memory model are left
+to the -m gpu tests."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import emulation_sources
+import synth
+
+HERE = os.path.join(emulation_sources.ROOT, "tests", "host_emulation")
+CUDA_INCLUDE = "/usr/local/cuda/include"
+
+
+@pytest.fixture(scope="module")
+def sweep(tmp_path_factory):
+    if shutil.which("g++") is None or not os.path.exists(os.path.join(CUDA_INCLUDE, "cuda_runtime.h")):
+        pytest.skip("g++ or the CUDA headers are missing")
+    d = tmp_path_factory.mktemp("sweep_emulation")
+    (d / "sweep_parts.inc").write_text(emulation_sources.sweep_parts())
+    shutil.copy(os.path.join(HERE, "shim_threads.h"), d / "shim_threads.h")
+    lib_path = d / "libsweep.so"
+    subprocess.run(["g++", "-std=c++20", "-O2", "-fPIC", "-shared", "-pthread", "-I", str(d), "-I", CUDA_INCLUDE,
+                    os.path.join(HERE, "sweep_harness.cpp"), "-o", str(lib_path)], check=True)
+    lib = ctypes.CDLL(str(lib_path))
+    F, D, I = (ctypes.POINTER(t) for t in (ctypes.c_float, ctypes.c_double, ctypes.c_int))
+    lib.emu_sweep.argtypes = [I, I, ctypes.c_int, F, F, F, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int,
+                              ctypes.c_int, D, ctypes.c_int]
+    return lib
+
+
+def _iv(v):
+    return (ctypes.c_int * 4)(*[int(x) for x in v])
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _internal32(a):
+    return np.ascontiguousarray(a.reshape(a.shape[0], 12, -1).transpose(0, 2, 1)).astype(np.complex64)
+
+
+def _oracle_layout(a):
+    return np.ascontiguousarray(a.transpose(0, 2, 1)).reshape(a.shape[0], 4, 3, -1).astype(np.complex128)
+
+
+def _sap_emulated(lib, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nclusters):
+    """ncycle cycles of E and O sweeps, as the library's driver launches them;
+    mode 3 replays the step lengths omegas[it] on every domain."""
+    L = eta.shape[3]
+    links = np.ascontiguousarray(U.astype(np.complex64))
+    e = _internal32(eta)
+    psi = np.zeros_like(e)
+    ndc = int(np.prod(dims)) // int(np.prod(block)) // 2
+    table = None
+    if mode == 3:
+        table = np.zeros((nmr, ndc, 2))
+        table[..., 0] = np.real(omegas)[:, None]
+        table[..., 1] = np.imag(omegas)[:, None]
+    tp = table.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if table is not None else None
+    for cyc in range(ncycle):
+        for colour in (0, 1):
+            rc = lib.emu_sweep(_iv(dims), _iv(block), colour, _fp(links), _fp(e), _fp(psi), L, kappa,
+                               int(cyc == 0 and colour == 0), nmr, mode, tp, nclusters)
+            assert rc == 0
+    return _oracle_layout(psi)
+
+
+def _rel_site(a, b):
+    V = a.shape[0]
+    return float(np.max(np.linalg.norm((a - b).reshape(V, -1), axis=1) / np.linalg.norm(b.reshape(V, -1), axis=1)))
+
+
+CASES = [
+    # dims, block, L, ncycle, nmr, clusters
+    ((8, 8, 8, 8), (4, 4, 4, 4), 3, 2, 3, 5),
+    ((16, 16, 16, 16), (8, 8, 8, 8), 1, 1, 2, 3),
+]
+
+
+@pytest.mark.parametrize("dims,block,L,ncycle,nmr,nclusters", CASES)
+@pytest.mark.parametrize("mode", [0, 3])
+def test_fused_sweep_matches_oracle(sweep, oracle_mod, dims, block, L, ncycle, nmr, nclusters, mode):
+    U = synth.su3_links(dims, 0.5, seed=71)
+    eta = synth.gaussian_source(dims, L, seed=72)
+    kappa = 0.125
+    omegas = np.array([0.9 + 0.05j, 1.1 - 0.02j, 0.95 + 0.01j])[:nmr]
+    got = _sap_emulated(sweep, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nclusters)
+    assert not np.isnan(got).any()
+    if mode == 0:
+        ref = oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, eta, mr_mode=oracle_mod.MR_COLUMN)
+    else:
+        nd = int(np.prod(dims)) // int(np.prod(block))
+        table = np.ascontiguousarray(np.broadcast_to(omegas[None, None, :, None], (ncycle, 2, nmr, nd)))
+        ref = oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, eta, mr_mode=oracle_mod.MR_FROZEN,
+                             omega_table=table.copy())
+    assert _rel_site(got, ref) < 1e-5
