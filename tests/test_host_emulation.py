@@ -16,32 +16,25 @@ import subprocess
 import numpy as np
 import pytest
 
+import emulation_sources
 import synth
 from lattice_helpers import domain_colour
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CSRC = os.path.join(ROOT, "paper_1104_0737_gb300", "csrc")
-HERE = os.path.join(ROOT, "tests", "host_emulation")
+HERE = os.path.join(emulation_sources.ROOT, "tests", "host_emulation")
 CUDA_INCLUDE = "/usr/local/cuda/include"
 
-# (file, start marker, end marker) of the device code each namespace gets
+# (namespace, file, start marker, end marker) of the device code to emulate
 PARTS = [
-    ("emu_dslash", "dslash.cu", "namespace {",
-     "// ---------------------------------------------------------------------------\n// Fused SAP colour sweep"),
-    ("emu_sap", "sap.cu", "namespace {",
-     "}  // namespace\n\n// ---------------------------------------------------------------------------\n// Host side"),
-    ("emu_clover", "clover.cu", "namespace {", "}  // namespace\n\nvoid clover_field("),
+    ("emu_dslash", "dslash.cu", "namespace {", emulation_sources.DSLASH_SEQ_END),
+    ("emu_sap", "sap.cu", "namespace {", "}  // namespace\n"),
+    ("emu_clover", "clover.cu", "namespace {", "}  // namespace\n"),
 ]
 
 
 def _device_parts():
-    out = ['#include "shim.h"', f'#include "{os.path.join(CSRC, "common.cuh")}"', "namespace mbicg {"]
+    out = ['#include "shim.h"', f'#include "{os.path.join(emulation_sources.CSRC, "common.cuh")}"', "namespace mbicg {"]
     for ns, name, start, end in PARTS:
-        with open(os.path.join(CSRC, name)) as f:
-            s = f.read()
-        a = s.index(start)
-        b = s.index(end, a)
-        out += [f"namespace {ns} {{", s[a + len(start):b], "}"]
+        out += [f"namespace {ns} {{", emulation_sources.cut(emulation_sources.read(name), start, end), "}"]
     out.append("}")
     return "\n".join(out)
 
