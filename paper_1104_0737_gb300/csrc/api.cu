@@ -330,11 +330,12 @@ struct Solver {
       CK(cudaMemcpyAsync(out, in, sizeof(cx<T>) * nl, cudaMemcpyDeviceToDevice, c->stream));
       return MBICG_OK;
     }
-    int mode = p.mr_mode;
-    double* tab = nullptr;
     const SsorParams sp{p.nssor, p.ssor_omega};
     const SsorParams* ssor = p.domain_solver == MBICG_DOMAIN_SSOR ? &sp : nullptr;
-    if (p.mr_mode == MBICG_MR_FROZEN && !ssor) {
+    // SSOR: a fixed linear operator, no step lengths to record
+    int mode = ssor ? MBICG_MR_COLUMN : p.mr_mode;
+    double* tab = nullptr;
+    if (mode == MBICG_MR_FROZEN) {
       // record until every entry of the table is set, then replay only
       mode = table_complete ? 3 : 2;
       tab = table;

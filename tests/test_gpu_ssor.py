@@ -79,6 +79,8 @@ def test_ssor_block_solve(oracle_mod, clover, prec_D):
         X = np.empty_like(B)
         st, iters, tres = mb.mbicg_block_solve(ctx, B, X, L, kappa, 1e-11, p)
         assert st == mb.MBICG_OK and max(tres) <= 1e-11
+        # SSOR makes M one linear operator: the iteration graph is used from the start
+        assert mb.mbicg_get_stats(ctx)["graph_iterations"] >= 1
         Xd = np.linalg.solve(dense_operator(op, dims), B.reshape(-1, L)).reshape(B.shape)
         assert rel_col_norm(X, Xd) < 1e-8
     finally:
