@@ -42,11 +42,50 @@ SWEEP_END = "// sets the sweep kernel's shared-memory and cluster attributes"
 DSLASH_SEQ_END = "// ---------------------------------------------------------------------------\n// Fused SAP colour sweep"
 
 
-def _bind_shared(src):
-    src = re.sub(r"extern __shared__ ([\w ]+?) (\w+)\[\];",
+def _split_top(s, sep=","):
+    out, depth, cur = [], 0, ""
+    for ch in s:
+        if ch in "[<(":
+            depth += 1
+        elif ch in "]>)":
+            depth -= 1
+        if ch == sep and depth == 0:
+            out.append(cur)
+            cur = ""
+        else:
+            cur += ch
+    out.append(cur)
+    return [x.strip() for x in out]
+
+
+def bind_shared(src):
+    """Dynamic shared memory -> the CTA arena; every static __shared__
+    declarator -> its own slot of the arena.  Returns (source, slots used)."""
+    src = re.sub(r"extern __shared__ (?:__align__\(\d+\) )?([\w ]+?) (\w+)\[\];",
                  r"\1* \2 = reinterpret_cast<\1*>(emu_dyn_smem());", src)
-    return re.sub(r"__shared__ (\w+) (\w+)((?:\[[^\]]+\])+);",
-                  r"auto& \2 = *reinterpret_cast<\1(*)\3>(emu_static_smem());", src)
+    slot = 0
+    out, pos = [], 0
+    for m in re.finditer(r"__shared__ ([^;]+);", src):
+        out.append(src[pos:m.start()])
+        parts = _split_top(m.group(1))
+        first = re.match(r"^(.*?)\s*\b(\w+)\s*((?:\[[^\]]*\])*)$", parts[0])
+        ctype = first.group(1).strip()
+        decls = [(first.group(2), first.group(3))]
+        for p in parts[1:]:
+            d = re.match(r"^(\w+)\s*((?:\[[^\]]*\])*)$", p)
+            decls.append((d.group(1), d.group(2)))
+        stmts = []
+        for name, dims in decls:
+            t = f"{ctype}{dims}"
+            stmts.append(f"static_assert(sizeof({t}) <= EMU_SLOT_BYTES, \"static shared variable too large\"); "
+                         f"auto& {name} = *reinterpret_cast<{ctype}(*){dims}>(emu_static_smem_slot({slot}));"
+                         if dims else
+                         f"auto& {name} = *reinterpret_cast<{ctype}*>(emu_static_smem_slot({slot}));")
+            slot += 1
+        out.append(" ".join(stmts))
+        pos = m.end()
+    out.append(src[pos:])
+    return "".join(out), slot
 
 
 def sweep_parts(csrc=CSRC):
@@ -62,6 +101,42 @@ def sweep_parts(csrc=CSRC):
                       "{ return emu_mapa(local, rank); }")
     ds = replace_body(ds, "__device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr)",
                       "{ return emu_ld_cluster_f4(addr); }")
-    ds = _bind_shared(ds)
-    return "\n".join(['#include "shim_threads.h"', common, "namespace mbicg {", "namespace emu_dslash {", ds,
-                      "}", "}"])
+    ds, slots = bind_shared(ds)
+    return "\n".join([f"#define EMU_STATIC_SLOTS {max(slots, 1)}", '#include "shim_threads.h"', common,
+                      "namespace mbicg {", "namespace emu_dslash {", ds, "}", "}"])
+
+
+MBAR_BODIES = {
+    "__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)":
+        "{ emu_mbar_init(bar, (int)count); }",
+    "__device__ __forceinline__ void mbar_fence_init()": "{}",
+    "__device__ __forceinline__ void mbar_arrive(uint64_t* bar)": "{ emu_mbar_update(bar, 1, 0, 0); }",
+    "__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)":
+        "{ emu_mbar_update(bar, 1, bytes, 0); }",
+    "__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)":
+        "{ return emu_mbar_try(bar, phase); }",
+    "__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, int limit = MBAR_SPIN_LIMIT)":
+        "{ (void)limit; return emu_mbar_wait(bar, phase); }",
+    "__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)":
+        "{ memcpy(dst, src, bytes); emu_mbar_update(bar, 0, 0, bytes); }",
+}
+
+
+def blas_parts(csrc=CSRC):
+    """common.cuh with the mbarrier and bulk-copy helpers emulated, the
+    declarations of internal.h, and the device part of blas.cu."""
+    common = read("common.cuh", csrc)
+    for sig, body in MBAR_BODIES.items():
+        common = replace_body(common, sig, body)
+    internal = read("internal.h", csrc).replace('#include "common.cuh"', "")
+    bl = cut(read("blas.cu", csrc), "namespace {", "}  // namespace\n")
+    # the Gram launcher: the same grid, the kernel run by the emulator
+    bl = replace_body(bl, "int launch_gram_t(",
+                      "{ (void)ex; using SH = GramShape<R, L, HERM>;"
+                      " const long long ntiles = (nsite + SH::TS - 1) / SH::TS;"
+                      " const int grid = (int)(ntiles < GRAM_CTAS ? ntiles : GRAM_CTAS);"
+                      " emu_launch(grid, 1, NT, SH::smem, [&] { k_gram<R, L, HERM>(nsite, A, B1, B2, flags, part, err); });"
+                      " return grid; }")
+    bl, slots = bind_shared(bl)
+    return "\n".join([f"#define EMU_STATIC_SLOTS {max(slots, 1)}", '#include "shim_threads.h"',
+                      common, internal, "namespace mbicg {", "namespace emu_blas {", bl, "}", "}"])

@@ -9,6 +9,10 @@
 #include <pthread.h>
 
 #include <barrier>
+#include <chrono>
+#include <condition_variable>
+#include <mutex>
+#include <unordered_map>
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
@@ -28,6 +32,7 @@ struct EmuCta {
   std::unique_ptr<std::barrier<>> bar;
   std::vector<std::unique_ptr<std::barrier<>>> warp_bar;
   std::vector<unsigned long long> warp_slot;
+  int or_flag = 0;
 };
 
 struct EmuCluster {
@@ -75,8 +80,15 @@ inline T __shfl_xor_sync(unsigned, T v, int o) {
   return r;
 }
 
+// Static __shared__ variables: the source cutter gives each declaration of the
+// emulated code its own slot of EMU_SLOT_BYTES after the dynamic part.
+#ifndef EMU_STATIC_SLOTS
+#define EMU_STATIC_SLOTS 1
+#endif
+constexpr size_t EMU_SLOT_BYTES = 8192;
 inline void* emu_dyn_smem() { return emu_t.cta->arena.data(); }
-inline void* emu_static_smem() { return emu_t.cta->arena.data() + emu_t.cta->dyn_bytes; }
+inline void* emu_static_smem_slot(int i) { return emu_t.cta->arena.data() + emu_t.cta->dyn_bytes + (size_t)i * EMU_SLOT_BYTES; }
+inline int __syncthreads_or(int p);
 
 namespace cooperative_groups {
 struct cluster_group {
@@ -115,13 +127,105 @@ inline float4 emu_ld_cluster_f4(uint32_t a) {
 
 #define __launch_bounds__(...)
 using std::fma;
+using std::isfinite;
 using std::isnan;
+// sin(pi x) and cos(pi x)
+inline void sincospi(double x, double* s, double* c) {
+  *s = std::sin(M_PI * x);
+  *c = std::cos(M_PI * x);
+}
+
+inline int __syncthreads_or(int p) {
+  EmuCta* c = emu_t.cta;
+  emu_t.cta->bar->arrive_and_wait();  // the previous use of the flag is over
+  if (p) __atomic_store_n(&c->or_flag, 1, __ATOMIC_SEQ_CST);
+  c->bar->arrive_and_wait();
+  const int r = __atomic_load_n(&c->or_flag, __ATOMIC_SEQ_CST);
+  c->bar->arrive_and_wait();
+  if (threadIdx.x == 0) __atomic_store_n(&c->or_flag, 0, __ATOMIC_SEQ_CST);
+  return r;
+}
+
+// mbarrier and bulk-copy emulation: the barrier's state lives in a side table
+// keyed by its shared-memory address; a bulk copy is a memcpy that then
+// completes its bytes on the barrier.  A phase completes when its arrivals
+// and its expected transaction bytes are both done.  A wait sleeps on a
+// condition variable; one that sees no progress for two seconds gives up, and
+// from then on every wait of the launch gives up at once (the kernel's own
+// path for a copy that never completes).
+struct EmuMbar {
+  int expected = 0, pending = 0;
+  long long tx = 0;
+  unsigned phases = 0;  // completed phases
+};
+struct EmuMbarTable {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::unordered_map<const void*, EmuMbar> tab;
+  bool gave_up = false;
+};
+inline EmuMbarTable& emu_mbars() {
+  static EmuMbarTable t;
+  return t;
+}
+inline void emu_mbar_settle(EmuMbar& b) {
+  if (b.pending == 0 && b.tx == 0) {
+    ++b.phases;
+    b.pending = b.expected;
+  }
+}
+inline void emu_mbar_init(const void* bar, int count) {
+  auto& t = emu_mbars();
+  std::lock_guard<std::mutex> g(t.mu);
+  EmuMbar& b = t.tab[bar];
+  b = EmuMbar{};
+  b.expected = b.pending = count;
+}
+// an arrival (tx_add extra transaction bytes expected) or completed bytes (done)
+inline void emu_mbar_update(const void* bar, int arrivals, long long tx_add, long long done) {
+  auto& t = emu_mbars();
+  {
+    std::lock_guard<std::mutex> g(t.mu);
+    EmuMbar& b = t.tab[bar];
+    b.tx += tx_add - done;
+    b.pending -= arrivals;
+    emu_mbar_settle(b);
+  }
+  t.cv.notify_all();
+}
+inline bool emu_mbar_try(const void* bar, uint32_t parity) {
+  auto& t = emu_mbars();
+  std::lock_guard<std::mutex> g(t.mu);
+  return (t.tab[bar].phases & 1u) != (parity & 1u);
+}
+inline bool emu_mbar_wait(const void* bar, uint32_t parity) {
+  auto& t = emu_mbars();
+  std::unique_lock<std::mutex> g(t.mu);
+  if (t.gave_up) return false;
+  const bool ok = t.cv.wait_for(g, std::chrono::seconds(2), [&] {
+    return t.gave_up || (t.tab[bar].phases & 1u) != (parity & 1u);
+  });
+  if (!ok || t.gave_up) {
+    t.gave_up = true;
+    t.cv.notify_all();
+    return false;
+  }
+  return true;
+}
+inline void emu_mbar_reset() {
+  auto& t = emu_mbars();
+  std::lock_guard<std::mutex> g(t.mu);
+  t.tab.clear();
+  t.gave_up = false;
+}
+inline long long min(long long a, long long b) { return a < b ? a : b; }
 
 // Runs kernel() for a grid of nclusters clusters of cs CTAs of `threads`
-// threads each (1-D), one cluster at a time; static_bytes of static shared
-// memory follow dyn_bytes of dynamic shared memory in each CTA's arena.
+// threads each (1-D), one cluster at a time; the static slots follow
+// dyn_bytes of dynamic shared memory in each CTA's arena.
 template <typename F>
-void emu_launch(int nclusters, int cs, int threads, size_t dyn_bytes, size_t static_bytes, F kernel) {
+void emu_launch(int nclusters, int cs, int threads, size_t dyn_bytes, F kernel) {
+  const size_t static_bytes = (size_t)EMU_STATIC_SLOTS * EMU_SLOT_BYTES;
   blockDim = {(unsigned)threads, 1, 1};
   gridDim = {(unsigned)(nclusters * cs), 1, 1};
   for (int cl = 0; cl < nclusters; ++cl) {

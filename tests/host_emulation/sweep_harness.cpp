@@ -32,7 +32,7 @@ static void run(const Geom& g, int colour, const float* links, const float* eta,
                 int psi_zero, int nmr, int mode, const double* table, int nclusters) {
   using SH = emu_dslash::SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   using C = cx<float>;
-  emu_launch(nclusters, SH::CS, SH::NS, SH::smem_bytes(), sizeof(float) * (SH::NS / 32) * 3, [&] {
+  emu_launch(nclusters, SH::CS, SH::NS, SH::smem_bytes(), [&] {
     emu_dslash::k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT>(g, colour, (const C*)links, (const C*)eta, (C*)psi, L,
                                                              kappa, psi_zero, nmr, mode, table);
   });
