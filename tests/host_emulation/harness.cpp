@@ -4,6 +4,8 @@
 // launches).
 #include "device_parts.inc"
 
+#include <vector>
+
 EmuDim blockIdx, threadIdx, blockDim, gridDim;
 namespace mbicg {
 namespace emu_dslash {
@@ -130,6 +132,30 @@ void emu_ssor_combine(const int* dims, const int* block, int colour, const doubl
 void emu_colour_add(const int* dims, const int* block, int colour, const double* x, double* psi, int L) {
   const Geom g = make_geom(dims, block);
   grid((g.nd / 2) * g.Vd, L, [&] { emu_sap::k_colour_add<double>(g, colour, (const C*)x, (C*)psi, L); });
+}
+// ABI blocks -> FP16 storage -> the FP16 operator -> ABI, with the link rows
+// rounded to FP16 as the library stores them
+void emu_half_operator(const int* dims, const double* U, const double* in, double* out, int L, double kappa) {
+  const Geom g = make_geom(dims, nullptr);
+  const long long V = g.V;
+  std::vector<__half2> l16((size_t)V * 24), q((size_t)V * L * 12), qo((size_t)V * L * 12);
+  std::vector<float> sc((size_t)V * L), so((size_t)V * L);
+  grid(1, 1, [&] { emu_half::k_links_to_half(V * 4, (const C*)U, l16.data()); });  // grid-stride
+  blockDim = {256, 1, 1};
+  for (long long idx = 0; idx < V * L; ++idx) {
+    blockIdx = {(unsigned)(idx / 256), 0, 0};
+    threadIdx = {(unsigned)(idx % 256), 0, 0};
+    emu_half::k_abi_to_half(V, L, (const C*)in, q.data(), sc.data());
+  }
+  grid(g.V, L, [&] {
+    emu_half::k_dslash_half(g, l16.data(), q.data(), sc.data(), qo.data(), so.data(), L, (float)kappa);
+  });
+  blockDim = {256, 1, 1};
+  for (long long idx = 0; idx < V * L; ++idx) {
+    blockIdx = {(unsigned)(idx / 256), 0, 0};
+    threadIdx = {(unsigned)(idx % 256), 0, 0};
+    emu_half::k_half_to_abi(V, L, qo.data(), so.data(), (C*)out);
+  }
 }
 void emu_mr_update(const int* dims, const int* block, int colour, const double* omega, double* r, const double* q,
                    double* x, double* psi, int L, int first, int last) {

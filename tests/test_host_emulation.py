@@ -28,11 +28,13 @@ PARTS = [
     ("emu_dslash", "dslash.cu", "namespace {", emulation_sources.DSLASH_SEQ_END),
     ("emu_sap", "sap.cu", "namespace {", "}  // namespace\n"),
     ("emu_clover", "clover.cu", "namespace {", "}  // namespace\n"),
+    ("emu_half", "half.cu", "namespace {", "}  // namespace\n"),
 ]
 
 
 def _device_parts():
-    out = ['#include "shim.h"', f'#include "{os.path.join(emulation_sources.CSRC, "common.cuh")}"', "namespace mbicg {"]
+    out = ['#include "shim.h"', "#include <cuda_fp16.h>", "#include <cstring>",
+           f'#include "{os.path.join(emulation_sources.CSRC, "common.cuh")}"', "namespace mbicg {"]
     for ns, name, start, end in PARTS:
         out += [f"namespace {ns} {{", emulation_sources.cut(emulation_sources.read(name), start, end), "}"]
     out.append("}")
@@ -65,6 +67,7 @@ def emu(tmp_path_factory):
                                    ctypes.c_int]
     lib.emu_ssor_combine.argtypes = [I, I, ctypes.c_int, D, D, D, D, D, ctypes.c_int, ctypes.c_double]
     lib.emu_colour_add.argtypes = [I, I, ctypes.c_int, D, D, ctypes.c_int]
+    lib.emu_half_operator.argtypes = [I, D, D, D, ctypes.c_int, ctypes.c_double]
     lib.emu_mr_update.argtypes = [I, I, ctypes.c_int, D, D, D, D, D, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     return lib
 
@@ -317,3 +320,42 @@ def test_ssor_sap_kernels(emu, oracle_mod, clover_case, clover):
     ref = oracle_mod.sap_ext(dims, block, c["U"], kappa, 2, eta, Tinv=c["Ti"] if clover else None,
                              solver=oracle_mod.DOMAIN_SSOR, nssor=1, omega=1.26)
     assert np.max(np.abs(_oracle_layout(psi) - ref)) < 1e-14 * np.max(np.abs(ref))
+# FP16 storage (half.cu)
+# ---------------------------------------------------------------------------
+def _comps(a):
+    """(V, 4, 3, L) complex -> (V, L, 24) reals of each (site, rhs) spinor."""
+    V, L = a.shape[0], a.shape[-1]
+    return np.stack([a.real, a.imag], -1).reshape(V, 12, L, 2).transpose(0, 2, 1, 3).reshape(V, L, 24)
+
+
+def _half_operator(emu, dims, U, psi, kappa):
+    out = np.zeros_like(psi)
+    emu.emu_half_operator(_iv(dims), _dp(np.ascontiguousarray(U)), _dp(np.ascontiguousarray(psi)), _dp(out),
+                          psi.shape[3], kappa)
+    return out
+
+
+@pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 3), ((6, 2, 4, 10), 2)])
+def test_fp16_kernels_round_trip_is_the_oracle_format(emu, oracle_mod, dims, L):
+    """kappa = 0: ABI -> FP16 storage -> operator -> ABI is the input as the
+    oracle's FP16 format represents it, bit for bit (a zero spinor included)."""
+    U = synth.su3_links(dims, 0.5, seed=95)
+    psi = synth.gaussian_source(dims, L, seed=96)
+    psi[3] = 0
+    assert np.array_equal(_half_operator(emu, dims, U, psi, 0.0), oracle_mod.quantize_fp16(psi))
+
+
+@pytest.mark.parametrize("dims,L", [((4, 4, 4, 4), 3), ((6, 2, 4, 10), 2)])
+def test_fp16_operator_kernel_matches_oracle(emu, oracle_mod, dims, L):
+    """The oracle on the FP16-represented links and input, rounded into the
+    FP16 format: equal up to one FP16 step of the output scale."""
+    U = synth.su3_links(dims, 0.5, seed=97)
+    psi = synth.gaussian_source(dims, L, seed=98)
+    kappa = 0.13
+    got = _half_operator(emu, dims, U, psi, kappa)
+    exp = oracle_mod.quantize_fp16(oracle_mod.apply_D(dims, oracle_mod.quantize_links_fp16(U), kappa,
+                                                      oracle_mod.quantize_fp16(psi)))
+    g, e = _comps(got), _comps(exp)
+    s = np.abs(e).max(axis=2, keepdims=True)
+    assert np.all(np.abs(g - e) <= 2.0 ** -10 * s)
+    assert np.mean(np.abs(g - e) > 2.0 ** -20 * s) < 0.05
