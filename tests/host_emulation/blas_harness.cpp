@@ -41,7 +41,53 @@ static void updates(int which, int ncta, int nrow, const void* U, const double* 
     });
 }
 
+template <typename R>
+static void convert(int to_internal, long long nsite, int L, const void* in, void* out) {
+  const int grid = (int)((nsite * L + NT - 1) / NT);
+  if (to_internal)
+    emu_launch(grid, 1, NT, 0, [&] { k_abi_to_internal<R>(nsite, L, (const cx<double>*)in, (cx<R>*)out); });
+  else
+    emu_launch(grid, 1, NT, 0, [&] { k_internal_to_abi<R>(nsite, L, (const cx<R>*)in, (cx<double>*)out); });
+}
+
 extern "C" {
+// ABI [site][12][rhs] FP64 <-> internal [site][rhs][12] in FP64 or FP32
+void emu_convert(int fp64, int to_internal, long long nsite, int L, const void* in, void* out) {
+  if (fp64) convert<double>(to_internal, nsite, L, in, out);
+  else convert<float>(to_internal, nsite, L, in, out);
+}
+int emu_convert_links(long long nlinks, const double* in, double* l64, float* l32) {
+  int bad = 0;
+  emu_launch(3, 1, NT, 0, [&] {
+    k_convert_links(nlinks, (const cx<double>*)in, (cx<double>*)l64, (cx<float>*)l32, &bad);
+  });
+  return bad;
+}
+void emu_residual_from(int fp64, long long nsite, int L, const double* B, const double* W, void* out, double* part,
+                       int ncta) {
+  if (fp64)
+    emu_launch(ncta, 1, NT, 0, [&] {
+      k_residual_from<double>(nsite, L, (const cx<double>*)B, (const cx<double>*)W, (cx<double>*)out, part);
+    });
+  else
+    emu_launch(ncta, 1, NT, 0, [&] {
+      k_residual_from<float>(nsite, L, (const cx<double>*)B, (const cx<double>*)W, (cx<float>*)out, part);
+    });
+}
+int emu_abi_check(long long nrow, int L, const double* in, double* part, int ncta) {
+  int bad = 0;
+  emu_launch(ncta, 1, NT, 0, [&] { k_abi_check(nrow, L, (const cx<double>*)in, part, &bad); });
+  return bad;
+}
+void emu_pack_dummies(long long nrow, int L, int Lt, const double* in, double* out, unsigned long long seed,
+                      int random) {
+  emu_launch(3, 1, NT, 0, [&] {
+    k_pack_dummies(nrow, L, Lt, (const cx<double>*)in, (cx<double>*)out, seed, random);
+  });
+}
+void emu_first_columns(long long nrow, int Lt, int L, const double* in, double* out) {
+  emu_launch(3, 1, NT, 0, [&] { k_first_columns(nrow, Lt, L, (const cx<double>*)in, (cx<double>*)out); });
+}
 int emu_lxl_alpha(int L, const double* part, int nparts, double* G, double* LU, int* piv, double* alpha) {
   int status = 0;
   one_cta(256, [&] { k_lxl_alpha(L, part, nparts, G, LU, piv, alpha, &status); });

@@ -4,9 +4,11 @@ shim_threads.h; the Gram kernel's bulk copies and mbarrier waits emulated),
 against their plain definitions: the fused block inner products (Algorithm 2,
 4.4, 4.9, 4.12 and the P^H P of the QR; FP64 and FP32 storage, ragged last
 tile, several CTAs), the block updates (4.5, 4.6 with 4.10, 4.11, 4.13 and the
-column norms; Y = X M of the QR), and the one-CTA L x L kernels: LU with
-partial pivoting for alpha and beta, zeta, and the Cholesky factor's inverse
-(plain and shifted) of CholeskyQR."""
+column norms; Y = X M of the QR), the one-CTA L x L kernels: LU with partial
+pivoting for alpha and beta, zeta, and the Cholesky factor's inverse (plain
+and shifted) of CholeskyQR; and the conversions: ABI <-> internal layout,
+the link copies with their NaN and SU(3) checks, the residual B - W with its
+column norms, the input scan, and the dummy right-hand-side columns."""
 import ctypes
 import os
 import shutil
@@ -38,6 +40,13 @@ def blas(tmp_path_factory):
     lib.emu_lxl_zeta_beta.argtypes = [ctypes.c_int, D, ctypes.c_int, D, I, D, ctypes.c_int]
     lib.emu_lxl_chol.argtypes = [ctypes.c_int, D, ctypes.c_int, D, ctypes.c_double, ctypes.c_double]
     lib.emu_gram.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, V, V, V, ctypes.c_int, D]
+    lib.emu_convert.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, V, V]
+    lib.emu_convert_links.argtypes = [ctypes.c_longlong, D, D, ctypes.POINTER(ctypes.c_float)]
+    lib.emu_residual_from.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_int, D, D, V, D, ctypes.c_int]
+    lib.emu_abi_check.argtypes = [ctypes.c_longlong, ctypes.c_int, D, D, ctypes.c_int]
+    lib.emu_pack_dummies.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, D, D, ctypes.c_ulonglong,
+                                     ctypes.c_int]
+    lib.emu_first_columns.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, D, D]
     lib.emu_updates.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, V, D, V, V, V,
                                 D, V, V, V, D, D, V]
     return lib
@@ -273,3 +282,95 @@ def test_block_updates(blas, fp64, L):
     assert np.max(np.abs(m(R2) - rr)) < scale(rr)
     assert np.max(np.abs(m(P2) - pr)) < scale(pr)
     assert np.max(np.abs(part.sum(0) - np.sum(np.abs(m(R2)) ** 2, 0))) < tol * np.max(np.sum(np.abs(rr) ** 2, 0))
+
+
+# ---------------------------------------------------------------------------
+# conversions, input checks, dummy columns
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("fp64", [1, 0])
+def test_layout_conversions(blas, fp64):
+    rng = np.random.default_rng(400)
+    nsite, L = 53, 5
+    abi = np.ascontiguousarray(_rand(rng, nsite, 12, L))        # [site][spin*3+colour][rhs]
+    dt = np.complex128 if fp64 else np.complex64
+    internal = np.zeros((nsite, L, 12), dt)
+    blas.emu_convert(fp64, 1, nsite, L, _v(abi), _v(internal))
+    assert np.array_equal(internal, abi.transpose(0, 2, 1).astype(dt))
+    back = np.zeros_like(abi)
+    blas.emu_convert(fp64, 0, nsite, L, _v(internal), _v(back))
+    assert np.array_equal(back, abi.astype(dt).astype(np.complex128))
+
+
+def _su3(rng, n):
+    H = _rand(rng, n, 3, 3)
+    H = (H + H.conj().transpose(0, 2, 1)) / 2
+    H -= np.trace(H, axis1=1, axis2=2)[:, None, None] * np.eye(3) / 3
+    w, v = np.linalg.eigh(H)
+    return v @ (np.exp(0.5j * w)[..., None] * v.conj().transpose(0, 2, 1))
+
+
+def test_link_conversion_and_checks(blas):
+    rng = np.random.default_rng(401)
+    n = 300
+    U = np.ascontiguousarray(_su3(rng, n))
+    l64, l32 = np.zeros_like(U), np.zeros(U.shape, np.complex64)
+    f32 = ctypes.POINTER(ctypes.c_float)
+    assert blas.emu_convert_links(n, _d(U), _d(l64), l32.ctypes.data_as(f32)) == 0
+    assert np.array_equal(l64, U) and np.array_equal(l32, U.astype(np.complex64))
+    bad = U.copy()
+    bad[7] *= np.exp(0.1j)  # unitary, det != 1
+    assert blas.emu_convert_links(n, _d(bad), _d(l64), l32.ctypes.data_as(f32)) == 2
+    bad = U.copy()
+    bad[9, 1, 2] += 1e-8  # not unitary
+    assert blas.emu_convert_links(n, _d(bad), _d(l64), l32.ctypes.data_as(f32)) == 2
+    bad = U.copy()
+    bad[11, 0, 0] = np.nan
+    assert blas.emu_convert_links(n, _d(bad), _d(l64), l32.ctypes.data_as(f32)) & 1
+
+
+@pytest.mark.parametrize("fp64", [1, 0])
+@pytest.mark.parametrize("L", [1, 5, 12])
+def test_residual_and_input_scan(blas, fp64, L):
+    rng = np.random.default_rng(402 + L)
+    nsite, ncta = 41, 3
+    B, W = (np.ascontiguousarray(_rand(rng, nsite, L, 12)) for _ in range(2))
+    dt = np.complex128 if fp64 else np.complex64
+    out = np.zeros((nsite, L, 12), dt)
+    part = np.zeros((ncta, L))
+    blas.emu_residual_from(fp64, nsite, L, _d(B), _d(W), _v(out), _d(part), ncta)
+    r = B - W
+    assert np.array_equal(out, r.astype(dt))
+    assert np.allclose(part.sum(0), np.sum(np.abs(r) ** 2, axis=(0, 2)), rtol=1e-14, atol=0)
+    blas.emu_residual_from(fp64, nsite, L, _d(B), None, _v(out), _d(part), ncta)  # W = NULL: R = B
+    assert np.array_equal(out, B.astype(dt))
+    # the ABI input scan: column norms and NaN/Inf
+    abi = np.ascontiguousarray(_rand(rng, nsite * 12, L))
+    part = np.zeros((ncta, L))
+    assert blas.emu_abi_check(nsite * 12, L, _d(abi), _d(part), ncta) == 0
+    assert np.allclose(part.sum(0), np.sum(np.abs(abi) ** 2, 0), rtol=1e-14, atol=0)
+    abi[17, L - 1] = np.inf
+    assert blas.emu_abi_check(nsite * 12, L, _d(abi), _d(part), ncta) & 1
+
+
+def test_dummy_columns(blas):
+    """The first L columns copied, the others seeded Gaussian numbers (zeros
+    when not random), the same for the same seed; first_columns inverts it."""
+    rng = np.random.default_rng(403)
+    nrow, L, Lt = 12 * 500, 3, 8
+    B = np.ascontiguousarray(_rand(rng, nrow, L))
+    out, out2, zero = (np.zeros((nrow, Lt), complex) for _ in range(3))
+    blas.emu_pack_dummies(nrow, L, Lt, _d(B), _d(out), 12345, 1)
+    blas.emu_pack_dummies(nrow, L, Lt, _d(B), _d(out2), 12345, 1)
+    blas.emu_pack_dummies(nrow, L, Lt, _d(B), _d(zero), 12345, 0)
+    assert np.array_equal(out[:, :L], B) and np.array_equal(out, out2)
+    assert not np.any(zero[:, L:])
+    d = out[:, L:].ravel()
+    x = np.concatenate([d.real, d.imag])
+    assert abs(x.mean()) < 0.02 and abs(x.var() - 1.0) < 0.03     # N(0, 1) parts, 60000 samples
+    assert abs(np.corrcoef(d.real, d.imag)[0, 1]) < 0.02
+    other = np.zeros_like(out)
+    blas.emu_pack_dummies(nrow, L, Lt, _d(B), _d(other), 54321, 1)
+    assert not np.allclose(other[:, L:], out[:, L:])
+    first = np.zeros((nrow, L), complex)
+    blas.emu_first_columns(nrow, Lt, L, _d(out), _d(first))
+    assert np.array_equal(first, B)
