@@ -362,26 +362,27 @@ __host__ __device__ constexpr int herm_off(int i, int j) {  // i < j
   return 6 + 2 * (i * 6 - i * (i + 1) / 2 + (j - i - 1));
 }
 
-// y = M x for the packed matrix M of one site (m: its 72 reals)
+// y = M x for the packed matrix M of one site (m: its 72 reals); each entry is
+// loaded where it is used (the off-diagonal ones twice, from L1), which keeps
+// few registers live inside kernels that are already near their limit
 template <typename R>
 __device__ __forceinline__ void herm_apply(const R* __restrict__ m, const Spinor<R>& x, Spinor<R>& y) {
   const cx<R>* xv = &x.c[0][0];
   cx<R>* yv = &y.c[0][0];
 #pragma unroll
   for (int b = 0; b < 2; ++b) {
-    R v[36];
-#pragma unroll
-    for (int k = 0; k < 36; ++k) v[k] = __ldg(m + 36 * b + k);
+    const R* mb = m + 36 * b;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
+      const R d = __ldg(mb + i);
       const cx<R> xi = xv[6 * b + i];
-      cx<R> acc = mk(v[i] * xi.re, v[i] * xi.im);
+      cx<R> acc = mk(d * xi.re, d * xi.im);
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
         if (j == i) continue;
         const int o = i < j ? herm_off(i, j) : herm_off(j, i);
-        const cx<R> e = i < j ? mk(v[o], v[o + 1]) : mk(v[o], -v[o + 1]);
-        cmac(acc, e, xv[6 * b + j]);
+        const R re = __ldg(mb + o), im = __ldg(mb + o + 1);
+        cmac(acc, i < j ? mk(re, im) : mk(re, -im), xv[6 * b + j]);
       }
       yv[6 * b + i] = acc;
     }

@@ -479,12 +479,14 @@ __device__ __forceinline__ void domain_hops(const Geom& g, const float4* vL, uin
   }
 }
 
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
+// CM = 1: the Jacobi-preconditioned clover matrix, every hop sum multiplied by
+// T^{-1} of its site (tinv, packed, read through L1)
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM>
 __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS,
                                   (SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS <= 256) ? 2 : 1)
     k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const cx<float>* __restrict__ eta,
                 cx<float>* __restrict__ psi, int L, float kappa, int psi_zero, int nmr, int mode,
-                const double* __restrict__ table) {
+                const double* __restrict__ table, const float* __restrict__ tinv) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   constexpr int NS = SH::NS;
   constexpr int CS = SH::CS;
@@ -569,6 +571,11 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
       Spinor<float> acc, pv;
       domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, true>(g, cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, c, s, L,
                                                        rhs, links, psi, acc);
+      if (CM == 1) {
+        Spinor<float> h;
+        herm_apply<float>(tinv + (size_t)s * HERM_PER_SITE, acc, h);
+        acc = h;
+      }
       load_spinor(eta + off, r0);
       planes_to_spinor(cur, NS, tid, pv);
 #pragma unroll
@@ -590,9 +597,15 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
       const bool last = (it == nmr - 1);
       Spinor<float> q, rv;
       const bool need_q = (mode == 0) || !last;
-      if (need_q)
+      if (need_q) {
         domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, false>(g, cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, c, s,
                                                           L, rhs, links, psi, q);
+        if (CM == 1) {
+          Spinor<float> h;
+          herm_apply<float>(tinv + (size_t)s * HERM_PER_SITE, q, h);
+          q = h;
+        }
+      }
       planes_to_spinor(cur, NS, tid, rv);
       if (need_q) {
 #pragma unroll
@@ -672,10 +685,10 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
 
 // sets the sweep kernel's shared-memory and cluster attributes and returns
 // how many of its clusters the GPU holds at once
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM>
 int sweep_setup(cudaLaunchConfig_t cfg) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
-  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT>;
+  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::smem_bytes());
   if (SH::CS > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cfg.gridDim = dim3((unsigned)SH::CS);
@@ -687,11 +700,12 @@ int sweep_setup(cudaLaunchConfig_t cfg) {
   return n;
 }
 
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM>
 bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
-                  cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table) {
+                  cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table,
+                  const float* tinv) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
-  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT>;
+  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM>;
   const size_t shm = SH::smem_bytes();
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(SH::NS);
@@ -707,11 +721,12 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
   // one persistent cluster per cluster slot of the GPU (clusters must fit
   // in one GPC, so fewer than SMs / CS may be resident at once); set up once
   // per process, thread-safely (contexts may run on several host threads)
-  static const int max_clusters = sweep_setup<DX, DY, DZ, DT, CX, CY, CZ, CT>(cfg);
+  static const int max_clusters = sweep_setup<DX, DY, DZ, DT, CX, CY, CZ, CT, CM>(cfg);
   const long long nitems = (long long)(g.nd / 2) * L;
   const int nclu = (int)std::min<long long>(max_clusters, nitems);
   cfg.gridDim = dim3((unsigned)(SH::CS * nclu));
-  cudaLaunchKernelEx(&cfg, kern, g, colour, links, eta, psi, L, (float)kappa, psi_zero ? 1 : 0, nmr, mode, table);
+  cudaLaunchKernelEx(&cfg, kern, g, colour, links, eta, psi, L, (float)kappa, psi_zero ? 1 : 0, nmr, mode, table,
+                     tinv);
   ++*ex.launches;
   return true;
 }
@@ -719,15 +734,26 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
 }  // namespace
 
 bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
-                     cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table) {
+                     cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table,
+                     const float* tinv) {
   if (mode == 1 || !g.su3) return false;  // the kernel rebuilds the third link row
   const int* bk = g.blk;
   // 8^4: eight CTAs of 8 x 4 x 4 x 4 sites (x, the unit-stride direction, is
   // not split, so its hops never leave the CTA); 4^4: one CTA
-  if (bk[0] == 8 && bk[1] == 8 && bk[2] == 8 && bk[3] == 8)
-    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
-  if (bk[0] == 4 && bk[1] == 4 && bk[2] == 4 && bk[3] == 4)
-    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
+  if (bk[0] == 8 && bk[1] == 8 && bk[2] == 8 && bk[3] == 8) {
+    if (tinv)
+      return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode,
+                                                     table, tinv);
+    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 0>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode,
+                                                   table, nullptr);
+  }
+  if (bk[0] == 4 && bk[1] == 4 && bk[2] == 4 && bk[3] == 4) {
+    if (tinv)
+      return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode,
+                                                     table, tinv);
+    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 0>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode,
+                                                   table, nullptr);
+  }
   return false;
 }
 

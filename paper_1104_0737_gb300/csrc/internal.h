@@ -135,12 +135,13 @@ template <typename R>
 void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* r,
                       cx<R>* q, double* dots, int L, double kappa, int* nchunk_out, const R* tinv = nullptr);
 // One whole colour sweep (residual, nmr MR steps, psi += x) in one kernel,
-// the domain kept on chip by a thread-block cluster; FP32, MR modes 0 and 2,
-// domain shapes 8^4 and 4^4.  Returns false (nothing launched) otherwise.
+// the domain kept on chip by a thread-block cluster; FP32, MR modes 0 and 3,
+// domain shapes 8^4 and 4^4, with T^{-1} (tinv) for the Jacobi-preconditioned
+// clover matrix.  Returns false (nothing launched) otherwise.
 // table: the frozen step lengths of this (cycle, colour), [nmr][nd/2] complex.
 bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
                      cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode,
-                     const double* table);
+                     const double* table, const float* tinv = nullptr);
 // SSOR (Sec. 2.2): one wavefront level of z = (1 - omega L)^{-1} y (fwd) or
 // z = (1 - omega U)^{-1} y on every domain of one colour, L and U the forward
 // and backward hops inside a domain (times T^{-1} with tinv); komega =
@@ -190,8 +191,7 @@ cudaError_t sap_prepare_ssor(const Geom& g, SapWork& w, cudaStream_t stream);
 // the shared sums where the domain's residual is nonzero; *unset is raised if
 // an entry stays unrecorded), 3 frozen replay.
 // table = complex [ncycle][2][nmr][nd/2] (modes 2, 3).
-// tinv != NULL: SAP for the Jacobi-preconditioned clover matrix (multi-kernel
-// path; the fused sweep has no clover term).  ssor != NULL: SSOR domain solves
+// tinv != NULL: SAP for the Jacobi-preconditioned clover matrix.  ssor != NULL: SSOR domain solves
 // instead of MR (nmr, mr_mode, table and unset unused; w.levels and w.ssor set).
 template <typename R>
 void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* eta, cx<R>* psi,

@@ -257,10 +257,11 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
   for (int cyc = 0; cyc < ncycle; ++cyc) {
     for (int colour = 0; colour < 2; ++colour) {
       if constexpr (std::is_same<R, float>::value) {
-        if (allow_fused && !tinv && (mr_mode == 0 || mr_mode == 3)) {
+        if (allow_fused && (mr_mode == 0 || mr_mode == 3)) {
           const double* tab = table ? table + ((long long)cyc * 2 + colour) * nmr * ndc * 2 : nullptr;
           Timed t(ex, KC_SAP_SWEEP);
-          if (sap_sweep_fused(ex, g, colour, links, eta, psi, L, kappa, cyc == 0 && colour == 0, nmr, mr_mode, tab))
+          if (sap_sweep_fused(ex, g, colour, links, eta, psi, L, kappa, cyc == 0 && colour == 0, nmr, mr_mode, tab,
+                              tinv))
             continue;
         }
       }
