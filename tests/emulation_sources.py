@@ -140,3 +140,123 @@ def blas_parts(csrc=CSRC):
     bl, slots = bind_shared(bl)
     return "\n".join([f"#define EMU_STATIC_SLOTS {max(slots, 1)}", '#include "shim_threads.h"',
                       common, internal, "namespace mbicg {", "namespace emu_blas {", bl, "}", "}"])
+
+
+def _split_launch_config(cfg):
+    parts = _split_top(cfg)
+    while len(parts) < 4:
+        parts.append("0")
+    return parts
+
+
+def _match_paren(src, i):
+    """Index of the parenthesis closing the one at src[i]."""
+    depth = 0
+    for j in range(i, len(src)):
+        if src[j] == "(":
+            depth += 1
+        elif src[j] == ")":
+            depth -= 1
+            if depth == 0:
+                return j
+    raise ValueError("unbalanced parentheses")
+
+
+def _kernel_name_start(src, i):
+    """Start of the (possibly templated) kernel name that ends at src[i - 1]."""
+    j = i
+    if src[j - 1] == ">":  # template arguments
+        depth = 0
+        while True:
+            j -= 1
+            if src[j] == ">":
+                depth += 1
+            elif src[j] == "<":
+                depth -= 1
+                if depth == 0:
+                    break
+    while j > 0 and (src[j - 1].isalnum() or src[j - 1] in "_:"):
+        j -= 1
+    return j
+
+
+def rewrite_launches(src):
+    """kernel<<<grid, block, smem, stream>>>(args) -> an emulated launch that
+    runs the kernel to completion, and cudaLaunchKernelEx(cfg, kernel, args)
+    -> emu_launch_ex(cfg, kernel, args)."""
+    while True:
+        i = src.find("<<<")
+        if i < 0:
+            break
+        start = _kernel_name_start(src, i)
+        k = src.index(">>>", i)
+        grid, block, smem, stream = _split_launch_config(src[i + 3:k])
+        a = src.index("(", k)
+        b = _match_paren(src, a)
+        call = f"{src[start:i]}{src[a:b + 1]}"
+        src = (src[:start] + f"emu_kernel_launch({grid}, {block}, {smem}, {stream}, [&] {{ {call}; }})" +
+               src[b + 1:])
+    return src.replace("cudaLaunchKernelEx(", "emu_launch_ex(")
+
+
+def driver_parts(csrc=CSRC):
+    """The SAP driver (sap.cu) and everything it launches (dslash.cu), host
+    code included, for the threaded emulation: launches rewritten onto the
+    emulator, inline PTX helpers replaced, shared memory bound to the arenas."""
+    common = read("common.cuh", csrc)
+    common = replace_body(common, "__device__ __forceinline__ void load_spinor(const cx<float>* p, Spinor<float>& s)",
+                          "{ for (int k = 0; k < 12; ++k) (&s.c[0][0])[k] = p[k]; }")
+    common = replace_body(common, "__device__ __forceinline__ void store_spinor(cx<float>* p, const Spinor<float>& s)",
+                          "{ for (int k = 0; k < 12; ++k) p[k] = (&s.c[0][0])[k]; }")
+    internal = read("internal.h", csrc).replace('#include "common.cuh"', "")
+    ds = read("dslash.cu", csrc)
+    ds = ds[ds.index("namespace mbicg {"):]
+    ds = replace_body(ds, "__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank)",
+                      "{ return emu_mapa(local, rank); }")
+    ds = replace_body(ds, "__device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr)",
+                      "{ return emu_ld_cluster_f4(addr); }")
+    sp = read("sap.cu", csrc)
+    sp = sp[sp.index("namespace mbicg {"):]
+    body = rewrite_launches(ds + "\n" + sp)
+    body, slots = bind_shared(body)
+    return "\n".join([f"#define EMU_STATIC_SLOTS {max(slots, 1)}", '#include "shim_threads.h"',
+                      "#include <algorithm>", "#include <cstdlib>", "#include <type_traits>",
+                      '#include "emu_runtime.h"', common, internal, body])
+
+
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def _patched_common(csrc):
+    common = read("common.cuh", csrc)
+    common = replace_body(common, "__device__ __forceinline__ void load_spinor(const cx<float>* p, Spinor<float>& s)",
+                          "{ for (int k = 0; k < 12; ++k) (&s.c[0][0])[k] = p[k]; }")
+    common = replace_body(common, "__device__ __forceinline__ void store_spinor(cx<float>* p, const Spinor<float>& s)",
+                          "{ for (int k = 0; k < 12; ++k) p[k] = (&s.c[0][0])[k]; }")
+    for sig, body in MBAR_BODIES.items():
+        common = replace_body(common, sig, body)
+    return common
+
+
+LIBRARY_SOURCES = ["api.cu", "dslash.cu", "sap.cu", "blas.cu", "half.cu"]
+
+
+def library_unit(name, csrc=CSRC):
+    """One translation unit of the library for the emulated build: the file
+    itself with common.cuh (inline PTX replaced) and internal.h inlined, the
+    launches rewritten onto the emulator and shared memory bound to the
+    arenas."""
+    src = read(name, csrc)
+    head = _patched_common(csrc) + "\n" + read("internal.h", csrc).replace('#include "common.cuh"', "")
+    src = src.replace('#include "internal.h"', head)
+    src = src.replace('#include "../../include/mbicg.h"', f'#include "{os.path.join(INCLUDE, "mbicg.h")}"')
+    src = src.replace("#include <cooperative_groups.h>", "")
+    if name == "dslash.cu":
+        src = replace_body(src, "__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank)",
+                           "{ return emu_mapa(local, rank); }")
+        src = replace_body(src, "__device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr)",
+                           "{ return emu_ld_cluster_f4(addr); }")
+    src = rewrite_launches(src)
+    src, slots = bind_shared(src)
+    return "\n".join([f"#define EMU_STATIC_SLOTS {max(slots, 1)}", '#include "shim_threads.h"',
+                      '#include "emu_runtime.h"', src])

@@ -224,9 +224,17 @@ inline long long min(long long a, long long b) { return a < b ? a : b; }
 // threads each (1-D), one cluster at a time; the static slots follow
 // dyn_bytes of dynamic shared memory in each CTA's arena.
 template <typename F>
+void emu_launch3(int nclusters, int cs, dim3 block, size_t dyn_bytes, F kernel);
+template <typename F>
 void emu_launch(int nclusters, int cs, int threads, size_t dyn_bytes, F kernel) {
+  emu_launch3(nclusters, cs, dim3((unsigned)threads, 1, 1), dyn_bytes, kernel);
+}
+// as emu_launch, with a 3-D CTA shape (thread t has x = t % block.x fastest)
+template <typename F>
+void emu_launch3(int nclusters, int cs, dim3 block, size_t dyn_bytes, F kernel) {
+  const int threads = (int)(block.x * block.y * block.z);
   const size_t static_bytes = (size_t)EMU_STATIC_SLOTS * EMU_SLOT_BYTES;
-  blockDim = {(unsigned)threads, 1, 1};
+  blockDim = {block.x, block.y, block.z};
   gridDim = {(unsigned)(nclusters * cs), 1, 1};
   for (int cl = 0; cl < nclusters; ++cl) {
     EmuCluster cluster;
@@ -254,7 +262,9 @@ void emu_launch(int nclusters, int cs, int threads, size_t dyn_bytes, F kernel) 
     for (int r = 0; r < cs; ++r)
       for (int t = 0; t < threads; ++t) {
         Arg& a = args[(size_t)r * threads + t];
-        a.t = EmuThread{{(unsigned)(cl * cs + r), 0, 0}, {(unsigned)t, 0, 0}, ctas[r].get(), &cluster, (unsigned)r};
+        const unsigned tx = (unsigned)t % block.x, ty = ((unsigned)t / block.x) % block.y,
+                       tz = (unsigned)t / (block.x * block.y);
+        a.t = EmuThread{{(unsigned)(cl * cs + r), 0, 0}, {tx, ty, tz}, ctas[r].get(), &cluster, (unsigned)r};
         a.k = &kernel;
         const int rc = pthread_create(&tids[(size_t)r * threads + t], &attr,
                                       [](void* p) -> void* {

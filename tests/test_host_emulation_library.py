@@ -1,0 +1,164 @@
+"""The whole library, host code and kernels, run on the CPU through its C ABI
+(test infrastructure: built here into a temporary directory from the CUDA
+sources, never by the package's build and never loaded by the package).
+Each CUDA source becomes a g++ translation unit (tests/emulation_sources.py:
+launches rewritten onto the threaded emulator, inline PTX replaced); the few
+CUDA runtime calls are emulated over host memory
+(tests/host_emulation/emu_cudart.cpp; stream capture is refused, so the
+solver runs its iterations eagerly).  Checked against the oracle: the
+operator with host pointers in FP64 and FP32, and mbicg_block_solve in FP64
+and in mixed precision (reliable updates), with dummy right-hand sides and an
+initial guess, plus the ABI's argument errors.  This exercises the solver's
+host logic of Algorithm 2 on a machine without a GPU; the -m gpu tests run the
+same code on the hardware."""
+import ctypes
+import os
+import shutil
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import emulation_sources
+import paper_1104_0737_gb300 as mb  # the ctypes structures only; no library is loaded
+import synth
+
+HERE = os.path.join(emulation_sources.ROOT, "tests", "host_emulation")
+CUDA_INCLUDE = "/usr/local/cuda/include"
+DIMS, L, KAPPA = (4, 4, 4, 4), 2, 0.12
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    if shutil.which("g++") is None or not os.path.exists(os.path.join(CUDA_INCLUDE, "cuda_runtime.h")):
+        pytest.skip("g++ or the CUDA headers are missing")
+    d = tmp_path_factory.mktemp("library_emulation")
+    for f in ("shim_threads.h", "emu_runtime.h"):
+        shutil.copy(os.path.join(HERE, f), d / f)
+    units = []
+    for name in emulation_sources.LIBRARY_SOURCES:
+        src = d / name.replace(".cu", ".cpp")
+        src.write_text(emulation_sources.library_unit(name))
+        units.append(src)
+    units.append(os.path.join(HERE, "emu_cudart.cpp"))
+    flags = ["g++", "-std=c++20", "-O1", "-fPIC", "-pthread", "-I", str(d), "-I", emulation_sources.CSRC,
+             "-I", CUDA_INCLUDE]
+
+    def compile_one(src):
+        obj = str(d / (os.path.basename(str(src)) + ".o"))
+        subprocess.run(flags + ["-c", str(src), "-o", obj], check=True)
+        return obj
+
+    with ThreadPoolExecutor(len(units)) as ex:
+        objs = list(ex.map(compile_one, units))
+    so = str(d / "libmbicg_emu.so")
+    # -Bsymbolic: calls bind to the emulated runtime even when the real CUDA
+    # runtime (linked into the real library) is loaded in the same process
+    subprocess.run(["g++", "-shared", "-pthread", "-Wl,-Bsymbolic", *objs, "-o", so], check=True)
+    lb = ctypes.CDLL(so)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    lb.mbicg_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.c_int, vp]
+    lb.mbicg_destroy.argtypes = [vp]
+    lb.mbicg_load_gauge.argtypes = [vp, vp]
+    lb.mbicg_apply_D.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    lb.mbicg_block_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                     ctypes.POINTER(mb.mbicg_params), ip, dp]
+    lb.mbicg_default_params.argtypes = [ctypes.POINTER(mb.mbicg_params)]
+    lb.mbicg_get_stats.argtypes = [vp, ctypes.POINTER(mb.mbicg_stats)]
+    lb.mbicg_last_error.restype = ctypes.c_char_p
+    lb.mbicg_last_error.argtypes = [vp]
+    return lb
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    c = ctypes.c_void_p()
+    assert lib.mbicg_create(ctypes.byref(c), (ctypes.c_int * 4)(*DIMS), 0, None) == mb.MBICG_OK
+    U = synth.su3_links(DIMS, 0.4, seed=1000)
+    assert lib.mbicg_load_gauge(c, ctypes.c_void_p(U.ctypes.data)) == mb.MBICG_OK
+    yield c, U
+    lib.mbicg_destroy(c)
+
+
+def _v(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _params(lib, **kw):
+    p = mb.mbicg_params()
+    lib.mbicg_default_params(ctypes.byref(p))
+    p.block = (ctypes.c_int * 4)(2, 2, 2, 2)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _solve(lib, c, B, X, p, tol=1e-10):
+    it = ctypes.c_int(0)
+    tres = np.zeros(B.shape[3])
+    rc = lib.mbicg_block_solve(c, _v(B), _v(X), B.shape[3], KAPPA, tol, ctypes.byref(p), ctypes.byref(it),
+                               tres.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    st = mb.mbicg_stats()
+    lib.mbicg_get_stats(c, ctypes.byref(st))
+    return rc, it.value, tres, st
+
+
+def _residual(oracle_mod, U, B, X):
+    R = B - oracle_mod.apply_D(DIMS, U, KAPPA, X)
+    n = B.shape[3]
+    return np.linalg.norm(R.reshape(-1, n), axis=0) / np.linalg.norm(B.reshape(-1, n), axis=0)
+
+
+@pytest.mark.parametrize("prec,tol", [(mb.MBICG_FP64, 1e-14), (mb.MBICG_FP32, 1e-6)])
+def test_operator_through_the_abi(lib, ctx, oracle_mod, prec, tol):
+    c, U = ctx
+    B = synth.gaussian_source(DIMS, L, seed=2001)
+    out = np.empty_like(B)
+    assert lib.mbicg_apply_D(c, _v(B), _v(out), L, KAPPA, prec) == mb.MBICG_OK
+    ref = oracle_mod.apply_D(DIMS, U, KAPPA, B)
+    assert np.max(np.abs(out - ref)) < tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec_D", [mb.MBICG_FP64, mb.MBICG_FP32])
+def test_block_solve_through_the_abi(lib, ctx, oracle_mod, prec_D):
+    c, U = ctx
+    B = synth.gaussian_source(DIMS, L, seed=2000)
+    X = np.empty_like(B)
+    rc, iters, tres, st = _solve(lib, c, B, X, _params(lib, prec_D=prec_D))
+    assert rc == mb.MBICG_OK and iters > 0, lib.mbicg_last_error(c)
+    assert np.max(tres) <= 1e-10 and np.max(_residual(oracle_mod, U, B, X)) <= 1e-10
+    # the mixed-precision loop refreshes its residual with the FP64 operator
+    assert (st.reliable_updates > 0) == (prec_D == mb.MBICG_FP32)
+    ref = oracle_mod.block_bicgstab(DIMS, U, KAPPA, B, 1e-12, ncycle=4, nmr=4, block=(2, 2, 2, 2),
+                                    mr_mode=oracle_mod.MR_FROZEN)
+    assert np.max(np.abs(X - ref["X"])) < 1e-8 * np.max(np.abs(ref["X"]))
+
+
+def test_dummy_columns_and_initial_guess(lib, ctx, oracle_mod):
+    c, U = ctx
+    B = synth.gaussian_source(DIMS, 2, seed=2002)
+    X = np.empty_like(B)
+    rc, _, tres, _ = _solve(lib, c, B, X, _params(lib, dummy_rhs=2, dummy_seed=7))
+    assert rc == mb.MBICG_OK and np.max(_residual(oracle_mod, U, B, X)) <= 1e-10
+    # restarting from the solution converges at once
+    X2 = X.copy()
+    rc, iters, _, _ = _solve(lib, c, B, X2, _params(lib, use_x0=1))
+    assert rc == mb.MBICG_OK and iters <= 1
+
+
+def test_abi_errors(lib, ctx):
+    c, _ = ctx
+    B = synth.gaussian_source(DIMS, 1, seed=2003)
+    X = np.empty_like(B)
+    assert _solve(lib, c, B, X, _params(lib), tol=0.0)[0] == mb.MBICG_EINVAL
+    assert _solve(lib, c, B, X, _params(lib, block=(ctypes.c_int * 4)(4, 4, 4, 4)))[0] == mb.MBICG_EINVAL
+    B0 = np.zeros_like(B)
+    assert _solve(lib, c, B0, X, _params(lib))[0] == mb.MBICG_EINVAL
+    Bn = B.copy()
+    Bn[0, 0, 0, 0] = np.nan
+    assert _solve(lib, c, Bn, X, _params(lib))[0] == mb.MBICG_ENAN
+    fresh = ctypes.c_void_p()
+    assert lib.mbicg_create(ctypes.byref(fresh), (ctypes.c_int * 4)(*DIMS), 0, None) == mb.MBICG_OK
+    assert _solve(lib, fresh, B, X, _params(lib))[0] == mb.MBICG_ENOGAUGE
+    lib.mbicg_destroy(fresh)

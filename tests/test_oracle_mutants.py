@@ -118,21 +118,25 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
         src = f.read()
     for name, old, _new, _pin in MUTANTS:
         assert old in src, f"mutation pattern no longer in oracle.c: {name}"
-    workers = 4
+    workers = max(4, os.cpu_count() or 4)
     threads = max(1, (os.cpu_count() or 4) // workers)
 
-    # control: the unmodified oracle passes every pin file used below
-    for pin in sorted({m[3] for m in MUTANTS}):
-        rc, out = _run_copy(str(tmp_path / f"control_{pin[:-3]}"), src, pin, os.cpu_count() or 4)
-        assert rc == 0, f"unmodified oracle fails {pin}:\n{out}"
+    # the controls (the unmodified oracle on every pin file used below) and the
+    # mutants in one pool
+    pins = sorted({m[3] for m in MUTANTS})
+    jobs = [("control " + pin, src, pin) for pin in pins] + \
+           [(name, src.replace(old, new, 1), pin) for name, old, new, pin in MUTANTS]
 
     def one(k):
-        name, old, new, pin = MUTANTS[k]
-        rc, out = _run_copy(str(tmp_path / f"m{k:02d}"), src.replace(old, new, 1), pin, threads)
+        name, source, pin = jobs[k]
+        rc, out = _run_copy(str(tmp_path / f"j{k:02d}"), source, pin, threads)
         return name, rc, out
 
     with ThreadPoolExecutor(workers) as ex:
-        results = list(ex.map(one, range(len(MUTANTS))))
+        done = list(ex.map(one, range(len(jobs))))
+    for name, rc, out in done[:len(pins)]:
+        assert rc == 0, f"unmodified oracle fails its pins ({name}):\n{out}"
+    results = done[len(pins):]
     missed = [n for n, rc, _ in results if rc == 0]
     broken = [(n, out) for n, rc, out in results if rc not in (0, 1)]
     assert not broken, f"mutants that did not build or collect: {broken}"
