@@ -19,3 +19,13 @@ def oracle_mod():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def emulated_library(tmp_path_factory):
+    """The test-only emulated library (tests/emulated_library.py), built once."""
+    import emulated_library as el
+
+    if not el.available():
+        pytest.skip("g++ or the CUDA headers are missing")
+    return el.build(str(tmp_path_factory.mktemp("library_emulation")))

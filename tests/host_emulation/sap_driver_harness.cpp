@@ -21,6 +21,10 @@ extern "C" cudaError_t cudaGetLastError(void) { return cudaSuccess; }
 // per-kernel timing stays off in the emulation; these only satisfy the linker
 extern "C" cudaError_t cudaEventCreate(cudaEvent_t*) { return cudaErrorNotSupported; }
 extern "C" cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t) { return cudaErrorNotSupported; }
+extern "C" cudaError_t cudaMemcpyAsync(void* d, const void* s, size_t n, enum cudaMemcpyKind, cudaStream_t) {
+  memmove(d, s, n);
+  return cudaSuccess;
+}
 extern "C" cudaError_t cudaMemsetAsync(void* p, int v, size_t n, cudaStream_t) {
   memset(p, v, n);
   return cudaSuccess;

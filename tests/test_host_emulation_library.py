@@ -1,6 +1,7 @@
 """The whole library, host code and kernels, run on the CPU through its C ABI
-(test infrastructure: built here into a temporary directory from the CUDA
-sources, never by the package's build and never loaded by the package).
+(test infrastructure: built by tests/emulated_library.py into a temporary
+directory from the CUDA sources, never by the package's build and never
+loaded by the package).
 Each CUDA source becomes a g++ translation unit (tests/emulation_sources.py:
 launches rewritten onto the threaded emulator, inline PTX replaced); the few
 CUDA runtime calls are emulated over host memory
@@ -12,63 +13,19 @@ initial guess, plus the ABI's argument errors.  This exercises the solver's
 host logic of Algorithm 2 on a machine without a GPU; the -m gpu tests run the
 same code on the hardware."""
 import ctypes
-import os
-import shutil
-import subprocess
-from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
 
-import emulation_sources
 import paper_1104_0737_gb300 as mb  # the ctypes structures only; no library is loaded
 import synth
 
-HERE = os.path.join(emulation_sources.ROOT, "tests", "host_emulation")
-CUDA_INCLUDE = "/usr/local/cuda/include"
 DIMS, L, KAPPA = (4, 4, 4, 4), 2, 0.12
 
 
 @pytest.fixture(scope="module")
-def lib(tmp_path_factory):
-    if shutil.which("g++") is None or not os.path.exists(os.path.join(CUDA_INCLUDE, "cuda_runtime.h")):
-        pytest.skip("g++ or the CUDA headers are missing")
-    d = tmp_path_factory.mktemp("library_emulation")
-    for f in ("shim_threads.h", "emu_runtime.h"):
-        shutil.copy(os.path.join(HERE, f), d / f)
-    units = []
-    for name in emulation_sources.LIBRARY_SOURCES:
-        src = d / name.replace(".cu", ".cpp")
-        src.write_text(emulation_sources.library_unit(name))
-        units.append(src)
-    units.append(os.path.join(HERE, "emu_cudart.cpp"))
-    flags = ["g++", "-std=c++20", "-O1", "-fPIC", "-pthread", "-I", str(d), "-I", emulation_sources.CSRC,
-             "-I", CUDA_INCLUDE]
-
-    def compile_one(src):
-        obj = str(d / (os.path.basename(str(src)) + ".o"))
-        subprocess.run(flags + ["-c", str(src), "-o", obj], check=True)
-        return obj
-
-    with ThreadPoolExecutor(len(units)) as ex:
-        objs = list(ex.map(compile_one, units))
-    so = str(d / "libmbicg_emu.so")
-    # -Bsymbolic: calls bind to the emulated runtime even when the real CUDA
-    # runtime (linked into the real library) is loaded in the same process
-    subprocess.run(["g++", "-shared", "-pthread", "-Wl,-Bsymbolic", *objs, "-o", so], check=True)
-    lb = ctypes.CDLL(so)
-    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
-    lb.mbicg_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.c_int, vp]
-    lb.mbicg_destroy.argtypes = [vp]
-    lb.mbicg_load_gauge.argtypes = [vp, vp]
-    lb.mbicg_apply_D.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
-    lb.mbicg_block_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                     ctypes.POINTER(mb.mbicg_params), ip, dp]
-    lb.mbicg_default_params.argtypes = [ctypes.POINTER(mb.mbicg_params)]
-    lb.mbicg_get_stats.argtypes = [vp, ctypes.POINTER(mb.mbicg_stats)]
-    lb.mbicg_last_error.restype = ctypes.c_char_p
-    lb.mbicg_last_error.argtypes = [vp]
-    return lb
+def lib(emulated_library):
+    return emulated_library
 
 
 @pytest.fixture(scope="module")
