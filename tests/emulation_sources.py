@@ -248,7 +248,7 @@ def library_unit(name, csrc=CSRC):
     arenas."""
     src = read(name, csrc)
     head = _patched_common(csrc) + "\n" + read("internal.h", csrc).replace('#include "common.cuh"', "")
-    src = src.replace('#include "internal.h"', head)
+    src = src.replace('#include "internal.h"', head.replace("#pragma once", ""))
     src = src.replace('#include "../../include/mbicg.h"', f'#include "{os.path.join(INCLUDE, "mbicg.h")}"')
     src = src.replace("#include <cooperative_groups.h>", "")
     if name == "dslash.cu":

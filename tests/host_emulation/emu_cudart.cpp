@@ -1,10 +1,13 @@
 // The CUDA runtime calls of the library's host code, over host memory, for
 // the emulated build: allocations are malloc'd and recorded (so the
 // library's host/device pointer test sees its own buffers as device memory),
-// copies and fills are immediate, streams and events are tokens, and stream
-// capture is refused (the solver then runs its iterations eagerly).
+// copies and fills are immediate, streams are tokens, an event records the
+// host clock (launches run to completion when they are made, so the time
+// between two events is the emulated work between them), and stream capture
+// is refused (the solver then runs its iterations eagerly).
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -48,6 +51,7 @@ void release(void* p, std::map<const char*, size_t>& m) {
   free(p);
 }
 int token = 1;
+std::map<size_t, std::chrono::steady_clock::time_point> event_times;
 }  // namespace
 
 extern "C" {
@@ -110,13 +114,29 @@ cudaError_t cudaEventCreate(cudaEvent_t* e) {
   *e = reinterpret_cast<cudaEvent_t>(static_cast<size_t>(++token));
   return cudaSuccess;
 }
-cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t) { return cudaSuccess; }
-cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
-cudaError_t cudaEventElapsedTime(float* ms, cudaEvent_t, cudaEvent_t) {
-  *ms = 0.0f;
+cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t) {
+  const auto now = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> g(mu);
+  event_times[reinterpret_cast<size_t>(e)] = now;
   return cudaSuccess;
 }
-cudaError_t cudaEventDestroy(cudaEvent_t) { return cudaSuccess; }
+cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
+cudaError_t cudaEventElapsedTime(float* ms, cudaEvent_t a, cudaEvent_t b) {
+  std::lock_guard<std::mutex> g(mu);
+  auto ia = event_times.find(reinterpret_cast<size_t>(a)), ib = event_times.find(reinterpret_cast<size_t>(b));
+  if (ia == event_times.end() || ib == event_times.end()) return cudaErrorInvalidResourceHandle;
+  *ms = std::chrono::duration<float, std::milli>(ib->second - ia->second).count();
+  return cudaSuccess;
+}
+cudaError_t cudaEventDestroy(cudaEvent_t e) {
+  std::lock_guard<std::mutex> g(mu);
+  event_times.erase(reinterpret_cast<size_t>(e));
+  return cudaSuccess;
+}
+cudaError_t cudaStreamIsCapturing(cudaStream_t, enum cudaStreamCaptureStatus* st) {
+  *st = cudaStreamCaptureStatusNone;  // capture is never begun
+  return cudaSuccess;
+}
 cudaError_t cudaStreamBeginCapture(cudaStream_t, enum cudaStreamCaptureMode) { return cudaErrorNotSupported; }
 cudaError_t cudaStreamEndCapture(cudaStream_t, cudaGraph_t* g) {
   *g = nullptr;
