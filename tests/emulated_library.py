@@ -19,9 +19,11 @@ def available():
     return shutil.which("g++") is not None and os.path.exists(os.path.join(CUDA_INCLUDE, "cuda_runtime.h"))
 
 
-def build(d):
-    """Compile and link into directory d; returns the ctypes library with the
-    argument types of the ABI calls the tests use."""
+ASAN_FLAGS = ["-fsanitize=address", "-fno-omit-frame-pointer"]
+
+
+def compile_library(d, extra_flags=()):
+    """Compile and link into directory d; returns the path of the library."""
     for f in ("shim_threads.h", "emu_runtime.h"):
         shutil.copy(os.path.join(HERE, f), os.path.join(d, f))
     units = []
@@ -31,8 +33,8 @@ def build(d):
             f.write(emulation_sources.library_unit(name))
         units.append(src)
     units.append(os.path.join(HERE, "emu_cudart.cpp"))
-    flags = ["g++", "-std=c++20", "-O1", "-fPIC", "-pthread", "-I", str(d), "-I", emulation_sources.CSRC,
-             "-I", CUDA_INCLUDE]
+    flags = ["g++", "-std=c++20", "-O1", "-fPIC", "-pthread", *extra_flags, "-I", str(d), "-I",
+             emulation_sources.CSRC, "-I", CUDA_INCLUDE]
 
     def compile_one(src):
         obj = os.path.join(d, os.path.basename(src) + ".o")
@@ -44,7 +46,12 @@ def build(d):
     so = os.path.join(d, "libmbicg_emu.so")
     # -Bsymbolic: calls bind to the emulated runtime even when the real CUDA
     # runtime (linked into the real library) is loaded in the same process
-    subprocess.run(["g++", "-shared", "-pthread", "-Wl,-Bsymbolic", *objs, "-o", so], check=True)
+    subprocess.run(["g++", "-shared", "-pthread", *extra_flags, "-Wl,-Bsymbolic", *objs, "-o", so], check=True)
+    return so
+
+
+def load(so):
+    """The library at so, with the argument types of the ABI calls the tests use."""
     lb = ctypes.CDLL(so)
     vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
     lb.mbicg_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.c_int, vp]
@@ -59,3 +66,18 @@ def build(d):
     lb.mbicg_last_error.restype = ctypes.c_char_p
     lb.mbicg_last_error.argtypes = [vp]
     return lb
+
+
+def build(d):
+    """compile_library then load."""
+    return load(compile_library(d))
+
+
+def asan_runtime():
+    """Path of gcc's AddressSanitizer runtime, or None."""
+    try:
+        r = subprocess.run(["gcc", "-print-file-name=libasan.so"], capture_output=True, text=True, check=True)
+    except (OSError, subprocess.CalledProcessError):
+        return None
+    path = r.stdout.strip()
+    return path if os.path.isabs(path) and os.path.exists(path) else None

@@ -1,0 +1,140 @@
+"""Drives the emulated library, built with AddressSanitizer, through its C ABI.
+Started by tests/test_host_emulation_asan.py as a child process with the
+sanitizer's runtime preloaded; argument: the library's path.  Every call
+must return MBICG_OK (or the error the case expects) and the sanitizer must
+report nothing; the numbers themselves are checked against the oracle by the
+other emulation tests, here only for being finite and converged."""
+import ctypes
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path[:0] = [ROOT, os.path.join(ROOT, "tests")]
+
+import numpy as np  # noqa: E402
+
+import emulated_library  # noqa: E402
+import paper_1104_0737_gb300 as mb  # noqa: E402  (the ctypes structures only)
+import synth  # noqa: E402
+
+KAPPA = 0.12
+T0 = time.perf_counter()
+
+
+def _v(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Ctx:
+    def __init__(self, lib, dims, seed):
+        self.lib, self.dims = lib, dims
+        self.c = ctypes.c_void_p()
+        assert lib.mbicg_create(ctypes.byref(self.c), (ctypes.c_int * 4)(*dims), 0, None) == mb.MBICG_OK
+        self.U = synth.su3_links(dims, 0.5, seed=seed)
+        assert lib.mbicg_load_gauge(self.c, _v(self.U)) == mb.MBICG_OK
+
+    def close(self):
+        self.lib.mbicg_destroy(self.c)
+
+    def params(self, block, **kw):
+        p = mb.mbicg_params()
+        self.lib.mbicg_default_params(ctypes.byref(p))
+        p.block = (ctypes.c_int * 4)(*block)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    def ok(self, rc, what):
+        assert rc == mb.MBICG_OK, f"{what}: {rc} {self.lib.mbicg_last_error(self.c)}"
+        print(f"ok {what} ({time.perf_counter() - T0:.1f} s)", flush=True)
+
+    def apply_D(self, L, prec):
+        psi = synth.gaussian_source(self.dims, L, seed=10 + L)
+        out = np.empty_like(psi)
+        self.ok(self.lib.mbicg_apply_D(self.c, _v(psi), _v(out), L, KAPPA, prec), f"apply_D L={L} prec={prec}")
+        assert np.isfinite(out).all()
+
+    def sap(self, L, block, **kw):
+        eta = synth.gaussian_source(self.dims, L, seed=20 + L)
+        out = np.empty_like(eta)
+        p = self.params(block, **kw)
+        self.ok(self.lib.mbicg_sap_precond(self.c, _v(eta), _v(out), L, KAPPA, ctypes.byref(p)),
+                f"sap {self.dims} L={L} {kw}")
+        assert np.isfinite(out).all()
+
+    def solve(self, L, block, tol=1e-9, X=None, **kw):
+        B = synth.gaussian_source(self.dims, L, seed=30 + L)
+        X = np.empty_like(B) if X is None else X
+        p = self.params(block, **kw)
+        it = ctypes.c_int(0)
+        tres = np.zeros(L)
+        self.ok(self.lib.mbicg_block_solve(self.c, _v(B), _v(X), L, KAPPA, tol, ctypes.byref(p), ctypes.byref(it),
+                                           tres.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                f"block_solve {self.dims} L={L} {kw}")
+        assert tres.max() <= tol, tres
+        return X
+
+
+def check_sanitizer(lib):
+    """The sanitizer is live, and an emulated device buffer ends exactly at its
+    size: the byte after it is poisoned, its last byte is not."""
+    is_poisoned = ctypes.CDLL(None).__asan_address_is_poisoned
+    is_poisoned.argtypes = [ctypes.c_void_p]
+    p = ctypes.c_void_p()
+    assert lib.cudaMalloc(ctypes.byref(p), ctypes.c_size_t(1000)) == 0
+    assert is_poisoned(p.value + 999) == 0 and is_poisoned(p.value + 1000) == 1
+    lib.cudaFree(p)
+    print("ok sanitizer", flush=True)
+
+
+def main(so):
+    lib = emulated_library.load(so)
+    check_sanitizer(lib)
+    small = Ctx(lib, (4, 4, 4, 4), seed=1)
+    b2 = (2, 2, 2, 2)
+    for L in (1, 3):
+        for prec in (mb.MBICG_FP64, mb.MBICG_FP32, mb.MBICG_FP16):
+            small.apply_D(L, prec)
+    for fused in ("1", "0"):
+        os.environ["MBICG_SAP_FUSED"] = fused
+        for mode in (mb.MBICG_MR_COLUMN, mb.MBICG_MR_BLOCK):
+            for prec in (mb.MBICG_FP64, mb.MBICG_FP32):
+                small.sap(3, b2, ncycle=1, nmr=2, mr_mode=mode, prec_sap=prec)
+    os.environ.pop("MBICG_SAP_FUSED")
+    small.solve(2, b2, prec_D=mb.MBICG_FP64)
+    X = small.solve(3, b2, prec_D=mb.MBICG_FP32, dummy_rhs=2, dummy_seed=5)
+    small.solve(3, b2, X=X, use_x0=1)
+    # SSOR domain solves, the clover term and its Jacobi preconditioning (Sec. 2.2)
+    for prec in (mb.MBICG_FP64, mb.MBICG_FP32):
+        small.sap(3, b2, ncycle=1, prec_sap=prec, domain_solver=1, nssor=2)
+    lib.mbicg_load_clover.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    lib.mbicg_apply_clover.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    small.ok(lib.mbicg_load_clover(small.c, 1.3), "load_clover")
+    psi = synth.gaussian_source(small.dims, 3, seed=40)
+    out = np.empty_like(psi)
+    for prec in (mb.MBICG_FP64, mb.MBICG_FP32):
+        for jacobi in (0, 1):
+            small.ok(lib.mbicg_apply_clover(small.c, _v(psi), _v(out), 3, KAPPA, prec, jacobi),
+                     f"apply_clover prec={prec} jacobi={jacobi}")
+            assert np.isfinite(out).all()
+    for solver in (0, 1):
+        for prec in (mb.MBICG_FP64, mb.MBICG_FP32):
+            small.sap(3, b2, ncycle=1, nmr=2, mr_mode=mb.MBICG_MR_COLUMN, prec_sap=prec, clover=1,
+                      domain_solver=solver)
+        small.solve(2, b2, clover=1, domain_solver=solver)
+    small.close()
+
+    # the 8-CTA cluster sweep over 4^4 domains, and a few iterations of a
+    # block solve on it (the frozen step lengths recorded, then replayed)
+    big = Ctx(lib, (8, 8, 8, 8), seed=2)
+    b4 = (4, 4, 4, 4)
+    big.sap(1, b4, ncycle=1, nmr=2, mr_mode=mb.MBICG_MR_COLUMN)
+    big.solve(1, b4, tol=1e-3, ncycle=1, nmr=2)
+    big.close()
+    print("done", flush=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1])

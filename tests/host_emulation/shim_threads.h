@@ -19,8 +19,13 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <memory>
+#include <semaphore>
 #include <vector>
+#if defined(__SANITIZE_ADDRESS__)
+#include <sanitizer/asan_interface.h>
+#endif
 
 struct EmuDim {
   unsigned x, y, z;
@@ -86,8 +91,17 @@ inline T __shfl_xor_sync(unsigned, T v, int o) {
 #define EMU_STATIC_SLOTS 1
 #endif
 constexpr size_t EMU_SLOT_BYTES = 8192;
+// under AddressSanitizer a poisoned gap follows the dynamic part (and the
+// arena), so that a kernel's access past its dynamic shared memory is reported
+#if defined(__SANITIZE_ADDRESS__)
+constexpr size_t EMU_SMEM_REDZONE = 256;
+#else
+constexpr size_t EMU_SMEM_REDZONE = 0;
+#endif
 inline void* emu_dyn_smem() { return emu_t.cta->arena.data(); }
-inline void* emu_static_smem_slot(int i) { return emu_t.cta->arena.data() + emu_t.cta->dyn_bytes + (size_t)i * EMU_SLOT_BYTES; }
+inline void* emu_static_smem_slot(int i) {
+  return emu_t.cta->arena.data() + emu_t.cta->dyn_bytes + EMU_SMEM_REDZONE + (size_t)i * EMU_SLOT_BYTES;
+}
 inline int __syncthreads_or(int p);
 
 namespace cooperative_groups {
@@ -220,6 +234,68 @@ inline void emu_mbar_reset() {
 }
 inline long long min(long long a, long long b) { return a < b ? a : b; }
 
+// Host threads that run the CUDA threads of one cluster at a time, all at
+// once (they meet at the emulated barriers).  Created on first use, 512 KB of
+// stack each, and reused by every later launch: creating a thread per CUDA
+// thread per launch dominated the emulation's run time.  One launch at a time.
+class EmuPool {
+ public:
+  static EmuPool& get() {
+    static EmuPool* p = new EmuPool();  // never destroyed: its threads wait until the process ends
+    return *p;
+  }
+  // fn(ctx, i) for i < n, each on its own thread; returns when all have returned
+  void run(size_t n, void (*fn)(void*, size_t), void* ctx) {
+    std::lock_guard<std::mutex> g(launch_mu_);
+    while (workers_.size() < n) add_worker();
+    fn_ = fn;
+    ctx_ = ctx;
+    left_.store(n, std::memory_order_relaxed);
+    for (size_t i = 0; i < n; ++i) workers_[i]->go.release();
+    if (n) done_.acquire();
+  }
+
+ private:
+  struct Worker {
+    EmuPool* pool;
+    size_t index;
+    std::binary_semaphore go{0};
+  };
+  static void* loop(void* p) {
+    Worker* w = static_cast<Worker*>(p);
+    EmuPool* pool = w->pool;
+    for (;;) {
+      w->go.acquire();
+      pool->fn_(pool->ctx_, w->index);
+      if (pool->left_.fetch_sub(1, std::memory_order_acq_rel) == 1) pool->done_.release();
+    }
+    return nullptr;
+  }
+  void add_worker() {
+    auto w = std::make_unique<Worker>();
+    w->pool = this;
+    w->index = workers_.size();
+    pthread_attr_t attr;
+    pthread_attr_init(&attr);
+    pthread_attr_setstacksize(&attr, 1 << 19);
+    pthread_attr_setdetachstate(&attr, PTHREAD_CREATE_DETACHED);
+    pthread_t tid;
+    const int rc = pthread_create(&tid, &attr, &EmuPool::loop, w.get());
+    pthread_attr_destroy(&attr);
+    if (rc != 0) {  // a missing thread would leave the others waiting at a barrier
+      fprintf(stderr, "emu_launch: pthread_create failed (%d)\n", rc);
+      abort();
+    }
+    workers_.push_back(std::move(w));
+  }
+  std::mutex launch_mu_;
+  std::vector<std::unique_ptr<Worker>> workers_;
+  void (*fn_)(void*, size_t) = nullptr;
+  void* ctx_ = nullptr;
+  std::atomic<size_t> left_{0};
+  std::binary_semaphore done_{0};
+};
+
 // Runs kernel() for a grid of nclusters clusters of cs CTAs of `threads`
 // threads each (1-D), one cluster at a time; the static slots follow
 // dyn_bytes of dynamic shared memory in each CTA's arena.
@@ -241,8 +317,12 @@ void emu_launch3(int nclusters, int cs, dim3 block, size_t dyn_bytes, F kernel) 
     std::vector<std::unique_ptr<EmuCta>> ctas;
     for (int r = 0; r < cs; ++r) {
       auto c = std::make_unique<EmuCta>();
-      c->arena.assign(dyn_bytes + static_bytes + 16, 0xff);
+      c->arena.assign(dyn_bytes + EMU_SMEM_REDZONE + static_bytes + 16, 0xff);
       c->dyn_bytes = dyn_bytes;
+#if defined(__SANITIZE_ADDRESS__)
+      ASAN_POISON_MEMORY_REGION(c->arena.data() + dyn_bytes, EMU_SMEM_REDZONE);
+      ASAN_POISON_MEMORY_REGION(c->arena.data() + dyn_bytes + EMU_SMEM_REDZONE + static_bytes, 16);
+#endif
       c->bar = std::make_unique<std::barrier<>>(threads);
       for (int w = 0; w < (threads + 31) / 32; ++w) c->warp_bar.push_back(std::make_unique<std::barrier<>>(32));
       c->warp_slot.assign((size_t)((threads + 31) / 32) * 32, 0);
@@ -255,10 +335,6 @@ void emu_launch3(int nclusters, int cs, dim3 block, size_t dyn_bytes, F kernel) 
       F* k;
     };
     std::vector<Arg> args((size_t)cs * threads);
-    std::vector<pthread_t> tids((size_t)cs * threads);
-    pthread_attr_t attr;
-    pthread_attr_init(&attr);
-    pthread_attr_setstacksize(&attr, 1 << 19);
     for (int r = 0; r < cs; ++r)
       for (int t = 0; t < threads; ++t) {
         Arg& a = args[(size_t)r * threads + t];
@@ -266,20 +342,11 @@ void emu_launch3(int nclusters, int cs, dim3 block, size_t dyn_bytes, F kernel) 
                        tz = (unsigned)t / (block.x * block.y);
         a.t = EmuThread{{(unsigned)(cl * cs + r), 0, 0}, {tx, ty, tz}, ctas[r].get(), &cluster, (unsigned)r};
         a.k = &kernel;
-        const int rc = pthread_create(&tids[(size_t)r * threads + t], &attr,
-                                      [](void* p) -> void* {
-                                        Arg* a = static_cast<Arg*>(p);
-                                        emu_t = a->t;
-                                        (*a->k)();
-                                        return nullptr;
-                                      },
-                                      &a);
-        if (rc != 0) {  // a missing thread would leave the others waiting at a barrier
-          fprintf(stderr, "emu_launch: pthread_create failed (%d)\n", rc);
-          abort();
-        }
       }
-    pthread_attr_destroy(&attr);
-    for (pthread_t& t : tids) pthread_join(t, nullptr);
+    EmuPool::get().run(args.size(), [](void* p, size_t i) {
+      Arg& a = static_cast<Arg*>(p)[i];
+      emu_t = a.t;
+      (*a.k)();
+    }, args.data());
   }
 }
