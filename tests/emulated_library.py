@@ -19,7 +19,9 @@ def available():
     return shutil.which("g++") is not None and os.path.exists(os.path.join(CUDA_INCLUDE, "cuda_runtime.h"))
 
 
-ASAN_FLAGS = ["-fsanitize=address", "-fno-omit-frame-pointer"]
+# AddressSanitizer, and UndefinedBehaviorSanitizer (misaligned vector accesses,
+# fixed-size array bounds, signed overflow, shifts) stopping at its first report
+SANITIZE_FLAGS = ["-fsanitize=address,undefined", "-fno-sanitize-recover=undefined", "-fno-omit-frame-pointer"]
 
 
 def compile_library(d, extra_flags=()):

@@ -1,7 +1,8 @@
-"""Drives the emulated library, built with AddressSanitizer, through its C ABI.
+"""Drives the emulated library, built with AddressSanitizer and
+UndefinedBehaviorSanitizer, through its C ABI.
 Started by tests/test_host_emulation_asan.py as a child process with the
 sanitizer's runtime preloaded; argument: the library's path.  Every call
-must return MBICG_OK (or the error the case expects) and the sanitizer must
+must return MBICG_OK (or the error the case expects) and the sanitizers must
 report nothing; the numbers themselves are checked against the oracle by the
 other emulation tests, here only for being finite and converged."""
 import ctypes
@@ -77,8 +78,9 @@ class Ctx:
 
 
 def check_sanitizer(lib):
-    """The sanitizer is live, and an emulated device buffer ends exactly at its
-    size: the byte after it is poisoned, its last byte is not."""
+    """Both sanitizers are live, and an emulated device buffer ends exactly at
+    its size: the byte after it is poisoned, its last byte is not."""
+    lib["__ubsan_handle_type_mismatch_v1_abort"]  # the alignment check's handler
     is_poisoned = ctypes.CDLL(None).__asan_address_is_poisoned
     is_poisoned.argtypes = [ctypes.c_void_p]
     p = ctypes.c_void_p()
