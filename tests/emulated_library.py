@@ -69,6 +69,14 @@ def load(so):
     lb.mbicg_get_stats.argtypes = [vp, ctypes.POINTER(mb.mbicg_stats)]
     lb.mbicg_last_error.restype = ctypes.c_char_p
     lb.mbicg_last_error.argtypes = [vp]
+    llp = ctypes.POINTER(ctypes.c_longlong)
+    lb.mbicg_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double]
+    lb.mbicg_server_add_field.argtypes = [vp, ip, vp, ctypes.POINTER(mb.mbicg_params), ctypes.c_int, ip]
+    lb.mbicg_server_submit.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, llp]
+    lb.mbicg_server_wait.argtypes = [vp, ctypes.c_longlong, vp, ip, dp, ctypes.POINTER(mb.mbicg_request_info)]
+    lb.mbicg_server_hold.argtypes = [vp, ctypes.c_int]
+    lb.mbicg_server_stats.argtypes = [vp, llp, llp, llp, ip]
+    lb.mbicg_server_destroy.argtypes = [vp]
     return lb
 
 

@@ -9,6 +9,7 @@ emulation tests, here only for being finite and converged."""
 import ctypes
 import os
 import sys
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -132,6 +133,38 @@ def main(so, sanitizer):
                       domain_solver=solver)
         small.solve(2, b2, clover=1, domain_solver=solver)
     small.close()
+
+    # the request server: two slots of one field, four clients on host threads
+    srv = ctypes.c_void_p()
+    assert lib.mbicg_server_create(ctypes.byref(srv), 0, 1.0) == mb.MBICG_OK
+    dims = (4, 4, 4, 4)
+    fid = ctypes.c_int(-1)
+    p = mb.mbicg_params()
+    lib.mbicg_default_params(ctypes.byref(p))
+    p.block = (ctypes.c_int * 4)(2, 2, 2, 2)
+    U = synth.su3_links(dims, 0.5, seed=4)
+    assert lib.mbicg_server_add_field(srv, (ctypes.c_int * 4)(*dims), _v(U), ctypes.byref(p), 2,
+                                      ctypes.byref(fid)) == mb.MBICG_OK
+    results = [None] * 4
+
+    def client(i):
+        B = synth.gaussian_source(dims, 1 + i % 2, seed=50 + i)
+        rid = ctypes.c_longlong(-1)
+        rc = lib.mbicg_server_submit(srv, fid.value, _v(B), B.shape[3], KAPPA, 1e-8, ctypes.byref(rid))
+        X = np.empty_like(B)
+        tres = np.zeros(B.shape[3])
+        rc2 = lib.mbicg_server_wait(srv, rid.value, _v(X), None, tres.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    None)
+        results[i] = (rc, rc2, float(tres.max()))
+
+    clients = [threading.Thread(target=client, args=(i,)) for i in range(4)]
+    for t in clients:
+        t.start()
+    for t in clients:
+        t.join()
+    lib.mbicg_server_destroy(srv)
+    assert all(r[0] == mb.MBICG_OK and r[1] == mb.MBICG_OK and r[2] <= 1e-8 for r in results), results
+    print(f"ok server ({time.perf_counter() - T0:.1f} s)", flush=True)
 
     # the 8-CTA cluster sweep over 4^4 domains, and an iteration or two of a
     # block solve on it (the frozen step lengths recorded, then replayed)

@@ -306,8 +306,15 @@ void emu_launch(int nclusters, int cs, int threads, size_t dyn_bytes, F kernel) 
   emu_launch3(nclusters, cs, dim3((unsigned)threads, 1, 1), dyn_bytes, kernel);
 }
 // as emu_launch, with a 3-D CTA shape (thread t has x = t % block.x fastest)
+// one launch at a time, also when several host threads launch (blockDim and
+// gridDim are process-wide)
+inline std::mutex& emu_launch_mutex() {
+  static std::mutex m;
+  return m;
+}
 template <typename F>
 void emu_launch3(int nclusters, int cs, dim3 block, size_t dyn_bytes, F kernel) {
+  std::lock_guard<std::mutex> launch_lock(emu_launch_mutex());
   const int threads = (int)(block.x * block.y * block.z);
   const size_t static_bytes = (size_t)EMU_STATIC_SLOTS * EMU_SLOT_BYTES;
   blockDim = {block.x, block.y, block.z};
