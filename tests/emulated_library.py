@@ -77,6 +77,10 @@ def load(so):
     lb.mbicg_server_hold.argtypes = [vp, ctypes.c_int]
     lb.mbicg_server_stats.argtypes = [vp, llp, llp, llp, ip]
     lb.mbicg_server_destroy.argtypes = [vp]
+    lb.mbicg_apply_D_noalloc.argtypes = [ip, vp, vp, vp, ctypes.c_int, ctypes.c_double, vp]
+    lb.mbicg_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip]
+    lb.cudaMalloc.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t]
+    lb.cudaFree.argtypes = [vp]
     return lb
 
 

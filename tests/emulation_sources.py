@@ -238,7 +238,7 @@ def _patched_common(csrc):
     return common
 
 
-LIBRARY_SOURCES = ["api.cu", "dslash.cu", "sap.cu", "blas.cu", "half.cu", "serve.cu", "clover.cu"]
+LIBRARY_SOURCES = ["api.cu", "dslash.cu", "sap.cu", "blas.cu", "half.cu", "serve.cu", "noalloc.cu", "selftest.cu", "clover.cu"]
 
 
 def library_unit(name, csrc=CSRC):

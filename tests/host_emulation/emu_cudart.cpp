@@ -89,6 +89,10 @@ cudaError_t cudaMemcpy(void* d, const void* s, size_t n, enum cudaMemcpyKind) {
   memmove(d, s, n);
   return cudaSuccess;
 }
+cudaError_t cudaMemset(void* p, int v, size_t n) {
+  memset(p, v, n);
+  return cudaSuccess;
+}
 cudaError_t cudaMemsetAsync(void* p, int v, size_t n, cudaStream_t) {
   memset(p, v, n);
   return cudaSuccess;
@@ -96,6 +100,15 @@ cudaError_t cudaMemsetAsync(void* p, int v, size_t n, cudaStream_t) {
 cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
 cudaError_t cudaDeviceSynchronize(void) { return cudaSuccess; }
 cudaError_t cudaSetDevice(int) { return cudaSuccess; }
+cudaError_t cudaGetDevice(int* d) {
+  *d = 0;
+  return cudaSuccess;
+}
+// a __device__ variable is a host variable here: its address is the "device" address
+cudaError_t cudaGetSymbolAddress(void** p, const void* symbol) {
+  *p = const_cast<void*>(symbol);
+  return cudaSuccess;
+}
 cudaError_t cudaGetDeviceCount(int* n) {
   *n = 1;
   return cudaSuccess;

@@ -104,6 +104,18 @@ def main(so, sanitizer):
     for L in (1, 3):
         for prec in (mb.MBICG_FP64, mb.MBICG_FP32, mb.MBICG_FP16):
             small.apply_D(L, prec)
+    # the allocation-free operator on emulated device buffers
+    U, psi = small.U, synth.gaussian_source(small.dims, 3, seed=60)
+    bufs = []
+    for a in (U, psi, psi):
+        p = ctypes.c_void_p()
+        assert lib.cudaMalloc(ctypes.byref(p), ctypes.c_size_t(a.nbytes)) == 0
+        ctypes.memmove(p, a.ctypes.data, a.nbytes)
+        bufs.append(p)
+    small.ok(lib.mbicg_apply_D_noalloc((ctypes.c_int * 4)(*small.dims), bufs[0], bufs[1], bufs[2], 3, KAPPA, None),
+             "apply_D_noalloc L=3")
+    for p in bufs:
+        lib.cudaFree(p)
     for fused in ("1", "0"):
         os.environ["MBICG_SAP_FUSED"] = fused
         for mode in (mb.MBICG_MR_COLUMN, mb.MBICG_MR_BLOCK):

@@ -315,6 +315,7 @@ inline std::mutex& emu_launch_mutex() {
 template <typename F>
 void emu_launch3(int nclusters, int cs, dim3 block, size_t dyn_bytes, F kernel) {
   std::lock_guard<std::mutex> launch_lock(emu_launch_mutex());
+  emu_mbar_reset();  // a wait that gave up in an earlier launch does not end this one's
   const int threads = (int)(block.x * block.y * block.z);
   const size_t static_bytes = (size_t)EMU_STATIC_SLOTS * EMU_SLOT_BYTES;
   blockDim = {block.x, block.y, block.z};

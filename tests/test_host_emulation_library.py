@@ -9,13 +9,17 @@ CUDA runtime calls are emulated over host memory
 solver runs its iterations eagerly).  Checked against the oracle: the
 operator with host pointers in FP64 and FP32, and mbicg_block_solve in FP64
 and in mixed precision (reliable updates), with dummy right-hand sides and an
-initial guess, plus the ABI's argument errors.  This exercises the solver's
+initial guess, the allocation-free operator on emulated device buffers, the
+give-up path of the bounded mbarrier wait, plus the ABI's argument errors.  This exercises the solver's
 host logic of Algorithm 2 on a machine without a GPU; the -m gpu tests run the
 same code on the hardware."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
+
+import emulation_sources
 
 import paper_1104_0737_gb300 as mb  # the ctypes structures only; no library is loaded
 import synth
@@ -119,3 +123,63 @@ def test_abi_errors(lib, ctx):
     assert lib.mbicg_create(ctypes.byref(fresh), (ctypes.c_int * 4)(*DIMS), 0, None) == mb.MBICG_OK
     assert _solve(lib, fresh, B, X, _params(lib))[0] == mb.MBICG_ENOGAUGE
     lib.mbicg_destroy(fresh)
+
+
+def _device_copy(lib, a):
+    """An emulated device buffer (the runtime's own allocation) holding a copy of a."""
+    p = ctypes.c_void_p()
+    assert lib.cudaMalloc(ctypes.byref(p), a.nbytes) == 0
+    ctypes.memmove(p, a.ctypes.data, a.nbytes)
+    return p
+
+
+def test_noalloc_operator(lib, ctx):
+    """mbicg_apply_D_noalloc (device pointers, a fixed scratch array) gives the
+    FP32 operator of mbicg_apply_D bit for bit, on two calls in a row with
+    different blocks; sizes beyond its scratch and host pointers are refused."""
+    c, U = ctx
+    dims = (ctypes.c_int * 4)(*DIMS)
+    dU = _device_copy(lib, U)
+    try:
+        for Lc, kappa, seed in ((3, 0.13, 2004), (1, 0.121, 2005)):
+            psi = synth.gaussian_source(DIMS, Lc, seed=seed)
+            ref = np.empty_like(psi)
+            assert lib.mbicg_apply_D(c, _v(psi), _v(ref), Lc, kappa, mb.MBICG_FP32) == mb.MBICG_OK
+            d_in = _device_copy(lib, psi)
+            d_out = _device_copy(lib, np.full_like(psi, np.nan))
+            assert lib.mbicg_apply_D_noalloc(dims, dU, d_in, d_out, Lc, kappa, None) == mb.MBICG_OK
+            out = np.empty_like(psi)
+            ctypes.memmove(out.ctypes.data, d_out, out.nbytes)
+            assert np.array_equal(out, ref)
+            lib.cudaFree(d_in)
+            lib.cudaFree(d_out)
+        big = (ctypes.c_int * 4)(16, 16, 16, 16)
+        assert lib.mbicg_apply_D_noalloc(big, dU, dU, dU, 12, 0.12, None) == mb.MBICG_EINVAL
+        host = np.zeros_like(U)
+        assert lib.mbicg_apply_D_noalloc(dims, _v(host), dU, dU, 1, 0.12, None) == mb.MBICG_EINVAL
+    finally:
+        lib.cudaFree(dU)
+
+
+def test_bounded_wait_gives_up_and_the_library_goes_on(lib, ctx, oracle_mod):
+    """mbicg_selftest_bounded_wait: a wait for bytes no copy delivers gives up
+    (the emulated wait ends after 2 s; on the GPU after the spin limit) and the
+    kernel reports ST_TIMEOUT instead of hanging; a barrier completed by an
+    arrival is waited for; afterwards a block solve, whose Gram kernel waits
+    on mbarriers, still runs; the argument errors."""
+    c, U = ctx
+    flag = ctypes.c_int(-1)
+    assert lib.mbicg_selftest_bounded_wait(0, 1000, 64, ctypes.byref(flag)) == mb.MBICG_OK and flag.value == 1
+    assert lib.mbicg_selftest_bounded_wait(0, 1000, 0, ctypes.byref(flag)) == mb.MBICG_OK and flag.value == 0
+    B = synth.gaussian_source(DIMS, 1, seed=2006)
+    X = np.empty_like(B)
+    rc, _, tres, _ = _solve(lib, c, B, X, _params(lib, prec_D=mb.MBICG_FP64))
+    assert rc == mb.MBICG_OK and np.max(_residual(oracle_mod, U, B, X)) <= 1e-10
+    for limit, nbytes in ((0, 16), (1 << 25, 16), (1000, -16), (1000, 8)):
+        assert lib.mbicg_selftest_bounded_wait(0, limit, nbytes, ctypes.byref(flag)) == mb.MBICG_EINVAL
+
+
+def test_every_cuda_source_is_emulated():
+    """The emulated library is built from every CUDA source of the package."""
+    sources = {f for f in os.listdir(emulation_sources.CSRC) if f.endswith(".cu")}
+    assert set(emulation_sources.LIBRARY_SOURCES) == sources

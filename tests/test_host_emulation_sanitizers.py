@@ -15,7 +15,8 @@ atomics order their accesses, so a shared- or global-memory access that no
 barrier orders against another thread's (a missing __syncthreads or cluster
 barrier) is reported as a data race, whatever the schedule of the run.
 
-The exercise runs the operator in FP64, FP32 and FP16, SAP with the fused
+The exercise runs the operator in FP64, FP32 and FP16 (and the
+allocation-free one on emulated device buffers), SAP with the fused
 cluster sweep and the multi-kernel path (per-column and block MR, FP64 and
 FP32), block solves with dummy columns and an initial guess, SSOR domain
 solves, the clover term and its Jacobi preconditioning (operators, SAP with
