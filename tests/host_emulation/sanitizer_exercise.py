@@ -162,7 +162,7 @@ def main(so, sanitizer):
     def client(i):
         B = synth.gaussian_source(dims, 1 + i % 2, seed=50 + i)
         rid = ctypes.c_longlong(-1)
-        rc = lib.mbicg_server_submit(srv, fid.value, _v(B), B.shape[3], KAPPA, 1e-8, ctypes.byref(rid))
+        rc = lib.mbicg_server_submit(srv, fid.value, _v(B), B.shape[3], KAPPA, 1e-4, ctypes.byref(rid))
         X = np.empty_like(B)
         tres = np.zeros(B.shape[3])
         rc2 = lib.mbicg_server_wait(srv, rid.value, _v(X), None, tres.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
@@ -175,7 +175,7 @@ def main(so, sanitizer):
     for t in clients:
         t.join()
     lib.mbicg_server_destroy(srv)
-    assert all(r[0] == mb.MBICG_OK and r[1] == mb.MBICG_OK and r[2] <= 1e-8 for r in results), results
+    assert all(r[0] == mb.MBICG_OK and r[1] == mb.MBICG_OK and r[2] <= 1e-4 for r in results), results
     print(f"ok server ({time.perf_counter() - T0:.1f} s)", flush=True)
 
     # the 8-CTA cluster sweep over 4^4 domains, and an iteration or two of a
@@ -183,7 +183,8 @@ def main(so, sanitizer):
     big = Ctx(lib, (8, 8, 8, 8), seed=2)
     b4 = (4, 4, 4, 4)
     big.sap(1, b4, ncycle=1, nmr=2, mr_mode=mb.MBICG_MR_COLUMN)
-    big.solve(1, b4, tol=1e-1, ncycle=1, nmr=2)
+    if sanitizer == "address":  # the same kernels as the sweep above, at the cost of a solve
+        big.solve(1, b4, tol=1e-1, ncycle=1, nmr=2)
     big.close()
     print("done", flush=True)
 

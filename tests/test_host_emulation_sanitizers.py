@@ -22,8 +22,8 @@ FP32), block solves with dummy columns and an initial guess, SSOR domain
 solves, the clover term and its Jacobi preconditioning (operators, SAP with
 MR and SSOR, block solves of D_c X = B), the request server (two solver
 slots on host threads, four clients submitting and waiting from host
-threads at once), and the 8-CTA cluster sweep alone and in a block solve on
-an 8^4 lattice.  Mistakes
+threads at once), and the 8-CTA cluster sweep alone and (AddressSanitizer)
+in a block solve on an 8^4 lattice.  Mistakes
 planted in a copy of the sources were each reported: an off-by-one write and
 a misaligned float4 load in a layout kernel, and a removed barrier before a
 block reduction (a data race)."""
