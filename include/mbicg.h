@@ -236,14 +236,17 @@ typedef enum {
   MBICG_K_NCLASS = 10
 } mbicg_kernel_class;
 
-/* enable != 0: from now on, time every kernel launch with CUDA events on the
- * context's stream and add it to its class (costs one event pair per launch).
+/* enable != 0: from now on, time the library's kernel launches with CUDA
+ * events on the context's stream, grouped in regions of one class (one event
+ * pair per region; a region holds one or two launches, e.g. the MR step
+ * length and update kernels of MBICG_K_SAP_UPDATE), and add them to their
+ * class.  Every kernel launch of mbicg_block_solve belongs to a region.
  * enable == 0 stops timing.  Either way the totals are reset. */
 int mbicg_set_profiling(mbicg_ctx* ctx, int enable);
 
-/* Copies the totals since profiling was enabled: ms[c] milliseconds and
- * launches[c] kernel launches of class c, for c < n (n <= MBICG_K_NCLASS).
- * Either pointer may be NULL. */
+/* Copies the totals since profiling was enabled: ms[c] milliseconds of the
+ * regions of class c and launches[c] the kernel launches in them, for c < n
+ * (n <= MBICG_K_NCLASS).  Either pointer may be NULL. */
 int mbicg_get_profile(const mbicg_ctx* ctx, double* ms, long long* launches, int n);
 
 /* Text of the last error on ctx ("" if none).  Valid until the next call. */

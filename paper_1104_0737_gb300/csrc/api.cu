@@ -216,7 +216,10 @@ int abi_norms(mbicg_ctx* c, const cx<double>* d, int L, double* norms, bool* bad
   SmallWork w{};
   w.norms = nrm;
   w.status = flag;  // lxl_norms ORs ST_NAN into it; abi_check sets bit 0
-  lxl_norms(ex, L, part, np, false, w);
+  {
+    Timed t(ex, KC_SMALL);
+    lxl_norms(ex, L, part, np, false, w);
+  }
   if ((rc = check_launch(c, "abi_norms"))) return rc;
   int st = 0;
   if ((rc = read_small(c, nrm, L, flag, norms, &st))) return rc;
@@ -381,7 +384,10 @@ struct Solver {
       Timed t(ex, KC_CONVERT);
       np = residual_from<T>(ex, V, L, B64, x_zero ? nullptr : W64, k.R, npart);
     }
-    lxl_norms(ex, L, npart, np, false, sm);
+    {
+      Timed t(ex, KC_SMALL);
+      lxl_norms(ex, L, npart, np, false, sm);
+    }
     int rc = check_launch(c, "true_residual");
     if (rc) return rc;
     int st = 0;
@@ -1128,8 +1134,14 @@ int mbicg_block_solve(mbicg_ctx* c, const double* B, double* X, int L, double ka
     const size_t nlt = (size_t)c->V * 12 * Lt;
     cx<double>*Bt, *Xt;
     if ((rc = buf(c, "dummy_B", nlt, &Bt)) || (rc = buf(c, "dummy_X", nlt, &Xt))) return rc;
-    pack_dummies(ex, c->V, L, Lt, dB, Bt, p->dummy_seed, true);
-    if (p->use_x0) pack_dummies(ex, c->V, L, Lt, dX, Xt, 0, false);
+    {
+      Timed t(ex, KC_CONVERT);
+      pack_dummies(ex, c->V, L, Lt, dB, Bt, p->dummy_seed, true);
+    }
+    if (p->use_x0) {
+      Timed t(ex, KC_CONVERT);
+      pack_dummies(ex, c->V, L, Lt, dX, Xt, 0, false);
+    }
     if ((rc = abi_norms(c, Bt, Lt, bnorm, &bad))) return rc;
     dB = Bt;
     dX = Xt;
@@ -1163,8 +1175,11 @@ int mbicg_block_solve(mbicg_ctx* c, const double* B, double* X, int L, double ka
   }
   if (true_res)
     for (int i = 0; i < L; ++i) true_res[i] = tres_all[i];
-  if (p->dummy_rhs > 0 && (st == MBICG_OK || st == MBICG_ENOTCONV || st == MBICG_EBREAKDOWN))
-    first_columns(exec_of(c), c->V, Lt, L, dX, static_cast<cx<double>*>(sx.dev));
+  if (p->dummy_rhs > 0 && (st == MBICG_OK || st == MBICG_ENOTCONV || st == MBICG_EBREAKDOWN)) {
+    const Exec ex = exec_of(c);
+    Timed t(ex, KC_CONVERT);
+    first_columns(ex, c->V, Lt, L, dX, static_cast<cx<double>*>(sx.dev));
+  }
   if (st == MBICG_ECUDA || st == MBICG_ENOMEM || st == MBICG_EINVAL) return st;
   if ((rc = stage_out(c, sx))) return rc;
   if (!sx.host) {

@@ -19,10 +19,12 @@ struct Prof {
   bool on = false;
   std::vector<cudaEvent_t> ev;  // pairs (start, stop)
   std::vector<int> cls;         // class of each pair
+  std::vector<long long> nl;    // kernel launches between the two events of each pair
   size_t used = 0;
+  long long first = 0;          // launch counter at the open pair's start
   double ms[16] = {0};
   long long count[16] = {0};
-  void begin(cudaStream_t s, int c) {
+  void begin(cudaStream_t s, int c, long long launches_now) {
     if (!on) return;
     if (used == cls.size()) {
       cudaEvent_t a, b;
@@ -31,13 +33,16 @@ struct Prof {
       ev.push_back(a);
       ev.push_back(b);
       cls.push_back(c);
+      nl.push_back(0);
     }
     cls[used] = c;
+    first = launches_now;
     cudaEventRecord(ev[2 * used], s);
   }
-  void end(cudaStream_t s) {
+  void end(cudaStream_t s, long long launches_now) {
     if (!on) return;
     cudaEventRecord(ev[2 * used + 1], s);
+    nl[used] = launches_now - first;
     ++used;
   }
   // call after the stream has been synchronised
@@ -45,7 +50,7 @@ struct Prof {
     for (size_t i = 0; i < used; ++i) {
       float t = 0;
       if (cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) ms[cls[i]] += t;
-      count[cls[i]] += 1;
+      count[cls[i]] += nl[i];
     }
     used = 0;
   }
@@ -76,8 +81,8 @@ struct Exec {
 // RAII: time the launches in a scope as one class
 struct Timed {
   const Exec& ex;
-  Timed(const Exec& e, int c) : ex(e) { if (ex.prof) ex.prof->begin(ex.stream, c); }
-  ~Timed() { if (ex.prof) ex.prof->end(ex.stream); }
+  Timed(const Exec& e, int c) : ex(e) { if (ex.prof) ex.prof->begin(ex.stream, c, *ex.launches); }
+  ~Timed() { if (ex.prof) ex.prof->end(ex.stream, *ex.launches); }
 };
 
 // ---------------------------------------------------------------------------

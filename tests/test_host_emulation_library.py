@@ -9,8 +9,11 @@ CUDA runtime calls are emulated over host memory
 solver runs its iterations eagerly).  Checked against the oracle: the
 operator with host pointers in FP64 and FP32, and mbicg_block_solve in FP64
 and in mixed precision (reliable updates), with dummy right-hand sides and an
-initial guess, the allocation-free operator on emulated device buffers, the
-give-up path of the bounded mbarrier wait, plus the ABI's argument errors.  This exercises the solver's
+initial guess, mbicg_sap_precond (per-column and block MR, FP64 and FP32),
+the residual history and the per-class launch profile, the FP16-storage
+operator against the oracle's FP16 format,
+the allocation-free operator on emulated device buffers, the give-up path of
+the bounded mbarrier wait, plus the ABI's argument errors.  This exercises the solver's
 host logic of Algorithm 2 on a machine without a GPU; the -m gpu tests run the
 same code on the hardware."""
 import ctypes
@@ -20,6 +23,7 @@ import numpy as np
 import pytest
 
 import emulation_sources
+import oracle
 
 import paper_1104_0737_gb300 as mb  # the ctypes structures only; no library is loaded
 import synth
@@ -183,3 +187,80 @@ def test_every_cuda_source_is_emulated():
     """The emulated library is built from every CUDA source of the package."""
     sources = {f for f in os.listdir(emulation_sources.CSRC) if f.endswith(".cu")}
     assert set(emulation_sources.LIBRARY_SOURCES) == sources
+
+
+def _comps(a):
+    """(V, 4, 3, L) complex -> (V, L, 24) reals of each (site, rhs) spinor."""
+    V, Lc = a.shape[0], a.shape[-1]
+    return np.stack([a.real, a.imag], -1).reshape(V, 12, Lc, 2).transpose(0, 2, 1, 3).reshape(V, Lc, 24)
+
+
+def test_fp16_operator_through_the_abi(lib, ctx, oracle_mod):
+    """mbicg_apply_D with MBICG_FP16 (conversions into and out of FP16 storage
+    with one scale per (site, column), the FP16 operator): kappa = 0 gives the
+    input as the oracle's FP16 format represents it, bit for bit (a zero spinor
+    keeps scale 0); kappa = 0.13 gives the oracle's operator on the
+    FP16-represented links and input, rounded into the format, up to one FP16
+    step of the output scale where the FP32 and FP64 sums round differently."""
+    c, U = ctx
+    psi = synth.gaussian_source(DIMS, 3, seed=2007)
+    psi[3] = 0
+    out = np.empty_like(psi)
+    assert lib.mbicg_apply_D(c, _v(psi), _v(out), 3, 0.0, mb.MBICG_FP16) == mb.MBICG_OK
+    assert np.array_equal(out, oracle.quantize_fp16(psi))
+    assert lib.mbicg_apply_D(c, _v(psi), _v(out), 3, 0.13, mb.MBICG_FP16) == mb.MBICG_OK
+    exp = oracle.quantize_fp16(oracle_mod.apply_D(DIMS, oracle.quantize_links_fp16(U), 0.13, oracle.quantize_fp16(psi)))
+    g, e = _comps(out), _comps(exp)
+    sc = np.abs(e).max(axis=2, keepdims=True)
+    assert np.all(np.abs(g - e) <= 2.0 ** -10 * sc)
+    assert np.mean(np.abs(g - e) > 2.0 ** -20 * sc) < 0.05
+
+
+@pytest.mark.parametrize("mode,prec,tol", [(0, mb.MBICG_FP64, 1e-12), (1, mb.MBICG_FP64, 1e-12),
+                                           (0, mb.MBICG_FP32, 1e-5), (1, mb.MBICG_FP32, 1e-5)])
+def test_sap_precond_through_the_abi(lib, ctx, oracle_mod, mode, prec, tol):
+    """mbicg_sap_precond (host pointers) against the oracle's SAP: per-column
+    and block-shared MR, FP64 and FP32."""
+    c, U = ctx
+    eta = synth.gaussian_source(DIMS, L, seed=2008)
+    out = np.empty_like(eta)
+    p = _params(lib, ncycle=2, nmr=3, mr_mode=mode, prec_sap=prec)
+    assert lib.mbicg_sap_precond(c, _v(eta), _v(out), L, KAPPA, ctypes.byref(p)) == mb.MBICG_OK
+    ref = oracle_mod.sap(DIMS, (2, 2, 2, 2), U, KAPPA, 2, 3, eta, mr_mode=mode)
+    assert np.max(np.abs(out - ref)) < tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec_D,dummies", [(mb.MBICG_FP64, 0), (mb.MBICG_FP32, 2)])
+def test_history_and_profile_through_the_abi(lib, ctx, prec_D, dummies):
+    """res_history holds the recursive residual after each iteration (one entry
+    per iteration, falling to the tolerance); with profiling on, every launch
+    of the solve (FP64, and mixed precision with dummy columns) is counted in
+    a kernel class and timed (the emulated events read the host clock): the
+    counts add up to the solve's launches, and the operator's class has its
+    two launches per iteration."""
+    c, _ = ctx
+    lib.mbicg_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.mbicg_get_profile.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+    ncls = 10  # MBICG_K_NCLASS of include/mbicg.h
+    B = synth.gaussian_source(DIMS, L, seed=2009)
+    X = np.empty_like(B)
+    hist = np.full(64, np.nan)
+    p = _params(lib, prec_D=prec_D, dummy_rhs=dummies, dummy_seed=3)
+    p.res_history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.res_history_len = len(hist)
+    assert lib.mbicg_set_profiling(c, 1) == mb.MBICG_OK
+    try:
+        rc, iters, tres, st = _solve(lib, c, B, X, p)
+        ms = np.zeros(ncls)
+        n = np.zeros(ncls, dtype=np.int64)
+        assert lib.mbicg_get_profile(c, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     n.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), ncls) == mb.MBICG_OK
+    finally:
+        lib.mbicg_set_profiling(c, 0)
+    assert rc == mb.MBICG_OK and 0 < iters <= len(hist)
+    h = hist[:iters]
+    assert np.all(np.isfinite(h)) and np.all(np.isnan(hist[iters:]))
+    assert h[-1] <= 1e-10 < h[0] and h[-1] < h[:-1].min()
+    assert n.sum() == st.kernel_launches > 0 and np.all(ms >= 0) and ms.sum() > 0
+    assert n[0] == 2 * iters  # MBICG_K_DSLASH
