@@ -49,6 +49,9 @@ typedef enum {
   MBICG_ECUDA = -7        /* a CUDA runtime error; see mbicg_last_error */
 } mbicg_status;
 
+/* SAP domain solvers. */
+typedef enum { MBICG_DOMAIN_MR = 0, MBICG_DOMAIN_SSOR = 1 } mbicg_domain_solver;
+
 /* Arithmetic and storage precision of an operator. */
 typedef enum { MBICG_FP64 = 0, MBICG_FP32 = 1, MBICG_FP16 = 2 } mbicg_prec;
 
@@ -95,6 +98,21 @@ typedef struct {
    * given columns only.  L + dummy_rhs <= 16.  Default 0. */
   int dummy_rhs;
   unsigned long long dummy_seed;
+  /* Nonzero: the matrix is the Jacobi-preconditioned clover matrix
+   * A = T^{-1} D_c of the clover term loaded by mbicg_load_clover (Sec. 2.2);
+   * mbicg_block_solve solves D_c X = B as A X = T^{-1} B (true_res and the
+   * stopping test refer to that system), mbicg_sap_precond preconditions A.
+   * Default 0 (the Wilson matrix). */
+  int clover;
+  /* SAP domain solver (Sec. 2.2): MBICG_DOMAIN_MR (default: nmr minimal-
+   * residual steps, mr_mode) or MBICG_DOMAIN_SSOR: the paper's SSOR
+   * approximation B = (1 - omega U)^{-1} [sum_{j=0}^{nssor} (1 - A^SSOR)^j]
+   * (1 - omega L)^{-1} on each domain (L, U the forward and backward hops
+   * inside the domain), a fixed linear operator.  0 <= nssor <= 16,
+   * 0 < ssor_omega < 2; defaults 1 and 1.26 (the paper's values). */
+  int domain_solver;
+  int nssor;
+  double ssor_omega;
 } mbicg_params;
 
 /* Counters of the last call on a context. */
@@ -114,7 +132,8 @@ typedef struct {
 
 /* Fills p with the defaults: ncycle 4, nmr 4, block {4,4,4,4},
  * MBICG_MR_FROZEN, prec_sap FP32, prec_D FP32, max_iter 1000, use_x0 0,
- * delta_ru 0.1, no history, no dummy right-hand sides. */
+ * delta_ru 0.1, no history, no dummy right-hand sides, no clover term,
+ * MR domain solves (nssor 1, ssor_omega 1.26 for SSOR). */
 void mbicg_default_params(mbicg_params* p);
 
 /* Creates a context for a lattice of extents dims on CUDA device `device`.
@@ -147,6 +166,29 @@ int mbicg_load_gauge(mbicg_ctx* ctx, const double* U);
  * 1 <= L <= 16.  in and out must not alias. */
 int mbicg_apply_D(mbicg_ctx* ctx, const double* in, double* out, int L, double kappa,
                   int prec);
+
+/* Clover term of the O(a)-improved Wilson-Dirac matrix (Sec. 2.2; the paper
+ * names the improvement, this is its standard clover-leaf form):
+ *   D_c = T - kappa H,   T_x = 1 + kappa C_x,
+ *   C_x = i csw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x),   sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu],
+ *   F_{mu nu}(x) = (Q_{mu nu}(x) - Q_{mu nu}(x)^dagger) / 8,
+ * Q_{mu nu}(x) the four plaquettes of the (mu, nu) plane that start and end at
+ * x, all traversed mu before nu.  Computes C from the loaded gauge field (FP64;
+ * 72 doubles per site plus FP32 copies and the inverse of T for the kappa of
+ * the next call: about 1.8 kB of device memory per site in all).  csw = 0
+ * switches the clover term off.  Loading another gauge field switches it off
+ * too.  Errors: MBICG_ENOGAUGE, MBICG_EINVAL (csw < 0 or not finite),
+ * MBICG_ENOMEM, MBICG_ECUDA. */
+int mbicg_load_clover(mbicg_ctx* ctx, double csw);
+
+/* out = D_c in (jacobi = 0) or out = A in = T^{-1} D_c in (jacobi = 1), with
+ * the clover term of mbicg_load_clover; layout, pointers and precision as
+ * mbicg_apply_D (MBICG_FP64 or MBICG_FP32; FP16 is rejected).  T^{-1} is
+ * formed for kappa when kappa changes (FP64 Gauss-Jordan per 6 x 6 chirality
+ * block).  Errors: as mbicg_apply_D, and MBICG_EINVAL when no clover term is
+ * loaded or 1 + kappa C is singular at some site. */
+int mbicg_apply_clover(mbicg_ctx* ctx, const double* in, double* out, int L, double kappa, int prec,
+                       int jacobi);
 
 /* out = M_SAP in (Sec. 2.2) with the parameters ncycle, nmr, block, mr_mode
  * (MBICG_MR_COLUMN or MBICG_MR_BLOCK) and prec_sap of *p.  1 <= L <= 16. */

@@ -19,10 +19,11 @@ from . import _build
 __all__ = [
     "MBICG_OK", "MBICG_EINVAL", "MBICG_ENOMEM", "MBICG_ENOGAUGE", "MBICG_ENOTCONV",
     "MBICG_EBREAKDOWN", "MBICG_ENAN", "MBICG_ECUDA", "MBICG_FP64", "MBICG_FP32", "MBICG_FP16",
-    "MBICG_MR_COLUMN", "MBICG_MR_BLOCK", "MBICG_MR_FROZEN", "KERNEL_CLASSES",
+    "MBICG_MR_COLUMN", "MBICG_MR_BLOCK", "MBICG_MR_FROZEN", "MBICG_DOMAIN_MR", "MBICG_DOMAIN_SSOR",
+    "KERNEL_CLASSES",
     "MbicgError", "mbicg_params", "mbicg_stats", "library_path", "load_library",
     "mbicg_default_params", "mbicg_create", "mbicg_destroy", "mbicg_load_gauge",
-    "mbicg_apply_D", "mbicg_sap_precond", "mbicg_block_solve", "mbicg_get_stats",
+    "mbicg_apply_D", "mbicg_load_clover", "mbicg_apply_clover", "mbicg_sap_precond", "mbicg_block_solve", "mbicg_get_stats",
     "mbicg_last_error", "mbicg_set_profiling", "mbicg_get_profile", "mbicg_apply_D_noalloc",
     "mbicg_request_info", "mbicg_server_create", "mbicg_server_add_field", "mbicg_server_submit",
     "mbicg_server_wait", "mbicg_server_hold", "mbicg_server_stats", "mbicg_server_destroy",
@@ -33,6 +34,7 @@ MBICG_OK, MBICG_EINVAL, MBICG_ENOMEM, MBICG_ENOGAUGE = 0, -1, -2, -3
 MBICG_ENOTCONV, MBICG_EBREAKDOWN, MBICG_ENAN, MBICG_ECUDA = -4, -5, -6, -7
 MBICG_FP64, MBICG_FP32, MBICG_FP16 = 0, 1, 2
 MBICG_MR_COLUMN, MBICG_MR_BLOCK, MBICG_MR_FROZEN = 0, 1, 2
+MBICG_DOMAIN_MR, MBICG_DOMAIN_SSOR = 0, 1
 KERNEL_CLASSES = ["dslash", "dslash64", "sap_resid", "sap_domain", "sap_update", "gram",
                   "axpy", "small", "convert", "sap_sweep"]
 
@@ -52,7 +54,8 @@ class mbicg_params(ctypes.Structure):
         ("mr_mode", ctypes.c_int), ("prec_sap", ctypes.c_int), ("prec_D", ctypes.c_int),
         ("max_iter", ctypes.c_int), ("use_x0", ctypes.c_int), ("delta_ru", ctypes.c_double),
         ("res_history", ctypes.POINTER(ctypes.c_double)), ("res_history_len", ctypes.c_int),
-        ("dummy_rhs", ctypes.c_int), ("dummy_seed", ctypes.c_ulonglong),
+        ("dummy_rhs", ctypes.c_int), ("dummy_seed", ctypes.c_ulonglong), ("clover", ctypes.c_int),
+        ("domain_solver", ctypes.c_int), ("nssor", ctypes.c_int), ("ssor_omega", ctypes.c_double),
     ]
 
 
@@ -95,6 +98,8 @@ def load_library(build_if_missing: bool = True):
     lib.mbicg_destroy.restype = None
     lib.mbicg_load_gauge.argtypes = [vp, vp]
     lib.mbicg_apply_D.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    lib.mbicg_load_clover.argtypes = [vp, ctypes.c_double]
+    lib.mbicg_apply_clover.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]
     lib.mbicg_sap_precond.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double,
                                       ctypes.POINTER(mbicg_params)]
     lib.mbicg_block_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -184,6 +189,16 @@ def mbicg_apply_D(ctx, inp, out, L: int, kappa: float, prec: int = MBICG_FP64) -
     pi, _ = _ptr(inp, "in")
     po, _ = _ptr(out, "out")
     _check(ctx, load_library().mbicg_apply_D(ctx, pi, po, int(L), float(kappa), int(prec)))
+
+
+def mbicg_load_clover(ctx, csw: float) -> None:
+    _check(ctx, load_library().mbicg_load_clover(ctx, float(csw)))
+
+
+def mbicg_apply_clover(ctx, inp, out, L: int, kappa: float, prec: int = MBICG_FP64, jacobi: int = 0) -> None:
+    pi, _ = _ptr(inp, "in")
+    po, _ = _ptr(out, "out")
+    _check(ctx, load_library().mbicg_apply_clover(ctx, pi, po, int(L), float(kappa), int(prec), int(jacobi)))
 
 
 def mbicg_sap_precond(ctx, inp, out, L: int, kappa: float, params: mbicg_params) -> None:

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libmbicg.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "dslash.cu", "sap.cu", "blas.cu", "noalloc.cu", "half.cu", "serve.cu", "selftest.cu", "tune.cu"]
+SOURCES = ["api.cu", "dslash.cu", "sap.cu", "blas.cu", "noalloc.cu", "half.cu", "serve.cu", "selftest.cu", "tune.cu",
+           "clover.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

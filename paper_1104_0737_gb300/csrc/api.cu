@@ -48,6 +48,14 @@ struct mbicg_ctx {
   Prof prof;
   std::map<std::string, std::pair<void*, size_t>> bufs;  // device workspaces
   double* h_small = nullptr;                            // pinned host scratch
+  // clover term (clover.cu): C packed per site in FP64 and FP32, T^{-1} for
+  // the kappa tinv_kappa (NaN: not formed); csw == 0: no clover term
+  double csw = 0.0;
+  double* C64 = nullptr;
+  float* C32 = nullptr;
+  double* Ti64 = nullptr;
+  float* Ti32 = nullptr;
+  double tinv_kappa = NAN;
 };
 
 namespace {
@@ -248,12 +256,20 @@ struct Solver {
   bool keep_table = false;  // continue with the frozen step lengths already recorded
   int Lc = 0;               // columns the stopping test covers (the others are dummies)
   SmallWork sm{};
+  // Jacobi-preconditioned clover matrix: T^{-1} per site (NULL: Wilson)
+  const double* ti64 = nullptr;
+  const float* ti32 = nullptr;
   double *gpart, *npart;
   double h_norm[MAXL + 1];
   double bnorm[MAXL];
 
   const cx<T>* links_T() const;
   const cx<TS>* links_S() const;
+  template <typename R>
+  const R* tinv() const {
+    return reinterpret_cast<const R*>(sizeof(R) == 8 ? static_cast<const void*>(ti64)
+                                                     : static_cast<const void*>(ti32));
+  }
 
   int alloc() {
     int rc;
@@ -283,6 +299,16 @@ struct Solver {
       if ((rc = buf(c, "sap_omega", (size_t)ndc * L * 2, &sw.omega))) return rc;
       if ((rc = buf(c, "sap_table", (size_t)p.ncycle * 2 * p.nmr * ndc * 2, &table))) return rc;
       if ((rc = buf(c, "sap_unset", 1, &unset))) return rc;
+      if (p.domain_solver == MBICG_DOMAIN_SSOR) {
+        const char* names4[4] = {"ssor_acc", "ssor_term", "ssor_pv", "ssor_pqv"};
+        for (int i = 0; i < 4; ++i) {
+          cx<TS>* b;
+          if ((rc = buf(c, names4[i], nl, &b))) return rc;
+          sw.ssor[i] = b;
+        }
+        if ((rc = buf(c, "ssor_levels", (size_t)g.Vd, &sw.levels))) return rc;
+        CK(sap_prepare_ssor(g, sw, c->stream));
+      }
       // every frozen step length starts unrecorded (NaN), unless this solve
       // continues another one with the same preconditioner
       if (!keep_table)
@@ -312,22 +338,26 @@ struct Solver {
       CK(cudaMemcpyAsync(out, in, sizeof(cx<T>) * nl, cudaMemcpyDeviceToDevice, c->stream));
       return MBICG_OK;
     }
-    int mode = p.mr_mode;
+    const SsorParams sp{p.nssor, p.ssor_omega};
+    const SsorParams* ssor = p.domain_solver == MBICG_DOMAIN_SSOR ? &sp : nullptr;
+    // SSOR: a fixed linear operator, no step lengths to record
+    int mode = ssor ? MBICG_MR_COLUMN : p.mr_mode;
     double* tab = nullptr;
-    if (p.mr_mode == MBICG_MR_FROZEN) {
+    if (mode == MBICG_MR_FROZEN) {
       // record until every entry of the table is set, then replay only
       mode = table_complete ? 3 : 2;
       tab = table;
       if (!table_complete) CK(cudaMemsetAsync(unset, 0, sizeof(int), c->stream));
     }
     if constexpr (std::is_same<T, TS>::value) {
-      sap_apply<TS>(ex, g, links_S(), in, out, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw);
+      sap_apply<TS>(ex, g, links_S(), in, out, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw, tinv<TS>(), ssor);
     } else {
       {
         Timed t(ex, KC_CONVERT);
         convert_block<T, TS>(ex, (long long)nl, in, eta_s);
       }
-      sap_apply<TS>(ex, g, links_S(), eta_s, psi_s, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw);
+      sap_apply<TS>(ex, g, links_S(), eta_s, psi_s, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw, tinv<TS>(),
+                    ssor);
       Timed t(ex, KC_CONVERT);
       convert_block<TS, T>(ex, (long long)nl, psi_s, out);
     }
@@ -343,7 +373,7 @@ struct Solver {
 
   int dslash(const cx<T>* in, cx<T>* out) {
     Timed t(ex, KC_DSLASH);
-    dslash_full<T>(ex, g, links_T(), in, out, L, kappa);
+    dslash_full<T>(ex, g, links_T(), in, out, L, kappa, tinv<T>(), ti64 ? 1 : 0);
     return MBICG_OK;
   }
 
@@ -352,7 +382,7 @@ struct Solver {
   int true_residual(double* rel, double* relmax, bool x_zero = false) {
     if (!x_zero) {
       Timed t(ex, KC_DSLASH64);
-      dslash_full<double>(ex, g, c->U64, X64, W64, L, kappa);
+      dslash_full<double>(ex, g, c->U64, X64, W64, L, kappa, ti64, ti64 ? 1 : 0);
     }
     int np;
     {
@@ -460,7 +490,8 @@ struct Solver {
   int launch_iteration() {
     const char* env = getenv("MBICG_GRAPHS");
     const bool enabled = !(env && env[0] == '0');
-    const bool stable = p.ncycle == 0 || p.mr_mode != MBICG_MR_FROZEN || table_complete;
+    const bool stable = p.ncycle == 0 || p.domain_solver == MBICG_DOMAIN_SSOR || p.mr_mode != MBICG_MR_FROZEN ||
+                        table_complete;
     if (!enabled || c->prof.on || !stable || graph_failed) return iteration_launches();
     if (!gexec) {
       const long long before = c->launches;
@@ -633,13 +664,21 @@ int check_params(mbicg_ctx* c, int L, const mbicg_params* p, bool solve) {
   if (!p) return fail(c, MBICG_EINVAL, "params is NULL");
   if (solve && (p->dummy_rhs < 0 || L + p->dummy_rhs > MAXL))
     return fail(c, MBICG_EINVAL, "dummy_rhs must be >= 0 with L + dummy_rhs <= 16");
+  if (p->clover != 0 && p->clover != 1) return fail(c, MBICG_EINVAL, "clover must be 0 or 1");
+  if (p->clover && !(c->csw > 0)) return fail(c, MBICG_EINVAL, "no clover term loaded");
   if (p->ncycle < 0 || p->ncycle > 64) return fail(c, MBICG_EINVAL, "ncycle out of range");
   if (p->ncycle > 0) {
     if (p->nmr < 1 || p->nmr > 256) return fail(c, MBICG_EINVAL, "nmr must be in [1, 256]");
     if (!valid_blocking(c, p->block))
       return fail(c, MBICG_EINVAL, "SAP block must divide the lattice into an even number (>= 2) of domains per direction");
-    if (p->mr_mode < 0 || p->mr_mode > 2 || (!solve && p->mr_mode == MBICG_MR_FROZEN))
+    if (p->domain_solver != MBICG_DOMAIN_MR && p->domain_solver != MBICG_DOMAIN_SSOR)
+      return fail(c, MBICG_EINVAL, "bad domain_solver");
+    if (p->domain_solver == MBICG_DOMAIN_SSOR) {
+      if (p->nssor < 0 || p->nssor > 16) return fail(c, MBICG_EINVAL, "nssor must be in [0, 16]");
+      if (!(p->ssor_omega > 0 && p->ssor_omega < 2)) return fail(c, MBICG_EINVAL, "ssor_omega must be in (0, 2)");
+    } else if (p->mr_mode < 0 || p->mr_mode > 2 || (!solve && p->mr_mode == MBICG_MR_FROZEN)) {
       return fail(c, MBICG_EINVAL, "bad mr_mode");
+    }
     if (p->prec_sap != MBICG_FP32 && p->prec_sap != MBICG_FP64)
       return fail(c, MBICG_EINVAL, "prec_sap must be MBICG_FP32 or MBICG_FP64");
   }
@@ -666,8 +705,38 @@ int run_solve(mbicg_ctx* c, const cx<double>* dB, cx<double>* dX, int L, double 
   s.kappa = kappa;
   s.p = *p;
   s.V = c->V;
+  if (p->clover) {
+    s.ti64 = c->Ti64;
+    s.ti32 = c->Ti32;
+  }
   for (int i = 0; i < L; ++i) s.bnorm[i] = bnorm[i];
   return s.run(dB, dX, tol, iters, true_res);
+}
+
+// T^{-1} = (1 + kappa C)^{-1} of the loaded clover term, formed when kappa changes
+int clover_for_kappa(mbicg_ctx* c, double kappa) {
+  if (!(c->csw > 0)) return fail(c, MBICG_EINVAL, "no clover term loaded");
+  if (c->tinv_kappa == kappa) return MBICG_OK;
+  int* st;
+  int rc;
+  if ((rc = buf(c, "clover_status", 1, &st))) return rc;
+  CK(cudaMemsetAsync(st, 0, sizeof(int), c->stream));
+  const Exec ex = exec_of(c);
+  {
+    Timed t(ex, KC_CONVERT);
+    clover_terms(ex, c->V, c->C64, kappa, c->Ti64, c->Ti32, c->C32, st);
+  }
+  if ((rc = check_launch(c, "clover_terms"))) return rc;
+  CK(cudaMemcpyAsync(c->h_small, st, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int bad = 0;
+  memcpy(&bad, c->h_small, sizeof(int));
+  if (bad) {
+    c->tinv_kappa = NAN;
+    return fail(c, MBICG_EINVAL, "1 + kappa C is singular at some site");
+  }
+  c->tinv_kappa = kappa;
+  return MBICG_OK;
 }
 
 }  // namespace
@@ -693,6 +762,9 @@ void mbicg_default_params(mbicg_params* p) {
   p->delta_ru = 0.1;
   p->res_history = nullptr;
   p->res_history_len = 0;
+  p->domain_solver = MBICG_DOMAIN_MR;
+  p->nssor = 1;
+  p->ssor_omega = 1.26;
 }
 
 int mbicg_create(mbicg_ctx** out, const int dims[4], int device, void* cuda_stream) {
@@ -747,6 +819,10 @@ void mbicg_destroy(mbicg_ctx* c) {
   if (c->U64) cudaFree(c->U64);
   if (c->U32) cudaFree(c->U32);
   if (c->U16) cudaFree(c->U16);
+  if (c->C64) cudaFree(c->C64);
+  if (c->C32) cudaFree(c->C32);
+  if (c->Ti64) cudaFree(c->Ti64);
+  if (c->Ti32) cudaFree(c->Ti32);
   c->prof.release();
   if (c->h_small) cudaFreeHost(c->h_small);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -759,6 +835,8 @@ int mbicg_load_gauge(mbicg_ctx* c, const double* U) {
   if (!U) return fail(c, MBICG_EINVAL, "U is NULL");
   CK(cudaSetDevice(c->device));
   c->launches = 0;
+  c->csw = 0.0;  // a clover term belongs to the previous field
+  c->tinv_kappa = NAN;
   const size_t n = (size_t)c->V * 36;  // complex numbers
   if (!c->U64) CK(cudaMalloc(&c->U64, sizeof(cx<double>) * n));
   if (!c->U32) CK(cudaMalloc(&c->U32, sizeof(cx<float>) * n));
@@ -861,6 +939,87 @@ int mbicg_apply_D(mbicg_ctx* c, const double* in, double* out, int L, double kap
   return MBICG_OK;
 }
 
+int mbicg_load_clover(mbicg_ctx* c, double csw) {
+  if (!c) return MBICG_EINVAL;
+  c->err.clear();
+  if (!(csw >= 0) || !isfinite(csw)) return fail(c, MBICG_EINVAL, "csw must be finite and >= 0");
+  if (!c->gauge) return fail(c, MBICG_ENOGAUGE, "no gauge field loaded");
+  CK(cudaSetDevice(c->device));
+  c->launches = 0;
+  c->tinv_kappa = NAN;
+  c->csw = 0.0;
+  if (csw == 0) return MBICG_OK;
+  const size_t n = (size_t)c->V * HERM_PER_SITE;
+  if (!c->C64) CK(cudaMalloc(&c->C64, sizeof(double) * n));
+  if (!c->C32) CK(cudaMalloc(&c->C32, sizeof(float) * n));
+  if (!c->Ti64) CK(cudaMalloc(&c->Ti64, sizeof(double) * n));
+  if (!c->Ti32) CK(cudaMalloc(&c->Ti32, sizeof(float) * n));
+  const Exec ex = exec_of(c);
+  {
+    Timed t(ex, KC_CONVERT);
+    clover_field(ex, lattice_geom(c, nullptr), c->U64, csw, c->C64);
+  }
+  int rc;
+  if ((rc = check_launch(c, "load_clover"))) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  c->prof.collect();
+  c->csw = csw;
+  c->stats.kernel_launches = c->launches;
+  return MBICG_OK;
+}
+
+int mbicg_apply_clover(mbicg_ctx* c, const double* in, double* out, int L, double kappa, int prec, int jacobi) {
+  if (!c) return MBICG_EINVAL;
+  c->err.clear();
+  if (!in || !out || in == out) return fail(c, MBICG_EINVAL, "in/out NULL or aliased");
+  if (L < 1 || L > MAXL) return fail(c, MBICG_EINVAL, "L must be in [1, 16]");
+  if (prec != MBICG_FP64 && prec != MBICG_FP32) return fail(c, MBICG_EINVAL, "prec must be FP64 or FP32");
+  if (jacobi != 0 && jacobi != 1) return fail(c, MBICG_EINVAL, "jacobi must be 0 or 1");
+  if (!c->gauge) return fail(c, MBICG_ENOGAUGE, "no gauge field loaded");
+  CK(cudaSetDevice(c->device));
+  c->launches = 0;
+  int rc;
+  if ((rc = clover_for_kappa(c, kappa))) return rc;
+  const size_t nl = (size_t)c->V * 12 * L;
+  Staged si, so;
+  if ((rc = stage_in(c, in, sizeof(cx<double>) * nl, "abi_in", true, &si))) return rc;
+  if ((rc = stage_in(c, out, sizeof(cx<double>) * nl, "abi_out", false, &so))) return rc;
+  const Exec ex = exec_of(c);
+  const Geom g = lattice_geom(c, nullptr);
+  const int cm = jacobi ? 1 : 2;
+  if (prec == MBICG_FP64) {
+    cx<double>*a, *b;
+    if ((rc = buf(c, "op64_a", nl, &a)) || (rc = buf(c, "op64_b", nl, &b))) return rc;
+    {
+      Timed t(ex, KC_CONVERT);
+      abi_to_internal<double>(ex, c->V, L, static_cast<const cx<double>*>(si.dev), a);
+    }
+    {
+      Timed t(ex, KC_DSLASH64);
+      dslash_full<double>(ex, g, c->U64, a, b, L, kappa, jacobi ? c->Ti64 : c->C64, cm);
+    }
+    Timed t(ex, KC_CONVERT);
+    internal_to_abi<double>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
+  } else {
+    cx<float>*a, *b;
+    if ((rc = buf(c, "op32_a", nl, &a)) || (rc = buf(c, "op32_b", nl, &b))) return rc;
+    {
+      Timed t(ex, KC_CONVERT);
+      abi_to_internal<float>(ex, c->V, L, static_cast<const cx<double>*>(si.dev), a);
+    }
+    {
+      Timed t(ex, KC_DSLASH);
+      dslash_full<float>(ex, g, c->U32, a, b, L, kappa, jacobi ? c->Ti32 : c->C32, cm);
+    }
+    Timed t(ex, KC_CONVERT);
+    internal_to_abi<float>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
+  }
+  if ((rc = check_launch(c, "apply_clover"))) return rc;
+  if ((rc = stage_out(c, so))) return rc;
+  c->stats.kernel_launches = c->launches;
+  return MBICG_OK;
+}
+
 int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double kappa, const mbicg_params* p) {
   if (!c) return MBICG_EINVAL;
   c->err.clear();
@@ -871,6 +1030,7 @@ int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double
   if (!c->gauge) return fail(c, MBICG_ENOGAUGE, "no gauge field loaded");
   CK(cudaSetDevice(c->device));
   c->launches = 0;
+  if (p->clover && (rc = clover_for_kappa(c, kappa))) return rc;
   const size_t nl = (size_t)c->V * 12 * L;
   Staged si, so;
   if ((rc = stage_in(c, in, sizeof(cx<double>) * nl, "abi_in", true, &si))) return rc;
@@ -894,13 +1054,31 @@ int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double
     const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
     if ((rc2 = buf(c, "sap_dots", (size_t)ndc * (g.Vd / S) * L * 3, &w.dots))) return rc2;
     if ((rc2 = buf(c, "sap_omega", (size_t)ndc * L * 2, &w.omega))) return rc2;
+    const SsorParams sp{p->nssor, p->ssor_omega};
+    if (p->domain_solver == MBICG_DOMAIN_SSOR) {
+      const char* names4[4] = {"ssor_acc", "ssor_term", "ssor_pv", "ssor_pqv"};
+      for (int i = 0; i < 4; ++i) {
+        cx<R>* b4;
+        if ((rc2 = buf(c, names4[i], nl, &b4))) return rc2;
+        w.ssor[i] = b4;
+      }
+      if ((rc2 = buf(c, "ssor_levels", (size_t)g.Vd, &w.levels))) return rc2;
+      if (sap_prepare_ssor(g, w, c->stream) != cudaSuccess) return fail(c, MBICG_ECUDA, "ssor level table");
+    }
     {
       Timed t(ex, KC_CONVERT);
       abi_to_internal<R>(ex, c->V, L, static_cast<const cx<double>*>(si.dev), a);
     }
-    sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, p->mr_mode, nullptr, nullptr, w);
+    const R* tinv = nullptr;
+    if (p->clover) tinv = reinterpret_cast<const R*>(sizeof(R) == 8 ? static_cast<const void*>(c->Ti64)
+                                                                     : static_cast<const void*>(c->Ti32));
+    sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, p->mr_mode, nullptr, nullptr, w, tinv,
+                 p->domain_solver == MBICG_DOMAIN_SSOR ? &sp : nullptr);
     Timed t(ex, KC_CONVERT);
     internal_to_abi<R>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
+    // the level table's host copy lives in w: wait for its upload before w goes
+    if (p->domain_solver == MBICG_DOMAIN_SSOR && cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return fail(c, MBICG_ECUDA, "sap_precond");
     return MBICG_OK;
   };
   if (p->prec_sap == MBICG_FP64) rc = run(double(0), c->U64);
@@ -941,6 +1119,17 @@ int mbicg_block_solve(mbicg_ctx* c, const double* B, double* X, int L, double ka
   }
   const cx<double>* dB = static_cast<const cx<double>*>(sb.dev);
   cx<double>* dX = static_cast<cx<double>*>(sx.dev);
+  if (p->clover) {
+    // D_c X = B is solved as A X = T^{-1} B with A = T^{-1} D_c
+    if ((rc = clover_for_kappa(c, kappa))) return rc;
+    cx<double>* Bc;
+    if ((rc = buf(c, "clover_B", nl, &Bc))) return rc;
+    clover_abi(exec_of(c), c->V, L, c->Ti64, dB, Bc);
+    if ((rc = abi_norms(c, Bc, L, bnorm, &bad))) return rc;
+    for (int i = 0; i < L; ++i)
+      if (!(bnorm[i] > 0)) return fail(c, MBICG_EINVAL, "T^{-1} B has a zero column");
+    dB = Bc;
+  }
   // dummy right-hand sides: solve the block widened by seeded Gaussian
   // columns; the stopping test and the results cover the first L columns
   const int Lt = L + p->dummy_rhs;

@@ -348,4 +348,45 @@ __device__ __forceinline__ void link_times(const Link<R>& u, const cx<R> h[2][3]
     }
 }
 
+// ---------------------------------------------------------------------------
+// Site-local Hermitian spin-colour matrices that are block diagonal in
+// chirality (the clover term and its inverse: sigma_{mu nu} commutes with
+// gamma_5 = diag(1, 1, -1, -1) in the chiral basis).  Per site two 6 x 6
+// blocks, spins 0-1 and spins 2-3, index 3 * spin + colour inside a block;
+// each block packed as its 6 real diagonal entries, then the 15 entries above
+// the diagonal row by row as (re, im): 36 reals per block, 72 per site.
+// ---------------------------------------------------------------------------
+constexpr int HERM_PER_SITE = 72;
+
+__host__ __device__ constexpr int herm_off(int i, int j) {  // i < j
+  return 6 + 2 * (i * 6 - i * (i + 1) / 2 + (j - i - 1));
+}
+
+// y = M x for the packed matrix M of one site (m: its 72 reals); each entry is
+// loaded where it is used (the off-diagonal ones twice, from L1), which keeps
+// few registers live inside kernels that are already near their limit
+template <typename R>
+__device__ __forceinline__ void herm_apply(const R* __restrict__ m, const Spinor<R>& x, Spinor<R>& y) {
+  const cx<R>* xv = &x.c[0][0];
+  cx<R>* yv = &y.c[0][0];
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const R* mb = m + 36 * b;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const R d = __ldg(mb + i);
+      const cx<R> xi = xv[6 * b + i];
+      cx<R> acc = mk(d * xi.re, d * xi.im);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (j == i) continue;
+        const int o = i < j ? herm_off(i, j) : herm_off(j, i);
+        const R re = __ldg(mb + o), im = __ldg(mb + o + 1);
+        cmac(acc, i < j ? mk(re, im) : mk(re, -im), xv[6 * b + j]);
+      }
+      yv[6 * b + i] = acc;
+    }
+  }
+}
+
 }  // namespace mbicg

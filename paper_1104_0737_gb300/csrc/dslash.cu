@@ -98,11 +98,35 @@ __host__ __device__ __forceinline__ int segment_of(int b, int wslice, int tt) {
   return (slab * tt + dt) * wslice + w;
 }
 
-template <typename R>
+// Clover variants of the operator (clover.cu): CM = 0 the Wilson matrix,
+// CM = 1 the Jacobi-preconditioned A = 1 - kappa M H with M = T^{-1},
+// CM = 2 D_c = 1 + kappa M - kappa H with M = C (M packed per site).
+template <typename R, int CM>
+__device__ __forceinline__ void finish_site(const R* __restrict__ clov, int s, R kappa, const Spinor<R>& p,
+                                            Spinor<R>& acc) {
+  if (CM == 1) {
+    Spinor<R> h;
+    herm_apply<R>(clov + (size_t)s * HERM_PER_SITE, acc, h);
+    acc = h;
+  } else if (CM == 2) {
+    Spinor<R> cp;
+    herm_apply<R>(clov + (size_t)s * HERM_PER_SITE, p, cp);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) (&acc.c[0][0])[k] = (&acc.c[0][0])[k] - (&cp.c[0][0])[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    cx<R>& o = (&acc.c[0][0])[k];
+    const cx<R> v = (&p.c[0][0])[k];
+    o = mk(fma(-kappa, o.re, v.re), fma(-kappa, o.im, v.im));
+  }
+}
+
+template <typename R, int CM>
 __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_dslash_full(Geom g, const cx<R>* __restrict__ links,
                                                      const cx<R>* __restrict__ in,
-                                                     cx<R>* __restrict__ out, int L, R kappa, int wslice,
-                                                     int tt) {
+                                                     cx<R>* __restrict__ out, int L, R kappa,
+                                                     const R* __restrict__ clov, int wslice, int tt) {
   const int rhs = threadIdx.x;
   const int s = segment_of(blockIdx.x, wslice, tt) * blockDim.y + threadIdx.y;
   if (s >= g.V) return;
@@ -112,22 +136,17 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_dslash_full(Geo
   hopping<R, false>(g, links, in, L, rhs, s, c, c, acc);
   Spinor<R> p;
   load_spinor(in + spinor_offset(s, L, rhs), p);
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    cx<R>& o = (&acc.c[0][0])[k];
-    const cx<R> v = (&p.c[0][0])[k];
-    o = mk(fma(-kappa, o.re, v.re), fma(-kappa, o.im, v.im));
-  }
+  finish_site<R, CM>(clov, s, kappa, p, acc);
   store_spinor(out + spinor_offset(s, L, rhs), acc);
 }
 
-template <typename R>
+template <typename R, int CM>
 __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Geom g, int colour,
                                                       const cx<R>* __restrict__ links,
                                                       const cx<R>* __restrict__ eta,
                                                       const cx<R>* __restrict__ psi,
                                                       cx<R>* __restrict__ r, int L, R kappa,
-                                                      int psi_zero) {
+                                                      int psi_zero, const R* __restrict__ clov) {
   const int rhs = threadIdx.x;
   const int slot = blockIdx.x * blockDim.y + threadIdx.y;
   int c[4], lc[4], k;
@@ -138,6 +157,11 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Ge
   if (!psi_zero) {
     Spinor<R> acc, p;
     hopping<R, false>(g, links, psi, L, rhs, s, c, c, acc);
+    if (CM == 1) {  // A = 1 - kappa T^{-1} H
+      Spinor<R> h;
+      herm_apply<R>(clov + (size_t)s * HERM_PER_SITE, acc, h);
+      acc = h;
+    }
     load_spinor(psi + spinor_offset(s, L, rhs), p);
     // r = eta - (psi - kappa eta_hop) = eta - psi + kappa eta_hop
 #pragma unroll
@@ -150,13 +174,13 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Ge
   store_spinor(r + spinor_offset(s, L, rhs), e);
 }
 
-template <typename R>
+template <typename R, int CM>
 __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_domain_apply(Geom g, int colour,
                                                           const cx<R>* __restrict__ links,
                                                           const cx<R>* __restrict__ r,
                                                           cx<R>* __restrict__ q,
                                                           double* __restrict__ dots, int L, R kappa,
-                                                          int nchunk) {
+                                                          int nchunk, const R* __restrict__ clov) {
   extern __shared__ unsigned char smem_raw[];
   R* red = reinterpret_cast<R*>(smem_raw);  // [3][S][L]
   const int rhs = threadIdx.x;
@@ -167,6 +191,11 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_domain_appl
   const int s = site_index(g, c);
   Spinor<R> acc, p;
   hopping<R, true>(g, links, r, L, rhs, s, c, lc, acc);
+  if (CM == 1) {  // A_dom = 1 - kappa T^{-1} H_dom
+    Spinor<R> h;
+    herm_apply<R>(clov + (size_t)s * HERM_PER_SITE, acc, h);
+    acc = h;
+  }
   load_spinor(r + spinor_offset(s, L, rhs), p);
   R nre = 0, nim = 0, den = 0;
 #pragma unroll
@@ -203,6 +232,65 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_domain_appl
     d[1] = red[n + rhs];
     d[2] = red[2 * n + rhs];
   }
+}
+
+// ---------------------------------------------------------------------------
+// SSOR domain solves (Sec. 2.2): one wavefront level of a triangular
+// substitution on every domain of one colour.  With L the forward and U the
+// backward hops inside a domain (times kappa T^{-1} for the clover matrix),
+// z = (1 - omega L)^{-1} y sets z_x = y_x + omega kappa [T^{-1}] (forward hops
+// of z)_x, and a forward hop raises the level lx + ly + lz + lt of the site by
+// one: the sites of one level depend only on the level above (below for U),
+// so each level is one launch over all domains of the colour.
+// ---------------------------------------------------------------------------
+template <typename R, int MU, bool FWD>
+__device__ __forceinline__ void hop_in_domain(const Geom& g, const cx<R>* __restrict__ links,
+                                              const cx<R>* __restrict__ in, int L, int rhs, int s, const int lc[4],
+                                              int stride, Spinor<R>& acc) {
+  // no hop inside a domain crosses the lattice boundary (>= 2 domains per direction)
+  if (FWD) {
+    if (lc[MU] != g.blk[MU] - 1)
+      hop<MU, -1>(acc, in + spinor_offset(s + stride, L, rhs), links + (size_t)(s * 4 + MU) * 9, false);
+  } else {
+    if (lc[MU] != 0)
+      hop<MU, +1>(acc, in + spinor_offset(s - stride, L, rhs), links + (size_t)((s - stride) * 4 + MU) * 9, false);
+  }
+}
+
+template <typename R, int CM, bool FWD>
+__global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_ssor_level(Geom g, int colour,
+                                                    const cx<R>* __restrict__ links, const R* __restrict__ tinv,
+                                                    const cx<R>* __restrict__ y, cx<R>* z, int L, R komega,
+                                                    const int* __restrict__ local, int count) {
+  const int rhs = threadIdx.x;
+  const int i = blockIdx.x * blockDim.y + threadIdx.y;
+  if (i >= (g.nd / 2) * count) return;
+  const int k = i / count;
+  const int slot = k * g.Vd + __ldg(local + (i - k * count));
+  int c[4], lc[4], kk;
+  colour_slot_coords(g, colour, slot, c, lc, &kk);
+  const int s = site_index(g, c);
+  const int st1 = g.d[0], st2 = st1 * g.d[1], st3 = st2 * g.d[2];
+  Spinor<R> h;
+  zero(h);
+  hop_in_domain<R, 0, FWD>(g, links, z, L, rhs, s, lc, 1, h);
+  hop_in_domain<R, 1, FWD>(g, links, z, L, rhs, s, lc, st1, h);
+  hop_in_domain<R, 2, FWD>(g, links, z, L, rhs, s, lc, st2, h);
+  hop_in_domain<R, 3, FWD>(g, links, z, L, rhs, s, lc, st3, h);
+  if (CM == 1) {
+    Spinor<R> t;
+    herm_apply<R>(tinv + (size_t)s * HERM_PER_SITE, h, t);
+    h = t;
+  }
+  Spinor<R> v;
+  load_spinor(y + spinor_offset(s, L, rhs), v);
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    cx<R>& o = (&v.c[0][0])[j];
+    const cx<R> a = (&h.c[0][0])[j];
+    o = mk(fma(komega, a.re, o.re), fma(komega, a.im, o.im));
+  }
+  store_spinor(z + spinor_offset(s, L, rhs), v);
 }
 
 // ---------------------------------------------------------------------------
@@ -407,12 +495,14 @@ __device__ __forceinline__ void domain_hops(const Geom& g, const float4* vL, uin
   }
 }
 
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
+// CM = 1: the Jacobi-preconditioned clover matrix, every hop sum multiplied by
+// T^{-1} of its site (tinv, packed, read through L1)
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM>
 __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS,
                                   (SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS <= 256) ? 2 : 1)
     k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const cx<float>* __restrict__ eta,
                 cx<float>* __restrict__ psi, int L, float kappa, int psi_zero, int nmr, int mode,
-                const double* __restrict__ table) {
+                const double* __restrict__ table, const float* __restrict__ tinv) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   constexpr int NS = SH::NS;
   constexpr int CS = SH::CS;
@@ -497,6 +587,11 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
       Spinor<float> acc, pv;
       domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, true>(g, cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, c, s, L,
                                                        rhs, links, psi, acc);
+      if (CM == 1) {
+        Spinor<float> h;
+        herm_apply<float>(tinv + (size_t)s * HERM_PER_SITE, acc, h);
+        acc = h;
+      }
       load_spinor(eta + off, r0);
       planes_to_spinor(cur, NS, tid, pv);
 #pragma unroll
@@ -518,9 +613,15 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
       const bool last = (it == nmr - 1);
       Spinor<float> q, rv;
       const bool need_q = (mode == 0) || !last;
-      if (need_q)
+      if (need_q) {
         domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, false>(g, cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, c, s,
                                                           L, rhs, links, psi, q);
+        if (CM == 1) {
+          Spinor<float> h;
+          herm_apply<float>(tinv + (size_t)s * HERM_PER_SITE, q, h);
+          q = h;
+        }
+      }
       planes_to_spinor(cur, NS, tid, rv);
       if (need_q) {
 #pragma unroll
@@ -600,10 +701,10 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
 
 // sets the sweep kernel's shared-memory and cluster attributes and returns
 // how many of its clusters the GPU holds at once
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM>
 int sweep_setup(cudaLaunchConfig_t cfg) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
-  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT>;
+  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::smem_bytes());
   if (SH::CS > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cfg.gridDim = dim3((unsigned)SH::CS);
@@ -615,11 +716,12 @@ int sweep_setup(cudaLaunchConfig_t cfg) {
   return n;
 }
 
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM>
 bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
-                  cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table) {
+                  cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table,
+                  const float* tinv) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
-  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT>;
+  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM>;
   const size_t shm = SH::smem_bytes();
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(SH::NS);
@@ -635,11 +737,12 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
   // one persistent cluster per cluster slot of the GPU (clusters must fit
   // in one GPC, so fewer than SMs / CS may be resident at once); set up once
   // per process, thread-safely (contexts may run on several host threads)
-  static const int max_clusters = sweep_setup<DX, DY, DZ, DT, CX, CY, CZ, CT>(cfg);
+  static const int max_clusters = sweep_setup<DX, DY, DZ, DT, CX, CY, CZ, CT, CM>(cfg);
   const long long nitems = (long long)(g.nd / 2) * L;
   const int nclu = (int)std::min<long long>(max_clusters, nitems);
   cfg.gridDim = dim3((unsigned)(SH::CS * nclu));
-  cudaLaunchKernelEx(&cfg, kern, g, colour, links, eta, psi, L, (float)kappa, psi_zero ? 1 : 0, nmr, mode, table);
+  cudaLaunchKernelEx(&cfg, kern, g, colour, links, eta, psi, L, (float)kappa, psi_zero ? 1 : 0, nmr, mode, table,
+                     tinv);
   ++*ex.launches;
   return true;
 }
@@ -647,15 +750,26 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
 }  // namespace
 
 bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
-                     cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table) {
+                     cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table,
+                     const float* tinv) {
   if (mode == 1 || !g.su3) return false;  // the kernel rebuilds the third link row
   const int* bk = g.blk;
   // 8^4: eight CTAs of 8 x 4 x 4 x 4 sites (x, the unit-stride direction, is
   // not split, so its hops never leave the CTA); 4^4: one CTA
-  if (bk[0] == 8 && bk[1] == 8 && bk[2] == 8 && bk[3] == 8)
-    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
-  if (bk[0] == 4 && bk[1] == 4 && bk[2] == 4 && bk[3] == 4)
-    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table);
+  if (bk[0] == 8 && bk[1] == 8 && bk[2] == 8 && bk[3] == 8) {
+    if (tinv)
+      return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode,
+                                                     table, tinv);
+    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 0>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode,
+                                                   table, nullptr);
+  }
+  if (bk[0] == 4 && bk[1] == 4 && bk[2] == 4 && bk[3] == 4) {
+    if (tinv)
+      return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode,
+                                                     table, tinv);
+    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 0>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode,
+                                                   table, nullptr);
+  }
   return false;
 }
 
@@ -678,14 +792,19 @@ int sap_sites_per_cta(const Geom& g, int L, bool fp64) {
 // one launch of the operator in configuration cfg (tune.h)
 template <typename R>
 void launch_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
-                   double kappa, DslashConfig cfg) {
+                   double kappa, DslashConfig cfg, const R* clov, int cm) {
   const int S = cfg.S;
   const dim3 block(L, S);
   const int grid = (g.V + S - 1) / S;
   const int slice = g.d[0] * g.d[1] * g.d[2];
   const bool slabs = cfg.order == 1 && slice % S == 0 && g.d[3] % 8 == 0;
-  k_dslash_full<R><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa, slabs ? slice / S : 0,
-                                                             slabs ? 8 : 1);
+  const int ws = slabs ? slice / S : 0, tt = slabs ? 8 : 1;
+  if (cm == 1)
+    k_dslash_full<R, 1><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa, clov, ws, tt);
+  else if (cm == 2)
+    k_dslash_full<R, 2><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa, clov, ws, tt);
+  else
+    k_dslash_full<R, 0><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa, nullptr, ws, tt);
   ++*ex.launches;
 }
 
@@ -702,8 +821,8 @@ DslashConfig dslash_config(const Geom& g, int L) {
 
 template <typename R>
 void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
-                 double kappa) {
-  launch_dslash<R>(ex, g, links, in, out, L, kappa, dslash_config<R>(g, L));
+                 double kappa, const R* clov, int cm) {
+  launch_dslash<R>(ex, g, links, in, out, L, kappa, dslash_config<R>(g, L), clov, cm);
 }
 
 template <typename R>
@@ -720,7 +839,7 @@ void tune_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>*
   }
   tune_table().pick(dslash_key((int)sizeof(R), g.d, L), (int)cand.size(), [&](int i) -> double {
     cudaEventRecord(e0, ex.stream);
-    launch_dslash<R>(ex, g, links, in, out, L, kappa, cand[i]);
+    launch_dslash<R>(ex, g, links, in, out, L, kappa, cand[i], nullptr, 0);
     cudaEventRecord(e1, ex.stream);
     float ms = -1.0f;
     if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -735,34 +854,62 @@ void tune_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>*
 
 template <typename R>
 void sap_residual(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* eta,
-                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero) {
+                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero, const R* tinv) {
   const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
   const int nslot = (g.nd / 2) * g.Vd;
-  k_sap_residual<R><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, psi, r, L,
-                                                                          (R)kappa, psi_zero ? 1 : 0);
+  if (tinv)
+    k_sap_residual<R, 1><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, psi, r, L,
+                                                                               (R)kappa, psi_zero ? 1 : 0, tinv);
+  else
+    k_sap_residual<R, 0><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, psi, r, L,
+                                                                               (R)kappa, psi_zero ? 1 : 0, nullptr);
   ++*ex.launches;
 }
 
 template <typename R>
 void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* r,
-                      cx<R>* q, double* dots, int L, double kappa, int* nchunk_out) {
+                      cx<R>* q, double* dots, int L, double kappa, int* nchunk_out, const R* tinv) {
   const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
   const int nchunk = g.Vd / S;
   const int nslot = (g.nd / 2) * g.Vd;
   const size_t shm = dots ? sizeof(R) * 3 * S * L : 0;
-  k_sap_domain_apply<R><<<(unsigned)(nslot / S), dim3(L, S), shm, ex.stream>>>(g, colour, links, r, q, dots,
-                                                                               L, (R)kappa, nchunk);
+  if (tinv)
+    k_sap_domain_apply<R, 1><<<(unsigned)(nslot / S), dim3(L, S), shm, ex.stream>>>(g, colour, links, r, q, dots,
+                                                                                    L, (R)kappa, nchunk, tinv);
+  else
+    k_sap_domain_apply<R, 0><<<(unsigned)(nslot / S), dim3(L, S), shm, ex.stream>>>(g, colour, links, r, q, dots,
+                                                                                    L, (R)kappa, nchunk, nullptr);
   ++*ex.launches;
   if (nchunk_out) *nchunk_out = nchunk;
 }
 
+template <typename R>
+void ssor_level(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const R* tinv, const cx<R>* y,
+                cx<R>* z, int L, double komega, const int* local, int count, bool fwd) {
+  const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
+  const int n = (g.nd / 2) * count;
+  const unsigned grid = (unsigned)((n + S - 1) / S);
+  const dim3 block(L, S);
+  if (tinv) {
+    if (fwd) k_ssor_level<R, 1, true><<<grid, block, 0, ex.stream>>>(g, colour, links, tinv, y, z, L, (R)komega, local, count);
+    else k_ssor_level<R, 1, false><<<grid, block, 0, ex.stream>>>(g, colour, links, tinv, y, z, L, (R)komega, local, count);
+  } else {
+    if (fwd) k_ssor_level<R, 0, true><<<grid, block, 0, ex.stream>>>(g, colour, links, nullptr, y, z, L, (R)komega, local, count);
+    else k_ssor_level<R, 0, false><<<grid, block, 0, ex.stream>>>(g, colour, links, nullptr, y, z, L, (R)komega, local, count);
+  }
+  ++*ex.launches;
+}
+
 #define INST(R)                                                                                          \
-  template void dslash_full<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double); \
+  template void dslash_full<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double,  \
+                               const R*, int);                                                          \
   template void tune_dslash<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double); \
   template void sap_residual<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, const cx<R>*,   \
-                                cx<R>*, int, double, bool);                                               \
+                                cx<R>*, int, double, bool, const R*);                                     \
   template void sap_domain_apply<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, cx<R>*,     \
-                                    double*, int, double, int*);
+                                    double*, int, double, int*, const R*);                                \
+  template void ssor_level<R>(const Exec&, const Geom&, int, const cx<R>*, const R*, const cx<R>*, cx<R>*, \
+                              int, double, const int*, int, bool);
 INST(float)
 INST(double)
 #undef INST

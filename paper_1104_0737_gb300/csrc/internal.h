@@ -4,6 +4,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -88,9 +89,12 @@ struct Timed {
 // Wilson-Dirac operator (dslash.cu), Sec. 2.1
 // ---------------------------------------------------------------------------
 // out = in - kappa * H in on every site, L columns.
+// With clov != NULL: cm = 1 the Jacobi-preconditioned clover matrix
+// out = in - kappa T^{-1} H in (clov = T^{-1}), cm = 2 the clover matrix
+// out = in + kappa C in - kappa H in (clov = C); packed per site (herm_off).
 template <typename R>
 void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out,
-                 int L, double kappa);
+                 int L, double kappa, const R* clov = nullptr, int cm = 0);
 // Times the operator's launch configurations for this lattice, L and
 // precision once per process (in -> out, both overwritten-safe scratch for
 // out) and records the fastest for dslash_full; does nothing while the stream
@@ -100,6 +104,16 @@ void tune_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>*
                  double kappa);
 // the autotuner is on when MBICG_AUTOTUNE is set and not "0"
 bool autotune_enabled();
+
+// Clover term (clover.cu), Sec. 2.2: C = i c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}
+// per site from the FP64 links (packed, 72 doubles per site); for one kappa
+// T^{-1} = (1 + kappa C)^{-1} in FP64 and FP32 and C in FP32 (bit 0 of *status
+// set if a block is singular); out = M in for a packed M on an ABI-layout
+// FP64 block (in and out may alias).
+void clover_field(const Exec& ex, const Geom& g, const cx<double>* U64, double csw, double* C64);
+void clover_terms(const Exec& ex, long long nsite, const double* C64, double kappa, double* Ti64, float* Ti32,
+                  float* C32, int* status);
+void clover_abi(const Exec& ex, long long nsite, int L, const double* M, const cx<double>* in, cx<double>* out);
 
 // ABI blocks with dummy columns: the L columns of in into the first L of Lt
 // columns of out, the rest seeded Gaussian random numbers (random) or zeros;
@@ -124,22 +138,31 @@ void dslash_half(const Exec& ex, const Geom& g, const __half2* l16, const __half
 // SAP pieces on the sites of the domains of one colour (the slot numbering of
 // colour_slot_coords; arrays are full-lattice, in the internal layout).
 //   r = eta - (psi - kappa H psi)   (psi_zero: r = eta)
+//   (tinv != NULL: the Jacobi-preconditioned clover matrix, H -> T^{-1} H)
 template <typename R>
 void sap_residual(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* eta,
-                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero);
+                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero, const R* tinv = nullptr);
 //   q = r - kappa H_dom r  (hops leaving the domain dropped) and, if dots is
 //   not NULL, per-CTA partial sums of q^H r and q^H q for every column:
 //   dots[((k * nchunk) + chunk) * L + rhs] = {Re q^H r, Im q^H r, q^H q}
 template <typename R>
 void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* r,
-                      cx<R>* q, double* dots, int L, double kappa, int* nchunk_out);
+                      cx<R>* q, double* dots, int L, double kappa, int* nchunk_out, const R* tinv = nullptr);
 // One whole colour sweep (residual, nmr MR steps, psi += x) in one kernel,
-// the domain kept on chip by a thread-block cluster; FP32, MR modes 0 and 2,
-// domain shapes 8^4 and 4^4.  Returns false (nothing launched) otherwise.
+// the domain kept on chip by a thread-block cluster; FP32, MR modes 0 and 3,
+// domain shapes 8^4 and 4^4, with T^{-1} (tinv) for the Jacobi-preconditioned
+// clover matrix.  Returns false (nothing launched) otherwise.
 // table: the frozen step lengths of this (cycle, colour), [nmr][nd/2] complex.
 bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
                      cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode,
-                     const double* table);
+                     const double* table, const float* tinv = nullptr);
+// SSOR (Sec. 2.2): one wavefront level of z = (1 - omega L)^{-1} y (fwd) or
+// z = (1 - omega U)^{-1} y on every domain of one colour, L and U the forward
+// and backward hops inside a domain (times T^{-1} with tinv); komega =
+// kappa * omega; local[0..count) the local site indices of the level.
+template <typename R>
+void ssor_level(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const R* tinv, const cx<R>* y,
+                cx<R>* z, int L, double komega, const int* local, int count, bool fwd);
 // Number of sites per CTA the SAP kernels use for L columns (divides Vd).
 int sap_sites_per_cta(const Geom& g, int L, bool fp64);
 
@@ -157,7 +180,24 @@ struct SapWork {
   size_t dots_len = 0;
   int L = 0;
   bool fp64 = false;
+  // SSOR domain solves: the local site indices of a domain sorted by
+  // wavefront level lx + ly + lz + lt (device copy of level_host), level k at
+  // [level_off[k], level_off[k + 1]); four full-lattice scratch blocks
+  int* levels = nullptr;
+  std::vector<int> level_host, level_off;
+  void* ssor[4] = {nullptr, nullptr, nullptr, nullptr};
 };
+
+// The SAP domain solver (Sec. 2.2): nmr MR steps (the default) or SSOR with
+// N_SSOR = nssor and relaxation omega.
+struct SsorParams {
+  int nssor;
+  double omega;
+};
+// Fills w.level_host / w.level_off for the domain shape of g and copies the
+// level table to w.levels (device, Vd ints) on the stream; w must stay alive
+// until the copy has completed.
+cudaError_t sap_prepare_ssor(const Geom& g, SapWork& w, cudaStream_t stream);
 
 // psi = M_SAP eta.  eta and psi are full-lattice blocks in the internal
 // layout and in the SAP precision (R).  mr_mode: 0 per column, 1 shared by the
@@ -165,10 +205,12 @@ struct SapWork {
 // the shared sums where the domain's residual is nonzero; *unset is raised if
 // an entry stays unrecorded), 3 frozen replay.
 // table = complex [ncycle][2][nmr][nd/2] (modes 2, 3).
+// tinv != NULL: SAP for the Jacobi-preconditioned clover matrix.  ssor != NULL: SSOR domain solves
+// instead of MR (nmr, mr_mode, table and unset unused; w.levels and w.ssor set).
 template <typename R>
 void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* eta, cx<R>* psi,
                int L, double kappa, int ncycle, int nmr, int mr_mode, double* table, int* unset,
-               SapWork& w);
+               SapWork& w, const R* tinv = nullptr, const SsorParams* ssor = nullptr);
 
 // ---------------------------------------------------------------------------
 // Block linear algebra (blas.cu)

@@ -240,7 +240,8 @@ def _patched_common(csrc):
     return common
 
 
-LIBRARY_SOURCES = ["api.cu", "dslash.cu", "sap.cu", "blas.cu", "half.cu", "serve.cu", "noalloc.cu", "selftest.cu", "tune.cu"]
+LIBRARY_SOURCES = ["api.cu", "dslash.cu", "sap.cu", "blas.cu", "half.cu", "serve.cu", "noalloc.cu", "selftest.cu", "tune.cu",
+                   "clover.cu"]
 
 
 def library_unit(name, csrc=CSRC):

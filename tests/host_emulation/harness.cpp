@@ -1,4 +1,4 @@
-// Host emulation of the library's FP64 operator and SAP kernels: every kernel
+// Host emulation of the library's FP64 operator, SAP and clover kernels: every kernel
 // body runs once per emulated (block, thread) in order.  device_parts.inc is
 // cut out of the CUDA sources by the test (kernels and device helpers, no
 // launches).
@@ -48,12 +48,14 @@ using C = cx<double>;
 
 extern "C" {
 // the operator with the launch shape of the library: CTAs of S sites, walked
-// in time slabs where the library uses them
-void emu_dslash(const int* dims, const double* U, const double* in, double* out, int L, double kappa, int S,
-                int order) {
+// in time slabs where the library uses them; cm: 0 Wilson, 1 Jacobi-
+// preconditioned clover (clov = T^{-1}), 2 clover (clov = C)
+void emu_dslash(const int* dims, const double* U, const double* in, double* out, int L, double kappa,
+                const double* clov, int cm, int S, int order) {
   const Geom g = make_geom(dims, nullptr);
   const int slice = g.d[0] * g.d[1] * g.d[2];
   const bool slabs = order == 1 && slice % S == 0 && g.d[3] % 8 == 0;
+  const int ws = slabs ? slice / S : 0, tt = slabs ? 8 : 1;
   const int nblk = (g.V + S - 1) / S;
   blockDim = {(unsigned)L, (unsigned)S, 1};
   gridDim = {(unsigned)nblk, 1, 1};
@@ -62,9 +64,30 @@ void emu_dslash(const int* dims, const double* U, const double* in, double* out,
       for (int r = 0; r < L; ++r) {
         blockIdx = {(unsigned)b, 0, 0};
         threadIdx = {(unsigned)r, (unsigned)y, 0};
-        emu_dslash::k_dslash_full<double>(g, (const C*)U, (const C*)in, (C*)out, L, kappa, slabs ? slice / S : 0,
-                                          slabs ? 8 : 1);
+        if (cm == 1)
+          emu_dslash::k_dslash_full<double, 1>(g, (const C*)U, (const C*)in, (C*)out, L, kappa, clov, ws, tt);
+        else if (cm == 2)
+          emu_dslash::k_dslash_full<double, 2>(g, (const C*)U, (const C*)in, (C*)out, L, kappa, clov, ws, tt);
+        else
+          emu_dslash::k_dslash_full<double, 0>(g, (const C*)U, (const C*)in, (C*)out, L, kappa, nullptr, ws, tt);
       }
+}
+void emu_clover_field(const int* dims, const double* U, double csw, double* Cl) {
+  const Geom g = make_geom(dims, nullptr);
+  grid(1, 1, [&] { emu_clover::k_clover_field(g, (const C*)U, csw, Cl); });  // grid-stride loop over sites
+}
+int emu_clover_terms(long long nsite, const double* Cl, double kappa, double* Ti64, float* Ti32, float* C32) {
+  int status = 0;
+  grid(1, 1, [&] { emu_clover::k_clover_terms(2 * nsite, Cl, kappa, Ti64, Ti32, C32, &status); });
+  return status;
+}
+void emu_clover_abi(long long nsite, int L, const double* M, const double* in, double* out) {
+  blockDim = {256, 1, 1};
+  for (long long idx = 0; idx < nsite * L; ++idx) {
+    blockIdx = {(unsigned)(idx / 256), 0, 0};
+    threadIdx = {(unsigned)(idx % 256), 0, 0};
+    emu_clover::k_clover_abi(nsite, L, M, (const C*)in, (C*)out);
+  }
 }
 int emu_segment_of(int b, int wslice, int tt) { return emu_dslash::segment_of(b, wslice, tt); }
 int emu_nslot(const int* dims, const int* block) {
@@ -78,19 +101,53 @@ void emu_slot(const int* dims, const int* block, int colour, int slot, int* site
   *site = site_index(g, c);
 }
 void emu_sap_residual(const int* dims, const int* block, const double* U, int colour, const double* eta,
-                      const double* psi, double* r, int L, double kappa, int psi_zero) {
+                      const double* psi, double* r, int L, double kappa, int psi_zero, const double* tinv) {
   const Geom g = make_geom(dims, block);
   grid((g.nd / 2) * g.Vd, L, [&] {
-    emu_dslash::k_sap_residual<double>(g, colour, (const C*)U, (const C*)eta, (const C*)psi, (C*)r, L, kappa,
-                                       psi_zero);
+    if (tinv)
+      emu_dslash::k_sap_residual<double, 1>(g, colour, (const C*)U, (const C*)eta, (const C*)psi, (C*)r, L, kappa,
+                                            psi_zero, tinv);
+    else
+      emu_dslash::k_sap_residual<double, 0>(g, colour, (const C*)U, (const C*)eta, (const C*)psi, (C*)r, L, kappa,
+                                            psi_zero, nullptr);
   });
 }
 void emu_sap_domain_apply(const int* dims, const int* block, const double* U, int colour, const double* r,
-                          double* q, int L, double kappa) {
+                          double* q, int L, double kappa, const double* tinv) {
   const Geom g = make_geom(dims, block);
   grid((g.nd / 2) * g.Vd, L, [&] {
-    emu_dslash::k_sap_domain_apply<double>(g, colour, (const C*)U, (const C*)r, (C*)q, nullptr, L, kappa, 1);
+    if (tinv)
+      emu_dslash::k_sap_domain_apply<double, 1>(g, colour, (const C*)U, (const C*)r, (C*)q, nullptr, L, kappa, 1,
+                                                tinv);
+    else
+      emu_dslash::k_sap_domain_apply<double, 0>(g, colour, (const C*)U, (const C*)r, (C*)q, nullptr, L, kappa, 1,
+                                                nullptr);
   });
+}
+void emu_ssor_level(const int* dims, const int* block, const double* U, const double* tinv, int colour,
+                    const double* y, double* z, int L, double komega, const int* local, int count, int fwd) {
+  const Geom g = make_geom(dims, block);
+  grid((g.nd / 2) * count, L, [&] {
+    const C* U_ = (const C*)U;
+    if (tinv) {
+      if (fwd) emu_dslash::k_ssor_level<double, 1, true>(g, colour, U_, tinv, (const C*)y, (C*)z, L, komega, local, count);
+      else emu_dslash::k_ssor_level<double, 1, false>(g, colour, U_, tinv, (const C*)y, (C*)z, L, komega, local, count);
+    } else {
+      if (fwd) emu_dslash::k_ssor_level<double, 0, true>(g, colour, U_, nullptr, (const C*)y, (C*)z, L, komega, local, count);
+      else emu_dslash::k_ssor_level<double, 0, false>(g, colour, U_, nullptr, (const C*)y, (C*)z, L, komega, local, count);
+    }
+  });
+}
+void emu_ssor_combine(const int* dims, const int* block, int colour, const double* pv, const double* qv,
+                      const double* pqv, double* term, double* acc, int L, double omega) {
+  const Geom g = make_geom(dims, block);
+  grid((g.nd / 2) * g.Vd, L, [&] {
+    emu_sap::k_ssor_combine<double>(g, colour, (const C*)pv, (const C*)qv, (const C*)pqv, (C*)term, (C*)acc, L, omega);
+  });
+}
+void emu_colour_add(const int* dims, const int* block, int colour, const double* x, double* psi, int L) {
+  const Geom g = make_geom(dims, block);
+  grid((g.nd / 2) * g.Vd, L, [&] { emu_sap::k_colour_add<double>(g, colour, (const C*)x, (C*)psi, L); });
 }
 // ABI blocks -> FP16 storage -> the FP16 operator -> ABI, with the link rows
 // rounded to FP16 as the library stores them

@@ -125,6 +125,25 @@ def main(so, sanitizer):
     small.solve(2, b2, prec_D=mb.MBICG_FP64)
     X = small.solve(3, b2, prec_D=mb.MBICG_FP32, dummy_rhs=2, dummy_seed=5)
     small.solve(3, b2, X=X, use_x0=1)
+    # SSOR domain solves, the clover term and its Jacobi preconditioning (Sec. 2.2)
+    for prec in (mb.MBICG_FP64, mb.MBICG_FP32):
+        small.sap(3, b2, ncycle=1, prec_sap=prec, domain_solver=1, nssor=2)
+    lib.mbicg_load_clover.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    lib.mbicg_apply_clover.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    small.ok(lib.mbicg_load_clover(small.c, 1.3), "load_clover")
+    psi = synth.gaussian_source(small.dims, 3, seed=40)
+    out = np.empty_like(psi)
+    for prec in (mb.MBICG_FP64, mb.MBICG_FP32):
+        for jacobi in (0, 1):
+            small.ok(lib.mbicg_apply_clover(small.c, _v(psi), _v(out), 3, KAPPA, prec, jacobi),
+                     f"apply_clover prec={prec} jacobi={jacobi}")
+            assert np.isfinite(out).all()
+    for solver in (0, 1):
+        for prec in (mb.MBICG_FP64, mb.MBICG_FP32):
+            small.sap(3, b2, ncycle=1, nmr=2, mr_mode=mb.MBICG_MR_COLUMN, prec_sap=prec, clover=1,
+                      domain_solver=solver)
+        small.solve(2, b2, clover=1, domain_solver=solver)
     small.close()
 
     # every launch configuration of the operator the autotuner times (CTA

@@ -37,12 +37,13 @@ def test_ctypes_structs_match_c_layout(tmp_path):
 #include <stdio.h>
 #include "mbicg.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mbicg_params), offsetof(mbicg_params, delta_ru),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mbicg_params), offsetof(mbicg_params, delta_ru),
          offsetof(mbicg_params, res_history), offsetof(mbicg_params, res_history_len),
          sizeof(mbicg_stats), offsetof(mbicg_stats, true_res_max),
          sizeof(mbicg_request_info), offsetof(mbicg_request_info, batch_columns),
          offsetof(mbicg_stats, graph_iterations), offsetof(mbicg_stats, precision_fallbacks),
-         offsetof(mbicg_params, dummy_rhs), offsetof(mbicg_params, dummy_seed));
+         offsetof(mbicg_params, dummy_rhs), offsetof(mbicg_params, dummy_seed), offsetof(mbicg_params, clover),
+         offsetof(mbicg_params, domain_solver), offsetof(mbicg_params, nssor), offsetof(mbicg_params, ssor_omega));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -54,7 +55,8 @@ int main(void) {
             ctypes.sizeof(mb.mbicg_stats), mb.mbicg_stats.true_res_max.offset,
             ctypes.sizeof(mb.mbicg_request_info), mb.mbicg_request_info.batch_columns.offset,
             mb.mbicg_stats.graph_iterations.offset, mb.mbicg_stats.precision_fallbacks.offset,
-            mb.mbicg_params.dummy_rhs.offset, mb.mbicg_params.dummy_seed.offset]
+            mb.mbicg_params.dummy_rhs.offset, mb.mbicg_params.dummy_seed.offset, mb.mbicg_params.clover.offset,
+            mb.mbicg_params.domain_solver.offset, mb.mbicg_params.nssor.offset, mb.mbicg_params.ssor_omega.offset]
     assert got == want
 
 
@@ -63,6 +65,8 @@ def test_default_params():
     assert (p.ncycle, p.nmr, list(p.block)) == (4, 4, [4, 4, 4, 4])
     assert p.mr_mode == mb.MBICG_MR_FROZEN and p.prec_D == mb.MBICG_FP32
     assert p.prec_sap == mb.MBICG_FP32 and p.max_iter == 1000 and p.delta_ru == 0.1
+    assert p.clover == 0
+    assert (p.domain_solver, p.nssor, p.ssor_omega) == (mb.MBICG_DOMAIN_MR, 1, 1.26)
     q = mb.mbicg_default_params(block=(2, 2, 2, 2), ncycle=1)
     assert list(q.block) == [2, 2, 2, 2] and q.ncycle == 1
 

@@ -1,7 +1,7 @@
 """The CUDA path's own FP64 kernels, compiled for the host and run once per
-emulated thread, against the oracle: the operator (Sec. 2.1) and the SAP
+emulated thread, against the oracle: the operator (Sec. 2.1), the SAP
 pieces (Sec. 2.2: the colour residual, the Dirichlet domain operator and the
-MR update).  This checks the kernels' arithmetic and index maps on a machine
+MR update) and the clover term with its Jacobi preconditioning (Sec. 2.2).  This checks the kernels' arithmetic and index maps on a machine
 without a GPU; the launch configurations, the FP32 and fused kernels and the
 device memory handling are covered by the -m gpu tests.
 
@@ -27,6 +27,7 @@ CUDA_INCLUDE = "/usr/local/cuda/include"
 PARTS = [
     ("emu_dslash", "dslash.cu", "namespace {", emulation_sources.DSLASH_SEQ_END),
     ("emu_sap", "sap.cu", "namespace {", "}  // namespace\n"),
+    ("emu_clover", "clover.cu", "namespace {", "}  // namespace\n"),
     ("emu_half", "half.cu", "namespace {", "}  // namespace\n"),
 ]
 
@@ -52,19 +53,28 @@ def emu(tmp_path_factory):
                     os.path.join(HERE, "harness.cpp"), "-o", str(lib_path)], check=True)
     lib = ctypes.CDLL(str(lib_path))
     D, I = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
-    lib.emu_dslash.argtypes = [I, D, D, D, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    F = ctypes.POINTER(ctypes.c_float)
+    lib.emu_dslash.argtypes = [I, D, D, D, ctypes.c_int, ctypes.c_double, D, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.emu_segment_of.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.emu_clover_field.argtypes = [I, D, ctypes.c_double, D]
+    lib.emu_clover_terms.argtypes = [ctypes.c_longlong, D, ctypes.c_double, D, F, F]
+    lib.emu_clover_abi.argtypes = [ctypes.c_longlong, ctypes.c_int, D, D, D]
     lib.emu_nslot.argtypes = [I, I]
     lib.emu_slot.argtypes = [I, I, ctypes.c_int, ctypes.c_int, I, I]
-    lib.emu_sap_residual.argtypes = [I, I, D, ctypes.c_int, D, D, D, ctypes.c_int, ctypes.c_double, ctypes.c_int]
-    lib.emu_sap_domain_apply.argtypes = [I, I, D, ctypes.c_int, D, D, ctypes.c_int, ctypes.c_double]
+    lib.emu_sap_residual.argtypes = [I, I, D, ctypes.c_int, D, D, D, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                     D]
+    lib.emu_sap_domain_apply.argtypes = [I, I, D, ctypes.c_int, D, D, ctypes.c_int, ctypes.c_double, D]
+    lib.emu_ssor_level.argtypes = [I, I, D, D, ctypes.c_int, D, D, ctypes.c_int, ctypes.c_double, I, ctypes.c_int,
+                                   ctypes.c_int]
+    lib.emu_ssor_combine.argtypes = [I, I, ctypes.c_int, D, D, D, D, D, ctypes.c_int, ctypes.c_double]
+    lib.emu_colour_add.argtypes = [I, I, ctypes.c_int, D, D, ctypes.c_int]
     lib.emu_half_operator.argtypes = [I, D, D, D, ctypes.c_int, ctypes.c_double]
     lib.emu_mr_update.argtypes = [I, I, ctypes.c_int, D, D, D, D, D, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     return lib
 
 
 def _dp(a):
-    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
 
 
 def _iv(v):
@@ -90,7 +100,7 @@ def test_operator_kernel_matches_oracle(emu, oracle_mod, dims, L, S):
     kappa = 0.1375
     a = _internal(psi)
     out = np.full_like(a, np.nan)
-    emu.emu_dslash(_iv(dims), _dp(U), _dp(a), _dp(out), L, kappa, S, 1)
+    emu.emu_dslash(_iv(dims), _dp(U), _dp(a), _dp(out), L, kappa, None, 0, S, 1)
     ref = oracle_mod.apply_D(dims, U, kappa, psi)
     assert np.max(np.abs(_oracle_layout(out) - ref)) < 1e-14 * np.max(np.abs(ref))
 
@@ -105,7 +115,7 @@ def test_operator_launch_configurations_are_bit_identical(emu, oracle_mod):
     for S in (32, 16, 8):
         for order in (0, 1):
             out = np.full_like(a, np.nan)
-            emu.emu_dslash(_iv(dims), _dp(U), _dp(a), _dp(out), L, 0.13, S, order)
+            emu.emu_dslash(_iv(dims), _dp(U), _dp(a), _dp(out), L, 0.13, None, 0, S, order)
             outs.append(out)
     assert all(np.array_equal(o, outs[0]) for o in outs[1:])
     ref = oracle_mod.apply_D(dims, U, 0.13, _oracle_layout(a))
@@ -152,7 +162,7 @@ def test_slot_map_covers_each_colour_once(emu, dims, block):
         assert np.array_equal(ks, np.repeat(np.arange(len(sl) // Vd), Vd))
 
 
-def _sap(emu, dims, block, U, kappa, eta, ncycle, nmr, mode):
+def _sap(emu, dims, block, U, kappa, eta, ncycle, nmr, mode, tinv=None):
     """psi = M_SAP eta with the emulated kernels, launched in the order of the
     library's multi-kernel SAP driver; the step lengths are formed here from
     the emulated q and r (per column, or shared by the columns)."""
@@ -164,9 +174,9 @@ def _sap(emu, dims, block, U, kappa, eta, ncycle, nmr, mode):
         for colour in (0, 1):
             sl = _slots(emu, dims, block, colour)
             emu.emu_sap_residual(_iv(dims), _iv(block), _dp(U), colour, _dp(e), _dp(psi), _dp(r), L, kappa,
-                                 int(cyc == 0 and colour == 0))
+                                 int(cyc == 0 and colour == 0), _dp(tinv))
             for it in range(nmr):
-                emu.emu_sap_domain_apply(_iv(dims), _iv(block), _dp(U), colour, _dp(r), _dp(q), L, kappa)
+                emu.emu_sap_domain_apply(_iv(dims), _iv(block), _dp(U), colour, _dp(r), _dp(q), L, kappa, _dp(tinv))
                 num = np.zeros((ndc, L), complex)
                 den = np.zeros((ndc, L))
                 for s, k in sl:
@@ -193,6 +203,160 @@ def test_sap_kernels_match_oracle(emu, oracle_mod, mode):
 
 
 # ---------------------------------------------------------------------------
+# clover term and Jacobi preconditioning
+# ---------------------------------------------------------------------------
+def _herm_off(i, j):
+    return 6 + 2 * (i * 6 - i * (i + 1) // 2 + (j - i - 1))
+
+
+def _unpack(P):
+    """Packed per-site Hermitian chirality blocks (72 reals) -> (V, 12, 12)."""
+    V = P.shape[0]
+    M = np.zeros((V, 12, 12), complex)
+    for b in range(2):
+        blk = P[:, 36 * b:36 * b + 36].astype(np.float64)
+        for i in range(6):
+            M[:, 6 * b + i, 6 * b + i] = blk[:, i]
+            for j in range(i + 1, 6):
+                o = _herm_off(i, j)
+                v = blk[:, o] + 1j * blk[:, o + 1]
+                M[:, 6 * b + i, 6 * b + j] = v
+                M[:, 6 * b + j, 6 * b + i] = np.conj(v)
+    return M
+
+
+@pytest.fixture(scope="module")
+def clover_case(emu, oracle_mod):
+    dims, kappa, csw = (4, 4, 2, 4), 0.13, 1.3
+    V = int(np.prod(dims))
+    U = np.ascontiguousarray(synth.su3_links(dims, 0.5, seed=95))
+    C = np.zeros((V, 72))
+    emu.emu_clover_field(_iv(dims), _dp(U), csw, _dp(C))
+    Ti64 = np.zeros((V, 72))
+    Ti32 = np.zeros((V, 72), np.float32)
+    C32 = np.zeros((V, 72), np.float32)
+    st = emu.emu_clover_terms(V, _dp(C), kappa, _dp(Ti64), Ti32.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                              C32.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    T = oracle_mod.clover(dims, U, kappa, csw)
+    return dict(dims=dims, kappa=kappa, V=V, U=U, C=C, Ti64=Ti64, Ti32=Ti32, C32=C32, status=st, T=T,
+                Ti=oracle_mod.clover_inverse(T))
+
+
+def test_clover_field_and_inverse_kernels(clover_case):
+    c = clover_case
+    assert c["status"] == 0
+    assert np.max(np.abs(np.eye(12) + c["kappa"] * _unpack(c["C"]) - c["T"])) < 1e-15
+    assert np.max(np.abs(_unpack(c["Ti64"]) - c["Ti"])) < 1e-14
+    assert np.max(np.abs(_unpack(c["Ti32"]) - c["Ti"])) < 1e-6
+    assert np.max(np.abs(c["C32"] - c["C"])) < 1e-6 * np.max(np.abs(c["C"]))
+
+
+def test_clover_operator_kernels(emu, oracle_mod, clover_case):
+    c = clover_case
+    dims, kappa, V, U = c["dims"], c["kappa"], c["V"], c["U"]
+    psi = synth.gaussian_source(dims, 3, seed=96)
+    a = _internal(psi)
+    out = np.zeros_like(a)
+    emu.emu_dslash(_iv(dims), _dp(U), _dp(a), _dp(out), 3, kappa, _dp(c["Ti64"]), 1, 32, 0)
+    ref = oracle_mod.apply_A(dims, U, kappa, c["Ti"], psi)
+    assert np.max(np.abs(_oracle_layout(out) - ref)) < 1e-14 * np.max(np.abs(ref))
+    emu.emu_dslash(_iv(dims), _dp(U), _dp(a), _dp(out), 3, kappa, _dp(c["C"]), 2, 32, 0)
+    ref = oracle_mod.apply_clover_D(dims, U, kappa, c["T"], psi)
+    assert np.max(np.abs(_oracle_layout(out) - ref)) < 1e-14 * np.max(np.abs(ref))
+    # T^{-1} on an ABI-layout block (the right-hand side of the solve)
+    o2 = np.zeros_like(psi)
+    emu.emu_clover_abi(V, 3, _dp(c["Ti64"]), _dp(psi), _dp(o2))
+    ref = np.einsum("vrc,vci->vri", c["Ti"], psi.reshape(V, 12, 3)).reshape(psi.shape)
+    assert np.max(np.abs(o2 - ref)) < 1e-14 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_clover_sap_kernels(emu, oracle_mod, clover_case, mode):
+    c = clover_case
+    block = (2, 2, 1, 2)
+    eta = synth.gaussian_source(c["dims"], 2, seed=97)
+    got = _sap(emu, c["dims"], block, c["U"], c["kappa"], eta, 2, 3, mode, tinv=c["Ti64"])
+    ref = oracle_mod.sap_ext(c["dims"], block, c["U"], c["kappa"], 2, eta, Tinv=c["Ti"],
+                             solver=oracle_mod.DOMAIN_MR, nmr=3, mr_mode=mode)
+    assert np.max(np.abs(got - ref)) < 1e-14 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------------------
+# SSOR domain solves
+# ---------------------------------------------------------------------------
+def _levels(block):
+    """Local site indices of a domain (x fastest) grouped by lx + ly + lz + lt."""
+    bx, by, bz, bt = block
+    n = bx * by * bz * bt
+    lev = [[] for _ in range(bx + by + bz + bt - 3)]
+    for l in range(n):
+        x, y, z, t = l % bx, (l // bx) % by, (l // (bx * by)) % bz, l // (bx * by * bz)
+        lev[x + y + z + t].append(l)
+    return [np.array(v, dtype=np.int32) for v in lev]
+
+
+def _ssor_colour(emu, dims, block, U, tinv, colour, y, kappa, nssor, omega):
+    """B y on the domains of one colour with the emulated kernels, launched in
+    the order of the library's SSOR driver."""
+    L = y.shape[1]
+    lev = _levels(block)
+    acc, term, qv, pv, pqv, out = (np.zeros_like(y) for _ in range(6))
+
+    def substitute(fwd, src, dst):
+        for k in (range(len(lev) - 1, -1, -1) if fwd else range(len(lev))):
+            loc = lev[k]
+            emu.emu_ssor_level(_iv(dims), _iv(block), _dp(U), _dp(tinv), colour, _dp(src), _dp(dst), L,
+                               kappa * omega, loc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(loc), int(fwd))
+
+    substitute(True, y, acc)
+    term[...] = acc
+    for _ in range(nssor):
+        substitute(False, term, qv)
+        substitute(True, term, pv)
+        substitute(True, qv, pqv)
+        emu.emu_ssor_combine(_iv(dims), _iv(block), colour, _dp(pv), _dp(qv), _dp(pqv), _dp(term), _dp(acc), L,
+                             omega)
+    substitute(False, acc, out)
+    return out
+
+
+@pytest.mark.parametrize("clover", [False, True])
+@pytest.mark.parametrize("nssor,omega", [(0, 1.0), (1, 1.26), (2, 0.9)])
+def test_ssor_domain_kernels(emu, oracle_mod, clover_case, clover, nssor, omega):
+    c = clover_case
+    dims, block = c["dims"], (2, 2, 1, 2)
+    tinv = c["Ti64"] if clover else None
+    y = synth.gaussian_source(dims, 2, seed=98)
+    col = domain_colour(dims, block)
+    for colour in (0, 1):
+        got = _oracle_layout(_ssor_colour(emu, dims, block, c["U"], tinv, colour, _internal(y), c["kappa"],
+                                          nssor, omega))
+        ref = oracle_mod.ssor_domains(dims, block, c["U"], c["kappa"], nssor, omega, colour, y,
+                                      Tinv=c["Ti"] if clover else None)
+        on = col == colour
+        assert np.max(np.abs(got[on] - ref[on])) < 1e-14 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("clover", [False, True])
+def test_ssor_sap_kernels(emu, oracle_mod, clover_case, clover):
+    """M_SAP with SSOR domain solves: per colour the residual kernel, the SSOR
+    solve and psi += x, in the order of the library's driver."""
+    c = clover_case
+    dims, block, kappa = c["dims"], (2, 2, 1, 2), c["kappa"]
+    tinv = c["Ti64"] if clover else None
+    eta = synth.gaussian_source(dims, 2, seed=99)
+    e = _internal(eta)
+    psi, r = np.zeros_like(e), np.zeros_like(e)
+    L = e.shape[1]
+    for cyc in range(2):
+        for colour in (0, 1):
+            emu.emu_sap_residual(_iv(dims), _iv(block), _dp(c["U"]), colour, _dp(e), _dp(psi), _dp(r), L, kappa,
+                                 int(cyc == 0 and colour == 0), _dp(tinv))
+            x = _ssor_colour(emu, dims, block, c["U"], tinv, colour, r, kappa, 1, 1.26)
+            emu.emu_colour_add(_iv(dims), _iv(block), colour, _dp(x), _dp(psi), L)
+    ref = oracle_mod.sap_ext(dims, block, c["U"], kappa, 2, eta, Tinv=c["Ti"] if clover else None,
+                             solver=oracle_mod.DOMAIN_SSOR, nssor=1, omega=1.26)
+    assert np.max(np.abs(_oracle_layout(psi) - ref)) < 1e-14 * np.max(np.abs(ref))
 # FP16 storage (half.cu)
 # ---------------------------------------------------------------------------
 def _comps(a):

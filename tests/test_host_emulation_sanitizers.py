@@ -19,10 +19,12 @@ The exercise runs the operator in FP64, FP32 and FP16 (and the
 allocation-free one on emulated device buffers), SAP with the fused
 cluster sweep and the multi-kernel path (per-column and block MR, FP64 and
 FP32), block solves with dummy columns and an initial guess, every launch
-configuration of the operator that the autotuner times, the request server
-(two solver slots on host threads, four clients submitting and waiting from
-host threads at once), and the 8-CTA cluster sweep alone and
-(AddressSanitizer) in a block solve on an 8^4 lattice.  Mistakes
+configuration of the operator that the autotuner times, SSOR domain solves,
+the clover term and its Jacobi preconditioning (operators, SAP with MR and
+SSOR, block solves of D_c X = B), the request server (two solver slots on
+host threads, four clients submitting and waiting from host threads at
+once), and the 8-CTA cluster sweep alone and (AddressSanitizer) in a block
+solve on an 8^4 lattice.  Mistakes
 planted in a copy of the sources were each reported: an off-by-one write and
 a misaligned float4 load in a layout kernel, and a removed barrier before a
 block reduction (a data race)."""

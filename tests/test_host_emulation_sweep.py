@@ -39,7 +39,7 @@ def sweep(tmp_path_factory):
     lib = ctypes.CDLL(str(lib_path))
     F, D, I = (ctypes.POINTER(t) for t in (ctypes.c_float, ctypes.c_double, ctypes.c_int))
     lib.emu_sweep.argtypes = [I, I, ctypes.c_int, F, F, F, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int,
-                              ctypes.c_int, D, ctypes.c_int]
+                              ctypes.c_int, D, ctypes.c_int, F]
     return lib
 
 
@@ -59,7 +59,7 @@ def _oracle_layout(a):
     return np.ascontiguousarray(a.transpose(0, 2, 1)).reshape(a.shape[0], 4, 3, -1).astype(np.complex128)
 
 
-def _sap_emulated(lib, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nclusters):
+def _sap_emulated(lib, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nclusters, tinv=None):
     """ncycle cycles of E and O sweeps, as the library's driver launches them;
     mode 3 replays the step lengths omegas[it] on every domain."""
     L = eta.shape[3]
@@ -76,7 +76,8 @@ def _sap_emulated(lib, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nc
     for cyc in range(ncycle):
         for colour in (0, 1):
             rc = lib.emu_sweep(_iv(dims), _iv(block), colour, _fp(links), _fp(e), _fp(psi), L, kappa,
-                               int(cyc == 0 and colour == 0), nmr, mode, tp, nclusters)
+                               int(cyc == 0 and colour == 0), nmr, mode, tp, nclusters,
+                               _fp(tinv) if tinv is not None else None)
             assert rc == 0
     return _oracle_layout(psi)
 
@@ -109,4 +110,45 @@ def test_fused_sweep_matches_oracle(sweep, oracle_mod, dims, block, L, ncycle, n
         table = np.ascontiguousarray(np.broadcast_to(omegas[None, None, :, None], (ncycle, 2, nmr, nd)))
         ref = oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, eta, mr_mode=oracle_mod.MR_FROZEN,
                              omega_table=table.copy())
+    assert _rel_site(got, ref) < 1e-5
+
+
+def _pack_herm(M):
+    """(V, 12, 12) Hermitian, block diagonal in chirality -> the library's packed
+    FP32 form: per block 6 real diagonal entries, then the entries above the
+    diagonal row by row as (re, im)."""
+    V = M.shape[0]
+    P = np.zeros((V, 72), np.float32)
+    for b in range(2):
+        o = 36 * b
+        for i in range(6):
+            P[:, o + i] = M[:, 6 * b + i, 6 * b + i].real
+        k = 6
+        for i in range(6):
+            for j in range(i + 1, 6):
+                P[:, o + k] = M[:, 6 * b + i, 6 * b + j].real
+                P[:, o + k + 1] = M[:, 6 * b + i, 6 * b + j].imag
+                k += 2
+    return np.ascontiguousarray(P)
+
+
+@pytest.mark.parametrize("dims,block,L,ncycle,nmr,nclusters", CASES)
+@pytest.mark.parametrize("mode", [0, 3])
+def test_fused_sweep_with_clover_matches_oracle(sweep, oracle_mod, dims, block, L, ncycle, nmr, nclusters, mode):
+    """The Jacobi-preconditioned clover matrix A = T^{-1} D_c in the sweep."""
+    U = synth.su3_links(dims, 0.5, seed=73)
+    eta = synth.gaussian_source(dims, L, seed=74)
+    kappa = 0.125
+    Ti = oracle_mod.clover_inverse(oracle_mod.clover(dims, U, kappa, 1.3))
+    omegas = np.array([0.9 + 0.05j, 1.1 - 0.02j, 0.95 + 0.01j])[:nmr]
+    got = _sap_emulated(sweep, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nclusters, tinv=_pack_herm(Ti))
+    assert not np.isnan(got).any()
+    if mode == 0:
+        ref = oracle_mod.sap_ext(dims, block, U, kappa, ncycle, eta, Tinv=Ti, solver=oracle_mod.DOMAIN_MR, nmr=nmr,
+                                 mr_mode=oracle_mod.MR_COLUMN)
+    else:
+        nd = int(np.prod(dims)) // int(np.prod(block))
+        table = np.ascontiguousarray(np.broadcast_to(omegas[None, None, :, None], (ncycle, 2, nmr, nd)))
+        ref = oracle_mod.sap_ext(dims, block, U, kappa, ncycle, eta, Tinv=Ti, solver=oracle_mod.DOMAIN_MR, nmr=nmr,
+                                 mr_mode=oracle_mod.MR_FROZEN, omega_table=table.copy())
     assert _rel_site(got, ref) < 1e-5
