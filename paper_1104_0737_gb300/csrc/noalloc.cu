@@ -1,13 +1,13 @@
 // noalloc.cu — an operator entry point that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA stream is
-// being captured into a graph (an allocation is not a capturable operation),
-// code inside a framework's memory pool that must not grow device memory
-// behind the pool's back, and real-time loops that may not take the
-// allocator's locks.  mbicg_apply_D_noalloc serves them: it computes the same
-// FP32 Wilson-Dirac operator as mbicg_apply_D(..., MBICG_FP32) with the caller's
-// device buffers and a fixed scratch area that is a file-scope __device__
-// array, so it needs no context, no cudaMalloc and no cudaFree.
+// Some callers cannot call cudaMalloc: code that runs inside a framework's
+// memory pool and must not grow device memory behind the pool's back,
+// real-time or latency-bound loops that may not take the allocator's locks or
+// wait for it, and programs whose device memory is fixed when they start.
+// mbicg_apply_D_noalloc serves them: it computes the same FP32 Wilson-Dirac
+// operator as mbicg_apply_D(..., MBICG_FP32) with the caller's device buffers
+// and a fixed scratch area that is a file-scope __device__ array, so it needs
+// no context, no cudaMalloc and no cudaFree.
 //
 // The scratch array exists once per device in every process that loads the
 // library and is held until the process exits.  Every call shares it and it
@@ -52,13 +52,16 @@ cudaError_t scratch_address(int device, void** out) {
   return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// p is device memory (or managed memory) of `device`: the kernels below
+// dereference the caller's pointers directly, so memory of another device or
+// of the host is refused.
+bool on_device(const void* p, int device) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
+    cudaGetLastError();  // no error was pending on entry: this one is ours
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == device;
 }
 
 // scratch bytes for V sites and L columns: FP32 links and two FP32 blocks
@@ -80,9 +83,12 @@ extern "C" int mbicg_apply_D_noalloc(const int dims[4], const double* U, const d
   }
   if (L < 1 || L > MAXL || V > (1ll << 27)) return MBICG_EINVAL;
   if (scratch_bytes(V, L) > NOALLOC_SCRATCH_BYTES) return MBICG_EINVAL;
-  if (!on_device(U) || !on_device(in) || !on_device(out)) return MBICG_EINVAL;
+  // an error left pending by earlier work of the caller is not this call's:
+  // report it without launching (and without clearing it)
+  if (cudaPeekAtLastError() != cudaSuccess) return MBICG_ECUDA;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= MAX_DEVICES) return MBICG_ECUDA;
+  if (!on_device(U, device) || !on_device(in, device) || !on_device(out, device)) return MBICG_EINVAL;
   void* base = nullptr;
   if (scratch_address(device, &base) != cudaSuccess) {
     cudaGetLastError();
@@ -108,9 +114,13 @@ extern "C" int mbicg_apply_D_noalloc(const int dims[4], const double* U, const d
   geom_init_divisors(g);
   long long launches = 0;
   const Exec ex{static_cast<cudaStream_t>(cuda_stream), &launches, nullptr};
+  // each launch checked by itself, so the status reflects this call's launches only
   convert_block<double, float>(ex, V * 36, reinterpret_cast<const cx<double>*>(U), U32);
+  if (cudaGetLastError() != cudaSuccess) return MBICG_ECUDA;
   abi_to_internal<float>(ex, V, L, reinterpret_cast<const cx<double>*>(in), a);
+  if (cudaGetLastError() != cudaSuccess) return MBICG_ECUDA;
   dslash_full<float>(ex, g, U32, a, b, L, kappa);
+  if (cudaGetLastError() != cudaSuccess) return MBICG_ECUDA;
   internal_to_abi<float>(ex, V, L, b, reinterpret_cast<cx<double>*>(out));
   if (cudaGetLastError() != cudaSuccess) return MBICG_ECUDA;
   return MBICG_OK;
