@@ -122,12 +122,21 @@ typedef struct {
   int restarts;           /* restarts after a breakdown */
   long long kernel_launches; /* kernels the library launched during the last call */
   double true_res_max;    /* max_i |b_i - A x_i| / |b_i| at return (FP64) */
-  int graph_iterations;   /* iterations replayed from one captured CUDA graph (the
-                             loop's launches once the frozen step lengths are
-                             recorded; off with MBICG_GRAPHS=0 or while profiling) */
+  int graph_iterations;   /* iterations run from captured CUDA graphs once the
+                             frozen step lengths are recorded: a graph whose
+                             conditional WHILE node repeats the iteration while
+                             the device's own test of Algorithm 2's WHILE
+                             condition holds (off with MBICG_DEVICE_LOOP=0: one
+                             graph launch and one host check per iteration; no
+                             graphs with MBICG_GRAPHS=0 or while profiling) */
   int precision_fallbacks; /* 1 when a solve with FP32 Krylov vectors broke down
                               after its restarts and was continued from its X
                               with FP64 Krylov vectors */
+  int host_syncs;         /* times the host waited for the device to read a
+                             residual norm or status during the last call:
+                             once per iteration while the step lengths are
+                             recorded, then once per stop of the device loop
+                             (convergence, reliable update, restart, max_iter) */
 } mbicg_stats;
 
 /* Fills p with the defaults: ncycle 4, nmr 4, block {4,4,4,4},
@@ -191,9 +200,37 @@ int mbicg_apply_clover(mbicg_ctx* ctx, const double* in, double* out, int L, dou
                        int jacobi);
 
 /* out = M_SAP in (Sec. 2.2) with the parameters ncycle, nmr, block, mr_mode
- * (MBICG_MR_COLUMN or MBICG_MR_BLOCK) and prec_sap of *p.  1 <= L <= 16. */
+ * (MBICG_MR_COLUMN or MBICG_MR_BLOCK; MBICG_MR_FROZEN through
+ * mbicg_sap_precond_frozen) and prec_sap of *p.  1 <= L <= 16. */
 int mbicg_sap_precond(mbicg_ctx* ctx, const double* in, double* out, int L, double kappa,
                       const mbicg_params* p);
+
+/* Length, in doubles, of the step-length table of mbicg_sap_precond_frozen
+ * for the SAP parameters *p (ncycle, nmr, block) on this context's lattice:
+ * 2 * ncycle * 2 * nmr * nd, nd = the number of domains. */
+int mbicg_sap_table_len(const mbicg_ctx* ctx, const mbicg_params* p, long long* n_doubles);
+
+/* out = M_SAP in (Sec. 2.2) with frozen MR step lengths: the preconditioner
+ * that mbicg_block_solve applies by default (MBICG_MR_FROZEN, the stationary M
+ * of Sec. 2.1), with its step-length table held by the caller.
+ *   table     host array of mbicg_sap_table_len doubles: complex step lengths
+ *             [cycle][colour][MR step][domain], the domain numbered
+ *             lexicographically by its coordinates (b0 + nb0 (b1 + nb1 (b2 +
+ *             nb2 b3)), nb = dims / block); entries of domains of the other
+ *             colour are not used.  NaN marks an entry not yet recorded.
+ *   complete  if not NULL: 1 on return when every entry the sweeps use is set.
+ * If any used entry is NaN, the call records: such an entry is set to the
+ * step length formed from the sums over all L columns the first time that
+ * domain's MR residual is nonzero in this call (MBICG_MR_BLOCK's formula) and
+ * written back to table; an entry whose domain residual stays zero stays NaN
+ * (it multiplies zero).  Otherwise the table is replayed unchanged, in FP32 by
+ * the fused on-chip sweep for 8^4 and 4^4 domains of an SU(3) field (the
+ * kernel the block solve uses).  A sequence of calls starting from an all-NaN
+ * table therefore builds the solver's table lazily, as mbicg_block_solve does.
+ * p: MR domain solves with mr_mode = MBICG_MR_FROZEN, prec_sap FP32 or FP64.
+ * Errors as mbicg_sap_precond; MBICG_EINVAL for a device-memory table. */
+int mbicg_sap_precond_frozen(mbicg_ctx* ctx, const double* in, double* out, int L, double kappa,
+                             const mbicg_params* p, double* table, int* complete);
 
 /* Solves A X = B for L right-hand sides by the modified block BiCGSTAB
  * (Algorithm 2 of Sec. 2.1: QR re-orthonormalisation of P, right
@@ -205,8 +242,9 @@ int mbicg_sap_precond(mbicg_ctx* ctx, const double* in, double* out, int L, doub
  *   iters      if not NULL: iterations done.
  *   true_res   if not NULL: L host doubles, |b_i - A x_i| / |b_i| in FP64.
  * 1 <= L <= 16 (L + p->dummy_rhs <= 16); tol > 0.
- * The QR of P is CholeskyQR2 (FP64 Krylov vectors) or shifted CholeskyQR3
- * (FP32 Krylov vectors).  A breakdown (rank-deficient P, singular R~^H V,
+ * The QR of P is shifted CholeskyQR3 (a first Cholesky pass on P^H P + s I,
+ * s = 1e-13 (FP64 Krylov vectors) or 1e-5 (FP32) times max_j |p_j|^2, then two
+ * plain passes; L = 1: two plain passes).  A breakdown (rank-deficient P, singular R~^H V,
  * Tr(Z^H Z) = 0) restarts from the current X (at most three times, not twice
  * in a row); with FP32 Krylov vectors a solve that still breaks down continues
  * from its X with FP64 Krylov vectors (mbicg_stats.precision_fallbacks).  Once
@@ -256,14 +294,16 @@ const char* mbicg_last_error(const mbicg_ctx* ctx);
 #define MBICG_NOALLOC_SCRATCH_MB 32
 
 /* out = A in in FP32, the same result as mbicg_apply_D(..., MBICG_FP32), for
- * callers that cannot allocate device memory: code recording a stream into a
- * CUDA graph (an allocation is not a capturable operation), code that must
- * stay inside a framework's memory pool, real-time loops that may not take
- * the allocator's locks.  It allocates nothing and needs no context.  The
- * paper has no counterpart to this entry point.
+ * callers that cannot allocate device memory: code running inside a
+ * framework's memory pool that must not grow device memory behind the pool,
+ * real-time or latency-bound loops that may not take the allocator's locks or
+ * wait for it, programs whose device memory is fixed when they start.  It
+ * allocates nothing and needs no context.  The paper has no counterpart to
+ * this entry point.
  *   dims         lattice extents (even, >= 2)
- *   U, in, out   device pointers in the layouts above; in and out must not
- *                alias; U is the FP64 gauge field
+ *   U, in, out   device pointers of the current device (cudaGetDevice) in the
+ *                layouts above; in and out must not alias; U is the FP64
+ *                gauge field (36 V complex numbers), in and out 12 V L each
  *   cuda_stream  a cudaStream_t or NULL; the work is ordered on it and the call
  *                returns without waiting for it
  * Its scratch is one file-scope device array of MBICG_NOALLOC_SCRATCH_MB MiB
@@ -274,8 +314,10 @@ const char* mbicg_last_error(const mbicg_ctx* ctx);
  * streams, two host threads) race on it.  The first call on a device looks
  * the array's address up (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture begins.
- * Returns MBICG_EINVAL for bad arguments or host pointers, MBICG_ECUDA if the
- * lookup or a launch fails. */
+ * Returns MBICG_EINVAL for bad arguments, host pointers or pointers of another
+ * device (nothing launched), MBICG_ECUDA if a CUDA error was already pending
+ * on entry (it is neither launched over nor cleared), if the lookup fails or
+ * if one of its launches fails. */
 int mbicg_apply_D_noalloc(const int dims[4], const double* U, const double* in, double* out, int L,
                           double kappa, void* cuda_stream);
 

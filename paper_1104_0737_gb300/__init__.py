@@ -23,7 +23,8 @@ __all__ = [
     "KERNEL_CLASSES",
     "MbicgError", "mbicg_params", "mbicg_stats", "library_path", "load_library",
     "mbicg_default_params", "mbicg_create", "mbicg_destroy", "mbicg_load_gauge",
-    "mbicg_apply_D", "mbicg_load_clover", "mbicg_apply_clover", "mbicg_sap_precond", "mbicg_block_solve", "mbicg_get_stats",
+    "mbicg_apply_D", "mbicg_load_clover", "mbicg_apply_clover", "mbicg_sap_precond", "mbicg_sap_table_len",
+    "mbicg_sap_precond_frozen", "mbicg_block_solve", "mbicg_get_stats",
     "mbicg_last_error", "mbicg_set_profiling", "mbicg_get_profile", "mbicg_apply_D_noalloc",
     "mbicg_request_info", "mbicg_server_create", "mbicg_server_add_field", "mbicg_server_submit",
     "mbicg_server_wait", "mbicg_server_hold", "mbicg_server_stats", "mbicg_server_destroy",
@@ -63,7 +64,7 @@ class mbicg_stats(ctypes.Structure):
     _fields_ = [
         ("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("restarts", ctypes.c_int),
         ("kernel_launches", ctypes.c_longlong), ("true_res_max", ctypes.c_double),
-        ("graph_iterations", ctypes.c_int), ("precision_fallbacks", ctypes.c_int),
+        ("graph_iterations", ctypes.c_int), ("precision_fallbacks", ctypes.c_int), ("host_syncs", ctypes.c_int),
     ]
 
 
@@ -102,6 +103,9 @@ def load_library(build_if_missing: bool = True):
     lib.mbicg_apply_clover.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]
     lib.mbicg_sap_precond.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double,
                                       ctypes.POINTER(mbicg_params)]
+    lib.mbicg_sap_table_len.argtypes = [vp, ctypes.POINTER(mbicg_params), ctypes.POINTER(ctypes.c_longlong)]
+    lib.mbicg_sap_precond_frozen.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double,
+                                             ctypes.POINTER(mbicg_params), dp, ip]
     lib.mbicg_block_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                       ctypes.POINTER(mbicg_params), ip, dp]
     lib.mbicg_get_stats.argtypes = [vp, ctypes.POINTER(mbicg_stats)]
@@ -208,6 +212,33 @@ def mbicg_sap_precond(ctx, inp, out, L: int, kappa: float, params: mbicg_params)
                                                  ctypes.byref(params)))
 
 
+def mbicg_sap_table_len(ctx, params: mbicg_params) -> int:
+    """Doubles in the step-length table of mbicg_sap_precond_frozen."""
+    n = ctypes.c_longlong(0)
+    _check(ctx, load_library().mbicg_sap_table_len(ctx, ctypes.byref(params), ctypes.byref(n)))
+    return n.value
+
+
+def mbicg_sap_precond_frozen(ctx, inp, out, L: int, kappa: float, params: mbicg_params, table) -> bool:
+    """out = M_SAP in with frozen step lengths held in `table` (host numpy
+    complex128, ncycle * 2 * nmr * n_domains entries, NaN = not yet recorded;
+    recorded entries are written back).  Returns True when every entry the
+    sweeps use is set."""
+    import numpy as np
+
+    pi, _ = _ptr(inp, "in")
+    po, _ = _ptr(out, "out")
+    n = mbicg_sap_table_len(ctx, params)
+    if (not isinstance(table, np.ndarray) or table.dtype != np.complex128 or not table.flags.c_contiguous
+            or 2 * table.size != n):
+        raise TypeError(f"table: need a C-contiguous complex128 numpy array of {n // 2} entries")
+    done = ctypes.c_int(0)
+    _check(ctx, load_library().mbicg_sap_precond_frozen(
+        ctx, pi, po, int(L), float(kappa), ctypes.byref(params),
+        table.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(done)))
+    return bool(done.value)
+
+
 def mbicg_block_solve(ctx, B, X, L: int, kappa: float, tol: float, params: mbicg_params):
     """Returns (status, iters, true_res list).  MBICG_ENOTCONV and
     MBICG_EBREAKDOWN are returned (X and true_res are filled); every other
@@ -242,20 +273,35 @@ def mbicg_get_profile(ctx) -> dict:
 
 def mbicg_apply_D_noalloc(dims, U, inp, out, L: int, kappa: float, stream=None) -> None:
     """out = A in (FP32) without any allocation, for callers that cannot
-    allocate device memory (stream capture, fixed memory pools).  U, inp, out:
-    CUDA tensors.  Ordered on `stream` (torch.cuda.Stream, raw handle or None);
+    allocate device memory (inside a framework's memory pool, real-time loops
+    that may not wait for the allocator, device memory fixed at start-up).
+    U, inp, out: CUDA tensors on the current device with V*36 and V*12*L
+    elements.  Ordered on `stream` (torch.cuda.Stream, raw handle or None);
     returns without waiting.  Concurrent calls share one scratch array and race."""
-    pu, _ = _ptr(U, "U")
-    pi, _ = _ptr(inp, "in")
-    po, _ = _ptr(out, "out")
+    V = 1
+    for d in dims:
+        V *= int(d)
+    pu, nu = _ptr(U, "U")
+    pi, ni = _ptr(inp, "in")
+    po, no = _ptr(out, "out")
+    if nu != V * 36 or ni != V * 12 * int(L) or no != V * 12 * int(L):
+        raise MbicgError(MBICG_EINVAL, f"mbicg_apply_D_noalloc: U needs {V * 36} and in/out {V * 12 * int(L)} "
+                                       f"complex numbers, got {nu}, {ni}, {no}")
+    for t, name in ((U, "U"), (inp, "in"), (out, "out")):
+        if not getattr(t, "is_cuda", False):
+            raise MbicgError(MBICG_EINVAL, f"mbicg_apply_D_noalloc: {name} must be a CUDA tensor")
+        import torch
+
+        if t.device.index != torch.cuda.current_device():
+            raise MbicgError(MBICG_EINVAL, f"mbicg_apply_D_noalloc: {name} is not on the current device")
     raw = None
     if stream is not None:
         raw = ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
     st = load_library().mbicg_apply_D_noalloc(d, pu, pi, po, int(L), float(kappa), raw)
     if st != MBICG_OK:
-        raise MbicgError(st, "mbicg_apply_D_noalloc failed (sizes beyond the scratch, host "
-                             "pointers or a CUDA error)")
+        raise MbicgError(st, "mbicg_apply_D_noalloc failed (sizes beyond the scratch, pointers not on the "
+                             "current device, or a CUDA error)")
 
 
 def _host(a, name: str):

@@ -60,7 +60,9 @@ struct mbicg_ctx {
 
 namespace {
 
-constexpr int H_SMALL = 4096;  // doubles of pinned host scratch
+constexpr int H_SMALL = 4096;     // doubles of pinned host scratch
+constexpr int H_CTL_IN = 2048;    // offsets (doubles) of the device loop's staging areas in it
+constexpr int H_CTL_OUT = 2304;
 
 int fail(mbicg_ctx* c, int code, const char* fmt, const char* a = "") {
   char buf[512];
@@ -191,6 +193,7 @@ int read_small(mbicg_ctx* c, const double* d, int n, const int* status, double* 
   if (status)
     CK(cudaMemcpyAsync(c->h_small + n, status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  ++c->stats.host_syncs;
   memcpy(out, c->h_small, sizeof(double) * n);
   if (status) memcpy(st, c->h_small + n, sizeof(int));
   c->prof.collect();
@@ -365,6 +368,7 @@ struct Solver {
       int flag = 1;
       CK(cudaMemcpyAsync(c->h_small, unset, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
+      ++c->stats.host_syncs;
       memcpy(&flag, c->h_small, sizeof(int));
       table_complete = (flag == 0);
     }
@@ -406,13 +410,18 @@ struct Solver {
     return MBICG_OK;
   }
 
-  // QR of P by CholeskyQR2; with FP32 Krylov vectors a shifted first pass
-  // (Cholesky of P^H P + s I, s = 1e-5 max_j |p_j|^2) and two plain passes
-  // (shifted CholeskyQR3): the plain Cholesky of an FP32 Gram matrix fails
-  // once cond(P) passes ~1/sqrt(u) ~ 4e3, the shifted pass brings any P of
-  // cond up to ~1/u to a well-conditioned basis of the same space first.
+  // QR of P by shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto,
+  // Yanagisawa 2020): a first pass on P^H P + s I (s = 1e-5 max_j |p_j|^2
+  // with FP32 Krylov vectors, 1e-13 max_j |p_j|^2 with FP64 ones), then two
+  // plain passes.  A plain Cholesky of the Gram matrix fails once cond(P)
+  // passes ~1/sqrt(u) (4e3 in FP32, 1e8 in FP64: nearly dependent right-hand
+  // sides reach it without a preconditioner); the shifted pass brings any P of
+  // cond up to ~1/u to a well-conditioned basis of the same space first, and
+  // the plain passes then give the Q of the unique QR.  One column (L = 1) is
+  // only normalised: two plain passes.
   int qr() {
-    const int npass = sizeof(T) == 4 ? 3 : 2;
+    const int npass = L == 1 ? 2 : 3;
+    const double shift = sizeof(T) == 4 ? 1e-5 : 1e-13;
     for (int pass = 0; pass < npass; ++pass) {
       int np;
       {
@@ -422,7 +431,7 @@ struct Solver {
       {
         Timed t(ex, KC_SMALL);
         lxl_cholesky_inverse(ex, L, gpart, np, sm, sizeof(T) == 4 ? 1e-12 : 1e-26,
-                             (sizeof(T) == 4 && pass == 0) ? 1e-5 : 0.0);
+                             (L > 1 && pass == 0) ? shift : 0.0);
       }
       Timed t(ex, KC_AXPY);
       block_transform<T>(ex, V, L, k.P, sm.M, k.P);
@@ -527,15 +536,119 @@ struct Solver {
     return MBICG_OK;
   }
 
-  ~Solver() {
-    if (gexec) {
-      cudaStreamSynchronize(c->stream);  // no replay of it still pending
-      cudaGraphExecDestroy(gexec);
-    }
+  // The loop on the device: one captured CUDA graph whose WHILE conditional
+  // node repeats the iteration and k_loop_control, which evaluates
+  // Algorithm 2's WHILE test (and whether a reliable update is due) on the
+  // device, so the host waits only when the loop stops.  Used where the
+  // iteration graph is (and not with MBICG_DEVICE_LOOP=0); if it cannot be
+  // built, the iteration graph with one host check per iteration is used.
+  cudaGraphExec_t gloop = nullptr;
+  cudaGraphConditionalHandle hcond = 0;
+  long long loop_kernels = 0;  // kernels of one pass of the loop's body
+  bool loop_failed = false;
+  LoopCtl* dctl = nullptr;
+  double* dbnorm = nullptr;
+  double* dhist = nullptr;
+  int hist_len = 0;
+  std::vector<std::pair<int, int>> hist_ranges;  // iterations whose history is on the device
+
+  bool loop_usable() const {
+    const char* env = getenv("MBICG_GRAPHS");
+    const char* dl = getenv("MBICG_DEVICE_LOOP");
+    const bool stable = p.ncycle == 0 || p.domain_solver == MBICG_DOMAIN_SSOR || p.mr_mode != MBICG_MR_FROZEN ||
+                        table_complete;
+    return !(env && env[0] == '0') && !(dl && dl[0] == '0') && !c->prof.on && stable && !loop_failed &&
+           !graph_failed;
   }
+
+  int build_loop() {
+    int rc;
+    if ((rc = buf(c, "loop_ctl", 1, &dctl))) return rc;
+    if ((rc = buf(c, "loop_bnorm", MAXL, &dbnorm))) return rc;
+    hist_len = std::max(1, p.max_iter);
+    if ((rc = buf(c, "loop_hist", (size_t)hist_len, &dhist))) return rc;
+    memcpy(c->h_small + H_CTL_IN, bnorm, sizeof(double) * MAXL);
+    CK(cudaMemcpyAsync(dbnorm, c->h_small + H_CTL_IN, sizeof(double) * MAXL, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));  // the pinned staging area is reused below
+    cudaGraph_t g = nullptr;
+    cudaGraphNode_t node = nullptr;
+    cudaGraphNodeParams np = {};
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+              cudaGraphConditionalHandleCreate(&hcond, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = hcond;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+    }
+    cudaGraph_t body = ok ? np.conditional.phGraph_out[0] : nullptr;
+    const long long before = c->launches;
+    if (ok)
+      ok = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+           cudaSuccess;
+    if (ok) {
+      const int rc2 = iteration_launches();
+      {
+        Timed t(ex, KC_SMALL);
+        loop_control(ex, dctl, sm.norms, dbnorm, sm.status, dhist, hist_len, hcond);
+      }
+      cudaGraph_t out = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(c->stream, &out);
+      ok = rc2 == MBICG_OK && e == cudaSuccess && cudaGraphInstantiate(&gloop, g, 0) == cudaSuccess;
+    }
+    loop_kernels = c->launches - before;
+    c->launches = before;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      const char* tr = getenv("MBICG_TRACE");
+      if (tr && tr[0] == '1') fprintf(stderr, "mbicg: device loop not used (%s)\n", c->err.c_str());
+      cudaGetLastError();
+      c->err.clear();
+      if (gloop) cudaGraphExecDestroy(gloop);
+      gloop = nullptr;
+      loop_failed = true;
+    }
+    return MBICG_OK;
+  }
+
+  // Iterations until the device's test stops the loop (at most max_iter - it);
+  // returns the iterations done, the norms and status of the last one.
+  int launch_loop(int it, double rmax_ru, int* done, int* st) {
+    LoopCtl h{};
+    h.it = it;
+    h.max_iter = p.max_iter;
+    h.Lc = std::min(L, Lc);
+    h.sloppy = sizeof(T) == 4 ? 1 : 0;
+    h.tol = tol_;
+    h.delta_ru = p.delta_ru;
+    h.rmax_ru = rmax_ru;
+    h.relmax = 0;
+    memcpy(c->h_small + H_CTL_IN, &h, sizeof(h));
+    CK(cudaMemcpyAsync(dctl, c->h_small + H_CTL_IN, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaGraphLaunch(gloop, c->stream));
+    CK(cudaMemcpyAsync(c->h_small + H_CTL_OUT, dctl, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    if (int rc = read_small(c, sm.norms, L, sm.status, h_norm, st)) return rc;
+    memcpy(&h, c->h_small + H_CTL_OUT, sizeof(h));
+    *done = h.it - it;
+    if (*done < 1 || *done > p.max_iter) return fail(c, MBICG_ECUDA, "the device loop returned a bad iteration count");
+    hist_ranges.push_back({it, *done});
+    c->launches += (long long)*done * loop_kernels;
+    c->stats.graph_iterations += *done;
+    return MBICG_OK;
+  }
+
+  ~Solver() {
+    if (gexec || gloop) cudaStreamSynchronize(c->stream);  // no replay of them still pending
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (gloop) cudaGraphExecDestroy(gloop);
+  }
+
+  double tol_ = 0;
 
   int run(const cx<double>* dB, cx<double>* dX, double tol, int* iters_out, double* true_res) {
     int rc;
+    tol_ = tol;
     nl = (size_t)V * 12 * L;
     if ((rc = alloc())) return rc;
     // B, X into the internal layout
@@ -573,10 +686,17 @@ struct Solver {
         if (relmax <= tol) break;
       }
       if (it >= p.max_iter) { status = MBICG_ENOTCONV; break; }
-      if ((rc = launch_iteration())) return rc;
-      int st = 0;
-      if ((rc = read_small(c, sm.norms, L, sm.status, h_norm, &st))) return rc;
-      ++it;
+      int st = 0, ndone = 1;
+      if (loop_usable() && !gloop) {
+        if ((rc = build_loop())) return rc;
+      }
+      if (loop_usable() && gloop) {
+        if ((rc = launch_loop(it, rmax_ru, &ndone, &st))) return rc;
+      } else {
+        if ((rc = launch_iteration())) return rc;
+        if ((rc = read_small(c, sm.norms, L, sm.status, h_norm, &st))) return rc;
+      }
+      it += ndone;
       true_fresh = false;
       relmax = 0;
       for (int i = 0; i < L; ++i) {
@@ -585,7 +705,7 @@ struct Solver {
         if (!(rel[i] <= relmax)) relmax = rel[i];
       }
       if (p.res_history && it - 1 < p.res_history_len) p.res_history[it - 1] = relmax;
-      if (trace) fprintf(stderr, "mbicg: iter %d max rel residual %.6e status 0x%x\n", it, relmax, st);
+      if (trace) fprintf(stderr, "mbicg: iter %d (+%d) max rel residual %.6e status 0x%x\n", it, ndone, relmax, st);
       if (st & ST_TIMEOUT) return fail(c, MBICG_ECUDA, "a bounded wait for a bulk copy gave up in a kernel");
       if (st & ST_NAN) { status = MBICG_ENAN; break; }
       if (st) {
@@ -610,6 +730,15 @@ struct Solver {
         c->stats.reliable_updates++;
         rmax_ru = relmax;
         true_fresh = true;
+      }
+    }
+    // the recursive residuals of the iterations the device loop ran
+    if (p.res_history && !hist_ranges.empty()) {
+      CK(cudaStreamSynchronize(c->stream));
+      for (const auto& r : hist_ranges) {
+        const int n = std::min(r.first + r.second, p.res_history_len) - r.first;
+        if (n > 0)
+          CK(cudaMemcpy(p.res_history + r.first, dhist + r.first, sizeof(double) * n, cudaMemcpyDeviceToHost));
       }
     }
     // final true residual in FP64 (R is no longer needed)
@@ -659,7 +788,9 @@ const cx<float>* Solver<float, double>::links_T() const { return c->U32; }
 template <>
 const cx<double>* Solver<float, double>::links_S() const { return c->U64; }
 
-int check_params(mbicg_ctx* c, int L, const mbicg_params* p, bool solve) {
+// solve: the block solve's parameters too; frozen: MBICG_MR_FROZEN allowed
+// (the block solve, or a SAP call with a caller-held step-length table)
+int check_params(mbicg_ctx* c, int L, const mbicg_params* p, bool solve, bool frozen) {
   if (L < 1 || L > MAXL) return fail(c, MBICG_EINVAL, "L must be in [1, 16]");
   if (!p) return fail(c, MBICG_EINVAL, "params is NULL");
   if (solve && (p->dummy_rhs < 0 || L + p->dummy_rhs > MAXL))
@@ -676,7 +807,7 @@ int check_params(mbicg_ctx* c, int L, const mbicg_params* p, bool solve) {
     if (p->domain_solver == MBICG_DOMAIN_SSOR) {
       if (p->nssor < 0 || p->nssor > 16) return fail(c, MBICG_EINVAL, "nssor must be in [0, 16]");
       if (!(p->ssor_omega > 0 && p->ssor_omega < 2)) return fail(c, MBICG_EINVAL, "ssor_omega must be in (0, 2)");
-    } else if (p->mr_mode < 0 || p->mr_mode > 2 || (!solve && p->mr_mode == MBICG_MR_FROZEN)) {
+    } else if (p->mr_mode < 0 || p->mr_mode > 2 || (!frozen && p->mr_mode == MBICG_MR_FROZEN)) {
       return fail(c, MBICG_EINVAL, "bad mr_mode");
     }
     if (p->prec_sap != MBICG_FP32 && p->prec_sap != MBICG_FP64)
@@ -1020,13 +1151,37 @@ int mbicg_apply_clover(mbicg_ctx* c, const double* in, double* out, int L, doubl
   return MBICG_OK;
 }
 
-int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double kappa, const mbicg_params* p) {
-  if (!c) return MBICG_EINVAL;
-  c->err.clear();
+}  // extern "C"
+
+namespace {
+
+// Lexicographic index of the k-th domain of colour `colour` (the enumeration
+// of colour_domain in common.cuh).
+long long colour_domain_lex(const Geom& g, int colour, int k) {
+  const int half = g.nb[0] / 2;
+  const int row0 = k / half;
+  const int j = 2 * (k - row0 * half);
+  int b[4];
+  b[1] = row0 % g.nb[1];
+  const int row1 = row0 / g.nb[1];
+  b[2] = row1 % g.nb[2];
+  b[3] = row1 / g.nb[2];
+  b[0] = j + (colour ^ ((b[1] + b[2] + b[3]) & 1));
+  return b[0] + (long long)g.nb[0] * (b[1] + (long long)g.nb[1] * (b[2] + (long long)g.nb[2] * b[3]));
+}
+
+// out = M_SAP in.  table_lex != NULL: frozen MR step lengths held by the
+// caller (host, complex [ncycle][2][nmr][nd], lexicographic domain index):
+// entries still NaN are recorded by this call and written back, and once
+// every entry the sweeps use is set the table is replayed (the solver's path).
+int sap_precond_impl(mbicg_ctx* c, const double* in, double* out, int L, double kappa, const mbicg_params* p,
+                     double* table_lex, int* complete) {
   if (!in || !out || in == out) return fail(c, MBICG_EINVAL, "in/out NULL or aliased");
   int rc;
-  if ((rc = check_params(c, L, p, false))) return rc;
+  if ((rc = check_params(c, L, p, false, table_lex != nullptr))) return rc;
   if (p->ncycle < 1) return fail(c, MBICG_EINVAL, "ncycle must be >= 1");
+  if (table_lex && (p->domain_solver != MBICG_DOMAIN_MR || p->mr_mode != MBICG_MR_FROZEN))
+    return fail(c, MBICG_EINVAL, "a step-length table needs MR domain solves with mr_mode MBICG_MR_FROZEN");
   if (!c->gauge) return fail(c, MBICG_ENOGAUGE, "no gauge field loaded");
   CK(cudaSetDevice(c->device));
   c->launches = 0;
@@ -1037,6 +1192,33 @@ int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double
   if ((rc = stage_in(c, out, sizeof(cx<double>) * nl, "abi_out", false, &so))) return rc;
   const Exec ex = exec_of(c);
   const Geom g = lattice_geom(c, p->block);
+  const int ndc = g.nd / 2;
+  // the caller's table in the library's layout, complex [ncycle][2][nmr][nd / 2]
+  const size_t ntab = (size_t)p->ncycle * 2 * p->nmr * ndc;
+  std::vector<double> htab;
+  double* dtab = nullptr;
+  int* unset = nullptr;
+  int mode = p->mr_mode;
+  if (table_lex) {
+    htab.resize(2 * ntab);
+    bool any_nan = false;
+    for (int cyc = 0; cyc < p->ncycle; ++cyc)
+      for (int col = 0; col < 2; ++col)
+        for (int it = 0; it < p->nmr; ++it)
+          for (int k = 0; k < ndc; ++k) {
+            const size_t row = ((size_t)cyc * 2 + col) * p->nmr + it;
+            const size_t src = (row * g.nd + colour_domain_lex(g, col, k)) * 2;
+            const size_t dst = (row * ndc + k) * 2;
+            htab[dst] = table_lex[src];
+            htab[dst + 1] = table_lex[src + 1];
+            any_nan = any_nan || isnan(htab[dst]) || isnan(htab[dst + 1]);
+          }
+    if ((rc = buf(c, "sapp_table", 2 * ntab, &dtab))) return rc;
+    if ((rc = buf(c, "sapp_unset", 1, &unset))) return rc;
+    CK(cudaMemcpyAsync(dtab, htab.data(), sizeof(double) * 2 * ntab, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(unset, 0, sizeof(int), c->stream));
+    mode = any_nan ? 2 : 3;  // record where unset, else replay
+  }
   auto run = [&](auto tag, const auto* links) -> int {
     using R = decltype(tag);
     cx<R>*a, *b, *r, *q, *x;
@@ -1050,7 +1232,6 @@ int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double
     w.r = r;
     w.q = q;
     w.x = x;
-    const int ndc = g.nd / 2;
     const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
     if ((rc2 = buf(c, "sap_dots", (size_t)ndc * (g.Vd / S) * L * 3, &w.dots))) return rc2;
     if ((rc2 = buf(c, "sap_omega", (size_t)ndc * L * 2, &w.omega))) return rc2;
@@ -1072,7 +1253,7 @@ int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double
     const R* tinv = nullptr;
     if (p->clover) tinv = reinterpret_cast<const R*>(sizeof(R) == 8 ? static_cast<const void*>(c->Ti64)
                                                                      : static_cast<const void*>(c->Ti32));
-    sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, p->mr_mode, nullptr, nullptr, w, tinv,
+    sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, mode, dtab, unset, w, tinv,
                  p->domain_solver == MBICG_DOMAIN_SSOR ? &sp : nullptr);
     Timed t(ex, KC_CONVERT);
     internal_to_abi<R>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
@@ -1086,8 +1267,58 @@ int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double
   if (rc) return rc;
   if ((rc = check_launch(c, "sap_precond"))) return rc;
   if ((rc = stage_out(c, so))) return rc;
+  if (table_lex) {
+    // the recorded entries back into the caller's table
+    CK(cudaMemcpyAsync(htab.data(), dtab, sizeof(double) * 2 * ntab, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    bool all_set = true;
+    for (int cyc = 0; cyc < p->ncycle; ++cyc)
+      for (int col = 0; col < 2; ++col)
+        for (int it = 0; it < p->nmr; ++it)
+          for (int k = 0; k < ndc; ++k) {
+            const size_t row = ((size_t)cyc * 2 + col) * p->nmr + it;
+            const size_t dst = (row * g.nd + colour_domain_lex(g, col, k)) * 2;
+            const size_t src = (row * ndc + k) * 2;
+            table_lex[dst] = htab[src];
+            table_lex[dst + 1] = htab[src + 1];
+            all_set = all_set && !isnan(htab[src]);
+          }
+    if (complete) *complete = all_set ? 1 : 0;
+  }
   c->stats.kernel_launches = c->launches;
   return MBICG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mbicg_sap_precond(mbicg_ctx* c, const double* in, double* out, int L, double kappa, const mbicg_params* p) {
+  if (!c) return MBICG_EINVAL;
+  c->err.clear();
+  return sap_precond_impl(c, in, out, L, kappa, p, nullptr, nullptr);
+}
+
+int mbicg_sap_table_len(const mbicg_ctx* c, const mbicg_params* p, long long* n_doubles) {
+  if (!c || !p || !n_doubles) return MBICG_EINVAL;
+  mbicg_ctx* m = const_cast<mbicg_ctx*>(c);
+  m->err.clear();
+  if (p->ncycle < 1 || p->nmr < 1) return fail(m, MBICG_EINVAL, "ncycle and nmr must be >= 1");
+  if (!valid_blocking(c, p->block))
+    return fail(m, MBICG_EINVAL, "SAP block must divide the lattice into an even number (>= 2) of domains per direction");
+  long long nd = 1;
+  for (int mu = 0; mu < 4; ++mu) nd *= c->dims[mu] / p->block[mu];
+  *n_doubles = 2LL * p->ncycle * 2 * p->nmr * nd;
+  return MBICG_OK;
+}
+
+int mbicg_sap_precond_frozen(mbicg_ctx* c, const double* in, double* out, int L, double kappa,
+                             const mbicg_params* p, double* table, int* complete) {
+  if (!c) return MBICG_EINVAL;
+  c->err.clear();
+  if (!table) return fail(c, MBICG_EINVAL, "table is NULL");
+  if (is_device_ptr(table)) return fail(c, MBICG_EINVAL, "table must be host memory");
+  return sap_precond_impl(c, in, out, L, kappa, p, table, complete);
 }
 
 int mbicg_block_solve(mbicg_ctx* c, const double* B, double* X, int L, double kappa, double tol,
@@ -1097,7 +1328,7 @@ int mbicg_block_solve(mbicg_ctx* c, const double* B, double* X, int L, double ka
   c->stats = mbicg_stats{};
   if (!B || !X || (const void*)B == (const void*)X) return fail(c, MBICG_EINVAL, "B/X NULL or aliased");
   int rc;
-  if ((rc = check_params(c, L, p, true))) return rc;
+  if ((rc = check_params(c, L, p, true, true))) return rc;
   if (!(tol > 0)) return fail(c, MBICG_EINVAL, "tol must be > 0");
   if (!c->gauge) return fail(c, MBICG_ENOGAUGE, "no gauge field loaded");
   CK(cudaSetDevice(c->device));

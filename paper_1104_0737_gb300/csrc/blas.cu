@@ -982,6 +982,30 @@ void lxl_norms(const Exec& ex, int L, const double* part, int nparts, bool from_
   ++*ex.launches;
 }
 
+__global__ void k_loop_control(LoopCtl* c, const double* __restrict__ norms, const double* __restrict__ bnorm,
+                               const int* __restrict__ status, double* __restrict__ hist, int hist_len,
+                               cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  double rm = 0;
+  for (int i = 0; i < c->Lc; ++i) {
+    const double r = sqrt(norms[i]) / bnorm[i];
+    if (!(r <= rm)) rm = r;  // a NaN propagates
+  }
+  c->relmax = rm;
+  const int it = c->it + 1;
+  if (it - 1 < hist_len) hist[it - 1] = rm;
+  c->it = it;
+  const bool cont = *status == 0 && rm == rm && rm > c->tol && it < c->max_iter &&
+                    !(c->sloppy && rm < c->delta_ru * c->rmax_ru);
+  cudaGraphSetConditional(h, cont ? 1u : 0u);
+}
+
+void loop_control(const Exec& ex, LoopCtl* ctl, const double* norms, const double* bnorm, const int* status,
+                  double* hist, int hist_len, cudaGraphConditionalHandle h) {
+  k_loop_control<<<1, 32, 0, ex.stream>>>(ctl, norms, bnorm, status, hist, hist_len, h);
+  ++*ex.launches;
+}
+
 #define INST(R)                                                                                                   \
   template int block_gram<R>(const Exec&, long long, int, const cx<R>*, const cx<R>*, const cx<R>*, int,        \
                              double*, int*);                                                                      \

@@ -296,20 +296,23 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_ssor_level(Geom
 // ---------------------------------------------------------------------------
 // Fused SAP colour sweep with the MR iterations on chip (FP32).
 //
-// One thread-block cluster per (domain of the colour, chunk of columns).  The
-// DX x DY x DZ x DT domain is cut into CX x CY x CZ x CT sub-blocks, one per
-// CTA of the cluster, one thread per site; cutting x, y and z in two gives
-// every CTA the same number of hops that leave the domain and of hops into a
-// neighbouring CTA, so no CTA lags at the cluster barriers.  Each CTA runs the
-// whole sweep for the columns of its chunk in turn.  The MR residual of its
-// sites lives in shared memory, double buffered so that one cluster barrier
-// per MR step separates the neighbour reads of one step from the writes of
-// the next; x and q stay in registers.  Spinors are stored as 6 float4
-// planes so consecutive threads read consecutive 16-byte words; hops into a
-// neighbouring CTA read its shared memory (distributed shared memory).  Links
-// are read through L1 (the domain's links serve every column and MR step).
-// For every column:
-//   r = eta - A psi on the domain (psi staged in shared memory, halo from global),
+// Persistent thread-block clusters walk the (domain of the colour, column)
+// items.  The DX x DY x DZ x DT domain is cut into CX x CY x CZ x CT
+// sub-blocks, one per CTA of the cluster, one thread per site; cutting y, z
+// and t in two gives every CTA the same number of hops that leave the domain
+// and of hops into a neighbouring CTA, so no CTA lags at the cluster
+// barriers.  The MR residual of its sites lives in shared memory, double
+// buffered so that one cluster barrier per MR step separates the neighbour
+// reads of one step from the writes of the next; x and q stay in registers.
+// Spinors are stored as 6 float4 planes so consecutive threads read
+// consecutive 16-byte words; hops into a neighbouring CTA read its shared
+// memory (distributed shared memory).  The first two rows of each site's
+// forward links are staged in shared memory once per domain and serve every
+// column and MR step.
+// The colour's residual r = eta - A psi is formed beforehand by the residual
+// kernel (a full-operator stencil over the colour's sites that streams psi
+// and eta from HBM with its halo), so the sweep itself only reads r and psi
+// and writes psi.  For every column:
 //   nmr times: q = A_dom r; omega (per column from the cluster-wide dots, or
 //   from the frozen table); x += omega r; r -= omega q,
 //   psi += x.
@@ -410,24 +413,17 @@ __device__ __forceinline__ void planes_to_link12(const float4* uS, int NS, int m
   }
 }
 
-// Hop sum over the eight neighbours of a site of the domain, reading the
+// Dirichlet hop sum of the domain operator A_dom over the eight neighbours of
+// a site of the domain (hops that leave the domain are dropped), reading the
 // neighbour's spinor from the (distributed) shared-memory planes at cluster
-// address vS when it lies in the domain, and the link rows from the planes
-// at uS (the site's own forward links; the neighbour's for a backward hop).
-// vS is a CTA-local shared address, uS the CTA's link planes already in the
-// cluster window; vL and uL are the same planes as pointers, read directly
-// where the hop cannot leave the CTA.
-// Hops that leave the domain are dropped (HALO = false: the Dirichlet
-// domain operator A_dom) or taken from global memory (HALO = true: the full
-// operator, psi_g and the global links, with the antiperiodic phase of the
-// t boundary).  sb: coordinates inside the CTA's sub-block, lc: inside the
-// domain, c: on the lattice.
-template <typename SH, int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, bool HALO>
-__device__ __forceinline__ void domain_hops(const Geom& g, const float4* vL, uint32_t vS, const float4* uL,
-                                            uint32_t uS, int tid, int rank,
-                                            const int sb[4], const int lc[4], const int c[4], int s, int L, int rhs,
-                                            const cx<float>* __restrict__ links,
-                                            const cx<float>* __restrict__ psi_g, Spinor<float>& acc) {
+// address vS and the link rows from the planes at uS (the site's own forward
+// links; the neighbour's for a backward hop).  vS is a CTA-local shared
+// address, uS the CTA's link planes already in the cluster window; vL and uL
+// are the same planes as pointers, read directly where the hop cannot leave
+// the CTA.  sb: coordinates inside the CTA's sub-block, lc: inside the domain.
+template <typename SH, int DX, int DY, int DZ, int DT, int CX, int CY, int CZ>
+__device__ __forceinline__ void domain_hops(const float4* vL, uint32_t vS, const float4* uL, uint32_t uS, int tid,
+                                            int rank, const int sb[4], const int lc[4], Spinor<float>& acc) {
   constexpr int NS = SH::NS;
   zero(acc);
 #pragma unroll
@@ -439,11 +435,11 @@ __device__ __forceinline__ void domain_hops(const Geom& g, const float4* vL, uin
       const int sub_stride = pick4(mu, 1, SH::SX, SH::SX * SH::SY, SH::SX * SH::SY * SH::SZ);
       const int cta_stride = pick4(mu, 1, CX, CX * CY, CX * CY * CZ);
       const bool leaves = fwd ? (lc[mu] == ext - 1) : (lc[mu] == 0);
-      if (leaves && !HALO) continue;
+      if (leaves) continue;
       Spinor<float> pn;
       Link<float> u;
-      float phase = 1.0f;
-      if (!leaves) {
+      const float phase = 1.0f;
+      {
         // the neighbour is in this CTA or, across a face of the sub-block,
         // at the same position on the far face of the next CTA
         const int sn_sub = sb[mu] + (fwd ? 1 : -1);
@@ -465,15 +461,6 @@ __device__ __forceinline__ void domain_hops(const Geom& g, const float4* vL, uin
           if (fwd) planes_to_link12(uL, NS, mu, tid, u);
           else cluster_planes_to_link12(cluster_addr(uS, other), NS, mu, nb, u);
         }
-      } else {
-        const int dm = g.d[mu];
-        const int stride = mu == 0 ? 1 : mu == 1 ? g.d[0] : mu == 2 ? g.d[0] * g.d[1] : g.d[0] * g.d[1] * g.d[2];
-        const bool wrap = fwd ? (c[mu] == dm - 1) : (c[mu] == 0);
-        const int sn = fwd ? (wrap ? s - (dm - 1) * stride : s + stride) : (wrap ? s + (dm - 1) * stride : s - stride);
-        if (mu == 3 && wrap) phase = -1.0f;
-        load_spinor(psi_g + spinor_offset(sn, L, rhs), pn);
-        if (fwd) planes_to_link12(uL, NS, mu, tid, u);
-        else load_link(links + (size_t)(sn * 4 + mu) * 9, u);
       }
       cx<float> h[2][3], w[2][3];
       if (fwd) {
@@ -500,8 +487,8 @@ __device__ __forceinline__ void domain_hops(const Geom& g, const float4* vL, uin
 template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM>
 __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS,
                                   (SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS <= 256) ? 2 : 1)
-    k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const cx<float>* __restrict__ eta,
-                cx<float>* __restrict__ psi, int L, float kappa, int psi_zero, int nmr, int mode,
+    k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const cx<float>* __restrict__ rin,
+                cx<float>* __restrict__ psi, int L, float kappa, int psi_mode, int nmr, int mode,
                 const double* __restrict__ table, const float* __restrict__ tinv) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   constexpr int NS = SH::NS;
@@ -573,36 +560,10 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
         }
     }
     const size_t off = spinor_offset(s, L, rhs);
+    // the colour's residual at entry: eta itself when psi = 0, else
+    // eta - A psi formed beforehand by the residual kernel
     Spinor<float> r0;
-    if (!psi_zero) {
-      // r = eta - A psi on the domain: psi staged in shared memory, the halo
-      // (neighbours in other domains) from global memory
-      {
-        Spinor<float> pv;
-        load_spinor(psi + off, pv);
-        spinor_to_planes(nxt, NS, tid, pv);
-      }
-      cluster.sync();
-      float4* t = cur; cur = nxt; nxt = t;
-      Spinor<float> acc, pv;
-      domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, true>(g, cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, c, s, L,
-                                                       rhs, links, psi, acc);
-      if (CM == 1) {
-        Spinor<float> h;
-        herm_apply<float>(tinv + (size_t)s * HERM_PER_SITE, acc, h);
-        acc = h;
-      }
-      load_spinor(eta + off, r0);
-      planes_to_spinor(cur, NS, tid, pv);
-#pragma unroll
-      for (int j = 0; j < 12; ++j) {
-        cx<float>& e = (&r0.c[0][0])[j];
-        const cx<float> pj = (&pv.c[0][0])[j], aj = (&acc.c[0][0])[j];
-        e = mk(fmaf(kappa, aj.re, e.re - pj.re), fmaf(kappa, aj.im, e.im - pj.im));
-      }
-    } else {
-      load_spinor(eta + off, r0);
-    }
+    load_spinor(rin + off, r0);
     spinor_to_planes(nxt, NS, tid, r0);
     cluster.sync();  // r0 (and, for the first column, every CTA's links) visible
     { float4* t = cur; cur = nxt; nxt = t; }
@@ -614,8 +575,7 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
       Spinor<float> q, rv;
       const bool need_q = (mode == 0) || !last;
       if (need_q) {
-        domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ, false>(g, cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, c, s,
-                                                          L, rhs, links, psi, q);
+        domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ>(cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, q);
         if (CM == 1) {
           Spinor<float> h;
           herm_apply<float>(tinv + (size_t)s * HERM_PER_SITE, q, h);
@@ -687,7 +647,7 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
     }
     // psi += x
     Spinor<float> pv;
-    if (psi_zero) zero(pv);
+    if (psi_mode == 1) zero(pv);
     else load_spinor(psi + off, pv);
 #pragma unroll
     for (int j = 0; j < 12; ++j) (&pv.c[0][0])[j] = (&pv.c[0][0])[j] + (&x.c[0][0])[j];
@@ -718,7 +678,7 @@ int sweep_setup(cudaLaunchConfig_t cfg) {
 
 template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM>
 bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
-                  cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table,
+                  cx<float>* psi, int L, double kappa, int psi_mode, int nmr, int mode, const double* table,
                   const float* tinv) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM>;
@@ -741,33 +701,38 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
   const long long nitems = (long long)(g.nd / 2) * L;
   const int nclu = (int)std::min<long long>(max_clusters, nitems);
   cfg.gridDim = dim3((unsigned)(SH::CS * nclu));
-  cudaLaunchKernelEx(&cfg, kern, g, colour, links, eta, psi, L, (float)kappa, psi_zero ? 1 : 0, nmr, mode, table,
-                     tinv);
+  cudaLaunchKernelEx(&cfg, kern, g, colour, links, eta, psi, L, (float)kappa, psi_mode, nmr, mode, table, tinv);
   ++*ex.launches;
   return true;
 }
 
 }  // namespace
 
+bool sap_sweep_fusable(const Geom& g, int mode) {
+  if (!(mode == 0 || mode == 3) || !g.su3) return false;  // the kernel rebuilds the third link row
+  const int* bk = g.blk;
+  return (bk[0] == 8 && bk[1] == 8 && bk[2] == 8 && bk[3] == 8) || (bk[0] == 4 && bk[1] == 4 && bk[2] == 4 && bk[3] == 4);
+}
+
 bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
-                     cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode, const double* table,
+                     cx<float>* psi, int L, double kappa, int psi_mode, int nmr, int mode, const double* table,
                      const float* tinv) {
-  if (mode == 1 || !g.su3) return false;  // the kernel rebuilds the third link row
+  if (!sap_sweep_fusable(g, mode)) return false;
   const int* bk = g.blk;
   // 8^4: eight CTAs of 8 x 4 x 4 x 4 sites (x, the unit-stride direction, is
   // not split, so its hops never leave the CTA); 4^4: one CTA
   if (bk[0] == 8 && bk[1] == 8 && bk[2] == 8 && bk[3] == 8) {
     if (tinv)
-      return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode,
+      return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_mode, nmr, mode,
                                                      table, tinv);
-    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 0>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode,
+    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 0>(ex, g, colour, links, eta, psi, L, kappa, psi_mode, nmr, mode,
                                                    table, nullptr);
   }
   if (bk[0] == 4 && bk[1] == 4 && bk[2] == 4 && bk[3] == 4) {
     if (tinv)
-      return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode,
+      return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_mode, nmr, mode,
                                                      table, tinv);
-    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 0>(ex, g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode,
+    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 0>(ex, g, colour, links, eta, psi, L, kappa, psi_mode, nmr, mode,
                                                    table, nullptr);
   }
   return false;

@@ -153,9 +153,13 @@ void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* li
 // domain shapes 8^4 and 4^4, with T^{-1} (tinv) for the Jacobi-preconditioned
 // clover matrix.  Returns false (nothing launched) otherwise.
 // table: the frozen step lengths of this (cycle, colour), [nmr][nd/2] complex.
-bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
-                     cx<float>* psi, int L, double kappa, bool psi_zero, int nmr, int mode,
+// rin: the residual of this colour's sites at entry (eta itself when
+// psi_mode = 1, psi = 0 on entry and psi = x on exit; psi_mode = 2: psi += x).
+bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* rin,
+                     cx<float>* psi, int L, double kappa, int psi_mode, int nmr, int mode,
                      const double* table, const float* tinv = nullptr);
+// whether sap_sweep_fused takes this domain shape, MR mode and field
+bool sap_sweep_fusable(const Geom& g, int mode);
 // SSOR (Sec. 2.2): one wavefront level of z = (1 - omega L)^{-1} y (fwd) or
 // z = (1 - omega U)^{-1} y on every domain of one colour, L and U the forward
 // and backward hops inside a domain (times T^{-1} with tinv); komega =
@@ -297,5 +301,24 @@ void lxl_cholesky_inverse(const Exec& ex, int L, const double* part, int nparts,
 // norms[i] = sum of partial column norms (part[cta][L], or gram slots when
 // from_gram, using the |D|^2 slots)
 void lxl_norms(const Exec& ex, int L, const double* part, int nparts, bool from_gram, SmallWork& w);
+
+// Device state of the Krylov loop while the device decides Algorithm 2's
+// WHILE test (a conditional node of a CUDA graph repeats the iteration):
+// the host writes it before a launch and reads it when the loop stops.
+struct LoopCtl {
+  int it;           // iterations done
+  int max_iter;
+  int Lc;           // columns the stopping test covers
+  int sloppy;       // FP32 Krylov vectors: stop for a reliable update
+  double tol;
+  double delta_ru;  // reliable update below delta_ru * rmax_ru
+  double rmax_ru;
+  double relmax;    // max_i |r_i| / |b_i| after the last iteration
+};
+// After one iteration: relmax from the column norms, history[it] = relmax,
+// ++it, and the loop's condition: continue while no status bit is set, relmax
+// is a number above tol, it < max_iter and no reliable update is due.
+void loop_control(const Exec& ex, LoopCtl* ctl, const double* norms, const double* bnorm, const int* status,
+                  double* hist, int hist_len, cudaGraphConditionalHandle h);
 
 }  // namespace mbicg

@@ -257,12 +257,20 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
   for (int cyc = 0; cyc < ncycle; ++cyc) {
     for (int colour = 0; colour < 2; ++colour) {
       if constexpr (std::is_same<R, float>::value) {
-        if (allow_fused && (mr_mode == 0 || mr_mode == 3)) {
+        if (allow_fused && sap_sweep_fusable(g, mr_mode)) {
+          // the colour's residual eta - A psi by the streaming residual
+          // kernel, then the MR steps on chip (psi = 0 before the first sweep:
+          // the residual is eta itself)
           const double* tab = table ? table + ((long long)cyc * 2 + colour) * nmr * ndc * 2 : nullptr;
+          const bool first = cyc == 0 && colour == 0;
+          if (!first) {
+            Timed t(ex, KC_SAP_RESID);
+            sap_residual<R>(ex, g, colour, links, eta, psi, r, L, kappa, false, tinv);
+          }
           Timed t(ex, KC_SAP_SWEEP);
-          if (sap_sweep_fused(ex, g, colour, links, eta, psi, L, kappa, cyc == 0 && colour == 0, nmr, mr_mode, tab,
-                              tinv))
-            continue;
+          sap_sweep_fused(ex, g, colour, links, first ? eta : r, psi, L, kappa, first ? 1 : 2, nmr, mr_mode, tab,
+                          tinv);
+          continue;
         }
       }
       {

@@ -165,6 +165,20 @@ cudaError_t cudaGraphInstantiate(cudaGraphExec_t*, cudaGraph_t, unsigned long lo
 cudaError_t cudaGraphDestroy(cudaGraph_t) { return cudaSuccess; }
 cudaError_t cudaGraphLaunch(cudaGraphExec_t, cudaStream_t) { return cudaErrorNotSupported; }
 cudaError_t cudaGraphExecDestroy(cudaGraphExec_t) { return cudaSuccess; }
+// the device loop's conditional graph is refused too, so the solver falls back
+// to one host check per eager iteration
+cudaError_t cudaGraphCreate(cudaGraph_t*, unsigned int) { return cudaErrorNotSupported; }
+cudaError_t cudaGraphConditionalHandleCreate(cudaGraphConditionalHandle*, cudaGraph_t, unsigned int, unsigned int) {
+  return cudaErrorNotSupported;
+}
+cudaError_t cudaGraphAddNode(cudaGraphNode_t*, cudaGraph_t, const cudaGraphNode_t*, const cudaGraphEdgeData*, size_t,
+                             struct cudaGraphNodeParams*) {
+  return cudaErrorNotSupported;
+}
+cudaError_t cudaStreamBeginCaptureToGraph(cudaStream_t, cudaGraph_t, const cudaGraphNode_t*, const cudaGraphEdgeData*,
+                                          size_t, enum cudaStreamCaptureMode) {
+  return cudaErrorNotSupported;
+}
 cudaError_t cudaFuncSetAttribute(const void*, enum cudaFuncAttribute, int) { return cudaSuccess; }
 cudaError_t cudaOccupancyMaxActiveClusters(int* n, const void*, const cudaLaunchConfig_t*) {
   *n = 3;

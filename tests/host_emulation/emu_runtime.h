@@ -34,3 +34,7 @@ template <typename... P>
 cudaError_t cudaOccupancyMaxActiveClusters(int* n, void (*k)(P...), const cudaLaunchConfig_t* c) {
   return cudaOccupancyMaxActiveClusters(n, reinterpret_cast<const void*>(k), c);
 }
+
+// the device-side setter of a conditional graph node's value (the emulated
+// runtime refuses to build such graphs, so it is never reached)
+inline void cudaGraphSetConditional(cudaGraphConditionalHandle, unsigned int) {}

@@ -29,28 +29,28 @@ static Geom make_geom(const int* dims, const int* block) {
 
 template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
 static void run(const Geom& g, int colour, const float* links, const float* eta, float* psi, int L, float kappa,
-                int psi_zero, int nmr, int mode, const double* table, int nclusters, const float* tinv) {
+                int psi_mode, int nmr, int mode, const double* table, int nclusters, const float* tinv) {
   using SH = emu_dslash::SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   using C = cx<float>;
   emu_launch(nclusters, SH::CS, SH::NS, SH::smem_bytes(), [&] {
     if (tinv)
       emu_dslash::k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, 1>(g, colour, (const C*)links, (const C*)eta, (C*)psi,
-                                                                  L, kappa, psi_zero, nmr, mode, table, tinv);
+                                                                  L, kappa, psi_mode, nmr, mode, table, tinv);
     else
       emu_dslash::k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, 0>(g, colour, (const C*)links, (const C*)eta, (C*)psi,
-                                                                  L, kappa, psi_zero, nmr, mode, table, nullptr);
+                                                                  L, kappa, psi_mode, nmr, mode, table, nullptr);
   });
 }
 
 extern "C" int emu_sweep(const int* dims, const int* block, int colour, const float* links, const float* eta,
-                         float* psi, int L, float kappa, int psi_zero, int nmr, int mode, const double* table,
+                         float* psi, int L, float kappa, int psi_mode, int nmr, int mode, const double* table,
                          int nclusters, const float* tinv) {
   const Geom g = make_geom(dims, block);
   emu_bad_access = 0;
   const bool b8 = block[0] == 8 && block[1] == 8 && block[2] == 8 && block[3] == 8;
   const bool b4 = block[0] == 4 && block[1] == 4 && block[2] == 4 && block[3] == 4;
-  if (b8) run<8, 8, 8, 8, 1, 2, 2, 2>(g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table, nclusters, tinv);
-  else if (b4) run<4, 4, 4, 4, 1, 1, 1, 1>(g, colour, links, eta, psi, L, kappa, psi_zero, nmr, mode, table, nclusters,
+  if (b8) run<8, 8, 8, 8, 1, 2, 2, 2>(g, colour, links, eta, psi, L, kappa, psi_mode, nmr, mode, table, nclusters, tinv);
+  else if (b4) run<4, 4, 4, 4, 1, 1, 1, 1>(g, colour, links, eta, psi, L, kappa, psi_mode, nmr, mode, table, nclusters,
                                           tinv);
   else return -1;
   return emu_bad_access ? -2 : 0;  // -2: an access left the cluster or a shared-memory arena

@@ -37,13 +37,14 @@ def test_ctypes_structs_match_c_layout(tmp_path):
 #include <stdio.h>
 #include "mbicg.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mbicg_params), offsetof(mbicg_params, delta_ru),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mbicg_params), offsetof(mbicg_params, delta_ru),
          offsetof(mbicg_params, res_history), offsetof(mbicg_params, res_history_len),
          sizeof(mbicg_stats), offsetof(mbicg_stats, true_res_max),
          sizeof(mbicg_request_info), offsetof(mbicg_request_info, batch_columns),
          offsetof(mbicg_stats, graph_iterations), offsetof(mbicg_stats, precision_fallbacks),
          offsetof(mbicg_params, dummy_rhs), offsetof(mbicg_params, dummy_seed), offsetof(mbicg_params, clover),
-         offsetof(mbicg_params, domain_solver), offsetof(mbicg_params, nssor), offsetof(mbicg_params, ssor_omega));
+         offsetof(mbicg_params, domain_solver), offsetof(mbicg_params, nssor), offsetof(mbicg_params, ssor_omega),
+         offsetof(mbicg_stats, host_syncs));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -56,7 +57,8 @@ int main(void) {
             ctypes.sizeof(mb.mbicg_request_info), mb.mbicg_request_info.batch_columns.offset,
             mb.mbicg_stats.graph_iterations.offset, mb.mbicg_stats.precision_fallbacks.offset,
             mb.mbicg_params.dummy_rhs.offset, mb.mbicg_params.dummy_seed.offset, mb.mbicg_params.clover.offset,
-            mb.mbicg_params.domain_solver.offset, mb.mbicg_params.nssor.offset, mb.mbicg_params.ssor_omega.offset]
+            mb.mbicg_params.domain_solver.offset, mb.mbicg_params.nssor.offset, mb.mbicg_params.ssor_omega.offset,
+            mb.mbicg_stats.host_syncs.offset]
     assert got == want
 
 

@@ -59,8 +59,11 @@ def _oracle_layout(a):
     return np.ascontiguousarray(a.transpose(0, 2, 1)).reshape(a.shape[0], 4, 3, -1).astype(np.complex128)
 
 
-def _sap_emulated(lib, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nclusters, tinv=None):
-    """ncycle cycles of E and O sweeps, as the library's driver launches them;
+def _sap_emulated(lib, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nclusters, oracle_mod, tinv=None,
+                  Ti=None):
+    """ncycle cycles of E and O sweeps, as the library's driver launches them:
+    before every sweep but the first the colour's residual eta - A psi (here
+    from the oracle's operator, in place of the library's residual kernel);
     mode 3 replays the step lengths omegas[it] on every domain."""
     L = eta.shape[3]
     links = np.ascontiguousarray(U.astype(np.complex64))
@@ -75,8 +78,16 @@ def _sap_emulated(lib, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nc
     tp = table.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if table is not None else None
     for cyc in range(ncycle):
         for colour in (0, 1):
-            rc = lib.emu_sweep(_iv(dims), _iv(block), colour, _fp(links), _fp(e), _fp(psi), L, kappa,
-                               int(cyc == 0 and colour == 0), nmr, mode, tp, nclusters,
+            first = cyc == 0 and colour == 0
+            if first:
+                r = e
+            else:
+                p64 = _oracle_layout(psi)
+                Ap = oracle_mod.apply_D(dims, U, kappa, p64) if Ti is None else oracle_mod.apply_A(dims, U, kappa,
+                                                                                                    Ti, p64)
+                r = _internal32(eta - Ap)
+            rc = lib.emu_sweep(_iv(dims), _iv(block), colour, _fp(links), _fp(r), _fp(psi), L, kappa,
+                               1 if first else 2, nmr, mode, tp, nclusters,
                                _fp(tinv) if tinv is not None else None)
             assert rc == 0
     return _oracle_layout(psi)
@@ -101,7 +112,7 @@ def test_fused_sweep_matches_oracle(sweep, oracle_mod, dims, block, L, ncycle, n
     eta = synth.gaussian_source(dims, L, seed=72)
     kappa = 0.125
     omegas = np.array([0.9 + 0.05j, 1.1 - 0.02j, 0.95 + 0.01j])[:nmr]
-    got = _sap_emulated(sweep, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nclusters)
+    got = _sap_emulated(sweep, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nclusters, oracle_mod)
     assert not np.isnan(got).any()
     if mode == 0:
         ref = oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, eta, mr_mode=oracle_mod.MR_COLUMN)
@@ -141,7 +152,8 @@ def test_fused_sweep_with_clover_matches_oracle(sweep, oracle_mod, dims, block, 
     kappa = 0.125
     Ti = oracle_mod.clover_inverse(oracle_mod.clover(dims, U, kappa, 1.3))
     omegas = np.array([0.9 + 0.05j, 1.1 - 0.02j, 0.95 + 0.01j])[:nmr]
-    got = _sap_emulated(sweep, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nclusters, tinv=_pack_herm(Ti))
+    got = _sap_emulated(sweep, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nclusters, oracle_mod,
+                        tinv=_pack_herm(Ti), Ti=Ti)
     assert not np.isnan(got).any()
     if mode == 0:
         ref = oracle_mod.sap_ext(dims, block, U, kappa, ncycle, eta, Tinv=Ti, solver=oracle_mod.DOMAIN_MR, nmr=nmr,
