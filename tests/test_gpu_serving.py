@@ -1,7 +1,8 @@
 """The request server (include/mbicg.h, serving): columns of several requests
 packed into one block solve give the same solutions as each request solved
-alone, within the solver's tolerance; slots of one field and of different
-fields solve concurrently; compatible requests only are packed."""
+alone, and as the oracle's solve of the same system (Algorithm 1), within
+the solver's tolerance; slots of one field and of different fields solve
+concurrently; compatible requests only are packed."""
 import threading
 
 import numpy as np
@@ -21,6 +22,14 @@ def params():
     return mb.mbicg_default_params(block=(4, 4, 4, 4), ncycle=4, nmr=4, max_iter=2000)
 
 
+def oracle_X(oracle_mod, dims, U, B, kappa=KAPPA):
+    """The oracle's solution of A X = B (no preconditioner: X does not depend
+    on it), to 1e-12."""
+    r = oracle_mod.block_bicgstab(dims, U, kappa, B, 1e-12, max_iter=3000)
+    assert r["status"] == 0
+    return r["X"]
+
+
 def solve(srv, field, B, L, kappa=KAPPA):
     rid = mb.mbicg_server_submit(srv, field, B, L, kappa, TOL)
     X = np.empty_like(B)
@@ -28,11 +37,12 @@ def solve(srv, field, B, L, kappa=KAPPA):
     return st, X, tres, info
 
 
-def test_packed_columns_equal_solo_solves():
+def test_packed_columns_equal_solo_solves(oracle_mod):
     srv = mb.mbicg_server_create(0, 60.0)
     try:
-        f1 = mb.mbicg_server_add_field(srv, F1, synth.su3_links(F1, 0.5, 901), params(), 1)
-        f2 = mb.mbicg_server_add_field(srv, F2, synth.su3_links(F2, 0.5, 902), params(), 1)
+        U1, U2 = synth.su3_links(F1, 0.5, 901), synth.su3_links(F2, 0.5, 902)
+        f1 = mb.mbicg_server_add_field(srv, F1, U1, params(), 1)
+        f2 = mb.mbicg_server_add_field(srv, F2, U2, params(), 1)
         B0 = synth.gaussian_source(F1, 3, seed=910)
         B1 = synth.gaussian_source(F1, 4, seed=911)
         B2 = synth.gaussian_source(F1, 5, seed=912)
@@ -58,6 +68,12 @@ def test_packed_columns_equal_solo_solves():
         # the same solution alone and in the mix: both within tol of A^-1 b,
         # so they differ by at most cond * tol; 1e-7 is the stated bound
         assert rel_col_norm(res[0][0], X0) < 1e-7
+        # and every request's columns against the oracle's solve of its system
+        assert rel_col_norm(X0, oracle_X(oracle_mod, F1, U1, B0)) < 1e-7
+        assert rel_col_norm(res[0][0], oracle_X(oracle_mod, F1, U1, B0)) < 1e-7
+        assert rel_col_norm(res[1][0], oracle_X(oracle_mod, F1, U1, B1)) < 1e-7
+        assert rel_col_norm(res[2][0], oracle_X(oracle_mod, F1, U1, B2)) < 1e-7
+        assert rel_col_norm(res[3][0], oracle_X(oracle_mod, F2, U2, B3)) < 1e-7
         # field 2's solve overlapped field 1's block
         a, b = res[0][1], res[3][1]
         assert a["start_ms"] < b["done_ms"] and b["start_ms"] < a["done_ms"]
@@ -67,20 +83,22 @@ def test_packed_columns_equal_solo_solves():
         mb.mbicg_server_destroy(srv)
 
 
-def test_two_slots_of_one_field_overlap_and_kappas_are_not_mixed():
+def test_two_slots_of_one_field_overlap_and_kappas_are_not_mixed(oracle_mod):
     srv = mb.mbicg_server_create(0, 60.0)
     try:
-        f = mb.mbicg_server_add_field(srv, F1, synth.su3_links(F1, 0.5, 903), params(), 2)
+        U = synth.su3_links(F1, 0.5, 903)
+        f = mb.mbicg_server_add_field(srv, F1, U, params(), 2)
         B = [synth.gaussian_source(F1, 6, seed=920 + i) for i in range(4)]
         mb.mbicg_server_hold(srv, True)
         ids = [mb.mbicg_server_submit(srv, f, B[0], 6, 0.12, TOL), mb.mbicg_server_submit(srv, f, B[1], 6, 0.125, TOL),
                mb.mbicg_server_submit(srv, f, B[2], 6, 0.12, TOL), mb.mbicg_server_submit(srv, f, B[3], 6, 0.125, TOL)]
         mb.mbicg_server_hold(srv, False)
         infos = []
-        for rid, b in zip(ids, B):
+        for rid, b, kappa in zip(ids, B, (0.12, 0.125, 0.12, 0.125)):
             X = np.empty_like(b)
             st, it, tres, info = mb.mbicg_server_wait(srv, rid, X, 6)
             assert st == mb.MBICG_OK and max(tres) <= TOL
+            assert rel_col_norm(X, oracle_X(oracle_mod, F1, U, b, kappa)) < 1e-7
             infos.append(info)
         # requests 0 and 2 (kappa 0.12) share a block, 1 and 3 (0.125) another
         assert [i["batch_columns"] for i in infos] == [12, 12, 12, 12]
@@ -90,7 +108,7 @@ def test_two_slots_of_one_field_overlap_and_kappas_are_not_mixed():
         mb.mbicg_server_destroy(srv)
 
 
-def test_concurrent_submitters_and_bad_requests():
+def test_concurrent_submitters_and_bad_requests(oracle_mod):
     srv = mb.mbicg_server_create(0, 60.0)
     try:
         f = mb.mbicg_server_add_field(srv, F2, synth.su3_links(F2, 0.5, 904), params(), 2)
@@ -112,14 +130,10 @@ def test_concurrent_submitters_and_bad_requests():
             t.start()
         for t in th:
             t.join()
-        ref_ctx = mb.mbicg_create(F2)
-        mb.mbicg_load_gauge(ref_ctx, synth.su3_links(F2, 0.5, 904))
+        U = synth.su3_links(F2, 0.5, 904)
         for i, (b, (st, X, tres, info)) in out.items():
             assert st == mb.MBICG_OK and max(tres) <= TOL
-            Xs = np.empty_like(b)
-            st2, _, tr2 = mb.mbicg_block_solve(ref_ctx, b, Xs, b.shape[-1], KAPPA, TOL, params())
-            assert st2 == mb.MBICG_OK and rel_col_norm(X, Xs) < 1e-7
-        mb.mbicg_destroy(ref_ctx)
+            assert rel_col_norm(X, oracle_X(oracle_mod, F2, U, b)) < 1e-7
     finally:
         mb.mbicg_server_destroy(srv)
 

@@ -174,24 +174,45 @@ def test_profiling_counts_kernels():
         mb.mbicg_destroy(ctx)
 
 
-def test_graph_replay_gives_the_eager_solution(monkeypatch):
-    """Once the frozen step lengths are recorded the loop is replayed from one
-    captured CUDA graph; the kernels and their order are the same, so the
-    solution and the iteration count are bit-identical to eager launches."""
+@pytest.mark.parametrize("prec", [mb.MBICG_FP32, mb.MBICG_FP64])
+def test_graph_replay_gives_the_eager_solution(monkeypatch, prec):
+    """Once the frozen step lengths are recorded the loop runs on the device:
+    one captured CUDA graph whose conditional WHILE node repeats the iteration
+    while the device's own test of Algorithm 2's WHILE condition holds, so
+    the host waits only when the loop stops (convergence, a reliable update).
+    The kernels and their order are the same as with one graph launch and one
+    host check per iteration (MBICG_DEVICE_LOOP=0) and as eager launches
+    (MBICG_GRAPHS=0): the solution, the iteration count and the residual
+    history are bit-identical."""
     dims, L = (8, 8, 8, 16), 4
     ctx, U = make_ctx(dims, 0.5, seed=81)
     try:
         B = synth.gaussian_source(dims, L, seed=82)
-        p = mb.mbicg_default_params(block=(4, 4, 4, 4), max_iter=500)
-        X1, X2 = np.empty_like(B), np.empty_like(B)
-        st1, it1, _ = mb.mbicg_block_solve(ctx, B, X1, L, 0.125, 1e-10, p)
-        g1 = mb.mbicg_get_stats(ctx)["graph_iterations"]
-        monkeypatch.setenv("MBICG_GRAPHS", "0")
-        st2, it2, _ = mb.mbicg_block_solve(ctx, B, X2, L, 0.125, 1e-10, p)
-        g2 = mb.mbicg_get_stats(ctx)["graph_iterations"]
-        assert st1 == st2 == mb.MBICG_OK and it1 == it2
-        assert g1 >= it1 - 2 and g2 == 0
-        assert np.array_equal(X1, X2)
+        runs = []
+        # one cycle of two MR steps and kappa 0.135: enough iterations for the
+        # device loop to run several in a row
+        for env in ({}, {"MBICG_DEVICE_LOOP": "0"}, {"MBICG_GRAPHS": "0"}):
+            for k in ("MBICG_DEVICE_LOOP", "MBICG_GRAPHS"):
+                monkeypatch.delenv(k, raising=False)
+            for k, v in env.items():
+                monkeypatch.setenv(k, v)
+            p, hist = history_params(500, block=(4, 4, 4, 4), ncycle=1, nmr=2, max_iter=500, prec_D=prec,
+                                     prec_sap=prec)
+            X = np.empty_like(B)
+            st, it, _ = mb.mbicg_block_solve(ctx, B, X, L, 0.135, 1e-10, p)
+            assert st == mb.MBICG_OK
+            runs.append((X, it, np.array(hist[:it]), mb.mbicg_get_stats(ctx)))
+        (X1, it1, h1, s1), (X2, it2, h2, s2), (X3, it3, h3, s3) = runs
+        assert it1 == it2 == it3
+        assert np.array_equal(X1, X2) and np.array_equal(X1, X3)
+        assert np.array_equal(h1, h2) and np.array_equal(h1, h3)
+        assert s1["graph_iterations"] >= it1 - 2 and s2["graph_iterations"] >= it1 - 2
+        assert s3["graph_iterations"] == 0
+        # one host wait per iteration without the device loop; with it, one per
+        # stop of the loop (a reliable update, a restart, the final check)
+        assert s2["host_syncs"] >= it2
+        stops = s1["reliable_updates"] + s1["restarts"] + 1
+        assert s2["host_syncs"] - s1["host_syncs"] >= s1["graph_iterations"] - stops
     finally:
         mb.mbicg_destroy(ctx)
 
