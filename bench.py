@@ -104,7 +104,7 @@ def sap_sweep_flops(V, L, nmr, frozen=True):
 
 
 # DRAM bytes per launch of the dominant kernel at the benchmark workload, from one
-# ncu capture (profiles/dram_traffic_wilson_32c64_L12.md), valid only for the
+# ncu capture of dram__bytes_read.sum + dram__bytes_write.sum, valid only for the
 # kernel source it was taken on (a hash of csrc/dslash.cu and csrc/common.cuh,
 # first 16 hex digits)
 NCU_TRAFFIC = {("sap_sweep", "wilson_32c64_L12"): {"bytes": 4.970e9, "source_sha256": "f3e1f38c88f3a05a"}}
@@ -262,6 +262,63 @@ def run_serving(device=0):
 
 
 # ---------------------------------------------------------------------------
+# Table 1 / Fig. 2 of Sec. 3.3: the 12 sources solved as 12/L blocks of L
+# ---------------------------------------------------------------------------
+def run_table1(ctx, cfg, dB, block_sizes=(1, 2, 3, 4, 6, 12)):
+    """Solve the workload's 12 right-hand sides as 12/L block solves of L
+    columns each, for every L of Table 1, on the resident gauge field; report
+    per L the time for all 12 (CUDA events), the iterations of each block,
+    NMVM (operator applications on single vectors in the Krylov loop: 2 L per
+    iteration, plus L for the initial residual), RHS solves/s, and the
+    recursive residual history of the first block (Fig. 2)."""
+    import ctypes
+
+    import torch
+
+    import paper_1104_0737_gb300 as mb
+
+    out = []
+    nrhs = dB.shape[-1]
+    for L in block_sizes:
+        if nrhs % L:
+            continue
+        hist = (ctypes.c_double * 5000)()
+        iters, nmvm, tres = [], 0, 0.0
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record()
+        for b in range(nrhs // L):
+            p = mb.mbicg_default_params(ncycle=cfg["ncycle"], nmr=cfg["nmr"], block=cfg["block"],
+                                        mr_mode=mb.MBICG_MR_FROZEN, prec_D=mb.MBICG_FP32,
+                                        prec_sap=mb.MBICG_FP32, max_iter=5000)
+            if b == 0:
+                p.res_history = hist
+                p.res_history_len = 5000
+            bb = dB[..., b * L:(b + 1) * L].contiguous()
+            xx = torch.empty_like(bb)
+            st, it, tr = mb.mbicg_block_solve(ctx, bb, xx, L, cfg["kappa"], cfg["tol"], p)
+            if st != mb.MBICG_OK:
+                raise RuntimeError(f"table-1 solve failed: L={L} block {b} status {st}")
+            iters.append(it)
+            nmvm += 2 * L * it + L
+            tres = max(tres, max(tr))
+        t1.record()
+        torch.cuda.synchronize()
+        sec = t0.elapsed_time(t1) / 1e3
+        k = iters[0]
+        out.append({"L": L, "blocks": nrhs // L, "time_s": sec, "rhs_per_s": nrhs / sec, "iters": iters,
+                    "nmvm": nmvm, "true_res_max": tres,
+                    "history_first_block": [float(hist[i]) for i in range(min(k, 5000))]})
+    t_l1 = next((r["time_s"] for r in out if r["L"] == 1), None)
+    n_l1 = next((r["nmvm"] for r in out if r["L"] == 1), None)
+    for r in out:
+        r["time_gain"] = t_l1 / r["time_s"] if t_l1 else None
+        r["nmvm_gain"] = n_l1 / r["nmvm"] if n_l1 else None
+    return out
+
+
+# ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
 def oracle_sample(cfg, iters_full, n_iter=2):
@@ -363,6 +420,8 @@ def main():
                     help="skip the Poisson request stream on three resident fields")
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="skip the plain FP64 one-RHS-at-a-time solve timed on the same GPU")
+    ap.add_argument("--table1", action="store_true",
+                    help="also solve the 12 sources as 12/L blocks of L = 1, 2, 3, 4, 6, 12 (Table 1, Fig. 2)")
     args = ap.parse_args()
     cfg = dict(WORKLOADS[args.workload])
     if args.kappa is not None:
@@ -437,7 +496,8 @@ def main():
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    graph_iters = mb.mbicg_get_stats(ctx)["graph_iterations"]
+    last_stats = mb.mbicg_get_stats(ctx)
+    graph_iters = last_stats["graph_iterations"]
     # per-kernel times from one more solve with CUDA events around every launch
     # group (outside the timed region: profiling runs the loop without its graph)
     mb.mbicg_set_profiling(ctx, True)
@@ -513,6 +573,10 @@ def main():
         fp64_arm = {"value": 1.0 / dt, "unit": UNIT, "iters": it1, "status": st,
                     "sample": "one FP64 L=1 solve (column 0), FP64 operator and SAP"}
 
+    table1 = None
+    if args.table1 and rank == 0:
+        table1 = run_table1(ctx, cfg, dB)
+
     mb.mbicg_destroy(ctx)
     del dB, dX
     serving = None
@@ -528,6 +592,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "iters": iters, "true_res_max": tres_max, "graph_iterations_last_step": graph_iters,
+            "host_syncs_last_step": last_stats["host_syncs"],
+            "reliable_updates_last_step": last_stats["reliable_updates"],
             "dslash_hbm_frac": dslash_frac,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "kernel_ms": {k: v[0] for k, v in prof.items()},
@@ -537,6 +603,8 @@ def main():
             out["fp64_one_rhs_arm"] = fp64_arm
         if serving:
             out["serving"] = serving
+        if table1:
+            out["table1"] = table1
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
