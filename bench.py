@@ -39,10 +39,11 @@ import synth  # noqa: E402
 # ---------------------------------------------------------------------------
 WORKLOADS = {
     # 32^3 x 64, eps 0.5 links, L = 12 point sources, SAP 8^4, mixed precision.
-    # kappa: chosen from a scan of kappa on this field so that the
-    # unpreconditioned BiCGSTAB (L = 1) needs more than 2000 iterations.
+    # kappa: from a scan of kappa on this field, unpreconditioned BiCGSTAB
+    # (L = 1, the first point source) needs 2970 iterations at 0.14774 (1971 at
+    # 0.1477, 2947 at 0.14773) and diverges at 0.14775.
     "wilson_32c64_L12": dict(dims=(32, 32, 32, 64), eps=0.5, gauge_seed=1003, L=12, source="point",
-                             kappa=0.14775, block=(8, 8, 8, 8), ncycle=4, nmr=4, tol=1e-10),
+                             kappa=0.14774, block=(8, 8, 8, 8), ncycle=4, nmr=4, tol=1e-10),
     # smaller lattices of the same family, for quick runs
     "wilson_16c32_L12": dict(dims=(16, 16, 16, 32), eps=0.5, gauge_seed=1002, L=12, source="point",
                              kappa=0.128, block=(8, 8, 8, 8), ncycle=4, nmr=4, tol=1e-10),
@@ -264,7 +265,7 @@ def run_serving(device=0):
 # ---------------------------------------------------------------------------
 # Table 1 / Fig. 2 of Sec. 3.3: the 12 sources solved as 12/L blocks of L
 # ---------------------------------------------------------------------------
-def run_table1(ctx, cfg, dB, block_sizes=(1, 2, 3, 4, 6, 12)):
+def run_table1(ctx, cfg, dB, prec_sap, block_sizes=(1, 2, 3, 4, 6, 12)):
     """Solve the workload's 12 right-hand sides as 12/L block solves of L
     columns each, for every L of Table 1, on the resident gauge field; report
     per L the time for all 12 (CUDA events), the iterations of each block,
@@ -291,7 +292,7 @@ def run_table1(ctx, cfg, dB, block_sizes=(1, 2, 3, 4, 6, 12)):
         for b in range(nrhs // L):
             p = mb.mbicg_default_params(ncycle=cfg["ncycle"], nmr=cfg["nmr"], block=cfg["block"],
                                         mr_mode=mb.MBICG_MR_FROZEN, prec_D=mb.MBICG_FP32,
-                                        prec_sap=mb.MBICG_FP32, max_iter=5000)
+                                        prec_sap=prec_sap, max_iter=5000)
             if b == 0:
                 p.res_history = hist
                 p.res_history_len = 5000
@@ -399,7 +400,8 @@ def _cfg_public(cfg):
     return {"lattice": "x".join(map(str, cfg["dims"])), "L": cfg["L"], "source": cfg["source"],
             "kappa": cfg["kappa"], "eps": cfg["eps"], "sap_block": "x".join(map(str, cfg["block"])),
             "ncycle": cfg["ncycle"], "nmr": cfg["nmr"], "tol": cfg["tol"],
-            "precision": "FP32 operator/SAP/Krylov vectors, FP64 X, QR, LxL, true residual",
+            "precision": "FP32 operator/Krylov vectors, SAP FP32 arithmetic with " + cfg.get("sap_storage", "FP32")
+                         + " storage, FP64 X, QR, LxL, true residual",
             "l2": "inputs larger than L2 (4.8 GB per block)"}
 
 
@@ -420,12 +422,20 @@ def main():
                     help="skip the Poisson request stream on three resident fields")
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="skip the plain FP64 one-RHS-at-a-time solve timed on the same GPU")
+    ap.add_argument("--prec-sap", default="fp32", choices=["fp32", "fp16"],
+                    help="storage of the preconditioner's blocks in the timed solve")
+    ap.add_argument("--no-alt-storage", action="store_true",
+                    help="skip the line of the other preconditioner storage (FP16 / FP32)")
+    ap.add_argument("--kappa-scan", default=None,
+                    help="comma-separated kappas: iterations of the unpreconditioned solve (L = 1, the first "
+                         "source, FP32 Krylov vectors with reliable updates) on the workload's field, then exit")
     ap.add_argument("--table1", action="store_true",
                     help="also solve the 12 sources as 12/L blocks of L = 1, 2, 3, 4, 6, 12 (Table 1, Fig. 2)")
     args = ap.parse_args()
     cfg = dict(WORKLOADS[args.workload])
     if args.kappa is not None:
         cfg["kappa"] = args.kappa
+    cfg["sap_storage"] = args.prec_sap.upper()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -452,12 +462,24 @@ def main():
     ctx = mb.mbicg_create(dims, device=local, stream=stream)
     mb.mbicg_load_gauge(ctx, U)
     del U
+    prec_sap = {"fp32": mb.MBICG_FP32, "fp16": mb.MBICG_FP16}[args.prec_sap]
     params = mb.mbicg_default_params(ncycle=cfg["ncycle"], nmr=cfg["nmr"], block=cfg["block"],
                                      mr_mode=mb.MBICG_MR_FROZEN, prec_D=mb.MBICG_FP32,
-                                     prec_sap=mb.MBICG_FP32, max_iter=5000)
+                                     prec_sap=prec_sap, max_iter=5000)
     dB = torch.from_numpy(B).to(f"cuda:{local}")
     dX = torch.empty_like(dB)
     torch.cuda.synchronize()
+    if args.kappa_scan:
+        # how hard the workload is without a preconditioner, per kappa
+        b1 = dB[..., :1].contiguous()
+        x1 = torch.empty_like(b1)
+        for kappa in [float(k) for k in args.kappa_scan.split(",")]:
+            p0 = mb.mbicg_default_params(ncycle=0, max_iter=12000)
+            st, it, tr = mb.mbicg_block_solve(ctx, b1, x1, 1, kappa, cfg["tol"], p0)
+            print(json.dumps({"kappa": kappa, "unpreconditioned_iters": it, "status": st, "true_res": tr[0]}),
+                  flush=True)
+        mb.mbicg_destroy(ctx)
+        return
 
     def solve(b, x):
         st, it, tres = mb.mbicg_block_solve(ctx, b, x, L, cfg["kappa"], cfg["tol"], params)
@@ -573,9 +595,35 @@ def main():
         fp64_arm = {"value": 1.0 / dt, "unit": UNIT, "iters": it1, "status": st,
                     "sample": "one FP64 L=1 solve (column 0), FP64 operator and SAP"}
 
+    # the same workload with the preconditioner's blocks in the other storage
+    # (FP16 with per-(site, column) scales, or FP32), timed the same way
+    alt = None
+    if not args.no_alt_storage and rank == 0:
+        other = "fp16" if args.prec_sap == "fp32" else "fp32"
+        pa = mb.mbicg_default_params(ncycle=cfg["ncycle"], nmr=cfg["nmr"], block=cfg["block"],
+                                     mr_mode=mb.MBICG_MR_FROZEN, prec_D=mb.MBICG_FP32,
+                                     prec_sap={"fp32": mb.MBICG_FP32, "fp16": mb.MBICG_FP16}[other],
+                                     max_iter=4 * max(iters) + 50)
+        st, it_a, tr_a = mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], pa)  # warm-up
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record()
+            its, trs = [], []
+            for _ in range(max(1, min(args.steps, 3))):
+                st, it_a, tr_a = mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], pa)
+                its.append(it_a)
+                trs.append(max(tr_a))
+            a1.record()
+        torch.cuda.synchronize()
+        ms = a0.elapsed_time(a1) / len(its)
+        alt = {"prec_sap": other, "value": L * 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "iters": its,
+               "true_res_max": max(trs), "status": st}
+
     table1 = None
     if args.table1 and rank == 0:
-        table1 = run_table1(ctx, cfg, dB)
+        table1 = run_table1(ctx, cfg, dB, prec_sap)
 
     mb.mbicg_destroy(ctx)
     del dB, dX
@@ -605,6 +653,8 @@ def main():
             out["serving"] = serving
         if table1:
             out["table1"] = table1
+        if alt:
+            out["alt_storage_line"] = alt
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()

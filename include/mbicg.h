@@ -77,7 +77,15 @@ typedef struct {
   int nmr;
   int block[4];
   int mr_mode;      /* mbicg_mr_mode */
-  int prec_sap;     /* MBICG_FP32 (default) or MBICG_FP64 */
+  int prec_sap;     /* MBICG_FP32 (default), MBICG_FP64, or MBICG_FP16: the
+                       preconditioner's blocks (its input, output, residual
+                       and psi) stored in HBM as FP16 spinors times one FP32
+                       scale per (site, column), FP32 arithmetic and links,
+                       the MR state on chip in FP32.  FP16 needs 8^4 or 4^4
+                       domains, SU(3) links, the Wilson matrix, MR domain
+                       solves with MBICG_MR_COLUMN or MBICG_MR_FROZEN (a
+                       frozen table is recorded in FP32, then replayed in
+                       FP16) and, in a block solve, prec_D = MBICG_FP32 */
   /* Krylov loop (Algorithm 2 of Sec. 2.1). */
   int prec_D;       /* operator and Krylov vectors: MBICG_FP64 (the paper's
                        double-precision outer solver) or MBICG_FP32 with FP64

@@ -262,6 +262,10 @@ struct Solver {
   // Jacobi-preconditioned clover matrix: T^{-1} per site (NULL: Wilson)
   const double* ti64 = nullptr;
   const float* ti32 = nullptr;
+  // the preconditioner in FP16 storage (prec_sap = MBICG_FP16, FP32 Krylov
+  // vectors): its blocks once the frozen step lengths replay
+  bool sap16 = false;
+  SapHalf sh{};
   double *gpart, *npart;
   double h_norm[MAXL + 1];
   double bnorm[MAXL];
@@ -312,6 +316,13 @@ struct Solver {
         if ((rc = buf(c, "ssor_levels", (size_t)g.Vd, &sw.levels))) return rc;
         CK(sap_prepare_ssor(g, sw, c->stream));
       }
+      if (sap16) {
+        const size_t nsp = (size_t)V * L;
+        if ((rc = buf(c, "h16_eta", nl, &sh.eta)) || (rc = buf(c, "h16_eta_sc", nsp, &sh.eta_sc)) ||
+            (rc = buf(c, "h16_psi", nl, &sh.psi)) || (rc = buf(c, "h16_psi_sc", nsp, &sh.psi_sc)) ||
+            (rc = buf(c, "h16_r", nl, &sh.r)) || (rc = buf(c, "h16_r_sc", nsp, &sh.r_sc)))
+          return rc;
+      }
       // every frozen step length starts unrecorded (NaN), unless this solve
       // continues another one with the same preconditioner
       if (!keep_table)
@@ -351,6 +362,22 @@ struct Solver {
       mode = table_complete ? 3 : 2;
       tab = table;
       if (!table_complete) CK(cudaMemsetAsync(unset, 0, sizeof(int), c->stream));
+    }
+    if constexpr (std::is_same<T, float>::value) {
+      if (sap16 && (mode == 0 || mode == 3)) {
+        // FP16 storage: P (or R) rounded into FP16 blocks, M applied on them
+        // with FP32 arithmetic, the result widened into U (or S)
+        {
+          Timed t(ex, KC_CONVERT);
+          block_to_half(ex, V * L, reinterpret_cast<const cx<float>*>(in), sh.eta, sh.eta_sc);
+        }
+        sap_apply_h(ex, g, c->U32, sh, L, kappa, p.ncycle, p.nmr, mode, tab, tinv<float>());
+        {
+          Timed t(ex, KC_CONVERT);
+          half_to_block(ex, V * L, sh.psi, sh.psi_sc, reinterpret_cast<cx<float>*>(out));
+        }
+        return check_launch(c, "apply_M");
+      }
     }
     if constexpr (std::is_same<T, TS>::value) {
       sap_apply<TS>(ex, g, links_S(), in, out, L, kappa, p.ncycle, p.nmr, mode, tab, unset, sw, tinv<TS>(), ssor);
@@ -810,12 +837,23 @@ int check_params(mbicg_ctx* c, int L, const mbicg_params* p, bool solve, bool fr
     } else if (p->mr_mode < 0 || p->mr_mode > 2 || (!frozen && p->mr_mode == MBICG_MR_FROZEN)) {
       return fail(c, MBICG_EINVAL, "bad mr_mode");
     }
-    if (p->prec_sap != MBICG_FP32 && p->prec_sap != MBICG_FP64)
-      return fail(c, MBICG_EINVAL, "prec_sap must be MBICG_FP32 or MBICG_FP64");
+    if (p->prec_sap != MBICG_FP32 && p->prec_sap != MBICG_FP64 && p->prec_sap != MBICG_FP16)
+      return fail(c, MBICG_EINVAL, "prec_sap must be MBICG_FP32, MBICG_FP64 or MBICG_FP16");
+    if (p->prec_sap == MBICG_FP16) {
+      if (p->domain_solver != MBICG_DOMAIN_MR || p->mr_mode == MBICG_MR_BLOCK || p->clover)
+        return fail(c, MBICG_EINVAL, "FP16 storage of the preconditioner takes MR domain solves with "
+                                     "MBICG_MR_COLUMN or MBICG_MR_FROZEN and the Wilson matrix");
+      Geom g16 = lattice_geom(c, p->block);
+      g16.su3 = 1;
+      if (!sap_sweep_fusable(g16, 3) || (c->gauge && !c->su3))
+        return fail(c, MBICG_EINVAL, "FP16 storage of the preconditioner needs 8^4 or 4^4 domains and SU(3) links");
+    }
   }
   if (solve) {
     if (p->prec_D != MBICG_FP32 && p->prec_D != MBICG_FP64)
       return fail(c, MBICG_EINVAL, "prec_D must be MBICG_FP32 or MBICG_FP64");
+    if (p->ncycle > 0 && p->prec_sap == MBICG_FP16 && p->prec_D != MBICG_FP32)
+      return fail(c, MBICG_EINVAL, "FP16 storage of the preconditioner needs prec_D = MBICG_FP32");
     if (p->max_iter < 0) return fail(c, MBICG_EINVAL, "max_iter < 0");
     if (!(p->delta_ru > 0 && p->delta_ru < 1)) return fail(c, MBICG_EINVAL, "delta_ru must be in (0, 1)");
   }
@@ -840,6 +878,7 @@ int run_solve(mbicg_ctx* c, const cx<double>* dB, cx<double>* dX, int L, double 
     s.ti64 = c->Ti64;
     s.ti32 = c->Ti32;
   }
+  s.sap16 = p->ncycle > 0 && p->prec_sap == MBICG_FP16 && std::is_same<T, float>::value;
   for (int i = 0; i < L; ++i) s.bnorm[i] = bnorm[i];
   return s.run(dB, dX, tol, iters, true_res);
 }
@@ -1253,8 +1292,30 @@ int sap_precond_impl(mbicg_ctx* c, const double* in, double* out, int L, double 
     const R* tinv = nullptr;
     if (p->clover) tinv = reinterpret_cast<const R*>(sizeof(R) == 8 ? static_cast<const void*>(c->Ti64)
                                                                      : static_cast<const void*>(c->Ti32));
-    sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, mode, dtab, unset, w, tinv,
-                 p->domain_solver == MBICG_DOMAIN_SSOR ? &sp : nullptr);
+    bool done = false;
+    if constexpr (std::is_same<R, float>::value) {
+      if (p->prec_sap == MBICG_FP16 && (mode == 0 || mode == 3)) {
+        // FP16 storage of the preconditioner's blocks (a table still being
+        // recorded is recorded by the FP32 path below)
+        SapHalf h{};
+        const size_t nsp = (size_t)c->V * L;
+        if ((rc2 = buf(c, "h16_eta", nl, &h.eta)) || (rc2 = buf(c, "h16_eta_sc", nsp, &h.eta_sc)) ||
+            (rc2 = buf(c, "h16_psi", nl, &h.psi)) || (rc2 = buf(c, "h16_psi_sc", nsp, &h.psi_sc)) ||
+            (rc2 = buf(c, "h16_r", nl, &h.r)) || (rc2 = buf(c, "h16_r_sc", nsp, &h.r_sc)))
+          return rc2;
+        {
+          Timed t(ex, KC_CONVERT);
+          block_to_half(ex, (long long)nsp, a, h.eta, h.eta_sc);
+        }
+        sap_apply_h(ex, g, links, h, L, kappa, p->ncycle, p->nmr, mode, dtab);
+        Timed t(ex, KC_CONVERT);
+        half_to_block(ex, (long long)nsp, h.psi, h.psi_sc, b);
+        done = true;
+      }
+    }
+    if (!done)
+      sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, mode, dtab, unset, w, tinv,
+                   p->domain_solver == MBICG_DOMAIN_SSOR ? &sp : nullptr);
     Timed t(ex, KC_CONVERT);
     internal_to_abi<R>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
     // the level table's host copy lives in w: wait for its upload before w goes

@@ -10,6 +10,7 @@
 // Sites are numbered lexicographically, s = x + Lx*(y + Ly*(z + Lz*t)).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -105,6 +106,47 @@ __device__ __forceinline__ void store_spinor(cx<double>* p, const Spinor<double>
   double2* q = reinterpret_cast<double2*>(p);
 #pragma unroll
   for (int k = 0; k < 12; ++k) q[k] = make_double2((&s.c[0][0])[k].re, (&s.c[0][0])[k].im);
+}
+
+// FP16 storage of a spinor (the FP16-storage operator and the preconditioner's
+// FP16 blocks): 12 __half2 (re, im) q times one FP32 scale s, the largest |re|
+// or |im| of the spinor, so every stored half lies in [-1, 1].
+__device__ __forceinline__ void load_spinor_h(const __half2* __restrict__ q, float s, Spinor<float>& v) {
+  const uint4* p = reinterpret_cast<const uint4*>(q);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint4 w = __ldg(p + k);
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      __half2 h;
+      memcpy(&h, &u[e], 4);
+      const float2 f = __half22float2(h);
+      (&v.c[0][0])[4 * k + e] = mk(f.x * s, f.y * s);
+    }
+  }
+}
+
+// rounds v into (q, s): s = max |re|, |im|; q = v / s to nearest FP16
+__device__ __forceinline__ void store_spinor_h(__half2* __restrict__ q, float* __restrict__ s,
+                                               const Spinor<float>& v) {
+  float m = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const cx<float> c = (&v.c[0][0])[k];
+    m = fmaxf(m, fmaxf(fabsf(c.re), fabsf(c.im)));
+  }
+  uint32_t u[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const cx<float> c = (&v.c[0][0])[k];
+    const __half2 h = m > 0.0f ? __floats2half2_rn(c.re / m, c.im / m) : __floats2half2_rn(0.0f, 0.0f);
+    memcpy(&u[k], &h, 4);
+  }
+  uint4* p = reinterpret_cast<uint4*>(q);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) p[k] = make_uint4(u[4 * k], u[4 * k + 1], u[4 * k + 2], u[4 * k + 3]);
+  *s = m;
 }
 
 template <typename R>

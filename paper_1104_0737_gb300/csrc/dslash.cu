@@ -174,6 +174,78 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Ge
   store_spinor(r + spinor_offset(s, L, rhs), e);
 }
 
+// The residual of the preconditioner's FP16 storage (Sec. 2.2, SAP in reduced
+// precision): r = eta - A psi on the sites of one colour with eta, psi and r
+// stored as FP16 spinors with a per-(site, column) scale, FP32 links and FP32
+// arithmetic.
+template <int MU, int SIGN>
+__device__ __forceinline__ void hop_h32(Spinor<float>& acc, const __half2* __restrict__ q, const float* __restrict__ sc,
+                                        size_t i, const cx<float>* __restrict__ link, bool flip) {
+  Spinor<float> p;
+  load_spinor_h(q + i * 12, __ldg(sc + i), p);
+  cx<float> h[2][3];
+  project<MU, SIGN>(p, h);
+  Link<float> u;
+  load_link(link, u);
+  cx<float> w[2][3];
+  link_times<(SIGN > 0)>(u, h, flip ? -1.0f : 1.0f, w);
+  reconstruct_add<MU, SIGN>(acc, w);
+}
+
+template <int MU>
+__device__ __forceinline__ void hops_h32(const Geom& g, const cx<float>* __restrict__ links,
+                                         const __half2* __restrict__ q, const float* __restrict__ sc, int L, int rhs,
+                                         int s, const int c[4], int stride, Spinor<float>& acc) {
+  const int dm = g.d[MU];
+  {
+    const bool wrap = (c[MU] == dm - 1);
+    const int sn = wrap ? s - (dm - 1) * stride : s + stride;
+    hop_h32<MU, -1>(acc, q, sc, (size_t)sn * L + rhs, links + (size_t)(s * 4 + MU) * 9, MU == 3 && wrap);
+  }
+  {
+    const bool wrap = (c[MU] == 0);
+    const int sn = wrap ? s + (dm - 1) * stride : s - stride;
+    hop_h32<MU, 1>(acc, q, sc, (size_t)sn * L + rhs, links + (size_t)(sn * 4 + MU) * 9, MU == 3 && wrap);
+  }
+}
+
+template <int CM>
+__global__ void __launch_bounds__(384, 2) k_sap_residual_h(Geom g, int colour, const cx<float>* __restrict__ links,
+                                                           const __half2* __restrict__ eta, const float* __restrict__ esc,
+                                                           const __half2* __restrict__ psi,
+                                                           const float* __restrict__ psc, __half2* __restrict__ r,
+                                                           float* __restrict__ rsc, int L, float kappa,
+                                                           const float* __restrict__ clov) {
+  const int rhs = threadIdx.x;
+  const int slot = blockIdx.x * blockDim.y + threadIdx.y;
+  int c[4], lc[4], k;
+  colour_slot_coords(g, colour, slot, c, lc, &k);
+  const int s = site_index(g, c);
+  const size_t i = (size_t)s * L + rhs;
+  Spinor<float> acc, e, p;
+  zero(acc);
+  const int st1 = g.d[0], st2 = st1 * g.d[1], st3 = st2 * g.d[2];
+  hops_h32<0>(g, links, psi, psc, L, rhs, s, c, 1, acc);
+  hops_h32<1>(g, links, psi, psc, L, rhs, s, c, st1, acc);
+  hops_h32<2>(g, links, psi, psc, L, rhs, s, c, st2, acc);
+  hops_h32<3>(g, links, psi, psc, L, rhs, s, c, st3, acc);
+  if (CM == 1) {  // A = 1 - kappa T^{-1} H
+    Spinor<float> h;
+    herm_apply<float>(clov + (size_t)s * HERM_PER_SITE, acc, h);
+    acc = h;
+  }
+  load_spinor_h(eta + i * 12, __ldg(esc + i), e);
+  load_spinor_h(psi + i * 12, __ldg(psc + i), p);
+  // r = eta - (psi - kappa eta_hop)
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    cx<float>& ej = (&e.c[0][0])[j];
+    const cx<float> pj = (&p.c[0][0])[j], aj = (&acc.c[0][0])[j];
+    ej = mk(fmaf(kappa, aj.re, ej.re - pj.re), fmaf(kappa, aj.im, ej.im - pj.im));
+  }
+  store_spinor_h(r + i * 12, rsc + i, e);
+}
+
 template <typename R, int CM>
 __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_domain_apply(Geom g, int colour,
                                                           const cx<R>* __restrict__ links,
@@ -364,6 +436,14 @@ __device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr) {
   return v;
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, L1 bypassed),
+// waited for by the issuing thread.
+__device__ __forceinline__ void cp_async_16(float4* dst, const float4* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Spinor of site `site` from 6 float4 planes of NS sites at cluster address base.
 __device__ __forceinline__ void cluster_planes_to_spinor(uint32_t base, int NS, int site, Spinor<float>& v) {
 #pragma unroll
@@ -484,12 +564,14 @@ __device__ __forceinline__ void domain_hops(const float4* vL, uint32_t vS, const
 
 // CM = 1: the Jacobi-preconditioned clover matrix, every hop sum multiplied by
 // T^{-1} of its site (tinv, packed, read through L1)
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM>
+// H: the residual rin and psi are FP16 spinors with per-(site, column) scales
+// rsc, psc (the preconditioner's FP16 storage), else FP32 (rsc, psc unused).
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM, bool H>
 __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS,
                                   (SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS <= 256) ? 2 : 1)
-    k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const cx<float>* __restrict__ rin,
-                cx<float>* __restrict__ psi, int L, float kappa, int psi_mode, int nmr, int mode,
-                const double* __restrict__ table, const float* __restrict__ tinv) {
+    k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const void* __restrict__ rin,
+                const float* __restrict__ rsc, void* __restrict__ psi, float* __restrict__ psc, int L, float kappa,
+                int psi_mode, int nmr, int mode, const double* __restrict__ table, const float* __restrict__ tinv) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   constexpr int NS = SH::NS;
   constexpr int CS = SH::CS;
@@ -534,6 +616,12 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
   float4* nxt = buf1;
   int k = -1, s = 0;
   int c[4];
+  // With frozen step lengths the last MR step applies no operator and leaves
+  // the buffer nxt idle (no CTA reads it after the barrier that ended the
+  // step before): there the next item's FP32 residual is copied into nxt with
+  // asynchronous 16-byte copies, so its HBM latency overlaps the step and the
+  // psi update instead of stalling the cluster at the next item's start.
+  bool have_rn = false;
   for (int item = item0; item < item1; ++item) {
     const int kk = item / L;
     const int rhs = item - kk * L;
@@ -562,9 +650,15 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
     const size_t off = spinor_offset(s, L, rhs);
     // the colour's residual at entry: eta itself when psi = 0, else
     // eta - A psi formed beforehand by the residual kernel
-    Spinor<float> r0;
-    load_spinor(rin + off, r0);
-    spinor_to_planes(nxt, NS, tid, r0);
+    if (have_rn) {
+      cp_async_wait_all();  // this thread's copies of r0 into nxt have landed
+    } else {
+      Spinor<float> r0;
+      if (H) load_spinor_h(static_cast<const __half2*>(rin) + off, __ldg(rsc + off / 12), r0);
+      else load_spinor(static_cast<const cx<float>*>(rin) + off, r0);
+      spinor_to_planes(nxt, NS, tid, r0);
+    }
+    have_rn = false;
     cluster.sync();  // r0 (and, for the first column, every CTA's links) visible
     { float4* t = cur; cur = nxt; nxt = t; }
     Spinor<float> x;
@@ -574,6 +668,29 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
       const bool last = (it == nmr - 1);
       Spinor<float> q, rv;
       const bool need_q = (mode == 0) || !last;
+      if (!H && last && !need_q) {
+        if (item + 1 < item1) {
+          // the next item: the next column of this site, or the first column
+          // of the next domain
+          const int kn = (item + 1) / L;
+          int sn = s;
+          if (kn != kk) {
+            int b[4], cn[4];
+            colour_domain(g, colour, kn, b);
+            cn[0] = b[0] * DX + lc[0];
+            cn[1] = b[1] * DY + lc[1];
+            cn[2] = b[2] * DZ + lc[2];
+            cn[3] = b[3] * DT + lc[3];
+            sn = site_index(g, cn);
+          }
+          const size_t offn = spinor_offset(sn, L, item + 1 - kn * L);
+          const float4* src = reinterpret_cast<const float4*>(static_cast<const cx<float>*>(rin) + offn);
+#pragma unroll
+          for (int j = 0; j < 6; ++j) cp_async_16(nxt + j * NS + tid, src + j);
+          cp_async_commit();
+          have_rn = true;
+        }
+      }
       if (need_q) {
         domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ>(cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, q);
         if (CM == 1) {
@@ -648,10 +765,12 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
     // psi += x
     Spinor<float> pv;
     if (psi_mode == 1) zero(pv);
-    else load_spinor(psi + off, pv);
+    else if (H) load_spinor_h(static_cast<const __half2*>(psi) + off, psc[off / 12], pv);
+    else load_spinor(static_cast<const cx<float>*>(psi) + off, pv);
 #pragma unroll
     for (int j = 0; j < 12; ++j) (&pv.c[0][0])[j] = (&pv.c[0][0])[j] + (&x.c[0][0])[j];
-    store_spinor(psi + off, pv);
+    if (H) store_spinor_h(static_cast<__half2*>(psi) + off, psc + off / 12, pv);
+    else store_spinor(static_cast<cx<float>*>(psi) + off, pv);
     // the next column writes psi into nxt: the last reads of nxt by other CTAs
     // were fenced by the barrier that followed them
   }
@@ -661,10 +780,10 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
 
 // sets the sweep kernel's shared-memory and cluster attributes and returns
 // how many of its clusters the GPU holds at once
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM>
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM, bool H>
 int sweep_setup(cudaLaunchConfig_t cfg) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
-  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM>;
+  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM, H>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::smem_bytes());
   if (SH::CS > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cfg.gridDim = dim3((unsigned)SH::CS);
@@ -676,12 +795,12 @@ int sweep_setup(cudaLaunchConfig_t cfg) {
   return n;
 }
 
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM>
-bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
-                  cx<float>* psi, int L, double kappa, int psi_mode, int nmr, int mode, const double* table,
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM, bool H>
+bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const void* rin, const float* rsc,
+                  void* psi, float* psc, int L, double kappa, int psi_mode, int nmr, int mode, const double* table,
                   const float* tinv) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
-  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM>;
+  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM, H>;
   const size_t shm = SH::smem_bytes();
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(SH::NS);
@@ -697,13 +816,35 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
   // one persistent cluster per cluster slot of the GPU (clusters must fit
   // in one GPC, so fewer than SMs / CS may be resident at once); set up once
   // per process, thread-safely (contexts may run on several host threads)
-  static const int max_clusters = sweep_setup<DX, DY, DZ, DT, CX, CY, CZ, CT, CM>(cfg);
+  static const int max_clusters = sweep_setup<DX, DY, DZ, DT, CX, CY, CZ, CT, CM, H>(cfg);
   const long long nitems = (long long)(g.nd / 2) * L;
   const int nclu = (int)std::min<long long>(max_clusters, nitems);
   cfg.gridDim = dim3((unsigned)(SH::CS * nclu));
-  cudaLaunchKernelEx(&cfg, kern, g, colour, links, eta, psi, L, (float)kappa, psi_mode, nmr, mode, table, tinv);
+  cudaLaunchKernelEx(&cfg, kern, g, colour, links, rin, rsc, psi, psc, L, (float)kappa, psi_mode, nmr, mode, table,
+                     tinv);
   ++*ex.launches;
   return true;
+}
+
+template <bool H>
+bool sweep_dispatch(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const void* rin,
+                    const float* rsc, void* psi, float* psc, int L, double kappa, int psi_mode, int nmr, int mode,
+                    const double* table, const float* tinv) {
+  const int* bk = g.blk;
+  // 8^4: eight CTAs of 8 x 4 x 4 x 4 sites (x, the unit-stride direction, is
+  // not split, so its hops never leave the CTA); 4^4: one CTA
+  if (bk[0] == 8) {
+    if (tinv)
+      return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 1, H>(ex, g, colour, links, rin, rsc, psi, psc, L, kappa, psi_mode,
+                                                        nmr, mode, table, tinv);
+    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 0, H>(ex, g, colour, links, rin, rsc, psi, psc, L, kappa, psi_mode,
+                                                      nmr, mode, table, nullptr);
+  }
+  if (tinv)
+    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 1, H>(ex, g, colour, links, rin, rsc, psi, psc, L, kappa, psi_mode,
+                                                      nmr, mode, table, tinv);
+  return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 0, H>(ex, g, colour, links, rin, rsc, psi, psc, L, kappa, psi_mode,
+                                                    nmr, mode, table, nullptr);
 }
 
 }  // namespace
@@ -718,24 +859,29 @@ bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>*
                      cx<float>* psi, int L, double kappa, int psi_mode, int nmr, int mode, const double* table,
                      const float* tinv) {
   if (!sap_sweep_fusable(g, mode)) return false;
-  const int* bk = g.blk;
-  // 8^4: eight CTAs of 8 x 4 x 4 x 4 sites (x, the unit-stride direction, is
-  // not split, so its hops never leave the CTA); 4^4: one CTA
-  if (bk[0] == 8 && bk[1] == 8 && bk[2] == 8 && bk[3] == 8) {
-    if (tinv)
-      return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_mode, nmr, mode,
-                                                     table, tinv);
-    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 0>(ex, g, colour, links, eta, psi, L, kappa, psi_mode, nmr, mode,
-                                                   table, nullptr);
-  }
-  if (bk[0] == 4 && bk[1] == 4 && bk[2] == 4 && bk[3] == 4) {
-    if (tinv)
-      return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 1>(ex, g, colour, links, eta, psi, L, kappa, psi_mode, nmr, mode,
-                                                     table, tinv);
-    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 0>(ex, g, colour, links, eta, psi, L, kappa, psi_mode, nmr, mode,
-                                                   table, nullptr);
-  }
-  return false;
+  return sweep_dispatch<false>(ex, g, colour, links, eta, nullptr, psi, nullptr, L, kappa, psi_mode, nmr, mode, table,
+                               tinv);
+}
+
+bool sap_sweep_fused_h(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const __half2* rin,
+                       const float* rsc, __half2* psi, float* psc, int L, double kappa, int psi_mode, int nmr,
+                       int mode, const double* table, const float* tinv) {
+  if (!sap_sweep_fusable(g, mode)) return false;
+  return sweep_dispatch<true>(ex, g, colour, links, rin, rsc, psi, psc, L, kappa, psi_mode, nmr, mode, table, tinv);
+}
+
+void sap_residual_h(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const __half2* eta,
+                    const float* esc, const __half2* psi, const float* psc, __half2* r, float* rsc, int L, double kappa,
+                    const float* tinv) {
+  const int S = sap_sites_per_cta(g, L, false);
+  const int nslot = (g.nd / 2) * g.Vd;
+  if (tinv)
+    k_sap_residual_h<1><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, esc, psi, psc, r,
+                                                                            rsc, L, (float)kappa, tinv);
+  else
+    k_sap_residual_h<0><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, esc, psi, psc, r,
+                                                                            rsc, L, (float)kappa, nullptr);
+  ++*ex.launches;
 }
 
 namespace {

@@ -21,44 +21,6 @@ namespace {
 
 constexpr int HT = 256;
 
-__device__ __forceinline__ void load_spinor_h(const __half2* __restrict__ q, float s, Spinor<float>& v) {
-  const uint4* p = reinterpret_cast<const uint4*>(q);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const uint4 w = __ldg(p + k);
-    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      __half2 h;
-      memcpy(&h, &u[e], 4);
-      const float2 f = __half22float2(h);
-      (&v.c[0][0])[4 * k + e] = mk(f.x * s, f.y * s);
-    }
-  }
-}
-
-// rounds v into (q, s): s = max |re|, |im|; q = v / s to nearest FP16
-__device__ __forceinline__ void store_spinor_h(__half2* __restrict__ q, float* __restrict__ s,
-                                               const Spinor<float>& v) {
-  float m = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    const cx<float> c = (&v.c[0][0])[k];
-    m = fmaxf(m, fmaxf(fabsf(c.re), fabsf(c.im)));
-  }
-  uint32_t u[12];
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    const cx<float> c = (&v.c[0][0])[k];
-    const __half2 h = m > 0.0f ? __floats2half2_rn(c.re / m, c.im / m) : __floats2half2_rn(0.0f, 0.0f);
-    memcpy(&u[k], &h, 4);
-  }
-  uint4* p = reinterpret_cast<uint4*>(q);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) p[k] = make_uint4(u[4 * k], u[4 * k + 1], u[4 * k + 2], u[4 * k + 3]);
-  *s = m;
-}
-
 __device__ __forceinline__ void load_link_h(const __half2* __restrict__ l, Link<float>& u) {
   const uint2* p = reinterpret_cast<const uint2*>(l);
   float2 f[6];
@@ -198,12 +160,42 @@ __global__ void k_links_to_half(long long nlinks, const cx<double>* __restrict__
   }
 }
 
+// FP32 internal block <-> FP16 storage, one thread per spinor (the same
+// [site][rhs] order, so the conversion is elementwise per spinor)
+__global__ void k_block_to_half(long long n, const cx<float>* __restrict__ in, __half2* __restrict__ q,
+                                float* __restrict__ sc) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Spinor<float> v;
+  load_spinor(in + i * 12, v);
+  store_spinor_h(q + i * 12, sc + i, v);
+}
+
+__global__ void k_half_to_block(long long n, const __half2* __restrict__ q, const float* __restrict__ sc,
+                                cx<float>* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Spinor<float> v;
+  load_spinor_h(q + i * 12, __ldg(sc + i), v);
+  store_spinor(out + i * 12, v);
+}
+
 unsigned grid_of(long long n) { return (unsigned)((n + HT - 1) / HT); }
 
 }  // namespace
 
 void abi_to_half(const Exec& ex, long long nsite, int L, const cx<double>* in, __half2* q, float* sc) {
   k_abi_to_half<<<grid_of(nsite * L), HT, 0, ex.stream>>>(nsite, L, in, q, sc);
+  ++*ex.launches;
+}
+
+void block_to_half(const Exec& ex, long long nspinor, const cx<float>* in, __half2* q, float* sc) {
+  k_block_to_half<<<grid_of(nspinor), HT, 0, ex.stream>>>(nspinor, in, q, sc);
+  ++*ex.launches;
+}
+
+void half_to_block(const Exec& ex, long long nspinor, const __half2* q, const float* sc, cx<float>* out) {
+  k_half_to_block<<<grid_of(nspinor), HT, 0, ex.stream>>>(nspinor, q, sc, out);
   ++*ex.launches;
 }
 

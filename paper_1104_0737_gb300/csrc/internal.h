@@ -131,6 +131,9 @@ cudaStream_t ctx_stream(const ::mbicg_ctx* c);
 void abi_to_half(const Exec& ex, long long nsite, int L, const cx<double>* in, __half2* q, float* sc);
 void half_to_abi(const Exec& ex, long long nsite, int L, const __half2* q, const float* sc, cx<double>* out);
 void links_to_half(const Exec& ex, long long nsite, const cx<double>* in, __half2* l16);
+// an FP32 internal block of nspinor (site, rhs) spinors <-> FP16 storage
+void block_to_half(const Exec& ex, long long nspinor, const cx<float>* in, __half2* q, float* sc);
+void half_to_block(const Exec& ex, long long nspinor, const __half2* q, const float* sc, cx<float>* out);
 // out = in - kappa * hops with FP16 storage and FP32 arithmetic (SU(3) links)
 void dslash_half(const Exec& ex, const Geom& g, const __half2* l16, const __half2* q, const float* sc, __half2* qo,
                  float* so, int L, double kappa);
@@ -160,6 +163,16 @@ bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>*
                      const double* table, const float* tinv = nullptr);
 // whether sap_sweep_fused takes this domain shape, MR mode and field
 bool sap_sweep_fusable(const Geom& g, int mode);
+// The same sweep on the preconditioner's FP16 storage: rin and psi as FP16
+// spinors with per-(site, column) scales rsc, psc (half.cu's format), FP32
+// arithmetic on chip.
+bool sap_sweep_fused_h(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const __half2* rin,
+                       const float* rsc, __half2* psi, float* psc, int L, double kappa, int psi_mode, int nmr,
+                       int mode, const double* table, const float* tinv = nullptr);
+// r = eta - A psi on the sites of one colour, eta, psi and r in FP16 storage
+void sap_residual_h(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const __half2* eta,
+                    const float* esc, const __half2* psi, const float* psc, __half2* r, float* rsc, int L, double kappa,
+                    const float* tinv = nullptr);
 // SSOR (Sec. 2.2): one wavefront level of z = (1 - omega L)^{-1} y (fwd) or
 // z = (1 - omega U)^{-1} y on every domain of one colour, L and U the forward
 // and backward hops inside a domain (times T^{-1} with tinv); komega =
@@ -202,6 +215,21 @@ struct SsorParams {
 // level table to w.levels (device, Vd ints) on the stream; w must stay alive
 // until the copy has completed.
 cudaError_t sap_prepare_ssor(const Geom& g, SapWork& w, cudaStream_t stream);
+
+// The preconditioner's FP16 storage: psi = M_SAP eta with eta, psi and the
+// colour residual r in FP16 storage (q, per-(site, column) scale), FP32
+// arithmetic and FP32 links; the fused sweep only (sap_sweep_fusable), MR
+// modes 0 (per column) and 3 (frozen replay of table).
+struct SapHalf {
+  __half2* eta;
+  float* eta_sc;
+  __half2* psi;
+  float* psi_sc;
+  __half2* r;
+  float* r_sc;
+};
+void sap_apply_h(const Exec& ex, const Geom& g, const cx<float>* links, const SapHalf& h, int L, double kappa,
+                 int ncycle, int nmr, int mr_mode, const double* table, const float* tinv = nullptr);
 
 // psi = M_SAP eta.  eta and psi are full-lattice blocks in the internal
 // layout and in the SAP precision (R).  mr_mode: 0 per column, 1 shared by the

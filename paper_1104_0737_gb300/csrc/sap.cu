@@ -297,6 +297,28 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
   }
 }
 
+void sap_apply_h(const Exec& ex, const Geom& g, const cx<float>* links, const SapHalf& h, int L, double kappa,
+                 int ncycle, int nmr, int mr_mode, const double* table, const float* tinv) {
+  const int ndc = g.nd / 2;
+  const size_t nsp = (size_t)g.V * L;
+  // psi = 0 (FP16 zeros and zero scales): the residual kernel reads psi on
+  // every site from the second sweep on
+  cudaMemsetAsync(h.psi, 0, sizeof(__half2) * 12 * nsp, ex.stream);
+  cudaMemsetAsync(h.psi_sc, 0, sizeof(float) * nsp, ex.stream);
+  for (int cyc = 0; cyc < ncycle; ++cyc)
+    for (int colour = 0; colour < 2; ++colour) {
+      const double* tab = table ? table + ((long long)cyc * 2 + colour) * nmr * ndc * 2 : nullptr;
+      const bool first = cyc == 0 && colour == 0;
+      if (!first) {
+        Timed t(ex, KC_SAP_RESID);
+        sap_residual_h(ex, g, colour, links, h.eta, h.eta_sc, h.psi, h.psi_sc, h.r, h.r_sc, L, kappa, tinv);
+      }
+      Timed t(ex, KC_SAP_SWEEP);
+      sap_sweep_fused_h(ex, g, colour, links, first ? h.eta : h.r, first ? h.eta_sc : h.r_sc, h.psi, h.psi_sc, L,
+                        kappa, first ? 1 : 2, nmr, mr_mode, tab, tinv);
+    }
+}
+
 template void sap_apply<float>(const Exec&, const Geom&, const cx<float>*, const cx<float>*, cx<float>*, int,
                                double, int, int, int, double*, int*, SapWork&, const float*, const SsorParams*);
 template void sap_apply<double>(const Exec&, const Geom&, const cx<double>*, const cx<double>*, cx<double>*,

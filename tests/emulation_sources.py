@@ -88,6 +88,15 @@ def bind_shared(src):
     return "".join(out), slot
 
 
+def _plain_cp_async(src):
+    """The sweep's asynchronous 16-byte copies as plain copies (they complete
+    at once on the emulator, so committing and waiting do nothing)."""
+    src = replace_body(src, "__device__ __forceinline__ void cp_async_16(float4* dst, const float4* src)",
+                       "{ *dst = *src; }")
+    src = replace_body(src, "__device__ __forceinline__ void cp_async_commit()", "{}")
+    return replace_body(src, "__device__ __forceinline__ void cp_async_wait_all()", "{}")
+
+
 def sweep_parts(csrc=CSRC):
     """common.cuh and the device part of dslash.cu (through the fused sweep
     kernel) for the threaded emulation."""
@@ -101,6 +110,7 @@ def sweep_parts(csrc=CSRC):
                       "{ return emu_mapa(local, rank); }")
     ds = replace_body(ds, "__device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr)",
                       "{ return emu_ld_cluster_f4(addr); }")
+    ds = _plain_cp_async(ds)
     ds, slots = bind_shared(ds)
     return "\n".join([f"#define EMU_STATIC_SLOTS {max(slots, 1)}", '#include "shim_threads.h"', common,
                       "namespace mbicg {", "namespace emu_dslash {", ds, "}", "}"])
@@ -259,6 +269,7 @@ def library_unit(name, csrc=CSRC):
                            "{ return emu_mapa(local, rank); }")
         src = replace_body(src, "__device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr)",
                            "{ return emu_ld_cluster_f4(addr); }")
+        src = _plain_cp_async(src)
     src = rewrite_launches(src)
     src, slots = bind_shared(src)
     return "\n".join([f"#define EMU_STATIC_SLOTS {max(slots, 1)}", '#include "shim_threads.h"',

@@ -99,11 +99,11 @@ def test_sap_full_size_32c64_L12(oracle_mod):
     ctx, U = make_ctx(dims, 0.5, seed=1003)
     try:
         eta = synth.gaussian_source(dims, L, seed=2003)
-        ref = oracle_mod.sap(dims, block, U, 0.14775, 1, 2, eta, mr_mode=mb.MBICG_MR_COLUMN)
+        ref = oracle_mod.sap(dims, block, U, 0.14774, 1, 2, eta, mr_mode=mb.MBICG_MR_COLUMN)
         out = np.empty_like(eta)
         p = mb.mbicg_default_params(ncycle=1, nmr=2, block=block, mr_mode=mb.MBICG_MR_COLUMN,
                                     prec_sap=mb.MBICG_FP32)
-        mb.mbicg_sap_precond(ctx, eta, out, L, 0.14775, p)
+        mb.mbicg_sap_precond(ctx, eta, out, L, 0.14774, p)
         assert rel_site_norm(out, ref) < 1e-5
     finally:
         mb.mbicg_destroy(ctx)

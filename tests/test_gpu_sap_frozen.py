@@ -149,7 +149,7 @@ def test_frozen_sap_full_size_32c64_L12(oracle_mod, monkeypatch):
     table by the fused sweep; one cycle of three MR steps keeps the oracle
     within a few minutes."""
     monkeypatch.setenv("MBICG_SAP_FUSED", "1")
-    dims, block, L, kappa = (32, 32, 32, 64), (8, 8, 8, 8), 12, 0.14775
+    dims, block, L, kappa = (32, 32, 32, 64), (8, 8, 8, 8), 12, 0.14774
     ctx, U = make_ctx(dims, 0.5, seed=1003)
     try:
         p = mb.mbicg_default_params(ncycle=1, nmr=3, block=block, mr_mode=mb.MBICG_MR_FROZEN,

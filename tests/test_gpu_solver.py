@@ -219,7 +219,7 @@ def test_graph_replay_gives_the_eager_solution(monkeypatch, prec):
 
 @pytest.mark.slow
 def test_benchmark_solve_true_residual_by_oracle(oracle_mod):
-    """The benchmark's solve (32^3 x 64, L = 12 point sources, kappa 0.14775,
+    """The benchmark's solve (32^3 x 64, L = 12 point sources, kappa 0.14774,
     SAP 8^4 / 4 cycles / 4 MR with frozen step lengths, mixed precision, tol
     1e-10): its solution checked by the oracle's own FP64 operator, column by
     column: |b_i - A x_i| / |b_i| <= 1e-10."""
@@ -230,9 +230,9 @@ def test_benchmark_solve_true_residual_by_oracle(oracle_mod):
         X = np.empty_like(B)
         p = mb.mbicg_default_params(ncycle=4, nmr=4, block=(8, 8, 8, 8), mr_mode=mb.MBICG_MR_FROZEN,
                                     max_iter=2000)
-        st, it, tres = mb.mbicg_block_solve(ctx, B, X, L, 0.14775, 1e-10, p)
+        st, it, tres = mb.mbicg_block_solve(ctx, B, X, L, 0.14774, 1e-10, p)
         assert st == mb.MBICG_OK
-        R = B - oracle_mod.apply_D(dims, U, 0.14775, X)
+        R = B - oracle_mod.apply_D(dims, U, 0.14774, X)
         rel = np.linalg.norm(R.reshape(-1, L), axis=0) / np.linalg.norm(B.reshape(-1, L), axis=0)
         assert np.max(rel) <= 1e-10, rel
         # the library's own FP64 true residuals agree with the oracle's

@@ -1,7 +1,8 @@
 """The 16^3 x 32 workload as block solves (Sec. 2.1, Algorithm 2 with SAP of
 Sec. 2.2): eps 0.5 links, kappa 0.125 and 0.128, L = 1, 4 and 12 Gaussian
 right-hand sides, SAP on 8^4 domains (4 cycles, 4 MR steps, frozen step
-lengths), mixed precision, tol 1e-10.
+lengths) with its blocks in FP16 storage (per-(site, column) scales) or FP32,
+FP32 Krylov vectors, FP64 X, QR factors and true residual, tol 1e-10.
 
 The oracle solves the same 12-column system once per kappa (Algorithm 1; the
 solution of A X = B does not depend on the preconditioner, so the oracle runs
@@ -37,14 +38,15 @@ def field():
     mb.mbicg_destroy(ctx)
 
 
+@pytest.mark.parametrize("prec_sap", [mb.MBICG_FP16, mb.MBICG_FP32])
 @pytest.mark.parametrize("kappa", [0.125, 0.128])
 @pytest.mark.parametrize("L", [1, 4, 12])
-def test_c2_block_solve_matches_oracle(oracle_mod, field, kappa, L):
+def test_c2_block_solve_matches_oracle(oracle_mod, field, kappa, L, prec_sap):
     ctx, U, B = field
     Xref = oracle_solution(oracle_mod, U, B, kappa)
     b = np.ascontiguousarray(B[..., :L])
     p = mb.mbicg_default_params(ncycle=4, nmr=4, block=BLOCK, mr_mode=mb.MBICG_MR_FROZEN,
-                                prec_D=mb.MBICG_FP32, prec_sap=mb.MBICG_FP32, max_iter=2000)
+                                prec_D=mb.MBICG_FP32, prec_sap=prec_sap, max_iter=2000)
     X = np.empty_like(b)
     st, iters, tres = mb.mbicg_block_solve(ctx, b, X, L, kappa, 1e-10, p)
     assert st == mb.MBICG_OK, (st, iters, tres)
