@@ -88,20 +88,30 @@ def sap_domain_bytes(V, L, real_bytes=4):
 
 def sap_sweep_bytes(V, L, real_bytes=4):
     """One colour sweep of the fused SAP kernel: on the sweep's half of the
-    sites eta and psi read and psi written, the four forward links read, and
-    psi of the other half read once for the domain boundaries."""
+    sites the colour's residual r and psi read, psi written, and the first two
+    rows of the four forward links (staged once per domain)."""
     spinor = 24 * real_bytes
-    return (V // 2) * (L * 3 * spinor + 4 * 18 * real_bytes) + (V // 2) * L * spinor
+    return (V // 2) * (L * 3 * spinor + 4 * 12 * real_bytes)
 
 
 def sap_sweep_flops(V, L, nmr, frozen=True):
-    """Residual eta - A psi (one operator application) and nmr MR steps, each a
-    domain operator application (not needed in the last step when the step
-    lengths are frozen) plus x += w r, r -= w q (16 flops per complex pair,
-    12 pairs) and, per column, the two dot products (8 flops per pair)."""
-    ops = 1 + (nmr - 1 if frozen else nmr)
+    """The MR steps of one colour sweep: nmr applications of the Dirichlet
+    domain operator (the last one is not needed when the step lengths are
+    frozen), x += w r and r -= w q (16 flops per complex pair, 12 pairs) and,
+    per column, the two dot products (8 flops per pair)."""
+    ops = nmr - 1 if frozen else nmr
     mr = nmr * 12 * 16 + (0 if frozen else nmr * 12 * 8)
     return (V // 2) * L * (ops * 1368 + mr)
+
+
+def sap_resid_bytes(V, L, block, real_bytes=4):
+    """The residual eta - A psi of one colour: eta and psi of the colour's
+    sites read, r written, psi of the faces of the neighbouring domains read
+    (one face layer per face: 2 * sum_mu V / block_mu sites over both colours,
+    half of them here) and the links (four forward links of each site, FP32)."""
+    spinor = 24 * real_bytes
+    faces = sum(V // b for b in block)  # face sites of one colour's domains
+    return (V // 2) * (L * 3 * spinor + 4 * 18 * real_bytes) + faces * L * spinor
 
 
 # DRAM bytes per launch of the dominant kernel at the benchmark workload, from one
@@ -536,6 +546,7 @@ def main():
     alu_peak = fp32_alu_peak_tflops(sm_mhz)
     models = {
         "sap_sweep": ("alu", sap_sweep_bytes(V, L), sap_sweep_flops(V, L, cfg["nmr"])),
+        "sap_resid": ("hbm", sap_resid_bytes(V, L, cfg["block"]), dslash_flops(V // 2, L)),
         "sap_domain": ("hbm", sap_domain_bytes(V, L), dslash_flops(V // 2, L)),
         "dslash": ("hbm", dslash_bytes(V, L), dslash_flops(V, L)),
     }
@@ -556,6 +567,8 @@ def main():
                     "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": avg_ms}
     dsl_ms = prof["dslash"][0] / prof["dslash"][1] if prof["dslash"][1] else None
     dslash_frac = (dslash_bytes(V, L) / (dsl_ms * 1e-3) / 1e9) / hbm_peak if dsl_ms else None
+    res_ms = prof["sap_resid"][0] / prof["sap_resid"][1] if prof["sap_resid"][1] else None
+    resid_frac = (sap_resid_bytes(V, L, cfg["block"]) / (res_ms * 1e-3) / 1e9) / hbm_peak if res_ms else None
 
     # end to end through the ABI with pinned host buffers
     e2e = None
@@ -642,7 +655,7 @@ def main():
             "iters": iters, "true_res_max": tres_max, "graph_iterations_last_step": graph_iters,
             "host_syncs_last_step": last_stats["host_syncs"],
             "reliable_updates_last_step": last_stats["reliable_updates"],
-            "dslash_hbm_frac": dslash_frac,
+            "dslash_hbm_frac": dslash_frac, "sap_resid_hbm_frac": resid_frac,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "kernel_ms": {k: v[0] for k, v in prof.items()},
             "kernel_launch_groups": {k: v[1] for k, v in prof.items()},

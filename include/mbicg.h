@@ -344,18 +344,24 @@ int mbicg_selftest_bounded_wait(int device, int spin_limit, int expect_bytes, in
  * paper, whose solver takes one block at a time; the method's block solve of
  * Sec. 2.1 is what packs the requests' columns together).
  *
- * Each field added to a server gets solver slots — a context with its own
- * CUDA stream, device buffers and host thread — as many as max_slots and the
- * HBM budget allow (at least one, else MBICG_ENOMEM).  A request is a source
- * block B of 1..12 columns (ABI layout, host memory, copied at submit) for one
- * field, kappa and tol.  A free slot of the field takes the oldest waiting
- * request and packs behind it, in arrival order, the waiting requests with the
- * same kappa and tol that fit into one block of at most 12 columns; it solves
- * the packed block with mbicg_block_solve (the field's params) and hands each
- * request its columns of X and of the true residuals.  Requests arriving while
- * every slot is busy wait for the next block; the slots of different fields,
- * and the slots of one field, solve concurrently.  Thread-safe: submit and
- * wait may be called from any host threads.
+ * Each field added to a server gets max_slots solver slots — a context with
+ * its own CUDA stream and host thread, holding the field's links.  A request
+ * is a source block B of 1..12 columns (ABI layout, host memory, copied at
+ * submit) for one field, kappa and tol.  A free slot of the field takes the
+ * oldest waiting request and packs behind it, in arrival order, the waiting
+ * requests with the same kappa and tol that fit into one block of at most 12
+ * columns; it solves the packed block with mbicg_block_solve (the field's
+ * params) and hands each request its columns of X and of the true residuals.
+ * Admission by HBM footprint: the server never holds more device memory than
+ * its budget.  The slots' links are charged when a field is added; a packed
+ * block is admitted only when the workspace of its block solve at its number
+ * of columns fits beside everything already held (packing stops at the
+ * request that would not fit); a slot keeps its workspace between solves;
+ * when a slot cannot admit even its oldest request, idle slots release their
+ * workspaces, and if that is not enough it waits for a running solve to
+ * finish.  Requests arriving while slots or memory are busy wait; the slots
+ * of different fields, and the slots of one field, solve concurrently.
+ * Thread-safe: submit and wait may be called from any host threads.
  * ------------------------------------------------------------------------ */
 typedef struct mbicg_server mbicg_server;
 
@@ -366,20 +372,25 @@ typedef struct {
   int batch_columns;  /* columns of the block it was solved in */
 } mbicg_request_info;
 
-/* A server on `device` that gives its solver slots at most hbm_budget_gb
- * gigabytes (1e9 bytes) of device memory, by the estimate
- * V (48 + 96 + 48) 12 * 12 + 1152 V bytes per slot. */
+/* A server on `device` whose slots hold at most hbm_budget_gb gigabytes (1e9
+ * bytes) of device memory: per slot 960 V bytes of links and 4 MiB, per
+ * admitted block solve of L columns about 12 V L (3 x 16 + 7 x 8 + 3 x 8 +
+ * 3 x 16) bytes for FP32 Krylov vectors and FP32 SAP storage (FP64 ones count
+ * 16 bytes per complex number; FP16 SAP storage adds 3 x 52 bytes per site
+ * and column). */
 int mbicg_server_create(mbicg_server** server, int device, double hbm_budget_gb);
 
 /* Makes the gauge field U (dims, layout of mbicg_load_gauge) resident with up
- * to max_slots solver slots solving with the parameters *p; *field_id names
- * it in submit. */
+ * to max_slots solver slots (as many as the budget holds the links of, at
+ * least one, else MBICG_ENOMEM) solving with the parameters *p; *field_id
+ * names it in submit. */
 int mbicg_server_add_field(mbicg_server* server, const int dims[4], const double* U,
                            const mbicg_params* p, int max_slots, int* field_id);
 
 /* Queues the solve of A X = B (L columns, 1 <= L <= 12, host memory, copied)
  * on field field_id; *request_id names it in wait.  MBICG_EINVAL for an
- * unknown field, L outside 1..12 or tol <= 0. */
+ * unknown field, L outside 1..12 or tol <= 0; MBICG_ENOMEM when a block of
+ * this request alone could never fit in the budget beside the slots' links. */
 int mbicg_server_submit(mbicg_server* server, int field_id, const double* B, int L,
                         double kappa, double tol, long long* request_id);
 
@@ -399,6 +410,10 @@ int mbicg_server_hold(mbicg_server* server, int hold);
 /* Block solves run, columns solved, the widest block, solver slots. */
 int mbicg_server_stats(mbicg_server* server, long long* solves, long long* columns,
                        long long* max_columns, int* slots);
+
+/* Device memory the server holds now (links and admitted workspaces), its
+ * budget, and how many times a slot had to wait for memory (each may be NULL). */
+int mbicg_server_memory(mbicg_server* server, double* used_gb, double* budget_gb, long long* memory_waits);
 
 /* Stops the slots (after their current solves) and frees everything; every
  * submitted request should have been waited for. */

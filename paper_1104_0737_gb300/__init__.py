@@ -27,7 +27,7 @@ __all__ = [
     "mbicg_sap_precond_frozen", "mbicg_block_solve", "mbicg_get_stats",
     "mbicg_last_error", "mbicg_set_profiling", "mbicg_get_profile", "mbicg_apply_D_noalloc",
     "mbicg_request_info", "mbicg_server_create", "mbicg_server_add_field", "mbicg_server_submit",
-    "mbicg_server_wait", "mbicg_server_hold", "mbicg_server_stats", "mbicg_server_destroy",
+    "mbicg_server_wait", "mbicg_server_hold", "mbicg_server_stats", "mbicg_server_memory", "mbicg_server_destroy",
     "mbicg_selftest_bounded_wait",
 ]
 
@@ -121,6 +121,7 @@ def load_library(build_if_missing: bool = True):
     lib.mbicg_server_wait.argtypes = [vp, ctypes.c_longlong, vp, ip, dp, ctypes.POINTER(mbicg_request_info)]
     lib.mbicg_server_stats.argtypes = [vp, llp, llp, llp, ip]
     lib.mbicg_server_hold.argtypes = [vp, ctypes.c_int]
+    lib.mbicg_server_memory.argtypes = [vp, dp, dp, llp]
     lib.mbicg_server_destroy.argtypes = [vp]
     lib.mbicg_server_destroy.restype = None
     lib.mbicg_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip]
@@ -340,7 +341,8 @@ def mbicg_server_submit(server, field: int, B, L: int, kappa: float, tol: float)
     st = load_library().mbicg_server_submit(server, int(field), _host(B, "B"), int(L), float(kappa),
                                             float(tol), ctypes.byref(rid))
     if st != MBICG_OK:
-        raise MbicgError(st, "mbicg_server_submit: unknown field, L outside 1..12 or tol <= 0")
+        raise MbicgError(st, "mbicg_server_submit: unknown field, L outside 1..12, tol <= 0, or a block "
+                             "that can never fit in the memory budget")
     return rid.value
 
 
@@ -370,6 +372,13 @@ def mbicg_server_stats(server) -> dict:
     n = ctypes.c_int()
     load_library().mbicg_server_stats(server, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(n))
     return {"solves": a.value, "columns": b.value, "max_columns": c.value, "slots": n.value}
+
+
+def mbicg_server_memory(server) -> dict:
+    """Device memory held (GB), the budget (GB) and the waits for memory."""
+    u, b, w = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+    load_library().mbicg_server_memory(server, ctypes.byref(u), ctypes.byref(b), ctypes.byref(w))
+    return {"used_gb": u.value, "budget_gb": b.value, "memory_waits": w.value}
 
 
 def mbicg_server_destroy(server) -> None:

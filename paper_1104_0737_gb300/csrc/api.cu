@@ -916,6 +916,19 @@ int clover_for_kappa(mbicg_ctx* c, double kappa) {
 // ---------------------------------------------------------------------------
 cudaStream_t mbicg::ctx_stream(const mbicg_ctx* c) { return c->stream; }
 
+size_t mbicg::ctx_workspace_bytes(const mbicg_ctx* c) {
+  size_t n = 0;
+  for (const auto& kv : c->bufs) n += kv.second.second < 256 ? 256 : kv.second.second;
+  return n;
+}
+
+void mbicg::ctx_release_workspace(mbicg_ctx* c) {
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->bufs) cudaFree(kv.second.first);
+  c->bufs.clear();
+}
+
 extern "C" {
 
 void mbicg_default_params(mbicg_params* p) {

@@ -124,6 +124,10 @@ void first_columns(const Exec& ex, long long nsite, int Lt, int L, const cx<doub
 
 // the CUDA stream a context orders its work on (api.cu)
 cudaStream_t ctx_stream(const ::mbicg_ctx* c);
+// device bytes of the context's workspaces (its gauge copies excluded), and
+// their release (after the context's stream has drained); api.cu
+size_t ctx_workspace_bytes(const ::mbicg_ctx* c);
+void ctx_release_workspace(::mbicg_ctx* c);
 
 // FP16 storage (half.cu): spinor blocks q[site][rhs][12] __half2 with one FP32
 // scale per (site, rhs) (the largest |re|, |im| of the spinor; the value is

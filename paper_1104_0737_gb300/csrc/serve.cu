@@ -1,16 +1,23 @@
 // serve.cu — a request loop over resident gauge fields.
 //
 // Requests are source blocks of 1..12 columns for one of several resident
-// gauge fields and a hopping parameter.  Each field has a fixed set of solver
-// slots, as many as the HBM budget admits (at least one); a slot is a solver
-// context with its own CUDA stream, device buffers and host thread.  A free
-// slot takes the oldest waiting request of its field and packs behind it, in
-// arrival order, the waiting requests with the same kappa and tolerance that
-// still fit into one block of at most 12 columns; the packed block is solved
-// by the modified block BiCGSTAB (Algorithm 2 of Sec. 2.1 — the method
-// solves the L columns of a block together) and the columns are handed back
-// to their requests.  Requests that arrive while the slots are busy wait and
-// join the next block their slot forms: slots of different fields, and
+// gauge fields and a hopping parameter.  Each field has solver slots (a
+// solver context with its own CUDA stream and host thread, holding the
+// field's links); a free slot takes the oldest waiting request of its field
+// and packs behind it, in arrival order, the waiting requests with the same
+// kappa and tolerance that still fit into one block of at most 12 columns;
+// the packed block is solved by the modified block BiCGSTAB (Algorithm 2 of
+// Sec. 2.1 — the method solves the L columns of a block together) and the
+// columns are handed back to their requests.
+//
+// Admission by HBM footprint: the server holds a device-memory budget.  The
+// slots' links are charged when a field is added; a packed block is admitted
+// only when the workspace of its block solve (the solver's blocks at its L,
+// the packing buffers) fits beside everything already held, and packing stops
+// at the request that would not fit.  A slot keeps its workspace between
+// solves (charged while held); when a slot cannot admit even the oldest
+// request, idle slots give their workspaces back, and if that is not enough
+// it waits for a running solve to finish.  Slots of different fields, and
 // several slots of one field, run their solves concurrently on the device.
 #include <algorithm>
 #include <chrono>
@@ -67,6 +74,9 @@ struct Slot {
   cx<double>* dB = nullptr;  // packed block
   cx<double>* dX = nullptr;
   cx<double>* dS = nullptr;  // one request's columns
+  int cap = 0;               // columns the packing buffers hold
+  double held = 0;           // bytes of workspace charged to this slot (beyond its links)
+  bool busy = false;
   std::thread th;
 };
 
@@ -82,6 +92,7 @@ struct Field {
 struct mbicg_server {
   int device = 0;
   double budget = 0, used = 0;  // bytes
+  long long mem_waits = 0;      // block solves that waited for memory
   std::vector<Field> fields;
   std::vector<Slot*> slots;
   std::deque<Request*> pending;
@@ -96,28 +107,76 @@ struct mbicg_server {
 
 namespace {
 
-// Device bytes one slot of a field holds: the solver's blocks (B, X, W in
-// FP64; R, P, R~, U, V, S, Z in FP32; SAP workspace) at 12 columns, the
-// packing buffers (three FP64 blocks) and the link copies.
-double slot_bytes(long long V) {
-  const double f64 = 16.0 * 12 * SERVE_MAXL * V, f32 = 8.0 * 12 * SERVE_MAXL * V;
-  return 3 * f64 + 10 * f32 + 3 * f64 + V * (576.0 + 288 + 96 + 192);
+// Device bytes a slot of a field holds for the links (FP64, FP32 and the
+// FP16 rows) and its fixed scratch.
+double slot_fixed_bytes(long long V) { return V * (576.0 + 288 + 96) + (1 << 22); }
+
+// Device bytes of the workspace of a block solve of L columns on V sites: B,
+// X and W in FP64, the seven Krylov blocks, the preconditioner's blocks (FP32
+// r, q, x; the FP16 storage on top when chosen), the packing buffers (packed
+// B and X, one request's columns) and the small per-CTA partial sums; 5 %
+// margin.
+double solve_bytes(long long V, int L, const mbicg_params& p) {
+  const double nl = 12.0 * V * L;
+  double b = 3 * 16 * nl;                                  // B64, X64, W64
+  b += 7 * (p.prec_D == MBICG_FP64 ? 16 : 8) * nl;         // R, P, R~, U, V, S, Z
+  if (p.ncycle > 0) {
+    const double sap = p.prec_sap == MBICG_FP64 ? 16 : 8;
+    b += 3 * sap * nl;                                     // SAP r, q, x
+    if ((p.prec_sap == MBICG_FP64) != (p.prec_D == MBICG_FP64)) b += 2 * sap * nl;  // eta, psi staging
+    if (p.prec_sap == MBICG_FP16) b += 3 * (4 * nl + 4.0 * V * L);
+  }
+  b += 3 * 16 * nl;                                        // packing buffers
+  return 1.05 * b + (8 << 20);
 }
 
-// takes the oldest waiting request of `field` and the compatible ones behind it
-std::vector<Request*> take_batch(mbicg_server* s, int field) {
+// Bytes a slot holds now: its context's workspaces and its packing buffers.
+double slot_held_bytes(const Slot* sl, long long V) {
+  return (double)ctx_workspace_bytes(sl->ctx) + 3.0 * sizeof(cx<double>) * V * 12 * sl->cap;
+}
+
+void release_slot_workspace(mbicg_server* s, Slot* sl) {
+  ctx_release_workspace(sl->ctx);
+  if (sl->dB) cudaFree(sl->dB);
+  if (sl->dX) cudaFree(sl->dX);
+  if (sl->dS) cudaFree(sl->dS);
+  sl->dB = sl->dX = sl->dS = nullptr;
+  sl->cap = 0;
+  s->used -= sl->held;
+  sl->held = 0;
+}
+
+// Takes the oldest waiting request of `field` and the compatible ones behind
+// it that fit into 12 columns and into the memory budget (the slot's own
+// workspace counts as available to it); charges the batch's workspace to the
+// slot.  *no_memory: the oldest request did not fit.  Called with s->mu held.
+std::vector<Request*> take_batch(mbicg_server* s, Slot* sl, bool* no_memory) {
+  const Field& f = s->fields[sl->field];
   std::vector<Request*> batch;
   int cols = 0;
+  *no_memory = false;
+  const double avail = s->budget - s->used + sl->held;
   for (auto it = s->pending.begin(); it != s->pending.end();) {
     Request* r = *it;
-    const bool fits = r->field == field && cols + r->L <= SERVE_MAXL &&
-                      (batch.empty() || (r->kappa == batch[0]->kappa && r->tol == batch[0]->tol));
-    if (fits) {
-      batch.push_back(r);
-      cols += r->L;
-      it = s->pending.erase(it);
-    } else {
+    const bool compatible = r->field == sl->field && cols + r->L <= SERVE_MAXL &&
+                            (batch.empty() || (r->kappa == batch[0]->kappa && r->tol == batch[0]->tol));
+    if (!compatible) {
       ++it;
+      continue;
+    }
+    if (solve_bytes(f.V, cols + r->L, f.params) > avail) {
+      if (batch.empty()) *no_memory = true;
+      break;  // later requests wait behind it: arrival order is kept
+    }
+    batch.push_back(r);
+    cols += r->L;
+    it = s->pending.erase(it);
+  }
+  if (!batch.empty()) {
+    const double need = solve_bytes(f.V, cols, f.params);
+    if (need > sl->held) {
+      s->used += need - sl->held;
+      sl->held = need;
     }
   }
   return batch;
@@ -134,7 +193,23 @@ void run_batch(mbicg_server* s, Slot* sl, std::vector<Request*>& batch) {
   int status = MBICG_OK, iters = 0;
   double tres[MAXL] = {0};
   cudaSetDevice(s->device);
-  {
+  if (sl->cap < L) {
+    // packing buffers for L columns (the previous ones are too small)
+    if (sl->dB) cudaFree(sl->dB);
+    if (sl->dX) cudaFree(sl->dX);
+    if (sl->dS) cudaFree(sl->dS);
+    sl->dB = sl->dX = sl->dS = nullptr;
+    sl->cap = 0;
+    const size_t blk = sizeof(cx<double>) * (size_t)nrow * L;
+    if (cudaMalloc(&sl->dB, blk) != cudaSuccess || cudaMalloc(&sl->dX, blk) != cudaSuccess ||
+        cudaMalloc(&sl->dS, blk) != cudaSuccess) {
+      cudaGetLastError();
+      status = MBICG_ENOMEM;
+    } else {
+      sl->cap = L;
+    }
+  }
+  if (status == MBICG_OK) {
     // the stream of the slot's context is its own non-blocking stream
     st = ctx_stream(sl->ctx);
     int o = 0;
@@ -155,7 +230,7 @@ void run_batch(mbicg_server* s, Slot* sl, std::vector<Request*>& batch) {
   for (Request* r : batch) {
     r->X.assign(2 * (size_t)nrow * r->L, 0.0);
     r->tres.assign(r->L, 0.0);
-    if (have_x) {
+    if (have_x && st) {
       k_pack_columns<<<1024, 256, 0, st>>>(nrow, L, o, r->L, sl->dX, sl->dS, 0);
       if (cudaMemcpyAsync(r->X.data(), sl->dS, sizeof(cx<double>) * nrow * r->L, cudaMemcpyDeviceToHost, st) !=
               cudaSuccess ||
@@ -166,7 +241,12 @@ void run_batch(mbicg_server* s, Slot* sl, std::vector<Request*>& batch) {
     o += r->L;
   }
   const double t1 = now_ms();
+  const double held = slot_held_bytes(sl, f.V);
   std::lock_guard<std::mutex> lk(s->mu);
+  // what the slot really holds now replaces the estimate charged for it
+  s->used += held - sl->held;
+  sl->held = held;
+  sl->busy = false;
   for (Request* r : batch) {
     r->status = status;
     r->iters = iters;
@@ -186,17 +266,38 @@ void worker(mbicg_server* s, Slot* sl) {
     std::vector<Request*> batch;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_work.wait(lk, [&] {
-        if (s->stop) return true;
-        if (s->hold) return false;
-        for (Request* r : s->pending)
-          if (r->field == sl->field) return true;
-        return false;
-      });
-      if (s->stop) return;
-      batch = take_batch(s, sl->field);
+      for (;;) {
+        s->cv_work.wait(lk, [&] {
+          if (s->stop) return true;
+          if (s->hold) return false;
+          for (Request* r : s->pending)
+            if (r->field == sl->field) return true;
+          return false;
+        });
+        if (s->stop) return;
+        bool no_memory = false;
+        batch = take_batch(s, sl, &no_memory);
+        if (!batch.empty()) break;
+        if (!no_memory) {
+          s->cv_done.wait(lk);
+          continue;
+        }
+        // the oldest request does not fit: idle slots give their workspaces
+        // back (their threads wait for the lock, so their contexts are not in
+        // use), then, if that was not enough, wait for a running solve
+        ++s->mem_waits;
+        bool freed = false;
+        for (Slot* o : s->slots)
+          if (o != sl && !o->busy && o->held > 0) {
+            release_slot_workspace(s, o);
+            freed = true;
+          }
+        if (!freed) s->cv_done.wait(lk);
+      }
+      sl->busy = true;
     }
-    if (!batch.empty()) run_batch(s, sl, batch);
+    run_batch(s, sl, batch);
+    s->cv_work.notify_all();  // memory it gave back may admit another slot's block
   }
 }
 
@@ -246,7 +347,7 @@ int mbicg_server_add_field(mbicg_server* s, const int dims[4], const double* U, 
     f.V *= dims[mu];
   }
   f.params = *p;
-  const double need = slot_bytes(f.V);
+  const double need = slot_fixed_bytes(f.V);
   std::vector<Slot*> made;
   int rc = MBICG_OK;
   cudaSetDevice(s->device);
@@ -262,14 +363,8 @@ int mbicg_server_add_field(mbicg_server* s, const int dims[4], const double* U, 
       free_slot(sl);
       break;
     }
-    const size_t blk = sizeof(cx<double>) * (size_t)f.V * 12 * SERVE_MAXL;
-    if (cudaMalloc(&sl->dB, blk) != cudaSuccess || cudaMalloc(&sl->dX, blk) != cudaSuccess ||
-        cudaMalloc(&sl->dS, blk) != cudaSuccess) {
-      cudaGetLastError();
-      free_slot(sl);
-      rc = MBICG_ENOMEM;
-      break;
-    }
+    // the links are resident; the staging buffer of their upload is not kept
+    ctx_release_workspace(sl->ctx);
     made.push_back(sl);
     std::lock_guard<std::mutex> lk(s->mu);
     s->used += need;
@@ -297,7 +392,15 @@ int mbicg_server_submit(mbicg_server* s, int field, const double* B, int L, doub
       delete r;
       return MBICG_EINVAL;
     }
-    r->B.assign(B, B + 2 * (size_t)s->fields[field].V * 12 * L);
+    const Field& f = s->fields[field];
+    // a block of this request alone must fit beside the slots' links
+    double fixed = 0;
+    for (const Field& g : s->fields) fixed += g.nslots * slot_fixed_bytes(g.V);
+    if (fixed + solve_bytes(f.V, L, f.params) > s->budget) {
+      delete r;
+      return MBICG_ENOMEM;
+    }
+    r->B.assign(B, B + 2 * (size_t)f.V * 12 * L);
   }
   r->field = field;
   r->L = L;
@@ -361,6 +464,15 @@ int mbicg_server_stats(mbicg_server* s, long long* solves, long long* columns, l
   return MBICG_OK;
 }
 
+int mbicg_server_memory(mbicg_server* s, double* used_gb, double* budget_gb, long long* memory_waits) {
+  if (!s) return MBICG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (used_gb) *used_gb = s->used / 1e9;
+  if (budget_gb) *budget_gb = s->budget / 1e9;
+  if (memory_waits) *memory_waits = s->mem_waits;
+  return MBICG_OK;
+}
+
 void mbicg_server_destroy(mbicg_server* s) {
   if (!s) return;
   {
@@ -368,6 +480,7 @@ void mbicg_server_destroy(mbicg_server* s) {
     s->stop = true;
   }
   s->cv_work.notify_all();
+  s->cv_done.notify_all();  // a slot waiting for memory goes back to its stop test
   for (Slot* sl : s->slots)
     if (sl->th.joinable()) sl->th.join();
   cudaSetDevice(s->device);

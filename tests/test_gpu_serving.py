@@ -138,12 +138,22 @@ def test_concurrent_submitters_and_bad_requests(oracle_mod):
         mb.mbicg_server_destroy(srv)
 
 
-def test_slots_follow_the_hbm_budget():
-    """A field gets as many solver slots as the budget admits: none (ENOMEM)
-    when one slot does not fit, one when only one fits although three were
-    asked for."""
+def solve_bytes(V, L):
+    """The server's estimate of a block solve's workspace (FP32 Krylov
+    vectors and SAP storage, include/mbicg.h): 12 V L (3*16 + 7*8 + 3*8 +
+    3*16) bytes, 5 % margin and 8 MiB."""
+    return 1.05 * 12 * V * L * (3 * 16 + 7 * 8 + 3 * 8 + 3 * 16) + (8 << 20)
+
+
+def test_admission_by_hbm_footprint(oracle_mod):
+    """Work is admitted by device-memory footprint as it arrives: with a
+    budget that holds the links of two slots and the workspace of only one
+    12-column block solve, the two slots never solve at the same time (the
+    second waits for memory), every request is solved, and the server never
+    holds more than its budget; a request whose block can never fit is
+    refused at submit; a budget below one slot's links refuses the field."""
     U = synth.su3_links(F2, 0.5, 905)
-    one_slot_gb = 2.0  # 8^3 x 8 at 12 columns: well under 2 GB per slot
+    V = int(np.prod(F2))
     srv = mb.mbicg_server_create(0, 1e-3)
     try:
         with pytest.raises(mb.MbicgError) as e:
@@ -151,15 +161,42 @@ def test_slots_follow_the_hbm_budget():
         assert e.value.status == mb.MBICG_ENOMEM
     finally:
         mb.mbicg_server_destroy(srv)
-    V = int(np.prod(F2))
-    per_slot = (3 * 16 + 10 * 8 + 3 * 16) * 12 * 12 * V + V * (576 + 288 + 96 + 192)
-    srv = mb.mbicg_server_create(0, 1.5 * per_slot / 1e9)
+    links = 2 * (V * 960 + (1 << 22))
+    budget = links + 1.5 * solve_bytes(V, 12)
+    srv = mb.mbicg_server_create(0, budget / 1e9)
     try:
-        f = mb.mbicg_server_add_field(srv, F2, U, params(), 3)
-        assert mb.mbicg_server_stats(srv)["slots"] == 1
-        B = synth.gaussian_source(F2, 2, seed=950)
-        st, X, tres, info = solve(srv, f, B, 2)
-        assert st == mb.MBICG_OK and max(tres) <= TOL
+        f = mb.mbicg_server_add_field(srv, F2, U, params(), 2)
+        assert mb.mbicg_server_stats(srv)["slots"] == 2
+        mb.mbicg_server_hold(srv, True)
+        Bs = [synth.gaussian_source(F2, 12, seed=950 + i) for i in range(4)]
+        kappas = (0.12, 0.125, 0.12, 0.125)  # no two of them pack together (12 columns each)
+        ids = [mb.mbicg_server_submit(srv, f, B, 12, k, TOL) for B, k in zip(Bs, kappas)]
+        mb.mbicg_server_hold(srv, False)
+        infos = []
+        for rid, B, k in zip(ids, Bs, kappas):
+            X = np.empty_like(B)
+            st, it, tres, info = mb.mbicg_server_wait(srv, rid, X, 12)
+            assert st == mb.MBICG_OK and max(tres) <= TOL
+            assert rel_col_norm(X, oracle_X(oracle_mod, F2, U, B, k)) < 1e-7
+            infos.append(info)
+        spans = sorted((i["start_ms"], i["done_ms"]) for i in infos)
+        for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+            assert b0 >= a1  # one 12-column solve at a time
+        mem = mb.mbicg_server_memory(srv)
+        assert mem["memory_waits"] >= 1
+        assert mem["used_gb"] * 1e9 <= budget
+        # a block that could never fit is refused at submit
+        srv2 = mb.mbicg_server_create(0, (links + 0.5 * solve_bytes(V, 12)) / 1e9)
+        try:
+            f2 = mb.mbicg_server_add_field(srv2, F2, U, params(), 2)
+            with pytest.raises(mb.MbicgError) as e:
+                mb.mbicg_server_submit(srv2, f2, Bs[0], 12, 0.12, TOL)
+            assert e.value.status == mb.MBICG_ENOMEM
+            # two columns fit: admitted and solved
+            b2 = np.ascontiguousarray(Bs[0][..., :2])
+            st, X2, tres2, _ = solve(srv2, f2, b2, 2, 0.12)
+            assert st == mb.MBICG_OK and max(tres2) <= TOL
+        finally:
+            mb.mbicg_server_destroy(srv2)
     finally:
         mb.mbicg_server_destroy(srv)
-    assert one_slot_gb > per_slot / 1e9
