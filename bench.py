@@ -97,11 +97,12 @@ def sap_sweep_bytes(V, L, real_bytes=4):
 def sap_sweep_flops(V, L, nmr, frozen=True):
     """The MR steps of one colour sweep: nmr applications of the Dirichlet
     domain operator (the last one is not needed when the step lengths are
-    frozen), x += w r and r -= w q (16 flops per complex pair, 12 pairs) and,
-    per column, the two dot products (8 flops per pair)."""
-    ops = nmr - 1 if frozen else nmr
-    mr = nmr * 12 * 16 + (0 if frozen else nmr * 12 * 8)
-    return (V // 2) * L * (ops * 1368 + mr)
+    frozen), x += w r and r -= w q (8 flops per complex multiply-add, 12 per
+    spinor: 192 flops, 96 in the last frozen step) and, per column, the two
+    dot products (12 flops per complex pair)."""
+    if frozen:
+        return (V // 2) * L * ((nmr - 1) * 1368 + (nmr - 1) * 192 + 96)
+    return (V // 2) * L * (nmr * 1368 + nmr * 192 + nmr * 12 * 12)
 
 
 def sap_resid_bytes(V, L, block, real_bytes=4):

@@ -145,9 +145,9 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Ge
                                                       const cx<R>* __restrict__ links,
                                                       const cx<R>* __restrict__ eta,
                                                       const cx<R>* __restrict__ psi,
-                                                      cx<R>* __restrict__ r, int L, R kappa,
+                                                      cx<R>* __restrict__ r, int L, int c0, R kappa,
                                                       int psi_zero, const R* __restrict__ clov) {
-  const int rhs = threadIdx.x;
+  const int rhs = c0 + threadIdx.x;
   const int slot = blockIdx.x * blockDim.y + threadIdx.y;
   int c[4], lc[4], k;
   colour_slot_coords(g, colour, slot, c, lc, &k);
@@ -214,9 +214,9 @@ __global__ void __launch_bounds__(384, 2) k_sap_residual_h(Geom g, int colour, c
                                                            const __half2* __restrict__ eta, const float* __restrict__ esc,
                                                            const __half2* __restrict__ psi,
                                                            const float* __restrict__ psc, __half2* __restrict__ r,
-                                                           float* __restrict__ rsc, int L, float kappa,
+                                                           float* __restrict__ rsc, int L, int c0, float kappa,
                                                            const float* __restrict__ clov) {
-  const int rhs = threadIdx.x;
+  const int rhs = c0 + threadIdx.x;
   const int slot = blockIdx.x * blockDim.y + threadIdx.y;
   int c[4], lc[4], k;
   colour_slot_coords(g, colour, slot, c, lc, &k);
@@ -570,8 +570,9 @@ template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM
 __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS,
                                   (SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS <= 256) ? 2 : 1)
     k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const void* __restrict__ rin,
-                const float* __restrict__ rsc, void* __restrict__ psi, float* __restrict__ psc, int L, float kappa,
-                int psi_mode, int nmr, int mode, const double* __restrict__ table, const float* __restrict__ tinv) {
+                const float* __restrict__ rsc, void* __restrict__ psi, float* __restrict__ psc, int L, int c0, int nc,
+                float kappa, int psi_mode, int nmr, int mode, const double* __restrict__ table,
+                const float* __restrict__ tinv) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   constexpr int NS = SH::NS;
   constexpr int CS = SH::CS;
@@ -604,7 +605,8 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
   // major, are cut into one contiguous range per cluster
   const int nclu = gridDim.x / CS;
   const int cid = blockIdx.x / CS;
-  const long long nitems = (long long)ndc * L;
+  // the columns c0 .. c0 + nc - 1 of the L-column blocks
+  const long long nitems = (long long)ndc * nc;
   const int item0 = (int)(nitems * cid / nclu);
   const int item1 = (int)(nitems * (cid + 1) / nclu);
   const uint32_t uA = cluster_addr(smem_addr(uS), (uint32_t)rank);  // own link planes, cluster window
@@ -623,8 +625,8 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
   // psi update instead of stalling the cluster at the next item's start.
   bool have_rn = false;
   for (int item = item0; item < item1; ++item) {
-    const int kk = item / L;
-    const int rhs = item - kk * L;
+    const int kk = item / nc;
+    const int rhs = c0 + item - kk * nc;
     if (kk != k) {
       k = kk;  // a new domain of this colour
       int b[4];
@@ -672,7 +674,7 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
         if (item + 1 < item1) {
           // the next item: the next column of this site, or the first column
           // of the next domain
-          const int kn = (item + 1) / L;
+          const int kn = (item + 1) / nc;
           int sn = s;
           if (kn != kk) {
             int b[4], cn[4];
@@ -683,7 +685,7 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
             cn[3] = b[3] * DT + lc[3];
             sn = site_index(g, cn);
           }
-          const size_t offn = spinor_offset(sn, L, item + 1 - kn * L);
+          const size_t offn = spinor_offset(sn, L, c0 + item + 1 - kn * nc);
           const float4* src = reinterpret_cast<const float4*>(static_cast<const cx<float>*>(rin) + offn);
 #pragma unroll
           for (int j = 0; j < 6; ++j) cp_async_16(nxt + j * NS + tid, src + j);
@@ -797,8 +799,8 @@ int sweep_setup(cudaLaunchConfig_t cfg) {
 
 template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM, bool H>
 bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const void* rin, const float* rsc,
-                  void* psi, float* psc, int L, double kappa, int psi_mode, int nmr, int mode, const double* table,
-                  const float* tinv) {
+                  void* psi, float* psc, int L, int c0, int nc, double kappa, int psi_mode, int nmr, int mode,
+                  const double* table, const float* tinv) {
   using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
   auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM, H>;
   const size_t shm = SH::smem_bytes();
@@ -817,33 +819,33 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
   // in one GPC, so fewer than SMs / CS may be resident at once); set up once
   // per process, thread-safely (contexts may run on several host threads)
   static const int max_clusters = sweep_setup<DX, DY, DZ, DT, CX, CY, CZ, CT, CM, H>(cfg);
-  const long long nitems = (long long)(g.nd / 2) * L;
+  const long long nitems = (long long)(g.nd / 2) * nc;
   const int nclu = (int)std::min<long long>(max_clusters, nitems);
   cfg.gridDim = dim3((unsigned)(SH::CS * nclu));
-  cudaLaunchKernelEx(&cfg, kern, g, colour, links, rin, rsc, psi, psc, L, (float)kappa, psi_mode, nmr, mode, table,
-                     tinv);
+  cudaLaunchKernelEx(&cfg, kern, g, colour, links, rin, rsc, psi, psc, L, c0, nc, (float)kappa, psi_mode, nmr, mode,
+                     table, tinv);
   ++*ex.launches;
   return true;
 }
 
 template <bool H>
 bool sweep_dispatch(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const void* rin,
-                    const float* rsc, void* psi, float* psc, int L, double kappa, int psi_mode, int nmr, int mode,
-                    const double* table, const float* tinv) {
+                    const float* rsc, void* psi, float* psc, int L, int c0, int nc, double kappa, int psi_mode, int nmr,
+                    int mode, const double* table, const float* tinv) {
   const int* bk = g.blk;
   // 8^4: eight CTAs of 8 x 4 x 4 x 4 sites (x, the unit-stride direction, is
   // not split, so its hops never leave the CTA); 4^4: one CTA
   if (bk[0] == 8) {
     if (tinv)
-      return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 1, H>(ex, g, colour, links, rin, rsc, psi, psc, L, kappa, psi_mode,
+      return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 1, H>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa, psi_mode,
                                                         nmr, mode, table, tinv);
-    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 0, H>(ex, g, colour, links, rin, rsc, psi, psc, L, kappa, psi_mode,
+    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 0, H>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa, psi_mode,
                                                       nmr, mode, table, nullptr);
   }
   if (tinv)
-    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 1, H>(ex, g, colour, links, rin, rsc, psi, psc, L, kappa, psi_mode,
+    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 1, H>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa, psi_mode,
                                                       nmr, mode, table, tinv);
-  return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 0, H>(ex, g, colour, links, rin, rsc, psi, psc, L, kappa, psi_mode,
+  return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 0, H>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa, psi_mode,
                                                     nmr, mode, table, nullptr);
 }
 
@@ -857,30 +859,32 @@ bool sap_sweep_fusable(const Geom& g, int mode) {
 
 bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* eta,
                      cx<float>* psi, int L, double kappa, int psi_mode, int nmr, int mode, const double* table,
-                     const float* tinv) {
+                     const float* tinv, int c0, int nc) {
   if (!sap_sweep_fusable(g, mode)) return false;
-  return sweep_dispatch<false>(ex, g, colour, links, eta, nullptr, psi, nullptr, L, kappa, psi_mode, nmr, mode, table,
-                               tinv);
+  return sweep_dispatch<false>(ex, g, colour, links, eta, nullptr, psi, nullptr, L, c0, nc > 0 ? nc : L, kappa,
+                               psi_mode, nmr, mode, table, tinv);
 }
 
 bool sap_sweep_fused_h(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const __half2* rin,
                        const float* rsc, __half2* psi, float* psc, int L, double kappa, int psi_mode, int nmr,
-                       int mode, const double* table, const float* tinv) {
+                       int mode, const double* table, const float* tinv, int c0, int nc) {
   if (!sap_sweep_fusable(g, mode)) return false;
-  return sweep_dispatch<true>(ex, g, colour, links, rin, rsc, psi, psc, L, kappa, psi_mode, nmr, mode, table, tinv);
+  return sweep_dispatch<true>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc > 0 ? nc : L, kappa, psi_mode, nmr,
+                              mode, table, tinv);
 }
 
 void sap_residual_h(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const __half2* eta,
                     const float* esc, const __half2* psi, const float* psc, __half2* r, float* rsc, int L, double kappa,
-                    const float* tinv) {
-  const int S = sap_sites_per_cta(g, L, false);
+                    const float* tinv, int c0, int nc) {
+  if (nc <= 0) nc = L;
+  const int S = sap_sites_per_cta(g, nc, false);
   const int nslot = (g.nd / 2) * g.Vd;
   if (tinv)
-    k_sap_residual_h<1><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, esc, psi, psc, r,
-                                                                            rsc, L, (float)kappa, tinv);
+    k_sap_residual_h<1><<<(unsigned)(nslot / S), dim3(nc, S), 0, ex.stream>>>(g, colour, links, eta, esc, psi, psc,
+                                                                             r, rsc, L, c0, (float)kappa, tinv);
   else
-    k_sap_residual_h<0><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, esc, psi, psc, r,
-                                                                            rsc, L, (float)kappa, nullptr);
+    k_sap_residual_h<0><<<(unsigned)(nslot / S), dim3(nc, S), 0, ex.stream>>>(g, colour, links, eta, esc, psi, psc,
+                                                                             r, rsc, L, c0, (float)kappa, nullptr);
   ++*ex.launches;
 }
 
@@ -965,15 +969,16 @@ void tune_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>*
 
 template <typename R>
 void sap_residual(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* eta,
-                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero, const R* tinv) {
-  const int S = sap_sites_per_cta(g, L, sizeof(R) == 8);
+                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero, const R* tinv, int c0, int nc) {
+  if (nc <= 0) nc = L;
+  const int S = sap_sites_per_cta(g, nc, sizeof(R) == 8);
   const int nslot = (g.nd / 2) * g.Vd;
   if (tinv)
-    k_sap_residual<R, 1><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, psi, r, L,
-                                                                               (R)kappa, psi_zero ? 1 : 0, tinv);
+    k_sap_residual<R, 1><<<(unsigned)(nslot / S), dim3(nc, S), 0, ex.stream>>>(g, colour, links, eta, psi, r, L, c0,
+                                                                                (R)kappa, psi_zero ? 1 : 0, tinv);
   else
-    k_sap_residual<R, 0><<<(unsigned)(nslot / S), dim3(L, S), 0, ex.stream>>>(g, colour, links, eta, psi, r, L,
-                                                                               (R)kappa, psi_zero ? 1 : 0, nullptr);
+    k_sap_residual<R, 0><<<(unsigned)(nslot / S), dim3(nc, S), 0, ex.stream>>>(g, colour, links, eta, psi, r, L, c0,
+                                                                                (R)kappa, psi_zero ? 1 : 0, nullptr);
   ++*ex.launches;
 }
 
@@ -1016,7 +1021,7 @@ void ssor_level(const Exec& ex, const Geom& g, int colour, const cx<R>* links, c
                                const R*, int);                                                          \
   template void tune_dslash<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double); \
   template void sap_residual<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, const cx<R>*,   \
-                                cx<R>*, int, double, bool, const R*);                                     \
+                                cx<R>*, int, double, bool, const R*, int, int);                           \
   template void sap_domain_apply<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, cx<R>*,     \
                                     double*, int, double, int*, const R*);                                \
   template void ssor_level<R>(const Exec&, const Geom&, int, const cx<R>*, const R*, const cx<R>*, cx<R>*, \

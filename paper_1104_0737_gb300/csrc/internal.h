@@ -76,6 +76,10 @@ struct Exec {
   cudaStream_t stream;
   long long* launches;
   Prof* prof;
+  // a second stream of the context for work that may overlap the first
+  // (NULL: none), and two events to fork to it and join back
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // RAII: time the launches in a scope as one class
@@ -148,7 +152,8 @@ void dslash_half(const Exec& ex, const Geom& g, const __half2* l16, const __half
 //   (tinv != NULL: the Jacobi-preconditioned clover matrix, H -> T^{-1} H)
 template <typename R>
 void sap_residual(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* eta,
-                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero, const R* tinv = nullptr);
+                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero, const R* tinv = nullptr,
+                  int c0 = 0, int nc = 0);
 //   q = r - kappa H_dom r  (hops leaving the domain dropped) and, if dots is
 //   not NULL, per-CTA partial sums of q^H r and q^H q for every column:
 //   dots[((k * nchunk) + chunk) * L + rhs] = {Re q^H r, Im q^H r, q^H q}
@@ -162,9 +167,11 @@ void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* li
 // table: the frozen step lengths of this (cycle, colour), [nmr][nd/2] complex.
 // rin: the residual of this colour's sites at entry (eta itself when
 // psi_mode = 1, psi = 0 on entry and psi = x on exit; psi_mode = 2: psi += x).
+// c0, nc: only the columns c0 .. c0 + nc - 1 of the L-column blocks (nc = 0:
+// all L); the preconditioner acts on each column by itself in modes 0 and 3.
 bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* rin,
                      cx<float>* psi, int L, double kappa, int psi_mode, int nmr, int mode,
-                     const double* table, const float* tinv = nullptr);
+                     const double* table, const float* tinv = nullptr, int c0 = 0, int nc = 0);
 // whether sap_sweep_fused takes this domain shape, MR mode and field
 bool sap_sweep_fusable(const Geom& g, int mode);
 // The same sweep on the preconditioner's FP16 storage: rin and psi as FP16
@@ -172,11 +179,11 @@ bool sap_sweep_fusable(const Geom& g, int mode);
 // arithmetic on chip.
 bool sap_sweep_fused_h(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const __half2* rin,
                        const float* rsc, __half2* psi, float* psc, int L, double kappa, int psi_mode, int nmr,
-                       int mode, const double* table, const float* tinv = nullptr);
+                       int mode, const double* table, const float* tinv = nullptr, int c0 = 0, int nc = 0);
 // r = eta - A psi on the sites of one colour, eta, psi and r in FP16 storage
 void sap_residual_h(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const __half2* eta,
                     const float* esc, const __half2* psi, const float* psc, __half2* r, float* rsc, int L, double kappa,
-                    const float* tinv = nullptr);
+                    const float* tinv = nullptr, int c0 = 0, int nc = 0);
 // SSOR (Sec. 2.2): one wavefront level of z = (1 - omega L)^{-1} y (fwd) or
 // z = (1 - omega U)^{-1} y on every domain of one colour, L and U the forward
 // and backward hops inside a domain (times T^{-1} with tinv); komega =

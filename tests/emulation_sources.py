@@ -227,6 +227,7 @@ def driver_parts(csrc=CSRC):
                       "{ return emu_mapa(local, rank); }")
     ds = replace_body(ds, "__device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr)",
                       "{ return emu_ld_cluster_f4(addr); }")
+    ds = _plain_cp_async(ds)
     sp = read("sap.cu", csrc)
     sp = sp[sp.index("namespace mbicg {"):]
     body = rewrite_launches(ds + "\n" + sp)

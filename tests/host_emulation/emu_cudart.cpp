@@ -139,6 +139,9 @@ cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t) {
   event_times[reinterpret_cast<size_t>(e)] = now;
   return cudaSuccess;
 }
+cudaError_t cudaEventCreateWithFlags(cudaEvent_t* e, unsigned int) { return cudaEventCreate(e); }
+// launches run to completion when they are made, so stream order holds already
+cudaError_t cudaStreamWaitEvent(cudaStream_t, cudaEvent_t, unsigned int) { return cudaSuccess; }
 cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
 cudaError_t cudaEventElapsedTime(float* ms, cudaEvent_t a, cudaEvent_t b) {
   std::lock_guard<std::mutex> g(mu);

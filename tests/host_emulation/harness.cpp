@@ -105,10 +105,10 @@ void emu_sap_residual(const int* dims, const int* block, const double* U, int co
   const Geom g = make_geom(dims, block);
   grid((g.nd / 2) * g.Vd, L, [&] {
     if (tinv)
-      emu_dslash::k_sap_residual<double, 1>(g, colour, (const C*)U, (const C*)eta, (const C*)psi, (C*)r, L, kappa,
+      emu_dslash::k_sap_residual<double, 1>(g, colour, (const C*)U, (const C*)eta, (const C*)psi, (C*)r, L, 0, kappa,
                                             psi_zero, tinv);
     else
-      emu_dslash::k_sap_residual<double, 0>(g, colour, (const C*)U, (const C*)eta, (const C*)psi, (C*)r, L, kappa,
+      emu_dslash::k_sap_residual<double, 0>(g, colour, (const C*)U, (const C*)eta, (const C*)psi, (C*)r, L, 0, kappa,
                                             psi_zero, nullptr);
   });
 }

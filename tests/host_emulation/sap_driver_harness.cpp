@@ -24,6 +24,8 @@ extern "C" cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t) { return cudaE
 extern "C" cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaErrorNotSupported; }
 extern "C" cudaError_t cudaEventElapsedTime(float*, cudaEvent_t, cudaEvent_t) { return cudaErrorNotSupported; }
 extern "C" cudaError_t cudaEventDestroy(cudaEvent_t) { return cudaSuccess; }
+// launches run to completion when they are made, so stream order holds already
+extern "C" cudaError_t cudaStreamWaitEvent(cudaStream_t, cudaEvent_t, unsigned int) { return cudaSuccess; }
 extern "C" cudaError_t cudaStreamIsCapturing(cudaStream_t, enum cudaStreamCaptureStatus* st) {
   *st = cudaStreamCaptureStatusNone;
   return cudaSuccess;

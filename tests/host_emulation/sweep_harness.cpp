@@ -35,12 +35,12 @@ static void run(const Geom& g, int colour, const float* links, const float* eta,
   emu_launch(nclusters, SH::CS, SH::NS, SH::smem_bytes(), [&] {
     if (tinv)
       emu_dslash::k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, 1, false>(g, colour, (const C*)links, eta, nullptr,
-                                                                         psi, nullptr, L, kappa, psi_mode, nmr, mode,
-                                                                         table, tinv);
+                                                                         psi, nullptr, L, 0, L, kappa, psi_mode, nmr,
+                                                                         mode, table, tinv);
     else
       emu_dslash::k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, 0, false>(g, colour, (const C*)links, eta, nullptr,
-                                                                         psi, nullptr, L, kappa, psi_mode, nmr, mode,
-                                                                         table, nullptr);
+                                                                         psi, nullptr, L, 0, L, kappa, psi_mode, nmr,
+                                                                         mode, table, nullptr);
   });
 }
 

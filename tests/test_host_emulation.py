@@ -33,8 +33,15 @@ PARTS = [
 
 
 def _device_parts():
-    out = ['#include "shim.h"', "#include <cuda_fp16.h>", "#include <cstring>",
-           f'#include "{os.path.join(emulation_sources.CSRC, "common.cuh")}"', "namespace mbicg {"]
+    # common.cuh with its inline-PTX spinor loads and stores written as plain C++
+    common = emulation_sources.read("common.cuh")
+    common = emulation_sources.replace_body(
+        common, "__device__ __forceinline__ void load_spinor(const cx<float>* p, Spinor<float>& s)",
+        "{ for (int k = 0; k < 12; ++k) (&s.c[0][0])[k] = p[k]; }")
+    common = emulation_sources.replace_body(
+        common, "__device__ __forceinline__ void store_spinor(cx<float>* p, const Spinor<float>& s)",
+        "{ for (int k = 0; k < 12; ++k) p[k] = (&s.c[0][0])[k]; }")
+    out = ['#include "shim.h"', "#include <cuda_fp16.h>", "#include <cstring>", common, "namespace mbicg {"]
     for ns, name, start, end in PARTS:
         out += [f"namespace {ns} {{", emulation_sources.cut(emulation_sources.read(name), start, end), "}"]
     out.append("}")
