@@ -35,8 +35,6 @@ struct mbicg_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  cudaStream_t aux = nullptr;  // second stream: work that may overlap `stream`
-  cudaEvent_t fork = nullptr, join = nullptr;
   int dims[4] = {0, 0, 0, 0};
   long long V = 0;
   cx<double>* U64 = nullptr;
@@ -151,7 +149,7 @@ bool valid_blocking(const mbicg_ctx* c, const int* block) {
   return vd <= (1 << 20);
 }
 
-Exec exec_of(mbicg_ctx* c) { return Exec{c->stream, &c->launches, &c->prof, c->aux, c->fork, c->join}; }
+Exec exec_of(mbicg_ctx* c) { return Exec{c->stream, &c->launches, &c->prof}; }
 
 int check_launch(mbicg_ctx* c, const char* where) {
   cudaError_t e = cudaGetLastError();
@@ -987,12 +985,6 @@ int mbicg_create(mbicg_ctx** out, const int dims[4], int device, void* cuda_stre
     }
     c->own_stream = true;
   }
-  if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();  // without them the preconditioner runs on one stream
-    c->aux = nullptr;
-  }
   if (cudaMallocHost(&c->h_small, sizeof(double) * H_SMALL) != cudaSuccess) {
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1015,10 +1007,6 @@ void mbicg_destroy(mbicg_ctx* c) {
   if (c->Ti64) cudaFree(c->Ti64);
   if (c->Ti32) cudaFree(c->Ti32);
   c->prof.release();
-  if (c->aux) cudaStreamSynchronize(c->aux);
-  if (c->aux) cudaStreamDestroy(c->aux);
-  if (c->fork) cudaEventDestroy(c->fork);
-  if (c->join) cudaEventDestroy(c->join);
   if (c->h_small) cudaFreeHost(c->h_small);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -76,10 +76,6 @@ struct Exec {
   cudaStream_t stream;
   long long* launches;
   Prof* prof;
-  // a second stream of the context for work that may overlap the first
-  // (NULL: none), and two events to fork to it and join back
-  cudaStream_t aux = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // RAII: time the launches in a scope as one class
@@ -168,7 +164,7 @@ void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* li
 // rin: the residual of this colour's sites at entry (eta itself when
 // psi_mode = 1, psi = 0 on entry and psi = x on exit; psi_mode = 2: psi += x).
 // c0, nc: only the columns c0 .. c0 + nc - 1 of the L-column blocks (nc = 0:
-// all L); the preconditioner acts on each column by itself in modes 0 and 3.
+// all L; the preconditioner acts on each column by itself in modes 0 and 3).
 bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const cx<float>* rin,
                      cx<float>* psi, int L, double kappa, int psi_mode, int nmr, int mode,
                      const double* table, const float* tinv = nullptr, int c0 = 0, int nc = 0);

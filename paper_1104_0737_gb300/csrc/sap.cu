@@ -168,14 +168,6 @@ __global__ void __launch_bounds__(512) k_colour_add(Geom g, int colour, const cx
 // ---------------------------------------------------------------------------
 namespace {
 
-// The fused sweeps of the two halves of the columns run on two streams when
-// the context has a second stream, L >= 2 and no per-kernel timing is on
-// (its events belong to one stream); MBICG_SAP_SPLIT=0 turns it off.
-bool split_columns(const Exec& ex, int L) {
-  const char* env = getenv("MBICG_SAP_SPLIT");
-  if (env && env[0] == '0') return false;
-  return ex.aux && ex.fork && ex.join && L >= 2 && !(ex.prof && ex.prof->on);
-}
 
 // out = B y on every domain of one colour (Sec. 2.2):
 //   B = (1 - omega U)^{-1} [sum_{j=0}^{nssor} (1 - Ahat)^j] (1 - omega L)^{-1},
@@ -263,33 +255,6 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
   }
   const char* fused_env = getenv("MBICG_SAP_FUSED");
   const bool allow_fused = !(fused_env && fused_env[0] == '0');
-  if constexpr (std::is_same<R, float>::value) {
-    if (allow_fused && sap_sweep_fusable(g, mr_mode) && split_columns(ex, L)) {
-      // Modes 0 and 3 act on every column by itself: two halves of the
-      // columns on two streams, so that one half's residual kernel runs on
-      // the SMs the other half's cluster sweep leaves idle.
-      Exec ea = ex;
-      ea.stream = ex.aux;
-      cudaEventRecord(ex.fork, ex.stream);
-      cudaStreamWaitEvent(ex.aux, ex.fork, 0);
-      const int n0 = L / 2;
-      for (int cyc = 0; cyc < ncycle; ++cyc)
-        for (int colour = 0; colour < 2; ++colour) {
-          const double* tab = table ? table + ((long long)cyc * 2 + colour) * nmr * ndc * 2 : nullptr;
-          const bool first = cyc == 0 && colour == 0;
-          for (int half = 0; half < 2; ++half) {
-            const Exec& e = half ? ea : ex;
-            const int c0 = half ? n0 : 0, nc = half ? L - n0 : n0;
-            if (!first) sap_residual<R>(e, g, colour, links, eta, psi, r, L, kappa, false, tinv, c0, nc);
-            sap_sweep_fused(e, g, colour, links, first ? eta : r, psi, L, kappa, first ? 1 : 2, nmr, mr_mode, tab,
-                            tinv, c0, nc);
-          }
-        }
-      cudaEventRecord(ex.join, ex.aux);
-      cudaStreamWaitEvent(ex.stream, ex.join, 0);
-      return;
-    }
-  }
   for (int cyc = 0; cyc < ncycle; ++cyc) {
     for (int colour = 0; colour < 2; ++colour) {
       if constexpr (std::is_same<R, float>::value) {
@@ -341,30 +306,6 @@ void sap_apply_h(const Exec& ex, const Geom& g, const cx<float>* links, const Sa
   // every site from the second sweep on
   cudaMemsetAsync(h.psi, 0, sizeof(__half2) * 12 * nsp, ex.stream);
   cudaMemsetAsync(h.psi_sc, 0, sizeof(float) * nsp, ex.stream);
-  if (split_columns(ex, L)) {
-    // two halves of the columns on two streams (as in sap_apply)
-    Exec ea = ex;
-    ea.stream = ex.aux;
-    cudaEventRecord(ex.fork, ex.stream);
-    cudaStreamWaitEvent(ex.aux, ex.fork, 0);
-    const int n0 = L / 2;
-    for (int cyc = 0; cyc < ncycle; ++cyc)
-      for (int colour = 0; colour < 2; ++colour) {
-        const double* tab = table ? table + ((long long)cyc * 2 + colour) * nmr * ndc * 2 : nullptr;
-        const bool first = cyc == 0 && colour == 0;
-        for (int half = 0; half < 2; ++half) {
-          const Exec& e = half ? ea : ex;
-          const int c0 = half ? n0 : 0, nc = half ? L - n0 : n0;
-          if (!first)
-            sap_residual_h(e, g, colour, links, h.eta, h.eta_sc, h.psi, h.psi_sc, h.r, h.r_sc, L, kappa, tinv, c0, nc);
-          sap_sweep_fused_h(e, g, colour, links, first ? h.eta : h.r, first ? h.eta_sc : h.r_sc, h.psi, h.psi_sc, L,
-                            kappa, first ? 1 : 2, nmr, mr_mode, tab, tinv, c0, nc);
-        }
-      }
-    cudaEventRecord(ex.join, ex.aux);
-    cudaStreamWaitEvent(ex.stream, ex.join, 0);
-    return;
-  }
   for (int cyc = 0; cyc < ncycle; ++cyc)
     for (int colour = 0; colour < 2; ++colour) {
       const double* tab = table ? table + ((long long)cyc * 2 + colour) * nmr * ndc * 2 : nullptr;
