@@ -70,7 +70,8 @@ typedef enum {
 typedef struct {
   /* SAP preconditioner, Sec. 2.2: psi = K sum_{j=0}^{ncycle-1} (1 - A K)^j eta
    * over checkerboard-coloured domains of extent block[4]; the domain solves
-   * B_EE, B_OO are nmr MR steps started from zero.  ncycle = 0 selects M = 1.
+   * B_EE, B_OO are nmr MR steps started from zero (1 <= nmr <= 256).
+   * ncycle = 0 selects M = 1.
    * Each block[mu] must divide dims[mu] and give an even number >= 2 of
    * domains in every direction. */
   int ncycle;

@@ -46,11 +46,14 @@ struct GramShape {
   static constexpr int LANES = NT / NB > 0 ? NT / NB : 1;
   static constexpr int TS = gram_tile_sites(L, (int)sizeof(R));
   static constexpr int TILE = TS * L * 12;  // complex numbers per tile per array
-  static constexpr int STAGES = 2;
+  // A^H A streams one array: six stages of it in the room of two stages of
+  // three arrays, so that more tiles are in flight per CTA
+  static constexpr int NARR = HERM ? 1 : 3;
+  static constexpr int STAGES = HERM ? 6 : 2;
   static constexpr size_t tile_bytes = sizeof(cx<R>) * (size_t)TILE;
   static constexpr size_t red_g = sizeof(cx<double>) * LANES * L * L;
   static constexpr size_t red_d = sizeof(cx<double>) * 2 * (NT / L) * L;
-  static constexpr size_t stage_area = tile_bytes * 3 * STAGES;
+  static constexpr size_t stage_area = tile_bytes * NARR * STAGES;
   static constexpr size_t red_bytes = red_g > red_d ? red_g : red_d;
   static constexpr size_t smem = (stage_area > red_bytes ? stage_area : red_bytes) + 64;
 };
@@ -61,7 +64,8 @@ __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __
                                              int flags, double* __restrict__ part, int* __restrict__ err) {
   using SH = GramShape<R, L, HERM>;
   constexpr int BB = SH::BB, NBI = SH::NBI, NB = SH::NB, LANES = SH::LANES, TS = SH::TS, TILE = SH::TILE;
-  constexpr int STAGES = SH::STAGES;
+  constexpr int STAGES = SH::STAGES, NARR = SH::NARR;
+  static_assert(STAGES * sizeof(uint64_t) <= 64, "the stages' mbarriers live in the last 64 bytes");
   // FP32 per-tile sums are widened into FP64 running sums every FLUSH tiles
   constexpr int FLUSH = sizeof(R) == 4 ? 8 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -69,10 +73,11 @@ __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __
   cx<R>* stage0 = reinterpret_cast<cx<R>*>(smem_raw);
 
   const bool g1 = flags & 1, g2 = flags & 2, d1 = flags & 4, d2 = flags & 8;
-  const bool a_is_b1 = (A == B1);
+  // HERM: A = B1 and G1 alone (the launcher's choice), one array per stage
+  const bool a_is_b1 = HERM || (A == B1);
   const bool loadA = g1 || g2 || a_is_b1;
   const bool loadB1 = !a_is_b1;
-  const bool loadB2 = B2 != nullptr;
+  const bool loadB2 = !HERM && B2 != nullptr;
   const int tid = threadIdx.x;
   const int blk = tid % NB;
   const int lane = tid / NB;
@@ -118,7 +123,7 @@ __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __
     const int ns = (int)min((long long)TS, nsite - site0);
     const uint32_t bytes = (uint32_t)(sizeof(cx<R>) * (size_t)ns * L * 12);
     const int st = j % STAGES;
-    cx<R>* dst = stage0 + (size_t)st * 3 * TILE;
+    cx<R>* dst = stage0 + (size_t)st * NARR * TILE;
     const uint32_t total = bytes * ((loadA ? 1 : 0) + (loadB1 ? 1 : 0) + (loadB2 ? 1 : 0));
     mbar_arrive_expect_tx(&bars[st], total);
     const size_t off = (size_t)site0 * L * 12;
@@ -138,7 +143,7 @@ __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __
     const bool arrived = mbar_wait_bounded(&bars[st], (uint32_t)((j / STAGES) & 1));
     const long long site0 = (blockIdx.x + (long long)j * gridDim.x) * TS;
     const int ns = (int)min((long long)TS, nsite - site0);
-    const cx<R>* sA = stage0 + (size_t)st * 3 * TILE;
+    const cx<R>* sA = stage0 + (size_t)st * NARR * TILE;
     const cx<R>* tB1 = a_is_b1 ? sA : sA + TILE;
     const cx<R>* sB2 = sA + 2 * TILE;
     const int nrows = ns * 12;
@@ -356,14 +361,16 @@ __global__ void __launch_bounds__(NT) k_update_alpha(int nrow, const cx<R>* __re
 
 // X += U alpha + zeta S (the X update of Algorithm 1, 4.9, which Algorithm 2
 // splits into 4.6 and 4.10), R -= zeta Z (4.11), P = R + (P - zeta V) beta
-// (4.13), and the squared column norms of the new R.
+// (4.13), and the squared column norms of the new R.  X is the solution in
+// the Krylov vectors' precision (with FP32 vectors, the sum of the updates
+// since the last reliable update).
 // zb = [zeta, beta (L x L)] complex double
 template <typename R, int L>
 __global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __restrict__ U,
                                                     const double* __restrict__ alpha, const cx<R>* __restrict__ S,
                                                     const cx<R>* __restrict__ Z, const cx<R>* __restrict__ V,
                                                     const double* __restrict__ zb, cx<R>* __restrict__ Rv,
-                                                    cx<R>* __restrict__ P, cx<double>* __restrict__ X64,
+                                                    cx<R>* __restrict__ P, cx<R>* __restrict__ X,
                                                     double* __restrict__ part) {
   __shared__ cx<R> sB[L * L];
   __shared__ cx<R> sA[L * L];
@@ -372,7 +379,6 @@ __global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __res
     sB[e] = mk((R)zb[2 + 2 * e], (R)zb[3 + 2 * e]);
     sA[e] = mk((R)alpha[2 * e], (R)alpha[2 * e + 1]);
   }
-  const cx<double> zeta64 = mk(zb[0], zb[1]);
   const cx<R> zeta = mk((R)zb[0], (R)zb[1]);
   __syncthreads();
   R nrm[L];
@@ -391,10 +397,10 @@ __global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __res
 #pragma unroll
         for (int k = 0; k < L; ++k) cmac(ua, u[k], sA[k * L + j]);
         const cx<R> s = S[b + j * 12];
-        cx<double> x = X64[b + j * 12];
-        x.re += (double)ua.re + (zeta64.re * (double)s.re - zeta64.im * (double)s.im);
-        x.im += (double)ua.im + (zeta64.re * (double)s.im + zeta64.im * (double)s.re);
-        X64[b + j * 12] = x;
+        cx<R> x = X[b + j * 12];
+        x.re += ua.re + (zeta.re * s.re - zeta.im * s.im);
+        x.im += ua.im + (zeta.re * s.im + zeta.im * s.re);
+        X[b + j * 12] = x;
       }
     }
 #pragma unroll
@@ -423,6 +429,20 @@ __global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __res
     }
     if (threadIdx.x == 0) part[(long long)blockIdx.x * L + j] = sred[0];
     __syncthreads();
+  }
+}
+
+// X64 += Xs, Xs = 0 (n complex numbers): the FP32 solution updates folded
+// into the FP64 solution
+__global__ void __launch_bounds__(NT) k_fold_solution(long long n, cx<float>* __restrict__ Xs,
+                                                      cx<double>* __restrict__ X64) {
+  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
+    const cx<float> d = Xs[i];
+    cx<double> x = X64[i];
+    x.re += (double)d.re;
+    x.im += (double)d.im;
+    X64[i] = x;
+    Xs[i] = mk(0.0f, 0.0f);
   }
 }
 
@@ -908,14 +928,19 @@ void block_update_alpha(const Exec& ex, long long nsite, int L, const cx<R>* V, 
 
 template <typename R>
 int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* U, const double* alpha, const cx<R>* S,
-                      const cx<R>* Z, const cx<R>* V, const double* zeta_beta, cx<R>* Rv, cx<R>* P, cx<double>* X64,
+                      const cx<R>* Z, const cx<R>* V, const double* zeta_beta, cx<R>* Rv, cx<R>* P, cx<R>* X,
                       double* part) {
   const int nrow = (int)(nsite * 12);
   const int grid = row_grid(nrow);
-  DISPATCH_L(L, (k_update_zeta<R, LL><<<grid, NT, 0, ex.stream>>>(nrow, U, alpha, S, Z, V, zeta_beta, Rv, P, X64,
+  DISPATCH_L(L, (k_update_zeta<R, LL><<<grid, NT, 0, ex.stream>>>(nrow, U, alpha, S, Z, V, zeta_beta, Rv, P, X,
                                                                   part)));
   ++*ex.launches;
   return grid;
+}
+
+void fold_solution(const Exec& ex, long long n, cx<float>* Xs, cx<double>* X64) {
+  k_fold_solution<<<row_grid(n), NT, 0, ex.stream>>>(n, Xs, X64);
+  ++*ex.launches;
 }
 
 template <typename R>
@@ -1012,7 +1037,7 @@ void loop_control(const Exec& ex, LoopCtl* ctl, const double* norms, const doubl
   template void block_transform<R>(const Exec&, long long, int, const cx<R>*, const double*, cx<R>*);              \
   template void block_update_alpha<R>(const Exec&, long long, int, const cx<R>*, const double*, cx<R>*);         \
   template int block_update_zeta<R>(const Exec&, long long, int, const cx<R>*, const double*, const cx<R>*,        \
-                                    const cx<R>*, const cx<R>*, const double*, cx<R>*, cx<R>*, cx<double>*,       \
+                                    const cx<R>*, const cx<R>*, const double*, cx<R>*, cx<R>*, cx<R>*,            \
                                     double*);                                                                    \
   template void abi_to_internal<R>(const Exec&, long long, int, const cx<double>*, cx<R>*);                        \
   template void internal_to_abi<R>(const Exec&, long long, int, const cx<R>*, cx<double>*);                        \

@@ -16,6 +16,10 @@
 
 namespace mbicg {
 
+// MR steps per domain solve (the sweep keeps a domain's frozen step lengths
+// in shared memory)
+constexpr int MAX_NMR = 256;
+
 // ---------------------------------------------------------------------------
 // complex numbers
 // ---------------------------------------------------------------------------

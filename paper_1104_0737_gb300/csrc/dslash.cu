@@ -444,6 +444,15 @@ __device__ __forceinline__ void cp_async_16(float4* dst, const float4* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// The cluster barrier in two halves: arrive publishes this thread's earlier
+// shared-memory writes to the cluster (release), wait returns once every
+// thread of the cluster has arrived and makes their writes visible (acquire).
+// Work between the two halves may read only what this CTA wrote.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
 // Spinor of site `site` from 6 float4 planes of NS sites at cluster address base.
 __device__ __forceinline__ void cluster_planes_to_spinor(uint32_t base, int NS, int site, Spinor<float>& v) {
 #pragma unroll
@@ -501,11 +510,16 @@ __device__ __forceinline__ void planes_to_link12(const float4* uS, int NS, int m
 // address, uS the CTA's link planes already in the cluster window; vL and uL
 // are the same planes as pointers, read directly where the hop cannot leave
 // the CTA.  sb: coordinates inside the CTA's sub-block, lc: inside the domain.
-template <typename SH, int DX, int DY, int DZ, int DT, int CX, int CY, int CZ>
+// PHASE 0 zeroes acc and adds the hops whose neighbour lies in this CTA for
+// the whole warp (x, and z or t where the warp's neighbouring layer is in
+// this CTA): they need only this CTA's barrier.  PHASE 1 adds the others (y,
+// and z or t into the next CTA), after the cluster barrier.  PHASE 2 zeroes
+// acc and adds all eight.
+template <int PHASE, typename SH, int DX, int DY, int DZ, int DT, int CX, int CY, int CZ>
 __device__ __forceinline__ void domain_hops(const float4* vL, uint32_t vS, const float4* uL, uint32_t uS, int tid,
                                             int rank, const int sb[4], const int lc[4], Spinor<float>& acc) {
   constexpr int NS = SH::NS;
-  zero(acc);
+  if (PHASE != 1) zero(acc);
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
@@ -531,7 +545,9 @@ __device__ __forceinline__ void domain_hops(const float4* vL, uint32_t vS, const
         // for the whole warp: branch, and read this CTA's planes directly.
         // In y it differs inside a warp: one cluster-window load path for all.
         constexpr bool warp_uniform_zt = SH::SX * SH::SY >= 32;
-        if (pick4(mu, CX, CY, CZ, SH::CS / (CX * CY * CZ)) == 1 || (mu >= 2 && warp_uniform_zt && !cross)) {
+        const bool in_cta = pick4(mu, CX, CY, CZ, SH::CS / (CX * CY * CZ)) == 1 || (mu >= 2 && warp_uniform_zt && !cross);
+        if ((PHASE == 0 && !in_cta) || (PHASE == 1 && in_cta)) continue;
+        if (in_cta) {
           // the neighbour is in this CTA: plain shared loads
           planes_to_spinor(reinterpret_cast<const float4*>(vL), NS, nb, pn);
           planes_to_link12(uL, NS, mu, fwd ? tid : nb, u);
@@ -584,6 +600,7 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
   float4* uS = sm4 + 12 * NS;                              // [12][NS] link rows 0, 1
   float* red = reinterpret_cast<float*>(sm4 + 24 * NS);   // [CS][4] partial dots
   __shared__ float wsum[NS / 32][3];
+  __shared__ float2 oms[MAX_NMR];  // frozen step lengths of the current domain
 
   const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x;
@@ -613,7 +630,10 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
 
   // A buffer is written only after the cluster barrier that follows the last
   // reads of it by other CTAs; every write is followed by a barrier before
-  // the buffer is read.
+  // the buffer is read.  The barrier after a residual is written is split:
+  // each thread arrives once its writes are done, the hops into this CTA's
+  // own planes run after a CTA barrier, and the wait for the other CTAs
+  // comes just before the hops that read them.
   float4* cur = buf0;
   float4* nxt = buf1;
   int k = -1, s = 0;
@@ -648,6 +668,12 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
           const float2 v0 = __ldg(gl + mu * 9 + 2 * q), v1 = __ldg(gl + mu * 9 + 2 * q + 1);
           uS[(mu * 3 + q) * NS + tid] = make_float4(v0.x, v0.y, v1.x, v1.y);
         }
+      // the domain's frozen step lengths, rounded to FP32 once per domain
+      if (mode != 0)
+        for (int it = tid; it < nmr; it += NS) {
+          const double* tb = table + ((size_t)it * ndc + k) * 2;
+          oms[it] = make_float2((float)tb[0], (float)tb[1]);
+        }
     }
     const size_t off = spinor_offset(s, L, rhs);
     // the colour's residual at entry: eta itself when psi = 0, else
@@ -661,7 +687,7 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
       spinor_to_planes(nxt, NS, tid, r0);
     }
     have_rn = false;
-    cluster.sync();  // r0 (and, for the first column, every CTA's links) visible
+    cluster_arrive();  // r0 (and, for the first column, this CTA's links and step lengths) written
     { float4* t = cur; cur = nxt; nxt = t; }
     Spinor<float> x;
     zero(x);
@@ -670,6 +696,19 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
       const bool last = (it == nmr - 1);
       Spinor<float> q, rv;
       const bool need_q = (mode == 0) || !last;
+      if (need_q) {
+        __syncthreads();  // this CTA's residual planes
+        domain_hops<0, SH, DX, DY, DZ, DT, CX, CY, CZ>(cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, q);
+        cluster_wait();  // the other CTAs' residual planes
+        domain_hops<1, SH, DX, DY, DZ, DT, CX, CY, CZ>(cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, q);
+        if (CM == 1) {
+          Spinor<float> h;
+          herm_apply<float>(tinv + (size_t)s * HERM_PER_SITE, q, h);
+          q = h;
+        }
+      } else {
+        cluster_wait();  // no CTA reads nxt any more
+      }
       if (!H && last && !need_q) {
         if (item + 1 < item1) {
           // the next item: the next column of this site, or the first column
@@ -691,14 +730,6 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
           for (int j = 0; j < 6; ++j) cp_async_16(nxt + j * NS + tid, src + j);
           cp_async_commit();
           have_rn = true;
-        }
-      }
-      if (need_q) {
-        domain_hops<SH, DX, DY, DZ, DT, CX, CY, CZ>(cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, q);
-        if (CM == 1) {
-          Spinor<float> h;
-          herm_apply<float>(tinv + (size_t)s * HERM_PER_SITE, q, h);
-          q = h;
         }
       }
       planes_to_spinor(cur, NS, tid, rv);
@@ -750,8 +781,8 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
         }
         om = tden > 0 ? mk((float)(tre / tden), (float)(tim / tden)) : mk(0.0f, 0.0f);
       } else {
-        const double* tb = table + ((size_t)it * ndc + k) * 2;
-        om = mk((float)tb[0], (float)tb[1]);
+        const float2 o2 = oms[it];
+        om = mk(o2.x, o2.y);
       }
 #pragma unroll
       for (int j = 0; j < 12; ++j) cmac((&x.c[0][0])[j], om, (&rv.c[0][0])[j]);
@@ -760,7 +791,7 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
 #pragma unroll
         for (int j = 0; j < 12; ++j) cmac((&rv.c[0][0])[j], mom, (&q.c[0][0])[j]);
         spinor_to_planes(nxt, NS, tid, rv);
-        cluster.sync();
+        cluster_arrive();
         float4* t = cur; cur = nxt; nxt = t;
       }
     }

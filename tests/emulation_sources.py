@@ -90,10 +90,13 @@ def bind_shared(src):
 
 def _plain_cp_async(src):
     """The sweep's asynchronous 16-byte copies as plain copies (they complete
-    at once on the emulator, so committing and waiting do nothing)."""
+    at once on the emulator, so committing and waiting do nothing), and the
+    two halves of its cluster barrier on the emulated cluster barrier."""
     src = replace_body(src, "__device__ __forceinline__ void cp_async_16(float4* dst, const float4* src)",
                        "{ *dst = *src; }")
     src = replace_body(src, "__device__ __forceinline__ void cp_async_commit()", "{}")
+    src = replace_body(src, "__device__ __forceinline__ void cluster_arrive()", "{ emu_cluster_arrive(); }")
+    src = replace_body(src, "__device__ __forceinline__ void cluster_wait()", "{ emu_cluster_wait(); }")
     return replace_body(src, "__device__ __forceinline__ void cp_async_wait_all()", "{}")
 
 

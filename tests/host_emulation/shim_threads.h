@@ -9,6 +9,7 @@
 #include <pthread.h>
 
 #include <barrier>
+#include <optional>
 #include <chrono>
 #include <condition_variable>
 #include <mutex>
@@ -122,6 +123,15 @@ T* cooperative_groups::cluster_group::map_shared_rank(T* p, unsigned r) const {
     r = 0;
   }
   return reinterpret_cast<T*>(emu_t.cluster->ctas[r]->arena.data() + off);
+}
+
+// the two halves of the cluster barrier: the arrival of this emulated thread
+// is held between them
+inline thread_local std::optional<std::barrier<>::arrival_token> emu_cluster_token;
+inline void emu_cluster_arrive() { emu_cluster_token.emplace(emu_t.cluster->bar->arrive()); }
+inline void emu_cluster_wait() {
+  emu_t.cluster->bar->wait(std::move(*emu_cluster_token));
+  emu_cluster_token.reset();
 }
 
 // shared::cluster window addresses: the CTA rank in the top 8 bits, the

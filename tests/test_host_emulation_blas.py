@@ -251,7 +251,7 @@ def test_block_updates(blas, fp64, L):
     dt = np.complex128 if fp64 else np.complex64
     tol = 1e-13 if fp64 else 1e-5
     U, S, Z, V, R, P = (np.ascontiguousarray(_rand(rng, nsite, L, 12).astype(dt)) for _ in range(6))
-    X64 = np.ascontiguousarray(_rand(rng, nsite, L, 12))
+    X0 = np.ascontiguousarray(_rand(rng, nsite, L, 12).astype(dt))
     alpha, beta, M = _rand(rng, L, L), _rand(rng, L, L), _rand(rng, L, L)
     zeta = 0.3 - 0.7j
     pack = lambda m: np.ascontiguousarray(np.stack([m.real, m.imag], -1).ravel())
@@ -271,17 +271,30 @@ def test_block_updates(blas, fp64, L):
     ref = m(R) - m(V) @ alpha
     assert np.max(np.abs(m(R1) - ref)) < scale(ref)
     # X += U alpha + zeta S, R -= zeta Z, P = R + (P - zeta V) beta, column norms of the new R
-    R2, P2, X2 = R.copy(), P.copy(), X64.copy()
+    R2, P2, X2 = R.copy(), P.copy(), X0.copy()
     part = np.zeros((ncta, L))
     blas.emu_updates(fp64, L, 2, ncta, nrow, _v(U), _d(pack(alpha)), _v(S), _v(Z), _v(V), _d(zb), _v(R2), _v(P2),
                      _v(X2), _d(part), None, None)
-    xr = _mat(X64) + m(U) @ alpha + zeta * m(S)
+    xr = m(X0) + m(U) @ alpha + zeta * m(S)
     rr = m(R) - zeta * m(Z)
     pr = rr + (m(P) - zeta * m(V)) @ beta
-    assert np.max(np.abs(_mat(X2) - xr)) < scale(xr)
+    assert np.max(np.abs(m(X2) - xr)) < scale(xr)
     assert np.max(np.abs(m(R2) - rr)) < scale(rr)
     assert np.max(np.abs(m(P2) - pr)) < scale(pr)
     assert np.max(np.abs(part.sum(0) - np.sum(np.abs(m(R2)) ** 2, 0))) < tol * np.max(np.sum(np.abs(rr) ** 2, 0))
+
+
+def test_fold_of_fp32_solution_updates(blas):
+    """X64 += Xs and Xs = 0: every FP32 update enters the FP64 solution exactly
+    (an FP32 number is an FP64 number; the sum is the FP64 rounding of it)."""
+    rng = np.random.default_rng(210)
+    n = 1000
+    X64 = np.ascontiguousarray(rng.standard_normal(n) + 1j * rng.standard_normal(n))
+    Xs = np.ascontiguousarray((rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64))
+    ref = X64 + Xs.astype(np.complex128)
+    blas.emu_updates(0, 3, 3, 3, n, None, None, None, None, None, None, None, None, _v(Xs), None, None, _v(X64))
+    assert np.array_equal(X64, ref)
+    assert not np.any(Xs)
 
 
 # ---------------------------------------------------------------------------
