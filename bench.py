@@ -441,6 +441,8 @@ def main():
     ap.add_argument("--kappa-scan", default=None,
                     help="comma-separated kappas: iterations of the unpreconditioned solve (L = 1, the first "
                          "source, FP32 Krylov vectors with reliable updates) on the workload's field, then exit")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the library's autotuner (launch shapes of the operator and the SAP sweep)")
     ap.add_argument("--table1", action="store_true",
                     help="also solve the 12 sources as 12/L blocks of L = 1, 2, 3, 4, 6, 12 (Table 1, Fig. 2)")
     args = ap.parse_args()
@@ -464,6 +466,13 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    # the library's autotuner: the first (warm-up) solve times the launch
+    # shapes that give bit-identical results and keeps the fastest
+    tune_file = None
+    if not args.no_autotune:
+        tune_file = os.path.join(tempfile.mkdtemp(prefix="mbicg_tune_"), "tune.txt")
+        os.environ["MBICG_AUTOTUNE"] = "1"
+        os.environ["MBICG_TUNE_FILE"] = tune_file
     import paper_1104_0737_gb300 as mb
 
     dims, L = cfg["dims"], cfg["L"]
@@ -595,6 +604,11 @@ def main():
         cpu = oracle_sample(cfg, int(np.median(iters)))
         cpu.pop("sample_seconds", None)
 
+    # legs without an untimed warm-up solve run untuned (a first solve of a
+    # new lattice, L or precision would otherwise time the candidates inside
+    # the timed region)
+    if tune_file:
+        os.environ["MBICG_AUTOTUNE"] = "0"
     fp64_arm = None
     if not args.no_fp64_arm and rank == 0:
         p64 = mb.mbicg_default_params(ncycle=cfg["ncycle"], nmr=cfg["nmr"], block=cfg["block"],
@@ -619,7 +633,11 @@ def main():
                                      mr_mode=mb.MBICG_MR_FROZEN, prec_D=mb.MBICG_FP32,
                                      prec_sap={"fp32": mb.MBICG_FP32, "fp16": mb.MBICG_FP16}[other],
                                      max_iter=4 * max(iters) + 50)
+        if tune_file:
+            os.environ["MBICG_AUTOTUNE"] = "1"
         st, it_a, tr_a = mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], pa)  # warm-up
+        if tune_file:
+            os.environ["MBICG_AUTOTUNE"] = "0"
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             a0 = torch.cuda.Event(enable_timing=True)
@@ -662,6 +680,13 @@ def main():
             "clocks": clk, "kernel_ms": {k: v[0] for k, v in prof.items()},
             "kernel_launch_groups": {k: v[1] for k, v in prof.items()},
         }
+        if tune_file and os.path.exists(tune_file):
+            # key -> index of the chosen candidate (tune.h: the operator's
+            # sites per CTA and CTA order; the sweep's shape 0/1/2 = 8-CTA
+            # clusters, 16-CTA clusters with two columns per thread, 16-CTA
+            # clusters with one)
+            with open(tune_file) as f:
+                out["autotuned"] = {k: int(v) for k, v in (line.split() for line in f if line.strip())}
         if fp64_arm:
             out["fp64_one_rhs_arm"] = fp64_arm
         if serving:

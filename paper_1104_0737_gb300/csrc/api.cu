@@ -347,6 +347,15 @@ struct Solver {
       // the operator's launch shape, once per lattice, L and precision (before any capture)
       tune_dslash<T>(ex, g, links_T(), k.U, k.V, L, kappa);
       tune_dslash<double>(ex, g, c->U64, X64, W64, L, kappa);
+      // the fused sweep's launch shape, on the SAP scratch blocks
+      if (p.ncycle > 0 && std::is_same<TS, float>::value && p.domain_solver == MBICG_DOMAIN_MR &&
+          sap_sweep_fusable(g, 3)) {
+        if (sap16)
+          tune_sap_sweep(ex, g, c->U32, sh.r, sh.r_sc, sh.psi, sh.psi_sc, L, kappa, p.nmr, table, true,
+                         tinv<float>());
+        else
+          tune_sap_sweep(ex, g, c->U32, sw.r, nullptr, sw.q, nullptr, L, kappa, p.nmr, table, false, tinv<float>());
+      }
     }
     return MBICG_OK;
   }

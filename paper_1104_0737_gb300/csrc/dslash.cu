@@ -16,6 +16,7 @@
 // eta, 48 more for phi - kappa eta.
 #include <cooperative_groups.h>
 #include <algorithm>
+#include <stdio.h>
 #include <stdlib.h>
 
 #include "internal.h"
@@ -393,14 +394,17 @@ __host__ __device__ constexpr int pick4(int mu, int a, int b, int c, int d) {
   return mu == 0 ? a : mu == 1 ? b : mu == 2 ? c : d;
 }
 
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT>
+// NCOL columns per thread: a thread sweeps NCOL consecutive columns of its
+// site at once, so each link is read and completed once for all of them.
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int NCOL>
 struct SweepShape {
   static constexpr int SX = DX / CX, SY = DY / CY, SZ = DZ / CZ, ST = DT / CT;
   static constexpr int NS = SX * SY * SZ * ST;  // sites per CTA = threads
   static constexpr int CS = CX * CY * CZ * CT;  // CTAs per cluster
-  // two residual buffers (6 float4 planes each), the first two rows of the
-  // four forward links of each site (12 float4 planes), partial dots
-  static constexpr size_t smem_bytes() { return (size_t)NS * (12 + 12) * 16 + 64 * sizeof(float); }
+  static constexpr int RP = 6 * NCOL;           // float4 planes of one residual buffer
+  // two residual buffers, the first two rows of the four forward links of
+  // each site (12 float4 planes), partial dots [CS][NCOL][4]
+  static constexpr size_t smem_bytes() { return (size_t)NS * (2 * RP + 12) * 16 + CS * NCOL * 4 * sizeof(float); }
 };
 
 __device__ __forceinline__ void spinor_to_planes(float4* vS, int NS, int site, const Spinor<float>& v) {
@@ -502,24 +506,23 @@ __device__ __forceinline__ void planes_to_link12(const float4* uS, int NS, int m
   }
 }
 
-// Dirichlet hop sum of the domain operator A_dom over the eight neighbours of
-// a site of the domain (hops that leave the domain are dropped), reading the
-// neighbour's spinor from the (distributed) shared-memory planes at cluster
-// address vS and the link rows from the planes at uS (the site's own forward
-// links; the neighbour's for a backward hop).  vS is a CTA-local shared
+// Dirichlet hop sums of the domain operator A_dom over the eight neighbours
+// of a site of the domain (hops that leave the domain are dropped) for NCOL
+// columns, reading each neighbour's spinors from the (distributed) shared-
+// memory planes at cluster address vS (column c at plane 6 c) and the link
+// rows from the planes at uS (the site's own forward links; the neighbour's
+// for a backward hop), once for all columns.  vS is a CTA-local shared
 // address, uS the CTA's link planes already in the cluster window; vL and uL
 // are the same planes as pointers, read directly where the hop cannot leave
 // the CTA.  sb: coordinates inside the CTA's sub-block, lc: inside the domain.
-// PHASE 0 zeroes acc and adds the hops whose neighbour lies in this CTA for
-// the whole warp (x, and z or t where the warp's neighbouring layer is in
-// this CTA): they need only this CTA's barrier.  PHASE 1 adds the others (y,
-// and z or t into the next CTA), after the cluster barrier.  PHASE 2 zeroes
-// acc and adds all eight.
-template <int PHASE, typename SH, int DX, int DY, int DZ, int DT, int CX, int CY, int CZ>
+// The hops are summed in a fixed order (x, y, z, t; forward first), the same
+// for every split of the domain and every NCOL.
+template <typename SH, int NCOL, int DX, int DY, int DZ, int DT, int CX, int CY, int CZ>
 __device__ __forceinline__ void domain_hops(const float4* vL, uint32_t vS, const float4* uL, uint32_t uS, int tid,
-                                            int rank, const int sb[4], const int lc[4], Spinor<float>& acc) {
+                                            int rank, const int sb[4], const int lc[4], Spinor<float> (&acc)[NCOL]) {
   constexpr int NS = SH::NS;
-  if (PHASE != 1) zero(acc);
+#pragma unroll
+  for (int c = 0; c < NCOL; ++c) zero(acc[c]);
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
@@ -530,48 +533,44 @@ __device__ __forceinline__ void domain_hops(const float4* vL, uint32_t vS, const
       const int cta_stride = pick4(mu, 1, CX, CX * CY, CX * CY * CZ);
       const bool leaves = fwd ? (lc[mu] == ext - 1) : (lc[mu] == 0);
       if (leaves) continue;
-      Spinor<float> pn;
+      // the neighbour is in this CTA or, across a face of the sub-block, at
+      // the same position on the far face of the next CTA
+      const int sn_sub = sb[mu] + (fwd ? 1 : -1);
+      const bool cross = sn_sub < 0 || sn_sub >= sub;
+      const int nb = cross ? tid + (fwd ? -(sub - 1) * sub_stride : (sub - 1) * sub_stride)
+                           : tid + (fwd ? sub_stride : -sub_stride);
+      // A warp covers one (z, t) position of the sub-block (SX * SY >= 32),
+      // so in z and t the choice between this CTA and the next is the same
+      // for the whole warp: branch, and read this CTA's planes directly.
+      // In y it differs inside a warp: one cluster-window load path for all.
+      constexpr bool warp_uniform_zt = SH::SX * SH::SY >= 32;
+      const bool in_cta = pick4(mu, CX, CY, CZ, SH::CS / (CX * CY * CZ)) == 1 || (mu >= 2 && warp_uniform_zt && !cross);
+      const uint32_t other = (uint32_t)(cross ? rank + (fwd ? cta_stride : -cta_stride) : rank);
       Link<float> u;
-      const float phase = 1.0f;
-      {
-        // the neighbour is in this CTA or, across a face of the sub-block,
-        // at the same position on the far face of the next CTA
-        const int sn_sub = sb[mu] + (fwd ? 1 : -1);
-        const bool cross = sn_sub < 0 || sn_sub >= sub;
-        const int nb = cross ? tid + (fwd ? -(sub - 1) * sub_stride : (sub - 1) * sub_stride)
-                             : tid + (fwd ? sub_stride : -sub_stride);
-        // A warp covers one (z, t) position of the sub-block (SX * SY >= 32),
-        // so in z and t the choice between this CTA and the next is the same
-        // for the whole warp: branch, and read this CTA's planes directly.
-        // In y it differs inside a warp: one cluster-window load path for all.
-        constexpr bool warp_uniform_zt = SH::SX * SH::SY >= 32;
-        const bool in_cta = pick4(mu, CX, CY, CZ, SH::CS / (CX * CY * CZ)) == 1 || (mu >= 2 && warp_uniform_zt && !cross);
-        if ((PHASE == 0 && !in_cta) || (PHASE == 1 && in_cta)) continue;
-        if (in_cta) {
-          // the neighbour is in this CTA: plain shared loads
-          planes_to_spinor(reinterpret_cast<const float4*>(vL), NS, nb, pn);
-          planes_to_link12(uL, NS, mu, fwd ? tid : nb, u);
+      if (fwd || in_cta) planes_to_link12(uL, NS, mu, fwd ? tid : nb, u);
+      else cluster_planes_to_link12(cluster_addr(uS, other), NS, mu, nb, u);
+      const uint32_t vO = in_cta ? 0u : cluster_addr(vS, other);
+#pragma unroll
+      for (int c = 0; c < NCOL; ++c) {
+        Spinor<float> pn;
+        if (in_cta) planes_to_spinor(vL + 6 * c * NS, NS, nb, pn);
+        else cluster_planes_to_spinor(vO + (uint32_t)(6 * c * NS * 16), NS, nb, pn);
+        cx<float> h[2][3], w[2][3];
+        const float phase = 1.0f;
+        if (fwd) {
+          switch (mu) {
+            case 0: project<0, -1>(pn, h); link_times<false>(u, h, phase, w); reconstruct_add<0, -1>(acc[c], w); break;
+            case 1: project<1, -1>(pn, h); link_times<false>(u, h, phase, w); reconstruct_add<1, -1>(acc[c], w); break;
+            case 2: project<2, -1>(pn, h); link_times<false>(u, h, phase, w); reconstruct_add<2, -1>(acc[c], w); break;
+            default: project<3, -1>(pn, h); link_times<false>(u, h, phase, w); reconstruct_add<3, -1>(acc[c], w); break;
+          }
         } else {
-          const uint32_t other = (uint32_t)(cross ? rank + (fwd ? cta_stride : -cta_stride) : rank);
-          cluster_planes_to_spinor(cluster_addr(vS, other), NS, nb, pn);
-          if (fwd) planes_to_link12(uL, NS, mu, tid, u);
-          else cluster_planes_to_link12(cluster_addr(uS, other), NS, mu, nb, u);
-        }
-      }
-      cx<float> h[2][3], w[2][3];
-      if (fwd) {
-        switch (mu) {
-          case 0: project<0, -1>(pn, h); link_times<false>(u, h, phase, w); reconstruct_add<0, -1>(acc, w); break;
-          case 1: project<1, -1>(pn, h); link_times<false>(u, h, phase, w); reconstruct_add<1, -1>(acc, w); break;
-          case 2: project<2, -1>(pn, h); link_times<false>(u, h, phase, w); reconstruct_add<2, -1>(acc, w); break;
-          default: project<3, -1>(pn, h); link_times<false>(u, h, phase, w); reconstruct_add<3, -1>(acc, w); break;
-        }
-      } else {
-        switch (mu) {
-          case 0: project<0, 1>(pn, h); link_times<true>(u, h, phase, w); reconstruct_add<0, 1>(acc, w); break;
-          case 1: project<1, 1>(pn, h); link_times<true>(u, h, phase, w); reconstruct_add<1, 1>(acc, w); break;
-          case 2: project<2, 1>(pn, h); link_times<true>(u, h, phase, w); reconstruct_add<2, 1>(acc, w); break;
-          default: project<3, 1>(pn, h); link_times<true>(u, h, phase, w); reconstruct_add<3, 1>(acc, w); break;
+          switch (mu) {
+            case 0: project<0, 1>(pn, h); link_times<true>(u, h, phase, w); reconstruct_add<0, 1>(acc[c], w); break;
+            case 1: project<1, 1>(pn, h); link_times<true>(u, h, phase, w); reconstruct_add<1, 1>(acc[c], w); break;
+            case 2: project<2, 1>(pn, h); link_times<true>(u, h, phase, w); reconstruct_add<2, 1>(acc[c], w); break;
+            default: project<3, 1>(pn, h); link_times<true>(u, h, phase, w); reconstruct_add<3, 1>(acc[c], w); break;
+          }
         }
       }
     }
@@ -582,24 +581,28 @@ __device__ __forceinline__ void domain_hops(const float4* vL, uint32_t vS, const
 // T^{-1} of its site (tinv, packed, read through L1)
 // H: the residual rin and psi are FP16 spinors with per-(site, column) scales
 // rsc, psc (the preconditioner's FP16 storage), else FP32 (rsc, psc unused).
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM, bool H>
-__global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS,
-                                  (SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS <= 256) ? 2 : 1)
+// NCOL: columns per thread; an item is a domain and NCOL consecutive columns
+// (when nc is not a multiple of NCOL, the last item's missing columns repeat
+// its first one and are not stored).
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM, bool H, int NCOL>
+__global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT, NCOL>::NS,
+                                  (SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT, NCOL>::NS <= 256 && NCOL == 1) ? 2 : 1)
     k_sap_sweep(Geom g, int colour, const cx<float>* __restrict__ links, const void* __restrict__ rin,
                 const float* __restrict__ rsc, void* __restrict__ psi, float* __restrict__ psc, int L, int c0, int nc,
                 float kappa, int psi_mode, int nmr, int mode, const double* __restrict__ table,
                 const float* __restrict__ tinv) {
-  using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
+  using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT, NCOL>;
   constexpr int NS = SH::NS;
   constexpr int CS = SH::CS;
+  constexpr int RP = SH::RP;
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ float4 sm4[];
-  float4* buf0 = sm4;                                      // [6][NS] residual
-  float4* buf1 = sm4 + 6 * NS;                             // [6][NS] residual
-  float4* uS = sm4 + 12 * NS;                              // [12][NS] link rows 0, 1
-  float* red = reinterpret_cast<float*>(sm4 + 24 * NS);   // [CS][4] partial dots
-  __shared__ float wsum[NS / 32][3];
+  float4* buf0 = sm4;                                       // [NCOL][6][NS] residual
+  float4* buf1 = sm4 + RP * NS;                             // [NCOL][6][NS] residual
+  float4* uS = sm4 + 2 * RP * NS;                           // [12][NS] link rows 0, 1
+  float* red = reinterpret_cast<float*>(sm4 + (2 * RP + 12) * NS);  // [CS][NCOL][4] partial dots
+  __shared__ float wsum[NS / 32][NCOL * 3];
   __shared__ float2 oms[MAX_NMR];  // frozen step lengths of the current domain
 
   const int rank = (int)cluster.block_rank();
@@ -618,22 +621,22 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
   lc[2] = cb[2] * SH::SZ + sb[2];
   lc[3] = cb[3] * SH::ST + sb[3];
   const int ndc = g.nd / 2;
-  // persistent clusters: the (domain, column) items of this colour, domain
-  // major, are cut into one contiguous range per cluster
+  // persistent clusters: the (domain, column group) items of this colour,
+  // domain major, are cut into one contiguous range per cluster
   const int nclu = gridDim.x / CS;
   const int cid = blockIdx.x / CS;
-  // the columns c0 .. c0 + nc - 1 of the L-column blocks
-  const long long nitems = (long long)ndc * nc;
+  const int ngrp = (nc + NCOL - 1) / NCOL;  // column groups of the columns c0 .. c0 + nc - 1
+  const long long nitems = (long long)ndc * ngrp;
   const int item0 = (int)(nitems * cid / nclu);
   const int item1 = (int)(nitems * (cid + 1) / nclu);
   const uint32_t uA = cluster_addr(smem_addr(uS), (uint32_t)rank);  // own link planes, cluster window
+  // the column of slot j of group grp (a missing one repeats the first)
+  auto column = [&](int grp, int j) { return c0 + grp * NCOL + ((grp * NCOL + j < nc) ? j : 0); };
 
   // A buffer is written only after the cluster barrier that follows the last
   // reads of it by other CTAs; every write is followed by a barrier before
-  // the buffer is read.  The barrier after a residual is written is split:
-  // each thread arrives once its writes are done, the hops into this CTA's
-  // own planes run after a CTA barrier, and the wait for the other CTAs
-  // comes just before the hops that read them.
+  // the buffer is read.  Each thread arrives at the barrier once its writes
+  // are done and waits just before the hops that read the other CTAs.
   float4* cur = buf0;
   float4* nxt = buf1;
   int k = -1, s = 0;
@@ -645,8 +648,8 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
   // psi update instead of stalling the cluster at the next item's start.
   bool have_rn = false;
   for (int item = item0; item < item1; ++item) {
-    const int kk = item / nc;
-    const int rhs = c0 + item - kk * nc;
+    const int kk = item / ngrp;
+    const int grp = item - kk * ngrp;
     if (kk != k) {
       k = kk;  // a new domain of this colour
       int b[4];
@@ -658,8 +661,8 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
       s = site_index(g, c);
       if (item != item0) cluster.sync();  // no CTA still reads the previous domain's links
       // the first two rows of this site's four forward links, for all columns
-      // of the domain; the barrier after the first staging of r or psi makes
-      // them visible to the cluster
+      // of the domain; the barrier after the first staging of r makes them
+      // visible to the cluster
       const float2* gl = reinterpret_cast<const float2*>(links + (size_t)s * 36);
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu)
@@ -675,137 +678,163 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
           oms[it] = make_float2((float)tb[0], (float)tb[1]);
         }
     }
-    const size_t off = spinor_offset(s, L, rhs);
     // the colour's residual at entry: eta itself when psi = 0, else
     // eta - A psi formed beforehand by the residual kernel
     if (have_rn) {
       cp_async_wait_all();  // this thread's copies of r0 into nxt have landed
     } else {
-      Spinor<float> r0;
-      if (H) load_spinor_h(static_cast<const __half2*>(rin) + off, __ldg(rsc + off / 12), r0);
-      else load_spinor(static_cast<const cx<float>*>(rin) + off, r0);
-      spinor_to_planes(nxt, NS, tid, r0);
+#pragma unroll
+      for (int j = 0; j < NCOL; ++j) {
+        const size_t off = spinor_offset(s, L, column(grp, j));
+        Spinor<float> r0;
+        if (H) load_spinor_h(static_cast<const __half2*>(rin) + off, __ldg(rsc + off / 12), r0);
+        else load_spinor(static_cast<const cx<float>*>(rin) + off, r0);
+        spinor_to_planes(nxt + 6 * j * NS, NS, tid, r0);
+      }
     }
     have_rn = false;
-    cluster_arrive();  // r0 (and, for the first column, this CTA's links and step lengths) written
+    cluster_arrive();  // r0 (and, for a new domain, this CTA's links and step lengths) written
     { float4* t = cur; cur = nxt; nxt = t; }
-    Spinor<float> x;
-    zero(x);
+    Spinor<float> x[NCOL];
+#pragma unroll
+    for (int j = 0; j < NCOL; ++j) zero(x[j]);
 
     for (int it = 0; it < nmr; ++it) {
       const bool last = (it == nmr - 1);
-      Spinor<float> q, rv;
       const bool need_q = (mode == 0) || !last;
+      Spinor<float> q[NCOL];
+      cluster_wait();  // the residual planes of every CTA (and, when !need_q, no CTA reads nxt any more)
       if (need_q) {
-        __syncthreads();  // this CTA's residual planes
-        domain_hops<0, SH, DX, DY, DZ, DT, CX, CY, CZ>(cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, q);
-        cluster_wait();  // the other CTAs' residual planes
-        domain_hops<1, SH, DX, DY, DZ, DT, CX, CY, CZ>(cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, q);
+        domain_hops<SH, NCOL, DX, DY, DZ, DT, CX, CY, CZ>(cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, q);
         if (CM == 1) {
-          Spinor<float> h;
-          herm_apply<float>(tinv + (size_t)s * HERM_PER_SITE, q, h);
-          q = h;
-        }
-      } else {
-        cluster_wait();  // no CTA reads nxt any more
-      }
-      if (!H && last && !need_q) {
-        if (item + 1 < item1) {
-          // the next item: the next column of this site, or the first column
-          // of the next domain
-          const int kn = (item + 1) / nc;
-          int sn = s;
-          if (kn != kk) {
-            int b[4], cn[4];
-            colour_domain(g, colour, kn, b);
-            cn[0] = b[0] * DX + lc[0];
-            cn[1] = b[1] * DY + lc[1];
-            cn[2] = b[2] * DZ + lc[2];
-            cn[3] = b[3] * DT + lc[3];
-            sn = site_index(g, cn);
+#pragma unroll
+          for (int j = 0; j < NCOL; ++j) {
+            Spinor<float> h;
+            herm_apply<float>(tinv + (size_t)s * HERM_PER_SITE, q[j], h);
+            q[j] = h;
           }
-          const size_t offn = spinor_offset(sn, L, c0 + item + 1 - kn * nc);
+        }
+      }
+      if (!H && last && !need_q && item + 1 < item1) {
+        // the next item: the next column group of this site, or the first
+        // one of the next domain
+        const int kn = (item + 1) / ngrp;
+        const int gn = item + 1 - kn * ngrp;
+        int sn = s;
+        if (kn != kk) {
+          int b[4], cn[4];
+          colour_domain(g, colour, kn, b);
+          cn[0] = b[0] * DX + lc[0];
+          cn[1] = b[1] * DY + lc[1];
+          cn[2] = b[2] * DZ + lc[2];
+          cn[3] = b[3] * DT + lc[3];
+          sn = site_index(g, cn);
+        }
+#pragma unroll
+        for (int j = 0; j < NCOL; ++j) {
+          const size_t offn = spinor_offset(sn, L, column(gn, j));
           const float4* src = reinterpret_cast<const float4*>(static_cast<const cx<float>*>(rin) + offn);
 #pragma unroll
-          for (int j = 0; j < 6; ++j) cp_async_16(nxt + j * NS + tid, src + j);
-          cp_async_commit();
-          have_rn = true;
+          for (int e = 0; e < 6; ++e) cp_async_16(nxt + (6 * j + e) * NS + tid, src + e);
         }
+        cp_async_commit();
+        have_rn = true;
       }
-      planes_to_spinor(cur, NS, tid, rv);
-      if (need_q) {
-#pragma unroll
-        for (int j = 0; j < 12; ++j) {
-          cx<float>& o = (&q.c[0][0])[j];
-          const cx<float> v = (&rv.c[0][0])[j];
-          o = mk(fmaf(-kappa, o.re, v.re), fmaf(-kappa, o.im, v.im));
-        }
-      }
-      cx<float> om;
+      cx<float> om[NCOL];
       if (mode == 0) {
-        float nre = 0, nim = 0, den = 0;
+        float dots[NCOL][3];
 #pragma unroll
-        for (int j = 0; j < 12; ++j) {
-          const cx<float> o = (&q.c[0][0])[j], v = (&rv.c[0][0])[j];
-          nre = fmaf(o.re, v.re, fmaf(o.im, v.im, nre));
-          nim = fmaf(o.re, v.im, fmaf(-o.im, v.re, nim));
-          den = fmaf(o.re, o.re, fmaf(o.im, o.im, den));
+        for (int j = 0; j < NCOL; ++j) {
+          Spinor<float> rv;
+          planes_to_spinor(cur + 6 * j * NS, NS, tid, rv);
+          float nre = 0, nim = 0, den = 0;
+#pragma unroll
+          for (int e = 0; e < 12; ++e) {
+            cx<float>& o = (&q[j].c[0][0])[e];
+            const cx<float> v = (&rv.c[0][0])[e];
+            o = mk(fmaf(-kappa, o.re, v.re), fmaf(-kappa, o.im, v.im));
+            nre = fmaf(o.re, v.re, fmaf(o.im, v.im, nre));
+            nim = fmaf(o.re, v.im, fmaf(-o.im, v.re, nim));
+            den = fmaf(o.re, o.re, fmaf(o.im, o.im, den));
+          }
+          dots[j][0] = nre;
+          dots[j][1] = nim;
+          dots[j][2] = den;
         }
         // CTA reduction: warp shuffles, then the warps' sums in a fixed order
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          nre += __shfl_xor_sync(0xffffffffu, nre, o);
-          nim += __shfl_xor_sync(0xffffffffu, nim, o);
-          den += __shfl_xor_sync(0xffffffffu, den, o);
-        }
-        if ((tid & 31) == 0) {
-          wsum[tid >> 5][0] = nre;
-          wsum[tid >> 5][1] = nim;
-          wsum[tid >> 5][2] = den;
-        }
+        for (int j = 0; j < NCOL; ++j)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dots[j][d] += __shfl_xor_sync(0xffffffffu, dots[j][d], o);
+            if ((tid & 31) == 0) wsum[tid >> 5][j * 3 + d] = dots[j][d];
+          }
         __syncthreads();
-        if (tid == 0) {
-          float a = 0, bb = 0, cc = 0;
-          for (int w = 0; w < NS / 32; ++w) { a += wsum[w][0]; bb += wsum[w][1]; cc += wsum[w][2]; }
-          red[rank * 4 + 0] = a;
-          red[rank * 4 + 1] = bb;
-          red[rank * 4 + 2] = cc;
+        if (tid < NCOL * 3) {
+          float a = 0;
+          for (int w = 0; w < NS / 32; ++w) a += wsum[w][tid];
+          red[rank * NCOL * 4 + (tid / 3) * 4 + tid % 3] = a;
         }
         cluster.sync();
-        double tre = 0, tim = 0, tden = 0;
-        for (int q2 = 0; q2 < CS; ++q2) {
-          const float* rr = cluster.map_shared_rank(red, q2);
-          tre += rr[q2 * 4 + 0];
-          tim += rr[q2 * 4 + 1];
-          tden += rr[q2 * 4 + 2];
+#pragma unroll
+        for (int j = 0; j < NCOL; ++j) {
+          double tre = 0, tim = 0, tden = 0;
+          for (int q2 = 0; q2 < CS; ++q2) {
+            const float* rr = cluster.map_shared_rank(red, q2) + q2 * NCOL * 4 + j * 4;
+            tre += rr[0];
+            tim += rr[1];
+            tden += rr[2];
+          }
+          om[j] = tden > 0 ? mk((float)(tre / tden), (float)(tim / tden)) : mk(0.0f, 0.0f);
         }
-        om = tden > 0 ? mk((float)(tre / tden), (float)(tim / tden)) : mk(0.0f, 0.0f);
       } else {
         const float2 o2 = oms[it];
-        om = mk(o2.x, o2.y);
+#pragma unroll
+        for (int j = 0; j < NCOL; ++j) om[j] = mk(o2.x, o2.y);
       }
 #pragma unroll
-      for (int j = 0; j < 12; ++j) cmac((&x.c[0][0])[j], om, (&rv.c[0][0])[j]);
-      if (!last) {
-        const cx<float> mom = mk(-om.re, -om.im);
+      for (int j = 0; j < NCOL; ++j) {
+        Spinor<float> rv;
+        planes_to_spinor(cur + 6 * j * NS, NS, tid, rv);
+        if (need_q && mode != 0) {
 #pragma unroll
-        for (int j = 0; j < 12; ++j) cmac((&rv.c[0][0])[j], mom, (&q.c[0][0])[j]);
-        spinor_to_planes(nxt, NS, tid, rv);
+          for (int e = 0; e < 12; ++e) {
+            cx<float>& o = (&q[j].c[0][0])[e];
+            const cx<float> v = (&rv.c[0][0])[e];
+            o = mk(fmaf(-kappa, o.re, v.re), fmaf(-kappa, o.im, v.im));
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 12; ++e) cmac((&x[j].c[0][0])[e], om[j], (&rv.c[0][0])[e]);
+        if (!last) {
+          const cx<float> mom = mk(-om[j].re, -om[j].im);
+#pragma unroll
+          for (int e = 0; e < 12; ++e) cmac((&rv.c[0][0])[e], mom, (&q[j].c[0][0])[e]);
+          spinor_to_planes(nxt + 6 * j * NS, NS, tid, rv);
+        }
+      }
+      if (!last) {
         cluster_arrive();
         float4* t = cur; cur = nxt; nxt = t;
       }
     }
-    // psi += x
-    Spinor<float> pv;
-    if (psi_mode == 1) zero(pv);
-    else if (H) load_spinor_h(static_cast<const __half2*>(psi) + off, psc[off / 12], pv);
-    else load_spinor(static_cast<const cx<float>*>(psi) + off, pv);
+    // psi += x for the group's columns
 #pragma unroll
-    for (int j = 0; j < 12; ++j) (&pv.c[0][0])[j] = (&pv.c[0][0])[j] + (&x.c[0][0])[j];
-    if (H) store_spinor_h(static_cast<__half2*>(psi) + off, psc + off / 12, pv);
-    else store_spinor(static_cast<cx<float>*>(psi) + off, pv);
-    // the next column writes psi into nxt: the last reads of nxt by other CTAs
-    // were fenced by the barrier that followed them
+    for (int j = 0; j < NCOL; ++j) {
+      if (grp * NCOL + j >= nc) break;
+      const size_t off = spinor_offset(s, L, c0 + grp * NCOL + j);
+      Spinor<float> pv;
+      if (psi_mode == 1) zero(pv);
+      else if (H) load_spinor_h(static_cast<const __half2*>(psi) + off, psc[off / 12], pv);
+      else load_spinor(static_cast<const cx<float>*>(psi) + off, pv);
+#pragma unroll
+      for (int e = 0; e < 12; ++e) (&pv.c[0][0])[e] = (&pv.c[0][0])[e] + (&x[j].c[0][0])[e];
+      if (H) store_spinor_h(static_cast<__half2*>(psi) + off, psc + off / 12, pv);
+      else store_spinor(static_cast<cx<float>*>(psi) + off, pv);
+    }
+    // the next item writes its residual into nxt: the last reads of nxt by
+    // other CTAs were fenced by the barrier that followed them
   }
   // no CTA of the cluster may exit while others still read its shared memory
   cluster.sync();
@@ -813,10 +842,10 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>::NS
 
 // sets the sweep kernel's shared-memory and cluster attributes and returns
 // how many of its clusters the GPU holds at once
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM, bool H>
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM, bool H, int NCOL>
 int sweep_setup(cudaLaunchConfig_t cfg) {
-  using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
-  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM, H>;
+  using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT, NCOL>;
+  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM, H, NCOL>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::smem_bytes());
   if (SH::CS > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cfg.gridDim = dim3((unsigned)SH::CS);
@@ -828,12 +857,12 @@ int sweep_setup(cudaLaunchConfig_t cfg) {
   return n;
 }
 
-template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM, bool H>
+template <int DX, int DY, int DZ, int DT, int CX, int CY, int CZ, int CT, int CM, bool H, int NCOL>
 bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const void* rin, const float* rsc,
                   void* psi, float* psc, int L, int c0, int nc, double kappa, int psi_mode, int nmr, int mode,
                   const double* table, const float* tinv) {
-  using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT>;
-  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM, H>;
+  using SH = SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT, NCOL>;
+  auto kern = k_sap_sweep<DX, DY, DZ, DT, CX, CY, CZ, CT, CM, H, NCOL>;
   const size_t shm = SH::smem_bytes();
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(SH::NS);
@@ -849,8 +878,8 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
   // one persistent cluster per cluster slot of the GPU (clusters must fit
   // in one GPC, so fewer than SMs / CS may be resident at once); set up once
   // per process, thread-safely (contexts may run on several host threads)
-  static const int max_clusters = sweep_setup<DX, DY, DZ, DT, CX, CY, CZ, CT, CM, H>(cfg);
-  const long long nitems = (long long)(g.nd / 2) * nc;
+  static const int max_clusters = sweep_setup<DX, DY, DZ, DT, CX, CY, CZ, CT, CM, H, NCOL>(cfg);
+  const long long nitems = (long long)(g.nd / 2) * ((nc + NCOL - 1) / NCOL);
   const int nclu = (int)std::min<long long>(max_clusters, nitems);
   cfg.gridDim = dim3((unsigned)(SH::CS * nclu));
   cudaLaunchKernelEx(&cfg, kern, g, colour, links, rin, rsc, psi, psc, L, c0, nc, (float)kappa, psi_mode, nmr, mode,
@@ -859,25 +888,51 @@ bool launch_sweep(const Exec& ex, const Geom& g, int colour, const cx<float>* li
   return true;
 }
 
+template <int CM, bool H>
+bool launch_sweep8(int shape, const Exec& ex, const Geom& g, int colour, const cx<float>* links, const void* rin,
+                   const float* rsc, void* psi, float* psc, int L, int c0, int nc, double kappa, int psi_mode, int nmr,
+                   int mode, const double* table, const float* tinv) {
+  if (shape == 1)
+    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 4, CM, H, 2>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa,
+                                                          psi_mode, nmr, mode, table, tinv);
+  if (shape == 2)
+    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 4, CM, H, 1>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa,
+                                                          psi_mode, nmr, mode, table, tinv);
+  return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, CM, H, 1>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa,
+                                                        psi_mode, nmr, mode, table, tinv);
+}
+
+// shape: one of the 8^4 launch shapes (tune.h); 4^4 domains have one (a
+// single CTA per domain)
 template <bool H>
-bool sweep_dispatch(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const void* rin,
+bool sweep_dispatch(int shape, const Exec& ex, const Geom& g, int colour, const cx<float>* links, const void* rin,
                     const float* rsc, void* psi, float* psc, int L, int c0, int nc, double kappa, int psi_mode, int nmr,
                     int mode, const double* table, const float* tinv) {
-  const int* bk = g.blk;
-  // 8^4: eight CTAs of 8 x 4 x 4 x 4 sites (x, the unit-stride direction, is
-  // not split, so its hops never leave the CTA); 4^4: one CTA
-  if (bk[0] == 8) {
+  if (g.blk[0] == 8) {
     if (tinv)
-      return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 1, H>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa, psi_mode,
-                                                        nmr, mode, table, tinv);
-    return launch_sweep<8, 8, 8, 8, 1, 2, 2, 2, 0, H>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa, psi_mode,
-                                                      nmr, mode, table, nullptr);
+      return launch_sweep8<1, H>(shape, ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa, psi_mode, nmr,
+                                 mode, table, tinv);
+    return launch_sweep8<0, H>(shape, ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa, psi_mode, nmr, mode,
+                               table, nullptr);
   }
   if (tinv)
-    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 1, H>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa, psi_mode,
-                                                      nmr, mode, table, tinv);
-  return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 0, H>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa, psi_mode,
-                                                    nmr, mode, table, nullptr);
+    return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 1, H, 1>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa,
+                                                         psi_mode, nmr, mode, table, tinv);
+  return launch_sweep<4, 4, 4, 4, 1, 1, 1, 1, 0, H, 1>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc, kappa,
+                                                       psi_mode, nmr, mode, table, nullptr);
+}
+
+// the launch shape of the sweep for this lattice, storage and L: the one
+// MBICG_SWEEP_SHAPE names, else the tuned one, else 0
+int sweep_shape(const Geom& g, bool half, bool clover, int L) {
+  if (g.blk[0] != 8) return 0;
+  if (const char* e = getenv("MBICG_SWEEP_SHAPE")) {
+    const int v = atoi(e);
+    if (e[0] >= '0' && e[0] <= '9' && v < SWEEP_SHAPES) return v;
+  }
+  int idx;
+  if (tune_table().lookup(sweep_key(half, clover, g.d, L), &idx) && idx >= 0 && idx < SWEEP_SHAPES) return idx;
+  return 0;
 }
 
 }  // namespace
@@ -892,16 +947,65 @@ bool sap_sweep_fused(const Exec& ex, const Geom& g, int colour, const cx<float>*
                      cx<float>* psi, int L, double kappa, int psi_mode, int nmr, int mode, const double* table,
                      const float* tinv, int c0, int nc) {
   if (!sap_sweep_fusable(g, mode)) return false;
-  return sweep_dispatch<false>(ex, g, colour, links, eta, nullptr, psi, nullptr, L, c0, nc > 0 ? nc : L, kappa,
-                               psi_mode, nmr, mode, table, tinv);
+  return sweep_dispatch<false>(sweep_shape(g, false, tinv != nullptr, L), ex, g, colour, links, eta, nullptr, psi,
+                               nullptr, L, c0, nc > 0 ? nc : L, kappa, psi_mode, nmr, mode, table, tinv);
 }
 
 bool sap_sweep_fused_h(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const __half2* rin,
                        const float* rsc, __half2* psi, float* psc, int L, double kappa, int psi_mode, int nmr,
                        int mode, const double* table, const float* tinv, int c0, int nc) {
   if (!sap_sweep_fusable(g, mode)) return false;
-  return sweep_dispatch<true>(ex, g, colour, links, rin, rsc, psi, psc, L, c0, nc > 0 ? nc : L, kappa, psi_mode, nmr,
-                              mode, table, tinv);
+  return sweep_dispatch<true>(sweep_shape(g, true, tinv != nullptr, L), ex, g, colour, links, rin, rsc, psi, psc, L, c0,
+                              nc > 0 ? nc : L, kappa, psi_mode, nmr, mode, table, tinv);
+}
+
+void tune_sap_sweep(const Exec& ex, const Geom& g, const cx<float>* links, void* rin, float* rsc, void* psi, float* psc,
+                    int L, double kappa, int nmr, const double* table, bool half, const float* tinv) {
+  if (g.blk[0] != 8 || !sap_sweep_fusable(g, 3)) return;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ex.stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return;
+  }
+  const char* tr = getenv("MBICG_TRACE");
+  const std::string key = sweep_key(half, tinv != nullptr, g.d, L);
+  int known;
+  if (tune_table().lookup(key, &known)) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return;
+  }
+  // defined contents for the timing runs (zeros; the runs overwrite psi)
+  const size_t n = (size_t)g.V * 12 * L;
+  if (cudaMemsetAsync(rin, 0, n * (half ? sizeof(__half2) : sizeof(cx<float>)), ex.stream) != cudaSuccess ||
+      cudaMemsetAsync(psi, 0, n * (half ? sizeof(__half2) : sizeof(cx<float>)), ex.stream) != cudaSuccess ||
+      (half && (cudaMemsetAsync(rsc, 0, sizeof(float) * g.V * L, ex.stream) != cudaSuccess ||
+                cudaMemsetAsync(psc, 0, sizeof(float) * g.V * L, ex.stream) != cudaSuccess))) {
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return;
+  }
+  tune_table().pick(key, SWEEP_SHAPES, [&](int i) -> double {
+    cudaEventRecord(e0, ex.stream);
+    if (half)
+      sweep_dispatch<true>(i, ex, g, 0, links, rin, rsc, psi, psc, L, 0, L, kappa, 2, nmr, 3, table, tinv);
+    else
+      sweep_dispatch<false>(i, ex, g, 0, links, rin, nullptr, psi, nullptr, L, 0, L, kappa, 2, nmr, 3, table, tinv);
+    cudaEventRecord(e1, ex.stream);
+    float ms = -1.0f;
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      return -1.0;
+    if (tr && tr[0] == '1') fprintf(stderr, "mbicg: tune %s shape %d: %.3f ms\n", key.c_str(), i, ms);
+    return ms;
+  });
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (const char* p = getenv("MBICG_TUNE_FILE")) tune_table().save(p);
 }
 
 void sap_residual_h(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const __half2* eta,

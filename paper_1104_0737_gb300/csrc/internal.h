@@ -176,6 +176,14 @@ bool sap_sweep_fusable(const Geom& g, int mode);
 bool sap_sweep_fused_h(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const __half2* rin,
                        const float* rsc, __half2* psi, float* psc, int L, double kappa, int psi_mode, int nmr,
                        int mode, const double* table, const float* tinv = nullptr, int c0 = 0, int nc = 0);
+// Times the fused sweep's launch shapes (tune.h) on 8^4 domains once per
+// process for this lattice, L, storage and operator (scratch blocks rin, psi
+// of L columns, FP16 with scales rsc, psc when half; table: any nmr x nd/2
+// complex step lengths of the right size) and records the fastest for the
+// sweeps; does nothing while the stream is being captured or when the choice
+// is already known.
+void tune_sap_sweep(const Exec& ex, const Geom& g, const cx<float>* links, void* rin, float* rsc, void* psi,
+                    float* psc, int L, double kappa, int nmr, const double* table, bool half, const float* tinv);
 // r = eta - A psi on the sites of one colour, eta, psi and r in FP16 storage
 void sap_residual_h(const Exec& ex, const Geom& g, int colour, const cx<float>* links, const __half2* eta,
                     const float* esc, const __half2* psi, const float* psc, __half2* r, float* rsc, int L, double kappa,

@@ -115,4 +115,11 @@ std::string dslash_key(int real_bytes, const int dims[4], int L) {
   return b;
 }
 
+std::string sweep_key(bool half, bool clover, const int dims[4], int L) {
+  char b[128];
+  snprintf(b, sizeof b, "sap_sweep/%s%s/%dx%dx%dx%d/L%d", half ? "fp16" : "fp32", clover ? "/clover" : "", dims[0],
+           dims[1], dims[2], dims[3], L);
+  return b;
+}
+
 }  // namespace mbicg

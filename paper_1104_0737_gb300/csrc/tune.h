@@ -46,4 +46,19 @@ struct DslashConfig {
 std::vector<DslashConfig> dslash_candidates(const int dims[4], int L, int max_threads);
 std::string dslash_key(int real_bytes, const int dims[4], int L);
 
+// Launch shapes of the fused SAP sweep on 8^4 domains; every shape sums each
+// column's hops in the same order, so with frozen step lengths (the solver's
+// mode) all give bit-identical results (per-column MR sums its dot products
+// over the CTAs of a cluster, which differ between shapes: rounding-level
+// differences there):
+//   0: clusters of 8 CTAs (the domain cut 1x2x2x2, 512 sites per CTA), one
+//      column per thread;
+//   1: clusters of 16 CTAs (1x2x2x4, 256 sites per CTA), two columns per
+//      thread (each link read once for both);
+//   2: clusters of 16 CTAs, one column per thread (two CTAs per SM).
+constexpr int SWEEP_SHAPES = 3;
+// half: FP16 storage of the residual and psi; clover: the Jacobi-preconditioned
+// clover operator
+std::string sweep_key(bool half, bool clover, const int dims[4], int L);
+
 }  // namespace mbicg

@@ -39,7 +39,7 @@ def sweep(tmp_path_factory):
     lib = ctypes.CDLL(str(lib_path))
     F, D, I = (ctypes.POINTER(t) for t in (ctypes.c_float, ctypes.c_double, ctypes.c_int))
     lib.emu_sweep.argtypes = [I, I, ctypes.c_int, F, F, F, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int,
-                              ctypes.c_int, D, ctypes.c_int, F]
+                              ctypes.c_int, D, ctypes.c_int, F, ctypes.c_int]
     return lib
 
 
@@ -60,7 +60,7 @@ def _oracle_layout(a):
 
 
 def _sap_emulated(lib, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nclusters, oracle_mod, tinv=None,
-                  Ti=None):
+                  Ti=None, shape=0):
     """ncycle cycles of E and O sweeps, as the library's driver launches them:
     before every sweep but the first the colour's residual eta - A psi (here
     from the oracle's operator, in place of the library's residual kernel);
@@ -88,7 +88,7 @@ def _sap_emulated(lib, dims, block, U, kappa, eta, ncycle, nmr, mode, omegas, nc
                 r = _internal32(eta - Ap)
             rc = lib.emu_sweep(_iv(dims), _iv(block), colour, _fp(links), _fp(r), _fp(psi), L, kappa,
                                1 if first else 2, nmr, mode, tp, nclusters,
-                               _fp(tinv) if tinv is not None else None)
+                               _fp(tinv) if tinv is not None else None, shape)
             assert rc == 0
     return _oracle_layout(psi)
 
@@ -122,6 +122,30 @@ def test_fused_sweep_matches_oracle(sweep, oracle_mod, dims, block, L, ncycle, n
         ref = oracle_mod.sap(dims, block, U, kappa, ncycle, nmr, eta, mr_mode=oracle_mod.MR_FROZEN,
                              omega_table=table.copy())
     assert _rel_site(got, ref) < 1e-5
+
+
+@pytest.mark.parametrize("mode", [0, 3])
+def test_sweep_shapes_are_bit_identical(sweep, oracle_mod, mode):
+    """8^4 domains on clusters of 8 CTAs (one column per thread) and of 16
+    CTAs (two columns per thread, or one): every shape sums a column's hops
+    in the same order, so with frozen step lengths (mode 3, the solver's) the
+    results agree bit for bit; per-column MR (mode 0) sums its dot products
+    over the CTAs of a cluster, which cover other sites in each shape, so its
+    step lengths and results agree to rounding.  L = 3 leaves the two-column
+    shape a last group with one column."""
+    dims, block, L, ncycle, nmr, nclusters = (16, 16, 16, 16), (8, 8, 8, 8), 3, 1, 2, 3
+    U = synth.su3_links(dims, 0.5, seed=73)
+    eta = synth.gaussian_source(dims, L, seed=74)
+    omegas = np.array([0.9 + 0.05j, 1.1 - 0.02j])
+    got = [_sap_emulated(sweep, dims, block, U, 0.125, eta, ncycle, nmr, mode, omegas, nclusters, oracle_mod,
+                         shape=sh) for sh in (0, 1, 2)]
+    if mode == 3:
+        assert np.array_equal(got[0], got[1]) and np.array_equal(got[0], got[2])
+    else:
+        ref = oracle_mod.sap(dims, block, U, 0.125, ncycle, nmr, eta, mr_mode=oracle_mod.MR_COLUMN)
+        for g in got:
+            assert _rel_site(g, ref) < 1e-5
+            assert _rel_site(g, got[0]) < 1e-6
 
 
 def _pack_herm(M):
