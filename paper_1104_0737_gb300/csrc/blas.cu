@@ -58,6 +58,32 @@ struct GramShape {
   static constexpr size_t smem = (stage_area > red_bytes ? stage_area : red_bytes) + 64;
 };
 
+// Running sums of the Gram kernel's per-tile partial sums.  FP32 blocks: a
+// pair of floats, each addition error-free by Knuth's TwoSum (the rounding
+// error of hi + a is carried in lo), about 48 significant bits — what FP64
+// running sums gave, without FP64 arithmetic, which runs at 1/64 of the FP32
+// rate here and, done by every thread at once, stalled the kernel.  FP64
+// blocks: one double.
+template <typename R>
+struct RunSum;
+template <>
+struct RunSum<double> {
+  double v = 0;
+  __device__ __forceinline__ void add(double a) { v += a; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <>
+struct RunSum<float> {
+  float hi = 0, lo = 0;
+  __device__ __forceinline__ void add(float a) {
+    const float s = hi + a;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (a - bp);
+    hi = s;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 template <typename R, int L, bool HERM>
 __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __restrict__ A,
                                              const cx<R>* __restrict__ B1, const cx<R>* __restrict__ B2,
@@ -95,20 +121,18 @@ __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __
   }
 
   cx<R> acc1[BB][BB], acc2[BB][BB];
-  cx<double> tot1[BB][BB], tot2[BB][BB];
+  RunSum<R> tot1[BB][BB][2], tot2[BB][BB][2];  // [re, im]
 #pragma unroll
   for (int i = 0; i < BB; ++i)
 #pragma unroll
     for (int j = 0; j < BB; ++j) {
       acc1[i][j] = acc2[i][j] = mk<R>(0, 0);
-      tot1[i][j] = tot2[i][j] = mk<double>(0, 0);
     }
   const int dcol = tid % L, dlane = tid / L;
   constexpr int DLANES = NT / L;
   cx<R> dacc1 = mk<R>(0, 0);
   R dacc2 = 0;
-  cx<double> dtot1 = mk<double>(0, 0);
-  double dtot2 = 0;
+  RunSum<R> dtot1[2], dtot2;
 
   const long long ntiles = (nsite + TS - 1) / TS;
   const int my_tiles = (int)(ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
@@ -188,11 +212,11 @@ __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __
       for (int i = 0; i < BB; ++i)
 #pragma unroll
         for (int jj = 0; jj < BB; ++jj) {
-          tot1[i][jj].re += acc1[i][jj].re; tot1[i][jj].im += acc1[i][jj].im;
-          tot2[i][jj].re += acc2[i][jj].re; tot2[i][jj].im += acc2[i][jj].im;
+          tot1[i][jj][0].add(acc1[i][jj].re); tot1[i][jj][1].add(acc1[i][jj].im);
+          tot2[i][jj][0].add(acc2[i][jj].re); tot2[i][jj][1].add(acc2[i][jj].im);
           acc1[i][jj] = acc2[i][jj] = mk<R>(0, 0);
         }
-      dtot1.re += dacc1.re; dtot1.im += dacc1.im; dtot2 += dacc2;
+      dtot1[0].add(dacc1.re); dtot1[1].add(dacc1.im); dtot2.add(dacc2);
       dacc1 = mk<R>(0, 0);
       dacc2 = 0;
     }
@@ -217,10 +241,10 @@ __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __
   for (int i = 0; i < BB; ++i)
 #pragma unroll
     for (int jj = 0; jj < BB; ++jj) {
-      tot1[i][jj].re += acc1[i][jj].re; tot1[i][jj].im += acc1[i][jj].im;
-      tot2[i][jj].re += acc2[i][jj].re; tot2[i][jj].im += acc2[i][jj].im;
+      tot1[i][jj][0].add(acc1[i][jj].re); tot1[i][jj][1].add(acc1[i][jj].im);
+      tot2[i][jj][0].add(acc2[i][jj].re); tot2[i][jj][1].add(acc2[i][jj].im);
     }
-  dtot1.re += dacc1.re; dtot1.im += dacc1.im; dtot2 += dacc2;
+  dtot1[0].add(dacc1.re); dtot1[1].add(dacc1.im); dtot2.add(dacc2);
 
   // reduce over lanes through shared memory, fixed order
   __syncthreads();
@@ -241,7 +265,9 @@ __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __
       for (int i = 0; i < BB; ++i)
 #pragma unroll
         for (int jj = 0; jj < BB; ++jj)
-          red[lane * L * L + (bi + i) * L + (bj + jj)] = pass == 0 ? tot1[i][jj] : tot2[i][jj];
+          red[lane * L * L + (bi + i) * L + (bj + jj)] =
+              pass == 0 ? mk(tot1[i][jj][0].value(), tot1[i][jj][1].value())
+                        : mk(tot2[i][jj][0].value(), tot2[i][jj][1].value());
     }
     __syncthreads();
     for (int e = tid; e < L * L; e += NT) {
@@ -262,8 +288,8 @@ __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __
     __syncthreads();
   }
   if (dlane < DLANES) {
-    red[dlane * L + dcol] = dtot1;
-    red[DLANES * L + dlane * L + dcol] = mk(dtot2, 0.0);
+    red[dlane * L + dcol] = mk(dtot1[0].value(), dtot1[1].value());
+    red[DLANES * L + dlane * L + dcol] = mk(dtot2.value(), 0.0);
   }
   __syncthreads();
   for (int e = tid; e < 2 * L; e += NT) {
