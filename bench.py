@@ -441,6 +441,8 @@ def main():
     ap.add_argument("--kappa-scan", default=None,
                     help="comma-separated kappas: iterations of the unpreconditioned solve (L = 1, the first "
                          "source, FP32 Krylov vectors with reliable updates) on the workload's field, then exit")
+    ap.add_argument("--no-ssor-line", action="store_true",
+                    help="skip the line with SSOR domain solves (Sec. 2.2) in place of MR")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the library's autotuner (launch shapes of the operator and the SAP sweep)")
     ap.add_argument("--table1", action="store_true",
@@ -654,6 +656,26 @@ def main():
         alt = {"prec_sap": other, "value": L * 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "iters": its,
                "true_res_max": max(trs), "status": st}
 
+    # the same workload with the paper's SSOR domain solves (Sec. 2.2: omega 1.26,
+    # N_SSOR = 1) in place of the MR steps: one warm-up solve, one timed
+    ssor = None
+    if not args.no_ssor_line and rank == 0:
+        ps = mb.mbicg_default_params(ncycle=cfg["ncycle"], block=cfg["block"], domain_solver=mb.MBICG_DOMAIN_SSOR,
+                                     nssor=1, ssor_omega=1.26, prec_D=mb.MBICG_FP32, prec_sap=mb.MBICG_FP32,
+                                     max_iter=4 * max(iters) + 50)
+        mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], ps)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record()
+            st, it_s, tr_s = mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], ps)
+            s1.record()
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1)
+        ssor = {"domain_solver": "SSOR omega 1.26, N_SSOR 1", "value": L * 1e3 / ms, "unit": UNIT,
+                "ms_per_step": ms, "iters": it_s, "true_res_max": max(tr_s), "status": st}
+
     table1 = None
     if args.table1 and rank == 0:
         table1 = run_table1(ctx, cfg, dB, prec_sap)
@@ -695,6 +717,8 @@ def main():
             out["table1"] = table1
         if alt:
             out["alt_storage_line"] = alt
+        if ssor:
+            out["ssor_line"] = ssor
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -237,9 +237,6 @@ int abi_norms(mbicg_ctx* c, const cx<double>* d, int L, double* norms, bool* bad
 template <typename T>
 struct Krylov {
   cx<T>*R, *P, *Rt, *U, *V, *S, *Z;
-  // the solution updates since the last reliable update in FP32 (folded into
-  // the FP64 X before every true residual); with FP64 vectors, X64 itself
-  cx<T>* X;
 };
 
 template <typename T, typename TS>
@@ -290,8 +287,6 @@ struct Solver {
     cx<T>** ptrs[7] = {&k.R, &k.P, &k.Rt, &k.U, &k.V, &k.S, &k.Z};
     for (int i = 0; i < 7; ++i)
       if ((rc = buf(c, names[i], nl, ptrs[i]))) return rc;
-    if (std::is_same<T, double>::value) k.X = reinterpret_cast<cx<T>*>(X64);
-    else if ((rc = buf(c, "kX", nl, &k.X))) return rc;
     if (p.ncycle > 0) {
       if (!std::is_same<T, TS>::value) {
         if ((rc = buf(c, "eta_s", nl, &eta_s))) return rc;
@@ -426,10 +421,6 @@ struct Solver {
   // is known, so R = B without applying the operator.
   int true_residual(double* rel, double* relmax, bool x_zero = false) {
     if (!x_zero) {
-      if (!std::is_same<T, double>::value) {
-        Timed t(ex, KC_AXPY);
-        fold_solution(ex, (long long)nl, reinterpret_cast<cx<float>*>(k.X), X64);
-      }
       Timed t(ex, KC_DSLASH64);
       dslash_full<double>(ex, g, c->U64, X64, W64, L, kappa, ti64, ti64 ? 1 : 0);
     }
@@ -526,7 +517,7 @@ struct Solver {
       int np;
       {
         Timed t(ex, KC_AXPY);
-        np = block_update_zeta<T>(ex, V, L, k.U, sm.alpha, k.S, k.Z, k.V, sm.zb, k.R, k.P, k.X, npart);
+        np = block_update_zeta<T>(ex, V, L, k.U, sm.alpha, k.S, k.Z, k.V, sm.zb, k.R, k.P, X64, npart);
       }
       Timed t(ex, KC_SMALL);
       lxl_norms(ex, L, npart, np, false, sm);
@@ -703,7 +694,6 @@ struct Solver {
       if (p.use_x0) abi_to_internal<double>(ex, V, L, dX, X64);
     }
     if (!p.use_x0) CK(cudaMemsetAsync(X64, 0, sizeof(cx<double>) * nl, c->stream));
-    if (!std::is_same<T, double>::value) CK(cudaMemsetAsync(k.X, 0, sizeof(cx<T>) * nl, c->stream));
     CK(cudaMemsetAsync(sm.status, 0, sizeof(int), c->stream));
     double rel[MAXL] = {0}, relmax;
     // line 2: R = B - A X

@@ -387,16 +387,17 @@ __global__ void __launch_bounds__(NT) k_update_alpha(int nrow, const cx<R>* __re
 
 // X += U alpha + zeta S (the X update of Algorithm 1, 4.9, which Algorithm 2
 // splits into 4.6 and 4.10), R -= zeta Z (4.11), P = R + (P - zeta V) beta
-// (4.13), and the squared column norms of the new R.  X is the solution in
-// the Krylov vectors' precision (with FP32 vectors, the sum of the updates
-// since the last reliable update).
+// (4.13), and the squared column norms of the new R.  X is accumulated in
+// FP64; its increment U alpha + zeta S is formed in the Krylov vectors'
+// precision (they are its inputs), so FP32 vectors cost two FP64 adds per
+// element rather than FP64 products (FP64 runs at 1/64 of the FP32 rate).
 // zb = [zeta, beta (L x L)] complex double
 template <typename R, int L>
 __global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __restrict__ U,
                                                     const double* __restrict__ alpha, const cx<R>* __restrict__ S,
                                                     const cx<R>* __restrict__ Z, const cx<R>* __restrict__ V,
                                                     const double* __restrict__ zb, cx<R>* __restrict__ Rv,
-                                                    cx<R>* __restrict__ P, cx<R>* __restrict__ X,
+                                                    cx<R>* __restrict__ P, cx<double>* __restrict__ X64,
                                                     double* __restrict__ part) {
   __shared__ cx<R> sB[L * L];
   __shared__ cx<R> sA[L * L];
@@ -423,10 +424,12 @@ __global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __res
 #pragma unroll
         for (int k = 0; k < L; ++k) cmac(ua, u[k], sA[k * L + j]);
         const cx<R> s = S[b + j * 12];
-        cx<R> x = X[b + j * 12];
-        x.re += ua.re + (zeta.re * s.re - zeta.im * s.im);
-        x.im += ua.im + (zeta.re * s.im + zeta.im * s.re);
-        X[b + j * 12] = x;
+        const R dre = ua.re + (zeta.re * s.re - zeta.im * s.im);
+        const R dim = ua.im + (zeta.re * s.im + zeta.im * s.re);
+        cx<double> x = X64[b + j * 12];
+        x.re += (double)dre;
+        x.im += (double)dim;
+        X64[b + j * 12] = x;
       }
     }
 #pragma unroll
@@ -455,20 +458,6 @@ __global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __res
     }
     if (threadIdx.x == 0) part[(long long)blockIdx.x * L + j] = sred[0];
     __syncthreads();
-  }
-}
-
-// X64 += Xs, Xs = 0 (n complex numbers): the FP32 solution updates folded
-// into the FP64 solution
-__global__ void __launch_bounds__(NT) k_fold_solution(long long n, cx<float>* __restrict__ Xs,
-                                                      cx<double>* __restrict__ X64) {
-  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
-    const cx<float> d = Xs[i];
-    cx<double> x = X64[i];
-    x.re += (double)d.re;
-    x.im += (double)d.im;
-    X64[i] = x;
-    Xs[i] = mk(0.0f, 0.0f);
   }
 }
 
@@ -954,19 +943,14 @@ void block_update_alpha(const Exec& ex, long long nsite, int L, const cx<R>* V, 
 
 template <typename R>
 int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* U, const double* alpha, const cx<R>* S,
-                      const cx<R>* Z, const cx<R>* V, const double* zeta_beta, cx<R>* Rv, cx<R>* P, cx<R>* X,
+                      const cx<R>* Z, const cx<R>* V, const double* zeta_beta, cx<R>* Rv, cx<R>* P, cx<double>* X64,
                       double* part) {
   const int nrow = (int)(nsite * 12);
   const int grid = row_grid(nrow);
-  DISPATCH_L(L, (k_update_zeta<R, LL><<<grid, NT, 0, ex.stream>>>(nrow, U, alpha, S, Z, V, zeta_beta, Rv, P, X,
+  DISPATCH_L(L, (k_update_zeta<R, LL><<<grid, NT, 0, ex.stream>>>(nrow, U, alpha, S, Z, V, zeta_beta, Rv, P, X64,
                                                                   part)));
   ++*ex.launches;
   return grid;
-}
-
-void fold_solution(const Exec& ex, long long n, cx<float>* Xs, cx<double>* X64) {
-  k_fold_solution<<<row_grid(n), NT, 0, ex.stream>>>(n, Xs, X64);
-  ++*ex.launches;
 }
 
 template <typename R>
@@ -1063,7 +1047,7 @@ void loop_control(const Exec& ex, LoopCtl* ctl, const double* norms, const doubl
   template void block_transform<R>(const Exec&, long long, int, const cx<R>*, const double*, cx<R>*);              \
   template void block_update_alpha<R>(const Exec&, long long, int, const cx<R>*, const double*, cx<R>*);         \
   template int block_update_zeta<R>(const Exec&, long long, int, const cx<R>*, const double*, const cx<R>*,        \
-                                    const cx<R>*, const cx<R>*, const double*, cx<R>*, cx<R>*, cx<R>*,            \
+                                    const cx<R>*, const cx<R>*, const double*, cx<R>*, cx<R>*, cx<double>*,       \
                                     double*);                                                                    \
   template void abi_to_internal<R>(const Exec&, long long, int, const cx<double>*, cx<R>*);                        \
   template void internal_to_abi<R>(const Exec&, long long, int, const cx<R>*, cx<double>*);                        \

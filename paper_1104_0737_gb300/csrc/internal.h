@@ -287,14 +287,13 @@ void block_transform(const Exec& ex, long long nsite, int L, const cx<R>* X, con
 template <typename R>
 void block_update_alpha(const Exec& ex, long long nsite, int L, const cx<R>* V, const double* alpha, cx<R>* Rv);
 
-// X += U alpha + zeta S; R -= zeta Z; P = R + (P - zeta V) beta; partial
-// column norms of the new R into part[cta][L] (doubles).  Returns the CTAs used.
+// X64 += U alpha + zeta S (the increment in R, accumulated in FP64); R -= zeta Z;
+// P = R + (P - zeta V) beta; partial column norms of the new R into
+// part[cta][L] (doubles).  Returns the CTAs used.
 template <typename R>
 int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* U, const double* alpha,
                       const cx<R>* S, const cx<R>* Z, const cx<R>* V, const double* zeta_beta, cx<R>* Rv,
-                      cx<R>* P, cx<R>* X, double* part);
-// X64 += Xs and Xs = 0 over n complex numbers
-void fold_solution(const Exec& ex, long long n, cx<float>* Xs, cx<double>* X64);
+                      cx<R>* P, cx<double>* X64, double* part);
 
 // ABI layout [site][sc][rhs] complex128 <-> internal [site][rhs][sc] in R.
 template <typename R>

@@ -120,7 +120,6 @@ double solve_bytes(long long V, int L, const mbicg_params& p) {
   const double nl = 12.0 * V * L;
   double b = 3 * 16 * nl;                                  // B64, X64, W64
   b += 7 * (p.prec_D == MBICG_FP64 ? 16 : 8) * nl;         // R, P, R~, U, V, S, Z
-  if (p.prec_D != MBICG_FP64) b += 8 * nl;                 // FP32 solution updates
   if (p.ncycle > 0) {
     const double sap = p.prec_sap == MBICG_FP64 ? 16 : 8;
     b += 3 * sap * nl;                                     // SAP r, q, x

@@ -30,16 +30,14 @@ static void updates(int which, int ncta, int nrow, const void* U, const double* 
                     const void* V, const double* zb, void* Rv, void* P, void* X, double* part, const double* M,
                     void* Y) {
   using C = cx<R>;
-  if (which == 3)  // X64 (in Y) += Xs (FP32, in X), Xs = 0
-    emu_launch(ncta, 1, NT, 0, [&] { k_fold_solution((long long)nrow, (cx<float>*)X, (cx<double>*)Y); });
-  else if (which == 0)
+  if (which == 0)
     emu_launch(ncta, 1, NT, 0, [&] { k_transform<R, L>(nrow, (const C*)U, M, (C*)Y); });
   else if (which == 1)
     emu_launch(ncta, 1, NT, 0, [&] { k_update_alpha<R, L>(nrow, (const C*)V, alpha, (C*)Rv); });
   else
     emu_launch(ncta, 1, NT, 0, [&] {
       k_update_zeta<R, L>(nrow, (const C*)U, alpha, (const C*)S, (const C*)Z, (const C*)V, zb, (C*)Rv, (C*)P,
-                          (C*)X, part);
+                          (cx<double>*)X, part);
     });
 }
 
@@ -120,9 +118,7 @@ int emu_gram(int fp64, int L, long long nsite, const void* A, const void* B1, co
 #undef G
   return 0;
 }
-// which: 0 Y = X M (X in U), 1 R -= V alpha, 2 the zeta update (X in the
-// vectors' precision), 3 the fold of FP32 solution updates into FP64
-// (nrow complex numbers)
+// which: 0 Y = X M (X in U), 1 R -= V alpha, 2 the zeta update (X in FP64)
 int emu_updates(int fp64, int L, int which, int ncta, int nrow, const void* U, const double* alpha, const void* S,
                 const void* Z, const void* V, const double* zb, void* Rv, void* P, void* X64, double* part,
                 const double* M, void* Y) {

@@ -251,7 +251,7 @@ def test_block_updates(blas, fp64, L):
     dt = np.complex128 if fp64 else np.complex64
     tol = 1e-13 if fp64 else 1e-5
     U, S, Z, V, R, P = (np.ascontiguousarray(_rand(rng, nsite, L, 12).astype(dt)) for _ in range(6))
-    X0 = np.ascontiguousarray(_rand(rng, nsite, L, 12).astype(dt))
+    X0 = np.ascontiguousarray(_rand(rng, nsite, L, 12))
     alpha, beta, M = _rand(rng, L, L), _rand(rng, L, L), _rand(rng, L, L)
     zeta = 0.3 - 0.7j
     pack = lambda m: np.ascontiguousarray(np.stack([m.real, m.imag], -1).ravel())
@@ -275,26 +275,14 @@ def test_block_updates(blas, fp64, L):
     part = np.zeros((ncta, L))
     blas.emu_updates(fp64, L, 2, ncta, nrow, _v(U), _d(pack(alpha)), _v(S), _v(Z), _v(V), _d(zb), _v(R2), _v(P2),
                      _v(X2), _d(part), None, None)
-    xr = m(X0) + m(U) @ alpha + zeta * m(S)
+    xr = _mat(X0) + m(U) @ alpha + zeta * m(S)
     rr = m(R) - zeta * m(Z)
     pr = rr + (m(P) - zeta * m(V)) @ beta
-    assert np.max(np.abs(m(X2) - xr)) < scale(xr)
+    # X accumulates in FP64: only the increment carries the vectors' rounding
+    assert np.max(np.abs(_mat(X2) - xr)) < tol * max(1.0, np.max(np.abs(xr - _mat(X0))))
     assert np.max(np.abs(m(R2) - rr)) < scale(rr)
     assert np.max(np.abs(m(P2) - pr)) < scale(pr)
     assert np.max(np.abs(part.sum(0) - np.sum(np.abs(m(R2)) ** 2, 0))) < tol * np.max(np.sum(np.abs(rr) ** 2, 0))
-
-
-def test_fold_of_fp32_solution_updates(blas):
-    """X64 += Xs and Xs = 0: every FP32 update enters the FP64 solution exactly
-    (an FP32 number is an FP64 number; the sum is the FP64 rounding of it)."""
-    rng = np.random.default_rng(210)
-    n = 1000
-    X64 = np.ascontiguousarray(rng.standard_normal(n) + 1j * rng.standard_normal(n))
-    Xs = np.ascontiguousarray((rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64))
-    ref = X64 + Xs.astype(np.complex128)
-    blas.emu_updates(0, 3, 3, 3, n, None, None, None, None, None, None, None, None, _v(Xs), None, None, _v(X64))
-    assert np.array_equal(X64, ref)
-    assert not np.any(Xs)
 
 
 # ---------------------------------------------------------------------------
