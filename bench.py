@@ -662,7 +662,7 @@ def main():
     if not args.no_ssor_line and rank == 0:
         ps = mb.mbicg_default_params(ncycle=cfg["ncycle"], block=cfg["block"], domain_solver=mb.MBICG_DOMAIN_SSOR,
                                      nssor=1, ssor_omega=1.26, prec_D=mb.MBICG_FP32, prec_sap=mb.MBICG_FP32,
-                                     max_iter=4 * max(iters) + 50)
+                                     max_iter=2 * max(iters) + 20)
         mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], ps)
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
