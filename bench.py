@@ -588,6 +588,7 @@ def main():
     if not args.no_e2e:
         hB = torch.from_numpy(B).pin_memory()
         hX = torch.empty_like(hB).pin_memory()
+        solve(hB, hX)  # untimed: the library's staging buffers for host blocks are allocated here
         torch.cuda.synchronize()
         if dist:
             dist.barrier()

@@ -461,6 +461,23 @@ __global__ void __launch_bounds__(NT) k_update_zeta(int nrow, const cx<R>* __res
   }
 }
 
+// dst (device memory) = src (registered host memory, read through its mapped
+// device address), n 16-byte words.  Every thread keeps four loads in flight,
+// so the host pages are fetched by the whole grid at once rather than by one
+// copy engine in sequence.
+__global__ void __launch_bounds__(NT) k_copy_mapped(long long n, const uint4* src, uint4* __restrict__ dst) {
+  const long long stride = (long long)gridDim.x * NT;
+  long long i = blockIdx.x * (long long)NT + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+    dst[i] = a;
+    dst[i + stride] = b;
+    dst[i + 2 * stride] = c;
+    dst[i + 3 * stride] = d;
+  }
+  for (; i < n; i += stride) dst[i] = src[i];
+}
+
 // Columns of an ABI block (rows [site][spin*colour], L columns) copied into
 // the first L of Lt columns, the other Lt - L filled with Gaussian random
 // numbers (or zeros): a counter-based generator, splitmix64 of (seed, row,
@@ -951,6 +968,12 @@ int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* U, co
                                                                   part)));
   ++*ex.launches;
   return grid;
+}
+
+void copy_from_mapped_host(const Exec& ex, const void* src, void* dst, size_t bytes) {
+  const long long n = (long long)(bytes / 16);
+  k_copy_mapped<<<row_grid(n), NT, 0, ex.stream>>>(n, static_cast<const uint4*>(src), static_cast<uint4*>(dst));
+  ++*ex.launches;
 }
 
 template <typename R>

@@ -295,6 +295,9 @@ int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* U, co
                       const cx<R>* S, const cx<R>* Z, const cx<R>* V, const double* zeta_beta, cx<R>* Rv,
                       cx<R>* P, cx<double>* X64, double* part);
 
+// dst (device) = src (registered host memory, its mapped device address),
+// bytes a multiple of 16 and both 16-byte aligned: a copy kernel
+void copy_from_mapped_host(const Exec& ex, const void* src, void* dst, size_t bytes);
 // ABI layout [site][sc][rhs] complex128 <-> internal [site][rhs][sc] in R.
 template <typename R>
 void abi_to_internal(const Exec& ex, long long nsite, int L, const cx<double>* in, cx<R>* out);

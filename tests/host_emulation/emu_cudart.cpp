@@ -122,7 +122,8 @@ cudaError_t cudaPointerGetAttributes(struct cudaPointerAttributes* a, const void
   memset(a, 0, sizeof(*a));
   const int k = kind_of(p);
   a->type = k == 2 ? cudaMemoryTypeDevice : k == 1 ? cudaMemoryTypeHost : cudaMemoryTypeUnregistered;
-  a->devicePointer = k == 2 ? const_cast<void*>(p) : nullptr;
+  // unified addressing: registered host memory is mapped at its own address
+  a->devicePointer = k >= 1 ? const_cast<void*>(p) : nullptr;
   a->hostPointer = k != 2 ? const_cast<void*>(p) : nullptr;
   return cudaSuccess;
 }
