@@ -42,6 +42,7 @@ struct mbicg_ctx {
   cx<double>* U64 = nullptr;
   cx<float>* U32 = nullptr;
   __half2* U16 = nullptr;  // first two rows of each link in FP16, [site][mu][6]
+  cx<float>* U12 = nullptr;  // first two rows of each FP32 link, [site][mu][6] (48 B, 16-byte aligned)
   bool gauge = false;
   bool su3 = false;  // every link SU(3): the fused SAP kernel may rebuild third rows
   std::string err;
@@ -163,6 +164,10 @@ bool valid_blocking(const mbicg_ctx* c, const int* block) {
 }
 
 Exec exec_of(mbicg_ctx* c) { return Exec{c->stream, &c->launches, &c->prof}; }
+
+// The FP32 links as two rows for the Wilson operator when every link is
+// SU(3) (the third row is rebuilt), else NULL (the full links are read).
+const cx<float>* links12(const mbicg_ctx* c) { return c->su3 ? c->U12 : nullptr; }
 
 int check_launch(mbicg_ctx* c, const char* where) {
   cudaError_t e = cudaGetLastError();
@@ -326,6 +331,7 @@ struct Solver {
       if ((rc = buf(c, "sap_q", nl, &q))) return rc;
       if ((rc = buf(c, "sap_x", nl, &x))) return rc;
       sw.r = r;
+      if (std::is_same<TS, float>::value) sw.links12 = links12(c);
       sw.q = q;
       sw.x = x;
       const int ndc = g.nd / 2;
@@ -369,7 +375,7 @@ struct Solver {
     if ((rc = buf(c, "sm_status", 1, &sm.status))) return rc;
     if (autotune_enabled()) {
       // the operator's launch shape, once per lattice, L and precision (before any capture)
-      tune_dslash<T>(ex, g, links_T(), k.U, k.V, L, kappa);
+      tune_dslash<T>(ex, g, links_T(), k.U, k.V, L, kappa, ti64 ? nullptr : links12(c));
       tune_dslash<double>(ex, g, c->U64, X64, W64, L, kappa);
       // the fused sweep's launch shape, on the SAP scratch blocks
       if (p.ncycle > 0 && std::is_same<TS, float>::value && p.domain_solver == MBICG_DOMAIN_MR &&
@@ -442,7 +448,7 @@ struct Solver {
 
   int dslash(const cx<T>* in, cx<T>* out) {
     Timed t(ex, KC_DSLASH);
-    dslash_full<T>(ex, g, links_T(), in, out, L, kappa, tinv<T>(), ti64 ? 1 : 0);
+    dslash_full<T>(ex, g, links_T(), in, out, L, kappa, tinv<T>(), ti64 ? 1 : 0, ti64 ? nullptr : links12(c));
     return MBICG_OK;
   }
 
@@ -1040,6 +1046,7 @@ void mbicg_destroy(mbicg_ctx* c) {
   if (c->U64) cudaFree(c->U64);
   if (c->U32) cudaFree(c->U32);
   if (c->U16) cudaFree(c->U16);
+  if (c->U12) cudaFree(c->U12);
   if (c->C64) cudaFree(c->C64);
   if (c->C32) cudaFree(c->C32);
   if (c->Ti64) cudaFree(c->Ti64);
@@ -1062,6 +1069,7 @@ int mbicg_load_gauge(mbicg_ctx* c, const double* U) {
   if (!c->U64) CK(cudaMalloc(&c->U64, sizeof(cx<double>) * n));
   if (!c->U32) CK(cudaMalloc(&c->U32, sizeof(cx<float>) * n));
   if (!c->U16) CK(cudaMalloc(&c->U16, sizeof(__half2) * (size_t)c->V * 24));
+  if (!c->U12) CK(cudaMalloc(&c->U12, sizeof(cx<float>) * (size_t)c->V * 24));
   Staged s;
   int rc = stage_in(c, U, sizeof(cx<double>) * n, "gauge_stage", true, &s);
   if (rc) return rc;
@@ -1073,6 +1081,7 @@ int mbicg_load_gauge(mbicg_ctx* c, const double* U) {
     Timed t(ex, KC_CONVERT);
     convert_links(ex, c->V, static_cast<const cx<double>*>(s.dev), c->U64, c->U32, flag);
     links_to_half(ex, c->V, static_cast<const cx<double>*>(s.dev), c->U16);
+    links_to_rows(ex, c->V, c->U32, c->U12);
   }
   if ((rc = check_launch(c, "load_gauge"))) return rc;
   int bad = 0;
@@ -1149,7 +1158,7 @@ int mbicg_apply_D(mbicg_ctx* c, const double* in, double* out, int L, double kap
     }
     {
       Timed t(ex, KC_DSLASH);
-      dslash_full<float>(ex, g, c->U32, a, b, L, kappa);
+      dslash_full<float>(ex, g, c->U32, a, b, L, kappa, nullptr, 0, links12(c));
     }
     Timed t(ex, KC_CONVERT);
     internal_to_abi<float>(ex, c->V, L, b, static_cast<cx<double>*>(so.dev));
@@ -1364,6 +1373,7 @@ int sap_precond_impl(mbicg_ctx* c, const double* in, double* out, int L, double 
         done = true;
       }
     }
+    if (std::is_same<R, float>::value) w.links12 = links12(c);
     if (!done)
       sap_apply<R>(ex, g, links, a, b, L, kappa, p->ncycle, p->nmr, mode, dtab, unset, w, tinv,
                    p->domain_solver == MBICG_DOMAIN_SSOR ? &sp : nullptr);

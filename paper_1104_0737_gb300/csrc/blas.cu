@@ -478,6 +478,15 @@ __global__ void __launch_bounds__(NT) k_copy_mapped(long long n, const uint4* sr
   for (; i < n; i += stride) dst[i] = src[i];
 }
 
+// The first two rows of every FP32 link: [site][mu][9] -> [site][mu][6]
+__global__ void __launch_bounds__(NT) k_links_to_rows(long long n, const cx<float>* __restrict__ U,
+                                                      cx<float>* __restrict__ R) {
+  for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
+    const long long l = i / 6, k = i - l * 6;
+    R[i] = U[l * 9 + k];
+  }
+}
+
 // Columns of an ABI block (rows [site][spin*colour], L columns) copied into
 // the first L of Lt columns, the other Lt - L filled with Gaussian random
 // numbers (or zeros): a counter-based generator, splitmix64 of (seed, row,
@@ -968,6 +977,12 @@ int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* U, co
                                                                   part)));
   ++*ex.launches;
   return grid;
+}
+
+void links_to_rows(const Exec& ex, long long nsite, const cx<float>* U32, cx<float>* U12) {
+  const long long n = nsite * 4 * 6;
+  k_links_to_rows<<<row_grid(n), NT, 0, ex.stream>>>(n, U32, U12);
+  ++*ex.launches;
 }
 
 void copy_from_mapped_host(const Exec& ex, const void* src, void* dst, size_t bytes) {

@@ -222,6 +222,29 @@ __device__ __forceinline__ void load_link(const cx<float>* p, Link<float>& u) {
     (&u.m[0][0])[k] = mk(v.x, v.y);
   }
 }
+// The third row of an SU(3) link from its first two: the complex conjugate of
+// their cross product (unitarity with det = 1).
+__device__ __forceinline__ void complete_third_row(Link<float>& u) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+    const cx<float> t = u.m[0][j1] * u.m[1][j2] - u.m[0][j2] * u.m[1][j1];
+    u.m[2][j] = conjg(t);
+  }
+}
+// An SU(3) link stored as its first two rows (6 complex numbers, 48 bytes,
+// 16-byte aligned): three 16-byte loads instead of nine 8-byte ones.
+__device__ __forceinline__ void load_link12(const cx<float>* p, Link<float>& u) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+  const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+  u.m[0][0] = mk(a.x, a.y);
+  u.m[0][1] = mk(a.z, a.w);
+  u.m[0][2] = mk(b.x, b.y);
+  u.m[1][0] = mk(b.z, b.w);
+  u.m[1][1] = mk(c.x, c.y);
+  u.m[1][2] = mk(c.z, c.w);
+  complete_third_row(u);
+}
 __device__ __forceinline__ void load_link(const cx<double>* p, Link<double>& u) {
   const double2* q = reinterpret_cast<const double2*>(p);
 #pragma unroll

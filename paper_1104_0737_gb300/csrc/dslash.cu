@@ -16,6 +16,7 @@
 // eta, 48 more for phi - kappa eta.
 #include <cooperative_groups.h>
 #include <algorithm>
+#include <type_traits>
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -33,14 +34,16 @@ constexpr int max_cta() { return sizeof(R) == 4 ? 384 : 256; }
 template <typename R>
 constexpr int min_ctas() { return sizeof(R) == 4 ? 2 : 1; }
 
-template <int MU, int SIGN, typename R>
+// R12: the links are stored as their first two rows (FP32 SU(3) fields)
+template <int MU, int SIGN, bool R12 = false, typename R>
 __device__ __forceinline__ void hop(Spinor<R>& acc, const cx<R>* psi_nb, const cx<R>* link, bool flip) {
   Spinor<R> p;
   load_spinor(psi_nb, p);
   cx<R> h[2][3];
   project<MU, SIGN>(p, h);
   Link<R> u;
-  load_link(link, u);
+  if constexpr (R12) load_link12(link, u);
+  else load_link(link, u);
   cx<R> w[2][3];
   const R ph = flip ? R(-1) : R(1);
   link_times<(SIGN > 0)>(u, h, ph, w);
@@ -51,7 +54,11 @@ __device__ __forceinline__ void hop(Spinor<R>& acc, const cx<R>* psi_nb, const c
 // element offset of (site, rhs) in a site-major block
 __device__ __forceinline__ size_t spinor_offset(int s, int L, int rhs) { return (size_t)(s * L + rhs) * 12; }
 
-template <typename R, bool DIRICHLET, int MU>
+// complex numbers per stored link: 9, or 6 for the two-row form
+template <bool R12>
+__host__ __device__ constexpr int link_stride() { return R12 ? 6 : 9; }
+
+template <typename R, bool DIRICHLET, int MU, bool R12 = false>
 __device__ __forceinline__ void hops_mu(const Geom& g, const cx<R>* __restrict__ links,
                                         const cx<R>* __restrict__ in, int L, int rhs, int s,
                                         const int c[4], const int lc[4], int stride, Spinor<R>& acc) {
@@ -60,17 +67,19 @@ __device__ __forceinline__ void hops_mu(const Geom& g, const cx<R>* __restrict__
   if (!DIRICHLET || lc[MU] != g.blk[MU] - 1) {
     const bool wrap = (c[MU] == dm - 1);
     const int sn = wrap ? s - (dm - 1) * stride : s + stride;
-    hop<MU, -1>(acc, in + spinor_offset(sn, L, rhs), links + (size_t)(s * 4 + MU) * 9, MU == 3 && wrap);
+    hop<MU, -1, R12>(acc, in + spinor_offset(sn, L, rhs), links + (size_t)(s * 4 + MU) * link_stride<R12>(),
+                     MU == 3 && wrap);
   }
   // backward: (1 + gamma_mu) U_mu(x - mu)^dagger phi_{x-mu}
   if (!DIRICHLET || lc[MU] != 0) {
     const bool wrap = (c[MU] == 0);
     const int sn = wrap ? s + (dm - 1) * stride : s - stride;
-    hop<MU, +1>(acc, in + spinor_offset(sn, L, rhs), links + (size_t)(sn * 4 + MU) * 9, MU == 3 && wrap);
+    hop<MU, +1, R12>(acc, in + spinor_offset(sn, L, rhs), links + (size_t)(sn * 4 + MU) * link_stride<R12>(),
+                     MU == 3 && wrap);
   }
 }
 
-template <typename R, bool DIRICHLET>
+template <typename R, bool DIRICHLET, bool R12 = false>
 __device__ __forceinline__ void hopping(const Geom& g, const cx<R>* __restrict__ links,
                                         const cx<R>* __restrict__ in, int L, int rhs, int s,
                                         const int c[4], const int lc[4], Spinor<R>& acc) {
@@ -78,10 +87,10 @@ __device__ __forceinline__ void hopping(const Geom& g, const cx<R>* __restrict__
   const int st1 = g.d[0];
   const int st2 = st1 * g.d[1];
   const int st3 = st2 * g.d[2];
-  hops_mu<R, DIRICHLET, 0>(g, links, in, L, rhs, s, c, lc, 1, acc);
-  hops_mu<R, DIRICHLET, 1>(g, links, in, L, rhs, s, c, lc, st1, acc);
-  hops_mu<R, DIRICHLET, 2>(g, links, in, L, rhs, s, c, lc, st2, acc);
-  hops_mu<R, DIRICHLET, 3>(g, links, in, L, rhs, s, c, lc, st3, acc);
+  hops_mu<R, DIRICHLET, 0, R12>(g, links, in, L, rhs, s, c, lc, 1, acc);
+  hops_mu<R, DIRICHLET, 1, R12>(g, links, in, L, rhs, s, c, lc, st1, acc);
+  hops_mu<R, DIRICHLET, 2, R12>(g, links, in, L, rhs, s, c, lc, st2, acc);
+  hops_mu<R, DIRICHLET, 3, R12>(g, links, in, L, rhs, s, c, lc, st3, acc);
 }
 
 // The order in which the CTAs of the operator walk the lattice.  A CTA takes a
@@ -123,7 +132,7 @@ __device__ __forceinline__ void finish_site(const R* __restrict__ clov, int s, R
   }
 }
 
-template <typename R, int CM>
+template <typename R, int CM, bool R12 = false>
 __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_dslash_full(Geom g, const cx<R>* __restrict__ links,
                                                      const cx<R>* __restrict__ in,
                                                      cx<R>* __restrict__ out, int L, R kappa,
@@ -134,14 +143,14 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_dslash_full(Geo
   int c[4];
   site_coords(g, s, c);
   Spinor<R> acc;
-  hopping<R, false>(g, links, in, L, rhs, s, c, c, acc);
+  hopping<R, false, R12>(g, links, in, L, rhs, s, c, c, acc);
   Spinor<R> p;
   load_spinor(in + spinor_offset(s, L, rhs), p);
   finish_site<R, CM>(clov, s, kappa, p, acc);
   store_spinor(out + spinor_offset(s, L, rhs), acc);
 }
 
-template <typename R, int CM>
+template <typename R, int CM, bool R12 = false>
 __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Geom g, int colour,
                                                       const cx<R>* __restrict__ links,
                                                       const cx<R>* __restrict__ eta,
@@ -157,7 +166,7 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Ge
   load_spinor(eta + spinor_offset(s, L, rhs), e);
   if (!psi_zero) {
     Spinor<R> acc, p;
-    hopping<R, false>(g, links, psi, L, rhs, s, c, c, acc);
+    hopping<R, false, R12>(g, links, psi, L, rhs, s, c, c, acc);
     if (CM == 1) {  // A = 1 - kappa T^{-1} H
       Spinor<R> h;
       herm_apply<R>(clov + (size_t)s * HERM_PER_SITE, acc, h);
@@ -481,12 +490,7 @@ __device__ __forceinline__ void cluster_planes_to_link12(uint32_t base, int NS, 
   u.m[1][0] = mk(b.z, b.w);
   u.m[1][1] = mk(c.x, c.y);
   u.m[1][2] = mk(c.z, c.w);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-    const cx<float> t = u.m[0][j1] * u.m[1][j2] - u.m[0][j2] * u.m[1][j1];
-    u.m[2][j] = conjg(t);
-  }
+  complete_third_row(u);
 }
 
 // As cluster_planes_to_link12, from the CTA's own planes.
@@ -498,12 +502,7 @@ __device__ __forceinline__ void planes_to_link12(const float4* uS, int NS, int m
   u.m[1][0] = mk(b.z, b.w);
   u.m[1][1] = mk(c.x, c.y);
   u.m[1][2] = mk(c.z, c.w);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-    const cx<float> t = u.m[0][j1] * u.m[1][j2] - u.m[0][j2] * u.m[1][j1];
-    u.m[2][j] = conjg(t);
-  }
+  complete_third_row(u);
 }
 
 // Dirichlet hop sums of the domain operator A_dom over the eight neighbours
@@ -1040,15 +1039,25 @@ int sap_sites_per_cta(const Geom& g, int L, bool fp64) {
 }
 
 // one launch of the operator in configuration cfg (tune.h)
+// links12: the FP32 links as their first two rows (SU(3) fields), used by the
+// Wilson operator in FP32 when given
 template <typename R>
 void launch_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
-                   double kappa, DslashConfig cfg, const R* clov, int cm) {
+                   double kappa, DslashConfig cfg, const R* clov, int cm, const cx<float>* links12) {
   const int S = cfg.S;
   const dim3 block(L, S);
   const int grid = (g.V + S - 1) / S;
   const int slice = g.d[0] * g.d[1] * g.d[2];
   const bool slabs = cfg.order == 1 && slice % S == 0 && g.d[3] % 8 == 0;
   const int ws = slabs ? slice / S : 0, tt = slabs ? 8 : 1;
+  if constexpr (std::is_same<R, float>::value) {
+    if (cm == 0 && links12) {
+      k_dslash_full<float, 0, true><<<(unsigned)grid, block, 0, ex.stream>>>(g, links12, in, out, L, (float)kappa,
+                                                                             nullptr, ws, tt);
+      ++*ex.launches;
+      return;
+    }
+  }
   if (cm == 1)
     k_dslash_full<R, 1><<<(unsigned)grid, block, 0, ex.stream>>>(g, links, in, out, L, (R)kappa, clov, ws, tt);
   else if (cm == 2)
@@ -1071,13 +1080,13 @@ DslashConfig dslash_config(const Geom& g, int L) {
 
 template <typename R>
 void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
-                 double kappa, const R* clov, int cm) {
-  launch_dslash<R>(ex, g, links, in, out, L, kappa, dslash_config<R>(g, L), clov, cm);
+                 double kappa, const R* clov, int cm, const cx<float>* links12) {
+  launch_dslash<R>(ex, g, links, in, out, L, kappa, dslash_config<R>(g, L), clov, cm, links12);
 }
 
 template <typename R>
 void tune_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
-                 double kappa) {
+                 double kappa, const cx<float>* links12) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(ex.stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
   const std::vector<DslashConfig> cand = dslash_candidates(g.d, L, max_cta<R>());
@@ -1089,7 +1098,7 @@ void tune_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>*
   }
   tune_table().pick(dslash_key((int)sizeof(R), g.d, L), (int)cand.size(), [&](int i) -> double {
     cudaEventRecord(e0, ex.stream);
-    launch_dslash<R>(ex, g, links, in, out, L, kappa, cand[i], nullptr, 0);
+    launch_dslash<R>(ex, g, links, in, out, L, kappa, cand[i], nullptr, 0, links12);
     cudaEventRecord(e1, ex.stream);
     float ms = -1.0f;
     if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -1104,10 +1113,19 @@ void tune_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>*
 
 template <typename R>
 void sap_residual(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* eta,
-                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero, const R* tinv, int c0, int nc) {
+                  const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero, const R* tinv, int c0, int nc,
+                  const cx<float>* links12) {
   if (nc <= 0) nc = L;
   const int S = sap_sites_per_cta(g, nc, sizeof(R) == 8);
   const int nslot = (g.nd / 2) * g.Vd;
+  if constexpr (std::is_same<R, float>::value) {
+    if (!tinv && links12) {
+      k_sap_residual<float, 0, true><<<(unsigned)(nslot / S), dim3(nc, S), 0, ex.stream>>>(
+          g, colour, links12, eta, psi, r, L, c0, (float)kappa, psi_zero ? 1 : 0, nullptr);
+      ++*ex.launches;
+      return;
+    }
+  }
   if (tinv)
     k_sap_residual<R, 1><<<(unsigned)(nslot / S), dim3(nc, S), 0, ex.stream>>>(g, colour, links, eta, psi, r, L, c0,
                                                                                 (R)kappa, psi_zero ? 1 : 0, tinv);
@@ -1153,10 +1171,11 @@ void ssor_level(const Exec& ex, const Geom& g, int colour, const cx<R>* links, c
 
 #define INST(R)                                                                                          \
   template void dslash_full<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double,  \
-                               const R*, int);                                                          \
-  template void tune_dslash<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double); \
+                               const R*, int, const cx<float>*);                                        \
+  template void tune_dslash<R>(const Exec&, const Geom&, const cx<R>*, const cx<R>*, cx<R>*, int, double,  \
+                               const cx<float>*);                                                       \
   template void sap_residual<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, const cx<R>*,   \
-                                cx<R>*, int, double, bool, const R*, int, int);                           \
+                                cx<R>*, int, double, bool, const R*, int, int, const cx<float>*);         \
   template void sap_domain_apply<R>(const Exec&, const Geom&, int, const cx<R>*, const cx<R>*, cx<R>*,     \
                                     double*, int, double, int*, const R*);                                \
   template void ssor_level<R>(const Exec&, const Geom&, int, const cx<R>*, const R*, const cx<R>*, cx<R>*, \

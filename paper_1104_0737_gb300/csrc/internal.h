@@ -88,20 +88,22 @@ struct Timed {
 // ---------------------------------------------------------------------------
 // Wilson-Dirac operator (dslash.cu), Sec. 2.1
 // ---------------------------------------------------------------------------
-// out = in - kappa * H in on every site, L columns.
+// out = in - kappa * H in on every site, L columns.  links12 (FP32, optional):
+// the links as their first two rows, [site][mu][6] complex, 48 bytes each
+// (SU(3) fields only): the FP32 Wilson operator then reads those.
 // With clov != NULL: cm = 1 the Jacobi-preconditioned clover matrix
 // out = in - kappa T^{-1} H in (clov = T^{-1}), cm = 2 the clover matrix
 // out = in + kappa C in - kappa H in (clov = C); packed per site (herm_off).
 template <typename R>
 void dslash_full(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out,
-                 int L, double kappa, const R* clov = nullptr, int cm = 0);
+                 int L, double kappa, const R* clov = nullptr, int cm = 0, const cx<float>* links12 = nullptr);
 // Times the operator's launch configurations for this lattice, L and
 // precision once per process (in -> out, both overwritten-safe scratch for
 // out) and records the fastest for dslash_full; does nothing while the stream
 // is being captured or when the choice is already known.
 template <typename R>
 void tune_dslash(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* in, cx<R>* out, int L,
-                 double kappa);
+                 double kappa, const cx<float>* links12 = nullptr);
 // the autotuner is on when MBICG_AUTOTUNE is set and not "0"
 bool autotune_enabled();
 
@@ -149,7 +151,7 @@ void dslash_half(const Exec& ex, const Geom& g, const __half2* l16, const __half
 template <typename R>
 void sap_residual(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* eta,
                   const cx<R>* psi, cx<R>* r, int L, double kappa, bool psi_zero, const R* tinv = nullptr,
-                  int c0 = 0, int nc = 0);
+                  int c0 = 0, int nc = 0, const cx<float>* links12 = nullptr);
 //   q = r - kappa H_dom r  (hops leaving the domain dropped) and, if dots is
 //   not NULL, per-CTA partial sums of q^H r and q^H q for every column:
 //   dots[((k * nchunk) + chunk) * L + rhs] = {Re q^H r, Im q^H r, q^H q}
@@ -208,6 +210,7 @@ struct SapWork {
   void* x = nullptr;
   double* dots = nullptr;     // partial sums
   double* omega = nullptr;    // complex step lengths [domain-of-colour][rhs]
+  const cx<float>* links12 = nullptr;  // FP32 links as two rows (SU(3) fields), else NULL
   size_t bytes_block = 0;     // size of one full-lattice block
   size_t dots_len = 0;
   int L = 0;
@@ -295,6 +298,8 @@ int block_update_zeta(const Exec& ex, long long nsite, int L, const cx<R>* U, co
                       const cx<R>* S, const cx<R>* Z, const cx<R>* V, const double* zeta_beta, cx<R>* Rv,
                       cx<R>* P, cx<double>* X64, double* part);
 
+// U12 = the first two rows of every FP32 link ([site][mu][6])
+void links_to_rows(const Exec& ex, long long nsite, const cx<float>* U32, cx<float>* U12);
 // dst (device) = src (registered host memory, its mapped device address),
 // bytes a multiple of 16 and both 16-byte aligned: a copy kernel
 void copy_from_mapped_host(const Exec& ex, const void* src, void* dst, size_t bytes);

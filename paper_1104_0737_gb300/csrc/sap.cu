@@ -244,7 +244,7 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
       for (int colour = 0; colour < 2; ++colour) {
         {
           Timed t(ex, KC_SAP_RESID);
-          sap_residual<R>(ex, g, colour, links, eta, psi, r, L, kappa, cyc == 0 && colour == 0, tinv);
+          sap_residual<R>(ex, g, colour, links, eta, psi, r, L, kappa, cyc == 0 && colour == 0, tinv, 0, 0, w.links12);
         }
         Timed t(ex, KC_SAP_DOMAIN);
         ssor_solve<R>(ex, g, colour, links, tinv, r, x, L, kappa, *ssor, w);
@@ -266,7 +266,7 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
           const bool first = cyc == 0 && colour == 0;
           if (!first) {
             Timed t(ex, KC_SAP_RESID);
-            sap_residual<R>(ex, g, colour, links, eta, psi, r, L, kappa, false, tinv);
+            sap_residual<R>(ex, g, colour, links, eta, psi, r, L, kappa, false, tinv, 0, 0, w.links12);
           }
           Timed t(ex, KC_SAP_SWEEP);
           sap_sweep_fused(ex, g, colour, links, first ? eta : r, psi, L, kappa, first ? 1 : 2, nmr, mr_mode, tab,
@@ -276,7 +276,7 @@ void sap_apply(const Exec& ex, const Geom& g, const cx<R>* links, const cx<R>* e
       }
       {
         Timed t(ex, KC_SAP_RESID);
-        sap_residual<R>(ex, g, colour, links, eta, psi, r, L, kappa, cyc == 0 && colour == 0, tinv);
+        sap_residual<R>(ex, g, colour, links, eta, psi, r, L, kappa, cyc == 0 && colour == 0, tinv, 0, 0, w.links12);
       }
       for (int it = 0; it < nmr; ++it) {
         const bool need_dots = (mr_mode != 3);

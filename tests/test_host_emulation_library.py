@@ -139,8 +139,10 @@ def _device_copy(lib, a):
 
 def test_noalloc_operator(lib, ctx):
     """mbicg_apply_D_noalloc (device pointers, a fixed scratch array) gives the
-    FP32 operator of mbicg_apply_D bit for bit, on two calls in a row with
-    different blocks; sizes beyond its scratch and host pointers are refused."""
+    FP32 operator of mbicg_apply_D, on two calls in a row with different
+    blocks, to FP32 rounding (mbicg_apply_D reads an SU(3) field's links as two
+    rows and rebuilds the third; the allocation-free call reads the caller's
+    full links); sizes beyond its scratch and host pointers are refused."""
     c, U = ctx
     dims = (ctypes.c_int * 4)(*DIMS)
     dU = _device_copy(lib, U)
@@ -154,7 +156,9 @@ def test_noalloc_operator(lib, ctx):
             assert lib.mbicg_apply_D_noalloc(dims, dU, d_in, d_out, Lc, kappa, None) == mb.MBICG_OK
             out = np.empty_like(psi)
             ctypes.memmove(out.ctypes.data, d_out, out.nbytes)
-            assert np.array_equal(out, ref)
+            V = ref.shape[0]
+            d = np.linalg.norm((out - ref).reshape(V, -1), axis=1) / np.linalg.norm(ref.reshape(V, -1), axis=1)
+            assert d.max() < 1e-6
             lib.cudaFree(d_in)
             lib.cudaFree(d_out)
         big = (ctypes.c_int * 4)(16, 16, 16, 16)
