@@ -107,9 +107,9 @@ struct mbicg_server {
 
 namespace {
 
-// Device bytes a slot of a field holds for the links (FP64, FP32 and the
-// FP16 rows) and its fixed scratch.
-double slot_fixed_bytes(long long V) { return V * (576.0 + 288 + 96) + (1 << 22); }
+// Device bytes a slot of a field holds for the links (FP64, FP32, the FP16
+// rows and the FP32 rows) and its fixed scratch.
+double slot_fixed_bytes(long long V) { return V * (576.0 + 288 + 96 + 192) + (1 << 22); }
 
 // Device bytes of the workspace of a block solve of L columns on V sites: B,
 // X and W in FP64, the seven Krylov blocks, the preconditioner's blocks (FP32
