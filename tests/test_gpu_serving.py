@@ -161,7 +161,7 @@ def test_admission_by_hbm_footprint(oracle_mod):
         assert e.value.status == mb.MBICG_ENOMEM
     finally:
         mb.mbicg_server_destroy(srv)
-    links = 2 * (V * 960 + (1 << 22))
+    links = 2 * (V * 1152 + (1 << 22))  # FP64, FP32, FP16-row and FP32-row links per slot
     budget = links + 1.5 * solve_bytes(V, 12)
     srv = mb.mbicg_server_create(0, budget / 1e9)
     try:
