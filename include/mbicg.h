@@ -374,7 +374,7 @@ typedef struct {
 } mbicg_request_info;
 
 /* A server on `device` whose slots hold at most hbm_budget_gb gigabytes (1e9
- * bytes) of device memory: per slot 960 V bytes of links and 4 MiB, per
+ * bytes) of device memory: per slot 1152 V bytes of links and 4 MiB, per
  * admitted block solve of L columns about 12 V L (3 x 16 + 7 x 8 + 3 x 8 +
  * 3 x 16) bytes for FP32 Krylov vectors and FP32 SAP storage (FP64 ones count
  * 16 bytes per complex number; FP16 SAP storage adds 3 x 52 bytes per site
