@@ -163,8 +163,9 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Ge
   colour_slot_coords(g, colour, slot, c, lc, &k);
   const int s = site_index(g, c);
   Spinor<R> e;
-  load_spinor(eta + spinor_offset(s, L, rhs), e);
   if (!psi_zero) {
+    // the hop sum first: eta and psi of the site are loaded after it, so that
+    // they hold no registers across the eight hops
     Spinor<R> acc, p;
     hopping<R, false, R12>(g, links, psi, L, rhs, s, c, c, acc);
     if (CM == 1) {  // A = 1 - kappa T^{-1} H
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Ge
       herm_apply<R>(clov + (size_t)s * HERM_PER_SITE, acc, h);
       acc = h;
     }
+    load_spinor(eta + spinor_offset(s, L, rhs), e);
     load_spinor(psi + spinor_offset(s, L, rhs), p);
     // r = eta - (psi - kappa eta_hop) = eta - psi + kappa eta_hop
 #pragma unroll
@@ -180,6 +182,8 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_sap_residual(Ge
       const cx<R> pj = (&p.c[0][0])[j], aj = (&acc.c[0][0])[j];
       ej = mk(fma(kappa, aj.re, ej.re - pj.re), fma(kappa, aj.im, ej.im - pj.im));
     }
+  } else {
+    load_spinor(eta + spinor_offset(s, L, rhs), e);
   }
   store_spinor(r + spinor_offset(s, L, rhs), e);
 }
