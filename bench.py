@@ -53,7 +53,7 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "wilson_32c64_L12"
 # Iterations the GPU solver takes on the default workload (measured); the CPU
 # baseline extrapolates its per-iteration time with it.
-GPU_ITERS = {"wilson_32c64_L12": 49}
+GPU_ITERS = {"wilson_32c64_L12": 50}
 
 METRIC = "RHS solves/s to true rel. residual 1e-10, 32^3x64 L=12; Dslash %HBM; p99 ms"
 UNIT = "RHS solves/s"
