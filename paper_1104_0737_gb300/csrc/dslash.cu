@@ -382,12 +382,14 @@ __global__ void __launch_bounds__(max_cta<R>(), min_ctas<R>()) k_ssor_level(Geom
 // ---------------------------------------------------------------------------
 // Fused SAP colour sweep with the MR iterations on chip (FP32).
 //
-// Persistent thread-block clusters walk the (domain of the colour, column)
-// items.  The DX x DY x DZ x DT domain is cut into CX x CY x CZ x CT
-// sub-blocks, one per CTA of the cluster, one thread per site; cutting y, z
-// and t in two gives every CTA the same number of hops that leave the domain
-// and of hops into a neighbouring CTA, so no CTA lags at the cluster
-// barriers.  The MR residual of its sites lives in shared memory, double
+// Persistent thread-block clusters walk the (domain of the colour, column
+// group) items, NCOL columns per thread.  The DX x DY x DZ x DT domain is cut
+// into CX x CY x CZ x CT sub-blocks, one per CTA of the cluster, one thread per
+// site; cutting y, z and t gives every CTA the same number of hops that leave
+// the domain and of hops into a neighbouring CTA, so no CTA lags at the
+// cluster barriers.  A column's hops are summed in one fixed order whatever
+// the cut and NCOL, so every launch shape gives the same bits with frozen
+// step lengths.  The MR residual of its sites lives in shared memory, double
 // buffered so that one cluster barrier per MR step separates the neighbour
 // reads of one step from the writes of the next; x and q stay in registers.
 // Spinors are stored as 6 float4 planes so consecutive threads read
