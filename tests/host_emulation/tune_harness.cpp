@@ -56,4 +56,10 @@ int tune_key(int real_bytes, const int* dims, int L, char* buf, int n) {
   strncpy(buf, k.c_str(), n);
   return (int)k.size();
 }
+int tune_sweep_key(int half, int clover, const int* dims, int L, char* buf, int n) {
+  const std::string k = sweep_key(half != 0, clover != 0, dims, L);
+  strncpy(buf, k.c_str(), n);
+  return (int)k.size();
+}
+int tune_sweep_shapes() { return SWEEP_SHAPES; }
 }

@@ -35,6 +35,7 @@ def tune(tmp_path_factory):
     lib.tune_lookup.argtypes = [ctypes.c_char_p]
     lib.tune_candidates.argtypes = [I, ctypes.c_int, ctypes.c_int, I]
     lib.tune_key.argtypes = [ctypes.c_int, I, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
+    lib.tune_sweep_key.argtypes = [ctypes.c_int, ctypes.c_int, I, ctypes.c_int, ctypes.c_char_p, ctypes.c_int]
     return lib
 
 
@@ -90,3 +91,24 @@ def test_operator_candidates(tune, dims, L, maxt):
     buf = ctypes.create_string_buffer(128)
     tune.tune_key(4, (ctypes.c_int * 4)(*dims), L, buf, 128)
     assert buf.value.decode() == f"dslash/fp32/{dims[0]}x{dims[1]}x{dims[2]}x{dims[3]}/L{L}"
+
+
+def test_sweep_keys(tune):
+    """One key per storage, operator, lattice and L for the SAP sweep's launch
+    shape (8-CTA clusters; 16-CTA clusters with two columns per thread; with
+    one): the keys bench.py prints under "autotuned" and MBICG_TUNE_FILE holds."""
+    assert tune.tune_sweep_shapes() == 3
+    buf = ctypes.create_string_buffer(128)
+    dims = (ctypes.c_int * 4)(32, 32, 32, 64)
+    keys = set()
+    for half in (0, 1):
+        for clover in (0, 1):
+            for L in (1, 12):
+                n = tune.tune_sweep_key(half, clover, dims, L, buf, 128)
+                k = buf.value.decode()
+                assert n == len(k) and k.startswith("sap_sweep/") and k.endswith(f"/32x32x32x64/L{L}")
+                assert (("fp16" in k) == bool(half)) and (("clover" in k) == bool(clover))
+                keys.add(k)
+    assert len(keys) == 8
+    tune.tune_sweep_key(0, 0, dims, 12, buf, 128)
+    assert buf.value.decode() == "sap_sweep/fp32/32x32x32x64/L12"
