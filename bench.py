@@ -119,8 +119,8 @@ def sap_resid_bytes(V, L, block, real_bytes=4):
 # ncu capture of dram__bytes_read.sum + dram__bytes_write.sum, valid only for the
 # kernel source it was taken on (a hash of csrc/dslash.cu and csrc/common.cuh,
 # first 16 hex digits)
-NCU_TRAFFIC = {("sap_sweep", "wilson_32c64_L12"): {"bytes": 2742926848 + 1168523008, "source_sha256": "b89489d2bea30fa6"},
-               ("sap_resid", "wilson_32c64_L12"): {"bytes": 3848248320 + 1193446400, "source_sha256": "b89489d2bea30fa6"}}
+NCU_TRAFFIC = {("sap_sweep", "wilson_32c64_L12"): {"bytes": 2743783680 + 1172062720, "source_sha256": "703e40b05b940475"},
+               ("sap_resid", "wilson_32c64_L12"): {"bytes": 3848284160 + 1190637312, "source_sha256": "703e40b05b940475"}}
 
 
 def ncu_traffic(kernel: str, workload: str):

@@ -704,46 +704,21 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT, NCO
 #pragma unroll
     for (int j = 0; j < NCOL; ++j) zero(x[j]);
 
-    for (int it = 0; it < nmr; ++it) {
+    // the MR steps that apply the operator: all of them with per-column step
+    // lengths, all but the last with frozen ones
+    const int nop = (mode == 0) ? nmr : nmr - 1;
+    for (int it = 0; it < nop; ++it) {
       const bool last = (it == nmr - 1);
-      const bool need_q = (mode == 0) || !last;
       Spinor<float> q[NCOL];
-      cluster_wait();  // the residual planes of every CTA (and, when !need_q, no CTA reads nxt any more)
-      if (need_q) {
-        domain_hops<SH, NCOL, DX, DY, DZ, DT, CX, CY, CZ>(cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, q);
-        if (CM == 1) {
-#pragma unroll
-          for (int j = 0; j < NCOL; ++j) {
-            Spinor<float> h;
-            herm_apply<float>(tinv + (size_t)s * HERM_PER_SITE, q[j], h);
-            q[j] = h;
-          }
-        }
-      }
-      if (!H && last && !need_q && item + 1 < item1) {
-        // the next item: the next column group of this site, or the first
-        // one of the next domain
-        const int kn = (item + 1) / ngrp;
-        const int gn = item + 1 - kn * ngrp;
-        int sn = s;
-        if (kn != kk) {
-          int b[4], cn[4];
-          colour_domain(g, colour, kn, b);
-          cn[0] = b[0] * DX + lc[0];
-          cn[1] = b[1] * DY + lc[1];
-          cn[2] = b[2] * DZ + lc[2];
-          cn[3] = b[3] * DT + lc[3];
-          sn = site_index(g, cn);
-        }
+      cluster_wait();  // the residual planes of every CTA
+      domain_hops<SH, NCOL, DX, DY, DZ, DT, CX, CY, CZ>(cur, smem_addr(cur), uS, uA, tid, rank, sb, lc, q);
+      if (CM == 1) {
 #pragma unroll
         for (int j = 0; j < NCOL; ++j) {
-          const size_t offn = spinor_offset(sn, L, column(gn, j));
-          const float4* src = reinterpret_cast<const float4*>(static_cast<const cx<float>*>(rin) + offn);
-#pragma unroll
-          for (int e = 0; e < 6; ++e) cp_async_16(nxt + (6 * j + e) * NS + tid, src + e);
+          Spinor<float> h;
+          herm_apply<float>(tinv + (size_t)s * HERM_PER_SITE, q[j], h);
+          q[j] = h;
         }
-        cp_async_commit();
-        have_rn = true;
       }
       cx<float> om[NCOL];
       if (mode == 0) {
@@ -802,7 +777,7 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT, NCO
       for (int j = 0; j < NCOL; ++j) {
         Spinor<float> rv;
         planes_to_spinor(cur + 6 * j * NS, NS, tid, rv);
-        if (need_q && mode != 0) {
+        if (mode != 0) {
 #pragma unroll
           for (int e = 0; e < 12; ++e) {
             cx<float>& o = (&q[j].c[0][0])[e];
@@ -824,19 +799,63 @@ __global__ void __launch_bounds__(SweepShape<DX, DY, DZ, DT, CX, CY, CZ, CT, NCO
         float4* t = cur; cur = nxt; nxt = t;
       }
     }
-    // psi += x for the group's columns
+    // psi += x for the group's columns.  With frozen step lengths the last MR
+    // step applies no operator: psi's loads are issued before its wait for
+    // the other CTAs, which hides their latency, and the step only adds
+    // omega r to x.
+    Spinor<float> pv[NCOL];
+#pragma unroll
+    for (int j = 0; j < NCOL; ++j) {
+      const size_t off = spinor_offset(s, L, c0 + grp * NCOL + j);
+      if (psi_mode == 1 || grp * NCOL + j >= nc) zero(pv[j]);
+      else if (H) load_spinor_h(static_cast<const __half2*>(psi) + off, psc[off / 12], pv[j]);
+      else load_spinor(static_cast<const cx<float>*>(psi) + off, pv[j]);
+    }
+    if (mode != 0) {
+      cluster_wait();  // no CTA reads nxt any more
+      if (!H && item + 1 < item1) {
+        // the next item: the next column group of this site, or the first
+        // one of the next domain
+        const int kn = (item + 1) / ngrp;
+        const int gn = item + 1 - kn * ngrp;
+        int sn = s;
+        if (kn != kk) {
+          int b[4], cn[4];
+          colour_domain(g, colour, kn, b);
+          cn[0] = b[0] * DX + lc[0];
+          cn[1] = b[1] * DY + lc[1];
+          cn[2] = b[2] * DZ + lc[2];
+          cn[3] = b[3] * DT + lc[3];
+          sn = site_index(g, cn);
+        }
+#pragma unroll
+        for (int j = 0; j < NCOL; ++j) {
+          const size_t offn = spinor_offset(sn, L, column(gn, j));
+          const float4* src = reinterpret_cast<const float4*>(static_cast<const cx<float>*>(rin) + offn);
+#pragma unroll
+          for (int e = 0; e < 6; ++e) cp_async_16(nxt + (6 * j + e) * NS + tid, src + e);
+        }
+        cp_async_commit();
+        have_rn = true;
+      }
+      const float2 o2 = oms[nmr - 1];
+      const cx<float> om = mk(o2.x, o2.y);
+#pragma unroll
+      for (int j = 0; j < NCOL; ++j) {
+        Spinor<float> rv;
+        planes_to_spinor(cur + 6 * j * NS, NS, tid, rv);
+#pragma unroll
+        for (int e = 0; e < 12; ++e) cmac((&x[j].c[0][0])[e], om, (&rv.c[0][0])[e]);
+      }
+    }
 #pragma unroll
     for (int j = 0; j < NCOL; ++j) {
       if (grp * NCOL + j >= nc) break;
       const size_t off = spinor_offset(s, L, c0 + grp * NCOL + j);
-      Spinor<float> pv;
-      if (psi_mode == 1) zero(pv);
-      else if (H) load_spinor_h(static_cast<const __half2*>(psi) + off, psc[off / 12], pv);
-      else load_spinor(static_cast<const cx<float>*>(psi) + off, pv);
 #pragma unroll
-      for (int e = 0; e < 12; ++e) (&pv.c[0][0])[e] = (&pv.c[0][0])[e] + (&x[j].c[0][0])[e];
-      if (H) store_spinor_h(static_cast<__half2*>(psi) + off, psc + off / 12, pv);
-      else store_spinor(static_cast<cx<float>*>(psi) + off, pv);
+      for (int e = 0; e < 12; ++e) (&pv[j].c[0][0])[e] = (&pv[j].c[0][0])[e] + (&x[j].c[0][0])[e];
+      if (H) store_spinor_h(static_cast<__half2*>(psi) + off, psc + off / 12, pv[j]);
+      else store_spinor(static_cast<cx<float>*>(psi) + off, pv[j]);
     }
     // the next item writes its residual into nxt: the last reads of nxt by
     // other CTAs were fenced by the barrier that followed them
