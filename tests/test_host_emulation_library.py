@@ -137,6 +137,47 @@ def _device_copy(lib, a):
     return p
 
 
+def _pinned_copy(lib, a):
+    """An emulated page-locked host buffer (the runtime's cudaMallocHost) holding
+    a copy of a, and a numpy view of it."""
+    p = ctypes.c_void_p()
+    assert lib.cudaMallocHost(ctypes.byref(p), a.nbytes) == 0
+    view = np.ctypeslib.as_array((ctypes.c_char * a.nbytes).from_address(p.value))
+    arr = np.frombuffer(view, dtype=a.dtype).reshape(a.shape)
+    arr[...] = a
+    return p, arr
+
+
+def test_pinned_host_blocks_take_the_mapped_copy(lib, ctx):
+    """Blocks in page-locked host memory are staged by the mapped-host copy
+    kernel (pageable ones by the runtime copy): the operator and a block solve
+    give the same bits either way."""
+    c, U = ctx
+    for prec in (mb.MBICG_FP64, mb.MBICG_FP32):
+        psi = synth.gaussian_source(DIMS, 3, seed=2010)
+        ref = np.empty_like(psi)
+        assert lib.mbicg_apply_D(c, _v(psi), _v(ref), 3, KAPPA, prec) == mb.MBICG_OK
+        pin, pin_arr = _pinned_copy(lib, psi)
+        pout, pout_arr = _pinned_copy(lib, np.zeros_like(psi))
+        assert lib.mbicg_apply_D(c, pin, pout, 3, KAPPA, prec) == mb.MBICG_OK
+        assert np.array_equal(pout_arr, ref)
+        lib.cudaFreeHost(pin)
+        lib.cudaFreeHost(pout)
+    B = synth.gaussian_source(DIMS, L, seed=2011)
+    X = np.empty_like(B)
+    assert _solve(lib, c, B, X, _params(lib))[0] == mb.MBICG_OK
+    pB, B_arr = _pinned_copy(lib, B)
+    pX, X_arr = _pinned_copy(lib, np.zeros_like(B))
+    it = ctypes.c_int(0)
+    tres = np.zeros(L)
+    p = _params(lib)
+    assert lib.mbicg_block_solve(c, pB, pX, L, KAPPA, 1e-10, ctypes.byref(p), ctypes.byref(it),
+                                 tres.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == mb.MBICG_OK
+    assert np.array_equal(X_arr, X)
+    lib.cudaFreeHost(pB)
+    lib.cudaFreeHost(pX)
+
+
 def test_noalloc_operator(lib, ctx):
     """mbicg_apply_D_noalloc (device pointers, a fixed scratch array) gives the
     FP32 operator of mbicg_apply_D, on two calls in a row with different
