@@ -116,6 +116,15 @@ def main(so, sanitizer):
              "apply_D_noalloc L=3")
     for p in bufs:
         lib.cudaFree(p)
+    # page-locked host blocks: staged by the mapped-host copy kernel
+    nbytes = int(np.prod(small.dims)) * 12 * 3 * 16
+    hb = [ctypes.c_void_p() for _ in range(2)]
+    for p in hb:
+        assert lib.cudaMallocHost(ctypes.byref(p), ctypes.c_size_t(nbytes)) == 0
+    ctypes.memmove(hb[0], psi.ctypes.data, nbytes)
+    small.ok(lib.mbicg_apply_D(small.c, hb[0], hb[1], 3, KAPPA, mb.MBICG_FP32), "apply_D from page-locked memory")
+    for p in hb:
+        lib.cudaFreeHost(p)
     for fused in ("1", "0"):
         os.environ["MBICG_SAP_FUSED"] = fused
         for mode in (mb.MBICG_MR_COLUMN, mb.MBICG_MR_BLOCK):
