@@ -72,9 +72,16 @@ def load_peaks():
 # ---------------------------------------------------------------------------
 # algorithmic bytes and flops per launch (FP32 storage, links counted once)
 # ---------------------------------------------------------------------------
-def dslash_bytes(V, L, real_bytes=4):
+# The synthetic fields are SU(3) (exponentials of i times traceless Hermitian
+# matrices), so the library's FP32 operator and SAP residual kernel read each
+# link as its first two rows (12 reals) and rebuild the third.
+FP32_LINK_REALS = 12
+
+
+def dslash_bytes(V, L, real_bytes=4, link_reals=18):
     # per site: L spinors read + L written (12 complex each), 4 forward links
-    return V * (L * 2 * 12 * 2 * real_bytes + 4 * 9 * 2 * real_bytes)
+    # of link_reals reals (18, or 12 when only the first two rows are read)
+    return V * (L * 2 * 12 * 2 * real_bytes + 4 * link_reals * real_bytes)
 
 
 def dslash_flops(V, L):
@@ -105,14 +112,24 @@ def sap_sweep_flops(V, L, nmr, frozen=True):
     return (V // 2) * L * (nmr * 1368 + nmr * 192 + nmr * 12 * 12)
 
 
-def sap_resid_bytes(V, L, block, real_bytes=4):
-    """The residual eta - A psi of one colour: eta and psi of the colour's
-    sites read, r written, psi of the faces of the neighbouring domains read
-    (one face layer per face: 2 * sum_mu V / block_mu sites over both colours,
-    half of them here) and the links (four forward links of each site, FP32)."""
+def sap_resid_bytes(V, L, block, real_bytes=4, link_reals=18):
+    """The residual eta - A psi of one colour, every operand moved once: eta
+    and psi of the colour's sites read and r written; psi of the other
+    colour's sites next to the colour's domains, which is the whole surface of
+    every domain of the other colour (all neighbours of a domain have the
+    other colour when the domain counts are even); the four forward links of
+    the colour's sites and, for each site on a backward face, the link of its
+    neighbour across that face (link_reals reals per link)."""
     spinor = 24 * real_bytes
-    faces = sum(V // b for b in block)  # face sites of one colour's domains
-    return (V // 2) * (L * 3 * spinor + 4 * 18 * real_bytes) + faces * L * spinor
+    link = link_reals * real_bytes
+    half = V // 2
+    vol = block[0] * block[1] * block[2] * block[3]
+    inner = 1
+    for b in block:
+        inner *= max(b - 2, 0)
+    surface = (half // vol) * (vol - inner)  # other-colour sites read for the halo
+    back_links = sum(half // b for b in block)
+    return half * (3 * L * spinor + 4 * link) + surface * L * spinor + back_links * link
 
 
 # DRAM bytes per launch of the dominant kernel at the benchmark workload, from one
@@ -559,9 +576,10 @@ def main():
     alu_peak = fp32_alu_peak_tflops(sm_mhz)
     models = {
         "sap_sweep": ("alu", sap_sweep_bytes(V, L), sap_sweep_flops(V, L, cfg["nmr"])),
-        "sap_resid": ("hbm", sap_resid_bytes(V, L, cfg["block"]), dslash_flops(V // 2, L)),
+        "sap_resid": ("hbm", sap_resid_bytes(V, L, cfg["block"], link_reals=FP32_LINK_REALS),
+                      dslash_flops(V // 2, L)),
         "sap_domain": ("hbm", sap_domain_bytes(V, L), dslash_flops(V // 2, L)),
-        "dslash": ("hbm", dslash_bytes(V, L), dslash_flops(V, L)),
+        "dslash": ("hbm", dslash_bytes(V, L, link_reals=FP32_LINK_REALS), dslash_flops(V, L)),
     }
     dom = max((k for k in models if prof[k][1] > 0), key=lambda k: prof[k][0])
     bound, nbytes, nflops = models[dom]
@@ -579,9 +597,11 @@ def main():
                     "frac": gbs / hbm_peak, "traffic": ncu_traffic(dom, args.workload), "peak_kind": peak_kind,
                     "algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": avg_ms}
     dsl_ms = prof["dslash"][0] / prof["dslash"][1] if prof["dslash"][1] else None
-    dslash_frac = (dslash_bytes(V, L) / (dsl_ms * 1e-3) / 1e9) / hbm_peak if dsl_ms else None
+    dsl_bytes = dslash_bytes(V, L, link_reals=FP32_LINK_REALS)
+    dslash_frac = (dsl_bytes / (dsl_ms * 1e-3) / 1e9) / hbm_peak if dsl_ms else None
     res_ms = prof["sap_resid"][0] / prof["sap_resid"][1] if prof["sap_resid"][1] else None
-    resid_frac = (sap_resid_bytes(V, L, cfg["block"]) / (res_ms * 1e-3) / 1e9) / hbm_peak if res_ms else None
+    res_bytes = sap_resid_bytes(V, L, cfg["block"], link_reals=FP32_LINK_REALS)
+    resid_frac = (res_bytes / (res_ms * 1e-3) / 1e9) / hbm_peak if res_ms else None
 
     # end to end through the ABI with pinned host buffers
     e2e = None

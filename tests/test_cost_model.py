@@ -48,3 +48,46 @@ def test_algorithmic_bytes():
     assert bench.dslash_bytes(2, 12) == 2 * (12 * 192 + 288)
     assert bench.dslash_bytes(1, 12, real_bytes=8) == 12 * 384 + 576
     assert bench.sap_domain_bytes(4, 3) == bench.dslash_bytes(2, 3)
+    # two-row links: 12 reals, 48 B in FP32
+    assert bench.dslash_bytes(1, 12, link_reals=12) == 12 * 192 + 192
+
+
+def _colour_residual_operands(dims, block):
+    """By enumeration: the sites of colour 0 (the domains whose coordinate sum
+    is even), the distinct sites whose psi the residual eta - A psi on them
+    reads, and the distinct (site, mu) links its hops use."""
+    import itertools
+
+    def colour(x):
+        return sum(x[m] // block[m] for m in range(4)) % 2
+
+    ncol, psi, links = 0, set(), set()
+    for x in itertools.product(*[range(n) for n in dims]):
+        if colour(x) != 0:
+            continue
+        ncol += 1
+        psi.add(x)
+        for mu in range(4):
+            fw = list(x)
+            fw[mu] = (x[mu] + 1) % dims[mu]
+            bw = list(x)
+            bw[mu] = (x[mu] - 1) % dims[mu]
+            psi.update([tuple(fw), tuple(bw)])
+            links.update([(x, mu), (tuple(bw), mu)])
+    return ncol, len(psi), len(links)
+
+
+@pytest.mark.parametrize("dims,block", [((8, 4, 4, 8), (4, 2, 2, 4)), ((8, 8, 4, 4), (2, 4, 2, 2)),
+                                        ((12, 6, 6, 12), (3, 3, 3, 6))])
+@pytest.mark.parametrize("link_reals", [18, 12])
+def test_sap_residual_bytes_count_each_operand_once(dims, block, link_reals):
+    """The residual kernel's algorithmic bytes against an enumeration of the
+    operands on small lattices with even domain counts: eta read and r
+    written on the colour's sites, each psi it needs read once, each link once."""
+    L = 3
+    ncol, npsi, nlinks = _colour_residual_operands(dims, block)
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    assert ncol == V // 2
+    spinor, link = 96, link_reals * 4
+    want = ncol * 2 * L * spinor + npsi * L * spinor + nlinks * link
+    assert bench.sap_resid_bytes(V, L, block, link_reals=link_reals) == want
