@@ -17,8 +17,7 @@
 // The host code cannot use the array's name as a device address (in host code
 // it names a host-side stand-in), so the address is fetched with
 // cudaGetSymbolAddress, once per device with that device current, by the first
-// call on that device; that first call should therefore come before any
-// stream capture begins.
+// call on that device.
 #include <mutex>
 
 #include "../../include/mbicg.h"
