@@ -165,12 +165,15 @@ int mbicg_create(mbicg_ctx** ctx, const int dims[4], int device, void* cuda_stre
 void mbicg_destroy(mbicg_ctx* ctx);
 
 /* Copies the gauge field U (layout above, 4 V SU(3) matrices, complex128)
- * into the library's own FP64, FP32 and FP16 copies (the FP16 copy keeps the
- * first two rows of each link).  Sec. 2.1: the links of Eq. (hoppingterm).
+ * into the library's own FP64, FP32 and FP16 copies and an FP32 copy of the
+ * first two rows of each link (the FP16 copy keeps those two rows as well).
+ * Sec. 2.1: the links of Eq. (hoppingterm).
  * Every link is checked for unitarity and det = 1 (to 1e-10); a field that is
  * not SU(3) is accepted, but the kernels that rebuild a link's third row from
- * its first two (the fused SAP sweep, FP16 storage) are then not used.
- * MBICG_ENAN if U holds NaN or Inf. */
+ * its first two (the fused SAP sweep, the FP32 operator's two-row reads, FP16
+ * storage) are then not used.  A loaded clover term is dropped.
+ * MBICG_ENAN if U holds NaN or Inf.  After any failure the context holds no
+ * field (MBICG_ENOGAUGE until a later load succeeds). */
 int mbicg_load_gauge(mbicg_ctx* ctx, const double* U);
 
 /* out = A in for L columns (Eq. (hoppingterm), (bloclhoppingterm) of

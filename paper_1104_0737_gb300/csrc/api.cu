@@ -1062,6 +1062,10 @@ int mbicg_load_gauge(mbicg_ctx* c, const double* U) {
   c->err.clear();
   if (!U) return fail(c, MBICG_EINVAL, "U is NULL");
   CK(cudaSetDevice(c->device));
+  // the copies are overwritten below: until they all hold the new field, no
+  // field is loaded
+  c->gauge = false;
+  c->su3 = false;
   c->launches = 0;
   c->csw = 0.0;  // a clover term belongs to the previous field
   c->tinv_kappa = NAN;
@@ -1090,10 +1094,7 @@ int mbicg_load_gauge(mbicg_ctx* c, const double* U) {
   c->prof.collect();
   memcpy(&bad, c->h_small, sizeof(int));
   c->stats.kernel_launches = c->launches;
-  if (bad & 1) {
-    c->gauge = false;
-    return fail(c, MBICG_ENAN, "gauge field holds NaN or Inf");
-  }
+  if (bad & 1) return fail(c, MBICG_ENAN, "gauge field holds NaN or Inf");
   c->su3 = (bad & 2) == 0;
   c->gauge = true;
   return MBICG_OK;

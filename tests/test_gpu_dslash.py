@@ -83,6 +83,9 @@ def test_dslash_errors():
         with pytest.raises(mb.MbicgError) as e:
             mb.mbicg_load_gauge(ctx, U)
         assert e.value.status == mb.MBICG_ENAN
+        with pytest.raises(mb.MbicgError) as e:
+            mb.mbicg_apply_D(ctx, psi, out, 2, 0.1, mb.MBICG_FP64)
+        assert e.value.status == mb.MBICG_ENOGAUGE  # a failed load leaves no field
         mb.mbicg_load_gauge(ctx, synth.su3_links(dims, 0.5, seed=2))
         for L in (0, 17):
             with pytest.raises(mb.MbicgError) as e:

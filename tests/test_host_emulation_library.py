@@ -126,6 +126,15 @@ def test_abi_errors(lib, ctx):
     fresh = ctypes.c_void_p()
     assert lib.mbicg_create(ctypes.byref(fresh), (ctypes.c_int * 4)(*DIMS), 0, None) == mb.MBICG_OK
     assert _solve(lib, fresh, B, X, _params(lib))[0] == mb.MBICG_ENOGAUGE
+    # a field that fails to load replaces the one before it by none
+    U = synth.su3_links(DIMS, 0.4, seed=1000)
+    assert lib.mbicg_load_gauge(fresh, _v(U)) == mb.MBICG_OK
+    Un = U.copy()
+    Un[7, 2, 1, 1] = np.inf
+    assert lib.mbicg_load_gauge(fresh, _v(Un)) == mb.MBICG_ENAN
+    assert _solve(lib, fresh, B, X, _params(lib))[0] == mb.MBICG_ENOGAUGE
+    assert lib.mbicg_load_gauge(fresh, _v(U)) == mb.MBICG_OK
+    assert _solve(lib, fresh, B, X, _params(lib))[0] == mb.MBICG_OK
     lib.mbicg_destroy(fresh)
 
 
