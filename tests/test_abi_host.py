@@ -109,3 +109,17 @@ def test_server_rejects_bad_arguments_without_a_device():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         assert lib.mbicg_server_create(ctypes.byref(srv), 0, 10.0) == mb.MBICG_ECUDA
+
+
+def test_a_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No fallback: without the CUDA library every call raises instead of
+    computing elsewhere."""
+    monkeypatch.setattr(mb, "_lib", None)
+    monkeypatch.setattr(mb._build, "LIB", str(tmp_path / "libmbicg.so"))
+    monkeypatch.setattr(mb._build, "needs_build", lambda: False)
+    with pytest.raises(OSError, match="CUDA library not built"):
+        mb.load_library()
+    with pytest.raises(OSError):
+        mb.mbicg_create((4, 4, 4, 4))
+    with pytest.raises(OSError):
+        mb.mbicg_default_params()
