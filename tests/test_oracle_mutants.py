@@ -38,6 +38,15 @@ MUTANTS = [
      "mask_colour(dims, block, 1 - colour, r, L);", SAP),
     ("SAP: one cycle too many", "for (int cyc = 0; cyc < ncycle; ++cyc) {",
      "for (int cyc = 0; cyc <= ncycle; ++cyc) {", SAP),
+    # the frozen step-length table (the stationary preconditioner of Sec. 2.1)
+    ("SAP frozen: one table entry for every cycle", "table + (((long)cyc * 2 + colour) * nmr + it) * nd + dd",
+     "table + (((long)0 * 2 + colour) * nmr + it) * nd + dd", SAP),
+    ("SAP frozen: one table entry for every MR step", "table + (((long)cyc * 2 + colour) * nmr + it) * nd + dd",
+     "table + (((long)cyc * 2 + colour) * nmr + 0) * nd + dd", SAP),
+    ("SAP frozen: recorded where the residual is zero", "if (mr_mode == 2 && d_sum > 0) *tab = om;",
+     "if (mr_mode == 2) *tab = om;", SAP),
+    ("SAP frozen: the replay ignores the table", "if (mr_mode == 2 && !isnan(creal(*tab))) {",
+     "if (0 && mr_mode == 2 && !isnan(creal(*tab))) {", SAP),
     # QR and L x L solves, Sec. 2.1
     ("QR: projection conjugated on the wrong side", "s += conj(A[n * L + i]) * A[n * L + j];",
      "s += A[n * L + i] * conj(A[n * L + j]);", SOLVER),
