@@ -933,38 +933,38 @@ int oracle_block_bicgstab_ext(const int dims[4], const double* Ud, double kappa,
   for (int i = 0; i < L; ++i)
     if (!(bn[i] > 0)) { status = -1; goto done; }
 
-  /* line 1: initial guess */
+  /* the initial guess */
   if (!use_x0) memset(X, 0, sizeof(cplx) * NL);
-  /* line 2: R = B - A X */
+  /* R = B - A X */
   oracle_apply_A(dims, Ud, kappa, Tinvd, (const double*)X, (double*)W, L);
   for (long n = 0; n < NL; ++n) R[n] = B[n] - W[n];
-  /* line 3: P = R */
+  /* P = R */
   memcpy(P, R, sizeof(cplx) * NL);
-  /* line 4: choose R~ */
+  /* R~: the caller's, else R */
   if (rtilde) memcpy(Rt, rtilde, sizeof(cplx) * NL);
   else memcpy(Rt, R, sizeof(cplx) * NL);
 
   column_norms(R, N, L, rn);
   while (max_rel(rn, bn, L) > tol) {
     if (k >= max_iter) { status = 1; break; }
-    /* 4.1 QR decomposition P = Q gamma, P <- Q */
+    /* QR decomposition P = Q gamma, P <- Q */
     if (oracle_qr_mgs((double*)P, N, L, NULL) != 0) { status = 2; break; }
-    /* 4.2 U = M P */
+    /* U = M P */
     apply_M(dims, Ud, kappa, &pc, P, Ub, L, NL);
-    /* 4.3 V = A U */
+    /* V = A U */
     oracle_apply_A(dims, Ud, kappa, Tinvd, (const double*)Ub, (double*)Vb, L);
-    /* 4.4 solve (R~^H V) alpha = R~^H R */
+    /* solve (R~^H V) alpha = R~^H R */
     block_gram(Rt, Vb, N, L, G);
     block_gram(Rt, R, N, L, alpha);
     if (oracle_lu_solve((const double*)G, (double*)alpha, L, L) != 0) { status = 2; break; }
-    /* 4.5 T = R - V alpha */
+    /* T = R - V alpha */
     block_times(Vb, alpha, N, L, W);
     for (long n = 0; n < NL; ++n) T[n] = R[n] - W[n];
-    /* 4.6 S = M T */
+    /* S = M T */
     apply_M(dims, Ud, kappa, &pc, T, S, L, NL);
-    /* 4.7 Z = A S */
+    /* Z = A S */
     oracle_apply_A(dims, Ud, kappa, Tinvd, (const double*)S, (double*)Z, L);
-    /* 4.8 zeta = Tr(Z^H T) / Tr(Z^H Z) */
+    /* zeta = Tr(Z^H T) / Tr(Z^H Z) */
     cplx zt = 0, zz = 0;
     {
       cplx* gzt = malloc(sizeof(cplx) * L * L);
@@ -977,16 +977,16 @@ int oracle_block_bicgstab_ext(const int dims[4], const double* Ud, double kappa,
     }
     if (!(cabs(zz) > 0)) { status = 2; break; }
     const cplx zeta = zt / zz;
-    /* 4.9 X <- X + U alpha + zeta S */
+    /* X <- X + U alpha + zeta S */
     block_times(Ub, alpha, N, L, W);
     for (long n = 0; n < NL; ++n) X[n] += W[n] + zeta * S[n];
-    /* 4.10 R = T - zeta Z */
+    /* R = T - zeta Z */
     for (long n = 0; n < NL; ++n) R[n] = T[n] - zeta * Z[n];
-    /* 4.11 solve (R~^H V) beta = - R~^H Z */
+    /* solve (R~^H V) beta = - R~^H Z */
     block_gram(Rt, Z, N, L, beta);
     for (int q = 0; q < L * L; ++q) beta[q] = -beta[q];
     if (oracle_lu_solve((const double*)G, (double*)beta, L, L) != 0) { status = 2; break; }
-    /* 4.12 P <- R + (P - zeta V) beta */
+    /* P <- R + (P - zeta V) beta */
     for (long n = 0; n < NL; ++n) T[n] = P[n] - zeta * Vb[n];
     block_times(T, beta, N, L, W);
     for (long n = 0; n < NL; ++n) P[n] = R[n] + W[n];

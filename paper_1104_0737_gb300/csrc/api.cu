@@ -510,16 +510,16 @@ struct Solver {
     return check_launch(c, "qr");
   }
 
-  // One iteration's launches, Algorithm 2 lines 4.1-4.13 and the column
+  // One iteration's launches (the loop body of Algorithm 2) and the column
   // norms, with no host synchronisation (so that it can be captured).
   int iteration_launches() {
     int rc;
-    // 4.1 QR of P
+    // QR of P
     if ((rc = qr())) return rc;
-    // 4.2 U = M P, 4.3 V = A U
+    // U = M P, V = A U
     if ((rc = apply_M(k.P, k.U))) return rc;
     if ((rc = dslash(k.U, k.V))) return rc;
-    // 4.4 (R~^H V) alpha = R~^H R
+    // (R~^H V) alpha = R~^H R
     {
       int np;
       {
@@ -529,15 +529,15 @@ struct Solver {
       Timed t(ex, KC_SMALL);
       lxl_alpha(ex, L, gpart, np, sm);
     }
-    // 4.5 R -= V alpha (4.6, X += U alpha, is folded into the update after zeta)
+    // R -= V alpha (X += U alpha is folded into the update after zeta)
     {
       Timed t(ex, KC_AXPY);
       block_update_alpha<T>(ex, V, L, k.V, sm.alpha, k.R);
     }
-    // 4.7 S = M R, 4.8 Z = A S
+    // S = M R, Z = A S
     if ((rc = apply_M(k.R, k.S))) return rc;
     if ((rc = dslash(k.S, k.Z))) return rc;
-    // 4.9 zeta = Tr(Z^H R)/Tr(Z^H Z), 4.12 (R~^H V) beta = -R~^H Z
+    // zeta = Tr(Z^H R)/Tr(Z^H Z), (R~^H V) beta = -R~^H Z
     {
       int np;
       {
@@ -547,7 +547,7 @@ struct Solver {
       Timed t(ex, KC_SMALL);
       lxl_zeta_beta(ex, L, gpart, np, sm);
     }
-    // 4.6 + 4.10 X += U alpha + zeta S, 4.11 R -= zeta Z, 4.13 P = R + (P - zeta V) beta
+    // X += U alpha + zeta S, R -= zeta Z, P = R + (P - zeta V) beta
     {
       int np;
       {
@@ -731,9 +731,9 @@ struct Solver {
     if (!p.use_x0) CK(cudaMemsetAsync(X64, 0, sizeof(cx<double>) * nl, c->stream));
     CK(cudaMemsetAsync(sm.status, 0, sizeof(int), c->stream));
     double rel[MAXL] = {0}, relmax;
-    // line 2: R = B - A X
+    // R = B - A X
     if ((rc = true_residual(rel, &relmax, !p.use_x0))) return rc;
-    // lines 3-4: P = R, R~ = R
+    // P = R, R~ = R
     CK(cudaMemcpyAsync(k.P, k.R, sizeof(cx<T>) * nl, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemcpyAsync(k.Rt, k.R, sizeof(cx<T>) * nl, cudaMemcpyDeviceToDevice, c->stream));
     double rmax_ru = relmax;

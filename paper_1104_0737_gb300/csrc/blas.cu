@@ -3,12 +3,13 @@
 //   - fused block inner products (R~^H V, R~^H R; R~^H Z with Tr(Z^H R) and
 //     Tr(Z^H Z); P^H P for the QR) with per-CTA partial sums on a fixed grid,
 //     so every reduction is formed in one fixed order (bitwise reproducible);
-//   - block AXPYs (lines 4.5-4.6 and 4.10-4.13) and the QR transform P <- P M;
+//   - block AXPYs (the updates of R, X and P) and the QR transform P <- P M;
 //   - layout and precision conversions at the ABI boundary;
 //   - the L x L algebra (LU with partial pivoting, Cholesky, triangular
 //     inverse) in FP64 in single-CTA kernels, so nothing leaves the device
 //     inside an iteration but the residual norms.
-// FP32 blocks: products in FP32, partial sums widened to FP64 every few tiles.
+// FP32 blocks: products in FP32, running sums as TwoSum pairs of FP32, the
+// per-CTA partial sums in FP64.
 #include <math.h>
 
 #include "internal.h"
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(NT) k_transform(int nrow, const cx<R>* X, cons
   }
 }
 
-// R -= V alpha (4.5); X += U alpha is deferred to k_update_zeta
+// R -= V alpha; X += U alpha is deferred to k_update_zeta
 template <typename R, int L>
 __global__ void __launch_bounds__(NT) k_update_alpha(int nrow, const cx<R>* __restrict__ V,
                                                      const double* __restrict__ alpha, cx<R>* __restrict__ Rv) {
@@ -387,9 +388,9 @@ __global__ void __launch_bounds__(NT) k_update_alpha(int nrow, const cx<R>* __re
   }
 }
 
-// X += U alpha + zeta S (the X update of Algorithm 1, 4.9, which Algorithm 2
-// splits into 4.6 and 4.10), R -= zeta Z (4.11), P = R + (P - zeta V) beta
-// (4.13), and the squared column norms of the new R.  X is accumulated in
+// X += U alpha + zeta S (one update in Algorithm 1, which Algorithm 2 splits
+// into its U alpha and zeta S parts), R -= zeta Z, P = R + (P - zeta V) beta,
+// and the squared column norms of the new R.  X is accumulated in
 // FP64; its increment U alpha + zeta S is formed in the Krylov vectors'
 // precision (they are its inputs), so FP32 vectors cost two FP64 adds per
 // element rather than FP64 products (FP64 runs at 1/64 of the FP32 rate).

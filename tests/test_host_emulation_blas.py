@@ -1,10 +1,11 @@
 """The block linear algebra kernels of the CUDA path, compiled for the host and
 run with one host thread per CUDA thread (tests/host_emulation/
 shim_threads.h; the Gram kernel's bulk copies and mbarrier waits emulated),
-against their plain definitions: the fused block inner products (Algorithm 2,
-4.4, 4.9, 4.12 and the P^H P of the QR; FP64 and FP32 storage, ragged last
-tile, several CTAs), the block updates (4.5, 4.6 with 4.10, 4.11, 4.13 and the
-column norms; Y = X M of the QR), the one-CTA L x L kernels: LU with partial
+against their plain definitions: the fused block inner products of Algorithm 2
+(R~^H V with R~^H R; R~^H Z with Tr(Z^H R) and Tr(Z^H Z); the P^H P of the QR;
+FP64 and FP32 storage, ragged last tile, several CTAs), the block updates
+(R -= V alpha; X += U alpha + zeta S, R -= zeta Z and P = R + (P - zeta V) beta
+with the column norms; Y = X M of the QR), the one-CTA L x L kernels: LU with partial
 pivoting for alpha and beta, zeta, and the Cholesky factor's inverse (plain
 and shifted) of CholeskyQR; and the conversions: ABI <-> internal layout,
 the link copies with their NaN and SU(3) checks, the residual B - W with its
@@ -176,9 +177,9 @@ def test_cholesky_failure(blas):
 # Gram kernel
 # ---------------------------------------------------------------------------
 GRAM_CASES = [  # (flags, A is B1)
-    (1 | 2, False),       # 4.4: R~^H V and R~^H R
+    (1 | 2, False),       # R~^H V and R~^H R (the alpha system)
     (1, True),            # P^H P of the QR (Hermitian path)
-    (1 | 4 | 8, False),   # 4.9, 4.12: R~^H Z, diag(Z^H R), diag(Z^H Z)
+    (1 | 4 | 8, False),   # R~^H Z, diag(Z^H R), diag(Z^H Z) (zeta and the beta system)
 ]
 
 
