@@ -5,9 +5,9 @@
  * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
  * CPU-baseline leg of the benchmark, never by the CUDA library.  It is written
  * to be checked against the paper by eye: full 4x4 spin matrices (no spin
- * projection), Algorithm 1 taken line by line, modified Gram-Schmidt for the
- * QR, LU with partial pivoting for the L x L solves, and every operator
- * applied through its plain definition.  Loops over sites are OpenMP parallel;
+ * projection), the steps of Algorithm 1 in the paper's order and notation,
+ * modified Gram-Schmidt for the QR, LU with partial pivoting for the L x L
+ * solves, and every operator applied through its plain definition.  Loops over sites are OpenMP parallel;
  * every sum is formed in a fixed order so results do not depend on the thread
  * count.
  *
