@@ -3,7 +3,7 @@ right-hand sides are nearly dependent: columns that differ by 1e-6 make P
 nearly rank deficient, and without the re-orthonormalisation the true
 residual drifts away from the recursive one (the oracle's mutation check
 shows 1e-9 .. 1e-6 at a recursive 1e-12).  With FP64 Krylov vectors
-(CholeskyQR2) the solve must reach the tolerance in the true residual."""
+(shifted CholeskyQR3) the solve must reach the tolerance in the true residual."""
 import numpy as np
 import pytest
 
