@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(NT, 2) k_gram(long long nsite, const cx<R>* __
   constexpr int BB = SH::BB, NBI = SH::NBI, NB = SH::NB, LANES = SH::LANES, TS = SH::TS, TILE = SH::TILE;
   constexpr int STAGES = SH::STAGES, NARR = SH::NARR;
   static_assert(STAGES * sizeof(uint64_t) <= 64, "the stages' mbarriers live in the last 64 bytes");
-  // FP32 per-tile sums are widened into FP64 running sums every FLUSH tiles
+  // FP32 accumulators collect FLUSH tiles, then go into the running sums
+  // (TwoSum pairs); FP64 accumulators go in after every tile
   constexpr int FLUSH = sizeof(R) == 4 ? 8 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (SH::smem - 64));
