@@ -4,9 +4,11 @@
 //
 // Solver state lives on the device for the whole solve: B and X in FP64, the
 // Krylov blocks R, P, R~, U, V, S, Z in the Krylov precision T (FP64, or FP32
-// with reliable updates).  The only device-to-host traffic inside an iteration
-// is the L squared residual norms and a status word, read once per iteration
-// for the stopping test of Algorithm 2.
+// with reliable updates).  The iterations run in a device-side loop (a CUDA
+// graph with a conditional WHILE node): nothing leaves the device until the
+// loop stops; the fallback, a graph per iteration, reads the L squared
+// residual norms and a status word once per iteration for the stopping test
+// of Algorithm 2.
 //
 // Mixed precision (FP32 Krylov loop): X accumulates in FP64; whenever
 // max_i |r_i|/|b_i| has dropped by delta_ru since the last update, the true

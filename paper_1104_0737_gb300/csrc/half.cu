@@ -10,7 +10,7 @@
 // The operator (Sec. 2.1, the hopping term of the Wilson-Dirac matrix) reads
 // FP16 neighbours and links, accumulates in FP32 and rounds its result into the
 // same format.  Per site and column it moves L x (2 x 52) + 96 bytes instead of
-// L x 192 + 288 in FP32.
+// L x 192 + 192 in FP32 with two-row links.
 #include <cuda_fp16.h>
 
 #include "internal.h"

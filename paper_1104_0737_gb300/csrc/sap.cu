@@ -4,15 +4,20 @@
 //   K = [[B_EE, 0], [-B_OO A_OE B_EE, B_OO]],
 // i.e. ncycle multiplicative cycles, each an E sweep then an O sweep on the
 // updated residual.  The domain solves B_EE, B_OO are nmr minimal-residual
-// steps started from zero (MR in place of the paper's SSOR).
+// steps started from zero, or the paper's SSOR solves (the wavefront kernels
+// below).
 //
 // Each colour sweep recomputes the residual on that colour from eta and the
 // current psi (r = eta - A psi), so no residual array has to be carried
 // between sweeps, then runs the MR steps on all domains of the colour at once:
 //   q = A_dom r (Dirichlet), omega = (q^H r)/(q^H q), x += omega r, r -= omega q
-// and finally adds x to psi.  Per MR step: the domain operator with fused
-// per-CTA dot products, a small kernel that forms the step lengths (per column,
-// shared by the block, or read from a frozen table), and the update.
+// and finally adds x to psi.  In FP32 (or FP16 storage), with 8^4 or 4^4
+// domains of an SU(3) field and per-column or replayed frozen step lengths,
+// the MR steps of a colour run on chip in one fused cluster kernel
+// (dslash.cu).  Otherwise, per MR step: the domain
+// operator with fused per-CTA dot products, a small kernel that forms the step
+// lengths (per column, shared by the block, or read from a frozen table), and
+// the update.  Frozen step lengths are recorded on this multi-kernel path.
 #include <math.h>
 #include <stdlib.h>
 
