@@ -43,8 +43,10 @@ typedef enum {
   MBICG_ENOMEM = -2,      /* device allocation failed */
   MBICG_ENOGAUGE = -3,    /* no gauge field loaded */
   MBICG_ENOTCONV = -4,    /* max_iter reached; X, iters, true_res are filled */
-  MBICG_EBREAKDOWN = -5,  /* singular R~^H V, zero Tr(Z^H Z) or rank-deficient P,
-                             also after one restart; X, iters, true_res filled */
+  MBICG_EBREAKDOWN = -5,  /* singular R~^H V, zero Tr(Z^H Z) or rank-deficient P
+                             again right after a restart from the current X, or
+                             a fourth time (with FP32 Krylov vectors: also in
+                             the FP64 continuation); X, iters, true_res filled */
   MBICG_ENAN = -6,        /* NaN or Inf in the input or in a residual norm */
   MBICG_ECUDA = -7        /* a CUDA runtime error; see mbicg_last_error */
 } mbicg_status;
@@ -260,8 +262,10 @@ int mbicg_sap_precond_frozen(mbicg_ctx* ctx, const double* in, double* out, int 
  * Tr(Z^H Z) = 0) restarts from the current X (at most three times, not twice
  * in a row); with FP32 Krylov vectors a solve that still breaks down continues
  * from its X with FP64 Krylov vectors (mbicg_stats.precision_fallbacks).  Once
- * the frozen step lengths are recorded each iteration's kernels are replayed
- * from one captured CUDA graph on the context's stream.
+ * the frozen step lengths are recorded, the iterations run from one captured
+ * CUDA graph on the context's stream whose conditional WHILE node repeats the
+ * iteration while the device's own stopping test holds; the host steps in only
+ * when that loop stops (convergence, reliable update, breakdown, max_iter).
  * Returns MBICG_OK, MBICG_ENOTCONV (max_iter reached or the final true
  * residual above tol), MBICG_EBREAKDOWN, MBICG_ENAN, or MBICG_EINVAL /
  * MBICG_ENOGAUGE / MBICG_ENOMEM / MBICG_ECUDA before or instead of a result. */
