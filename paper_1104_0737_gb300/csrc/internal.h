@@ -158,8 +158,9 @@ void sap_residual(const Exec& ex, const Geom& g, int colour, const cx<R>* links,
 template <typename R>
 void sap_domain_apply(const Exec& ex, const Geom& g, int colour, const cx<R>* links, const cx<R>* r,
                       cx<R>* q, double* dots, int L, double kappa, int* nchunk_out, const R* tinv = nullptr);
-// One whole colour sweep (residual, nmr MR steps, psi += x) in one kernel,
-// the domain kept on chip by a thread-block cluster; FP32, MR modes 0 and 3,
+// The rest of a colour sweep once its residual is formed (nmr MR steps from
+// rin, then psi += x) in one kernel, the domain kept on chip by a
+// thread-block cluster; FP32, MR modes 0 and 3,
 // domain shapes 8^4 and 4^4, with T^{-1} (tinv) for the Jacobi-preconditioned
 // clover matrix.  Returns false (nothing launched) otherwise.
 // table: the frozen step lengths of this (cycle, colour), [nmr][nd/2] complex.
