@@ -328,7 +328,8 @@ const char* mbicg_last_error(const mbicg_ctx* ctx);
  * rounded up to 256 bytes, must fit in it, else MBICG_EINVAL (nothing is
  * launched).  Every call shares the array; calls that overlap on the GPU (two
  * streams, two host threads) race on it.  The first call on a device looks
- * the array's address up (cudaGetSymbolAddress) with that device current.
+ * the array's address up (cudaGetSymbolAddress) with that device current;
+ * make that first call on each device before any stream capture begins.
  * Returns MBICG_EINVAL for bad arguments, host pointers or pointers of another
  * device (nothing launched), MBICG_ECUDA if a CUDA error was already pending
  * on entry (it is neither launched over nor cleared), if the lookup fails or

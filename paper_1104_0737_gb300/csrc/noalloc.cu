@@ -17,7 +17,8 @@
 // The host code cannot use the array's name as a device address (in host code
 // it names a host-side stand-in), so the address is fetched with
 // cudaGetSymbolAddress, once per device with that device current, by the first
-// call on that device.
+// call on that device; that first call should come before any stream capture
+// begins on that device.
 #include <mutex>
 
 #include "../../include/mbicg.h"
