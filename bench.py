@@ -425,6 +425,16 @@ def whole_job_rate(world: int, L: int, steps: int, seconds: float) -> float:
     return world * L * steps / seconds
 
 
+def leg_error(name: str, exc: BaseException) -> dict:
+    """A side leg of the bench (end to end, CPU baseline, FP64 arm, other
+    storage, SSOR, Table 1, serving) that raised: reported on stderr and in
+    the line in place of that leg's result, so that the timed solve's line is
+    still printed."""
+    msg = f"{type(exc).__name__}: {exc}"
+    print(f"bench.py: the {name} leg failed: {msg}", file=sys.stderr, flush=True)
+    return {"error": msg}
+
+
 def _cfg_public(cfg):
     return {"lattice": "x".join(map(str, cfg["dims"])), "L": cfg["L"], "source": cfg["source"],
             "kappa": cfg["kappa"], "eps": cfg["eps"], "sap_block": "x".join(map(str, cfg["block"])),
@@ -605,27 +615,35 @@ def main():
 
     # end to end through the ABI with pinned host buffers
     e2e = None
-    if not args.no_e2e:
-        hB = torch.from_numpy(B).pin_memory()
-        hX = torch.empty_like(hB).pin_memory()
-        solve(hB, hX)  # untimed: the library's staging buffers for host blocks are allocated here
-        torch.cuda.synchronize()
+    try:
+        if not args.no_e2e:
+            hB = torch.from_numpy(B).pin_memory()
+            hX = torch.empty_like(hB).pin_memory()
+            solve(hB, hX)  # untimed: the library's staging buffers for host blocks are allocated here
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                solve(hB, hX)
+            t1 = time.perf_counter()
+            e2e_s = t1 - t0
+            e2e_s = max_over_ranks(e2e_s, dist, f"cuda:{local}")
+            nb = B.nbytes
+            e2e = {"value": whole_job_rate(world, L, args.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": nb,
+                   "d2h_bytes_per_step": nb}
+    except Exception as e:  # a failed side leg ends that leg only
         if dist:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            solve(hB, hX)
-        t1 = time.perf_counter()
-        e2e_s = t1 - t0
-        e2e_s = max_over_ranks(e2e_s, dist, f"cuda:{local}")
-        nb = B.nbytes
-        e2e = {"value": whole_job_rate(world, L, args.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": nb,
-               "d2h_bytes_per_step": nb}
+            raise  # the other replicas wait in max_over_ranks: fail the job instead
+        e2e = leg_error("e2e", e)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(cfg, int(np.median(iters)))
-        cpu.pop("sample_seconds", None)
+    try:
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            cpu = oracle_sample(cfg, int(np.median(iters)))
+            cpu.pop("sample_seconds", None)
+    except Exception as e:  # a failed side leg ends that leg only
+        cpu = leg_error("cpu", e)
 
     # legs without an untimed warm-up solve run untuned (a first solve of a
     # new lattice, L or precision would otherwise time the candidates inside
@@ -633,79 +651,96 @@ def main():
     if tune_file:
         os.environ["MBICG_AUTOTUNE"] = "0"
     fp64_arm = None
-    if not args.no_fp64_arm and rank == 0:
-        p64 = mb.mbicg_default_params(ncycle=cfg["ncycle"], nmr=cfg["nmr"], block=cfg["block"],
-                                      mr_mode=mb.MBICG_MR_FROZEN, prec_D=mb.MBICG_FP64,
-                                      prec_sap=mb.MBICG_FP64, max_iter=5000)
-        b1 = dB[..., :1].contiguous()
-        x1 = torch.empty_like(b1)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, it1, tr1 = mb.mbicg_block_solve(ctx, b1, x1, 1, cfg["kappa"], cfg["tol"], p64)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        fp64_arm = {"value": 1.0 / dt, "unit": UNIT, "iters": it1, "status": st,
-                    "sample": "one FP64 L=1 solve (column 0), FP64 operator and SAP"}
+    try:
+        if not args.no_fp64_arm and rank == 0:
+            p64 = mb.mbicg_default_params(ncycle=cfg["ncycle"], nmr=cfg["nmr"], block=cfg["block"],
+                                          mr_mode=mb.MBICG_MR_FROZEN, prec_D=mb.MBICG_FP64,
+                                          prec_sap=mb.MBICG_FP64, max_iter=5000)
+            b1 = dB[..., :1].contiguous()
+            x1 = torch.empty_like(b1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, it1, tr1 = mb.mbicg_block_solve(ctx, b1, x1, 1, cfg["kappa"], cfg["tol"], p64)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            fp64_arm = {"value": 1.0 / dt, "unit": UNIT, "iters": it1, "status": st,
+                        "sample": "one FP64 L=1 solve (column 0), FP64 operator and SAP"}
+    except Exception as e:  # a failed side leg ends that leg only
+        fp64_arm = leg_error("fp64_arm", e)
 
     # the same workload with the preconditioner's blocks in the other storage
     # (FP16 with per-(site, column) scales, or FP32): one warm-up solve and one
     # timed solve, stopped at twice the iterations of the main line (FP16
     # storage does not converge on this workload)
     alt = None
-    if not args.no_alt_storage and rank == 0:
-        other = "fp16" if args.prec_sap == "fp32" else "fp32"
-        pa = mb.mbicg_default_params(ncycle=cfg["ncycle"], nmr=cfg["nmr"], block=cfg["block"],
-                                     mr_mode=mb.MBICG_MR_FROZEN, prec_D=mb.MBICG_FP32,
-                                     prec_sap={"fp32": mb.MBICG_FP32, "fp16": mb.MBICG_FP16}[other],
-                                     max_iter=2 * max(iters) + 20)
-        if tune_file:
-            os.environ["MBICG_AUTOTUNE"] = "1"
-        st, it_a, tr_a = mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], pa)  # warm-up
+    try:
+        if not args.no_alt_storage and rank == 0:
+            other = "fp16" if args.prec_sap == "fp32" else "fp32"
+            pa = mb.mbicg_default_params(ncycle=cfg["ncycle"], nmr=cfg["nmr"], block=cfg["block"],
+                                         mr_mode=mb.MBICG_MR_FROZEN, prec_D=mb.MBICG_FP32,
+                                         prec_sap={"fp32": mb.MBICG_FP32, "fp16": mb.MBICG_FP16}[other],
+                                         max_iter=2 * max(iters) + 20)
+            if tune_file:
+                os.environ["MBICG_AUTOTUNE"] = "1"
+            st, it_a, tr_a = mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], pa)  # warm-up
+            if tune_file:
+                os.environ["MBICG_AUTOTUNE"] = "0"
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record()
+                st, it_a, tr_a = mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], pa)
+                its, trs = [it_a], [max(tr_a)]
+                a1.record()
+            torch.cuda.synchronize()
+            ms = a0.elapsed_time(a1) / len(its)
+            alt = {"prec_sap": other, "value": L * 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "iters": its,
+                   "true_res_max": max(trs), "status": st}
+    except Exception as e:  # a failed side leg ends that leg only
         if tune_file:
             os.environ["MBICG_AUTOTUNE"] = "0"
-        torch.cuda.synchronize()
-        with torch.cuda.stream(stream):
-            a0 = torch.cuda.Event(enable_timing=True)
-            a1 = torch.cuda.Event(enable_timing=True)
-            a0.record()
-            st, it_a, tr_a = mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], pa)
-            its, trs = [it_a], [max(tr_a)]
-            a1.record()
-        torch.cuda.synchronize()
-        ms = a0.elapsed_time(a1) / len(its)
-        alt = {"prec_sap": other, "value": L * 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "iters": its,
-               "true_res_max": max(trs), "status": st}
+        alt = leg_error("alt", e)
 
     # the same workload with the paper's SSOR domain solves (Sec. 2.2: omega 1.26,
     # N_SSOR = 1) in place of the MR steps: one warm-up solve, one timed
     ssor = None
-    if not args.no_ssor_line and rank == 0:
-        ps = mb.mbicg_default_params(ncycle=cfg["ncycle"], block=cfg["block"], domain_solver=mb.MBICG_DOMAIN_SSOR,
-                                     nssor=1, ssor_omega=1.26, prec_D=mb.MBICG_FP32, prec_sap=mb.MBICG_FP32,
-                                     max_iter=2 * max(iters) + 20)
-        mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], ps)
-        torch.cuda.synchronize()
-        with torch.cuda.stream(stream):
-            s0 = torch.cuda.Event(enable_timing=True)
-            s1 = torch.cuda.Event(enable_timing=True)
-            s0.record()
-            st, it_s, tr_s = mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], ps)
-            s1.record()
-        torch.cuda.synchronize()
-        ms = s0.elapsed_time(s1)
-        ssor = {"domain_solver": "SSOR omega 1.26, N_SSOR 1", "value": L * 1e3 / ms, "unit": UNIT,
-                "ms_per_step": ms, "iters": it_s, "true_res_max": max(tr_s), "status": st}
+    try:
+        if not args.no_ssor_line and rank == 0:
+            ps = mb.mbicg_default_params(ncycle=cfg["ncycle"], block=cfg["block"], domain_solver=mb.MBICG_DOMAIN_SSOR,
+                                         nssor=1, ssor_omega=1.26, prec_D=mb.MBICG_FP32, prec_sap=mb.MBICG_FP32,
+                                         max_iter=2 * max(iters) + 20)
+            mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], ps)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                s0 = torch.cuda.Event(enable_timing=True)
+                s1 = torch.cuda.Event(enable_timing=True)
+                s0.record()
+                st, it_s, tr_s = mb.mbicg_block_solve(ctx, dB, dX, L, cfg["kappa"], cfg["tol"], ps)
+                s1.record()
+            torch.cuda.synchronize()
+            ms = s0.elapsed_time(s1)
+            ssor = {"domain_solver": "SSOR omega 1.26, N_SSOR 1", "value": L * 1e3 / ms, "unit": UNIT,
+                    "ms_per_step": ms, "iters": it_s, "true_res_max": max(tr_s), "status": st}
+    except Exception as e:  # a failed side leg ends that leg only
+        ssor = leg_error("ssor", e)
 
     table1 = None
-    if args.table1 and rank == 0:
-        table1 = run_table1(ctx, cfg, dB, prec_sap)
+    try:
+        if args.table1 and rank == 0:
+            table1 = run_table1(ctx, cfg, dB, prec_sap)
+    except Exception as e:  # a failed side leg ends that leg only
+        table1 = leg_error("table1", e)
 
     mb.mbicg_destroy(ctx)
     del dB, dX
     serving = None
-    if rank == 0 and world == 1 and not args.no_serving:
-        torch.cuda.empty_cache()
-        serving = run_serving(local)
+    try:
+        if rank == 0 and world == 1 and not args.no_serving:
+            torch.cuda.empty_cache()
+            serving = run_serving(local)
+    except Exception as e:  # a failed side leg ends that leg only
+        serving = leg_error("serving", e)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
