@@ -369,7 +369,9 @@ int mbicg_selftest_bounded_wait(int device, int spin_limit, int expect_bytes, in
  * workspaces, and if that is not enough it waits for a running solve to
  * finish.  Requests arriving while slots or memory are busy wait; the slots
  * of different fields, and the slots of one field, solve concurrently.
- * Thread-safe: submit and wait may be called from any host threads.
+ * Thread-safe: submit and wait may be called from any host threads, and a
+ * field may be added while the slots of others are solving (calls adding
+ * fields are taken one at a time).
  * ------------------------------------------------------------------------ */
 typedef struct mbicg_server mbicg_server;
 

@@ -70,6 +70,8 @@ struct Request {
 
 struct Slot {
   int field = 0;
+  long long V = 0;        // the field's sites and solver parameters, copied so that
+  mbicg_params params{};  // a running solve never reads the server's field list
   mbicg_ctx* ctx = nullptr;
   cx<double>* dB = nullptr;  // packed block
   cx<double>* dX = nullptr;
@@ -95,6 +97,7 @@ struct mbicg_server {
   long long mem_waits = 0;      // block solves that waited for memory
   std::vector<Field> fields;
   std::vector<Slot*> slots;
+  std::mutex add_mu;  // one mbicg_server_add_field at a time
   std::deque<Request*> pending;
   std::map<long long, Request*> requests;
   std::mutex mu;
@@ -182,9 +185,10 @@ std::vector<Request*> take_batch(mbicg_server* s, Slot* sl, bool* no_memory) {
   return batch;
 }
 
+// Called without s->mu: the fields' list may grow meanwhile (another
+// mbicg_server_add_field), so only the slot's own copy of its field is read.
 void run_batch(mbicg_server* s, Slot* sl, std::vector<Request*>& batch) {
-  const Field& f = s->fields[sl->field];
-  const long long nrow = f.V * 12;
+  const long long nrow = sl->V * 12;
   int L = 0;
   for (Request* r : batch) L += r->L;
   const double t0 = now_ms();
@@ -224,7 +228,7 @@ void run_batch(mbicg_server* s, Slot* sl, std::vector<Request*>& batch) {
   }
   if (status == MBICG_OK)
     status = mbicg_block_solve(sl->ctx, reinterpret_cast<const double*>(sl->dB), reinterpret_cast<double*>(sl->dX),
-                               L, batch[0]->kappa, batch[0]->tol, &f.params, &iters, tres);
+                               L, batch[0]->kappa, batch[0]->tol, &sl->params, &iters, tres);
   const bool have_x = status == MBICG_OK || status == MBICG_ENOTCONV || status == MBICG_EBREAKDOWN;
   int o = 0;
   for (Request* r : batch) {
@@ -241,7 +245,7 @@ void run_batch(mbicg_server* s, Slot* sl, std::vector<Request*>& batch) {
     o += r->L;
   }
   const double t1 = now_ms();
-  const double held = slot_held_bytes(sl, f.V);
+  const double held = slot_held_bytes(sl, sl->V);
   std::lock_guard<std::mutex> lk(s->mu);
   // what the slot really holds now replaces the estimate charged for it
   s->used += held - sl->held;
@@ -350,6 +354,8 @@ int mbicg_server_add_field(mbicg_server* s, const int dims[4], const double* U, 
   const double need = slot_fixed_bytes(f.V);
   std::vector<Slot*> made;
   int rc = MBICG_OK;
+  // the new field's index is the list's length until this call appends it
+  std::lock_guard<std::mutex> add_lk(s->add_mu);
   cudaSetDevice(s->device);
   for (int k = 0; k < max_slots; ++k) {
     {
@@ -357,7 +363,12 @@ int mbicg_server_add_field(mbicg_server* s, const int dims[4], const double* U, 
       if (s->used + need > s->budget) break;  // admission by HBM footprint
     }
     Slot* sl = new Slot();
-    sl->field = (int)s->fields.size();
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      sl->field = (int)s->fields.size();
+    }
+    sl->V = f.V;
+    sl->params = f.params;
     if ((rc = mbicg_create(&sl->ctx, dims, s->device, nullptr)) != MBICG_OK ||
         (rc = mbicg_load_gauge(sl->ctx, U)) != MBICG_OK) {
       free_slot(sl);
@@ -385,23 +396,20 @@ int mbicg_server_submit(mbicg_server* s, int field, const double* B, int L, doub
                         long long* request_id) {
   if (!s || !B || !request_id || L < 1 || L > SERVE_MAXL || !(tol > 0)) return MBICG_EINVAL;
   if (on_device(B)) return MBICG_EINVAL;  // B is read on the host
-  Request* r = new Request();
+  long long V = 0;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    if (field < 0 || field >= (int)s->fields.size()) {
-      delete r;
-      return MBICG_EINVAL;
-    }
+    if (field < 0 || field >= (int)s->fields.size()) return MBICG_EINVAL;
     const Field& f = s->fields[field];
     // a block of this request alone must fit beside the slots' links
     double fixed = 0;
     for (const Field& g : s->fields) fixed += g.nslots * slot_fixed_bytes(g.V);
-    if (fixed + solve_bytes(f.V, L, f.params) > s->budget) {
-      delete r;
-      return MBICG_ENOMEM;
-    }
-    r->B.assign(B, B + 2 * (size_t)f.V * 12 * L);
+    if (fixed + solve_bytes(f.V, L, f.params) > s->budget) return MBICG_ENOMEM;
+    V = f.V;
   }
+  // the copy of B is made without the lock: the slots' bookkeeping goes on meanwhile
+  Request* r = new Request();
+  r->B.assign(B, B + 2 * (size_t)V * 12 * L);
   r->field = field;
   r->L = L;
   r->kappa = kappa;

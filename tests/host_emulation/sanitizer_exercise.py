@@ -189,8 +189,26 @@ def main(so, sanitizer):
     clients = [threading.Thread(target=client, args=(i,)) for i in range(4)]
     for t in clients:
         t.start()
+    # two more fields added while the clients' block solves run (the server's
+    # list of fields grows under the running slots), each then given a request
+    more = []
+    for k, d in enumerate(((4, 4, 4, 8), (4, 4, 8, 4))):
+        f2 = ctypes.c_int(-1)
+        U2 = synth.su3_links(d, 0.5, seed=5 + k)
+        assert lib.mbicg_server_add_field(srv, (ctypes.c_int * 4)(*d), _v(U2), ctypes.byref(p), 1,
+                                          ctypes.byref(f2)) == mb.MBICG_OK
+        more.append((d, f2.value))
     for t in clients:
         t.join()
+    for d, f2 in more:
+        B = synth.gaussian_source(d, 2, seed=60 + f2)
+        rid = ctypes.c_longlong(-1)
+        assert lib.mbicg_server_submit(srv, f2, _v(B), 2, KAPPA, 1e-4, ctypes.byref(rid)) == mb.MBICG_OK
+        X = np.empty_like(B)
+        tres = np.zeros(2)
+        rc2 = lib.mbicg_server_wait(srv, rid.value, _v(X), None, tres.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    None)
+        results.append((mb.MBICG_OK, rc2, float(tres.max())))
     lib.mbicg_server_destroy(srv)
     assert all(r[0] == mb.MBICG_OK and r[1] == mb.MBICG_OK and r[2] <= 1e-4 for r in results), results
     print(f"ok server ({time.perf_counter() - T0:.1f} s)", flush=True)

@@ -150,6 +150,36 @@ def test_concurrent_submitters(lib, oracle_mod):
         srv.close()
 
 
+def test_fields_added_while_slots_solve(lib, oracle_mod):
+    """Fields added while another field's block solves run (the server's list
+    of fields grows under the running slots): every request, before and after,
+    is solved on its own field (residual with the oracle's operator)."""
+    srv = Server(lib)
+    U1 = synth.su3_links(F1, 0.5, seed=1305)
+    try:
+        f1 = srv.add_field(F1, U1, 2)
+        B = [synth.gaussian_source(F1, 3, seed=1350 + i) for i in range(2)]
+        ids = [srv.submit(f1, b)[1] for b in B]
+        extra = []
+        for k, dims in enumerate((F2, (4, 4, 8, 4), (8, 4, 4, 4))):
+            U = synth.su3_links(dims, 0.5, seed=1306 + k)
+            extra.append((dims, U, srv.add_field(dims, U, 1)))
+        checks = [(rid, b, F1, U1) for rid, b in zip(ids, B)]
+        for dims, U, f in extra:
+            b = synth.gaussian_source(dims, 2, seed=1360 + f)
+            checks.append((srv.submit(f, b)[1], b, dims, U))
+        for rid, b, dims, U in checks:
+            rc, X, tres, info = srv.wait(rid, b)
+            assert rc == mb.MBICG_OK and tres.max() <= TOL
+            R = b - oracle_mod.apply_D(dims, U, KAPPA, X)
+            n = b.shape[3]
+            rel = np.linalg.norm(R.reshape(-1, n), axis=0) / np.linalg.norm(b.reshape(-1, n), axis=0)
+            assert rel.max() <= 1e-9
+        assert srv.stats()[3] == 5
+    finally:
+        srv.close()
+
+
 def test_server_argument_errors(lib):
     srv = Server(lib)
     try:
