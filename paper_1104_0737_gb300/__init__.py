@@ -144,6 +144,27 @@ def _ptr(a, name: str):
     return ctypes.c_void_p(a.ctypes.data), a.size
 
 
+def _need(ctx, name: str, have: int, per_site: int) -> None:
+    """Refuses, before the call, a block or field with fewer complex numbers
+    than the context's lattice needs (per_site per site): the library reads
+    and writes the full size through the pointer, past the end of a shorter
+    buffer.  Skipped for a context without recorded extents."""
+    dims = getattr(ctx, "dims", None)
+    if dims is None:
+        return
+    V = 1
+    for d in dims:
+        V *= d
+    if have < V * per_site:
+        raise MbicgError(MBICG_EINVAL, f"{name}: {have} complex numbers, the lattice needs {V * per_site}")
+
+
+def _columns_ok(L) -> bool:
+    """L within the library's range: only then are block sizes checked here
+    (the library itself refuses other L)."""
+    return 1 <= int(L) <= 16
+
+
 def _check(ctx, status: int, allowed=(MBICG_OK,)):
     if status not in allowed:
         raise MbicgError(status, mbicg_last_error(ctx))
@@ -186,13 +207,17 @@ def mbicg_last_error(ctx) -> str:
 
 
 def mbicg_load_gauge(ctx, U) -> None:
-    p, _ = _ptr(U, "U")
+    p, n = _ptr(U, "U")
+    _need(ctx, "U", n, 36)
     _check(ctx, load_library().mbicg_load_gauge(ctx, p))
 
 
 def mbicg_apply_D(ctx, inp, out, L: int, kappa: float, prec: int = MBICG_FP64) -> None:
-    pi, _ = _ptr(inp, "in")
-    po, _ = _ptr(out, "out")
+    pi, ni = _ptr(inp, "in")
+    po, no = _ptr(out, "out")
+    if _columns_ok(L):
+        _need(ctx, "in", ni, 12 * int(L))
+        _need(ctx, "out", no, 12 * int(L))
     _check(ctx, load_library().mbicg_apply_D(ctx, pi, po, int(L), float(kappa), int(prec)))
 
 
@@ -201,14 +226,20 @@ def mbicg_load_clover(ctx, csw: float) -> None:
 
 
 def mbicg_apply_clover(ctx, inp, out, L: int, kappa: float, prec: int = MBICG_FP64, jacobi: int = 0) -> None:
-    pi, _ = _ptr(inp, "in")
-    po, _ = _ptr(out, "out")
+    pi, ni = _ptr(inp, "in")
+    po, no = _ptr(out, "out")
+    if _columns_ok(L):
+        _need(ctx, "in", ni, 12 * int(L))
+        _need(ctx, "out", no, 12 * int(L))
     _check(ctx, load_library().mbicg_apply_clover(ctx, pi, po, int(L), float(kappa), int(prec), int(jacobi)))
 
 
 def mbicg_sap_precond(ctx, inp, out, L: int, kappa: float, params: mbicg_params) -> None:
-    pi, _ = _ptr(inp, "in")
-    po, _ = _ptr(out, "out")
+    pi, ni = _ptr(inp, "in")
+    po, no = _ptr(out, "out")
+    if _columns_ok(L):
+        _need(ctx, "in", ni, 12 * int(L))
+        _need(ctx, "out", no, 12 * int(L))
     _check(ctx, load_library().mbicg_sap_precond(ctx, pi, po, int(L), float(kappa),
                                                  ctypes.byref(params)))
 
@@ -227,8 +258,11 @@ def mbicg_sap_precond_frozen(ctx, inp, out, L: int, kappa: float, params: mbicg_
     sweeps use is set."""
     import numpy as np
 
-    pi, _ = _ptr(inp, "in")
-    po, _ = _ptr(out, "out")
+    pi, ni = _ptr(inp, "in")
+    po, no = _ptr(out, "out")
+    if _columns_ok(L):
+        _need(ctx, "in", ni, 12 * int(L))
+        _need(ctx, "out", no, 12 * int(L))
     n = mbicg_sap_table_len(ctx, params)
     if (not isinstance(table, np.ndarray) or table.dtype != np.complex128 or not table.flags.c_contiguous
             or 2 * table.size != n):
@@ -244,8 +278,11 @@ def mbicg_block_solve(ctx, B, X, L: int, kappa: float, tol: float, params: mbicg
     """Returns (status, iters, true_res list).  MBICG_ENOTCONV and
     MBICG_EBREAKDOWN are returned (X and true_res are filled); every other
     failure raises MbicgError."""
-    pb, _ = _ptr(B, "B")
-    px, _ = _ptr(X, "X")
+    pb, nb = _ptr(B, "B")
+    px, nx = _ptr(X, "X")
+    if _columns_ok(L):
+        _need(ctx, "B", nb, 12 * int(L))
+        _need(ctx, "X", nx, 12 * int(L))
     iters = ctypes.c_int(0)
     tres = (ctypes.c_double * max(1, int(L)))()
     st = load_library().mbicg_block_solve(ctx, pb, px, int(L), float(kappa), float(tol),
@@ -320,6 +357,10 @@ def mbicg_server_create(device: int = 0, hbm_budget_gb: float = 100.0):
     st = load_library().mbicg_server_create(ctypes.byref(srv), int(device), float(hbm_budget_gb))
     if st != MBICG_OK:
         raise MbicgError(st, "mbicg_server_create failed")
+    # sites per field and complex numbers per request, for the size checks of
+    # submit and wait (the library copies the full block through the pointer)
+    srv.field_sites = {}
+    srv.request_size = {}
     return srv
 
 
@@ -327,22 +368,38 @@ def mbicg_server_add_field(server, dims, U, params: mbicg_params, max_slots: int
     """Makes the gauge field U (host numpy) resident with up to max_slots
     solver slots; returns its field id."""
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    V = 1
+    for x in dims:
+        V *= int(x)
+    pu = _host(U, "U")
+    if U.size < 36 * V:
+        raise MbicgError(MBICG_EINVAL, f"mbicg_server_add_field: U has {U.size} complex numbers, "
+                                       f"the lattice needs {36 * V}")
     fid = ctypes.c_int(-1)
-    st = load_library().mbicg_server_add_field(server, d, _host(U, "U"), ctypes.byref(params),
+    st = load_library().mbicg_server_add_field(server, d, pu, ctypes.byref(params),
                                                int(max_slots), ctypes.byref(fid))
     if st != MBICG_OK:
         raise MbicgError(st, "mbicg_server_add_field failed (HBM budget, bad dims or a CUDA error)")
+    if hasattr(server, "field_sites"):
+        server.field_sites[fid.value] = V
     return fid.value
 
 
 def mbicg_server_submit(server, field: int, B, L: int, kappa: float, tol: float) -> int:
     """Queues A X = B (host numpy, L columns, copied now); returns the request id."""
     rid = ctypes.c_longlong(0)
-    st = load_library().mbicg_server_submit(server, int(field), _host(B, "B"), int(L), float(kappa),
+    pb = _host(B, "B")
+    V = getattr(server, "field_sites", {}).get(int(field))
+    if V is not None and 1 <= int(L) <= 12 and B.size < 12 * V * int(L):
+        raise MbicgError(MBICG_EINVAL, f"mbicg_server_submit: B has {B.size} complex numbers, "
+                                       f"{L} columns need {12 * V * int(L)}")
+    st = load_library().mbicg_server_submit(server, int(field), pb, int(L), float(kappa),
                                             float(tol), ctypes.byref(rid))
     if st != MBICG_OK:
         raise MbicgError(st, "mbicg_server_submit: unknown field, L outside 1..12, tol <= 0, or a block "
                              "that can never fit in the memory budget")
+    if V is not None:
+        server.request_size[rid.value] = (12 * V * int(L), int(L))
     return rid.value
 
 
@@ -352,8 +409,15 @@ def mbicg_server_wait(server, request_id: int, X, L: int):
     it = ctypes.c_int(0)
     tres = (ctypes.c_double * max(1, int(L)))()
     info = mbicg_request_info()
-    st = load_library().mbicg_server_wait(server, int(request_id), _host(X, "X"), ctypes.byref(it), tres,
+    px = _host(X, "X")
+    known = getattr(server, "request_size", {}).get(int(request_id))
+    if known is not None and (X.size < known[0] or int(L) != known[1]):
+        raise MbicgError(MBICG_EINVAL, f"mbicg_server_wait: the request has {known[1]} columns "
+                                       f"({known[0]} complex numbers); got L = {L} and X of {X.size}")
+    st = load_library().mbicg_server_wait(server, int(request_id), px, ctypes.byref(it), tres,
                                           ctypes.byref(info))
+    if known is not None and st != MBICG_EINVAL:
+        server.request_size.pop(int(request_id), None)
     if st not in (MBICG_OK, MBICG_ENOTCONV, MBICG_EBREAKDOWN):
         raise MbicgError(st, "mbicg_server_wait: unknown request or a failed block solve")
     return st, it.value, [tres[i] for i in range(int(L))], {k: getattr(info, k) for k, _ in info._fields_}
