@@ -66,6 +66,7 @@ struct Request {
   int status = 1, iters = 0, batch_cols = 0;
   double t_submit = 0, t_start = 0, t_done = 0;
   bool done = false;
+  bool claimed = false;  // a wait has taken it: any other wait for it is refused
 };
 
 struct Slot {
@@ -431,10 +432,11 @@ int mbicg_server_wait(mbicg_server* s, long long request_id, double* X, int* ite
   {
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->requests.find(request_id);
-    if (it == s->requests.end()) return MBICG_EINVAL;
+    if (it == s->requests.end() || it->second->claimed) return MBICG_EINVAL;
     r = it->second;
+    r->claimed = true;
     s->cv_done.wait(lk, [&] { return r->done; });
-    s->requests.erase(it);
+    s->requests.erase(request_id);
   }
   if (X) std::copy(r->X.begin(), r->X.end(), X);
   if (iters) *iters = r->iters;

@@ -180,6 +180,35 @@ def test_fields_added_while_slots_solve(lib, oracle_mod):
         srv.close()
 
 
+def test_one_wait_per_request(lib):
+    """Two host threads waiting for the same request: one gets the solution,
+    the other MBICG_EINVAL (whether it came while the first waited or after it
+    returned); a wait after that is refused too."""
+    srv = Server(lib)
+    try:
+        f = srv.add_field(F1, synth.su3_links(F1, 0.5, seed=1307), 1)
+        B = synth.gaussian_source(F1, 2, seed=1370)
+        rc, rid = srv.submit(f, B)
+        assert rc == mb.MBICG_OK
+        out = [None, None]
+
+        def waiter(i):
+            out[i] = srv.wait(rid, B)
+
+        threads = [threading.Thread(target=waiter, args=(i,)) for i in range(2)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        codes = sorted(o[0] for o in out)
+        assert codes == sorted([mb.MBICG_OK, mb.MBICG_EINVAL])
+        good = next(o for o in out if o[0] == mb.MBICG_OK)
+        assert good[2].max() <= TOL
+        assert srv.wait(rid, B)[0] == mb.MBICG_EINVAL
+    finally:
+        srv.close()
+
+
 def test_server_argument_errors(lib):
     srv = Server(lib)
     try:
