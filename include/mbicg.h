@@ -23,6 +23,7 @@
  * (cudaPointerGetAttributes).  Device pointers are used in place and the call
  * is ordered on the context's stream; host pointers are staged through device
  * buffers and the call returns after the result is back in host memory.
+ * Device memory of another device is refused (MBICG_EINVAL).
  * The caller owns every pointer it passes; the library owns the context, its
  * copies of the gauge field and its workspaces.
  *
@@ -407,7 +408,9 @@ int mbicg_server_submit(mbicg_server* server, int field_id, const double* B, int
 /* Blocks until the request is solved, then copies its columns of X (host,
  * caller owned, the request's L columns), the iterations of its block solve,
  * its true residuals (L doubles) and its timings (each may be NULL), forgets
- * the request and returns the status of its block solve. */
+ * the request and returns the status of its block solve.  One wait per
+ * request: another wait for it, while the first waits or after it returned,
+ * gets MBICG_EINVAL. */
 int mbicg_server_wait(mbicg_server* server, long long request_id, double* X, int* iters,
                       double* true_res, mbicg_request_info* info);
 

@@ -126,6 +126,17 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device that owns p when p is device memory (not managed memory, which
+// every device may reach), else -1.
+int owning_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return a.type == cudaMemoryTypeDevice ? a.device : -1;
+}
+
 // The device address of registered (page-locked, mapped) host memory, else
 // NULL (pageable memory, which no kernel may read).
 const void* mapped_host_ptr(const void* p) {
@@ -190,6 +201,10 @@ int stage_in(mbicg_ctx* c, const void* user, size_t bytes, const char* name, boo
   s->bytes = bytes;
   s->host = !is_device_ptr(user);
   if (!s->host) {
+    // the kernels read and write it directly: memory of another device would
+    // be a peer access that may not be enabled
+    const int d = owning_device(user);
+    if (d >= 0 && d != c->device) return fail(c, MBICG_EINVAL, "%s: device memory of another device", name);
     s->dev = const_cast<void*>(user);
     return MBICG_OK;
   }

@@ -81,6 +81,7 @@ def load(so):
     lb.mbicg_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip]
     lb.cudaMalloc.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t]
     lb.cudaFree.argtypes = [vp]
+    lb.emu_set_owner.argtypes = [vp, ctypes.c_int]
     return lb
 
 

@@ -22,6 +22,12 @@ int emu_bad_access = 0;
 namespace {
 std::mutex mu;
 std::map<const char*, size_t> device_allocs, host_allocs;
+std::map<const char*, int> owners;  // device allocations of a device other than 0
+int owner_of(const void* p) {
+  std::lock_guard<std::mutex> g(mu);
+  auto it = owners.find(static_cast<const char*>(p));
+  return it == owners.end() ? 0 : it->second;
+}
 int kind_of(const void* p) {  // 2 device, 1 pinned host, 0 other
   std::lock_guard<std::mutex> g(mu);
   const char* c = static_cast<const char*>(p);
@@ -53,6 +59,7 @@ void release(void* p, std::map<const char*, size_t>& m) {
   {
     std::lock_guard<std::mutex> g(mu);
     m.erase(static_cast<const char*>(p));
+    owners.erase(static_cast<const char*>(p));
   }
   free(p);
 }
@@ -125,7 +132,14 @@ cudaError_t cudaPointerGetAttributes(struct cudaPointerAttributes* a, const void
   // unified addressing: registered host memory is mapped at its own address
   a->devicePointer = k >= 1 ? const_cast<void*>(p) : nullptr;
   a->hostPointer = k != 2 ? const_cast<void*>(p) : nullptr;
+  a->device = k == 2 ? owner_of(p) : 0;
   return cudaSuccess;
+}
+// Test hook (no CUDA counterpart): the emulated device allocation at p is
+// reported as memory of `device`.
+void emu_set_owner(const void* p, int device) {
+  std::lock_guard<std::mutex> g(mu);
+  owners[static_cast<const char*>(p)] = device;
 }
 cudaError_t cudaGetLastError(void) { return cudaSuccess; }
 cudaError_t cudaPeekAtLastError(void) { return cudaSuccess; }

@@ -219,6 +219,37 @@ def test_noalloc_operator(lib, ctx):
         lib.cudaFree(dU)
 
 
+def test_memory_of_another_device_refused(lib, ctx):
+    """Device memory that belongs to another device than the context's (the
+    emulated runtime reports a buffer as device 1's) is refused with
+    MBICG_EINVAL by the operator, the block solve and the allocation-free
+    operator: their kernels would read it directly.  The same buffer reported
+    as the context's device is accepted."""
+    c, U = ctx
+    psi = synth.gaussian_source(DIMS, 1, seed=2006)
+    d_in = _device_copy(lib, psi)
+    d_out = _device_copy(lib, np.zeros_like(psi))
+    dU = _device_copy(lib, U)
+    dims = (ctypes.c_int * 4)(*DIMS)
+    p = _params(lib)
+    it = ctypes.c_int(0)
+    tres = np.zeros(1)
+    try:
+        lib.emu_set_owner(d_in, 1)
+        assert lib.mbicg_apply_D(c, d_in, d_out, 1, KAPPA, mb.MBICG_FP64) == mb.MBICG_EINVAL
+        assert b"another device" in lib.mbicg_last_error(c)
+        assert lib.mbicg_block_solve(c, d_in, d_out, 1, KAPPA, 1e-10, ctypes.byref(p), ctypes.byref(it),
+                                     tres.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == mb.MBICG_EINVAL
+        assert lib.mbicg_apply_D_noalloc(dims, dU, d_in, d_out, 1, KAPPA, None) == mb.MBICG_EINVAL
+        lib.emu_set_owner(d_in, 0)
+        assert lib.mbicg_apply_D(c, d_in, d_out, 1, KAPPA, mb.MBICG_FP64) == mb.MBICG_OK
+        lib.emu_set_owner(dU, 1)
+        assert lib.mbicg_apply_D_noalloc(dims, dU, d_in, d_out, 1, KAPPA, None) == mb.MBICG_EINVAL
+    finally:
+        for d in (d_in, d_out, dU):
+            lib.cudaFree(d)
+
+
 def test_bounded_wait_gives_up_and_the_library_goes_on(lib, ctx, oracle_mod):
     """mbicg_selftest_bounded_wait: a wait for bytes no copy delivers gives up
     (the emulated wait ends after 2 s; on the GPU after the spin limit) and the
