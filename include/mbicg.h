@@ -368,7 +368,9 @@ int mbicg_selftest_bounded_wait(int device, int spin_limit, int expect_bytes, in
  * request that would not fit); a slot keeps its workspace between solves;
  * when a slot cannot admit even its oldest request, idle slots release their
  * workspaces, and if that is not enough it waits for a running solve to
- * finish.  Requests arriving while slots or memory are busy wait; the slots
+ * finish; when no solve is running, the request can never be admitted (fields
+ * added after its submission took the budget) and its wait returns
+ * MBICG_ENOMEM.  Requests arriving while slots or memory are busy wait; the slots
  * of different fields, and the slots of one field, solve concurrently.
  * Thread-safe: submit and wait may be called from any host threads, and a
  * field may be added while the slots of others are solving (calls adding

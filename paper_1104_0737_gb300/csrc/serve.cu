@@ -17,7 +17,9 @@
 // at the request that would not fit.  A slot keeps its workspace between
 // solves (charged while held); when a slot cannot admit even the oldest
 // request, idle slots give their workspaces back, and if that is not enough
-// it waits for a running solve to finish.  Slots of different fields, and
+// it waits for a running solve to finish; with no solve running, the request
+// can never be admitted (fields added after it took the budget) and ends with
+// MBICG_ENOMEM.  Slots of different fields, and
 // several slots of one field, run their solves concurrently on the device.
 #include <algorithm>
 #include <chrono>
@@ -291,13 +293,35 @@ void worker(mbicg_server* s, Slot* sl) {
         // back (their threads wait for the lock, so their contexts are not in
         // use), then, if that was not enough, wait for a running solve
         ++s->mem_waits;
-        bool freed = false;
-        for (Slot* o : s->slots)
+        bool freed = false, running = false;
+        for (Slot* o : s->slots) {
+          running = running || o->busy;
           if (o != sl && !o->busy && o->held > 0) {
             release_slot_workspace(s, o);
             freed = true;
           }
-        if (!freed) s->cv_done.wait(lk);
+        }
+        if (freed) continue;
+        if (running) {
+          s->cv_done.wait(lk);
+          continue;
+        }
+        // nothing runs and no idle slot holds memory, yet the oldest request
+        // of this field does not fit: fields added after it was submitted
+        // took the budget, and it can never be admitted.  It ends with
+        // MBICG_ENOMEM.
+        for (auto it = s->pending.begin(); it != s->pending.end(); ++it)
+          if ((*it)->field == sl->field) {
+            Request* r = *it;
+            s->pending.erase(it);
+            r->X.assign(2 * (size_t)sl->V * 12 * r->L, 0.0);
+            r->tres.assign(r->L, 0.0);
+            r->status = MBICG_ENOMEM;
+            r->t_start = r->t_done = now_ms();
+            r->done = true;
+            break;
+          }
+        s->cv_done.notify_all();
       }
       sl->busy = true;
     }

@@ -75,6 +75,7 @@ def load(so):
     lb.mbicg_server_submit.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, llp]
     lb.mbicg_server_wait.argtypes = [vp, ctypes.c_longlong, vp, ip, dp, ctypes.POINTER(mb.mbicg_request_info)]
     lb.mbicg_server_hold.argtypes = [vp, ctypes.c_int]
+    lb.mbicg_server_memory.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), llp]
     lb.mbicg_server_stats.argtypes = [vp, llp, llp, llp, ip]
     lb.mbicg_server_destroy.argtypes = [vp]
     lb.mbicg_apply_D_noalloc.argtypes = [ip, vp, vp, vp, ctypes.c_int, ctypes.c_double, vp]

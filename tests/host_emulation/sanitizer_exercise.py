@@ -211,6 +211,53 @@ def main(so, sanitizer):
         results.append((mb.MBICG_OK, rc2, float(tres.max())))
     lib.mbicg_server_destroy(srv)
     assert all(r[0] == mb.MBICG_OK and r[1] == mb.MBICG_OK and r[2] <= 1e-4 for r in results), results
+
+    # admission by memory: two slots, a budget for their links and one
+    # 2-column block solve; two requests of different kappas, so the second
+    # slot waits for memory and releases the idle slot's workspace
+    V = 4 ** 4
+    budget = 2 * (V * 1152 + (1 << 22)) + 1.5 * (1.05 * 12 * V * 2 * 176 + (8 << 20))
+    srv = ctypes.c_void_p()
+    assert lib.mbicg_server_create(ctypes.byref(srv), 0, budget / 1e9) == mb.MBICG_OK
+    fid = ctypes.c_int(-1)
+    assert lib.mbicg_server_add_field(srv, (ctypes.c_int * 4)(*dims), _v(U), ctypes.byref(p), 2,
+                                      ctypes.byref(fid)) == mb.MBICG_OK
+    assert lib.mbicg_server_hold(srv, 1) == mb.MBICG_OK
+    reqs = []
+    for k, kappa in enumerate((0.12, 0.125, 0.12)):
+        B = synth.gaussian_source(dims, 2, seed=70 + k)
+        rid = ctypes.c_longlong(-1)
+        assert lib.mbicg_server_submit(srv, fid.value, _v(B), 2, kappa, 1e-4, ctypes.byref(rid)) == mb.MBICG_OK
+        reqs.append((rid.value, B))
+    assert lib.mbicg_server_hold(srv, 0) == mb.MBICG_OK
+    for rid, B in reqs:
+        X = np.empty_like(B)
+        tres = np.zeros(2)
+        rc2 = lib.mbicg_server_wait(srv, rid, _v(X), None, tres.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    None)
+        assert rc2 == mb.MBICG_OK and tres.max() <= 1e-4, (rc2, tres)
+    lib.mbicg_server_destroy(srv)
+
+    # a request that a field added after its submission made unadmissible
+    # ends with MBICG_ENOMEM (no solve runs, no idle workspace to release)
+    d2 = (4, 4, 4, 8)
+    budget = (V * 1152 + (1 << 22)) + (2 * V * 1152 + (1 << 22)) + (1.05 * 12 * V * 2 * 176 + (8 << 20)) - 1e3
+    srv = ctypes.c_void_p()
+    assert lib.mbicg_server_create(ctypes.byref(srv), 0, budget / 1e9) == mb.MBICG_OK
+    assert lib.mbicg_server_add_field(srv, (ctypes.c_int * 4)(*dims), _v(U), ctypes.byref(p), 1,
+                                      ctypes.byref(fid)) == mb.MBICG_OK
+    assert lib.mbicg_server_hold(srv, 1) == mb.MBICG_OK
+    B = synth.gaussian_source(dims, 2, seed=80)
+    rid = ctypes.c_longlong(-1)
+    assert lib.mbicg_server_submit(srv, fid.value, _v(B), 2, KAPPA, 1e-4, ctypes.byref(rid)) == mb.MBICG_OK
+    f2 = ctypes.c_int(-1)
+    U2 = synth.su3_links(d2, 0.5, seed=8)
+    assert lib.mbicg_server_add_field(srv, (ctypes.c_int * 4)(*d2), _v(U2), ctypes.byref(p), 1,
+                                      ctypes.byref(f2)) == mb.MBICG_OK
+    assert lib.mbicg_server_hold(srv, 0) == mb.MBICG_OK
+    X = np.empty_like(B)
+    assert lib.mbicg_server_wait(srv, rid.value, _v(X), None, None, None) == mb.MBICG_ENOMEM
+    lib.mbicg_server_destroy(srv)
     print(f"ok server ({time.perf_counter() - T0:.1f} s)", flush=True)
 
     # the 8-CTA cluster sweep over 4^4 domains, and an iteration or two of a

@@ -209,6 +209,83 @@ def test_one_wait_per_request(lib):
         srv.close()
 
 
+def _solve_bytes(V, L):
+    """The server's estimate of one block solve's workspace with the default
+    parameters (FP32 Krylov vectors and SAP storage) and the packing buffers:
+    12 V L (3*16 + 7*8 + 3*8 + 3*16) bytes, 5 % margin and 8 MiB."""
+    return 1.05 * 12 * V * L * (3 * 16 + 7 * 8 + 3 * 8 + 3 * 16) + (8 << 20)
+
+
+def test_admission_by_memory_budget(lib, oracle_mod):
+    """Two slots and a budget for their links and one 4-column block solve:
+    the slots never solve at once (the second waits for memory, idle slots
+    give their workspaces back), every request is solved on its own (kappas
+    differ, so nothing packs), and the memory held stays within the budget."""
+    V = int(np.prod(F1))
+    links = 2 * (V * 1152 + (1 << 22))
+    budget = links + 1.5 * _solve_bytes(V, 4)
+    s = ctypes.c_void_p()
+    assert lib.mbicg_server_create(ctypes.byref(s), 0, budget / 1e9) == mb.MBICG_OK
+    srv = Server.__new__(Server)
+    srv.lib, srv.s = lib, s
+    U = synth.su3_links(F1, 0.5, seed=1308)
+    try:
+        f = srv.add_field(F1, U, 2)
+        assert srv.stats()[3] == 2
+        kappas = (0.12, 0.121, 0.122, 0.123)  # all different: no two requests pack together
+        B = [synth.gaussian_source(F1, 4, seed=1380 + i) for i in range(4)]
+        assert lib.mbicg_server_hold(s, 1) == mb.MBICG_OK
+        ids = [srv.submit(f, b, kappa=k)[1] for b, k in zip(B, kappas)]
+        assert lib.mbicg_server_hold(s, 0) == mb.MBICG_OK
+        spans = []
+        for rid, b, k in zip(ids, B, kappas):
+            rc, X, tres, info = srv.wait(rid, b)
+            assert rc == mb.MBICG_OK and tres.max() <= TOL
+            R = b - oracle_mod.apply_D(F1, U, k, X)
+            rel = np.linalg.norm(R.reshape(-1, 4), axis=0) / np.linalg.norm(b.reshape(-1, 4), axis=0)
+            assert rel.max() <= 1e-9
+            spans.append((info.start_ms, info.done_ms))
+        spans.sort()
+        for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+            assert b0 >= a1  # one block solve at a time
+        used, cap, waits = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+        assert lib.mbicg_server_memory(s, ctypes.byref(used), ctypes.byref(cap), ctypes.byref(waits)) == 0
+        assert waits.value >= 1 and used.value * 1e9 <= budget
+    finally:
+        srv.close()
+
+
+def test_request_that_can_no_longer_fit_ends_with_enomem(lib):
+    """A request admitted at submit (its block fits beside the links held
+    then), after which a second field's links take the budget: with nothing
+    running and no idle workspace to release, it can never be admitted and its
+    wait returns MBICG_ENOMEM instead of waiting forever; a smaller request
+    that still fits is solved afterwards."""
+    V1, V2 = int(np.prod(F1)), int(np.prod(F2))
+    links = (V1 * 1152 + (1 << 22)) + (V2 * 1152 + (1 << 22))
+    budget = links + _solve_bytes(V1, 4) - 1e3
+    s = ctypes.c_void_p()
+    assert lib.mbicg_server_create(ctypes.byref(s), 0, budget / 1e9) == mb.MBICG_OK
+    srv = Server.__new__(Server)
+    srv.lib, srv.s = lib, s
+    try:
+        f1 = srv.add_field(F1, synth.su3_links(F1, 0.5, seed=1309), 1)
+        B4 = synth.gaussian_source(F1, 4, seed=1390)
+        assert lib.mbicg_server_hold(s, 1) == mb.MBICG_OK
+        rc, rid = srv.submit(f1, B4)
+        assert rc == mb.MBICG_OK
+        srv.add_field(F2, synth.su3_links(F2, 0.5, seed=1310), 1)
+        assert lib.mbicg_server_hold(s, 0) == mb.MBICG_OK
+        assert srv.wait(rid, B4)[0] == mb.MBICG_ENOMEM
+        B1 = synth.gaussian_source(F1, 1, seed=1391)
+        rc, rid = srv.submit(f1, B1)
+        assert rc == mb.MBICG_OK
+        rc, X, tres, info = srv.wait(rid, B1)
+        assert rc == mb.MBICG_OK and tres.max() <= TOL
+    finally:
+        srv.close()
+
+
 def test_server_argument_errors(lib):
     srv = Server(lib)
     try:
