@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import threading
 
 from . import _build
 
@@ -75,6 +76,7 @@ class mbicg_request_info(ctypes.Structure):
 
 
 _lib = None
+_lib_lock = threading.Lock()  # the first load (and build) happens once, whichever thread asks first
 
 
 def library_path() -> str:
@@ -86,6 +88,13 @@ def load_library(build_if_missing: bool = True):
     global _lib
     if _lib is not None:
         return _lib
+    with _lib_lock:
+        if _lib is None:
+            _lib = _load(build_if_missing)
+    return _lib
+
+
+def _load(build_if_missing: bool):
     if build_if_missing and _build.needs_build():
         _build.build()
     if not os.path.exists(_build.LIB):
@@ -125,7 +134,6 @@ def load_library(build_if_missing: bool = True):
     lib.mbicg_server_destroy.argtypes = [vp]
     lib.mbicg_server_destroy.restype = None
     lib.mbicg_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip]
-    _lib = lib
     return lib
 
 

@@ -123,3 +123,30 @@ def test_a_missing_library_fails_loudly(tmp_path, monkeypatch):
         mb.mbicg_create((4, 4, 4, 4))
     with pytest.raises(OSError):
         mb.mbicg_default_params()
+
+
+def test_first_loads_from_several_threads_build_once(monkeypatch):
+    """Host threads that make their first library call at the same time share
+    one load: the build step runs once, and every thread gets the same
+    library."""
+    import threading
+    import time
+
+    real = mb.load_library()
+    calls = []
+
+    def build():
+        calls.append(1)
+        time.sleep(0.2)  # a build takes a while: the other threads arrive meanwhile
+
+    monkeypatch.setattr(mb, "_lib", None)
+    monkeypatch.setattr(mb._build, "needs_build", lambda: not calls)
+    monkeypatch.setattr(mb._build, "build", build)
+    got = [None] * 4
+    threads = [threading.Thread(target=lambda i=i: got.__setitem__(i, mb.load_library())) for i in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert len(calls) == 1
+    assert all(g is got[0] for g in got) and got[0]._name == real._name
