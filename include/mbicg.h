@@ -410,9 +410,10 @@ int mbicg_server_submit(mbicg_server* server, int field_id, const double* B, int
 /* Blocks until the request is solved, then copies its columns of X (host,
  * caller owned, the request's L columns), the iterations of its block solve,
  * its true residuals (L doubles) and its timings (each may be NULL), forgets
- * the request and returns the status of its block solve.  One wait per
- * request: another wait for it, while the first waits or after it returned,
- * gets MBICG_EINVAL. */
+ * the request and returns the status of its block solve (MBICG_ENOMEM, with X
+ * zero, for a request that could never be admitted).  One wait per request:
+ * another wait for it, while the first waits or after it returned, gets
+ * MBICG_EINVAL. */
 int mbicg_server_wait(mbicg_server* server, long long request_id, double* X, int* iters,
                       double* true_res, mbicg_request_info* info);
 
